@@ -1,0 +1,75 @@
+"""Calibrate the distance threshold theta of the synthetic join workloads with the oracle.
+
+TEST INFRASTRUCTURE: run by hand (``python -m oracle.calibrate``) to (re)write
+``tests/golden/workloads.json``.  Only the oracle computes distances here.
+
+For a workload whose theta is meant to give about t S-matches per R node, theta is the
+median, over a sample of R nodes, of the distance from that node to its t-th nearest S
+node (the oracle's k-closest-pairs search with a single source and k = t).  The graph's
+edge count and weight sum are stored beside theta so a run can tell whether it
+regenerated the same graph.
+"""
+from __future__ import annotations
+
+import json
+import os
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+from oracle import oracle as O  # noqa: E402
+from paper_1607_07696_gb300 import inputs as I  # noqa: E402
+
+OUT = os.path.join(ROOT, "tests", "golden", "workloads.json")
+
+
+def graph_digest(e: I.EdgeList) -> dict:
+    return {"n": int(e.n), "m": int(e.m), "wsum": int(e.w.astype(np.uint64).sum()),
+            "xsum": int((e.src.astype(np.uint64) * 3 + e.dst.astype(np.uint64)).sum())}
+
+
+def theta_for_matches(g: O.OGraph, R, S, t: int, sample: int) -> tuple[int, list[int]]:
+    ds = []
+    for u in list(R[:sample]):
+        p = g.kcp([int(u)], S, t)
+        if len(p) == t:
+            ds.append(int(p.d[-1]))
+    return int(np.median(ds)), ds
+
+
+def main() -> None:
+    o = O.default()
+    out = {}
+    t0 = time.time()
+    w = I.c1_grid_join()
+    out["grid4096_theta1500"] = {"theta": 1500, "graph": graph_digest(w.graph)}
+
+    w = I.c2_road_join(None)
+    g = o.graph(w.graph.n, w.graph.src, w.graph.dst, w.graph.w)
+    th, _ = theta_for_matches(g, w.R, w.S, 50, 256)
+    out["road264k_join"] = {"theta": th, "matches_per_u": 50, "sample": 256,
+                            "graph": graph_digest(w.graph)}
+    print("road264k_join theta", th, f"{time.time() - t0:.1f}s", flush=True)
+
+    w = I.c3_road_clustered()
+    g = o.graph(w.graph.n, w.graph.src, w.graph.dst, w.graph.w)
+    th, _ = theta_for_matches(g, w.R, w.S, 50, 256)
+    out["road1070k_clustered"] = {"theta_join": th, "matches_per_u": 50, "sample": 256,
+                                  "k": [100, 10_000, 1_000_000], "graph": graph_digest(w.graph)}
+    print("road1070k_clustered theta", th, f"{time.time() - t0:.1f}s", flush=True)
+
+    os.makedirs(os.path.dirname(OUT), exist_ok=True)
+    old = json.load(open(OUT)) if os.path.exists(OUT) else {}
+    old.update(out)
+    with open(OUT, "w") as f:
+        json.dump(old, f, indent=1, sort_keys=True)
+        f.write("\n")
+
+
+if __name__ == "__main__":
+    main()

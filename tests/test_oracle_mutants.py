@@ -1,0 +1,82 @@
+"""Plant plausible mistakes in the CPU oracle and check the pin suite catches each one.
+
+Every mutant is the oracle's C source with one small textual change (a flipped
+comparison, a dropped term, swapped operands), compiled on the CPU into a temporary
+library.  A mutant that passes every pin would mean the pins cannot see that kind of
+mistake, so the test fails.
+"""
+import os
+
+import pytest
+
+import pins
+from oracle import oracle as O
+
+MUTANTS = {
+    # the theta cut becomes exclusive (Abstract: dist <= theta is inclusive)
+    "strict_theta_cut": ("            if (nd > bound) continue;\n            if (nd < dist[y]) {\n"
+                         "                dist[y] = nd;\n                rc = heap_push(&h, nd, y);\n"
+                         "                if (rc) break;\n            }\n        }\n    }\n    /* nodes",
+                         "            if (nd >= bound) continue;\n            if (nd < dist[y]) {\n"
+                         "                dist[y] = nd;\n                rc = heap_push(&h, nd, y);\n"
+                         "                if (rc) break;\n            }\n        }\n    }\n    /* nodes"),
+    # parallel edges keep their largest weight instead of the least
+    "multi_edge_max": ("if (x->w != y->w) return x->w < y->w ? -1 : 1;",
+                       "if (x->w != y->w) return x->w > y->w ? -1 : 1;"),
+    # an undirected edge only one way
+    "one_way_edges": ("        if (undirected) {\n", "        if (0) {\n"),
+    # kCP tie-break (d, v, u) instead of (d, u, v)
+    "kcp_tiebreak_vu": ("    if (x->u != y->u) return x->u < y->u ? -1 : 1;\n    if (x->v != y->v) return x->v < y->v ? -1 : 1;\n    return 0;\n}\n\nvoid og_pairs_free",
+                        "    if (x->v != y->v) return x->v < y->v ? -1 : 1;\n    if (x->u != y->u) return x->u < y->u ? -1 : 1;\n    return 0;\n}\n\nvoid og_pairs_free"),
+    # kCP keeps the worse candidate
+    "kcp_keep_worse": ("} else if (trip_less(&c, &h->a[0])) {", "} else if (trip_less(&h->a[0], &c)) {"),
+    # kCP tightens its bound before k pairs are held
+    "kcp_early_bound": ("            if (kh.len == kh.k && kh.a[0].d < bound) bound = kh.a[0].d;\n            if (it.key > bound) break;",
+                        "            if (kh.len > 0 && kh.a[0].d < bound) bound = kh.a[0].d;\n            if (it.key > bound) break;"),
+    # kCP prunes ties at the bound
+    "kcp_prune_ties": ("            if (it.key > bound) break;\n            done[it.node] = 1;\n            out->arcs",
+                       "            if (it.key >= bound && kh.len == kh.k) break;\n            done[it.node] = 1;\n            out->arcs"),
+    # heap pops the larger child: not a min-heap any more
+    "heap_wrong_child": ("if (c + 1 < h->len && h->a[c + 1].key < h->a[c].key) c++;",
+                         "if (c + 1 < h->len && h->a[c + 1].key > h->a[c].key) c++;"),
+    # a relaxation that forgets the arc weight
+    "dropped_weight": ("            uint64_t nd = it.key + g->w[e];\n            uint32_t y = g->to[e];\n            if (nd > bound) continue;\n            if (nd < dist[y]) {\n                dist[y] = nd;\n                rc = heap_push(&h, nd, y);\n                if (rc) break;\n            }\n        }\n    }\n    /* nodes",
+                       "            uint64_t nd = it.key + 1;\n            uint32_t y = g->to[e];\n            if (nd > bound) continue;\n            if (nd < dist[y]) {\n                dist[y] = nd;\n                rc = heap_push(&h, nd, y);\n                if (rc) break;\n            }\n        }\n    }\n    /* nodes"),
+    # the join sorted (v, u)
+    "join_sorted_vu": ("        qsort(t, n, sizeof(og_triple), cmp_uv);", "        qsort(t, n, sizeof(og_triple), cmp_duv);"),
+    # overlap of R and S no longer rejected
+    "overlap_accepted": ("        if (S[i] >= n || mark[S[i]]) { free(mark); return OG_EINVAL; }",
+                         "        if (S[i] >= n || mark[S[i]] == 2) { free(mark); return OG_EINVAL; }"),
+    # emits a pair for every reached node, not only members of S
+    "emit_non_members": ("            if (!inS[x] || dist[x] == OG_INF) continue;",
+                         "            if (dist[x] == OG_INF) continue;"),
+    # Floyd-Warshall with the intermediate loop in the middle
+    "fw_loop_order": ("    for (uint32_t m = 0; m < n; m++)\n        for (uint32_t i = 0; i < n; i++) {",
+                      "    for (uint32_t i = 0; i < n; i++)\n        for (uint32_t m = 0; m < n; m++) {"),
+}
+
+
+def _run_pins(o):
+    failures = []
+    for pin in pins.ALL_PINS:
+        try:
+            pin(o)
+        except Exception as e:  # a crash or a wrong answer both count as caught
+            failures.append(f"{pin.__name__}: {e}")
+    return failures
+
+
+@pytest.mark.parametrize("name", sorted(MUTANTS))
+def test_mutant_is_caught(name, tmp_path):
+    src = open(O.SRC).read()
+    old, new = MUTANTS[name]
+    assert src.count(old) == 1, f"mutation site for {name} not found exactly once"
+    msrc = tmp_path / f"{name}.c"
+    msrc.write_text(src.replace(old, new))
+    lib = O.build(str(msrc), str(tmp_path / f"lib{name}.so"))
+    failures = _run_pins(O.Oracle(lib))
+    assert failures, f"mutant {name} passed every pin"
+
+
+def test_real_oracle_passes_all(oracle):
+    assert _run_pins(oracle) == []
