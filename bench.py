@@ -1,0 +1,355 @@
+#!/usr/bin/env python
+"""Benchmark of the theta-join engine on the 264k-node road-like workload.
+
+One step = one whole query: validate R and S, build the S bitmap, sort R into tiles,
+search every tile (delta-stepping over the distance slab), emit the pairs within theta,
+sort them by (u, v).  The headline ``value`` is join pairs/s with R and S already in
+device memory (CUDA events on the query stream, L2 flushed between steps); ``e2e`` is
+the same metric through the host-buffer call, with the copies of R and S to the device
+and of the pairs back to the host inside the timed region.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl engine|reference]
+
+Under torchrun (N > 1) every rank joins its own R and S (same sizes, other seeds) over
+the same graph -- weak scaling with no collective on the data path; rank 0 prints the
+line, with the slowest rank's time.  ``--impl reference`` times the CPU oracle on the
+host (the paper publishes no code and no absolute numbers to compare against).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "join pairs/s"
+UNIT = "pairs/s"
+WORKLOADS = json.load(open(os.path.join(ROOT, "tests", "golden", "workloads.json")))
+ENGINE_SRC = os.path.join(ROOT, "paper_1607_07696_gb300", "csrc", "rn_engine.cu")
+PROFILE = os.path.join(ROOT, "profiles", "tile_search_road264k.json")
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="engine", choices=["engine", "reference"])
+    ap.add_argument("--workload", default="road264k_join",
+                    choices=["road264k_join", "grid4096_theta1500", "road1070k_join"])
+    ap.add_argument("--tile-width", type=int, default=0)
+    ap.add_argument("--delta", type=int, default=0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def make_workload(name: str, rank: int):
+    from paper_1607_07696_gb300 import inputs as I
+
+    if name == "road264k_join":
+        spec = WORKLOADS["road264k_join"]
+        w = I.c2_road_join(spec["theta"])
+        if rank:
+            w.R, w.S = I.disjoint_sets(w.graph.n, len(w.R), len(w.S), I.BASE_SEED + 1000 + 7919 * rank)
+        return w, spec
+    if name == "grid4096_theta1500":
+        spec = WORKLOADS["grid4096_theta1500"]
+        w = I.c1_grid_join()
+        if rank:
+            w.R, w.S = I.disjoint_sets(w.graph.n, len(w.R), len(w.S), I.BASE_SEED + 7919 * rank)
+        return w, spec
+    spec = dict(WORKLOADS["road1070k_clustered"])
+    w = I.c3_road_clustered(theta=spec["theta_join"])
+    spec["theta"] = spec["theta_join"]
+    return w, spec
+
+
+# ------------------------------------------------------------------ clocks ----
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons while the timed region runs."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines: list[str] = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *exc):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self) -> dict:
+        sm, mx, reasons = [], 0.0, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.lines:
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx = max(mx, float(f[2]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, f[5:9]):
+                if val.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx or None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ------------------------------------------------------------------ helpers ----
+
+def measured_peak_gbs():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        return float(json.load(open(p))["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def engine_hash() -> str:
+    return hashlib.sha256(open(ENGINE_SRC, "rb").read()).hexdigest()[:16]
+
+
+def profiled_traffic(workload: str):
+    """DRAM bytes per launch of the tile search from the committed ncu summary, or None
+    when there is none or the kernel source changed since it was taken."""
+    if not os.path.exists(PROFILE):
+        return None
+    p = json.load(open(PROFILE))
+    if p.get("workload") != workload or p.get("engine_sha") != engine_hash():
+        return None
+    return p.get("dram_bytes_per_launch")
+
+
+def cpu_baseline(w, spec, sample_sources: int = 1500) -> dict:
+    """The CPU oracle, as it stands, on the first sources of R (single thread)."""
+    from oracle import oracle as O
+
+    og = O.default().graph(w.graph.n, w.graph.src, w.graph.dst, w.graph.w)
+    R = w.R[:sample_sources]
+    t0 = time.perf_counter()
+    p = og.join(R, w.S, spec["theta"])
+    dt = time.perf_counter() - t0
+    return {"value": len(p) / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"{len(R)} of {len(w.R)} R sources against all {len(w.S)} S nodes, "
+                      f"theta {spec['theta']}, {dt:.1f} s, {len(p)} pairs"}
+
+
+# ------------------------------------------------------------------- engine ----
+
+def run_engine(args):
+    import numpy as np
+    import torch
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl")
+    from paper_1607_07696_gb300 import rn
+
+    if not os.path.exists(rn.LIB_PATH):
+        from paper_1607_07696_gb300 import build as B
+
+        B.build()
+    w, spec = make_workload(args.workload, rank)
+    e = w.graph
+    cfg = {"tile_width": args.tile_width, "delta": args.delta}
+    g = rn.rn_graph_load(e.src, e.dst, e.w, e.n, cfg=cfg)
+    info = rn.rn_graph_info(g)
+    stream = torch.cuda.Stream()
+    dR = torch.as_tensor(w.R.astype(np.int32), device="cuda")
+    dS = torch.as_tensor(w.S.astype(np.int32), device="cuda")
+    out = rn.DevicePairs()
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")  # 256 MB > 129 MB L2
+    theta = spec["theta"]
+
+    def step():
+        return rn.rn_distance_join_dev(g, dR, dS, theta, out, stream)
+
+    with torch.cuda.stream(stream):
+        for _ in range(args.warmup):
+            step()
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    times, search_ms, stats = [], [], None
+    with ClockSampler(local) as clk:
+        for i in range(args.steps):
+            with torch.cuda.stream(stream):
+                flush.fill_(i & 0xFF)
+                a = torch.cuda.Event(enable_timing=True)
+                b = torch.cuda.Event(enable_timing=True)
+                a.record(stream)
+                npairs = step()
+                b.record(stream)
+            b.synchronize()
+            times.append(a.elapsed_time(b))
+            stats = rn.rn_last_query_stats()
+            search_ms.append(stats["search_ms"])
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    total_ms = sum(times)
+    pairs_all = npairs
+    if dist:
+        t = torch.tensor([total_ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+        pc = torch.tensor([float(npairs)], device="cuda")
+        dist.all_reduce(pc, op=dist.ReduceOp.SUM)
+        pairs_all = int(pc.item())
+    value = pairs_all * args.steps / (total_ms / 1e3)
+
+    # end to end through the host-buffer call: R, S in pinned memory, pairs to the host
+    Rh = torch.as_tensor(w.R.astype(np.int32)).pin_memory().numpy()
+    Sh = torch.as_tensor(w.S.astype(np.int32)).pin_memory().numpy()
+    rn.rn_distance_join(g, Rh, Sh, theta)  # warm the host path's buffers
+    e2e_t = []
+    for i in range(max(3, args.steps // 2)):
+        flush.fill_(i & 0xFF)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        u, v, d = rn.rn_distance_join(g, Rh, Sh, theta)
+        e2e_t.append(time.perf_counter() - t0)
+    e2e_value = len(u) / statistics.median(e2e_t)
+    assert len(u) == npairs
+
+    if rank != 0:
+        if dist:
+            dist.destroy_process_group()
+        return
+    T = stats["tile_width"]
+    alg_bytes = (8 * stats["slots"] + 8 * stats["slot_arcs"] + 8 * T * stats["slots"]
+                 + stats["slots"] / 8 + 12 * npairs)
+    smean = statistics.mean(search_ms)
+    achieved = alg_bytes / (smean / 1e3) / 1e9
+    peak, peak_kind = measured_peak_gbs()
+    line = {
+        "metric": METRIC,
+        "value": value,
+        "unit": UNIT,
+        "n_gpus": world,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": total_ms / args.steps,
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "u32",
+        "data": "synthetic",
+        "config": {
+            "workload": args.workload,
+            "n": e.n, "m": e.m, "nR": len(w.R), "nS": len(w.S), "theta": theta,
+            "pairs": npairs, "tile_width": T, "delta": stats["delta"],
+            "parallelism": f"replicas x{world}" if world > 1 else "1 GPU",
+            "l2": "flushed between steps (256 MB write outside the timed events)",
+        },
+        "gteps": (spec.get("alg_arcs", 0) / (total_ms / args.steps / 1e3) / 1e9) if spec.get("alg_arcs") else None,
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 4 * (len(w.R) + len(w.S)),
+                "d2h_bytes_per_step": 12 * npairs},
+        "gpu_launches": int(stats["launches"]) * args.steps,
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "traffic": profiled_traffic(args.workload),
+                     "kernel": "k_tile_search", "peak_kind": peak_kind,
+                     "search_ms": smean, "alg_bytes_per_launch": alg_bytes},
+        "clocks": clk.summary(),
+        "engine": {"reorder_ms": info["reorder_ms"], "slots": stats["slots"],
+                   "slot_arcs": stats["slot_arcs"], "scans": stats["scans"],
+                   "retried_tiles": stats["retried_tiles"], "device_ms": stats["device_ms"]},
+    }
+    if not args.no_cpu_baseline and world == 1:
+        line["cpu_baseline"] = cpu_baseline(w, spec)
+    print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
+# ---------------------------------------------------------------- reference ----
+
+def run_reference(args):
+    """The CPU oracle timed on the host cores, on bounded samples of the same workload."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    from oracle import oracle as O
+
+    w, spec = make_workload(args.workload, 0)
+    og = O.default().graph(w.graph.n, w.graph.src, w.graph.dst, w.graph.w)
+    per_step = 400
+    theta = spec["theta"]
+    nR = len(w.R)
+    for i in range(args.warmup):
+        og.join(w.R[:50], w.S, theta)
+    total_pairs, total_s = 0, 0.0
+    for i in range(args.steps):
+        lo = (i * per_step) % max(1, nR - per_step)
+        R = w.R[lo:lo + per_step]
+        t0 = time.perf_counter()
+        p = og.join(R, w.S, theta)
+        total_s += time.perf_counter() - t0
+        total_pairs += len(p)
+    value = total_pairs / total_s
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1e3 * total_s / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+        "impl": "reference",
+        "config": {"workload": args.workload, "n": w.graph.n, "m": w.graph.m, "nR": nR,
+                   "nS": len(w.S), "theta": theta},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": f"each step: {per_step} of {nR} R sources against all "
+                                   f"{len(w.S)} S nodes"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_engine(args)
+
+
+if __name__ == "__main__":
+    main()

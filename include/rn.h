@@ -1,0 +1,199 @@
+/*
+ * rn.h -- C ABI of the GB300 road-network distance-join engine.
+ *
+ * The engine answers the two queries of Tsatsanifos, "Parallelized Proximity-Based
+ * Query Processing Methods for Road Networks" (2016), over a graph it keeps resident
+ * in GPU memory:
+ *
+ *   distance join   all pairs (u in R, v in S) with network distance dist(u,v) <= theta
+ *                   (Abstract; Section 1; Section 4, the distance predicate theta);
+ *   k closest pairs the k pairs (u in R, v in S) of least network distance, none of
+ *                   them farther than theta (Abstract; Section 1; Section 4, where the
+ *                   single interface takes both k and theta, Algorithm 2).
+ *
+ * Conventions shared by every call:
+ *   - Node ids are the caller's ids, 0 .. n-1.  R and S are sets: no id twice, and no id
+ *     in both (Abstract: two disjoint sets).  Violations return RN_EINVAL.
+ *   - Weights are integers in [1, 2^24); distances are exact unsigned integers.
+ *   - theta is an integer in [0, 2^31], or RN_INF meaning "no bound", which the engine
+ *     treats as 2^31: pairs farther apart than 2^31 are never reported.  A path is cut
+ *     only when its cost is greater than theta, so theta itself is included (Algorithm 4
+ *     returns when a path cost exceeds the threshold).
+ *   - Results are exact and deterministic: a join is sorted by (u, v); k closest pairs
+ *     are sorted by (d, u, v), which also breaks ties at the k-th distance.
+ *   - Every call returns an rn_status.  No C++ exception crosses this boundary.  On
+ *     failure rn_last_error() gives a message for the calling thread.
+ *   - Host arrays passed in are read only and may be freed when the call returns.
+ *     Results in rn_pairs are host memory owned by the library: free with
+ *     rn_pairs_free.  Results in rn_dpairs are device memory owned by the library:
+ *     free with rn_dpairs_free (a struct may be reused across calls; its buffers grow
+ *     as needed).
+ *   - A graph serialises the queries issued on it (an internal mutex); queries on
+ *     different graphs may run concurrently from different host threads.
+ */
+#ifndef RN_H
+#define RN_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    RN_OK = 0,
+    RN_EINVAL = 1,      /* bad argument: id >= n, repeated id, R and S overlap, theta > 2^31,
+                           k = 0, weight outside [1, 2^24), unknown flag */
+    RN_ENOMEM = 2,      /* host or device allocation failed */
+    RN_ECUDA = 3,       /* a CUDA call failed; rn_last_error() names it */
+    RN_ETIMEOUT = 4,    /* a bounded wait ran out (serving) */
+    RN_ECANCELLED = 5,  /* the query was cancelled (serving) */
+    RN_EBUSY = 6,       /* no admission slot free right now (serving) */
+    RN_EINTERNAL = 7,   /* an internal invariant failed (a bug: please report) */
+    RN_ENOTIMPL = 8     /* the requested feature is not built */
+} rn_status;
+
+#define RN_UNDIRECTED 1u    /* every edge (a, b, w) is also an edge (b, a, w) */
+#define RN_REORDER 2u       /* relabel nodes by recursive bisection for locality */
+#define RN_INF 0xFFFFFFFFu  /* theta: no bound (treated as RN_THETA_MAX) */
+#define RN_THETA_MAX 0x80000000u
+#define RN_WEIGHT_LIMIT 0x01000000u /* weights must be < 2^24 */
+
+/* An opaque graph resident in GPU memory. */
+typedef struct rn_graph rn_graph;
+
+/* cudaStream_t without the CUDA headers; NULL means the legacy default stream. */
+typedef struct CUstream_st *rn_stream;
+
+/* Result pairs in host memory, struct-of-arrays, n entries each. */
+typedef struct {
+    uint32_t *u;
+    uint32_t *v;
+    uint32_t *d;
+    uint64_t n;
+} rn_pairs;
+
+/* Result pairs in device memory, struct-of-arrays; cap = allocated entries. */
+typedef struct {
+    uint32_t *u;
+    uint32_t *v;
+    uint32_t *d;
+    uint64_t n;
+    uint64_t cap;
+} rn_dpairs;
+
+/* Engine knobs.  Zero in any field means "choose automatically". */
+typedef struct {
+    uint32_t tile_width;  /* sources searched together by one thread block: 32, 64 or 128 */
+    uint32_t delta;       /* bucket width of the delta-stepping search, in weight units */
+    uint32_t leaf_size;   /* recursive-bisection leaf size used by RN_REORDER */
+    float alpha;          /* smoothing parameter of the bisection (Eq. 1-2), in [0, 1];
+                             negative selects the default, 0.5 */
+} rn_config;
+
+/* Graph facts, filled by rn_graph_info. */
+typedef struct {
+    uint32_t n;
+    uint64_t arcs;          /* directed arcs after cleaning (2 per undirected edge) */
+    uint32_t max_degree;
+    uint32_t median_weight;
+    uint32_t flags;
+    double reorder_ms;      /* host time spent on the recursive bisection */
+    uint64_t device_bytes;  /* device memory held by the graph and its workspace */
+} rn_graph_stats;
+
+/* Counters of the calling thread's last query (rn_last_query_stats). */
+typedef struct {
+    uint64_t pairs;         /* pairs returned */
+    uint64_t tiles;         /* source tiles searched */
+    uint64_t retried_tiles; /* tiles searched again with a larger slab after an overflow */
+    uint64_t scans;         /* slab rows scanned (a node's arcs relaxed for a whole tile) */
+    uint32_t tile_width;
+    uint32_t delta;
+    uint32_t passes;        /* search passes (k closest pairs widens its radius by passes) */
+    uint32_t theta_final;   /* k closest pairs: the k-th distance found, else theta */
+    uint32_t launches;      /* kernels the query launched */
+    uint64_t slots;         /* sum over tiles of the nodes the tile reached (its union ball) */
+    uint64_t slot_arcs;     /* sum over tiles of the arcs leaving those nodes */
+    double device_ms;       /* device time of the query, CUDA events on its stream */
+    double search_ms;       /* device time of the first tile-search launch, CUDA events */
+} rn_query_stats;
+
+/*
+ * rn_graph_load -- build a graph from an edge list and upload it to the current GPU.
+ *   src, dst, w : m edges, host arrays, endpoints < n, weights in [1, 2^24).
+ *   flags       : RN_UNDIRECTED and/or RN_REORDER.
+ *   cfg         : may be NULL (defaults).
+ * Self-loops are dropped and parallel arcs keep their least weight (neither changes a
+ * distance).  With RN_REORDER the nodes are relabelled by the recursive two-seed
+ * bisection of Section 3 (Algorithm 1, smoothed by Eq. 1-2) so that every partition of
+ * the hierarchy is a contiguous id range; ids seen by the caller never change.
+ * Returns RN_EINVAL for a bad endpoint, weight or flag, RN_ENOMEM / RN_ECUDA otherwise.
+ */
+rn_status rn_graph_load(const uint32_t *src, const uint32_t *dst, const uint32_t *w, uint64_t m,
+                        uint32_t n, uint32_t flags, const rn_config *cfg, rn_graph **out);
+void rn_graph_free(rn_graph *g);
+rn_status rn_graph_info(const rn_graph *g, rn_graph_stats *out);
+/*
+ * rn_bisection_order -- the relabelling RN_REORDER applies, computed on the host alone
+ * (no GPU is touched): order[i] = the original id placed at internal id i, n entries,
+ * caller-allocated.  Recursive two-seed bisection (Section 3, Algorithm 1): two
+ * clusters grow from two far-apart seeds, each step extending the cluster whose
+ * horizon holds the lighter edge, the edge weights smoothed by the relative cluster
+ * populations with parameter cfg->alpha (Eq. 1-2); parts of at most cfg->leaf_size
+ * nodes (default 512) are leaves.  Same arguments and errors as rn_graph_load.
+ */
+rn_status rn_bisection_order(const uint32_t *src, const uint32_t *dst, const uint32_t *w, uint64_t m,
+                             uint32_t n, uint32_t flags, const rn_config *cfg, uint32_t *order);
+/* Copy the relabelling out: perm[orig] = internal id (n entries). */
+rn_status rn_graph_permutation(const rn_graph *g, uint32_t *perm);
+/* Change the knobs of later queries (tile_width, delta); NULL restores the defaults. */
+rn_status rn_graph_set_config(rn_graph *g, const rn_config *cfg);
+
+/*
+ * rn_distance_join -- all (u in R, v in S) with dist(u, v) <= theta, sorted by (u, v)
+ * (Abstract; Section 4: a threshold theta and no restrictive k).
+ *   R, S  : host arrays of nR / nS node ids (sets, disjoint).
+ *   out   : filled with library-owned host arrays; free with rn_pairs_free.
+ * Synchronous: the pairs are in host memory when it returns.
+ */
+rn_status rn_distance_join(const rn_graph *g, const uint32_t *R, uint32_t nR, const uint32_t *S,
+                           uint32_t nS, uint32_t theta, rn_pairs *out);
+
+/*
+ * rn_distance_join_dev -- the same join with inputs and outputs in device memory.
+ *   dR, dS : device arrays (caller-owned).  out : library-owned device buffers (see
+ *   above); out->n receives the pair count.  All work is ordered on `stream`; the call
+ *   returns after the pairs are complete (it reads the pair count back).
+ */
+rn_status rn_distance_join_dev(const rn_graph *g, const uint32_t *dR, uint32_t nR,
+                               const uint32_t *dS, uint32_t nS, uint32_t theta, rn_dpairs *out,
+                               rn_stream stream);
+
+/*
+ * rn_kcp -- the k closest pairs (u in R, v in S) with dist(u, v) <= theta, sorted by
+ * (d, u, v); fewer than k if fewer pairs lie within theta (Abstract; Section 4,
+ * Algorithm 2 "k items within theta"; the global k-th distance of Algorithm 3 bounds
+ * every search).  k >= 1.  theta = RN_INF for no distance bound.
+ */
+rn_status rn_kcp(const rn_graph *g, const uint32_t *R, uint32_t nR, const uint32_t *S,
+                 uint32_t nS, uint64_t k, uint32_t theta, rn_pairs *out);
+rn_status rn_kcp_dev(const rn_graph *g, const uint32_t *dR, uint32_t nR, const uint32_t *dS,
+                     uint32_t nS, uint64_t k, uint32_t theta, rn_dpairs *out, rn_stream stream);
+
+void rn_pairs_free(rn_pairs *p);
+void rn_dpairs_free(rn_dpairs *p);
+
+/* Message of the calling thread's last failure ("" if none).  Valid until the next call. */
+const char *rn_last_error(void);
+/* Counters of the calling thread's last successful query. */
+rn_status rn_last_query_stats(rn_query_stats *out);
+/* Library version string. */
+const char *rn_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* RN_H */

@@ -43,16 +43,24 @@ def theta_for_matches(g: O.OGraph, R, S, t: int, sample: int) -> tuple[int, list
 
 
 def main() -> None:
+    """Recompute every stored workload parameter (about half a minute)."""
     o = O.default()
     out = {}
     t0 = time.time()
     w = I.c1_grid_join()
-    out["grid4096_theta1500"] = {"theta": 1500, "graph": graph_digest(w.graph)}
+    g = o.graph(w.graph.n, w.graph.src, w.graph.dst, w.graph.w)
+    full = g.join(w.R, w.S, w.theta)
+    out["grid4096_theta1500"] = {"theta": 1500, "pairs": len(full), "alg_arcs": full.arcs,
+                                 "graph": graph_digest(w.graph)}
 
     w = I.c2_road_join(None)
     g = o.graph(w.graph.n, w.graph.src, w.graph.dst, w.graph.w)
     th, _ = theta_for_matches(g, w.R, w.S, 50, 256)
+    full = g.join(w.R, w.S, th)
+    # alg_arcs: the arcs the plain per-source searches of the oracle look at (the sum
+    # over sources of the out-degrees of the nodes within theta), the GTEPS numerator
     out["road264k_join"] = {"theta": th, "matches_per_u": 50, "sample": 256,
+                            "pairs": len(full), "alg_arcs": full.arcs,
                             "graph": graph_digest(w.graph)}
     print("road264k_join theta", th, f"{time.time() - t0:.1f}s", flush=True)
 

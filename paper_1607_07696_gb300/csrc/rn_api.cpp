@@ -1,0 +1,341 @@
+// rn_api.cpp -- the extern "C" boundary of the engine (include/rn.h): argument checks,
+// ownership of results, error codes and thread-local error messages.  Every entry point
+// catches everything; no exception crosses the ABI.
+#include <algorithm>
+#include <chrono>
+#include <cstdlib>
+#include <cstring>
+#include <memory>
+#include <new>
+
+#include <cuda_runtime.h>
+
+#include "rn_internal.h"
+
+namespace {
+
+thread_local std::string g_last_error;
+thread_local rn_query_stats g_last_stats{};
+thread_local bool g_have_stats = false;
+
+rn_status set_error(rn_status s, const std::string &msg) {
+    g_last_error = msg;
+    return s;
+}
+
+template <class F>
+rn_status guarded(F &&f) {
+    try {
+        g_last_error.clear();
+        f();
+        return RN_OK;
+    } catch (const rn::Error &e) {
+        return set_error(e.status, e.msg);
+    } catch (const std::bad_alloc &) {
+        return set_error(RN_ENOMEM, "host allocation failed");
+    } catch (const std::exception &e) {
+        return set_error(RN_EINTERNAL, e.what());
+    } catch (...) {
+        return set_error(RN_EINTERNAL, "unknown failure");
+    }
+}
+
+// Host-side check of R and S (ids < n, no repeats, disjoint), for a precise message
+// before anything reaches the device.
+void check_sets_host(uint32_t n, const uint32_t *R, uint32_t nR, const uint32_t *S, uint32_t nS) {
+    if ((nR && !R) || (nS && !S)) rn::fail(RN_EINVAL, "null R or S with a non-zero size");
+    std::vector<uint8_t> mark(n, 0);
+    for (uint32_t i = 0; i < nR; i++) {
+        if (R[i] >= n) rn::fail(RN_EINVAL, "R[" + std::to_string(i) + "] >= n");
+        if (mark[R[i]]) rn::fail(RN_EINVAL, "R repeats node " + std::to_string(R[i]));
+        mark[R[i]] = 1;
+    }
+    for (uint32_t i = 0; i < nS; i++) {
+        if (S[i] >= n) rn::fail(RN_EINVAL, "S[" + std::to_string(i) + "] >= n");
+        if (mark[S[i]] == 2) rn::fail(RN_EINVAL, "S repeats node " + std::to_string(S[i]));
+        if (mark[S[i]] == 1) rn::fail(RN_EINVAL, "node " + std::to_string(S[i]) + " is in both R and S");
+        mark[S[i]] = 2;
+    }
+}
+
+void check_theta(uint32_t theta) {
+    if (theta != RN_INF && theta > RN_THETA_MAX) rn::fail(RN_EINVAL, "theta must be <= 2^31 or RN_INF");
+}
+
+void ensure(uint32_t **p, uint32_t *cap, uint32_t want) {
+    if (*p && *cap >= want) return;
+    rn::device_free(*p);
+    *p = nullptr;
+    *cap = std::max<uint32_t>(want, 1024);
+    *p = (uint32_t *)rn::device_alloc(size_t(*cap) * 4);
+}
+
+void to_host_pairs(const rn_dpairs &d, rn_pairs *out, cudaStream_t st) {
+    out->n = d.n;
+    size_t b = std::max<uint64_t>(d.n, 1) * 4;
+    out->u = (uint32_t *)std::malloc(b);
+    out->v = (uint32_t *)std::malloc(b);
+    out->d = (uint32_t *)std::malloc(b);
+    if (!out->u || !out->v || !out->d) {
+        rn_pairs_free(out);
+        rn::fail(RN_ENOMEM, "host result allocation failed");
+    }
+    if (d.n) {
+        cudaMemcpyAsync(out->u, d.u, d.n * 4, cudaMemcpyDeviceToHost, st);
+        cudaMemcpyAsync(out->v, d.v, d.n * 4, cudaMemcpyDeviceToHost, st);
+        cudaMemcpyAsync(out->d, d.d, d.n * 4, cudaMemcpyDeviceToHost, st);
+        cudaError_t e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess) {
+            rn_pairs_free(out);
+            rn::fail(RN_ECUDA, std::string("copying pairs to the host: ") + cudaGetErrorString(e));
+        }
+    }
+}
+
+}  // namespace
+
+namespace {
+
+rn::HostScratch &scratch_of(rn_graph *g) {
+    rn::HostScratch &h = g->hs;
+    if (!h.stream) {
+        cudaStream_t s = nullptr;
+        cudaError_t err = cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking);
+        if (err != cudaSuccess) rn::fail(RN_ECUDA, std::string("cudaStreamCreate: ") + cudaGetErrorString(err));
+        h.stream = s;
+    }
+    return h;
+}
+
+void drop_scratch(rn_graph *g) {
+    rn::HostScratch &h = g->hs;
+    rn::device_free(h.dR);
+    rn::device_free(h.dS);
+    rn::dpairs_release(&h.res);
+    if (h.stream) cudaStreamDestroy((cudaStream_t)h.stream);
+    h = rn::HostScratch{};
+}
+
+uint32_t median_weight(const rn::HostGraph &g) {
+    if (g.w.empty()) return 1;
+    std::vector<uint32_t> w(g.w);
+    std::nth_element(w.begin(), w.begin() + w.size() / 2, w.end());
+    return w[w.size() / 2];
+}
+
+void apply_config(rn_graph *g, const rn_config *cfg) {
+    rn::EngineConfig c;
+    if (cfg) {
+        if (cfg->tile_width && cfg->tile_width != 32 && cfg->tile_width != 64 && cfg->tile_width != 128)
+            rn::fail(RN_EINVAL, "tile_width must be 0, 32, 64 or 128");
+        if (cfg->tile_width) c.tile_width = cfg->tile_width;
+        c.delta = cfg->delta;
+    }
+    g->cfg = c;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *rn_version(void) { return "rn-join 0.1 (sm_103a)"; }
+
+const char *rn_last_error(void) { return g_last_error.c_str(); }
+
+rn_status rn_last_query_stats(rn_query_stats *out) {
+    if (!out) return set_error(RN_EINVAL, "null output");
+    if (!g_have_stats) return set_error(RN_EINVAL, "no query has completed on this thread");
+    *out = g_last_stats;
+    return RN_OK;
+}
+
+rn_status rn_graph_load(const uint32_t *src, const uint32_t *dst, const uint32_t *w, uint64_t m,
+                        uint32_t n, uint32_t flags, const rn_config *cfg, rn_graph **out) {
+    return guarded([&] {
+        if (!out) rn::fail(RN_EINVAL, "null output");
+        *out = nullptr;
+        if (m && (!src || !dst || !w)) rn::fail(RN_EINVAL, "null edge arrays");
+        if (flags & ~(RN_UNDIRECTED | RN_REORDER)) rn::fail(RN_EINVAL, "unknown flag");
+        auto g = std::make_unique<rn_graph>();
+        apply_config(g.get(), cfg);
+        rn::HostGraph h = rn::build_csr(n, m, src, dst, w, (flags & RN_UNDIRECTED) != 0);
+        std::vector<uint32_t> order(n), perm(n);
+        auto t0 = std::chrono::steady_clock::now();
+        if (flags & RN_REORDER) {
+            uint32_t leaf = cfg && cfg->leaf_size ? cfg->leaf_size : 512;
+            float alpha = (cfg && cfg->alpha >= 0.0f) ? cfg->alpha : 0.5f;
+            order = rn::bisection_order(h, leaf, alpha);
+            h = rn::relabel(h, order);
+        } else {
+            for (uint32_t i = 0; i < n; i++) order[i] = i;
+        }
+        auto t1 = std::chrono::steady_clock::now();
+        for (uint32_t i = 0; i < n; i++) perm[order[i]] = i;
+        g->info.n = n;
+        g->info.arcs = h.arcs();
+        g->info.flags = flags;
+        g->info.median_weight = median_weight(h);
+        uint32_t maxd = 0;
+        for (uint32_t x = 0; x < n; x++) maxd = std::max(maxd, h.row_ptr[x + 1] - h.row_ptr[x]);
+        g->info.max_degree = maxd;
+        g->info.reorder_ms = std::chrono::duration<double, std::milli>(t1 - t0).count();
+        cudaGetDevice(&g->device);
+        rn::upload_graph(h, perm, order, &g->dev);
+        try {
+            g->ws = rn::workspace_create(g->dev);
+        } catch (...) {
+            rn::free_graph(&g->dev);
+            throw;
+        }
+        g->perm = std::move(perm);
+        *out = g.release();
+    });
+}
+
+rn_status rn_bisection_order(const uint32_t *src, const uint32_t *dst, const uint32_t *w, uint64_t m,
+                             uint32_t n, uint32_t flags, const rn_config *cfg, uint32_t *order) {
+    return guarded([&] {
+        if (!order) rn::fail(RN_EINVAL, "null output");
+        if (m && (!src || !dst || !w)) rn::fail(RN_EINVAL, "null edge arrays");
+        if (flags & ~(RN_UNDIRECTED | RN_REORDER)) rn::fail(RN_EINVAL, "unknown flag");
+        rn::HostGraph h = rn::build_csr(n, m, src, dst, w, (flags & RN_UNDIRECTED) != 0);
+        uint32_t leaf = cfg && cfg->leaf_size ? cfg->leaf_size : 512;
+        float alpha = (cfg && cfg->alpha >= 0.0f) ? cfg->alpha : 0.5f;
+        std::vector<uint32_t> o = rn::bisection_order(h, leaf, alpha);
+        std::memcpy(order, o.data(), size_t(n) * 4);
+    });
+}
+
+void rn_graph_free(rn_graph *g) {
+    if (!g) return;
+    try {
+        drop_scratch(g);
+        rn::workspace_destroy(g->ws);
+        rn::free_graph(&g->dev);
+    } catch (...) {
+    }
+    delete g;
+}
+
+rn_status rn_graph_info(const rn_graph *g, rn_graph_stats *out) {
+    return guarded([&] {
+        if (!g || !out) rn::fail(RN_EINVAL, "null argument");
+        *out = g->info;
+        out->device_bytes = (uint64_t(g->dev.n) + 1) * 4 + g->dev.arcs * 8 + uint64_t(g->dev.n) * 8 +
+                            rn::workspace_bytes(g->ws);
+    });
+}
+
+rn_status rn_graph_permutation(const rn_graph *g, uint32_t *perm) {
+    return guarded([&] {
+        if (!g || !perm) rn::fail(RN_EINVAL, "null argument");
+        std::memcpy(perm, g->perm.data(), g->perm.size() * 4);
+    });
+}
+
+rn_status rn_graph_set_config(rn_graph *g, const rn_config *cfg) {
+    return guarded([&] {
+        if (!g) rn::fail(RN_EINVAL, "null graph");
+        std::lock_guard<std::mutex> lk(g->mu);
+        apply_config(g, cfg);
+    });
+}
+
+rn_status rn_distance_join_dev(const rn_graph *cg, const uint32_t *dR, uint32_t nR, const uint32_t *dS,
+                               uint32_t nS, uint32_t theta, rn_dpairs *out, rn_stream stream) {
+    return guarded([&] {
+        if (!cg || !out) rn::fail(RN_EINVAL, "null argument");
+        if ((nR && !dR) || (nS && !dS)) rn::fail(RN_EINVAL, "null R or S with a non-zero size");
+        check_theta(theta);
+        rn_graph *g = const_cast<rn_graph *>(cg);
+        std::lock_guard<std::mutex> lk(g->mu);
+        rn_query_stats st{};
+        rn::run_join(g->dev, g->ws, g->cfg, g->info.median_weight, dR, nR, dS, nS, theta, out,
+                     (void *)stream, &st);
+        g_last_stats = st;
+        g_have_stats = true;
+    });
+}
+
+rn_status rn_distance_join(const rn_graph *cg, const uint32_t *R, uint32_t nR, const uint32_t *S,
+                           uint32_t nS, uint32_t theta, rn_pairs *out) {
+    return guarded([&] {
+        if (!cg || !out) rn::fail(RN_EINVAL, "null argument");
+        *out = rn_pairs{};
+        check_theta(theta);
+        rn_graph *g = const_cast<rn_graph *>(cg);
+        check_sets_host(g->dev.n, R, nR, S, nS);
+        std::lock_guard<std::mutex> lk(g->mu);
+        rn::HostScratch &hs = scratch_of(g);
+        ensure(&hs.dR, &hs.capR, nR);
+        ensure(&hs.dS, &hs.capS, nS);
+        rn::copy_to_device(hs.dR, R, size_t(nR) * 4, hs.stream);
+        rn::copy_to_device(hs.dS, S, size_t(nS) * 4, hs.stream);
+        rn_query_stats st{};
+        rn::run_join(g->dev, g->ws, g->cfg, g->info.median_weight, hs.dR, nR, hs.dS, nS, theta, &hs.res,
+                     (void *)hs.stream, &st);
+        to_host_pairs(hs.res, out, (cudaStream_t)hs.stream);
+        g_last_stats = st;
+        g_have_stats = true;
+    });
+}
+
+rn_status rn_kcp_dev(const rn_graph *cg, const uint32_t *dR, uint32_t nR, const uint32_t *dS, uint32_t nS,
+                     uint64_t k, uint32_t theta, rn_dpairs *out, rn_stream stream) {
+    return guarded([&] {
+        if (!cg || !out) rn::fail(RN_EINVAL, "null argument");
+        if ((nR && !dR) || (nS && !dS)) rn::fail(RN_EINVAL, "null R or S with a non-zero size");
+        if (k == 0) rn::fail(RN_EINVAL, "k must be >= 1");
+        check_theta(theta);
+        rn_graph *g = const_cast<rn_graph *>(cg);
+        std::lock_guard<std::mutex> lk(g->mu);
+        rn_query_stats st{};
+        rn::run_kcp(g->dev, g->ws, g->cfg, g->info.median_weight, dR, nR, dS, nS, k, theta, out,
+                    (void *)stream, &st);
+        g_last_stats = st;
+        g_have_stats = true;
+    });
+}
+
+rn_status rn_kcp(const rn_graph *cg, const uint32_t *R, uint32_t nR, const uint32_t *S, uint32_t nS,
+                 uint64_t k, uint32_t theta, rn_pairs *out) {
+    return guarded([&] {
+        if (!cg || !out) rn::fail(RN_EINVAL, "null argument");
+        *out = rn_pairs{};
+        if (k == 0) rn::fail(RN_EINVAL, "k must be >= 1");
+        check_theta(theta);
+        rn_graph *g = const_cast<rn_graph *>(cg);
+        check_sets_host(g->dev.n, R, nR, S, nS);
+        std::lock_guard<std::mutex> lk(g->mu);
+        rn::HostScratch &hs = scratch_of(g);
+        ensure(&hs.dR, &hs.capR, nR);
+        ensure(&hs.dS, &hs.capS, nS);
+        rn::copy_to_device(hs.dR, R, size_t(nR) * 4, hs.stream);
+        rn::copy_to_device(hs.dS, S, size_t(nS) * 4, hs.stream);
+        rn_query_stats st{};
+        rn::run_kcp(g->dev, g->ws, g->cfg, g->info.median_weight, hs.dR, nR, hs.dS, nS, k, theta, &hs.res,
+                    (void *)hs.stream, &st);
+        to_host_pairs(hs.res, out, (cudaStream_t)hs.stream);
+        g_last_stats = st;
+        g_have_stats = true;
+    });
+}
+
+void rn_pairs_free(rn_pairs *p) {
+    if (!p) return;
+    std::free(p->u);
+    std::free(p->v);
+    std::free(p->d);
+    p->u = p->v = p->d = nullptr;
+    p->n = 0;
+}
+
+void rn_dpairs_free(rn_dpairs *p) {
+    if (!p) return;
+    try {
+        rn::dpairs_release(p);
+    } catch (...) {
+    }
+}
+
+}  // extern "C"

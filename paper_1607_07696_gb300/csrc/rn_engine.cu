@@ -1,0 +1,1055 @@
+// rn_engine.cu -- the GPU engine of the theta-bounded many-source road-network join
+// and its k-closest-pairs variant (Tsatsanifos 2016: Abstract, Section 4).
+//
+// The paper runs one best-first search from every u in R and keeps the S nodes it
+// reaches within theta (Section 4, local processing).  Here those searches run a tile
+// of T sources at a time (T = 32, 64 or 128) in one thread block:
+//
+//   * a hash map in shared memory assigns every node the tile reaches a slot;
+//   * slot h owns row h of a distance slab in global memory (L2-resident), T uint32
+//     lanes wide -- lane t is the tentative distance from source t -- so a warp reads
+//     or relaxes a whole row with one coalesced 128*T/32-byte access;
+//   * the rows are relaxed by delta-stepping: a near queue in shared memory holds the
+//     slots whose smallest improved lane lies in the current bucket, and the bucket
+//     advances when the queue drains; a slot's arcs are relaxed for all T lanes at
+//     once with fire-and-forget atomicMin;
+//   * a relaxation is dropped when its cost is greater than the bound (theta, or the
+//     k-closest-pairs radius), so costs equal to the bound are kept (Algorithm 4);
+//   * when the tile's search ends, every slot whose node is in S emits the lanes within
+//     the bound as (u, v, d) through a warp ballot and a block prefix sum, with one
+//     global atomicAdd per block;
+//   * pairs are put in canonical order by an LSD radix sort.
+//
+// All arithmetic is on unsigned integers: distances are at most 2^31 and weights are
+// below 2^24, so d + w never wraps, and the result is exact.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <string>
+
+#include "rn_internal.h"
+
+namespace rn {
+
+#define RN_CUDA(x)                                                                        \
+    do {                                                                                  \
+        cudaError_t e_ = (x);                                                             \
+        if (e_ != cudaSuccess) {                                                          \
+            cudaGetLastError();                                                           \
+            fail(e_ == cudaErrorMemoryAllocation ? RN_ENOMEM : RN_ECUDA,                  \
+                 std::string(#x) + ": " + cudaGetErrorString(e_));                        \
+        }                                                                                 \
+    } while (0)
+
+constexpr uint32_t INF = 0xFFFFFFFFu;
+constexpr uint32_t EMPTY = 0xFFFFFFFFu;
+constexpr unsigned FULL = 0xFFFFFFFFu;
+
+// ------------------------------------------------------------------ memory ----
+
+void *device_alloc(size_t bytes) {
+    void *p = nullptr;
+    RN_CUDA(cudaMalloc(&p, bytes ? bytes : 16));
+    return p;
+}
+
+void device_free(void *p) {
+    if (p) cudaFree(p);
+}
+
+void copy_to_host(void *dst, const void *src, size_t bytes, void *stream) {
+    if (!bytes) return;
+    RN_CUDA(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToHost, (cudaStream_t)stream));
+    RN_CUDA(cudaStreamSynchronize((cudaStream_t)stream));
+}
+
+void copy_to_device(void *dst, const void *src, size_t bytes, void *stream) {
+    if (!bytes) return;
+    RN_CUDA(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, (cudaStream_t)stream));
+}
+
+void stream_sync(void *stream) { RN_CUDA(cudaStreamSynchronize((cudaStream_t)stream)); }
+
+void dpairs_reserve(rn_dpairs *p, uint64_t cap) {
+    if (p->u && p->cap >= cap) return;
+    dpairs_release(p);
+    cap = std::max<uint64_t>(cap, 1024);
+    p->u = (uint32_t *)device_alloc(cap * 4);
+    p->v = (uint32_t *)device_alloc(cap * 4);
+    p->d = (uint32_t *)device_alloc(cap * 4);
+    p->cap = cap;
+}
+
+void dpairs_release(rn_dpairs *p) {
+    device_free(p->u);
+    device_free(p->v);
+    device_free(p->d);
+    p->u = p->v = p->d = nullptr;
+    p->cap = 0;
+    p->n = 0;
+}
+
+void upload_graph(const HostGraph &g, const std::vector<uint32_t> &perm,
+                  const std::vector<uint32_t> &iperm, DeviceGraph *out) {
+    DeviceGraph d;
+    d.n = g.n;
+    d.arcs = g.arcs();
+    try {
+        d.row_ptr = (uint32_t *)device_alloc((size_t(g.n) + 1) * 4);
+        d.adj = (uint32_t *)device_alloc(std::max<size_t>(d.arcs, 1) * 8);
+        d.perm = (uint32_t *)device_alloc(size_t(g.n) * 4);
+        d.iperm = (uint32_t *)device_alloc(size_t(g.n) * 4);
+        std::vector<uint32_t> adj(2 * d.arcs);
+        for (uint64_t e = 0; e < d.arcs; e++) {
+            adj[2 * e] = g.col[e];
+            adj[2 * e + 1] = g.w[e];
+        }
+        RN_CUDA(cudaMemcpy(d.row_ptr, g.row_ptr.data(), (size_t(g.n) + 1) * 4, cudaMemcpyHostToDevice));
+        if (d.arcs) RN_CUDA(cudaMemcpy(d.adj, adj.data(), d.arcs * 8, cudaMemcpyHostToDevice));
+        RN_CUDA(cudaMemcpy(d.perm, perm.data(), size_t(g.n) * 4, cudaMemcpyHostToDevice));
+        RN_CUDA(cudaMemcpy(d.iperm, iperm.data(), size_t(g.n) * 4, cudaMemcpyHostToDevice));
+    } catch (...) {
+        free_graph(&d);
+        throw;
+    }
+    *out = d;
+}
+
+void free_graph(DeviceGraph *g) {
+    device_free(g->row_ptr);
+    device_free(g->adj);
+    device_free(g->perm);
+    device_free(g->iperm);
+    *g = DeviceGraph{};
+}
+
+// ---------------------------------------------------------------- workspace ----
+
+// Device-resident control block of one query.
+struct Control {
+    uint32_t err;          // 1: id >= n, 2: repeated id or R/S overlap
+    uint32_t r_count;      // R nodes after validation
+    uint32_t tile_next;    // work-queue head of the persistent search
+    uint32_t n_failed;     // tiles whose slab overflowed
+    unsigned long long pairs;
+    unsigned long long scans;
+    unsigned long long slots;      // sum over tiles of slab rows used
+    unsigned long long slot_arcs;  // sum over tiles of arcs leaving the rows' nodes
+};
+
+constexpr int SEARCH_THREADS = 512;
+constexpr int SEARCH_WARPS = SEARCH_THREADS / 32;
+constexpr uint32_t QCAP = 2048;        // near-queue entries (two queues)
+constexpr uint32_t SMEM_H = 8192;      // slots of the shared-memory map
+constexpr int CTAS_PER_SM = 2;
+
+struct Workspace {
+    uint32_t n = 0, nwords = 0;
+    int num_sms = 0;
+    uint32_t *used_bits = nullptr, *rbits = nullptr, *sbits = nullptr;
+    uint32_t *block_sums = nullptr;
+    uint32_t *rsorted = nullptr;
+    uint32_t rsorted_cap = 0;
+    uint32_t *failed = nullptr, *failed2 = nullptr;  // tiles to search again (ping-pong)
+    uint32_t failed_cap = 0, failed2_cap = 0;
+    Control *ctl = nullptr;
+    Control *ctl_host = nullptr;  // pinned
+    // slab of the persistent search: one region of SMEM_H rows per block, per width
+    uint32_t *slab = nullptr;
+    size_t slab_bytes = 0;
+    uint32_t slab_ctas = 0;
+    // raw pairs and radix-sort buffers
+    unsigned long long *keyA = nullptr, *keyB = nullptr;
+    uint32_t *valA = nullptr, *valB = nullptr;
+    uint64_t pair_cap = 0;
+    uint32_t *hist = nullptr;
+    size_t hist_cap = 0;
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr, evs0 = nullptr, evs1 = nullptr;
+    uint32_t launches = 0;  // kernels launched by the current query
+    uint64_t bytes = 0;
+};
+
+static void ws_alloc(Workspace *ws, void **p, size_t bytes) {
+    *p = device_alloc(bytes);
+    ws->bytes += bytes;
+}
+
+Workspace *workspace_create(const DeviceGraph &g) {
+    Workspace *ws = new Workspace();
+    try {
+        int dev = 0;
+        RN_CUDA(cudaGetDevice(&dev));
+        RN_CUDA(cudaDeviceGetAttribute(&ws->num_sms, cudaDevAttrMultiProcessorCount, dev));
+        ws->n = g.n;
+        ws->nwords = (g.n + 31) / 32;
+        ws_alloc(ws, (void **)&ws->used_bits, size_t(ws->nwords) * 4);
+        ws_alloc(ws, (void **)&ws->rbits, size_t(ws->nwords) * 4);
+        ws_alloc(ws, (void **)&ws->sbits, size_t(ws->nwords) * 4);
+        ws_alloc(ws, (void **)&ws->block_sums, (ws->nwords / 1024 + 2) * 4);
+        ws_alloc(ws, (void **)&ws->ctl, sizeof(Control));
+        RN_CUDA(cudaMallocHost(&ws->ctl_host, sizeof(Control)));
+        RN_CUDA(cudaEventCreate(&ws->ev0));
+        RN_CUDA(cudaEventCreate(&ws->ev1));
+        RN_CUDA(cudaEventCreate(&ws->evs0));
+        RN_CUDA(cudaEventCreate(&ws->evs1));
+    } catch (...) {
+        workspace_destroy(ws);
+        throw;
+    }
+    return ws;
+}
+
+void workspace_destroy(Workspace *ws) {
+    if (!ws) return;
+    device_free(ws->used_bits);
+    device_free(ws->rbits);
+    device_free(ws->sbits);
+    device_free(ws->block_sums);
+    device_free(ws->rsorted);
+    device_free(ws->failed);
+    device_free(ws->failed2);
+    device_free(ws->ctl);
+    device_free(ws->slab);
+    device_free(ws->keyA);
+    device_free(ws->keyB);
+    device_free(ws->valA);
+    device_free(ws->valB);
+    device_free(ws->hist);
+    if (ws->ctl_host) cudaFreeHost(ws->ctl_host);
+    if (ws->ev0) cudaEventDestroy(ws->ev0);
+    if (ws->ev1) cudaEventDestroy(ws->ev1);
+    if (ws->evs0) cudaEventDestroy(ws->evs0);
+    if (ws->evs1) cudaEventDestroy(ws->evs1);
+    delete ws;
+}
+
+uint64_t workspace_bytes(const Workspace *ws) { return ws ? ws->bytes : 0; }
+
+template <class T>
+static void grow(Workspace *ws, T **p, uint64_t *cap, uint64_t want, uint64_t elem) {
+    if (*p && *cap >= want) return;
+    if (*p) {
+        device_free(*p);
+        ws->bytes -= *cap * elem;
+    }
+    *p = nullptr;
+    uint64_t c = std::max<uint64_t>(want, 1024);
+    *p = (T *)device_alloc(c * elem);
+    ws->bytes += c * elem;
+    *cap = c;
+}
+
+// --------------------------------------------------------------- set prep ----
+
+// Mark one set: reject ids >= n and ids already marked (a repeat, or an id of R met
+// again in S: the sets must be disjoint), and set the membership bit of the internal
+// id.
+__global__ void k_mark_set(const uint32_t *__restrict__ ids, uint32_t cnt, uint32_t n,
+                           const uint32_t *__restrict__ perm, uint32_t *used_bits,
+                           uint32_t *set_bits, Control *ctl) {
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < cnt; i += gridDim.x * blockDim.x) {
+        uint32_t id = ids[i];
+        if (id >= n) {
+            atomicOr(&ctl->err, 1u);
+            continue;
+        }
+        uint32_t bit = 1u << (id & 31);
+        uint32_t old = atomicOr(&used_bits[id >> 5], bit);
+        if (old & bit) {
+            atomicOr(&ctl->err, 2u);
+            continue;
+        }
+        uint32_t in = perm[id];
+        atomicOr(&set_bits[in >> 5], 1u << (in & 31));
+    }
+}
+
+// Set bits per block of 1024 words.
+__global__ void k_bits_count(const uint32_t *__restrict__ bits, uint32_t nwords, uint32_t *block_sums) {
+    __shared__ uint32_t warp_sum[32];
+    uint32_t i = blockIdx.x * 1024 + threadIdx.x;
+    uint32_t c = i < nwords ? __popc(bits[i]) : 0;
+    c = __reduce_add_sync(FULL, c);
+    if ((threadIdx.x & 31) == 0) warp_sum[threadIdx.x >> 5] = c;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        uint32_t s = __reduce_add_sync(FULL, warp_sum[threadIdx.x]);
+        if (threadIdx.x == 0) block_sums[blockIdx.x] = s;
+    }
+}
+
+// Write the ids of the set bits in increasing order (R sorted by internal id, so a
+// tile holds R nodes of one neighbourhood).  The last block stores the total.
+__global__ void k_bits_compact(const uint32_t *__restrict__ bits, uint32_t nwords,
+                               const uint32_t *__restrict__ block_sums, uint32_t nblocks,
+                               uint32_t *out, Control *ctl) {
+    __shared__ uint32_t warp_sum[32];
+    __shared__ uint32_t s_base;
+    if (threadIdx.x < 32) {
+        uint32_t s = 0;
+        for (uint32_t b = threadIdx.x; b < blockIdx.x; b += 32) s += block_sums[b];
+        s = __reduce_add_sync(FULL, s);
+        if (threadIdx.x == 0) {
+            s_base = s;
+            if (blockIdx.x == nblocks - 1) ctl->r_count = s + block_sums[blockIdx.x];
+        }
+    }
+    uint32_t i = blockIdx.x * 1024 + threadIdx.x;
+    uint32_t word = i < nwords ? bits[i] : 0;
+    uint32_t c = __popc(word);
+    uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    uint32_t incl = c;
+    for (int o = 1; o < 32; o <<= 1) {
+        uint32_t t = __shfl_up_sync(FULL, incl, o);
+        if (lane >= o) incl += t;
+    }
+    if (lane == 31) warp_sum[warp] = incl;
+    __syncthreads();
+    if (warp == 0) {
+        uint32_t v = warp_sum[lane];
+        uint32_t x = v;
+        for (int o = 1; o < 32; o <<= 1) {
+            uint32_t t = __shfl_up_sync(FULL, x, o);
+            if (lane >= o) x += t;
+        }
+        warp_sum[lane] = x - v;
+    }
+    __syncthreads();
+    uint32_t pos = s_base + warp_sum[warp] + incl - c;
+    while (word) {
+        uint32_t b = __ffs(word) - 1;
+        word &= word - 1;
+        out[pos++] = i * 32 + b;
+    }
+}
+
+// ------------------------------------------------------------ tile search ----
+
+struct SearchArgs {
+    const uint32_t *__restrict__ row_ptr;
+    const uint2 *__restrict__ adj;
+    const uint32_t *__restrict__ iperm;
+    const uint32_t *__restrict__ sbits;
+    const uint32_t *__restrict__ src;       // R, internal ids, ascending
+    const uint32_t *__restrict__ tile_list; // tiles to search (retry), or null: all
+    uint32_t ntiles;                        // entries of tile_list, or tiles of R
+    uint32_t bound;                         // theta
+    uint32_t delta;
+    uint32_t *slab;                         // per-block regions of H rows x T lanes
+    uint32_t *gmap;                         // global slot maps (2 H words per block), or null
+    uint32_t H, hshift, max_fill;
+    uint32_t vbits;                         // key = (u << vbits) | v
+    Control *ctl;
+    uint32_t *failed;
+    unsigned long long *out_key;
+    uint32_t *out_d;
+    uint64_t out_cap;
+};
+
+template <int L>
+struct Row {
+    uint32_t x[L];
+};
+
+template <int L>
+__device__ __forceinline__ Row<L> load_row(const uint32_t *p) {
+    Row<L> r;
+    if constexpr (L == 1) {
+        r.x[0] = __ldcg(p);
+    } else if constexpr (L == 2) {
+        uint2 v = __ldcg(reinterpret_cast<const uint2 *>(p));
+        r.x[0] = v.x;
+        r.x[1] = v.y;
+    } else {
+        uint4 v = __ldcg(reinterpret_cast<const uint4 *>(p));
+        r.x[0] = v.x;
+        r.x[1] = v.y;
+        r.x[2] = v.z;
+        r.x[3] = v.w;
+    }
+    return r;
+}
+
+template <int L>
+__device__ __forceinline__ void store_inf(uint32_t *p) {
+    if constexpr (L == 1) {
+        __stcg(p, INF);
+    } else if constexpr (L == 2) {
+        __stcg(reinterpret_cast<uint2 *>(p), make_uint2(INF, INF));
+    } else {
+        __stcg(reinterpret_cast<uint4 *>(p), make_uint4(INF, INF, INF, INF));
+    }
+}
+
+__device__ __forceinline__ uint32_t slot_hash(uint32_t y, uint32_t hshift) {
+    return (y * 0x9E3779B1u) >> hshift;
+}
+
+// Slot of node y in the tile's map, inserting it if absent.  Linear probing; EMPTY when
+// the map is full (the tile then fails and is searched again with a larger map).
+__device__ __forceinline__ uint32_t find_or_insert(uint32_t *hkeys, uint32_t H, uint32_t hshift,
+                                                   uint32_t y, uint32_t *fill, uint32_t max_fill,
+                                                   uint32_t *fail_flag) {
+    uint32_t h = slot_hash(y, hshift);
+    volatile uint32_t *vk = hkeys;
+    for (uint32_t probe = 0; probe < H; probe++) {
+        uint32_t k = vk[h];
+        if (k == y) return h;
+        if (k == EMPTY) {
+            uint32_t prev = atomicCAS(&hkeys[h], EMPTY, y);
+            if (prev == EMPTY) {
+                if (atomicAdd(fill, 1u) >= max_fill) *(volatile uint32_t *)fail_flag = 1;
+                return h;
+            }
+            if (prev == y) return h;
+        }
+        h = (h + 1) & (H - 1);
+    }
+    *(volatile uint32_t *)fail_flag = 1;
+    return EMPTY;
+}
+
+// One thread block searches one tile of T = 32 L sources at a time (persistent: blocks
+// pop tiles from a global counter).  GMAP = false keeps the slot map (node id and
+// pending priority of every slot) in shared memory; GMAP = true keeps it in global
+// memory so a tile whose union ball outgrows shared memory can be searched again with
+// a larger map.
+template <int L, bool GMAP>
+__global__ void __launch_bounds__(SEARCH_THREADS, CTAS_PER_SM) k_tile_search(SearchArgs a) {
+    constexpr int T = 32 * L;
+    extern __shared__ uint32_t smem[];
+    uint32_t *hkeys, *prio, *qa;
+    if constexpr (GMAP) {
+        hkeys = a.gmap + size_t(blockIdx.x) * 2 * a.H;
+        prio = hkeys + a.H;
+        qa = smem;
+    } else {
+        hkeys = smem;
+        prio = hkeys + a.H;
+        qa = prio + a.H;
+    }
+    uint32_t *qb = qa + QCAP;
+    __shared__ uint32_t src_orig[T];
+    __shared__ uint32_t s_tile, s_ncur, s_nnext, s_cursor, s_fill, s_fail, s_stop, s_minp;
+    __shared__ uint32_t s_warp_cnt[SEARCH_WARPS];
+    __shared__ unsigned long long s_base;
+
+    const uint32_t tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    uint32_t *slab = a.slab + size_t(blockIdx.x) * a.H * T;
+    const uint32_t bound = a.bound;
+    const uint64_t delta = a.delta;
+    unsigned long long my_scans = 0, my_slots = 0, my_arcs = 0;
+
+    if (__ldcg(&a.ctl->err)) return;
+    const uint32_t nR = __ldcg(&a.ctl->r_count);
+    const uint32_t ntiles = a.tile_list ? a.ntiles : (nR + T - 1) / T;
+
+    for (;;) {
+        if (tid == 0) s_tile = atomicAdd(&a.ctl->tile_next, 1u);
+        for (uint32_t i = tid; i < a.H; i += SEARCH_THREADS) {
+            hkeys[i] = EMPTY;
+            prio[i] = INF;
+        }
+        if (tid == 0) {
+            s_ncur = 0;
+            s_nnext = 0;
+            s_cursor = 0;
+            s_fill = 0;
+            s_fail = 0;
+            s_stop = 0;
+        }
+        __syncthreads();
+        const uint32_t ti = s_tile;
+        if (ti >= ntiles) break;
+        const uint32_t tile = a.tile_list ? a.tile_list[ti] : ti;
+        const uint32_t first = tile * T;
+        const uint32_t tsz = min(uint32_t(T), nR - first);
+
+        // sources: lane t of every row belongs to R node first + t, at distance 0
+        if (tid < T) src_orig[tid] = 0;
+        __syncthreads();
+        if (tid < tsz) {
+            uint32_t y = a.src[first + tid];
+            src_orig[tid] = a.iperm[y];
+            uint32_t h = find_or_insert(hkeys, a.H, a.hshift, y, &s_fill, a.max_fill, &s_fail);
+            __stcg(&slab[size_t(h) * T + tid], 0u);
+            prio[h] = 0;
+            qa[atomicAdd(&s_ncur, 1u)] = h;
+        }
+        uint32_t *qcur = qa, *qnext = qb;
+        uint64_t tau = delta;  // end (exclusive) of the current bucket
+        if (tau > uint64_t(bound) + 1) tau = uint64_t(bound) + 1;
+
+        for (;;) {
+            // ---- rounds of the current bucket: relax the near queue until it drains
+            for (;;) {
+                // s_ncur and s_stop are written only by thread 0 after the barrier that
+                // ends a round (or by the collect step before this barrier), and read
+                // here by all threads before the next round's barrier: every thread
+                // takes the same decision.
+                __syncthreads();
+                const uint32_t ncur = min(s_ncur, QCAP);
+                if (ncur == 0 || s_stop) break;
+                for (;;) {
+                    uint32_t i = 0;
+                    if (lane == 0) i = atomicAdd(&s_cursor, 1u);
+                    i = __shfl_sync(FULL, i, 0);
+                    if (i >= ncur) break;
+                    const uint32_t x = qcur[i];
+                    uint32_t p = 0;
+                    if (lane == 0) p = atomicExch(&prio[x], INF);
+                    p = __shfl_sync(FULL, p, 0);
+                    if (p == INF) continue;  // scanned since it was queued
+                    __threadfence_block();
+                    my_scans++;
+                    const uint32_t y0 = hkeys[x];
+                    const Row<L> dx = load_row<L>(slab + size_t(x) * T + lane * L);
+                    uint32_t dmin = dx.x[0];
+#pragma unroll
+                    for (int j = 1; j < L; j++) dmin = min(dmin, dx.x[j]);
+                    dmin = __reduce_min_sync(FULL, dmin);
+                    if (dmin > bound) continue;
+                    const uint32_t beg = __ldg(&a.row_ptr[y0]), end = __ldg(&a.row_ptr[y0 + 1]);
+                    for (uint32_t e0 = beg; e0 < end; e0 += 32) {
+                        const uint32_t e = e0 + lane;
+                        uint2 arc = make_uint2(0, 0);
+                        bool need = false;
+                        if (e < end) {
+                            arc = __ldg(&a.adj[e]);
+                            need = dmin + arc.y <= bound;
+                        }
+                        uint32_t hy = EMPTY;
+                        if (need) hy = find_or_insert(hkeys, a.H, a.hshift, arc.x, &s_fill, a.max_fill, &s_fail);
+                        uint32_t m = __ballot_sync(FULL, hy != EMPTY);
+                        while (m) {
+                            const int j = __ffs(m) - 1;
+                            m &= m - 1;
+                            const uint32_t hj = __shfl_sync(FULL, hy, j);
+                            const uint32_t wj = __shfl_sync(FULL, arc.y, j);
+                            uint32_t *row = slab + size_t(hj) * T + lane * L;
+                            const Row<L> cur = load_row<L>(row);
+                            uint32_t imin = INF;
+#pragma unroll
+                            for (int q = 0; q < L; q++) {
+                                if (dx.x[q] != INF) {
+                                    const uint32_t d = dx.x[q] + wj;
+                                    if (d <= bound && d < cur.x[q]) {
+                                        atomicMin(row + q, d);
+                                        imin = min(imin, d);
+                                    }
+                                }
+                            }
+                            imin = __reduce_min_sync(FULL, imin);
+                            if (imin != INF) {
+                                __threadfence_block();
+                                __syncwarp();
+                                if (lane == 0) {
+                                    const uint32_t old = atomicMin(&prio[hj], imin);
+                                    if (imin < tau && (old == INF || old >= tau)) {
+                                        const uint32_t qi = atomicAdd(&s_nnext, 1u);
+                                        if (qi < QCAP) qnext[qi] = hj;
+                                    }
+                                }
+                            }
+                        }
+                    }
+                }
+                __syncthreads();
+                if (tid == 0) {
+                    s_ncur = s_nnext;
+                    s_nnext = 0;
+                    s_cursor = 0;
+                    s_stop = s_fail;
+                }
+                uint32_t *t = qcur;
+                qcur = qnext;
+                qnext = t;
+            }
+            if (s_fail) break;
+            // ---- the near queue is empty: find the smallest pending priority
+            if (tid == 0) s_minp = INF;
+            __syncthreads();
+            uint32_t mp = INF;
+            for (uint32_t h = tid; h < a.H; h += SEARCH_THREADS) mp = min(mp, prio[h]);
+            mp = __reduce_min_sync(FULL, mp);
+            if (lane == 0 && mp != INF) atomicMin(&s_minp, mp);
+            __syncthreads();
+            const uint32_t minp = s_minp;
+            if (minp == INF) break;  // nothing pending: the tile's search is complete
+            if (minp >= tau) {
+                tau = (uint64_t(minp) / delta + 1) * delta;
+                if (tau > uint64_t(bound) + 1) tau = uint64_t(bound) + 1;
+            }
+            // ---- collect every pending slot of the (new) bucket into the near queue
+            for (uint32_t h = tid; h < a.H; h += SEARCH_THREADS) {
+                if (prio[h] < tau) {
+                    const uint32_t qi = atomicAdd(&s_ncur, 1u);
+                    if (qi < QCAP) qcur[qi] = h;
+                }
+            }
+        }
+        __syncthreads();
+
+        // ---- emission: every slot of an S node, every lane within the bound
+        const bool ok = !s_fail;
+        if (ok) {
+            uint32_t cnt = 0;
+            for (uint32_t h = warp; h < a.H; h += SEARCH_WARPS) {
+                const uint32_t y = hkeys[h];
+                if (y == EMPTY || !((__ldg(&a.sbits[y >> 5]) >> (y & 31)) & 1u)) continue;
+                const Row<L> r = load_row<L>(slab + size_t(h) * T + lane * L);
+#pragma unroll
+                for (int q = 0; q < L; q++) cnt += __popc(__ballot_sync(FULL, r.x[q] <= bound));
+            }
+            if (lane == 0) s_warp_cnt[warp] = cnt;
+            __syncthreads();
+            if (tid == 0) {
+                uint32_t run = 0;
+                for (int w = 0; w < SEARCH_WARPS; w++) {
+                    uint32_t c = s_warp_cnt[w];
+                    s_warp_cnt[w] = run;
+                    run += c;
+                }
+                s_base = atomicAdd(&a.ctl->pairs, (unsigned long long)run);
+            }
+            __syncthreads();
+            unsigned long long pos = s_base + s_warp_cnt[warp];
+            const uint32_t lt = (1u << lane) - 1;
+            for (uint32_t h = warp; h < a.H; h += SEARCH_WARPS) {
+                const uint32_t y = hkeys[h];
+                if (y == EMPTY || !((__ldg(&a.sbits[y >> 5]) >> (y & 31)) & 1u)) continue;
+                const Row<L> r = load_row<L>(slab + size_t(h) * T + lane * L);
+                const unsigned long long v = __ldg(&a.iperm[y]);
+#pragma unroll
+                for (int q = 0; q < L; q++) {
+                    const bool hit = r.x[q] <= bound;
+                    const uint32_t b = __ballot_sync(FULL, hit);
+                    if (hit) {
+                        const unsigned long long idx = pos + __popc(b & lt);
+                        if (idx < a.out_cap) {
+                            const unsigned long long u = src_orig[lane * L + q];
+                            a.out_key[idx] = (u << a.vbits) | v;
+                            a.out_d[idx] = r.x[q];
+                        }
+                    }
+                    pos += __popc(b);
+                }
+            }
+        } else if (tid == 0) {
+            a.failed[atomicAdd(&a.ctl->n_failed, 1u)] = tile;
+        }
+        // ---- leave the region clean (every row INF) for the next tile
+        for (uint32_t h = warp; h < a.H; h += SEARCH_WARPS) {
+            const uint32_t y = hkeys[h];
+            if (y == EMPTY) continue;
+            store_inf<L>(slab + size_t(h) * T + lane * L);
+            if (ok) {
+                my_slots++;
+                my_arcs += __ldg(&a.row_ptr[y + 1]) - __ldg(&a.row_ptr[y]);
+            }
+        }
+        __syncthreads();
+    }
+    if (lane == 0) {
+        atomicAdd(&a.ctl->scans, my_scans);
+        atomicAdd(&a.ctl->slots, my_slots);
+        atomicAdd(&a.ctl->slot_arcs, my_arcs);
+    }
+}
+
+// ------------------------------------------------------------- radix sort ----
+// LSD radix sort of (64-bit key, 32-bit value) records, 8 bits per pass.  Stable within
+// a pass: a block's 2048 records are ranked warp by warp and round by round.
+
+constexpr int RS_THREADS = 256;
+constexpr int RS_WARPS = RS_THREADS / 32;
+constexpr int RS_ROUNDS = 8;
+constexpr int RS_TILE = RS_THREADS * RS_ROUNDS;
+
+__device__ __forceinline__ uint32_t rs_digit(unsigned long long k, uint32_t v, int shift) {
+    // shift < 64: bits of the key; shift >= 64: bits of the value
+    return shift < 64 ? uint32_t(k >> shift) & 0xFFu : (v >> (shift - 64)) & 0xFFu;
+}
+
+__global__ void k_rs_hist(const unsigned long long *__restrict__ keys, const uint32_t *__restrict__ vals,
+                          uint64_t n, int shift, uint32_t *hist, uint32_t nblocks) {
+    __shared__ uint32_t cnt[256];
+    for (int i = threadIdx.x; i < 256; i += RS_THREADS) cnt[i] = 0;
+    __syncthreads();
+    const uint64_t base = uint64_t(blockIdx.x) * RS_TILE;
+    for (int r = 0; r < RS_ROUNDS; r++) {
+        const uint64_t i = base + uint64_t(r) * RS_THREADS + threadIdx.x;
+        if (i < n) atomicAdd(&cnt[rs_digit(keys[i], vals[i], shift)], 1u);
+    }
+    __syncthreads();
+    for (int d = threadIdx.x; d < 256; d += RS_THREADS) hist[uint64_t(d) * nblocks + blockIdx.x] = cnt[d];
+}
+
+// Exclusive scan of hist[0..total) in place, one block.
+__global__ void k_rs_scan(uint32_t *hist, uint32_t total) {
+    __shared__ uint32_t warp_sum[32];
+    __shared__ uint32_t carry;
+    if (threadIdx.x == 0) carry = 0;
+    __syncthreads();
+    const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (uint32_t base = 0; base < total; base += 1024) {
+        const uint32_t i = base + threadIdx.x;
+        const uint32_t v = i < total ? hist[i] : 0;
+        uint32_t x = v;
+        for (int o = 1; o < 32; o <<= 1) {
+            uint32_t t = __shfl_up_sync(FULL, x, o);
+            if (lane >= o) x += t;
+        }
+        if (lane == 31) warp_sum[warp] = x;
+        __syncthreads();
+        if (warp == 0) {
+            uint32_t s = warp_sum[lane], y = s;
+            for (int o = 1; o < 32; o <<= 1) {
+                uint32_t t = __shfl_up_sync(FULL, y, o);
+                if (lane >= o) y += t;
+            }
+            warp_sum[lane] = y - s;
+        }
+        __syncthreads();
+        const uint32_t c = carry;
+        if (i < total) hist[i] = c + warp_sum[warp] + x - v;
+        __syncthreads();
+        if (threadIdx.x == 1023) carry = c + warp_sum[warp] + x;
+        __syncthreads();
+    }
+}
+
+// Scatter pass.  With out_u != null the pass is the last one of a join sort and writes
+// the struct-of-arrays result (u = key >> vbits, v = key & mask, d = value) directly.
+__global__ void k_rs_scatter(const unsigned long long *__restrict__ kin, const uint32_t *__restrict__ vin,
+                             unsigned long long *kout, uint32_t *vout, uint64_t n, int shift,
+                             const uint32_t *__restrict__ hist, uint32_t nblocks, uint32_t *out_u,
+                             uint32_t *out_v, uint32_t *out_d, uint32_t vbits) {
+    __shared__ uint32_t wcnt[RS_WARPS][256];
+    const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int i = threadIdx.x; i < RS_WARPS * 256; i += RS_THREADS) (&wcnt[0][0])[i] = 0;
+    __syncthreads();
+    const uint64_t base = uint64_t(blockIdx.x) * RS_TILE + uint64_t(warp) * (RS_ROUNDS * 32);
+    unsigned long long k[RS_ROUNDS];
+    uint32_t v[RS_ROUNDS], dg[RS_ROUNDS], rank[RS_ROUNDS];
+    const uint32_t lt = (1u << lane) - 1;
+#pragma unroll
+    for (int r = 0; r < RS_ROUNDS; r++) {
+        const uint64_t i = base + uint64_t(r) * 32 + lane;
+        const bool valid = i < n;
+        k[r] = valid ? kin[i] : 0ull;
+        v[r] = valid ? vin[i] : 0u;
+        dg[r] = valid ? rs_digit(k[r], v[r], shift) : 256u;
+        const uint32_t peers = __match_any_sync(FULL, dg[r]);
+        const uint32_t before = valid ? wcnt[warp][dg[r]] : 0u;
+        __syncwarp();
+        rank[r] = before + __popc(peers & lt);
+        if (valid && (peers & lt) == 0) wcnt[warp][dg[r]] = before + __popc(peers);
+        __syncwarp();
+    }
+    __syncthreads();
+    for (int d = threadIdx.x; d < 256; d += RS_THREADS) {
+        uint32_t run = 0;
+        for (int w = 0; w < RS_WARPS; w++) {
+            const uint32_t c = wcnt[w][d];
+            wcnt[w][d] = run;
+            run += c;
+        }
+    }
+    __syncthreads();
+    const unsigned long long vmask = (1ull << vbits) - 1;
+#pragma unroll
+    for (int r = 0; r < RS_ROUNDS; r++) {
+        if (dg[r] == 256u) continue;
+        const uint64_t pos = uint64_t(hist[uint64_t(dg[r]) * nblocks + blockIdx.x]) + wcnt[warp][dg[r]] + rank[r];
+        if (out_u) {
+            out_u[pos] = uint32_t(k[r] >> vbits);
+            out_v[pos] = uint32_t(k[r] & vmask);
+            out_d[pos] = v[r];
+        } else {
+            kout[pos] = k[r];
+            vout[pos] = v[r];
+        }
+    }
+}
+
+// Sort n records in (keyA, valA) by the listed digit shifts (least significant first);
+// the last pass writes the struct-of-arrays result into out.
+static void radix_sort_to_pairs(Workspace *ws, uint64_t n, const std::vector<int> &shifts,
+                                uint32_t vbits, rn_dpairs *out, cudaStream_t st) {
+    if (n == 0) return;
+    if (n > 0xFFFFFFFFull) fail(RN_EINVAL, "more than 2^32 - 1 result pairs");
+    const uint32_t nblocks = uint32_t((n + RS_TILE - 1) / RS_TILE);
+    grow(ws, &ws->hist, &ws->hist_cap, uint64_t(nblocks) * 256, 4);
+    unsigned long long *ki = ws->keyA, *ko = ws->keyB;
+    uint32_t *vi = ws->valA, *vo = ws->valB;
+    for (size_t p = 0; p < shifts.size(); p++) {
+        const bool last = p + 1 == shifts.size();
+        k_rs_hist<<<nblocks, RS_THREADS, 0, st>>>(ki, vi, n, shifts[p], ws->hist, nblocks);
+        k_rs_scan<<<1, 1024, 0, st>>>(ws->hist, nblocks * 256);
+        k_rs_scatter<<<nblocks, RS_THREADS, 0, st>>>(ki, vi, ko, vo, n, shifts[p], ws->hist, nblocks,
+                                                     last ? out->u : nullptr, last ? out->v : nullptr,
+                                                     last ? out->d : nullptr, vbits);
+        std::swap(ki, ko);
+        std::swap(vi, vo);
+        ws->launches += 3;
+    }
+    RN_CUDA(cudaGetLastError());
+}
+
+// ------------------------------------------------------------ orchestration ----
+
+static uint32_t bits_for(uint32_t n) {
+    uint32_t b = 1;
+    while (b < 32 && (1ull << b) < n) b++;
+    return b;
+}
+
+static size_t search_smem(uint32_t H, bool gmap) { return (gmap ? 0 : size_t(H) * 8) + size_t(QCAP) * 8; }
+
+template <int L, bool GMAP>
+static void launch_search(const SearchArgs &a, uint32_t grid, cudaStream_t st) {
+    const size_t smem = search_smem(a.H, GMAP);
+    static std::once_flag once;
+    std::call_once(once, [&] {
+        RN_CUDA(cudaFuncSetAttribute(k_tile_search<L, GMAP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     int(search_smem(SMEM_H, GMAP))));
+    });
+    k_tile_search<L, GMAP><<<grid, SEARCH_THREADS, smem, st>>>(a);
+    RN_CUDA(cudaGetLastError());
+}
+
+static void search(uint32_t T, bool gmap, const SearchArgs &a, uint32_t grid, cudaStream_t st) {
+    switch (T * 2 + (gmap ? 1 : 0)) {
+        case 64: launch_search<1, false>(a, grid, st); break;
+        case 65: launch_search<1, true>(a, grid, st); break;
+        case 128: launch_search<2, false>(a, grid, st); break;
+        case 129: launch_search<2, true>(a, grid, st); break;
+        case 256: launch_search<4, false>(a, grid, st); break;
+        case 257: launch_search<4, true>(a, grid, st); break;
+        default: fail(RN_EINVAL, "tile width must be 32, 64 or 128");
+    }
+}
+
+static Control read_control(Workspace *ws, cudaStream_t st) {
+    RN_CUDA(cudaMemcpyAsync(ws->ctl_host, ws->ctl, sizeof(Control), cudaMemcpyDeviceToHost, st));
+    RN_CUDA(cudaStreamSynchronize(st));
+    return *ws->ctl_host;
+}
+
+// Search every tile (the shared-memory map first), then search again, with a global
+// map four times larger each time, the tiles whose union ball overflowed.  The map
+// never needs to exceed the next power of two >= 2n, where it cannot overflow.
+static Control search_all(const DeviceGraph &g, Workspace *ws, uint32_t T, SearchArgs a,
+                          uint32_t ntiles, cudaStream_t st, uint64_t *retried) {
+    const uint32_t grid_max = uint32_t(ws->num_sms) * CTAS_PER_SM;
+    const uint32_t grid = std::max<uint32_t>(1, std::min(ntiles, grid_max));
+    a.gmap = nullptr;
+    a.tile_list = nullptr;
+    a.ntiles = ntiles;
+    a.H = SMEM_H;
+    a.hshift = 32 - bits_for(SMEM_H);
+    a.max_fill = SMEM_H * 3 / 4;
+    a.failed = ws->failed;
+    RN_CUDA(cudaEventRecord(ws->evs0, st));
+    if (ntiles) {
+        search(T, false, a, grid, st);
+        ws->launches++;
+    }
+    RN_CUDA(cudaEventRecord(ws->evs1, st));
+    Control c = read_control(ws, st);
+    uint64_t hcap = 1;
+    while (hcap < 2ull * g.n) hcap <<= 1;
+    uint64_t H = SMEM_H;
+    uint32_t *list = ws->failed, *next = ws->failed2;
+    while (c.n_failed && !c.err) {
+        if (H >= hcap) fail(RN_EINTERNAL, "slot map overflowed at its largest size");
+        H = std::min<uint64_t>(H * 4, hcap);
+        const uint32_t nf = c.n_failed;
+        *retried += nf;
+        const size_t per_block = (2 * H + H * T) * 4;
+        const size_t budget = size_t(8) << 30;
+        const uint32_t rgrid = uint32_t(std::max<size_t>(1, std::min<size_t>({nf, grid_max, budget / per_block})));
+        uint32_t *mem = (uint32_t *)device_alloc(per_block * rgrid);
+        try {
+            RN_CUDA(cudaMemsetAsync(mem, 0xFF, per_block * rgrid, st));
+            RN_CUDA(cudaMemsetAsync(&ws->ctl->tile_next, 0, 8, st));  // tile_next, n_failed
+            std::swap(list, next);
+            SearchArgs r = a;
+            r.gmap = mem;
+            r.slab = mem + size_t(rgrid) * 2 * H;
+            r.H = uint32_t(H);
+            r.hshift = 32 - bits_for(uint32_t(H));
+            r.max_fill = uint32_t(H * 3 / 4);
+            r.tile_list = list;
+            r.ntiles = nf;
+            r.failed = next;
+            search(T, true, r, rgrid, st);
+            ws->launches++;
+            c = read_control(ws, st);
+        } catch (...) {
+            device_free(mem);
+            throw;
+        }
+        device_free(mem);
+    }
+    return c;
+}
+
+static uint32_t choose_delta(const EngineConfig &cfg, uint32_t median_w) {
+    if (cfg.delta) return cfg.delta;
+    return std::max<uint32_t>(1, median_w);
+}
+
+static void ensure_u32(uint32_t **p, uint32_t *cap, uint32_t want) {
+    if (*p && *cap >= want) return;
+    device_free(*p);
+    *p = nullptr;
+    *cap = std::max<uint32_t>(want, 1024);
+    *p = (uint32_t *)device_alloc(size_t(*cap) * 4);
+}
+
+static void ensure_pairs(Workspace *ws, uint64_t want) {
+    if (ws->pair_cap >= want && ws->keyA) return;
+    want = std::max<uint64_t>(want, 1 << 16);
+    for (void **p : {(void **)&ws->keyA, (void **)&ws->keyB, (void **)&ws->valA, (void **)&ws->valB}) {
+        device_free(*p);
+        *p = nullptr;
+    }
+    ws->bytes -= ws->pair_cap * 24;
+    ws->pair_cap = 0;
+    ws->keyA = (unsigned long long *)device_alloc(want * 8);
+    ws->keyB = (unsigned long long *)device_alloc(want * 8);
+    ws->valA = (uint32_t *)device_alloc(want * 4);
+    ws->valB = (uint32_t *)device_alloc(want * 4);
+    ws->pair_cap = want;
+    ws->bytes += want * 24;
+}
+
+static void ensure_slab(Workspace *ws) {
+    const uint32_t grid_max = uint32_t(ws->num_sms) * CTAS_PER_SM;
+    if (ws->slab && ws->slab_ctas >= grid_max) return;
+    device_free(ws->slab);
+    ws->slab = nullptr;
+    ws->bytes -= ws->slab_bytes;
+    ws->slab_bytes = size_t(SMEM_H) * 128 * 4 * grid_max;  // rows of the widest tile
+    ws->slab = (uint32_t *)device_alloc(ws->slab_bytes);
+    RN_CUDA(cudaMemset(ws->slab, 0xFF, ws->slab_bytes));  // every row INF
+    ws->slab_ctas = grid_max;
+    ws->bytes += ws->slab_bytes;
+}
+
+// a2: validate R and S on the device, build the S membership bitmap and the list of R
+// nodes in increasing internal id (so consecutive sources are graph neighbours).
+static void prep_sets(const DeviceGraph &g, Workspace *ws, const uint32_t *dR, uint32_t nR,
+                      const uint32_t *dS, uint32_t nS, cudaStream_t st) {
+    RN_CUDA(cudaMemsetAsync(ws->used_bits, 0, size_t(ws->nwords) * 4, st));
+    RN_CUDA(cudaMemsetAsync(ws->rbits, 0, size_t(ws->nwords) * 4, st));
+    RN_CUDA(cudaMemsetAsync(ws->sbits, 0, size_t(ws->nwords) * 4, st));
+    RN_CUDA(cudaMemsetAsync(ws->ctl, 0, sizeof(Control), st));
+    if (nR)
+        k_mark_set<<<std::min<uint32_t>((nR + 255) / 256, 4096), 256, 0, st>>>(dR, nR, g.n, g.perm, ws->used_bits,
+                                                                               ws->rbits, ws->ctl);
+    if (nS)
+        k_mark_set<<<std::min<uint32_t>((nS + 255) / 256, 4096), 256, 0, st>>>(dS, nS, g.n, g.perm, ws->used_bits,
+                                                                               ws->sbits, ws->ctl);
+    ensure_u32(&ws->rsorted, &ws->rsorted_cap, std::max<uint32_t>(nR, 1));
+    const uint32_t nblocks = (ws->nwords + 1023) / 1024;
+    k_bits_count<<<nblocks, 1024, 0, st>>>(ws->rbits, ws->nwords, ws->block_sums);
+    k_bits_compact<<<nblocks, 1024, 0, st>>>(ws->rbits, ws->nwords, ws->block_sums, nblocks, ws->rsorted, ws->ctl);
+    ws->launches += (nR ? 1 : 0) + (nS ? 1 : 0) + 2;
+    RN_CUDA(cudaGetLastError());
+}
+
+static void check_control(const Control &c) {
+    if (c.err & 1u) fail(RN_EINVAL, "a node id of R or S is >= n");
+    if (c.err & 2u) fail(RN_EINVAL, "R or S repeats an id, or R and S overlap");
+}
+
+void run_join(const DeviceGraph &g, Workspace *ws, const EngineConfig &cfg, uint32_t median_w,
+              const uint32_t *dR, uint32_t nR, const uint32_t *dS, uint32_t nS, uint32_t theta,
+              rn_dpairs *out, void *stream, rn_query_stats *stats) {
+    cudaStream_t st = (cudaStream_t)stream;
+    if (theta == RN_INF) theta = RN_THETA_MAX;
+    if (theta > RN_THETA_MAX) fail(RN_EINVAL, "theta must be <= 2^31 or RN_INF");
+    const uint32_t T = cfg.tile_width ? cfg.tile_width : 32;
+    if (T != 32 && T != 64 && T != 128) fail(RN_EINVAL, "tile width must be 32, 64 or 128");
+    const uint32_t delta = choose_delta(cfg, median_w);
+    *stats = rn_query_stats{};
+    stats->tile_width = T;
+    stats->delta = delta;
+    stats->theta_final = theta;
+    ws->launches = 0;
+    RN_CUDA(cudaEventRecord(ws->ev0, st));
+
+    prep_sets(g, ws, dR, nR, dS, nS, st);
+    const uint32_t ntiles = (nR + T - 1) / T;
+    ensure_u32(&ws->failed, &ws->failed_cap, std::max<uint32_t>(ntiles, 1));
+    ensure_u32(&ws->failed2, &ws->failed2_cap, std::max<uint32_t>(ntiles, 1));
+    ensure_slab(ws);
+    ensure_pairs(ws, std::max<uint64_t>(ws->pair_cap, uint64_t(nR) * 64));
+
+    const uint32_t vbits = bits_for(g.n);
+    SearchArgs a{};
+    a.row_ptr = g.row_ptr;
+    a.adj = reinterpret_cast<const uint2 *>(g.adj);
+    a.iperm = g.iperm;
+    a.sbits = ws->sbits;
+    a.src = ws->rsorted;
+    a.bound = theta;
+    a.delta = delta;
+    a.slab = ws->slab;
+    a.vbits = vbits;
+    a.ctl = ws->ctl;
+    a.out_key = ws->keyA;
+    a.out_d = ws->valA;
+    a.out_cap = ws->pair_cap;
+    uint64_t retried = 0;
+    Control c = search_all(g, ws, T, a, ntiles, st, &retried);
+    check_control(c);
+    if (c.pairs > ws->pair_cap) {
+        // the pair buffer was too small: grow it and search again (same result)
+        ensure_pairs(ws, c.pairs + c.pairs / 8);
+        prep_sets(g, ws, dR, nR, dS, nS, st);
+        a.out_key = ws->keyA;
+        a.out_d = ws->valA;
+        a.out_cap = ws->pair_cap;
+        c = search_all(g, ws, T, a, ntiles, st, &retried);
+        check_control(c);
+        if (c.pairs > ws->pair_cap) fail(RN_EINTERNAL, "pair count changed between passes");
+    }
+    const uint64_t np = c.pairs;
+
+    // a5: canonical order by (u, v), written straight into the caller's buffers
+    dpairs_reserve(out, np);
+    std::vector<int> shifts;
+    for (uint32_t sh = 0; sh < 2 * vbits; sh += 8) shifts.push_back(int(sh));
+    radix_sort_to_pairs(ws, np, shifts, vbits, out, st);
+    out->n = np;
+    RN_CUDA(cudaEventRecord(ws->ev1, st));
+    RN_CUDA(cudaEventSynchronize(ws->ev1));
+    float ms = 0, sms = 0;
+    RN_CUDA(cudaEventElapsedTime(&ms, ws->ev0, ws->ev1));
+    RN_CUDA(cudaEventElapsedTime(&sms, ws->evs0, ws->evs1));
+    stats->pairs = np;
+    stats->tiles = ntiles;
+    stats->retried_tiles = retried;
+    stats->scans = c.scans;
+    stats->slots = c.slots;
+    stats->slot_arcs = c.slot_arcs;
+    stats->passes = 1;
+    stats->launches = ws->launches;
+    stats->device_ms = ms;
+    stats->search_ms = sms;
+}
+
+void run_kcp(const DeviceGraph &, Workspace *, const EngineConfig &, uint32_t, const uint32_t *,
+             uint32_t, const uint32_t *, uint32_t, uint64_t, uint32_t, rn_dpairs *, void *,
+             rn_query_stats *) {
+    fail(RN_ENOTIMPL, "k closest pairs is not built yet");
+}
+
+}  // namespace rn

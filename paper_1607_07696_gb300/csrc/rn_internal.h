@@ -1,0 +1,111 @@
+// Internal declarations shared by the host runtime (rn_graph.cpp, rn_api.cpp) and the
+// CUDA engine (rn_engine.cu).  Not part of the public ABI (include/rn.h).
+#pragma once
+
+#include <cstdint>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "rn.h"
+
+namespace rn {
+
+// Every internal failure is thrown as an Error and turned into an rn_status at the ABI.
+struct Error {
+    rn_status status;
+    std::string msg;
+};
+
+[[noreturn]] void fail(rn_status s, const std::string &msg);
+
+// Compressed sparse rows in host memory: the arcs leaving node x are
+// (col[e], w[e]) for e in [row_ptr[x], row_ptr[x+1]), sorted by (col, w).
+struct HostGraph {
+    uint32_t n = 0;
+    std::vector<uint32_t> row_ptr;
+    std::vector<uint32_t> col;
+    std::vector<uint32_t> w;
+    uint64_t arcs() const { return col.size(); }
+};
+
+// Edge list -> cleaned CSR (self-loops dropped, parallel arcs reduced to least weight).
+HostGraph build_csr(uint32_t n, uint64_t m, const uint32_t *src, const uint32_t *dst,
+                    const uint32_t *w, bool undirected);
+
+// Recursive two-seed bisection (Algorithm 1 with the smoothing of Eq. 1-2).  Returns
+// order[i] = the original id placed at internal id i; every partition of the hierarchy
+// occupies a contiguous range of internal ids.
+std::vector<uint32_t> bisection_order(const HostGraph &g, uint32_t leaf_size, float alpha);
+
+// CSR of g relabelled so that internal id i is original node order[i].
+HostGraph relabel(const HostGraph &g, const std::vector<uint32_t> &order);
+
+// The graph as it lives on the device.
+struct DeviceGraph {
+    uint32_t n = 0;
+    uint64_t arcs = 0;
+    uint32_t *row_ptr = nullptr;  // n + 1
+    uint32_t *adj = nullptr;      // 2 * arcs: (col, w) interleaved, 8-byte aligned
+    uint32_t *perm = nullptr;     // original id -> internal id
+    uint32_t *iperm = nullptr;    // internal id -> original id
+};
+
+struct Workspace;  // device scratch owned by a graph (rn_engine.cu)
+
+struct QueryStats {
+    rn_query_stats s{};
+};
+
+// Engine entry points (rn_engine.cu).  All device pointers; work ordered on `stream`.
+Workspace *workspace_create(const DeviceGraph &g);
+void workspace_destroy(Workspace *ws);
+uint64_t workspace_bytes(const Workspace *ws);
+
+struct EngineConfig {
+    uint32_t tile_width = 32;
+    uint32_t delta = 0;  // 0: derive from the weights
+};
+
+void run_join(const DeviceGraph &g, Workspace *ws, const EngineConfig &cfg, uint32_t median_w,
+              const uint32_t *dR, uint32_t nR, const uint32_t *dS, uint32_t nS, uint32_t theta,
+              rn_dpairs *out, void *stream, rn_query_stats *stats);
+
+void run_kcp(const DeviceGraph &g, Workspace *ws, const EngineConfig &cfg, uint32_t median_w,
+             const uint32_t *dR, uint32_t nR, const uint32_t *dS, uint32_t nS, uint64_t k,
+             uint32_t theta, rn_dpairs *out, void *stream, rn_query_stats *stats);
+
+void upload_graph(const HostGraph &g, const std::vector<uint32_t> &perm,
+                  const std::vector<uint32_t> &iperm, DeviceGraph *out);
+void free_graph(DeviceGraph *g);
+void dpairs_reserve(rn_dpairs *p, uint64_t cap);
+void dpairs_release(rn_dpairs *p);
+void copy_to_host(void *dst, const void *src, size_t bytes, void *stream);
+void copy_to_device(void *dst, const void *src, size_t bytes, void *stream);
+void *device_alloc(size_t bytes);
+void device_free(void *p);
+void stream_sync(void *stream);
+
+}  // namespace rn
+
+namespace rn {
+// Device copies of host R and S and a device result buffer, used by the host-buffer
+// entry points of one graph.
+struct HostScratch {
+    uint32_t *dR = nullptr, *dS = nullptr;
+    uint32_t capR = 0, capS = 0;
+    rn_dpairs res{};
+    void *stream = nullptr;  // cudaStream_t owned by the graph
+};
+}  // namespace rn
+
+struct rn_graph {
+    rn::DeviceGraph dev;
+    rn::Workspace *ws = nullptr;
+    rn::EngineConfig cfg;
+    rn_graph_stats info{};
+    std::vector<uint32_t> perm;  // host copy: original -> internal
+    std::mutex mu;
+    rn::HostScratch hs;
+    int device = 0;
+};

@@ -1,0 +1,288 @@
+"""Python binding of the engine's C ABI (include/rn.h): argument marshalling only.
+
+Every function here forwards to the function of the same name in ``librn.so``; all the
+work of a query runs in the library's CUDA kernels.  The library is built in-tree by
+``paper_1607_07696_gb300.build`` (or ``__graft_entry__.build()``); importing this module
+without it raises -- there is no fallback of any kind.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from dataclasses import dataclass
+
+import numpy as np
+
+LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "librn.so")
+
+RN_OK, RN_EINVAL, RN_ENOMEM, RN_ECUDA, RN_ETIMEOUT = 0, 1, 2, 3, 4
+RN_ECANCELLED, RN_EBUSY, RN_EINTERNAL, RN_ENOTIMPL = 5, 6, 7, 8
+RN_UNDIRECTED, RN_REORDER = 1, 2
+RN_INF = 0xFFFFFFFF
+RN_THETA_MAX = 1 << 31
+
+_NAMES = {0: "RN_OK", 1: "RN_EINVAL", 2: "RN_ENOMEM", 3: "RN_ECUDA", 4: "RN_ETIMEOUT",
+          5: "RN_ECANCELLED", 6: "RN_EBUSY", 7: "RN_EINTERNAL", 8: "RN_ENOTIMPL"}
+
+
+class RNError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+class rn_pairs(C.Structure):
+    _fields_ = [("u", C.POINTER(C.c_uint32)), ("v", C.POINTER(C.c_uint32)),
+                ("d", C.POINTER(C.c_uint32)), ("n", C.c_uint64)]
+
+
+class rn_dpairs(C.Structure):
+    _fields_ = [("u", C.c_void_p), ("v", C.c_void_p), ("d", C.c_void_p), ("n", C.c_uint64),
+                ("cap", C.c_uint64)]
+
+
+class rn_config(C.Structure):
+    _fields_ = [("tile_width", C.c_uint32), ("delta", C.c_uint32), ("leaf_size", C.c_uint32),
+                ("alpha", C.c_float)]
+
+
+class rn_graph_stats(C.Structure):
+    _fields_ = [("n", C.c_uint32), ("arcs", C.c_uint64), ("max_degree", C.c_uint32),
+                ("median_weight", C.c_uint32), ("flags", C.c_uint32), ("reorder_ms", C.c_double),
+                ("device_bytes", C.c_uint64)]
+
+
+class rn_query_stats(C.Structure):
+    _fields_ = [("pairs", C.c_uint64), ("tiles", C.c_uint64), ("retried_tiles", C.c_uint64),
+                ("scans", C.c_uint64), ("tile_width", C.c_uint32), ("delta", C.c_uint32),
+                ("passes", C.c_uint32), ("theta_final", C.c_uint32), ("launches", C.c_uint32),
+                ("slots", C.c_uint64), ("slot_arcs", C.c_uint64), ("device_ms", C.c_double),
+                ("search_ms", C.c_double)]
+
+
+# Every symbol include/rn.h declares, with its ctypes signature (restype, argtypes).
+_P32 = C.POINTER(C.c_uint32)
+_G = C.c_void_p
+SIGNATURES = {
+    "rn_graph_load": (C.c_int, [_P32, _P32, _P32, C.c_uint64, C.c_uint32, C.c_uint32,
+                                C.POINTER(rn_config), C.POINTER(C.c_void_p)]),
+    "rn_graph_free": (None, [_G]),
+    "rn_bisection_order": (C.c_int, [_P32, _P32, _P32, C.c_uint64, C.c_uint32, C.c_uint32,
+                                     C.POINTER(rn_config), _P32]),
+    "rn_graph_info": (C.c_int, [_G, C.POINTER(rn_graph_stats)]),
+    "rn_graph_permutation": (C.c_int, [_G, _P32]),
+    "rn_graph_set_config": (C.c_int, [_G, C.POINTER(rn_config)]),
+    "rn_distance_join": (C.c_int, [_G, _P32, C.c_uint32, _P32, C.c_uint32, C.c_uint32,
+                                   C.POINTER(rn_pairs)]),
+    "rn_distance_join_dev": (C.c_int, [_G, C.c_void_p, C.c_uint32, C.c_void_p, C.c_uint32,
+                                       C.c_uint32, C.POINTER(rn_dpairs), C.c_void_p]),
+    "rn_kcp": (C.c_int, [_G, _P32, C.c_uint32, _P32, C.c_uint32, C.c_uint64, C.c_uint32,
+                         C.POINTER(rn_pairs)]),
+    "rn_kcp_dev": (C.c_int, [_G, C.c_void_p, C.c_uint32, C.c_void_p, C.c_uint32, C.c_uint64,
+                             C.c_uint32, C.POINTER(rn_dpairs), C.c_void_p]),
+    "rn_pairs_free": (None, [C.POINTER(rn_pairs)]),
+    "rn_dpairs_free": (None, [C.POINTER(rn_dpairs)]),
+    "rn_last_error": (C.c_char_p, []),
+    "rn_last_query_stats": (C.c_int, [C.POINTER(rn_query_stats)]),
+    "rn_version": (C.c_char_p, []),
+}
+
+_lib = None
+
+
+def lib() -> C.CDLL:
+    """The loaded engine library (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImportError(f"{LIB_PATH} is missing: build it with "
+                              "`python -m paper_1607_07696_gb300.build`")
+        L = C.CDLL(LIB_PATH)
+        for name, (res, args) in SIGNATURES.items():
+            fn = getattr(L, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = L
+    return _lib
+
+
+def _check(status: int) -> None:
+    if status != RN_OK:
+        raise RNError(status, lib().rn_last_error().decode())
+
+
+def _u32(a) -> np.ndarray:
+    a = np.asarray(a)
+    if a.dtype == np.uint32:
+        return np.ascontiguousarray(a)
+    if a.size and (a.min() < 0 or a.max() > 0xFFFFFFFF):
+        raise ValueError("ids and weights must fit in uint32")
+    if a.dtype == np.int32 and a.flags.c_contiguous:
+        return a.view(np.uint32)  # no copy: keeps pinned host memory pinned
+    return np.ascontiguousarray(a, dtype=np.uint32)
+
+
+def _p32(a: np.ndarray):
+    return a.ctypes.data_as(_P32)
+
+
+def _dev_ptr(t) -> int:
+    """Device address of a CUDA tensor of 32-bit ints (int32 or uint32)."""
+    if not t.is_cuda or t.element_size() != 4 or not t.is_contiguous():
+        raise ValueError("device arrays must be contiguous 32-bit CUDA tensors")
+    return t.data_ptr()
+
+
+def _stream_ptr(stream) -> int | None:
+    if stream is None:
+        return None
+    return int(getattr(stream, "cuda_stream", stream))
+
+
+def _config(cfg: dict | None):
+    if cfg is None:
+        return None
+    c = rn_config()
+    c.tile_width = int(cfg.get("tile_width", 0))
+    c.delta = int(cfg.get("delta", 0))
+    c.leaf_size = int(cfg.get("leaf_size", 0))
+    c.alpha = float(cfg.get("alpha", -1.0))
+    return C.byref(c)
+
+
+class Graph:
+    """Owner of an ``rn_graph*``; freed with the object."""
+
+    def __init__(self, handle: int, n: int):
+        self.handle = C.c_void_p(handle)
+        self.n = n
+
+    def __del__(self):
+        h = getattr(self, "handle", None)
+        if h and h.value and _lib is not None:
+            _lib.rn_graph_free(h)
+            self.handle = None
+
+
+def rn_graph_load(src, dst, w, n: int, flags: int = RN_UNDIRECTED | RN_REORDER,
+                  cfg: dict | None = None) -> Graph:
+    s, d, ww = _u32(src), _u32(dst), _u32(w)
+    if not (len(s) == len(d) == len(ww)):
+        raise ValueError("edge arrays differ in length")
+    out = C.c_void_p()
+    _check(lib().rn_graph_load(_p32(s), _p32(d), _p32(ww), len(s), int(n), int(flags),
+                               _config(cfg), C.byref(out)))
+    return Graph(out.value, int(n))
+
+
+def rn_bisection_order(src, dst, w, n: int, flags: int = RN_UNDIRECTED,
+                       cfg: dict | None = None) -> np.ndarray:
+    """Host-only: order[i] = original id placed at internal id i by RN_REORDER."""
+    s, d, ww = _u32(src), _u32(dst), _u32(w)
+    order = np.zeros(int(n), np.uint32)
+    _check(lib().rn_bisection_order(_p32(s), _p32(d), _p32(ww), len(s), int(n), int(flags),
+                                    _config(cfg), _p32(order)))
+    return order
+
+
+def rn_graph_info(g: Graph) -> dict:
+    st = rn_graph_stats()
+    _check(lib().rn_graph_info(g.handle, C.byref(st)))
+    return {f: getattr(st, f) for f, _ in rn_graph_stats._fields_}
+
+
+def rn_graph_permutation(g: Graph) -> np.ndarray:
+    p = np.zeros(g.n, np.uint32)
+    _check(lib().rn_graph_permutation(g.handle, _p32(p)))
+    return p
+
+
+def rn_graph_set_config(g: Graph, cfg: dict | None) -> None:
+    _check(lib().rn_graph_set_config(g.handle, _config(cfg)))
+
+
+def _take_pairs(p: rn_pairs):
+    n = int(p.n)
+    try:
+        if n == 0:
+            z = np.zeros(0, np.uint32)
+            return z, z.copy(), z.copy()
+        u = np.ctypeslib.as_array(p.u, shape=(n,)).copy()
+        v = np.ctypeslib.as_array(p.v, shape=(n,)).copy()
+        d = np.ctypeslib.as_array(p.d, shape=(n,)).copy()
+        return u, v, d
+    finally:
+        lib().rn_pairs_free(C.byref(p))
+
+
+def rn_distance_join(g: Graph, R, S, theta: int):
+    """Host arrays in, host arrays out: (u, v, d) sorted by (u, v)."""
+    r, s = _u32(R), _u32(S)
+    p = rn_pairs()
+    _check(lib().rn_distance_join(g.handle, _p32(r), len(r), _p32(s), len(s), int(theta), C.byref(p)))
+    return _take_pairs(p)
+
+
+def rn_kcp(g: Graph, R, S, k: int, theta: int = RN_INF):
+    """Host arrays in, host arrays out: (u, v, d) sorted by (d, u, v)."""
+    r, s = _u32(R), _u32(S)
+    p = rn_pairs()
+    _check(lib().rn_kcp(g.handle, _p32(r), len(r), _p32(s), len(s), int(k), int(theta), C.byref(p)))
+    return _take_pairs(p)
+
+
+class DevicePairs:
+    """Library-owned device result buffers (an ``rn_dpairs``), reusable across calls."""
+
+    def __init__(self):
+        self.s = rn_dpairs()
+
+    def __del__(self):
+        if _lib is not None and getattr(self, "s", None) is not None:
+            _lib.rn_dpairs_free(C.byref(self.s))
+
+    @property
+    def n(self) -> int:
+        return int(self.s.n)
+
+    def tensors(self):
+        """(u, v, d) as int32 torch views of the device buffers (valid until the next call)."""
+        import torch
+
+        n = self.n
+
+        class _View:
+            def __init__(self, ptr):
+                self.__cuda_array_interface__ = {"shape": (n,), "typestr": "<i4",
+                                                 "data": (int(ptr or 0), False), "version": 3}
+
+        if n == 0:
+            z = torch.zeros(0, dtype=torch.int32, device="cuda")
+            return z, z.clone(), z.clone()
+        return tuple(torch.as_tensor(_View(p), device="cuda") for p in (self.s.u, self.s.v, self.s.d))
+
+    def numpy(self):
+        return tuple(t.cpu().numpy().view(np.uint32) for t in self.tensors())
+
+
+def rn_distance_join_dev(g: Graph, dR, dS, theta: int, out: DevicePairs, stream=None) -> int:
+    """Device tensors in, library-owned device buffers out; returns the pair count."""
+    _check(lib().rn_distance_join_dev(g.handle, _dev_ptr(dR), dR.numel(), _dev_ptr(dS), dS.numel(),
+                                      int(theta), C.byref(out.s), _stream_ptr(stream)))
+    return out.n
+
+
+def rn_kcp_dev(g: Graph, dR, dS, k: int, theta: int, out: DevicePairs, stream=None) -> int:
+    _check(lib().rn_kcp_dev(g.handle, _dev_ptr(dR), dR.numel(), _dev_ptr(dS), dS.numel(), int(k),
+                            int(theta), C.byref(out.s), _stream_ptr(stream)))
+    return out.n
+
+
+def rn_last_query_stats() -> dict:
+    st = rn_query_stats()
+    _check(lib().rn_last_query_stats(C.byref(st)))
+    return {f: getattr(st, f) for f, _ in rn_query_stats._fields_}
+
+
+def rn_version() -> str:
+    return lib().rn_version().decode()

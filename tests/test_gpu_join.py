@@ -1,0 +1,200 @@
+"""Parity of the GPU theta-join (through the C ABI) with the CPU oracle: bit-exact.
+
+Distances are integers, so the bar is equality of every (u, v, d) triple and of the
+order (sorted by (u, v)).  Sizes run from a handful of nodes to the 264k-node road-like
+workload in full, and the 1.07M-node clustered workload on sampled sources.
+"""
+import json
+import os
+
+import numpy as np
+import pytest
+
+from paper_1607_07696_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+WORKLOADS = json.load(open(os.path.join(ROOT, "tests", "golden", "workloads.json")))
+
+
+@pytest.fixture(scope="module")
+def rn():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    from paper_1607_07696_gb300 import build as B
+
+    B.build()
+    from paper_1607_07696_gb300 import rn as RN
+
+    return RN
+
+
+def dev_join(rn, g, R, S, theta, out=None):
+    import torch
+
+    out = out or rn.DevicePairs()
+    dR = torch.as_tensor(np.asarray(R, dtype=np.int64).astype(np.int32), device="cuda")
+    dS = torch.as_tensor(np.asarray(S, dtype=np.int64).astype(np.int32), device="cuda")
+    rn.rn_distance_join_dev(g, dR, dS, theta, out)
+    return out.numpy()
+
+
+def assert_same(got, ref, what=""):
+    u, v, d = got
+    assert len(u) == len(ref), f"{what}: {len(u)} pairs, oracle {len(ref)}"
+    assert np.array_equal(u, ref.u), f"{what}: u differs"
+    assert np.array_equal(v, ref.v), f"{what}: v differs"
+    assert np.array_equal(d.astype(np.uint64), ref.d), f"{what}: d differs"
+
+
+def load(rn, e, flags=None, cfg=None):
+    flags = rn.RN_UNDIRECTED | rn.RN_REORDER if flags is None else flags
+    return rn.rn_graph_load(e.src, e.dst, e.w, e.n, flags=flags, cfg=cfg)
+
+
+@pytest.mark.parametrize("T", [32, 64, 128])
+def test_grid4096_full(rn, oracle, T):
+    w = I.c1_grid_join()
+    e = w.graph
+    g = load(rn, e, cfg={"tile_width": T})
+    ref = oracle.graph(e.n, e.src, e.dst, e.w).join(w.R, w.S, w.theta)
+    assert_same(dev_join(rn, g, w.R, w.S, w.theta), ref, f"grid T={T} dev")
+    assert_same(rn.rn_distance_join(g, w.R, w.S, w.theta), ref, f"grid T={T} host")
+    st = rn.rn_last_query_stats()
+    assert st["pairs"] == len(ref) and st["tile_width"] == T
+
+
+@pytest.mark.parametrize("seed", range(24))
+def test_random_small(rn, oracle, seed):
+    rng = np.random.default_rng(seed)
+    n = int(rng.integers(2, 3000))
+    kind = seed % 3
+    if kind == 0:
+        e = I.random_graph(n, int(rng.integers(0, 3 * n)), seed, 1, int(rng.integers(1, 1 << 16)))
+    elif kind == 1:
+        e = I.road_graph(max(n, 16), int(2.77 * max(n, 16)), seed)
+    else:
+        e = I.random_graph(n, int(2 * n), seed, 1, 7)
+    n = e.n
+    directed = seed % 4 == 3
+    reorder = seed % 5 != 4
+    flags = (0 if directed else rn.RN_UNDIRECTED) | (rn.RN_REORDER if reorder else 0)
+    T = [32, 64, 128][seed % 3]
+    cfg = {"tile_width": T, "delta": int(rng.choice([0, 1, 50, 1 << 20]))}
+    g = load(rn, e, flags, cfg)
+    og = oracle.graph(n, e.src, e.dst, e.w, undirected=not directed)
+    perm = rng.permutation(n)
+    nR = int(rng.integers(1, max(2, n // 2)))
+    nS = int(rng.integers(0, n - nR + 1))
+    R, S = perm[:nR], perm[nR:nR + nS]
+    D = og.sssp(int(R[0]))[0]
+    finite = D[D != np.uint64(2**64 - 1)]
+    thetas = [0, int(np.median(finite)) if finite.size else 5, rn.RN_INF]
+    for theta in thetas:
+        ref = og.join(R, S, min(theta, rn.RN_THETA_MAX))
+        assert_same(dev_join(rn, g, R, S, theta), ref, f"seed {seed} theta {theta}")
+
+
+def test_edge_cases(rn, oracle):
+    e = I.road_graph(2000, 5540, 3)
+    g = load(rn, e)
+    og = oracle.graph(e.n, e.src, e.dst, e.w)
+    R, S = I.disjoint_sets(e.n, 333, 400, 4)  # 333 = ragged last tile for every width
+    th = 20000
+    for (r, s) in [(R, S), (R[:0], S), (R, S[:0]), (R[:0], S[:0]), (R[:1], S), (R[:33], S[:1])]:
+        assert_same(dev_join(rn, g, r, s, th), og.join(r, s, th), f"|R|={len(r)} |S|={len(s)}")
+    # all but one node in R, the last in S
+    allR = np.arange(e.n - 1)
+    assert_same(dev_join(rn, g, allR, [e.n - 1], th), og.join(allR, [e.n - 1], th), "R = V - {s}")
+    # theta at the largest allowed value and RN_INF agree
+    a = dev_join(rn, g, R[:40], S, rn.RN_THETA_MAX)
+    b = dev_join(rn, g, R[:40], S, rn.RN_INF)
+    assert all(np.array_equal(x, y) for x, y in zip(a, b))
+
+
+def test_invalid_inputs_rejected(rn):
+    import torch
+
+    e = I.road_graph(500, 1385, 5)
+    g = load(rn, e)
+    bad = [([1, 2, 3], [4, 500]), ([1, 1], [4]), ([1], [4, 4]), ([1, 2], [2, 3])]
+    for R, S in bad:
+        with pytest.raises(rn.RNError) as ex:
+            dev_join(rn, g, R, S, 100)
+        assert ex.value.status == rn.RN_EINVAL
+        with pytest.raises(rn.RNError) as ex:
+            rn.rn_distance_join(g, R, S, 100)
+        assert ex.value.status == rn.RN_EINVAL
+    with pytest.raises(rn.RNError) as ex:
+        rn.rn_distance_join(g, [1], [2], rn.RN_THETA_MAX + 1)
+    assert ex.value.status == rn.RN_EINVAL
+    # the graph still answers correctly after rejected calls
+    R, S = [1, 2, 3], [4, 5, 6]
+    u, v, d = dev_join(rn, g, R, S, 1 << 31)
+    assert len(u) == 9
+
+
+def test_slab_overflow_retry(rn, oracle):
+    # unbounded search from 64 sources on a 40k-node graph: every tile's union ball is
+    # the whole component, far beyond the shared-memory map, so tiles are searched
+    # again with a global map
+    e = I.road_graph(40_000, 110_800, 21)
+    g = load(rn, e)
+    R, S = I.disjoint_sets(e.n, 64, 3000, 22)
+    ref = oracle.graph(e.n, e.src, e.dst, e.w).join(R, S, rn.RN_THETA_MAX)
+    assert_same(dev_join(rn, g, R, S, rn.RN_INF), ref, "unbounded")
+    assert rn.rn_last_query_stats()["retried_tiles"] > 0
+    # and the engine is clean afterwards
+    R2, S2 = I.disjoint_sets(e.n, 500, 500, 23)
+    ref2 = oracle.graph(e.n, e.src, e.dst, e.w).join(R2, S2, 30000)
+    assert_same(dev_join(rn, g, R2, S2, 30000), ref2, "after retry")
+
+
+def test_pair_buffer_growth_and_repeat(rn, oracle):
+    e = I.road_graph(20_000, 55_400, 31)
+    g = load(rn, e)
+    og = oracle.graph(e.n, e.src, e.dst, e.w)
+    R, S = I.disjoint_sets(e.n, 40, 8000, 32)
+    out = rn.DevicePairs()
+    small = dev_join(rn, g, R[:2], S[:2], 100, out)
+    ref = og.join(R, S, 400_000)  # hundreds of pairs per source: more than the first estimate
+    got1 = dev_join(rn, g, R, S, 400_000, out)
+    assert_same(got1, ref, "grown")
+    got2 = dev_join(rn, g, R, S, 400_000, out)
+    assert all(np.array_equal(x, y) for x, y in zip(got1, got2)), "repeat differs"
+    assert len(small[0]) <= 4
+
+
+def test_road264k_full(rn, oracle):
+    spec = WORKLOADS["road264k_join"]
+    w = I.c2_road_join(spec["theta"])
+    e = w.graph
+    assert e.m == spec["graph"]["m"]
+    g = load(rn, e)
+    ref = oracle.graph(e.n, e.src, e.dst, e.w).join(w.R, w.S, w.theta)
+    got = dev_join(rn, g, w.R, w.S, w.theta)
+    assert_same(got, ref, "road264k")
+    assert_same(rn.rn_distance_join(g, w.R, w.S, w.theta), ref, "road264k host")
+
+
+def test_road1070k_join_sampled(rn, oracle):
+    spec = WORKLOADS["road1070k_clustered"]
+    w = I.c3_road_clustered()
+    e = w.graph
+    g = load(rn, e)
+    theta = spec["theta_join"]
+    u, v, d = dev_join(rn, g, w.R, w.S, theta)
+    # properties that hold at any size
+    assert np.all(d <= theta)
+    key = u.astype(np.uint64) << np.uint64(32) | v.astype(np.uint64)
+    assert np.all(key[1:] > key[:-1]), "not strictly sorted by (u, v)"
+    assert np.isin(u, w.R).all() and np.isin(v, w.S).all()
+    # every pair of 300 sampled sources, against the oracle one source at a time
+    rng = np.random.default_rng(5)
+    sample = np.sort(rng.choice(w.R, size=300, replace=False))
+    og = oracle.graph(e.n, e.src, e.dst, e.w)
+    ref = og.join(sample, w.S, theta)
+    m = np.isin(u, sample)
+    assert_same((u[m], v[m], d[m]), ref, "road1070k sampled sources")
