@@ -47,6 +47,7 @@ def parse():
                     choices=["road264k_join", "grid4096_theta1500", "road1070k_join"])
     ap.add_argument("--tile-width", type=int, default=0)
     ap.add_argument("--delta", type=int, default=0)
+    ap.add_argument("--tile-sources", type=int, default=0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     return ap.parse_args()
 
@@ -137,6 +138,13 @@ def measured_peak_gbs():
     return 6800.0, "fallback"
 
 
+def graph_digest(e) -> dict:
+    import numpy as np
+
+    return {"n": int(e.n), "m": int(e.m), "wsum": int(e.w.astype(np.uint64).sum()),
+            "xsum": int((e.src.astype(np.uint64) * 3 + e.dst.astype(np.uint64)).sum())}
+
+
 def engine_hash() -> str:
     return hashlib.sha256(open(ENGINE_SRC, "rb").read()).hexdigest()[:16]
 
@@ -189,7 +197,7 @@ def run_engine(args):
         B.build()
     w, spec = make_workload(args.workload, rank)
     e = w.graph
-    cfg = {"tile_width": args.tile_width, "delta": args.delta}
+    cfg = {"tile_width": args.tile_width, "delta": args.delta, "tile_sources": args.tile_sources}
     g = rn.rn_graph_load(e.src, e.dst, e.w, e.n, cfg=cfg)
     info = rn.rn_graph_info(g)
     stream = torch.cuda.Stream()
@@ -278,7 +286,10 @@ def run_engine(args):
         "config": {
             "workload": args.workload,
             "n": e.n, "m": e.m, "nR": len(w.R), "nS": len(w.S), "theta": theta,
-            "pairs": npairs, "tile_width": T, "delta": stats["delta"],
+            "pairs": npairs, "tile_width": T, "tile_sources": stats["tile_sources"],
+            "tiles": stats["tiles"], "delta": stats["delta"],
+            "graph_matches_calibration": graph_digest(e) == spec.get("graph"),
+            "blocks_per_sm": stats["blocks_per_sm"],
             "parallelism": f"replicas x{world}" if world > 1 else "1 GPU",
             "l2": "flushed between steps (256 MB write outside the timed events)",
         },

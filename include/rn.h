@@ -85,7 +85,10 @@ typedef struct {
 
 /* Engine knobs.  Zero in any field means "choose automatically". */
 typedef struct {
-    uint32_t tile_width;  /* sources searched together by one thread block: 32, 64 or 128 */
+    uint32_t tile_width;  /* lanes of a slab row, the most sources one thread block
+                             searches together: 32, 64 or 128 */
+    uint32_t tile_sources;/* sources per tile, <= tile_width; 0 spreads R over whole
+                             waves of resident blocks */
     uint32_t delta;       /* bucket width of the delta-stepping search, in weight units */
     uint32_t leaf_size;   /* recursive-bisection leaf size used by RN_REORDER */
     float alpha;          /* smoothing parameter of the bisection (Eq. 1-2), in [0, 1];
@@ -110,10 +113,12 @@ typedef struct {
     uint64_t retried_tiles; /* tiles searched again with a larger slab after an overflow */
     uint64_t scans;         /* slab rows scanned (a node's arcs relaxed for a whole tile) */
     uint32_t tile_width;
+    uint32_t tile_sources;  /* sources per tile */
     uint32_t delta;
     uint32_t passes;        /* search passes (k closest pairs widens its radius by passes) */
     uint32_t theta_final;   /* k closest pairs: the k-th distance found, else theta */
     uint32_t launches;      /* kernels the query launched */
+    uint32_t blocks_per_sm; /* resident search blocks per SM (occupancy of the first launch) */
     uint64_t slots;         /* sum over tiles of the nodes the tile reached (its union ball) */
     uint64_t slot_arcs;     /* sum over tiles of the arcs leaving those nodes */
     double device_ms;       /* device time of the query, CUDA events on its stream */

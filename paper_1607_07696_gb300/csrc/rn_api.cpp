@@ -129,6 +129,7 @@ void apply_config(rn_graph *g, const rn_config *cfg) {
         if (cfg->tile_width && cfg->tile_width != 32 && cfg->tile_width != 64 && cfg->tile_width != 128)
             rn::fail(RN_EINVAL, "tile_width must be 0, 32, 64 or 128");
         if (cfg->tile_width) c.tile_width = cfg->tile_width;
+        c.tile_src = cfg->tile_sources;
         c.delta = cfg->delta;
     }
     g->cfg = c;
@@ -164,7 +165,7 @@ rn_status rn_graph_load(const uint32_t *src, const uint32_t *dst, const uint32_t
         if (flags & RN_REORDER) {
             uint32_t leaf = cfg && cfg->leaf_size ? cfg->leaf_size : 512;
             float alpha = (cfg && cfg->alpha >= 0.0f) ? cfg->alpha : 0.5f;
-            order = rn::bisection_order(h, leaf, alpha);
+            order = rn::bisection_order(h, leaf, alpha, (flags & RN_UNDIRECTED) != 0);
             h = rn::relabel(h, order);
         } else {
             for (uint32_t i = 0; i < n; i++) order[i] = i;
@@ -201,7 +202,7 @@ rn_status rn_bisection_order(const uint32_t *src, const uint32_t *dst, const uin
         rn::HostGraph h = rn::build_csr(n, m, src, dst, w, (flags & RN_UNDIRECTED) != 0);
         uint32_t leaf = cfg && cfg->leaf_size ? cfg->leaf_size : 512;
         float alpha = (cfg && cfg->alpha >= 0.0f) ? cfg->alpha : 0.5f;
-        std::vector<uint32_t> o = rn::bisection_order(h, leaf, alpha);
+        std::vector<uint32_t> o = rn::bisection_order(h, leaf, alpha, (flags & RN_UNDIRECTED) != 0);
         std::memcpy(order, o.data(), size_t(n) * 4);
     });
 }

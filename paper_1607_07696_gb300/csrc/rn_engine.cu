@@ -143,7 +143,8 @@ struct Control {
 constexpr int SEARCH_THREADS = 512;
 constexpr int SEARCH_WARPS = SEARCH_THREADS / 32;
 constexpr uint32_t QCAP = 2048;        // near-queue entries (two queues)
-constexpr uint32_t SMEM_H = 8192;      // slots of the shared-memory map
+constexpr uint32_t SMEM_H = 8192;      // slots of the shared-memory map, 2 blocks per SM
+constexpr uint32_t SMEM_H1 = 16384;    // slots of the larger shared-memory map, 1 block per SM
 constexpr int CTAS_PER_SM = 2;
 
 struct Workspace {
@@ -161,6 +162,8 @@ struct Workspace {
     uint32_t *slab = nullptr;
     size_t slab_bytes = 0;
     uint32_t slab_ctas = 0;
+    uint32_t *gretry = nullptr;  // global maps and slabs of the largest retries
+    size_t gretry_bytes = 0;
     // raw pairs and radix-sort buffers
     unsigned long long *keyA = nullptr, *keyB = nullptr;
     uint32_t *valA = nullptr, *valB = nullptr;
@@ -169,6 +172,7 @@ struct Workspace {
     size_t hist_cap = 0;
     cudaEvent_t ev0 = nullptr, ev1 = nullptr, evs0 = nullptr, evs1 = nullptr;
     uint32_t launches = 0;  // kernels launched by the current query
+    int blocks_per_sm = 0;  // occupancy of the shared-map search kernel
     uint64_t bytes = 0;
 };
 
@@ -213,6 +217,7 @@ void workspace_destroy(Workspace *ws) {
     device_free(ws->failed2);
     device_free(ws->ctl);
     device_free(ws->slab);
+    device_free(ws->gretry);
     device_free(ws->keyA);
     device_free(ws->keyB);
     device_free(ws->valA);
@@ -336,6 +341,7 @@ struct SearchArgs {
     const uint32_t *__restrict__ src;       // R, internal ids, ascending
     const uint32_t *__restrict__ tile_list; // tiles to search (retry), or null: all
     uint32_t ntiles;                        // entries of tile_list, or tiles of R
+    uint32_t tile_src;                      // sources per tile (<= T; lanes beyond stay INF)
     uint32_t bound;                         // theta
     uint32_t delta;
     uint32_t *slab;                         // per-block regions of H rows x T lanes
@@ -413,24 +419,37 @@ __device__ __forceinline__ uint32_t find_or_insert(uint32_t *hkeys, uint32_t H, 
 }
 
 // One thread block searches one tile of T = 32 L sources at a time (persistent: blocks
-// pop tiles from a global counter).  GMAP = false keeps the slot map (node id and
-// pending priority of every slot) in shared memory; GMAP = true keeps it in global
-// memory so a tile whose union ball outgrows shared memory can be searched again with
-// a larger map.
+// pop tiles from a global counter).  Thread `lane` of a warp owns sources
+// lane*L .. lane*L+L-1 of every slab row.
+//
+// Per slot h the map keeps, besides its node id hkeys[h]:
+//   prio[h]  the least improved-but-unrelaxed distance in the row, INF when clean;
+//   dmask[h] which thread-lanes of the row improved since the row was last relaxed.
+// A relaxation by a warp is: atomicMin on the slab (fire and forget), a block-scope
+// fence, then dmask |= improved lanes, then prio = min(prio, least improved value)
+// (pushing h on the near queue when it becomes dirty inside the current bucket).  A
+// scan takes prio first and skips a clean slot; only then does it take dmask, fence,
+// and read the row.  With that order every improvement is relaxed at least once after
+// it happened, and a rescan relaxes only the lanes that changed.
+//
+// GMAP = false keeps the map in shared memory; GMAP = true keeps it in global memory
+// so a tile whose union ball outgrows shared memory can be searched again.
 template <int L, bool GMAP>
 __global__ void __launch_bounds__(SEARCH_THREADS, CTAS_PER_SM) k_tile_search(SearchArgs a) {
     constexpr int T = 32 * L;
+    constexpr int B = 4;  // arcs relaxed together (their row loads are in flight at once)
+    constexpr int P = L == 1 ? 4 : (L == 2 ? 2 : 1);  // queue items a warp scans together
     extern __shared__ uint32_t smem[];
-    uint32_t *hkeys, *prio, *qa;
+    uint32_t *hkeys, *prio, *dmask, *qa;
     if constexpr (GMAP) {
-        hkeys = a.gmap + size_t(blockIdx.x) * 2 * a.H;
-        prio = hkeys + a.H;
+        hkeys = a.gmap + size_t(blockIdx.x) * 3 * a.H;
         qa = smem;
     } else {
         hkeys = smem;
-        prio = hkeys + a.H;
-        qa = prio + a.H;
+        qa = smem + 3 * a.H;
     }
+    prio = hkeys + a.H;
+    dmask = prio + a.H;
     uint32_t *qb = qa + QCAP;
     __shared__ uint32_t src_orig[T];
     __shared__ uint32_t s_tile, s_ncur, s_nnext, s_cursor, s_fill, s_fail, s_stop, s_minp;
@@ -445,13 +464,15 @@ __global__ void __launch_bounds__(SEARCH_THREADS, CTAS_PER_SM) k_tile_search(Sea
 
     if (__ldcg(&a.ctl->err)) return;
     const uint32_t nR = __ldcg(&a.ctl->r_count);
-    const uint32_t ntiles = a.tile_list ? a.ntiles : (nR + T - 1) / T;
+    const uint32_t all_tiles = (nR + a.tile_src - 1) / a.tile_src;
+    const uint32_t ntiles = a.tile_list ? a.ntiles : all_tiles;
 
     for (;;) {
         if (tid == 0) s_tile = atomicAdd(&a.ctl->tile_next, 1u);
         for (uint32_t i = tid; i < a.H; i += SEARCH_THREADS) {
             hkeys[i] = EMPTY;
             prio[i] = INF;
+            dmask[i] = 0;
         }
         if (tid == 0) {
             s_ncur = 0;
@@ -461,21 +482,22 @@ __global__ void __launch_bounds__(SEARCH_THREADS, CTAS_PER_SM) k_tile_search(Sea
             s_fail = 0;
             s_stop = 0;
         }
+        if (tid < T) src_orig[tid] = 0;
         __syncthreads();
         const uint32_t ti = s_tile;
         if (ti >= ntiles) break;
         const uint32_t tile = a.tile_list ? a.tile_list[ti] : ti;
-        const uint32_t first = tile * T;
-        const uint32_t tsz = min(uint32_t(T), nR - first);
+        if (tile >= all_tiles) continue;  // defensive: never index past R
+        const uint32_t first = tile * a.tile_src;
+        const uint32_t tsz = min(a.tile_src, nR - first);
 
         // sources: lane t of every row belongs to R node first + t, at distance 0
-        if (tid < T) src_orig[tid] = 0;
-        __syncthreads();
         if (tid < tsz) {
-            uint32_t y = a.src[first + tid];
+            const uint32_t y = a.src[first + tid];
             src_orig[tid] = a.iperm[y];
-            uint32_t h = find_or_insert(hkeys, a.H, a.hshift, y, &s_fill, a.max_fill, &s_fail);
+            const uint32_t h = find_or_insert(hkeys, a.H, a.hshift, y, &s_fill, a.max_fill, &s_fail);
             __stcg(&slab[size_t(h) * T + tid], 0u);
+            atomicOr(&dmask[h], 1u << (tid / L));
             prio[h] = 0;
             qa[atomicAdd(&s_ncur, 1u)] = h;
         }
@@ -493,64 +515,125 @@ __global__ void __launch_bounds__(SEARCH_THREADS, CTAS_PER_SM) k_tile_search(Sea
                 __syncthreads();
                 const uint32_t ncur = min(s_ncur, QCAP);
                 if (ncur == 0 || s_stop) break;
+                // Each warp takes P queue items at a time: their prio / dmask exchanges,
+                // CSR offsets and slab rows are fetched together, their arcs are
+                // concatenated across the lanes, and up to B arcs' destination rows are
+                // in flight at once.
                 for (;;) {
-                    uint32_t i = 0;
-                    if (lane == 0) i = atomicAdd(&s_cursor, 1u);
-                    i = __shfl_sync(FULL, i, 0);
-                    if (i >= ncur) break;
-                    const uint32_t x = qcur[i];
-                    uint32_t p = 0;
-                    if (lane == 0) p = atomicExch(&prio[x], INF);
-                    p = __shfl_sync(FULL, p, 0);
-                    if (p == INF) continue;  // scanned since it was queued
+                    uint32_t base = 0;
+                    if (lane == 0) base = atomicAdd(&s_cursor, uint32_t(P));
+                    base = __shfl_sync(FULL, base, 0);
+                    if (base >= ncur) break;
+                    uint32_t x = EMPTY, mask = 0, beg = 0, deg = 0;
+                    if (lane < P && base + lane < ncur) {
+                        x = qcur[base + lane];
+                        const uint32_t p = atomicExch(&prio[x], INF);
+                        if (p != INF) mask = atomicExch(&dmask[x], 0u);
+                        if (mask) {
+                            const uint32_t y0 = hkeys[x];
+                            beg = __ldg(&a.row_ptr[y0]);
+                            deg = __ldg(&a.row_ptr[y0 + 1]) - beg;
+                        }
+                    }
+                    if (__ballot_sync(FULL, mask != 0) == 0) continue;  // all clean
                     __threadfence_block();
-                    my_scans++;
-                    const uint32_t y0 = hkeys[x];
-                    const Row<L> dx = load_row<L>(slab + size_t(x) * T + lane * L);
-                    uint32_t dmin = dx.x[0];
+                    Row<L> dx[P];
+                    uint32_t ms[P], bg[P], pref[P + 1], dmn[P];
+                    pref[0] = 0;
 #pragma unroll
-                    for (int j = 1; j < L; j++) dmin = min(dmin, dx.x[j]);
-                    dmin = __reduce_min_sync(FULL, dmin);
-                    if (dmin > bound) continue;
-                    const uint32_t beg = __ldg(&a.row_ptr[y0]), end = __ldg(&a.row_ptr[y0 + 1]);
-                    for (uint32_t e0 = beg; e0 < end; e0 += 32) {
-                        const uint32_t e = e0 + lane;
+                    for (int j = 0; j < P; j++) {
+                        const uint32_t xj = __shfl_sync(FULL, x, j);
+                        ms[j] = __shfl_sync(FULL, mask, j);
+                        bg[j] = __shfl_sync(FULL, beg, j);
+                        pref[j + 1] = pref[j] + __shfl_sync(FULL, deg, j);
+#pragma unroll
+                        for (int q = 0; q < L; q++) dx[j].x[q] = INF;
+                        if ((ms[j] >> lane) & 1u) dx[j] = load_row<L>(slab + size_t(xj) * T + lane * L);
+                    }
+#pragma unroll
+                    for (int j = 0; j < P; j++) {
+                        uint32_t v = dx[j].x[0];
+#pragma unroll
+                        for (int q = 1; q < L; q++) v = min(v, dx[j].x[q]);
+                        dmn[j] = __reduce_min_sync(FULL, v);
+                        if (ms[j]) my_scans++;
+                    }
+                    const uint32_t total = pref[P];
+                    for (uint32_t g0 = 0; g0 < total; g0 += 32) {
+                        const uint32_t gi = g0 + lane;
+                        // item of arc gi: the last j with pref[j] <= gi
+                        uint32_t jj = 0, pj = 0, bj = bg[0], dj = dmn[0];
+#pragma unroll
+                        for (int j = 1; j < P; j++)
+                            if (gi >= pref[j]) {
+                                jj = j;
+                                pj = pref[j];
+                                bj = bg[j];
+                                dj = dmn[j];
+                            }
                         uint2 arc = make_uint2(0, 0);
                         bool need = false;
-                        if (e < end) {
-                            arc = __ldg(&a.adj[e]);
-                            need = dmin + arc.y <= bound;
+                        if (gi < total) {
+                            arc = __ldg(&a.adj[bj + (gi - pj)]);
+                            need = dj <= bound && dj + arc.y <= bound;
                         }
                         uint32_t hy = EMPTY;
                         if (need) hy = find_or_insert(hkeys, a.H, a.hshift, arc.x, &s_fill, a.max_fill, &s_fail);
                         uint32_t m = __ballot_sync(FULL, hy != EMPTY);
                         while (m) {
-                            const int j = __ffs(m) - 1;
-                            m &= m - 1;
-                            const uint32_t hj = __shfl_sync(FULL, hy, j);
-                            const uint32_t wj = __shfl_sync(FULL, arc.y, j);
-                            uint32_t *row = slab + size_t(hj) * T + lane * L;
-                            const Row<L> cur = load_row<L>(row);
-                            uint32_t imin = INF;
+                            uint32_t hj[B], wj[B], jk[B];
+                            Row<L> cur[B], src[B];
 #pragma unroll
-                            for (int q = 0; q < L; q++) {
-                                if (dx.x[q] != INF) {
-                                    const uint32_t d = dx.x[q] + wj;
-                                    if (d <= bound && d < cur.x[q]) {
-                                        atomicMin(row + q, d);
-                                        imin = min(imin, d);
+                            for (int k = 0; k < B; k++) {
+                                const bool have = m != 0;  // warp-uniform
+                                const int l = have ? __ffs(m) - 1 : 0;
+                                if (have) m &= m - 1;
+                                const uint32_t h = __shfl_sync(FULL, hy, l);
+                                wj[k] = __shfl_sync(FULL, arc.y, l);
+                                jk[k] = __shfl_sync(FULL, jj, l);
+                                hj[k] = have ? h : EMPTY;
+                            }
+#pragma unroll
+                            for (int k = 0; k < B; k++) {
+                                src[k] = dx[0];
+#pragma unroll
+                                for (int j = 1; j < P; j++)
+                                    if (jk[k] == uint32_t(j)) src[k] = dx[j];
+#pragma unroll
+                                for (int q = 0; q < L; q++) cur[k].x[q] = 0;
+                                uint32_t sm = src[k].x[0];
+#pragma unroll
+                                for (int q = 1; q < L; q++) sm = min(sm, src[k].x[q]);
+                                if (hj[k] != EMPTY && sm != INF && sm + wj[k] <= bound)
+                                    cur[k] = load_row<L>(slab + size_t(hj[k]) * T + lane * L);
+                            }
+#pragma unroll
+                            for (int k = 0; k < B; k++) {
+                                if (hj[k] == EMPTY) continue;  // warp-uniform
+                                uint32_t *row = slab + size_t(hj[k]) * T + lane * L;
+                                uint32_t imin = INF;
+#pragma unroll
+                                for (int q = 0; q < L; q++) {
+                                    if (src[k].x[q] != INF) {
+                                        const uint32_t d = src[k].x[q] + wj[k];
+                                        if (d <= bound && d < cur[k].x[q]) {
+                                            atomicMin(row + q, d);
+                                            imin = min(imin, d);
+                                        }
                                     }
                                 }
-                            }
-                            imin = __reduce_min_sync(FULL, imin);
-                            if (imin != INF) {
-                                __threadfence_block();
-                                __syncwarp();
-                                if (lane == 0) {
-                                    const uint32_t old = atomicMin(&prio[hj], imin);
-                                    if (imin < tau && (old == INF || old >= tau)) {
-                                        const uint32_t qi = atomicAdd(&s_nnext, 1u);
-                                        if (qi < QCAP) qnext[qi] = hj;
+                                const uint32_t bal = __ballot_sync(FULL, imin != INF);
+                                if (bal) {
+                                    imin = __reduce_min_sync(FULL, imin);
+                                    __threadfence_block();
+                                    __syncwarp();
+                                    if (lane == 0) {
+                                        atomicOr(&dmask[hj[k]], bal);
+                                        const uint32_t old = atomicMin(&prio[hj[k]], imin);
+                                        if (imin < tau && (old == INF || old >= tau)) {
+                                            const uint32_t qi = atomicAdd(&s_nnext, 1u);
+                                            if (qi < QCAP) qnext[qi] = hj[k];
+                                        }
                                     }
                                 }
                             }
@@ -808,7 +891,9 @@ static uint32_t bits_for(uint32_t n) {
     return b;
 }
 
-static size_t search_smem(uint32_t H, bool gmap) { return (gmap ? 0 : size_t(H) * 8) + size_t(QCAP) * 8; }
+// Dynamic shared memory of a search block: the slot map (node, prio, dmask) unless it
+// lives in global memory, and the two near queues.
+static size_t search_smem(uint32_t H, bool gmap) { return (gmap ? 0 : size_t(H) * 12) + size_t(QCAP) * 8; }
 
 template <int L, bool GMAP>
 static void launch_search(const SearchArgs &a, uint32_t grid, cudaStream_t st) {
@@ -816,10 +901,20 @@ static void launch_search(const SearchArgs &a, uint32_t grid, cudaStream_t st) {
     static std::once_flag once;
     std::call_once(once, [&] {
         RN_CUDA(cudaFuncSetAttribute(k_tile_search<L, GMAP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     int(search_smem(SMEM_H, GMAP))));
+                                     int(search_smem(SMEM_H1, GMAP))));
+        RN_CUDA(cudaFuncSetAttribute(k_tile_search<L, GMAP>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                     100));
     });
     k_tile_search<L, GMAP><<<grid, SEARCH_THREADS, smem, st>>>(a);
     RN_CUDA(cudaGetLastError());
+}
+
+template <int L>
+static int search_occupancy(uint32_t H) {
+    int b = 0;
+    RN_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_tile_search<L, false>, SEARCH_THREADS,
+                                                          search_smem(H, false)));
+    return b;
 }
 
 static void search(uint32_t T, bool gmap, const SearchArgs &a, uint32_t grid, cudaStream_t st) {
@@ -840,24 +935,28 @@ static Control read_control(Workspace *ws, cudaStream_t st) {
     return *ws->ctl_host;
 }
 
-// Search every tile (the shared-memory map first), then search again, with a global
-// map four times larger each time, the tiles whose union ball overflowed.  The map
-// never needs to exceed the next power of two >= 2n, where it cannot overflow.
+// Search every tile with the 8192-slot shared-memory map (two blocks per SM), then
+// search the tiles whose union ball overflowed it again: first with a 16384-slot
+// shared-memory map (one block per SM), then with global maps four times larger each
+// time.  The map never needs more than the next power of two >= 2n slots, where it
+// cannot overflow.
 static Control search_all(const DeviceGraph &g, Workspace *ws, uint32_t T, SearchArgs a,
                           uint32_t ntiles, cudaStream_t st, uint64_t *retried) {
     const uint32_t grid_max = uint32_t(ws->num_sms) * CTAS_PER_SM;
-    const uint32_t grid = std::max<uint32_t>(1, std::min(ntiles, grid_max));
     a.gmap = nullptr;
     a.tile_list = nullptr;
     a.ntiles = ntiles;
     a.H = SMEM_H;
     a.hshift = 32 - bits_for(SMEM_H);
-    a.max_fill = SMEM_H * 3 / 4;
+    a.max_fill = SMEM_H * 7 / 8;
     a.failed = ws->failed;
+    a.slab = ws->slab;
     RN_CUDA(cudaEventRecord(ws->evs0, st));
     if (ntiles) {
-        search(T, false, a, grid, st);
+        search(T, false, a, std::max<uint32_t>(1, std::min(ntiles, grid_max)), st);
         ws->launches++;
+        ws->blocks_per_sm = T == 32 ? search_occupancy<1>(SMEM_H)
+                          : T == 64 ? search_occupancy<2>(SMEM_H) : search_occupancy<4>(SMEM_H);
     }
     RN_CUDA(cudaEventRecord(ws->evs1, st));
     Control c = read_control(ws, st);
@@ -867,34 +966,45 @@ static Control search_all(const DeviceGraph &g, Workspace *ws, uint32_t T, Searc
     uint32_t *list = ws->failed, *next = ws->failed2;
     while (c.n_failed && !c.err) {
         if (H >= hcap) fail(RN_EINTERNAL, "slot map overflowed at its largest size");
-        H = std::min<uint64_t>(H * 4, hcap);
         const uint32_t nf = c.n_failed;
         *retried += nf;
-        const size_t per_block = (2 * H + H * T) * 4;
-        const size_t budget = size_t(8) << 30;
-        const uint32_t rgrid = uint32_t(std::max<size_t>(1, std::min<size_t>({nf, grid_max, budget / per_block})));
-        uint32_t *mem = (uint32_t *)device_alloc(per_block * rgrid);
-        try {
-            RN_CUDA(cudaMemsetAsync(mem, 0xFF, per_block * rgrid, st));
-            RN_CUDA(cudaMemsetAsync(&ws->ctl->tile_next, 0, 8, st));  // tile_next, n_failed
-            std::swap(list, next);
-            SearchArgs r = a;
-            r.gmap = mem;
-            r.slab = mem + size_t(rgrid) * 2 * H;
+        RN_CUDA(cudaMemsetAsync(&ws->ctl->tile_next, 0, 8, st));  // tile_next, n_failed
+        SearchArgs r = a;
+        r.tile_list = list;
+        r.ntiles = nf;
+        r.failed = next;
+        if (H == SMEM_H) {
+            H = SMEM_H1;  // same slab (it holds grid_max regions of SMEM_H rows)
+            r.H = SMEM_H1;
+            r.hshift = 32 - bits_for(SMEM_H1);
+            r.max_fill = SMEM_H1 * 7 / 8;
+            search(T, false, r, std::min<uint32_t>(nf, uint32_t(ws->num_sms)), st);
+        } else {
+            H = std::min<uint64_t>(H * 4, hcap);
+            const size_t per_block = (3 * H + H * T) * 4;
+            const size_t budget = size_t(8) << 30;
+            const uint32_t rgrid =
+                uint32_t(std::max<size_t>(1, std::min<size_t>({nf, grid_max, budget / per_block})));
+            if (ws->gretry_bytes < per_block * rgrid) {
+                device_free(ws->gretry);
+                ws->gretry = nullptr;
+                ws->bytes -= ws->gretry_bytes;
+                ws->gretry_bytes = 0;
+                ws->gretry = (uint32_t *)device_alloc(per_block * rgrid);
+                ws->gretry_bytes = per_block * rgrid;
+                ws->bytes += ws->gretry_bytes;
+            }
+            RN_CUDA(cudaMemsetAsync(ws->gretry, 0xFF, per_block * rgrid, st));  // rows INF
+            r.gmap = ws->gretry;
+            r.slab = ws->gretry + size_t(rgrid) * 3 * H;
             r.H = uint32_t(H);
             r.hshift = 32 - bits_for(uint32_t(H));
-            r.max_fill = uint32_t(H * 3 / 4);
-            r.tile_list = list;
-            r.ntiles = nf;
-            r.failed = next;
+            r.max_fill = uint32_t(H * 7 / 8);
             search(T, true, r, rgrid, st);
-            ws->launches++;
-            c = read_control(ws, st);
-        } catch (...) {
-            device_free(mem);
-            throw;
         }
-        device_free(mem);
+        ws->launches++;
+        c = read_control(ws, st);
+        std::swap(list, next);  // this launch's failures are the next launch's tiles
     }
     return c;
 }
@@ -986,7 +1096,16 @@ void run_join(const DeviceGraph &g, Workspace *ws, const EngineConfig &cfg, uint
     RN_CUDA(cudaEventRecord(ws->ev0, st));
 
     prep_sets(g, ws, dR, nR, dS, nS, st);
-    const uint32_t ntiles = (nR + T - 1) / T;
+    // sources per tile: as many as fit a row, but spread so the tiles fill the resident
+    // blocks in whole waves (a last wave of a few tiles would double the search time)
+    const uint32_t grid_max = uint32_t(ws->num_sms) * CTAS_PER_SM;
+    uint32_t tile_src = T;
+    if (nR) {
+        const uint64_t waves = (uint64_t(nR) + uint64_t(T) * grid_max - 1) / (uint64_t(T) * grid_max);
+        tile_src = uint32_t(std::min<uint64_t>(T, (nR + waves * grid_max - 1) / (waves * grid_max)));
+        if (cfg.tile_src) tile_src = std::min(cfg.tile_src, T);
+    }
+    const uint32_t ntiles = (nR + tile_src - 1) / tile_src;
     ensure_u32(&ws->failed, &ws->failed_cap, std::max<uint32_t>(ntiles, 1));
     ensure_u32(&ws->failed2, &ws->failed2_cap, std::max<uint32_t>(ntiles, 1));
     ensure_slab(ws);
@@ -1003,6 +1122,7 @@ void run_join(const DeviceGraph &g, Workspace *ws, const EngineConfig &cfg, uint
     a.delta = delta;
     a.slab = ws->slab;
     a.vbits = vbits;
+    a.tile_src = tile_src;
     a.ctl = ws->ctl;
     a.out_key = ws->keyA;
     a.out_d = ws->valA;
@@ -1036,12 +1156,14 @@ void run_join(const DeviceGraph &g, Workspace *ws, const EngineConfig &cfg, uint
     RN_CUDA(cudaEventElapsedTime(&sms, ws->evs0, ws->evs1));
     stats->pairs = np;
     stats->tiles = ntiles;
+    stats->tile_sources = tile_src;
     stats->retried_tiles = retried;
     stats->scans = c.scans;
     stats->slots = c.slots;
     stats->slot_arcs = c.slot_arcs;
     stats->passes = 1;
     stats->launches = ws->launches;
+    stats->blocks_per_sm = uint32_t(ws->blocks_per_sm);
     stats->device_ms = ms;
     stats->search_ms = sms;
 }

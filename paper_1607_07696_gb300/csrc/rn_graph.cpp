@@ -174,7 +174,7 @@ struct Bisector {
             std::vector<uint32_t> seen;
             for (uint32_t x : part) {
                 if (stamp[x] == st_done) continue;
-                bfs(x, lbl, seen);
+                bfs(x, lbl, seen);  // symmetric graph: the component of x, disjoint from earlier ones
                 for (uint32_t y : seen) stamp[y] = st_done;
                 comps.push_back(seen);
             }
@@ -214,8 +214,23 @@ struct Bisector {
 
 }  // namespace
 
-std::vector<uint32_t> bisection_order(const HostGraph &g, uint32_t leaf_size, float alpha) {
+std::vector<uint32_t> bisection_order(const HostGraph &g0, uint32_t leaf_size, float alpha, bool symmetric) {
     if (alpha < 0.0f || alpha > 1.0f) fail(RN_EINVAL, "alpha must lie in [0, 1]");
+    // The partitioning looks at proximity only, so a directed graph is bisected through
+    // its symmetrised form (every arc both ways, least weight kept).
+    HostGraph sym;
+    if (!symmetric) {
+        std::vector<uint32_t> src, dst;
+        src.reserve(g0.arcs());
+        dst.reserve(g0.arcs());
+        for (uint32_t x = 0; x < g0.n; x++)
+            for (uint32_t e = g0.row_ptr[x]; e < g0.row_ptr[x + 1]; e++) {
+                src.push_back(x);
+                dst.push_back(g0.col[e]);
+            }
+        sym = build_csr(g0.n, src.size(), src.data(), dst.data(), g0.w.data(), true);
+    }
+    const HostGraph &g = symmetric ? g0 : sym;
     Bisector b(g, std::max<uint32_t>(leaf_size, 2), alpha);
     std::vector<uint32_t> all(g.n);
     for (uint32_t x = 0; x < g.n; x++) all[x] = x;

@@ -36,7 +36,7 @@ HostGraph build_csr(uint32_t n, uint64_t m, const uint32_t *src, const uint32_t 
 // Recursive two-seed bisection (Algorithm 1 with the smoothing of Eq. 1-2).  Returns
 // order[i] = the original id placed at internal id i; every partition of the hierarchy
 // occupies a contiguous range of internal ids.
-std::vector<uint32_t> bisection_order(const HostGraph &g, uint32_t leaf_size, float alpha);
+std::vector<uint32_t> bisection_order(const HostGraph &g, uint32_t leaf_size, float alpha, bool symmetric);
 
 // CSR of g relabelled so that internal id i is original node order[i].
 HostGraph relabel(const HostGraph &g, const std::vector<uint32_t> &order);
@@ -64,7 +64,8 @@ uint64_t workspace_bytes(const Workspace *ws);
 
 struct EngineConfig {
     uint32_t tile_width = 32;
-    uint32_t delta = 0;  // 0: derive from the weights
+    uint32_t tile_src = 0;  // sources per tile; 0: spread over whole waves of blocks
+    uint32_t delta = 0;     // 0: derive from the weights
 };
 
 void run_join(const DeviceGraph &g, Workspace *ws, const EngineConfig &cfg, uint32_t median_w,

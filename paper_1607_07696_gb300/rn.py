@@ -42,8 +42,8 @@ class rn_dpairs(C.Structure):
 
 
 class rn_config(C.Structure):
-    _fields_ = [("tile_width", C.c_uint32), ("delta", C.c_uint32), ("leaf_size", C.c_uint32),
-                ("alpha", C.c_float)]
+    _fields_ = [("tile_width", C.c_uint32), ("tile_sources", C.c_uint32), ("delta", C.c_uint32),
+                ("leaf_size", C.c_uint32), ("alpha", C.c_float)]
 
 
 class rn_graph_stats(C.Structure):
@@ -54,8 +54,10 @@ class rn_graph_stats(C.Structure):
 
 class rn_query_stats(C.Structure):
     _fields_ = [("pairs", C.c_uint64), ("tiles", C.c_uint64), ("retried_tiles", C.c_uint64),
-                ("scans", C.c_uint64), ("tile_width", C.c_uint32), ("delta", C.c_uint32),
+                ("scans", C.c_uint64), ("tile_width", C.c_uint32), ("tile_sources", C.c_uint32),
+                ("delta", C.c_uint32),
                 ("passes", C.c_uint32), ("theta_final", C.c_uint32), ("launches", C.c_uint32),
+                ("blocks_per_sm", C.c_uint32),
                 ("slots", C.c_uint64), ("slot_arcs", C.c_uint64), ("device_ms", C.c_double),
                 ("search_ms", C.c_double)]
 
@@ -144,6 +146,7 @@ def _config(cfg: dict | None):
         return None
     c = rn_config()
     c.tile_width = int(cfg.get("tile_width", 0))
+    c.tile_sources = int(cfg.get("tile_sources", 0))
     c.delta = int(cfg.get("delta", 0))
     c.leaf_size = int(cfg.get("leaf_size", 0))
     c.alpha = float(cfg.get("alpha", -1.0))

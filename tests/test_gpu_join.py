@@ -66,6 +66,16 @@ def test_grid4096_full(rn, oracle, T):
     assert st["pairs"] == len(ref) and st["tile_width"] == T
 
 
+@pytest.mark.parametrize("T,ts", [(32, 1), (32, 7), (64, 33), (128, 100), (32, 32)])
+def test_tile_sources(rn, oracle, T, ts):
+    e = I.road_graph(30_000, 83_100, 41)
+    g = load(rn, e, cfg={"tile_width": T, "tile_sources": ts})
+    R, S = I.disjoint_sets(e.n, 700, 2000, 42)
+    ref = oracle.graph(e.n, e.src, e.dst, e.w).join(R, S, 60_000)
+    assert_same(dev_join(rn, g, R, S, 60_000), ref, f"T={T} sources/tile={ts}")
+    assert rn.rn_last_query_stats()["tile_sources"] == min(ts, T)
+
+
 @pytest.mark.parametrize("seed", range(24))
 def test_random_small(rn, oracle, seed):
     rng = np.random.default_rng(seed)

@@ -77,3 +77,15 @@ def test_leaves_are_compact(rn):
 def test_alpha_out_of_range_rejected(rn):
     with pytest.raises(rn.RNError):
         rn.rn_bisection_order([0], [1], [1], 2, cfg={"alpha": 1.5})
+
+
+@pytest.mark.parametrize("seed", range(12))
+def test_random_multigraphs_directed_and_not(rn, seed):
+    # sparse random multigraphs (many components, self-loops, parallel and one-way arcs)
+    rng = np.random.default_rng(seed)
+    n = int(rng.integers(2, 3000))
+    e = I.random_graph(n, int(rng.integers(0, 3 * n)), seed, 1, 50)
+    for flags in (0, rn.RN_UNDIRECTED):
+        o = rn.rn_bisection_order(e.src, e.dst, e.w, e.n, flags=flags,
+                                  cfg={"leaf_size": int(rng.integers(2, 300))})
+        assert np.array_equal(np.sort(o), np.arange(e.n, dtype=np.uint32))
