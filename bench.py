@@ -304,7 +304,12 @@ def run_engine(args):
         "clocks": clk.summary(),
         "engine": {"reorder_ms": info["reorder_ms"], "slots": stats["slots"],
                    "slot_arcs": stats["slot_arcs"], "scans": stats["scans"],
-                   "retried_tiles": stats["retried_tiles"], "device_ms": stats["device_ms"]},
+                   "retried_tiles": stats["retried_tiles"], "device_ms": stats["device_ms"],
+                   "rounds": stats["rounds"], "round_items": stats["round_items"],
+                   "boundaries": stats["boundaries"], "cycles_rounds": stats["cycles_rounds"],
+                   "cycles_boundaries": stats["cycles_boundaries"],
+                   "cycles_emission": stats["cycles_emission"],
+                   "cycles_step_a": stats["cycles_step_a"], "round_arcs": stats["round_arcs"]},
     }
     if not args.no_cpu_baseline and world == 1:
         line["cpu_baseline"] = cpu_baseline(w, spec)

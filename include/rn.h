@@ -123,6 +123,12 @@ typedef struct {
     uint64_t slot_arcs;     /* sum over tiles of the arcs leaving those nodes */
     double device_ms;       /* device time of the query, CUDA events on its stream */
     double search_ms;       /* device time of the first tile-search launch, CUDA events */
+    /* search telemetry, summed over blocks: relaxation rounds, queue items over all
+       rounds, bucket boundaries, and SM cycles in rounds, boundaries and emission */
+    uint64_t rounds, round_items, boundaries;
+    uint64_t cycles_rounds, cycles_boundaries, cycles_emission;
+    uint64_t cycles_step_a; /* part of cycles_rounds spent taking items and their offsets */
+    uint64_t round_arcs;    /* arcs of the scanned items, over all rounds */
 } rn_query_stats;
 
 /*

@@ -138,14 +138,24 @@ struct Control {
     unsigned long long scans;
     unsigned long long slots;      // sum over tiles of slab rows used
     unsigned long long slot_arcs;  // sum over tiles of arcs leaving the rows' nodes
+    // phase counters of the search (thread 0 of every block): rounds, queue items of
+    // all rounds, bucket boundaries, and SM cycles spent in rounds, boundaries, emission
+    unsigned long long rounds, round_items, boundaries;
+    unsigned long long cyc_round, cyc_bound, cyc_emit;
+    unsigned long long cyc_stepA, round_arcs;
 };
 
-constexpr int SEARCH_THREADS = 512;
-constexpr int SEARCH_WARPS = SEARCH_THREADS / 32;
-constexpr uint32_t QCAP = 2048;        // near-queue entries (two queues)
-constexpr uint32_t SMEM_H = 8192;      // slots of the shared-memory map, 2 blocks per SM
-constexpr uint32_t SMEM_H1 = 16384;    // slots of the larger shared-memory map, 1 block per SM
-constexpr int CTAS_PER_SM = 2;
+// Two block shapes: NARROW blocks (512 threads, an 8192-slot shared map, two blocks per
+// SM) search every tile first; WIDE blocks (1024 threads, a 16384-slot map, one block
+// per SM) search again the tiles whose union ball overflowed, and run the global-map
+// retries.  A block of THREADS threads keeps two near queues of 2 THREADS entries and
+// stages 0.75 THREADS queue items per round step.
+constexpr int NARROW = 512, WIDE = 1024;
+constexpr uint32_t SMEM_H = 8192;      // slots of the narrow block's map
+constexpr uint32_t SMEM_HW = 16384;    // slots of the wide block's map
+constexpr int CTAS_PER_SM = 2;         // narrow blocks resident per SM
+__host__ __device__ constexpr uint32_t qcap_of(int threads) { return 2u * threads; }
+__host__ __device__ constexpr uint32_t icap_of(int threads) { return 3u * threads / 4; }
 
 struct Workspace {
     uint32_t n = 0, nwords = 0;
@@ -360,6 +370,45 @@ struct Row {
     uint32_t x[L];
 };
 
+// Slot of node y, inserting it if absent, without touching the fill counter: *inserted
+// tells the caller, which counts inserts once per warp.  EMPTY when the map is full.
+__device__ __forceinline__ uint32_t find_or_insert_nf(uint32_t *hkeys, uint32_t H, uint32_t hshift, uint32_t y,
+                                                      bool *inserted) {
+    uint32_t h = (y * 0x9E3779B1u) >> hshift;
+    volatile uint32_t *vk = hkeys;
+    *inserted = false;
+    for (uint32_t probe = 0; probe < H; probe++) {
+        const uint32_t k = vk[h];
+        if (k == y) return h;
+        if (k == EMPTY) {
+            const uint32_t prev = atomicCAS(&hkeys[h], EMPTY, y);
+            if (prev == EMPTY) {
+                *inserted = true;
+                return h;
+            }
+            if (prev == y) return h;
+        }
+        h = (h + 1) & (H - 1);
+    }
+    return EMPTY;
+}
+
+// Warp-aggregated append: every lane with want = true gets a distinct index of the
+// queue (one shared atomic per warp).  All 32 lanes must call.
+__device__ __forceinline__ void warp_push(bool want, uint32_t value, uint32_t *count, uint32_t *queue,
+                                          uint32_t cap) {
+    const uint32_t b = __ballot_sync(FULL, want);
+    if (!b) return;
+    const uint32_t lane = threadIdx.x & 31;
+    uint32_t base = 0;
+    if (lane == 0) base = atomicAdd(count, uint32_t(__popc(b)));
+    base = __shfl_sync(FULL, base, 0);
+    if (want) {
+        const uint32_t qi = base + __popc(b & ((1u << lane) - 1));
+        if (qi < cap) queue[qi] = value;
+    }
+}
+
 template <int L>
 __device__ __forceinline__ Row<L> load_row(const uint32_t *p) {
     Row<L> r;
@@ -418,29 +467,72 @@ __device__ __forceinline__ uint32_t find_or_insert(uint32_t *hkeys, uint32_t H, 
     return EMPTY;
 }
 
-// One thread block searches one tile of T = 32 L sources at a time (persistent: blocks
-// pop tiles from a global counter).  Thread `lane` of a warp owns sources
-// lane*L .. lane*L+L-1 of every slab row.
+// Exclusive prefix sum of v over the block; *total receives the sum.  All threads call;
+// warp_buf must hold THREADS / 32 + 1 words.
+template <int THREADS>
+__device__ __forceinline__ uint32_t block_exclusive_scan(uint32_t v, uint32_t *warp_buf, uint32_t *total) {
+    constexpr int SEARCH_WARPS = THREADS / 32;
+    const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    uint32_t x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t t = __shfl_up_sync(FULL, x, o);
+        if (lane >= uint32_t(o)) x += t;
+    }
+    if (lane == 31) warp_buf[warp] = x;
+    __syncthreads();
+    if (warp == 0) {
+        const uint32_t w = lane < SEARCH_WARPS ? warp_buf[lane] : 0;
+        uint32_t y = w;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t t = __shfl_up_sync(FULL, y, o);
+            if (lane >= uint32_t(o)) y += t;
+        }
+        if (lane < SEARCH_WARPS) warp_buf[lane] = y - w;
+        if (lane == 31) warp_buf[SEARCH_WARPS] = y;  // warp_buf holds SEARCH_WARPS + 1 words
+    }
+    __syncthreads();
+    const uint32_t r = warp_buf[warp] + x - v;
+    *total = warp_buf[SEARCH_WARPS];
+    __syncthreads();
+    return r;
+}
+
+// One thread block searches one tile of up to T = 32 L sources at a time (persistent:
+// blocks pop tiles from a global counter).  Lane-group j of a slab row holds sources
+// j*L .. j*L+L-1.
 //
 // Per slot h the map keeps, besides its node id hkeys[h]:
 //   prio[h]  the least improved-but-unrelaxed distance in the row, INF when clean;
-//   dmask[h] which thread-lanes of the row improved since the row was last relaxed.
-// A relaxation by a warp is: atomicMin on the slab (fire and forget), a block-scope
-// fence, then dmask |= improved lanes, then prio = min(prio, least improved value)
-// (pushing h on the near queue when it becomes dirty inside the current bucket).  A
-// scan takes prio first and skips a clean slot; only then does it take dmask, fence,
-// and read the row.  With that order every improvement is relaxed at least once after
-// it happened, and a rescan relaxes only the lanes that changed.
+//   dmask[h] which lane-groups of the row improved since the row was last relaxed.
+// A relaxation is: atomicMin on the slab (fire and forget), then dmask |= improved
+// groups, then prio = min(prio, least improved value) (pushing h on the near queue when
+// it becomes dirty inside the current bucket).  A scan takes prio, skips a clean slot,
+// takes dmask and reads the dirty groups of the row.  Scans (step A below) and
+// relaxations (step B) never overlap: a block barrier separates them, and the barrier
+// makes every slab update of step B visible to the block before the next step A reads
+// the row.  So every improvement is relaxed at least once after it happened, and a
+// rescan relaxes only the groups that changed.
+//
+// A round relaxes the near queue in block-wide steps of up to ICAP items: one thread per
+// item takes its prio and dmask, its CSR offsets and the least dirty value; a block
+// prefix sum over the items' degrees lays their arcs out; then one thread per arc loads
+// it, finds (or inserts) the head's slot, and relaxes every dirty lane-group of the
+// item into that slot.  So a round costs a few memory round trips, not one per arc.
 //
 // GMAP = false keeps the map in shared memory; GMAP = true keeps it in global memory
 // so a tile whose union ball outgrows shared memory can be searched again.
-template <int L, bool GMAP>
-__global__ void __launch_bounds__(SEARCH_THREADS, CTAS_PER_SM) k_tile_search(SearchArgs a) {
+template <int L, bool GMAP, int THREADS>
+__global__ void __launch_bounds__(THREADS, (THREADS == NARROW ? CTAS_PER_SM : 1)) k_tile_search(SearchArgs a) {
     constexpr int T = 32 * L;
-    constexpr int B = 4;  // arcs relaxed together (their row loads are in flight at once)
-    constexpr int P = L == 1 ? 4 : (L == 2 ? 2 : 1);  // queue items a warp scans together
+    constexpr int G = 4 / L;  // lane-groups of one arc relaxed together
+    constexpr int SEARCH_THREADS = THREADS;
+    constexpr int SEARCH_WARPS = THREADS / 32;
+    constexpr uint32_t QCAP = qcap_of(THREADS);
+    constexpr uint32_t ICAP = icap_of(THREADS);
     extern __shared__ uint32_t smem[];
-    uint32_t *hkeys, *prio, *dmask, *qa;
+    uint32_t *hkeys, *qa;
     if constexpr (GMAP) {
         hkeys = a.gmap + size_t(blockIdx.x) * 3 * a.H;
         qa = smem;
@@ -448,12 +540,17 @@ __global__ void __launch_bounds__(SEARCH_THREADS, CTAS_PER_SM) k_tile_search(Sea
         hkeys = smem;
         qa = smem + 3 * a.H;
     }
-    prio = hkeys + a.H;
-    dmask = prio + a.H;
+    uint32_t *prio = hkeys + a.H;
+    uint32_t *dmask = prio + a.H;
     uint32_t *qb = qa + QCAP;
+    uint32_t *it_x = qb + QCAP;        // staged items: slot,
+    uint32_t *it_mask = it_x + ICAP;   // dirty groups,
+    uint32_t *it_beg = it_mask + ICAP; // first arc,
+    uint32_t *it_off = it_beg + ICAP;  // arc offset in the step,
+    uint32_t *it_dmin = it_off + ICAP; // least dirty value
     __shared__ uint32_t src_orig[T];
-    __shared__ uint32_t s_tile, s_ncur, s_nnext, s_cursor, s_fill, s_fail, s_stop, s_minp;
-    __shared__ uint32_t s_warp_cnt[SEARCH_WARPS];
+    __shared__ uint32_t s_tile, s_ncur, s_nnext, s_fill, s_fail, s_stop, s_minp;
+    __shared__ uint32_t s_warp[SEARCH_WARPS + 1];
     __shared__ unsigned long long s_base;
 
     const uint32_t tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -461,6 +558,9 @@ __global__ void __launch_bounds__(SEARCH_THREADS, CTAS_PER_SM) k_tile_search(Sea
     const uint32_t bound = a.bound;
     const uint64_t delta = a.delta;
     unsigned long long my_scans = 0, my_slots = 0, my_arcs = 0;
+    unsigned long long c_rounds = 0, c_items = 0, c_bounds = 0, c_arcs = 0;
+    unsigned long long y_stepA = 0, y_stepB = 0, y_bound = 0, y_emit = 0;
+    long long t_mark = clock64();
 
     if (__ldcg(&a.ctl->err)) return;
     const uint32_t nR = __ldcg(&a.ctl->r_count);
@@ -477,7 +577,6 @@ __global__ void __launch_bounds__(SEARCH_THREADS, CTAS_PER_SM) k_tile_search(Sea
         if (tid == 0) {
             s_ncur = 0;
             s_nnext = 0;
-            s_cursor = 0;
             s_fill = 0;
             s_fail = 0;
             s_stop = 0;
@@ -514,137 +613,158 @@ __global__ void __launch_bounds__(SEARCH_THREADS, CTAS_PER_SM) k_tile_search(Sea
                 // takes the same decision.
                 __syncthreads();
                 const uint32_t ncur = min(s_ncur, QCAP);
+                if (tid == 0) {
+                    const long long t = clock64();
+                    y_bound += t - t_mark;
+                    t_mark = t;
+                }
                 if (ncur == 0 || s_stop) break;
-                // Each warp takes P queue items at a time: their prio / dmask exchanges,
-                // CSR offsets and slab rows are fetched together, their arcs are
-                // concatenated across the lanes, and up to B arcs' destination rows are
-                // in flight at once.
-                for (;;) {
-                    uint32_t base = 0;
-                    if (lane == 0) base = atomicAdd(&s_cursor, uint32_t(P));
-                    base = __shfl_sync(FULL, base, 0);
-                    if (base >= ncur) break;
-                    uint32_t x = EMPTY, mask = 0, beg = 0, deg = 0;
-                    if (lane < P && base + lane < ncur) {
-                        x = qcur[base + lane];
+                if (tid == 0) {
+                    c_rounds++;
+                    c_items += ncur;
+                }
+                for (uint32_t c0 = 0; c0 < ncur; c0 += ICAP) {
+                    const uint32_t nc = min(ICAP, ncur - c0);
+                    // -- step A: one thread per queue item
+                    uint32_t deg = 0;
+                    if (tid < nc) {
+                        const uint32_t x = qcur[c0 + tid];
+                        uint32_t mask = 0, beg = 0, dmin = INF;
                         const uint32_t p = atomicExch(&prio[x], INF);
                         if (p != INF) mask = atomicExch(&dmask[x], 0u);
                         if (mask) {
+                            my_scans++;
                             const uint32_t y0 = hkeys[x];
                             beg = __ldg(&a.row_ptr[y0]);
                             deg = __ldg(&a.row_ptr[y0 + 1]) - beg;
+                            const uint32_t *xrow = slab + size_t(x) * T;
+                            for (uint32_t m = mask; m;) {
+                                Row<L> r[G];
+#pragma unroll
+                                for (int k = 0; k < G; k++) {
+#pragma unroll
+                                    for (int q = 0; q < L; q++) r[k].x[q] = INF;
+                                    if (m) {
+                                        r[k] = load_row<L>(xrow + (__ffs(m) - 1) * L);
+                                        m &= m - 1;
+                                    }
+                                }
+#pragma unroll
+                                for (int k = 0; k < G; k++)
+#pragma unroll
+                                    for (int q = 0; q < L; q++) dmin = min(dmin, r[k].x[q]);
+                            }
+                            if (dmin > bound) deg = 0;
                         }
+                        it_x[tid] = x;
+                        it_mask[tid] = mask;
+                        it_beg[tid] = beg;
+                        it_dmin[tid] = dmin;
                     }
-                    if (__ballot_sync(FULL, mask != 0) == 0) continue;  // all clean
-                    __threadfence_block();
-                    Row<L> dx[P];
-                    uint32_t ms[P], bg[P], pref[P + 1], dmn[P];
-                    pref[0] = 0;
-#pragma unroll
-                    for (int j = 0; j < P; j++) {
-                        const uint32_t xj = __shfl_sync(FULL, x, j);
-                        ms[j] = __shfl_sync(FULL, mask, j);
-                        bg[j] = __shfl_sync(FULL, beg, j);
-                        pref[j + 1] = pref[j] + __shfl_sync(FULL, deg, j);
-#pragma unroll
-                        for (int q = 0; q < L; q++) dx[j].x[q] = INF;
-                        if ((ms[j] >> lane) & 1u) dx[j] = load_row<L>(slab + size_t(xj) * T + lane * L);
+                    uint32_t total;
+                    const uint32_t off = block_exclusive_scan<THREADS>(deg, s_warp, &total);
+                    if (tid < nc) it_off[tid] = off;
+                    __syncthreads();
+                    if (tid == 0) {
+                        const long long t = clock64();
+                        y_stepA += t - t_mark;
+                        t_mark = t;
+                        c_arcs += total;
                     }
+                    // -- step B: one thread per arc of the staged items, two arcs in flight
+                    // (warp-uniform trip count, so the ballots below see every lane)
+                    for (uint32_t g0 = tid & ~31u; g0 < total; g0 += 2 * SEARCH_THREADS) {
+                        uint32_t item[2], hy[2], w[2];
+                        bool push[2] = {false, false};
 #pragma unroll
-                    for (int j = 0; j < P; j++) {
-                        uint32_t v = dx[j].x[0];
-#pragma unroll
-                        for (int q = 1; q < L; q++) v = min(v, dx[j].x[q]);
-                        dmn[j] = __reduce_min_sync(FULL, v);
-                        if (ms[j]) my_scans++;
-                    }
-                    const uint32_t total = pref[P];
-                    for (uint32_t g0 = 0; g0 < total; g0 += 32) {
-                        const uint32_t gi = g0 + lane;
-                        // item of arc gi: the last j with pref[j] <= gi
-                        uint32_t jj = 0, pj = 0, bj = bg[0], dj = dmn[0];
-#pragma unroll
-                        for (int j = 1; j < P; j++)
-                            if (gi >= pref[j]) {
-                                jj = j;
-                                pj = pref[j];
-                                bj = bg[j];
-                                dj = dmn[j];
+                        for (int u = 0; u < 2; u++) {
+                            const uint32_t gi = g0 + lane + u * SEARCH_THREADS;
+                            hy[u] = EMPTY;
+                            w[u] = 0;
+                            item[u] = 0;
+                            if (gi >= total) continue;
+                            uint32_t lo = 0, hi = nc - 1;  // last item whose arcs start at or before gi
+                            while (lo < hi) {
+                                const uint32_t mid = (lo + hi + 1) >> 1;
+                                if (it_off[mid] <= gi) lo = mid;
+                                else hi = mid - 1;
                             }
-                        uint2 arc = make_uint2(0, 0);
-                        bool need = false;
-                        if (gi < total) {
-                            arc = __ldg(&a.adj[bj + (gi - pj)]);
-                            need = dj <= bound && dj + arc.y <= bound;
+                            item[u] = lo;
+                            const uint2 arc = __ldg(&a.adj[it_beg[lo] + (gi - it_off[lo])]);
+                            w[u] = arc.y;
+                            hy[u] = arc.x;  // the head node until its slot is known
                         }
-                        uint32_t hy = EMPTY;
-                        if (need) hy = find_or_insert(hkeys, a.H, a.hshift, arc.x, &s_fill, a.max_fill, &s_fail);
-                        uint32_t m = __ballot_sync(FULL, hy != EMPTY);
-                        while (m) {
-                            uint32_t hj[B], wj[B], jk[B];
-                            Row<L> cur[B], src[B];
+                        uint32_t inserted = 0;
 #pragma unroll
-                            for (int k = 0; k < B; k++) {
-                                const bool have = m != 0;  // warp-uniform
-                                const int l = have ? __ffs(m) - 1 : 0;
-                                if (have) m &= m - 1;
-                                const uint32_t h = __shfl_sync(FULL, hy, l);
-                                wj[k] = __shfl_sync(FULL, arc.y, l);
-                                jk[k] = __shfl_sync(FULL, jj, l);
-                                hj[k] = have ? h : EMPTY;
+                        for (int u = 0; u < 2; u++) {
+                            if (hy[u] == EMPTY) continue;
+                            if (it_dmin[item[u]] + w[u] > bound) {
+                                hy[u] = EMPTY;
+                                continue;
                             }
+                            bool ins;
+                            hy[u] = find_or_insert_nf(hkeys, a.H, a.hshift, hy[u], &ins);
+                            if (hy[u] == EMPTY) s_fail = 1;
+                            inserted += ins;
+                        }
+                        inserted = __reduce_add_sync(FULL, inserted);
+                        if (lane == 0 && inserted && atomicAdd(&s_fill, inserted) + inserted > a.max_fill)
+                            s_fail = 1;
 #pragma unroll
-                            for (int k = 0; k < B; k++) {
-                                src[k] = dx[0];
+                        for (int u = 0; u < 2; u++) {
+                            if (hy[u] == EMPTY) continue;
+                            const uint32_t *xrow = slab + size_t(it_x[item[u]]) * T;
+                            uint32_t *yrow = slab + size_t(hy[u]) * T;
+                            uint32_t imask = 0, imin = INF;
+                            for (uint32_t m = it_mask[item[u]]; m;) {
+                                uint32_t jj[G];
+                                Row<L> dv[G], cv[G];
 #pragma unroll
-                                for (int j = 1; j < P; j++)
-                                    if (jk[k] == uint32_t(j)) src[k] = dx[j];
+                                for (int k = 0; k < G; k++) {
+                                    jj[k] = m ? uint32_t(__ffs(m) - 1) : 32u;
+                                    if (m) m &= m - 1;
+                                }
 #pragma unroll
-                                for (int q = 0; q < L; q++) cur[k].x[q] = 0;
-                                uint32_t sm = src[k].x[0];
+                                for (int k = 0; k < G; k++) {
+                                    if (jj[k] < 32) {
+                                        dv[k] = load_row<L>(xrow + jj[k] * L);
+                                        cv[k] = load_row<L>(yrow + jj[k] * L);
+                                    }
+                                }
 #pragma unroll
-                                for (int q = 1; q < L; q++) sm = min(sm, src[k].x[q]);
-                                if (hj[k] != EMPTY && sm != INF && sm + wj[k] <= bound)
-                                    cur[k] = load_row<L>(slab + size_t(hj[k]) * T + lane * L);
-                            }
+                                for (int k = 0; k < G; k++) {
+                                    if (jj[k] >= 32) continue;
 #pragma unroll
-                            for (int k = 0; k < B; k++) {
-                                if (hj[k] == EMPTY) continue;  // warp-uniform
-                                uint32_t *row = slab + size_t(hj[k]) * T + lane * L;
-                                uint32_t imin = INF;
-#pragma unroll
-                                for (int q = 0; q < L; q++) {
-                                    if (src[k].x[q] != INF) {
-                                        const uint32_t d = src[k].x[q] + wj[k];
-                                        if (d <= bound && d < cur[k].x[q]) {
-                                            atomicMin(row + q, d);
+                                    for (int q = 0; q < L; q++) {
+                                        if (dv[k].x[q] == INF) continue;
+                                        const uint32_t d = dv[k].x[q] + w[u];
+                                        if (d <= bound && d < cv[k].x[q]) {
+                                            atomicMin(yrow + jj[k] * L + q, d);
                                             imin = min(imin, d);
-                                        }
-                                    }
-                                }
-                                const uint32_t bal = __ballot_sync(FULL, imin != INF);
-                                if (bal) {
-                                    imin = __reduce_min_sync(FULL, imin);
-                                    __threadfence_block();
-                                    __syncwarp();
-                                    if (lane == 0) {
-                                        atomicOr(&dmask[hj[k]], bal);
-                                        const uint32_t old = atomicMin(&prio[hj[k]], imin);
-                                        if (imin < tau && (old == INF || old >= tau)) {
-                                            const uint32_t qi = atomicAdd(&s_nnext, 1u);
-                                            if (qi < QCAP) qnext[qi] = hj[k];
+                                            imask |= 1u << jj[k];
                                         }
                                     }
                                 }
                             }
+                            if (imask) {
+                                atomicOr(&dmask[hy[u]], imask);
+                                const uint32_t old = atomicMin(&prio[hy[u]], imin);
+                                push[u] = imin < tau && (old == INF || old >= tau);
+                            }
                         }
+#pragma unroll
+                        for (int u = 0; u < 2; u++) warp_push(push[u], hy[u], &s_nnext, qnext, QCAP);
+                    }
+                    __syncthreads();
+                    if (tid == 0) {
+                        const long long t = clock64();
+                        y_stepB += t - t_mark;
+                        t_mark = t;
                     }
                 }
-                __syncthreads();
                 if (tid == 0) {
                     s_ncur = s_nnext;
                     s_nnext = 0;
-                    s_cursor = 0;
                     s_stop = s_fail;
                 }
                 uint32_t *t = qcur;
@@ -653,7 +773,10 @@ __global__ void __launch_bounds__(SEARCH_THREADS, CTAS_PER_SM) k_tile_search(Sea
             }
             if (s_fail) break;
             // ---- the near queue is empty: find the smallest pending priority
-            if (tid == 0) s_minp = INF;
+            if (tid == 0) {
+                s_minp = INF;
+                c_bounds++;
+            }
             __syncthreads();
             uint32_t mp = INF;
             for (uint32_t h = tid; h < a.H; h += SEARCH_THREADS) mp = min(mp, prio[h]);
@@ -667,79 +790,108 @@ __global__ void __launch_bounds__(SEARCH_THREADS, CTAS_PER_SM) k_tile_search(Sea
                 if (tau > uint64_t(bound) + 1) tau = uint64_t(bound) + 1;
             }
             // ---- collect every pending slot of the (new) bucket into the near queue
-            for (uint32_t h = tid; h < a.H; h += SEARCH_THREADS) {
-                if (prio[h] < tau) {
-                    const uint32_t qi = atomicAdd(&s_ncur, 1u);
-                    if (qi < QCAP) qcur[qi] = h;
-                }
-            }
+            for (uint32_t h = tid; h < a.H; h += SEARCH_THREADS)  // H is a multiple of THREADS
+                warp_push(prio[h] < tau, h, &s_ncur, qcur, QCAP);
         }
         __syncthreads();
+        if (tid == 0) {
+            const long long t = clock64();
+            y_bound += t - t_mark;
+            t_mark = t;
+        }
 
-        // ---- emission: every slot of an S node, every lane within the bound
+        // ---- emission: every slot of an S node, every lane within the bound.  Warps
+        // take 32 consecutive slots at a time and ballot the ones holding S nodes.
         const bool ok = !s_fail;
+        const uint32_t lt = (1u << lane) - 1;
         if (ok) {
             uint32_t cnt = 0;
-            for (uint32_t h = warp; h < a.H; h += SEARCH_WARPS) {
-                const uint32_t y = hkeys[h];
-                if (y == EMPTY || !((__ldg(&a.sbits[y >> 5]) >> (y & 31)) & 1u)) continue;
-                const Row<L> r = load_row<L>(slab + size_t(h) * T + lane * L);
+            for (uint32_t c = warp * 32; c < a.H; c += SEARCH_WARPS * 32) {
+                const uint32_t yl = hkeys[c + lane];
+                const bool in_s = yl != EMPTY && ((__ldg(&a.sbits[yl >> 5]) >> (yl & 31)) & 1u);
+                for (uint32_t b = __ballot_sync(FULL, in_s); b; b &= b - 1) {
+                    const uint32_t h = c + __ffs(b) - 1;
+                    const Row<L> r = load_row<L>(slab + size_t(h) * T + lane * L);
 #pragma unroll
-                for (int q = 0; q < L; q++) cnt += __popc(__ballot_sync(FULL, r.x[q] <= bound));
+                    for (int q = 0; q < L; q++) cnt += __popc(__ballot_sync(FULL, r.x[q] <= bound));
+                }
             }
-            if (lane == 0) s_warp_cnt[warp] = cnt;
+            if (lane == 0) s_warp[warp] = cnt;
             __syncthreads();
             if (tid == 0) {
                 uint32_t run = 0;
                 for (int w = 0; w < SEARCH_WARPS; w++) {
-                    uint32_t c = s_warp_cnt[w];
-                    s_warp_cnt[w] = run;
+                    uint32_t c = s_warp[w];
+                    s_warp[w] = run;
                     run += c;
                 }
                 s_base = atomicAdd(&a.ctl->pairs, (unsigned long long)run);
             }
             __syncthreads();
-            unsigned long long pos = s_base + s_warp_cnt[warp];
-            const uint32_t lt = (1u << lane) - 1;
-            for (uint32_t h = warp; h < a.H; h += SEARCH_WARPS) {
-                const uint32_t y = hkeys[h];
-                if (y == EMPTY || !((__ldg(&a.sbits[y >> 5]) >> (y & 31)) & 1u)) continue;
-                const Row<L> r = load_row<L>(slab + size_t(h) * T + lane * L);
-                const unsigned long long v = __ldg(&a.iperm[y]);
+            unsigned long long pos = s_base + s_warp[warp];
+            for (uint32_t c = warp * 32; c < a.H; c += SEARCH_WARPS * 32) {
+                const uint32_t yl = hkeys[c + lane];
+                const bool in_s = yl != EMPTY && ((__ldg(&a.sbits[yl >> 5]) >> (yl & 31)) & 1u);
+                for (uint32_t b = __ballot_sync(FULL, in_s); b; b &= b - 1) {
+                    const uint32_t src_lane = __ffs(b) - 1;
+                    const uint32_t h = c + src_lane;
+                    const uint32_t y = __shfl_sync(FULL, yl, src_lane);
+                    const Row<L> r = load_row<L>(slab + size_t(h) * T + lane * L);
+                    const unsigned long long v = __ldg(&a.iperm[y]);
 #pragma unroll
-                for (int q = 0; q < L; q++) {
-                    const bool hit = r.x[q] <= bound;
-                    const uint32_t b = __ballot_sync(FULL, hit);
-                    if (hit) {
-                        const unsigned long long idx = pos + __popc(b & lt);
-                        if (idx < a.out_cap) {
-                            const unsigned long long u = src_orig[lane * L + q];
-                            a.out_key[idx] = (u << a.vbits) | v;
-                            a.out_d[idx] = r.x[q];
+                    for (int q = 0; q < L; q++) {
+                        const bool hit = r.x[q] <= bound;
+                        const uint32_t bb = __ballot_sync(FULL, hit);
+                        if (hit) {
+                            const unsigned long long idx = pos + __popc(bb & lt);
+                            if (idx < a.out_cap) {
+                                const unsigned long long u = src_orig[lane * L + q];
+                                a.out_key[idx] = (u << a.vbits) | v;
+                                a.out_d[idx] = r.x[q];
+                            }
                         }
+                        pos += __popc(bb);
                     }
-                    pos += __popc(b);
                 }
             }
         } else if (tid == 0) {
             a.failed[atomicAdd(&a.ctl->n_failed, 1u)] = tile;
         }
         // ---- leave the region clean (every row INF) for the next tile
-        for (uint32_t h = warp; h < a.H; h += SEARCH_WARPS) {
-            const uint32_t y = hkeys[h];
-            if (y == EMPTY) continue;
-            store_inf<L>(slab + size_t(h) * T + lane * L);
-            if (ok) {
+        for (uint32_t c = warp * 32; c < a.H; c += SEARCH_WARPS * 32) {
+            const uint32_t yl = hkeys[c + lane];
+            const bool used = yl != EMPTY;
+            if (ok && used) {
                 my_slots++;
-                my_arcs += __ldg(&a.row_ptr[y + 1]) - __ldg(&a.row_ptr[y]);
+                my_arcs += __ldg(&a.row_ptr[yl + 1]) - __ldg(&a.row_ptr[yl]);
             }
+            for (uint32_t b = __ballot_sync(FULL, used); b; b &= b - 1)
+                store_inf<L>(slab + size_t(c + __ffs(b) - 1) * T + lane * L);
         }
         __syncthreads();
+        if (tid == 0) {
+            const long long t = clock64();
+            y_emit += t - t_mark;
+            t_mark = t;
+        }
     }
+    my_slots = __reduce_add_sync(FULL, uint32_t(my_slots));
+    my_arcs = __reduce_add_sync(FULL, uint32_t(my_arcs));
+    my_scans = __reduce_add_sync(FULL, uint32_t(my_scans));
     if (lane == 0) {
         atomicAdd(&a.ctl->scans, my_scans);
         atomicAdd(&a.ctl->slots, my_slots);
         atomicAdd(&a.ctl->slot_arcs, my_arcs);
+    }
+    if (tid == 0) {
+        atomicAdd(&a.ctl->rounds, c_rounds);
+        atomicAdd(&a.ctl->round_items, c_items);
+        atomicAdd(&a.ctl->boundaries, c_bounds);
+        atomicAdd(&a.ctl->cyc_round, y_stepA + y_stepB);
+        atomicAdd(&a.ctl->cyc_stepA, y_stepA);
+        atomicAdd(&a.ctl->round_arcs, c_arcs);
+        atomicAdd(&a.ctl->cyc_bound, y_bound);
+        atomicAdd(&a.ctl->cyc_emit, y_emit);
     }
 }
 
@@ -892,40 +1044,54 @@ static uint32_t bits_for(uint32_t n) {
 }
 
 // Dynamic shared memory of a search block: the slot map (node, prio, dmask) unless it
-// lives in global memory, and the two near queues.
-static size_t search_smem(uint32_t H, bool gmap) { return (gmap ? 0 : size_t(H) * 12) + size_t(QCAP) * 8; }
+// lives in global memory, the two near queues and the staged items.
+static size_t search_smem(uint32_t H, bool gmap, int threads) {
+    return (gmap ? 0 : size_t(H) * 12) + size_t(qcap_of(threads)) * 8 + size_t(icap_of(threads)) * 20;
+}
 
-template <int L, bool GMAP>
+template <int L, bool GMAP, int THREADS>
 static void launch_search(const SearchArgs &a, uint32_t grid, cudaStream_t st) {
-    const size_t smem = search_smem(a.H, GMAP);
+    const size_t smem = search_smem(a.H, GMAP, THREADS);
     static std::once_flag once;
     std::call_once(once, [&] {
-        RN_CUDA(cudaFuncSetAttribute(k_tile_search<L, GMAP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     int(search_smem(SMEM_H1, GMAP))));
-        RN_CUDA(cudaFuncSetAttribute(k_tile_search<L, GMAP>, cudaFuncAttributePreferredSharedMemoryCarveout,
-                                     100));
+        RN_CUDA(cudaFuncSetAttribute(k_tile_search<L, GMAP, THREADS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     int(search_smem(THREADS == NARROW ? SMEM_H : SMEM_HW, GMAP, THREADS))));
+        RN_CUDA(cudaFuncSetAttribute(k_tile_search<L, GMAP, THREADS>,
+                                     cudaFuncAttributePreferredSharedMemoryCarveout, 100));
     });
-    k_tile_search<L, GMAP><<<grid, SEARCH_THREADS, smem, st>>>(a);
+    k_tile_search<L, GMAP, THREADS><<<grid, THREADS, smem, st>>>(a);
     RN_CUDA(cudaGetLastError());
 }
 
 template <int L>
-static int search_occupancy(uint32_t H) {
+static int search_occupancy() {
     int b = 0;
-    RN_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_tile_search<L, false>, SEARCH_THREADS,
-                                                          search_smem(H, false)));
+    RN_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_tile_search<L, false, NARROW>, NARROW,
+                                                          search_smem(SMEM_H, false, NARROW)));
     return b;
 }
 
-static void search(uint32_t T, bool gmap, const SearchArgs &a, uint32_t grid, cudaStream_t st) {
-    switch (T * 2 + (gmap ? 1 : 0)) {
-        case 64: launch_search<1, false>(a, grid, st); break;
-        case 65: launch_search<1, true>(a, grid, st); break;
-        case 128: launch_search<2, false>(a, grid, st); break;
-        case 129: launch_search<2, true>(a, grid, st); break;
-        case 256: launch_search<4, false>(a, grid, st); break;
-        case 257: launch_search<4, true>(a, grid, st); break;
-        default: fail(RN_EINVAL, "tile width must be 32, 64 or 128");
+enum class Shape { Narrow, Wide, WideGlobal };
+
+static void search(uint32_t T, Shape shape, const SearchArgs &a, uint32_t grid, cudaStream_t st) {
+    const int L = int(T / 32);
+    if (T != 32 && T != 64 && T != 128) fail(RN_EINVAL, "tile width must be 32, 64 or 128");
+    switch (shape) {
+        case Shape::Narrow:
+            if (L == 1) launch_search<1, false, NARROW>(a, grid, st);
+            else if (L == 2) launch_search<2, false, NARROW>(a, grid, st);
+            else launch_search<4, false, NARROW>(a, grid, st);
+            break;
+        case Shape::Wide:
+            if (L == 1) launch_search<1, false, WIDE>(a, grid, st);
+            else if (L == 2) launch_search<2, false, WIDE>(a, grid, st);
+            else launch_search<4, false, WIDE>(a, grid, st);
+            break;
+        case Shape::WideGlobal:
+            if (L == 1) launch_search<1, true, WIDE>(a, grid, st);
+            else if (L == 2) launch_search<2, true, WIDE>(a, grid, st);
+            else launch_search<4, true, WIDE>(a, grid, st);
+            break;
     }
 }
 
@@ -935,11 +1101,10 @@ static Control read_control(Workspace *ws, cudaStream_t st) {
     return *ws->ctl_host;
 }
 
-// Search every tile with the 8192-slot shared-memory map (two blocks per SM), then
-// search the tiles whose union ball overflowed it again: first with a 16384-slot
-// shared-memory map (one block per SM), then with global maps four times larger each
-// time.  The map never needs more than the next power of two >= 2n slots, where it
-// cannot overflow.
+// Search every tile with narrow blocks (8192-slot shared maps, two per SM), then
+// search the tiles whose union ball overflowed again: with wide blocks (16384-slot
+// shared maps), then with global maps four times larger each time.  The map never
+// needs more than the next power of two >= 2n slots, where it cannot overflow.
 static Control search_all(const DeviceGraph &g, Workspace *ws, uint32_t T, SearchArgs a,
                           uint32_t ntiles, cudaStream_t st, uint64_t *retried) {
     const uint32_t grid_max = uint32_t(ws->num_sms) * CTAS_PER_SM;
@@ -953,10 +1118,9 @@ static Control search_all(const DeviceGraph &g, Workspace *ws, uint32_t T, Searc
     a.slab = ws->slab;
     RN_CUDA(cudaEventRecord(ws->evs0, st));
     if (ntiles) {
-        search(T, false, a, std::max<uint32_t>(1, std::min(ntiles, grid_max)), st);
+        search(T, Shape::Narrow, a, std::max<uint32_t>(1, std::min(ntiles, grid_max)), st);
         ws->launches++;
-        ws->blocks_per_sm = T == 32 ? search_occupancy<1>(SMEM_H)
-                          : T == 64 ? search_occupancy<2>(SMEM_H) : search_occupancy<4>(SMEM_H);
+        ws->blocks_per_sm = T == 32 ? search_occupancy<1>() : T == 64 ? search_occupancy<2>() : search_occupancy<4>();
     }
     RN_CUDA(cudaEventRecord(ws->evs1, st));
     Control c = read_control(ws, st);
@@ -974,17 +1138,19 @@ static Control search_all(const DeviceGraph &g, Workspace *ws, uint32_t T, Searc
         r.ntiles = nf;
         r.failed = next;
         if (H == SMEM_H) {
-            H = SMEM_H1;  // same slab (it holds grid_max regions of SMEM_H rows)
-            r.H = SMEM_H1;
-            r.hshift = 32 - bits_for(SMEM_H1);
-            r.max_fill = SMEM_H1 * 7 / 8;
-            search(T, false, r, std::min<uint32_t>(nf, uint32_t(ws->num_sms)), st);
+            // wide blocks reuse the slab: it holds grid_max regions of SMEM_H rows,
+            // that is num_sms regions of SMEM_HW rows
+            H = SMEM_HW;
+            r.H = SMEM_HW;
+            r.hshift = 32 - bits_for(SMEM_HW);
+            r.max_fill = SMEM_HW * 7 / 8;
+            search(T, Shape::Wide, r, std::min<uint32_t>(nf, uint32_t(ws->num_sms)), st);
         } else {
             H = std::min<uint64_t>(H * 4, hcap);
             const size_t per_block = (3 * H + H * T) * 4;
             const size_t budget = size_t(8) << 30;
             const uint32_t rgrid =
-                uint32_t(std::max<size_t>(1, std::min<size_t>({nf, grid_max, budget / per_block})));
+                uint32_t(std::max<size_t>(1, std::min<size_t>({size_t(nf), size_t(ws->num_sms), budget / per_block})));
             if (ws->gretry_bytes < per_block * rgrid) {
                 device_free(ws->gretry);
                 ws->gretry = nullptr;
@@ -1000,7 +1166,7 @@ static Control search_all(const DeviceGraph &g, Workspace *ws, uint32_t T, Searc
             r.H = uint32_t(H);
             r.hshift = 32 - bits_for(uint32_t(H));
             r.max_fill = uint32_t(H * 7 / 8);
-            search(T, true, r, rgrid, st);
+            search(T, Shape::WideGlobal, r, rgrid, st);
         }
         ws->launches++;
         c = read_control(ws, st);
@@ -1009,9 +1175,12 @@ static Control search_all(const DeviceGraph &g, Workspace *ws, uint32_t T, Searc
     return c;
 }
 
+// Bucket width: four median arc weights unless configured.  Wider buckets mean fewer
+// rounds (each round is a few memory round trips for the whole block) at the price of
+// some relaxations redone inside a bucket.
 static uint32_t choose_delta(const EngineConfig &cfg, uint32_t median_w) {
     if (cfg.delta) return cfg.delta;
-    return std::max<uint32_t>(1, median_w);
+    return std::max<uint32_t>(1, 4 * median_w);
 }
 
 static void ensure_u32(uint32_t **p, uint32_t *cap, uint32_t want) {
@@ -1166,6 +1335,14 @@ void run_join(const DeviceGraph &g, Workspace *ws, const EngineConfig &cfg, uint
     stats->blocks_per_sm = uint32_t(ws->blocks_per_sm);
     stats->device_ms = ms;
     stats->search_ms = sms;
+    stats->rounds = c.rounds;
+    stats->round_items = c.round_items;
+    stats->boundaries = c.boundaries;
+    stats->cycles_rounds = c.cyc_round;
+    stats->cycles_boundaries = c.cyc_bound;
+    stats->cycles_emission = c.cyc_emit;
+    stats->cycles_step_a = c.cyc_stepA;
+    stats->round_arcs = c.round_arcs;
 }
 
 void run_kcp(const DeviceGraph &, Workspace *, const EngineConfig &, uint32_t, const uint32_t *,

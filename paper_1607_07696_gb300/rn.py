@@ -59,7 +59,10 @@ class rn_query_stats(C.Structure):
                 ("passes", C.c_uint32), ("theta_final", C.c_uint32), ("launches", C.c_uint32),
                 ("blocks_per_sm", C.c_uint32),
                 ("slots", C.c_uint64), ("slot_arcs", C.c_uint64), ("device_ms", C.c_double),
-                ("search_ms", C.c_double)]
+                ("search_ms", C.c_double), ("rounds", C.c_uint64), ("round_items", C.c_uint64),
+                ("boundaries", C.c_uint64), ("cycles_rounds", C.c_uint64),
+                ("cycles_boundaries", C.c_uint64), ("cycles_emission", C.c_uint64),
+                ("cycles_step_a", C.c_uint64), ("round_arcs", C.c_uint64)]
 
 
 # Every symbol include/rn.h declares, with its ctypes signature (restype, argtypes).
