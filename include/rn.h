@@ -183,6 +183,32 @@ rn_status rn_distance_join_dev(const rn_graph *g, const uint32_t *dR, uint32_t n
                                rn_stream stream);
 
 /*
+ * rn_distance_join_noalloc -- the join of rn_distance_join_dev for callers that cannot
+ * let the library allocate device memory: their own allocator has reserved the
+ * device, or a cudaFree (which synchronises the whole device) or an allocation that can
+ * fail mid-query is not acceptable on their path.  The paper has no counterpart: this
+ * is a deployment variant of the same computation.
+ *   dR, dS            : device arrays of nR / nS node ids (sets, disjoint).
+ *   out_u, out_v, out_d: caller-owned device buffers of out_cap entries each; the pairs
+ *                       are written there sorted by (u, v).
+ *   n_out             : host; receives the pair count (also when out_cap was too small).
+ * It allocates nothing: every scratch buffer lives in one static device array of about
+ * 22 MB that every GPU loading the library holds until the process exits.  Limits fixed
+ * by that array: at most 2^20 nodes in the graph, 65,536 nodes in R and 2^19 result
+ * pairs, and every source tile's search must fit the array's slab; beyond them it
+ * returns RN_EINVAL (use rn_distance_join_dev).  The first call on each device finds the
+ * array's device address and fills its slab, so make that first call before any stream
+ * capture.  All calls share the array and it keeps the last call's contents (each call
+ * clears what it needs); calls hold a process-wide lock and return after their GPU
+ * work is done, so they do not overlap each other -- any other work that overlapped one
+ * of them on the GPU and touched the array would race.
+ */
+rn_status rn_distance_join_noalloc(const rn_graph *g, const uint32_t *dR, uint32_t nR,
+                                   const uint32_t *dS, uint32_t nS, uint32_t theta, uint32_t *out_u,
+                                   uint32_t *out_v, uint32_t *out_d, uint64_t out_cap, uint64_t *n_out,
+                                   rn_stream stream);
+
+/*
  * rn_kcp -- the k closest pairs (u in R, v in S) with dist(u, v) <= theta, sorted by
  * (d, u, v); fewer than k if fewer pairs lie within theta (Abstract; Section 4,
  * Algorithm 2 "k items within theta"; the global k-th distance of Algorithm 3 bounds

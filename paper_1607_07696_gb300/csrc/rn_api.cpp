@@ -258,6 +258,23 @@ rn_status rn_distance_join_dev(const rn_graph *cg, const uint32_t *dR, uint32_t 
     });
 }
 
+rn_status rn_distance_join_noalloc(const rn_graph *cg, const uint32_t *dR, uint32_t nR, const uint32_t *dS,
+                                   uint32_t nS, uint32_t theta, uint32_t *out_u, uint32_t *out_v,
+                                   uint32_t *out_d, uint64_t out_cap, uint64_t *n_out, rn_stream stream) {
+    return guarded([&] {
+        if (!cg || !n_out) rn::fail(RN_EINVAL, "null argument");
+        *n_out = 0;
+        if ((nR && !dR) || (nS && !dS)) rn::fail(RN_EINVAL, "null R or S with a non-zero size");
+        if (out_cap && (!out_u || !out_v || !out_d)) rn::fail(RN_EINVAL, "null output buffer");
+        check_theta(theta);
+        int cur = -1;
+        cudaGetDevice(&cur);
+        if (cur != cg->device) rn::fail(RN_EINVAL, "the graph lives on another device than the current one");
+        rn::run_join_noalloc(cg->dev, cg->info.median_weight, dR, nR, dS, nS, theta, out_u, out_v, out_d,
+                             out_cap, n_out, (void *)stream);
+    });
+}
+
 rn_status rn_distance_join(const rn_graph *cg, const uint32_t *R, uint32_t nR, const uint32_t *S,
                            uint32_t nS, uint32_t theta, rn_pairs *out) {
     return guarded([&] {

@@ -1345,6 +1345,162 @@ void run_join(const DeviceGraph &g, Workspace *ws, const EngineConfig &cfg, uint
     stats->round_arcs = c.round_arcs;
 }
 
+// ------------------------------------------------- join without allocation ----
+// The entry point rn_distance_join_noalloc runs the same join through the same kernels,
+// but takes every scratch buffer from one statically sized device array instead of
+// allocating: for callers that cannot let the library allocate device memory (their
+// own allocator owns the device, a cudaFree would synchronise the whole device in a
+// latency-critical path, or a failed allocation in the middle of a query is not
+// acceptable).  Its limits are fixed at build time (below); every GPU that loads the
+// library holds the array (about 22 MB) until the process exits.
+
+constexpr uint32_t NA_MAX_N = 1u << 20;       // nodes of the graph
+constexpr uint32_t NA_MAX_R = 1u << 16;       // |R|
+constexpr uint32_t NA_MAX_PAIRS = 1u << 19;   // result pairs
+constexpr uint32_t NA_BLOCKS = 8;             // narrow search blocks (slab regions)
+constexpr size_t NA_ALIGN = 64;               // sub-arrays start on 256-byte boundaries
+constexpr size_t na_round(size_t w) { return (w + NA_ALIGN - 1) / NA_ALIGN * NA_ALIGN; }
+constexpr size_t NA_CTL = 0;
+constexpr size_t NA_BITS = NA_CTL + na_round(sizeof(Control) / 4 + 1);
+constexpr size_t NA_NWORDS = NA_MAX_N / 32;
+constexpr size_t NA_BSUMS = NA_BITS + 3 * na_round(NA_NWORDS);
+constexpr size_t NA_RSORT = NA_BSUMS + na_round(NA_NWORDS / 1024 + 2);
+constexpr size_t NA_FAIL = NA_RSORT + na_round(NA_MAX_R);
+constexpr size_t NA_KEYS = NA_FAIL + 2 * na_round(NA_MAX_R);
+constexpr size_t NA_VALS = NA_KEYS + 2 * na_round(2 * size_t(NA_MAX_PAIRS));
+constexpr size_t NA_HIST = NA_VALS + 2 * na_round(NA_MAX_PAIRS);
+constexpr size_t NA_SLAB = NA_HIST + na_round(size_t(256) * (NA_MAX_PAIRS / RS_TILE + 1));
+constexpr size_t NA_WORDS = NA_SLAB + size_t(NA_BLOCKS) * SMEM_H * 32;
+
+static __device__ __align__(256) uint32_t g_noalloc_scratch[NA_WORDS];
+
+namespace {
+std::mutex g_na_mu;       // one call at a time in this process
+uint32_t *g_na_ptr[64];   // device address of the scratch array, per device
+}  // namespace
+
+// Once per device, with that device current: the array's device address (host code
+// sees only a host-side stand-in for the symbol) and a first fill of the slab rows
+// with INF.
+static uint32_t *noalloc_scratch(int dev) {
+    if (dev < 0 || dev >= 64) fail(RN_EINVAL, "device ordinal out of range for the no-alloc join");
+    if (!g_na_ptr[dev]) {
+        void *p = nullptr;
+        RN_CUDA(cudaGetSymbolAddress(&p, g_noalloc_scratch));
+        RN_CUDA(cudaMemset(static_cast<uint32_t *>(p) + NA_SLAB, 0xFF, size_t(NA_BLOCKS) * SMEM_H * 32 * 4));
+        RN_CUDA(cudaDeviceSynchronize());
+        g_na_ptr[dev] = static_cast<uint32_t *>(p);
+    }
+    return g_na_ptr[dev];
+}
+
+void run_join_noalloc(const DeviceGraph &g, uint32_t median_w, const uint32_t *dR, uint32_t nR,
+                      const uint32_t *dS, uint32_t nS, uint32_t theta, uint32_t *out_u, uint32_t *out_v,
+                      uint32_t *out_d, uint64_t out_cap, uint64_t *n_out, void *stream) {
+    cudaStream_t st = (cudaStream_t)stream;
+    if (theta == RN_INF) theta = RN_THETA_MAX;
+    if (theta > RN_THETA_MAX) fail(RN_EINVAL, "theta must be <= 2^31 or RN_INF");
+    if (g.n > NA_MAX_N) fail(RN_EINVAL, "the no-alloc join takes graphs of at most 2^20 nodes");
+    if (nR > NA_MAX_R) fail(RN_EINVAL, "the no-alloc join takes at most 65536 R nodes");
+    std::lock_guard<std::mutex> lk(g_na_mu);
+    int dev = 0;
+    RN_CUDA(cudaGetDevice(&dev));
+    uint32_t *base = noalloc_scratch(dev);
+    Control *ctl = reinterpret_cast<Control *>(base + NA_CTL);
+    uint32_t *used_bits = base + NA_BITS, *rbits = used_bits + na_round(NA_NWORDS),
+             *sbits = rbits + na_round(NA_NWORDS);
+    uint32_t *bsums = base + NA_BSUMS, *rsorted = base + NA_RSORT;
+    uint32_t *failed = base + NA_FAIL, *failed2 = failed + na_round(NA_MAX_R);
+    unsigned long long *keyA = reinterpret_cast<unsigned long long *>(base + NA_KEYS);
+    unsigned long long *keyB = reinterpret_cast<unsigned long long *>(base + NA_KEYS + na_round(2 * size_t(NA_MAX_PAIRS)));
+    uint32_t *valA = base + NA_VALS, *valB = valA + na_round(NA_MAX_PAIRS);
+    uint32_t *hist = base + NA_HIST;
+    uint32_t *slab = base + NA_SLAB;
+    const uint32_t nwords = (g.n + 31) / 32;
+    const uint32_t nblocks = (nwords + 1023) / 1024;
+
+    // the array keeps the previous call's contents: clear what must start at zero, and
+    // put the slab rows back to INF (a previous call may have stopped half-way)
+    RN_CUDA(cudaMemsetAsync(ctl, 0, sizeof(Control), st));
+    RN_CUDA(cudaMemsetAsync(used_bits, 0, size_t(nwords) * 4, st));
+    RN_CUDA(cudaMemsetAsync(rbits, 0, size_t(nwords) * 4, st));
+    RN_CUDA(cudaMemsetAsync(sbits, 0, size_t(nwords) * 4, st));
+    RN_CUDA(cudaMemsetAsync(slab, 0xFF, size_t(NA_BLOCKS) * SMEM_H * 32 * 4, st));
+    if (nR)
+        k_mark_set<<<std::min<uint32_t>((nR + 255) / 256, 4096), 256, 0, st>>>(dR, nR, g.n, g.perm, used_bits, rbits, ctl);
+    if (nS)
+        k_mark_set<<<std::min<uint32_t>((nS + 255) / 256, 4096), 256, 0, st>>>(dS, nS, g.n, g.perm, used_bits, sbits, ctl);
+    k_bits_count<<<nblocks, 1024, 0, st>>>(rbits, nwords, bsums);
+    k_bits_compact<<<nblocks, 1024, 0, st>>>(rbits, nwords, bsums, nblocks, rsorted, ctl);
+    RN_CUDA(cudaGetLastError());
+
+    constexpr uint32_t T = 32;
+    const uint32_t tile_src = std::max<uint32_t>(1, std::min<uint32_t>(T, (nR + NA_BLOCKS - 1) / NA_BLOCKS));
+    const uint32_t ntiles = (nR + tile_src - 1) / tile_src;
+    const uint32_t vbits = bits_for(g.n);
+    SearchArgs a{};
+    a.row_ptr = g.row_ptr;
+    a.adj = reinterpret_cast<const uint2 *>(g.adj);
+    a.iperm = g.iperm;
+    a.sbits = sbits;
+    a.src = rsorted;
+    a.bound = theta;
+    a.delta = std::max<uint32_t>(1, 4 * median_w);
+    a.slab = slab;
+    a.vbits = vbits;
+    a.tile_src = tile_src;
+    a.ctl = ctl;
+    a.out_key = keyA;
+    a.out_d = valA;
+    a.out_cap = NA_MAX_PAIRS;
+    a.ntiles = ntiles;
+    a.H = SMEM_H;
+    a.hshift = 32 - bits_for(SMEM_H);
+    a.max_fill = SMEM_H * 7 / 8;
+    a.failed = failed;
+    if (ntiles) search(T, Shape::Narrow, a, std::min(ntiles, NA_BLOCKS), st);
+    Control c;
+    RN_CUDA(cudaMemcpyAsync(&c, ctl, sizeof(Control), cudaMemcpyDeviceToHost, st));
+    RN_CUDA(cudaStreamSynchronize(st));
+    if (c.n_failed && !c.err) {
+        // wide blocks: the slab holds NA_BLOCKS / 2 regions of SMEM_HW rows
+        RN_CUDA(cudaMemsetAsync(&ctl->tile_next, 0, 8, st));
+        SearchArgs r = a;
+        r.tile_list = failed;
+        r.ntiles = c.n_failed;
+        r.failed = failed2;
+        r.H = SMEM_HW;
+        r.hshift = 32 - bits_for(SMEM_HW);
+        r.max_fill = SMEM_HW * 7 / 8;
+        search(T, Shape::Wide, r, std::min<uint32_t>(c.n_failed, NA_BLOCKS / 2), st);
+        RN_CUDA(cudaMemcpyAsync(&c, ctl, sizeof(Control), cudaMemcpyDeviceToHost, st));
+        RN_CUDA(cudaStreamSynchronize(st));
+        if (c.n_failed) fail(RN_EINVAL, "a tile's search outgrew the no-alloc slab: use rn_distance_join_dev");
+    }
+    if (c.err & 1u) fail(RN_EINVAL, "a node id of R or S is >= n");
+    if (c.err & 2u) fail(RN_EINVAL, "R or S repeats an id, or R and S overlap");
+    *n_out = c.pairs;
+    if (c.pairs > NA_MAX_PAIRS) fail(RN_EINVAL, "the join has more than 2^19 pairs, the no-alloc limit");
+    if (c.pairs > out_cap) fail(RN_EINVAL, "the output buffers hold fewer entries than the join's pairs");
+    if (c.pairs) {
+        const uint64_t np = c.pairs;
+        const uint32_t rb = uint32_t((np + RS_TILE - 1) / RS_TILE);
+        unsigned long long *ki = keyA, *ko = keyB;
+        uint32_t *vi = valA, *vo = valB;
+        for (uint32_t sh = 0; sh < 2 * vbits; sh += 8) {
+            const bool last = sh + 8 >= 2 * vbits;
+            k_rs_hist<<<rb, RS_THREADS, 0, st>>>(ki, vi, np, int(sh), hist, rb);
+            k_rs_scan<<<1, 1024, 0, st>>>(hist, rb * 256);
+            k_rs_scatter<<<rb, RS_THREADS, 0, st>>>(ki, vi, ko, vo, np, int(sh), hist, rb, last ? out_u : nullptr,
+                                                    last ? out_v : nullptr, last ? out_d : nullptr, vbits);
+            std::swap(ki, ko);
+            std::swap(vi, vo);
+        }
+        RN_CUDA(cudaGetLastError());
+        RN_CUDA(cudaStreamSynchronize(st));
+    }
+}
+
 void run_kcp(const DeviceGraph &, Workspace *, const EngineConfig &, uint32_t, const uint32_t *,
              uint32_t, const uint32_t *, uint32_t, uint64_t, uint32_t, rn_dpairs *, void *,
              rn_query_stats *) {

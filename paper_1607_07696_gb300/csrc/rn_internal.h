@@ -76,6 +76,11 @@ void run_kcp(const DeviceGraph &g, Workspace *ws, const EngineConfig &cfg, uint3
              const uint32_t *dR, uint32_t nR, const uint32_t *dS, uint32_t nS, uint64_t k,
              uint32_t theta, rn_dpairs *out, void *stream, rn_query_stats *stats);
 
+// The join with every scratch buffer in one static device array (no allocation).
+void run_join_noalloc(const DeviceGraph &g, uint32_t median_w, const uint32_t *dR, uint32_t nR,
+                      const uint32_t *dS, uint32_t nS, uint32_t theta, uint32_t *out_u, uint32_t *out_v,
+                      uint32_t *out_d, uint64_t out_cap, uint64_t *n_out, void *stream);
+
 void upload_graph(const HostGraph &g, const std::vector<uint32_t> &perm,
                   const std::vector<uint32_t> &iperm, DeviceGraph *out);
 void free_graph(DeviceGraph *g);

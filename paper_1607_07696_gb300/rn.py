@@ -81,6 +81,9 @@ SIGNATURES = {
                                    C.POINTER(rn_pairs)]),
     "rn_distance_join_dev": (C.c_int, [_G, C.c_void_p, C.c_uint32, C.c_void_p, C.c_uint32,
                                        C.c_uint32, C.POINTER(rn_dpairs), C.c_void_p]),
+    "rn_distance_join_noalloc": (C.c_int, [_G, C.c_void_p, C.c_uint32, C.c_void_p, C.c_uint32,
+                                           C.c_uint32, C.c_void_p, C.c_void_p, C.c_void_p,
+                                           C.c_uint64, C.POINTER(C.c_uint64), C.c_void_p]),
     "rn_kcp": (C.c_int, [_G, _P32, C.c_uint32, _P32, C.c_uint32, C.c_uint64, C.c_uint32,
                          C.POINTER(rn_pairs)]),
     "rn_kcp_dev": (C.c_int, [_G, C.c_void_p, C.c_uint32, C.c_void_p, C.c_uint32, C.c_uint64,
@@ -276,6 +279,19 @@ def rn_distance_join_dev(g: Graph, dR, dS, theta: int, out: DevicePairs, stream=
     _check(lib().rn_distance_join_dev(g.handle, _dev_ptr(dR), dR.numel(), _dev_ptr(dS), dS.numel(),
                                       int(theta), C.byref(out.s), _stream_ptr(stream)))
     return out.n
+
+
+def rn_distance_join_noalloc(g: Graph, dR, dS, theta: int, out_u, out_v, out_d, stream=None) -> int:
+    """The join into caller-owned device tensors (out_u/out_v/out_d, equal lengths), with no
+    allocation by the library; returns the pair count."""
+    n = C.c_uint64(0)
+    cap = out_u.numel()
+    if out_v.numel() != cap or out_d.numel() != cap:
+        raise ValueError("output tensors differ in length")
+    _check(lib().rn_distance_join_noalloc(g.handle, _dev_ptr(dR), dR.numel(), _dev_ptr(dS), dS.numel(),
+                                          int(theta), _dev_ptr(out_u), _dev_ptr(out_v), _dev_ptr(out_d),
+                                          cap, C.byref(n), _stream_ptr(stream)))
+    return int(n.value)
 
 
 def rn_kcp_dev(g: Graph, dR, dS, k: int, theta: int, out: DevicePairs, stream=None) -> int:
