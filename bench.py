@@ -146,7 +146,11 @@ def graph_digest(e) -> dict:
 
 
 def engine_hash() -> str:
-    return hashlib.sha256(open(ENGINE_SRC, "rb").read()).hexdigest()[:16]
+    """Hash of the tile-search section of the engine source (the profiled kernel)."""
+    src = open(ENGINE_SRC).read()
+    a = src.index("// ------------------------------------------------------------ tile search ----")
+    b = src.index("// ------------------------------------------------------------- radix sort ----")
+    return hashlib.sha256(src[a:b].encode()).hexdigest()[:16]
 
 
 def profiled_traffic(workload: str):
