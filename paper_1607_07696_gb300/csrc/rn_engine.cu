@@ -25,6 +25,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <cmath>
 #include <cstdio>
 #include <cstring>
 #include <mutex>
@@ -173,6 +174,7 @@ struct Workspace {
     size_t slab_bytes = 0;
     uint32_t slab_ctas = 0;
     uint32_t *gretry = nullptr;  // global maps and slabs of the largest retries
+    uint32_t *kcp = nullptr;     // k closest pairs: histogram, live threshold, select state
     size_t gretry_bytes = 0;
     // raw pairs and radix-sort buffers
     unsigned long long *keyA = nullptr, *keyB = nullptr;
@@ -228,6 +230,7 @@ void workspace_destroy(Workspace *ws) {
     device_free(ws->ctl);
     device_free(ws->slab);
     device_free(ws->gretry);
+    device_free(ws->kcp);
     device_free(ws->keyA);
     device_free(ws->keyB);
     device_free(ws->valA);
@@ -363,7 +366,17 @@ struct SearchArgs {
     unsigned long long *out_key;
     uint32_t *out_d;
     uint64_t out_cap;
+    // k closest pairs (null for a join): a histogram of the distances of every pair
+    // emitted so far (bin = d >> hist_shift, KCP_BINS bins) and the live threshold, the
+    // least bin edge below which at least kcp_k pairs lie; each tile searches with
+    // min(bound, *theta_live)
+    uint32_t *kcp_hist;
+    uint32_t *theta_live;
+    unsigned long long kcp_k;
+    uint32_t hist_shift;
 };
+
+constexpr uint32_t KCP_BINS = 2048;
 
 template <int L>
 struct Row {
@@ -555,8 +568,8 @@ __global__ void __launch_bounds__(THREADS, (THREADS == NARROW ? CTAS_PER_SM : 1)
 
     const uint32_t tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     uint32_t *slab = a.slab + size_t(blockIdx.x) * a.H * T;
-    const uint32_t bound = a.bound;
     const uint64_t delta = a.delta;
+    __shared__ uint32_t s_bound;
     unsigned long long my_scans = 0, my_slots = 0, my_arcs = 0;
     unsigned long long c_rounds = 0, c_items = 0, c_bounds = 0, c_arcs = 0;
     unsigned long long y_stepA = 0, y_stepB = 0, y_bound = 0, y_emit = 0;
@@ -580,6 +593,7 @@ __global__ void __launch_bounds__(THREADS, (THREADS == NARROW ? CTAS_PER_SM : 1)
             s_fill = 0;
             s_fail = 0;
             s_stop = 0;
+            s_bound = a.theta_live ? min(a.bound, __ldcg(a.theta_live)) : a.bound;
         }
         if (tid < T) src_orig[tid] = 0;
         __syncthreads();
@@ -587,6 +601,7 @@ __global__ void __launch_bounds__(THREADS, (THREADS == NARROW ? CTAS_PER_SM : 1)
         if (ti >= ntiles) break;
         const uint32_t tile = a.tile_list ? a.tile_list[ti] : ti;
         if (tile >= all_tiles) continue;  // defensive: never index past R
+        const uint32_t bound = s_bound;  // this tile's bound, the same for every thread
         const uint32_t first = tile * a.tile_src;
         const uint32_t tsz = min(a.tile_src, nR - first);
 
@@ -849,8 +864,39 @@ __global__ void __launch_bounds__(THREADS, (THREADS == NARROW ? CTAS_PER_SM : 1)
                                 a.out_key[idx] = (u << a.vbits) | v;
                                 a.out_d[idx] = r.x[q];
                             }
+                            if (a.kcp_hist) atomicAdd(&a.kcp_hist[r.x[q] >> a.hist_shift], 1u);
                         }
                         pos += __popc(bb);
+                    }
+                }
+            }
+            if (a.kcp_hist) {
+                // the tile's pairs are counted: lower the live threshold to the edge of
+                // the first bin where the pairs emitted so far reach k (they are exact,
+                // distinct pairs, so the k-th distance cannot lie above that edge)
+                __syncthreads();
+                if (warp == 0) {
+                    constexpr uint32_t PER = KCP_BINS / 32;
+                    unsigned long long own = 0;
+#pragma unroll 8
+                    for (uint32_t i = 0; i < PER; i++) own += __ldcg(&a.kcp_hist[lane * PER + i]);
+                    unsigned long long incl = own;
+                    for (int o = 1; o < 32; o <<= 1) {
+                        const unsigned long long t = __shfl_up_sync(FULL, incl, o);
+                        if (lane >= uint32_t(o)) incl += t;
+                    }
+                    const uint32_t reach = __ballot_sync(FULL, incl >= a.kcp_k);
+                    if (reach && lane == uint32_t(__ffs(reach) - 1)) {
+                        unsigned long long cum = incl - own;
+                        for (uint32_t i = 0; i < PER; i++) {
+                            cum += __ldcg(&a.kcp_hist[lane * PER + i]);
+                            if (cum >= a.kcp_k) {
+                                const unsigned long long edge =
+                                    ((unsigned long long)(lane * PER + i + 1) << a.hist_shift) - 1;
+                                atomicMin(a.theta_live, uint32_t(min(edge, 0xFFFFFFFFull)));
+                                break;
+                            }
+                        }
                     }
                 }
             }
@@ -923,37 +969,40 @@ __global__ void k_rs_hist(const unsigned long long *__restrict__ keys, const uin
     for (int d = threadIdx.x; d < 256; d += RS_THREADS) hist[uint64_t(d) * nblocks + blockIdx.x] = cnt[d];
 }
 
-// Exclusive scan of hist[0..total) in place, one block.
+// Exclusive scan of hist[0..total) in place, one block of 1024 threads: each warp owns a
+// contiguous chunk; it sums the chunk with coalesced loads, the block scans the 32 warp
+// sums, then each warp rewrites its chunk 32 entries at a time with a warp scan.
 __global__ void k_rs_scan(uint32_t *hist, uint32_t total) {
     __shared__ uint32_t warp_sum[32];
-    __shared__ uint32_t carry;
-    if (threadIdx.x == 0) carry = 0;
-    __syncthreads();
     const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    for (uint32_t base = 0; base < total; base += 1024) {
-        const uint32_t i = base + threadIdx.x;
-        const uint32_t v = i < total ? hist[i] : 0;
+    const uint32_t chunk = ((total + 31) / 32 + 31) & ~31u;  // multiple of 32
+    const uint32_t lo = min(total, warp * chunk), hi = min(total, lo + chunk);
+    uint32_t s = 0;
+#pragma unroll 8
+    for (uint32_t i = lo + lane; i < hi; i += 32) s += hist[i];
+    s = __reduce_add_sync(FULL, s);
+    if (lane == 0) warp_sum[warp] = s;
+    __syncthreads();
+    if (warp == 0) {
+        const uint32_t v = warp_sum[lane];
         uint32_t x = v;
         for (int o = 1; o < 32; o <<= 1) {
-            uint32_t t = __shfl_up_sync(FULL, x, o);
-            if (lane >= o) x += t;
+            const uint32_t t = __shfl_up_sync(FULL, x, o);
+            if (lane >= uint32_t(o)) x += t;
         }
-        if (lane == 31) warp_sum[warp] = x;
-        __syncthreads();
-        if (warp == 0) {
-            uint32_t s = warp_sum[lane], y = s;
-            for (int o = 1; o < 32; o <<= 1) {
-                uint32_t t = __shfl_up_sync(FULL, y, o);
-                if (lane >= o) y += t;
-            }
-            warp_sum[lane] = y - s;
+        warp_sum[lane] = x - v;
+    }
+    __syncthreads();
+    uint32_t carry = warp_sum[warp];
+    for (uint32_t i = lo; i < hi; i += 32) {
+        const uint32_t v = i + lane < hi ? hist[i + lane] : 0;
+        uint32_t x = v;
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t t = __shfl_up_sync(FULL, x, o);
+            if (lane >= uint32_t(o)) x += t;
         }
-        __syncthreads();
-        const uint32_t c = carry;
-        if (i < total) hist[i] = c + warp_sum[warp] + x - v;
-        __syncthreads();
-        if (threadIdx.x == 1023) carry = c + warp_sum[warp] + x;
-        __syncthreads();
+        if (i + lane < hi) hist[i + lane] = carry + x - v;
+        carry += __shfl_sync(FULL, x, 31);
     }
 }
 
@@ -1108,6 +1157,8 @@ static Control read_control(Workspace *ws, cudaStream_t st) {
 static Control search_all(const DeviceGraph &g, Workspace *ws, uint32_t T, SearchArgs a,
                           uint32_t ntiles, cudaStream_t st, uint64_t *retried) {
     const uint32_t grid_max = uint32_t(ws->num_sms) * CTAS_PER_SM;
+    if (ntiles && (!a.src || !a.slab || !a.sbits || !a.out_key || !a.out_d || !a.row_ptr || !a.adj || !a.ctl))
+        fail(RN_EINTERNAL, "tile search without its buffers");
     a.gmap = nullptr;
     a.tile_list = nullptr;
     a.ntiles = ntiles;
@@ -1303,6 +1354,7 @@ void run_join(const DeviceGraph &g, Workspace *ws, const EngineConfig &cfg, uint
         // the pair buffer was too small: grow it and search again (same result)
         ensure_pairs(ws, c.pairs + c.pairs / 8);
         prep_sets(g, ws, dR, nR, dS, nS, st);
+        a.src = ws->rsorted;
         a.out_key = ws->keyA;
         a.out_d = ws->valA;
         a.out_cap = ws->pair_cap;
@@ -1501,10 +1553,237 @@ void run_join_noalloc(const DeviceGraph &g, uint32_t median_w, const uint32_t *d
     }
 }
 
-void run_kcp(const DeviceGraph &, Workspace *, const EngineConfig &, uint32_t, const uint32_t *,
-             uint32_t, const uint32_t *, uint32_t, uint64_t, uint32_t, rn_dpairs *, void *,
-             rn_query_stats *) {
-    fail(RN_ENOTIMPL, "k closest pairs is not built yet");
+// ---------------------------------------------------------- k closest pairs ----
+// The answer is the first k of all pairs within theta in (d, u, v) order (Abstract;
+// Section 4; Algorithm 2 takes both k and theta).  The search runs in radius passes:
+// pass i searches every tile with bound tau_i, and inside a pass a global threshold --
+// the least histogram edge below which k exact pairs have been emitted (Algorithm 3's
+// global k-th distance) -- tightens the bound of every later tile.  A pass that ends
+// with fewer than k pairs was searched with tau_i everywhere, so its pairs are all the
+// pairs within tau_i: the next pass widens tau by the planar growth of the pair count
+// (pairs ~ tau^2).  Once k pairs exist, every pair with d <= the k-th distance is in
+// the candidates; a device radix select finds that distance, it is broadcast through
+// device memory to a compaction, and the survivors are sorted by (d, u, v).
+
+struct SelState {
+    uint32_t prefix;         // digits of the k-th value chosen so far
+    uint32_t pad;
+    unsigned long long krem; // rank of the k-th value among the candidates still matching
+};
+
+__global__ void k_set_u32(uint32_t *p, uint32_t v) { *p = v; }
+
+__global__ void k_sel_init(SelState *st, unsigned long long k) {
+    st->prefix = 0;
+    st->krem = k;
+}
+
+// Histogram of one 11/11/10-bit digit of the candidates whose higher digits equal the
+// prefix chosen so far.
+__global__ void k_sel_hist(const uint32_t *__restrict__ vals, uint64_t n, int shift, uint32_t nbits, uint32_t himask,
+                           const SelState *st, uint32_t *hist) {
+    __shared__ uint32_t h[2048];
+    for (uint32_t i = threadIdx.x; i < 2048; i += blockDim.x) h[i] = 0;
+    __syncthreads();
+    const uint32_t prefix = st->prefix;
+    const uint32_t dmask = (1u << nbits) - 1;
+    for (uint64_t i = uint64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += uint64_t(gridDim.x) * blockDim.x) {
+        const uint32_t v = vals[i];
+        if ((v & himask) == prefix) atomicAdd(&h[(v >> shift) & dmask], 1u);
+    }
+    __syncthreads();
+    for (uint32_t i = threadIdx.x; i < (1u << nbits); i += blockDim.x)
+        if (h[i]) atomicAdd(&hist[i], h[i]);
+}
+
+// One warp: the digit whose bin holds the krem-th candidate; clears the histogram.
+__global__ void k_sel_pick(uint32_t *hist, uint32_t nbits, int shift, SelState *st) {
+    const uint32_t lane = threadIdx.x;
+    const uint32_t nb = 1u << nbits, per = nb / 32;
+    unsigned long long own = 0;
+    for (uint32_t i = 0; i < per; i++) own += hist[lane * per + i];
+    unsigned long long incl = own;
+    for (int o = 1; o < 32; o <<= 1) {
+        const unsigned long long t = __shfl_up_sync(FULL, incl, o);
+        if (lane >= uint32_t(o)) incl += t;
+    }
+    const unsigned long long krem = st->krem;
+    const uint32_t reach = __ballot_sync(FULL, incl >= krem);
+    const uint32_t who = reach ? uint32_t(__ffs(reach) - 1) : 31u;
+    if (lane == who) {
+        unsigned long long cum = incl - own;
+        uint32_t b = lane * per + per - 1;
+        for (uint32_t i = 0; i < per; i++) {
+            const uint32_t c = hist[lane * per + i];
+            if (cum + c >= krem) {
+                b = lane * per + i;
+                break;
+            }
+            cum += c;
+        }
+        st->prefix |= b << shift;
+        st->krem = krem - cum;
+    }
+    __syncwarp();
+    for (uint32_t i = lane; i < nb; i += 32) hist[i] = 0;
+}
+
+// Keep the candidates with d <= the selected threshold (ties included).
+__global__ void k_compact_le(const unsigned long long *__restrict__ kin, const uint32_t *__restrict__ vin,
+                             uint64_t n, const SelState *st, unsigned long long *kout, uint32_t *vout,
+                             unsigned long long *count) {
+    const uint32_t theta = st->prefix;
+    const uint32_t lane = threadIdx.x & 31;
+    for (uint64_t base = (uint64_t(blockIdx.x) * blockDim.x + threadIdx.x) & ~31ull; base < n;
+         base += uint64_t(gridDim.x) * blockDim.x) {
+        const uint64_t i = base + lane;
+        const bool keep = i < n && vin[i] <= theta;
+        const uint32_t b = __ballot_sync(FULL, keep);
+        if (!b) continue;
+        unsigned long long pos = 0;
+        if (lane == 0) pos = atomicAdd(count, (unsigned long long)__popc(b));
+        pos = __shfl_sync(FULL, pos, 0);
+        if (keep) {
+            const unsigned long long at = pos + __popc(b & ((1u << lane) - 1));
+            kout[at] = kin[i];
+            vout[at] = vin[i];
+        }
+    }
+}
+
+void run_kcp(const DeviceGraph &g, Workspace *ws, const EngineConfig &cfg, uint32_t median_w, const uint32_t *dR,
+             uint32_t nR, const uint32_t *dS, uint32_t nS, uint64_t k, uint32_t theta, rn_dpairs *out, void *stream,
+             rn_query_stats *stats) {
+    cudaStream_t st = (cudaStream_t)stream;
+    if (k == 0) fail(RN_EINVAL, "k must be >= 1");
+    if (theta == RN_INF) theta = RN_THETA_MAX;
+    if (theta > RN_THETA_MAX) fail(RN_EINVAL, "theta must be <= 2^31 or RN_INF");
+    const uint32_t T = cfg.tile_width ? cfg.tile_width : 32;
+    if (T != 32 && T != 64 && T != 128) fail(RN_EINVAL, "tile width must be 32, 64 or 128");
+    const uint32_t delta = choose_delta(cfg, median_w);
+    *stats = rn_query_stats{};
+    stats->tile_width = T;
+    stats->delta = delta;
+    ws->launches = 0;
+    RN_CUDA(cudaEventRecord(ws->ev0, st));
+
+    const uint32_t grid_max = uint32_t(ws->num_sms) * CTAS_PER_SM;
+    uint32_t tile_src = T;
+    if (nR) {
+        const uint64_t waves = (uint64_t(nR) + uint64_t(T) * grid_max - 1) / (uint64_t(T) * grid_max);
+        tile_src = uint32_t(std::min<uint64_t>(T, (nR + waves * grid_max - 1) / (waves * grid_max)));
+        if (cfg.tile_src) tile_src = std::min(cfg.tile_src, T);
+    }
+    const uint32_t ntiles = (nR + tile_src - 1) / tile_src;
+    ensure_u32(&ws->failed, &ws->failed_cap, std::max<uint32_t>(ntiles, 1));
+    ensure_u32(&ws->failed2, &ws->failed2_cap, std::max<uint32_t>(ntiles, 1));
+    ensure_slab(ws);
+    ensure_pairs(ws, std::max<uint64_t>(ws->pair_cap, std::min<uint64_t>(k + (k >> 2) + 4096, uint64_t(nR) * 64 + 4096)));
+    if (!ws->kcp) {
+        ws->kcp = (uint32_t *)device_alloc((KCP_BINS + 16) * 4 + sizeof(SelState));
+        ws->bytes += (KCP_BINS + 16) * 4 + sizeof(SelState);
+    }
+    uint32_t *hist = ws->kcp, *theta_live = ws->kcp + KCP_BINS;
+    SelState *sel = reinterpret_cast<SelState *>(ws->kcp + KCP_BINS + 16);
+
+    const uint32_t vbits = bits_for(g.n);
+    SearchArgs a{};
+    a.row_ptr = g.row_ptr;
+    a.adj = reinterpret_cast<const uint2 *>(g.adj);
+    a.iperm = g.iperm;
+    a.sbits = ws->sbits;
+    a.delta = delta;
+    a.slab = ws->slab;
+    a.vbits = vbits;
+    a.tile_src = tile_src;
+    a.ctl = ws->ctl;
+    a.kcp_hist = hist;
+    a.theta_live = theta_live;
+    a.kcp_k = k;
+    uint64_t tau = std::min<uint64_t>(theta, delta);
+    uint64_t retried = 0;
+    uint32_t passes = 0;
+    Control c{};
+    unsigned long long scans = 0;
+    for (;;) {
+        prep_sets(g, ws, dR, nR, dS, nS, st);
+        a.src = ws->rsorted;  // prep_sets may have (re)allocated the R list
+        RN_CUDA(cudaMemsetAsync(hist, 0, KCP_BINS * 4, st));
+        k_set_u32<<<1, 1, 0, st>>>(theta_live, uint32_t(tau));
+        ws->launches++;
+        uint32_t shift = 0;
+        while ((tau >> shift) >= KCP_BINS) shift++;
+        a.bound = uint32_t(tau);
+        a.hist_shift = shift;
+        a.out_key = ws->keyA;
+        a.out_d = ws->valA;
+        a.out_cap = ws->pair_cap;
+        c = search_all(g, ws, T, a, ntiles, st, &retried);
+        check_control(c);
+        if (c.pairs > ws->pair_cap) {  // the candidate buffer was too small: same pass again
+            ensure_pairs(ws, c.pairs + c.pairs / 4);
+            continue;
+        }
+        passes++;
+        scans += c.scans;
+        if (c.pairs >= k || tau >= theta) break;
+        // widen: pairs grow about as tau^2 on a road network
+        double f = c.pairs ? std::sqrt(double(k) / double(c.pairs)) * 1.25 : 4.0;
+        f = std::max(f, 1.5);
+        tau = std::min<uint64_t>(theta, uint64_t(double(tau) * f) + 1);
+    }
+    const uint64_t m = c.pairs;
+    uint64_t kept = m;
+    uint32_t theta_k = uint32_t(tau);
+    if (m > k) {
+        // device radix select of the k-th distance (11 + 11 + 10 bits), then broadcast
+        // through device memory to the compaction
+        k_sel_init<<<1, 1, 0, st>>>(sel, k);
+        RN_CUDA(cudaMemsetAsync(hist, 0, KCP_BINS * 4, st));
+        const uint32_t grid = std::min<uint64_t>((m + 255) / 256, uint64_t(ws->num_sms) * 8);
+        const int shifts[3] = {21, 10, 0};
+        const uint32_t nbits[3] = {11, 11, 10};
+        const uint32_t himask[3] = {0u, 0xFFE00000u, 0xFFFFFC00u};
+        for (int r = 0; r < 3; r++) {
+            k_sel_hist<<<grid, 256, 0, st>>>(ws->valA, m, shifts[r], nbits[r], himask[r], sel, hist);
+            k_sel_pick<<<1, 32, 0, st>>>(hist, nbits[r], shifts[r], sel);
+        }
+        RN_CUDA(cudaMemsetAsync(&ws->ctl->pairs, 0, 8, st));
+        k_compact_le<<<grid, 256, 0, st>>>(ws->keyA, ws->valA, m, sel, ws->keyB, ws->valB, &ws->ctl->pairs);
+        ws->launches += 1 + 6 + 1;
+        RN_CUDA(cudaGetLastError());
+        SelState hs{};
+        RN_CUDA(cudaMemcpyAsync(&hs, sel, sizeof(hs), cudaMemcpyDeviceToHost, st));
+        c = read_control(ws, st);
+        kept = c.pairs;
+        theta_k = hs.prefix;
+        std::swap(ws->keyA, ws->keyB);
+        std::swap(ws->valA, ws->valB);
+    }
+    // canonical (d, u, v) order: (u, v) digits first, then the distance digits
+    dpairs_reserve(out, kept);
+    std::vector<int> shifts;
+    for (uint32_t sh = 0; sh < 2 * vbits; sh += 8) shifts.push_back(int(sh));
+    const uint32_t dbits = bits_for(theta_k + 1);
+    for (uint32_t sh = 0; sh < dbits; sh += 8) shifts.push_back(64 + int(sh));
+    radix_sort_to_pairs(ws, kept, shifts, vbits, out, st);
+    out->n = std::min<uint64_t>(k, kept);
+    RN_CUDA(cudaEventRecord(ws->ev1, st));
+    RN_CUDA(cudaEventSynchronize(ws->ev1));
+    float ms = 0, sms = 0;
+    RN_CUDA(cudaEventElapsedTime(&ms, ws->ev0, ws->ev1));
+    RN_CUDA(cudaEventElapsedTime(&sms, ws->evs0, ws->evs1));
+    stats->pairs = out->n;
+    stats->tiles = ntiles;
+    stats->tile_sources = tile_src;
+    stats->retried_tiles = retried;
+    stats->scans = scans;
+    stats->passes = passes;
+    stats->theta_final = m >= k ? theta_k : uint32_t(tau);
+    stats->launches = ws->launches;
+    stats->blocks_per_sm = uint32_t(ws->blocks_per_sm);
+    stats->device_ms = ms;
+    stats->search_ms = sms;
 }
 
 }  // namespace rn
