@@ -28,8 +28,8 @@
  *     rn_pairs_free.  Results in rn_dpairs are device memory owned by the library:
  *     free with rn_dpairs_free (a struct may be reused across calls; its buffers grow
  *     as needed).
- *   - A graph serialises the queries issued on it (an internal mutex); queries on
- *     different graphs may run concurrently from different host threads.
+ *   - Queries may be issued from any host thread; those on one device run one at a
+ *     time (they share the device's search slab).
  */
 #ifndef RN_H
 #define RN_H
@@ -218,6 +218,65 @@ rn_status rn_kcp(const rn_graph *g, const uint32_t *R, uint32_t nR, const uint32
                  uint32_t nS, uint64_t k, uint32_t theta, rn_pairs *out);
 rn_status rn_kcp_dev(const rn_graph *g, const uint32_t *dR, uint32_t nR, const uint32_t *dS,
                      uint32_t nS, uint64_t k, uint32_t theta, rn_dpairs *out, rn_stream stream);
+
+/* ------------------------------------------------------------------ batches ---- */
+
+/* One theta-join of a batch.  R and S are host arrays and g a loaded graph, read only by
+ * rn_batch_create (or rn_join_batch), which copies what it needs: the batch holds no
+ * reference to them afterwards.  All graphs of a batch live on the current device. */
+typedef struct {
+    const rn_graph *g;
+    const uint32_t *R;
+    uint32_t nR;
+    const uint32_t *S;
+    uint32_t nS;
+    uint32_t theta;
+} rn_query;
+
+typedef struct rn_batch rn_batch;
+
+typedef struct {
+    uint32_t autotune;  /* 1: before the first run, time every candidate plan (tile width,
+                           bucket width, block shape) on the batch and keep, per size class
+                           of instance (log2 n, log2 |R|), the one with the least SM cycles;
+                           plans are remembered for later batches of the process */
+    uint32_t use_graph; /* 1: after the first (eager) run, capture the whole batch in a CUDA
+                           graph and replay it on later runs */
+} rn_batch_config;
+
+typedef struct {
+    uint32_t instances, groups;  /* groups: launches of one block shape and tile width */
+    uint64_t tiles, retried_tiles, pairs;
+    uint32_t eager_runs, graph_runs, launches_per_run, tuned, candidates;
+    double device_ms;            /* last run, CUDA events on the batch's stream */
+} rn_batch_stats;
+
+/*
+ * rn_batch_create -- upload nq theta-joins (each as rn_distance_join, Section 4) for
+ * batched execution.  The graphs are copied into one disjoint union on the device (node
+ * ids shifted per instance), every instance's sources are padded to whole tiles, and the
+ * (instance, source tile) work items are searched by one persistent launch per tile
+ * width and block shape, each tile with its instance's theta; all pairs are sorted at
+ * once, which groups them by instance in (u, v) order.  cfg may be NULL (no autotuning,
+ * CUDA graph on).  RN_EINVAL for a bad query (the message names its index), graphs on
+ * other devices, or more than 2^32 - 2 nodes or arcs in all; RN_ENOMEM if device memory
+ * runs out.
+ */
+rn_status rn_batch_create(const rn_query *q, uint32_t nq, const rn_batch_config *cfg, rn_batch **out);
+/* Run every query of the batch; returns when all pairs are in device memory.  Work is
+ * ordered after prior work of `stream` (which may be NULL) and `stream` waits for it. */
+rn_status rn_batch_run(rn_batch *b, rn_stream stream);
+/* Instance i's pairs of the last run, sorted by (u, v): a library-owned host copy. */
+rn_status rn_batch_pairs(const rn_batch *b, uint32_t i, rn_pairs *out);
+/* Instance i's pairs of the last run as device pointers owned by the batch (valid until
+ * the next rn_batch_run or rn_batch_free). */
+rn_status rn_batch_pairs_dev(const rn_batch *b, uint32_t i, const uint32_t **u, const uint32_t **v,
+                             const uint32_t **d, uint64_t *n);
+rn_status rn_batch_stats_get(const rn_batch *b, rn_batch_stats *out);
+void rn_batch_free(rn_batch *b);
+/* One call: create a batch (no autotuning), run it once, copy every instance's pairs to
+ * outs[0..nq) (free each with rn_pairs_free), free the batch. */
+rn_status rn_join_batch(const rn_query *q, uint32_t nq, rn_pairs *outs);
 
 void rn_pairs_free(rn_pairs *p);
 void rn_dpairs_free(rn_dpairs *p);

@@ -71,6 +71,26 @@ def main() -> None:
                                   "k": [100, 10_000, 1_000_000], "graph": graph_digest(w.graph)}
     print("road1070k_clustered theta", th, f"{time.time() - t0:.1f}s", flush=True)
 
+    # the batch: theta per instance for its target matches per R node (32 sampled R);
+    # an instance whose sampled sources reach fewer S nodes than the target gets the
+    # largest distance its samples reached
+    thetas, digests = [], []
+    for sp in I.c4_batch_specs():
+        e, R, S = I.c4_instance(sp)
+        g = o.graph(e.n, e.src, e.dst, e.w)
+        t = max(1, int(round(sp.matches)))
+        ds, far = [], 0
+        for u in list(R[:32]):
+            p = g.kcp([int(u)], S, t)
+            if len(p):
+                far = max(far, int(p.d[-1]))
+            if len(p) == t:
+                ds.append(int(p.d[-1]))
+        thetas.append(int(np.median(ds)) if ds else far)
+        digests.append(graph_digest(e)["wsum"])
+    out["batch512"] = {"theta": thetas, "sample": 32, "graph_wsum": digests}
+    print("batch512", len(thetas), f"{time.time() - t0:.1f}s", flush=True)
+
     os.makedirs(os.path.dirname(OUT), exist_ok=True)
     old = json.load(open(OUT)) if os.path.exists(OUT) else {}
     old.update(out)

@@ -339,6 +339,128 @@ rn_status rn_kcp(const rn_graph *cg, const uint32_t *R, uint32_t nR, const uint3
     });
 }
 
+struct rn_batch {
+    rn::Batch *b = nullptr;
+    rn_batch_config cfg{0, 1};
+    bool tuned = false;
+};
+
+static rn::Batch *make_batch(const rn_query *q, uint32_t nq) {
+    if (!q && nq) rn::fail(RN_EINVAL, "null queries");
+    if (nq == 0) rn::fail(RN_EINVAL, "empty batch");
+    int cur = -1;
+    cudaGetDevice(&cur);
+    std::vector<const rn::DeviceGraph *> graphs(nq);
+    std::vector<const std::vector<uint32_t> *> perms(nq);
+    std::vector<uint32_t> med(nq), nR(nq), nS(nq), theta(nq);
+    std::vector<const uint32_t *> R(nq), S(nq);
+    for (uint32_t i = 0; i < nq; i++) {
+        const rn_query &x = q[i];
+        if (!x.g) rn::fail(RN_EINVAL, "query " + std::to_string(i) + " has no graph");
+        if (x.g->device != cur) rn::fail(RN_EINVAL, "query " + std::to_string(i) + "'s graph is on another device");
+        check_theta(x.theta);
+        try {
+            check_sets_host(x.g->dev.n, x.R, x.nR, x.S, x.nS);
+        } catch (const rn::Error &e) {
+            rn::fail(e.status, "query " + std::to_string(i) + ": " + e.msg);
+        }
+        graphs[i] = &x.g->dev;
+        perms[i] = &x.g->perm;
+        med[i] = x.g->info.median_weight;
+        R[i] = x.R;
+        S[i] = x.S;
+        nR[i] = x.nR;
+        nS[i] = x.nS;
+        theta[i] = x.theta;
+    }
+    return rn::batch_create(graphs, perms, med, R, nR, S, nS, theta);
+}
+
+rn_status rn_batch_create(const rn_query *q, uint32_t nq, const rn_batch_config *cfg, rn_batch **out) {
+    return guarded([&] {
+        if (!out) rn::fail(RN_EINVAL, "null output");
+        *out = nullptr;
+        auto h = std::make_unique<rn_batch>();
+        if (cfg) h->cfg = *cfg;
+        h->b = make_batch(q, nq);
+        *out = h.release();
+    });
+}
+
+rn_status rn_batch_run(rn_batch *h, rn_stream stream) {
+    return guarded([&] {
+        if (!h || !h->b) rn::fail(RN_EINVAL, "null batch");
+        if (h->cfg.autotune && !h->tuned) {
+            rn::batch_tune(h->b);
+            h->tuned = true;
+        }
+        rn::batch_run(h->b, (void *)stream, h->cfg.use_graph != 0);
+    });
+}
+
+rn_status rn_batch_pairs_dev(const rn_batch *h, uint32_t i, const uint32_t **u, const uint32_t **v,
+                             const uint32_t **d, uint64_t *n) {
+    return guarded([&] {
+        if (!h || !h->b || !u || !v || !d || !n) rn::fail(RN_EINVAL, "null argument");
+        rn::batch_pairs_dev(h->b, i, u, v, d, n);
+    });
+}
+
+rn_status rn_batch_pairs(const rn_batch *h, uint32_t i, rn_pairs *out) {
+    return guarded([&] {
+        if (!h || !h->b || !out) rn::fail(RN_EINVAL, "null argument");
+        *out = rn_pairs{};
+        const uint32_t *u, *v, *d;
+        uint64_t n = 0;
+        rn::batch_pairs_dev(h->b, i, &u, &v, &d, &n);
+        rn_dpairs view{const_cast<uint32_t *>(u), const_cast<uint32_t *>(v), const_cast<uint32_t *>(d), n, n};
+        to_host_pairs(view, out, nullptr);
+    });
+}
+
+rn_status rn_batch_stats_get(const rn_batch *h, rn_batch_stats *out) {
+    return guarded([&] {
+        if (!h || !h->b || !out) rn::fail(RN_EINVAL, "null argument");
+        *out = rn::batch_stats(h->b);
+    });
+}
+
+void rn_batch_free(rn_batch *h) {
+    if (!h) return;
+    try {
+        rn::batch_destroy(h->b);
+    } catch (...) {
+    }
+    delete h;
+}
+
+rn_status rn_join_batch(const rn_query *q, uint32_t nq, rn_pairs *outs) {
+    return guarded([&] {
+        if (!outs) rn::fail(RN_EINVAL, "null output");
+        for (uint32_t i = 0; i < nq; i++) outs[i] = rn_pairs{};
+        rn_batch h;
+        h.cfg.use_graph = 0;
+        h.b = make_batch(q, nq);
+        try {
+            rn::batch_run(h.b, nullptr, false);
+            for (uint32_t i = 0; i < nq; i++) {
+                const uint32_t *u, *v, *d;
+                uint64_t n = 0;
+                rn::batch_pairs_dev(h.b, i, &u, &v, &d, &n);
+                rn_dpairs view{const_cast<uint32_t *>(u), const_cast<uint32_t *>(v), const_cast<uint32_t *>(d), n, n};
+                to_host_pairs(view, &outs[i], nullptr);
+            }
+        } catch (...) {
+            for (uint32_t i = 0; i < nq; i++) rn_pairs_free(&outs[i]);
+            rn::batch_destroy(h.b);
+            h.b = nullptr;
+            throw;
+        }
+        rn::batch_destroy(h.b);
+        h.b = nullptr;
+    });
+}
+
 void rn_pairs_free(rn_pairs *p) {
     if (!p) return;
     std::free(p->u);

@@ -28,8 +28,10 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <map>
 #include <mutex>
 #include <string>
+#include <tuple>
 
 #include "rn_internal.h"
 
@@ -112,6 +114,9 @@ void upload_graph(const HostGraph &g, const std::vector<uint32_t> &perm,
         if (d.arcs) RN_CUDA(cudaMemcpy(d.adj, adj.data(), d.arcs * 8, cudaMemcpyHostToDevice));
         RN_CUDA(cudaMemcpy(d.perm, perm.data(), size_t(g.n) * 4, cudaMemcpyHostToDevice));
         RN_CUDA(cudaMemcpy(d.iperm, iperm.data(), size_t(g.n) * 4, cudaMemcpyHostToDevice));
+        // a copy from pageable memory may still be in flight when cudaMemcpy returns, and
+        // queries run on streams that do not wait for the legacy stream
+        RN_CUDA(cudaDeviceSynchronize());
     } catch (...) {
         free_graph(&d);
         throw;
@@ -144,7 +149,16 @@ struct Control {
     unsigned long long rounds, round_items, boundaries;
     unsigned long long cyc_round, cyc_bound, cyc_emit;
     unsigned long long cyc_stepA, round_arcs;
+    uint32_t check[4];  // first failed device-side check of the batch path: code, index, value
 };
+
+// Record the first failed device-side check (the access it guarded is skipped).
+__device__ __forceinline__ void record_check(Control *ctl, uint32_t code, uint32_t index, uint32_t value) {
+    if (atomicCAS(&ctl->check[0], 0u, code) == 0u) {
+        ctl->check[1] = index;
+        ctl->check[2] = value;
+    }
+}
 
 // Two block shapes: NARROW blocks (512 threads, an 8192-slot shared map, two blocks per
 // SM) search every tile first; WIDE blocks (1024 threads, a 16384-slot map, one block
@@ -158,6 +172,19 @@ constexpr int CTAS_PER_SM = 2;         // narrow blocks resident per SM
 __host__ __device__ constexpr uint32_t qcap_of(int threads) { return 2u * threads; }
 __host__ __device__ constexpr uint32_t icap_of(int threads) { return 3u * threads / 4; }
 
+// Per device: the slab of the persistent search (one region of SMEM_H rows of the widest
+// tile per resident narrow block) and the buffer of the global-map retries.  Every graph
+// on the device shares them, so queries on one device run one at a time (mu).
+struct DeviceShared {
+    std::mutex mu;
+    uint32_t *slab = nullptr;
+    size_t slab_bytes = 0;
+    uint32_t slab_ctas = 0;
+    uint32_t *gretry = nullptr;
+    size_t gretry_bytes = 0;
+};
+static DeviceShared g_shared[64];
+
 struct Workspace {
     uint32_t n = 0, nwords = 0;
     int num_sms = 0;
@@ -169,11 +196,7 @@ struct Workspace {
     uint32_t failed_cap = 0, failed2_cap = 0;
     Control *ctl = nullptr;
     Control *ctl_host = nullptr;  // pinned
-    // slab of the persistent search: one region of SMEM_H rows per block, per width
-    uint32_t *slab = nullptr;
-    size_t slab_bytes = 0;
-    uint32_t slab_ctas = 0;
-    uint32_t *gretry = nullptr;  // global maps and slabs of the largest retries
+    struct DeviceShared *sh = nullptr;  // the device's slab, shared by every graph on it
     uint32_t *kcp = nullptr;     // k closest pairs: histogram, live threshold, select state
     size_t gretry_bytes = 0;
     // raw pairs and radix-sort buffers
@@ -199,6 +222,8 @@ Workspace *workspace_create(const DeviceGraph &g) {
         int dev = 0;
         RN_CUDA(cudaGetDevice(&dev));
         RN_CUDA(cudaDeviceGetAttribute(&ws->num_sms, cudaDevAttrMultiProcessorCount, dev));
+        if (dev < 0 || dev >= 64) fail(RN_EINVAL, "device ordinal out of range");
+        ws->sh = &g_shared[dev];
         ws->n = g.n;
         ws->nwords = (g.n + 31) / 32;
         ws_alloc(ws, (void **)&ws->used_bits, size_t(ws->nwords) * 4);
@@ -228,8 +253,6 @@ void workspace_destroy(Workspace *ws) {
     device_free(ws->failed);
     device_free(ws->failed2);
     device_free(ws->ctl);
-    device_free(ws->slab);
-    device_free(ws->gretry);
     device_free(ws->kcp);
     device_free(ws->keyA);
     device_free(ws->keyB);
@@ -374,6 +397,28 @@ struct SearchArgs {
     uint32_t *theta_live;
     unsigned long long kcp_k;
     uint32_t hist_shift;
+    // batch (null for a single query): the graph is the disjoint union of the batch's
+    // graphs and tile t belongs to instance tile_inst[t], searched with bound
+    // tile_bound[t] and bucket width tile_delta[t]; nR_fixed (non-zero) gives the
+    // number of sources instead of the control block; per-instance pair counts and SM
+    // cycles (for the autotuner) are added to inst_pairs / inst_cycles
+    const uint32_t *tile_bound;
+    const uint32_t *tile_delta;
+    const uint32_t *tile_inst;
+    uint32_t nR_fixed;
+    unsigned long long *inst_pairs;
+    unsigned long long *inst_cycles;
+};
+
+// What a block needs to know about the tile it searches.
+struct TileCtx {
+    const uint32_t *row_ptr;
+    const uint2 *adj;
+    const uint32_t *iperm;
+    const uint32_t *sbits;
+    const uint32_t *src;
+    unsigned long long key_prefix;
+    uint32_t local, nR, tile_src, bound, delta, inst;
 };
 
 constexpr uint32_t KCP_BINS = 2048;
@@ -568,17 +613,21 @@ __global__ void __launch_bounds__(THREADS, (THREADS == NARROW ? CTAS_PER_SM : 1)
 
     const uint32_t tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     uint32_t *slab = a.slab + size_t(blockIdx.x) * a.H * T;
-    const uint64_t delta = a.delta;
-    __shared__ uint32_t s_bound;
-    unsigned long long my_scans = 0, my_slots = 0, my_arcs = 0;
-    unsigned long long c_rounds = 0, c_items = 0, c_bounds = 0, c_arcs = 0;
-    unsigned long long y_stepA = 0, y_stepB = 0, y_bound = 0, y_emit = 0;
-    long long t_mark = clock64();
+    __shared__ TileCtx s_cx;
+    uint32_t my_scans = 0, my_slots = 0, my_arcs = 0;
+    // telemetry, kept by thread 0 in shared memory: rounds, round items, boundaries,
+    // round arcs, cycles in step A, step B, boundaries, emission; clock marks
+    enum { T_ROUNDS, T_ITEMS, T_BOUNDS, T_ARCS, T_STEPA, T_STEPB, T_BOUND, T_EMIT, T_N };
+    __shared__ unsigned long long s_tel[T_N];
+    __shared__ long long s_mark, s_tile0;
+    if (tid < T_N) s_tel[tid] = 0;
+    if (tid == 0) s_mark = clock64();
 
     if (__ldcg(&a.ctl->err)) return;
-    const uint32_t nR = __ldcg(&a.ctl->r_count);
-    const uint32_t all_tiles = (nR + a.tile_src - 1) / a.tile_src;
+    const uint32_t nR1 = a.nR_fixed ? a.nR_fixed : __ldcg(&a.ctl->r_count);  // sources
+    const uint32_t all_tiles = (nR1 + a.tile_src - 1) / a.tile_src;
     const uint32_t ntiles = a.tile_list ? a.ntiles : all_tiles;
+
 
     for (;;) {
         if (tid == 0) s_tile = atomicAdd(&a.ctl->tile_next, 1u);
@@ -593,7 +642,6 @@ __global__ void __launch_bounds__(THREADS, (THREADS == NARROW ? CTAS_PER_SM : 1)
             s_fill = 0;
             s_fail = 0;
             s_stop = 0;
-            s_bound = a.theta_live ? min(a.bound, __ldcg(a.theta_live)) : a.bound;
         }
         if (tid < T) src_orig[tid] = 0;
         __syncthreads();
@@ -601,14 +649,36 @@ __global__ void __launch_bounds__(THREADS, (THREADS == NARROW ? CTAS_PER_SM : 1)
         if (ti >= ntiles) break;
         const uint32_t tile = a.tile_list ? a.tile_list[ti] : ti;
         if (tile >= all_tiles) continue;  // defensive: never index past R
-        const uint32_t bound = s_bound;  // this tile's bound, the same for every thread
-        const uint32_t first = tile * a.tile_src;
-        const uint32_t tsz = min(a.tile_src, nR - first);
+        if (tid == 0) {
+            TileCtx c;
+            c.row_ptr = a.row_ptr;
+            c.adj = a.adj;
+            c.iperm = a.iperm;
+            c.sbits = a.sbits;
+            c.src = a.src;
+            c.nR = nR1;
+            c.tile_src = a.tile_src;
+            c.bound = a.tile_bound ? a.tile_bound[tile]
+                                   : (a.theta_live ? min(a.bound, __ldcg(a.theta_live)) : a.bound);
+            c.delta = a.tile_delta ? a.tile_delta[tile] : a.delta;
+            c.local = tile;
+            c.inst = a.tile_inst ? a.tile_inst[tile] : 0u;
+            c.key_prefix = 0;
+            s_cx = c;
+            s_tile0 = clock64();
+        }
+        __syncthreads();
+        const uint32_t *row_ptr = s_cx.row_ptr;
+        const uint2 *adj = s_cx.adj;
+        const uint32_t bound = s_cx.bound;  // this tile's bound, the same for every thread
+        const uint64_t delta = s_cx.delta;
+        const uint32_t first = s_cx.local * s_cx.tile_src;
+        const uint32_t tsz = min(s_cx.tile_src, s_cx.nR - first);
 
         // sources: lane t of every row belongs to R node first + t, at distance 0
         if (tid < tsz) {
-            const uint32_t y = a.src[first + tid];
-            src_orig[tid] = a.iperm[y];
+            const uint32_t y = s_cx.src[first + tid];
+            src_orig[tid] = s_cx.iperm[y];
             const uint32_t h = find_or_insert(hkeys, a.H, a.hshift, y, &s_fill, a.max_fill, &s_fail);
             __stcg(&slab[size_t(h) * T + tid], 0u);
             atomicOr(&dmask[h], 1u << (tid / L));
@@ -630,13 +700,13 @@ __global__ void __launch_bounds__(THREADS, (THREADS == NARROW ? CTAS_PER_SM : 1)
                 const uint32_t ncur = min(s_ncur, QCAP);
                 if (tid == 0) {
                     const long long t = clock64();
-                    y_bound += t - t_mark;
-                    t_mark = t;
+                    s_tel[T_BOUND] += t - s_mark;
+                    s_mark = t;
                 }
                 if (ncur == 0 || s_stop) break;
                 if (tid == 0) {
-                    c_rounds++;
-                    c_items += ncur;
+                    s_tel[T_ROUNDS]++;
+                    s_tel[T_ITEMS] += ncur;
                 }
                 for (uint32_t c0 = 0; c0 < ncur; c0 += ICAP) {
                     const uint32_t nc = min(ICAP, ncur - c0);
@@ -650,8 +720,8 @@ __global__ void __launch_bounds__(THREADS, (THREADS == NARROW ? CTAS_PER_SM : 1)
                         if (mask) {
                             my_scans++;
                             const uint32_t y0 = hkeys[x];
-                            beg = __ldg(&a.row_ptr[y0]);
-                            deg = __ldg(&a.row_ptr[y0 + 1]) - beg;
+                            beg = __ldg(&row_ptr[y0]);
+                            deg = __ldg(&row_ptr[y0 + 1]) - beg;
                             const uint32_t *xrow = slab + size_t(x) * T;
                             for (uint32_t m = mask; m;) {
                                 Row<L> r[G];
@@ -682,9 +752,9 @@ __global__ void __launch_bounds__(THREADS, (THREADS == NARROW ? CTAS_PER_SM : 1)
                     __syncthreads();
                     if (tid == 0) {
                         const long long t = clock64();
-                        y_stepA += t - t_mark;
-                        t_mark = t;
-                        c_arcs += total;
+                        s_tel[T_STEPA] += t - s_mark;
+                        s_mark = t;
+                        s_tel[T_ARCS] += total;
                     }
                     // -- step B: one thread per arc of the staged items, two arcs in flight
                     // (warp-uniform trip count, so the ballots below see every lane)
@@ -705,7 +775,7 @@ __global__ void __launch_bounds__(THREADS, (THREADS == NARROW ? CTAS_PER_SM : 1)
                                 else hi = mid - 1;
                             }
                             item[u] = lo;
-                            const uint2 arc = __ldg(&a.adj[it_beg[lo] + (gi - it_off[lo])]);
+                            const uint2 arc = __ldg(&adj[it_beg[lo] + (gi - it_off[lo])]);
                             w[u] = arc.y;
                             hy[u] = arc.x;  // the head node until its slot is known
                         }
@@ -773,8 +843,8 @@ __global__ void __launch_bounds__(THREADS, (THREADS == NARROW ? CTAS_PER_SM : 1)
                     __syncthreads();
                     if (tid == 0) {
                         const long long t = clock64();
-                        y_stepB += t - t_mark;
-                        t_mark = t;
+                        s_tel[T_STEPB] += t - s_mark;
+                        s_mark = t;
                     }
                 }
                 if (tid == 0) {
@@ -790,7 +860,7 @@ __global__ void __launch_bounds__(THREADS, (THREADS == NARROW ? CTAS_PER_SM : 1)
             // ---- the near queue is empty: find the smallest pending priority
             if (tid == 0) {
                 s_minp = INF;
-                c_bounds++;
+                s_tel[T_BOUNDS]++;
             }
             __syncthreads();
             uint32_t mp = INF;
@@ -811,8 +881,8 @@ __global__ void __launch_bounds__(THREADS, (THREADS == NARROW ? CTAS_PER_SM : 1)
         __syncthreads();
         if (tid == 0) {
             const long long t = clock64();
-            y_bound += t - t_mark;
-            t_mark = t;
+            s_tel[T_BOUND] += t - s_mark;
+            s_mark = t;
         }
 
         // ---- emission: every slot of an S node, every lane within the bound.  Warps
@@ -823,7 +893,7 @@ __global__ void __launch_bounds__(THREADS, (THREADS == NARROW ? CTAS_PER_SM : 1)
             uint32_t cnt = 0;
             for (uint32_t c = warp * 32; c < a.H; c += SEARCH_WARPS * 32) {
                 const uint32_t yl = hkeys[c + lane];
-                const bool in_s = yl != EMPTY && ((__ldg(&a.sbits[yl >> 5]) >> (yl & 31)) & 1u);
+                const bool in_s = yl != EMPTY && ((__ldg(&s_cx.sbits[yl >> 5]) >> (yl & 31)) & 1u);
                 for (uint32_t b = __ballot_sync(FULL, in_s); b; b &= b - 1) {
                     const uint32_t h = c + __ffs(b) - 1;
                     const Row<L> r = load_row<L>(slab + size_t(h) * T + lane * L);
@@ -841,18 +911,19 @@ __global__ void __launch_bounds__(THREADS, (THREADS == NARROW ? CTAS_PER_SM : 1)
                     run += c;
                 }
                 s_base = atomicAdd(&a.ctl->pairs, (unsigned long long)run);
+                if (a.inst_pairs) atomicAdd(&a.inst_pairs[s_cx.inst], (unsigned long long)run);
             }
             __syncthreads();
             unsigned long long pos = s_base + s_warp[warp];
             for (uint32_t c = warp * 32; c < a.H; c += SEARCH_WARPS * 32) {
                 const uint32_t yl = hkeys[c + lane];
-                const bool in_s = yl != EMPTY && ((__ldg(&a.sbits[yl >> 5]) >> (yl & 31)) & 1u);
+                const bool in_s = yl != EMPTY && ((__ldg(&s_cx.sbits[yl >> 5]) >> (yl & 31)) & 1u);
                 for (uint32_t b = __ballot_sync(FULL, in_s); b; b &= b - 1) {
                     const uint32_t src_lane = __ffs(b) - 1;
                     const uint32_t h = c + src_lane;
                     const uint32_t y = __shfl_sync(FULL, yl, src_lane);
                     const Row<L> r = load_row<L>(slab + size_t(h) * T + lane * L);
-                    const unsigned long long v = __ldg(&a.iperm[y]);
+                    const unsigned long long v = __ldg(&s_cx.iperm[y]);
 #pragma unroll
                     for (int q = 0; q < L; q++) {
                         const bool hit = r.x[q] <= bound;
@@ -861,7 +932,7 @@ __global__ void __launch_bounds__(THREADS, (THREADS == NARROW ? CTAS_PER_SM : 1)
                             const unsigned long long idx = pos + __popc(bb & lt);
                             if (idx < a.out_cap) {
                                 const unsigned long long u = src_orig[lane * L + q];
-                                a.out_key[idx] = (u << a.vbits) | v;
+                                a.out_key[idx] = s_cx.key_prefix | (u << a.vbits) | v;
                                 a.out_d[idx] = r.x[q];
                             }
                             if (a.kcp_hist) atomicAdd(&a.kcp_hist[r.x[q] >> a.hist_shift], 1u);
@@ -909,7 +980,7 @@ __global__ void __launch_bounds__(THREADS, (THREADS == NARROW ? CTAS_PER_SM : 1)
             const bool used = yl != EMPTY;
             if (ok && used) {
                 my_slots++;
-                my_arcs += __ldg(&a.row_ptr[yl + 1]) - __ldg(&a.row_ptr[yl]);
+                my_arcs += __ldg(&row_ptr[yl + 1]) - __ldg(&row_ptr[yl]);
             }
             for (uint32_t b = __ballot_sync(FULL, used); b; b &= b - 1)
                 store_inf<L>(slab + size_t(c + __ffs(b) - 1) * T + lane * L);
@@ -917,27 +988,28 @@ __global__ void __launch_bounds__(THREADS, (THREADS == NARROW ? CTAS_PER_SM : 1)
         __syncthreads();
         if (tid == 0) {
             const long long t = clock64();
-            y_emit += t - t_mark;
-            t_mark = t;
+            s_tel[T_EMIT] += t - s_mark;
+            s_mark = t;
+            if (a.inst_cycles) atomicAdd(&a.inst_cycles[s_cx.inst], (unsigned long long)(t - s_tile0));
         }
     }
-    my_slots = __reduce_add_sync(FULL, uint32_t(my_slots));
-    my_arcs = __reduce_add_sync(FULL, uint32_t(my_arcs));
-    my_scans = __reduce_add_sync(FULL, uint32_t(my_scans));
+    my_slots = __reduce_add_sync(FULL, my_slots);
+    my_arcs = __reduce_add_sync(FULL, my_arcs);
+    my_scans = __reduce_add_sync(FULL, my_scans);
     if (lane == 0) {
-        atomicAdd(&a.ctl->scans, my_scans);
-        atomicAdd(&a.ctl->slots, my_slots);
-        atomicAdd(&a.ctl->slot_arcs, my_arcs);
+        atomicAdd(&a.ctl->scans, (unsigned long long)my_scans);
+        atomicAdd(&a.ctl->slots, (unsigned long long)my_slots);
+        atomicAdd(&a.ctl->slot_arcs, (unsigned long long)my_arcs);
     }
     if (tid == 0) {
-        atomicAdd(&a.ctl->rounds, c_rounds);
-        atomicAdd(&a.ctl->round_items, c_items);
-        atomicAdd(&a.ctl->boundaries, c_bounds);
-        atomicAdd(&a.ctl->cyc_round, y_stepA + y_stepB);
-        atomicAdd(&a.ctl->cyc_stepA, y_stepA);
-        atomicAdd(&a.ctl->round_arcs, c_arcs);
-        atomicAdd(&a.ctl->cyc_bound, y_bound);
-        atomicAdd(&a.ctl->cyc_emit, y_emit);
+        atomicAdd(&a.ctl->rounds, s_tel[T_ROUNDS]);
+        atomicAdd(&a.ctl->round_items, s_tel[T_ITEMS]);
+        atomicAdd(&a.ctl->boundaries, s_tel[T_BOUNDS]);
+        atomicAdd(&a.ctl->cyc_round, s_tel[T_STEPA] + s_tel[T_STEPB]);
+        atomicAdd(&a.ctl->cyc_stepA, s_tel[T_STEPA]);
+        atomicAdd(&a.ctl->round_arcs, s_tel[T_ARCS]);
+        atomicAdd(&a.ctl->cyc_bound, s_tel[T_BOUND]);
+        atomicAdd(&a.ctl->cyc_emit, s_tel[T_EMIT]);
     }
 }
 
@@ -1011,7 +1083,7 @@ __global__ void k_rs_scan(uint32_t *hist, uint32_t total) {
 __global__ void k_rs_scatter(const unsigned long long *__restrict__ kin, const uint32_t *__restrict__ vin,
                              unsigned long long *kout, uint32_t *vout, uint64_t n, int shift,
                              const uint32_t *__restrict__ hist, uint32_t nblocks, uint32_t *out_u,
-                             uint32_t *out_v, uint32_t *out_d, uint32_t vbits) {
+                             uint32_t *out_v, uint32_t *out_d, uint32_t vbits, uint32_t umask = 0xFFFFFFFFu) {
     __shared__ uint32_t wcnt[RS_WARPS][256];
     const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     for (int i = threadIdx.x; i < RS_WARPS * 256; i += RS_THREADS) (&wcnt[0][0])[i] = 0;
@@ -1050,7 +1122,7 @@ __global__ void k_rs_scatter(const unsigned long long *__restrict__ kin, const u
         if (dg[r] == 256u) continue;
         const uint64_t pos = uint64_t(hist[uint64_t(dg[r]) * nblocks + blockIdx.x]) + wcnt[warp][dg[r]] + rank[r];
         if (out_u) {
-            out_u[pos] = uint32_t(k[r] >> vbits);
+            out_u[pos] = uint32_t(k[r] >> vbits) & umask;
             out_v[pos] = uint32_t(k[r] & vmask);
             out_d[pos] = v[r];
         } else {
@@ -1155,21 +1227,24 @@ static Control read_control(Workspace *ws, cudaStream_t st) {
 // shared maps), then with global maps four times larger each time.  The map never
 // needs more than the next power of two >= 2n slots, where it cannot overflow.
 static Control search_all(const DeviceGraph &g, Workspace *ws, uint32_t T, SearchArgs a,
-                          uint32_t ntiles, cudaStream_t st, uint64_t *retried) {
+                          uint32_t ntiles, cudaStream_t st, uint64_t *retried, bool wide = false) {
     const uint32_t grid_max = uint32_t(ws->num_sms) * CTAS_PER_SM;
+    a.slab = ws->sh->slab;
     if (ntiles && (!a.src || !a.slab || !a.sbits || !a.out_key || !a.out_d || !a.row_ptr || !a.adj || !a.ctl))
         fail(RN_EINTERNAL, "tile search without its buffers");
     a.gmap = nullptr;
     a.tile_list = nullptr;
     a.ntiles = ntiles;
-    a.H = SMEM_H;
-    a.hshift = 32 - bits_for(SMEM_H);
-    a.max_fill = SMEM_H * 7 / 8;
+    const uint32_t H0 = wide ? SMEM_HW : SMEM_H;
+    a.H = H0;
+    a.hshift = 32 - bits_for(H0);
+    a.max_fill = H0 * 7 / 8;
     a.failed = ws->failed;
-    a.slab = ws->slab;
+    a.slab = ws->sh->slab;
     RN_CUDA(cudaEventRecord(ws->evs0, st));
     if (ntiles) {
-        search(T, Shape::Narrow, a, std::max<uint32_t>(1, std::min(ntiles, grid_max)), st);
+        if (wide) search(T, Shape::Wide, a, std::max<uint32_t>(1, std::min(ntiles, uint32_t(ws->num_sms))), st);
+        else search(T, Shape::Narrow, a, std::max<uint32_t>(1, std::min(ntiles, grid_max)), st);
         ws->launches++;
         ws->blocks_per_sm = T == 32 ? search_occupancy<1>() : T == 64 ? search_occupancy<2>() : search_occupancy<4>();
     }
@@ -1177,7 +1252,7 @@ static Control search_all(const DeviceGraph &g, Workspace *ws, uint32_t T, Searc
     Control c = read_control(ws, st);
     uint64_t hcap = 1;
     while (hcap < 2ull * g.n) hcap <<= 1;
-    uint64_t H = SMEM_H;
+    uint64_t H = H0;
     uint32_t *list = ws->failed, *next = ws->failed2;
     while (c.n_failed && !c.err) {
         if (H >= hcap) fail(RN_EINTERNAL, "slot map overflowed at its largest size");
@@ -1202,18 +1277,17 @@ static Control search_all(const DeviceGraph &g, Workspace *ws, uint32_t T, Searc
             const size_t budget = size_t(8) << 30;
             const uint32_t rgrid =
                 uint32_t(std::max<size_t>(1, std::min<size_t>({size_t(nf), size_t(ws->num_sms), budget / per_block})));
-            if (ws->gretry_bytes < per_block * rgrid) {
-                device_free(ws->gretry);
-                ws->gretry = nullptr;
-                ws->bytes -= ws->gretry_bytes;
-                ws->gretry_bytes = 0;
-                ws->gretry = (uint32_t *)device_alloc(per_block * rgrid);
-                ws->gretry_bytes = per_block * rgrid;
-                ws->bytes += ws->gretry_bytes;
+            DeviceShared *sh = ws->sh;
+            if (sh->gretry_bytes < per_block * rgrid) {
+                device_free(sh->gretry);
+                sh->gretry = nullptr;
+                sh->gretry_bytes = 0;
+                sh->gretry = (uint32_t *)device_alloc(per_block * rgrid);
+                sh->gretry_bytes = per_block * rgrid;
             }
-            RN_CUDA(cudaMemsetAsync(ws->gretry, 0xFF, per_block * rgrid, st));  // rows INF
-            r.gmap = ws->gretry;
-            r.slab = ws->gretry + size_t(rgrid) * 3 * H;
+            RN_CUDA(cudaMemsetAsync(sh->gretry, 0xFF, per_block * rgrid, st));  // rows INF
+            r.gmap = sh->gretry;
+            r.slab = sh->gretry + size_t(rgrid) * 3 * H;
             r.H = uint32_t(H);
             r.hshift = 32 - bits_for(uint32_t(H));
             r.max_fill = uint32_t(H * 7 / 8);
@@ -1261,15 +1335,15 @@ static void ensure_pairs(Workspace *ws, uint64_t want) {
 
 static void ensure_slab(Workspace *ws) {
     const uint32_t grid_max = uint32_t(ws->num_sms) * CTAS_PER_SM;
-    if (ws->slab && ws->slab_ctas >= grid_max) return;
-    device_free(ws->slab);
-    ws->slab = nullptr;
-    ws->bytes -= ws->slab_bytes;
-    ws->slab_bytes = size_t(SMEM_H) * 128 * 4 * grid_max;  // rows of the widest tile
-    ws->slab = (uint32_t *)device_alloc(ws->slab_bytes);
-    RN_CUDA(cudaMemset(ws->slab, 0xFF, ws->slab_bytes));  // every row INF
-    ws->slab_ctas = grid_max;
-    ws->bytes += ws->slab_bytes;
+    DeviceShared *sh = ws->sh;
+    if (sh->slab && sh->slab_ctas >= grid_max) return;
+    device_free(sh->slab);
+    sh->slab = nullptr;
+    sh->slab_bytes = size_t(SMEM_H) * 128 * 4 * grid_max;  // rows of the widest tile
+    sh->slab = (uint32_t *)device_alloc(sh->slab_bytes);
+    RN_CUDA(cudaMemset(sh->slab, 0xFF, sh->slab_bytes));  // every row INF
+    RN_CUDA(cudaDeviceSynchronize());  // before any search on a stream of its own
+    sh->slab_ctas = grid_max;
 }
 
 // a2: validate R and S on the device, build the S membership bitmap and the list of R
@@ -1295,6 +1369,9 @@ static void prep_sets(const DeviceGraph &g, Workspace *ws, const uint32_t *dR, u
 }
 
 static void check_control(const Control &c) {
+    if (c.check[0])
+        fail(RN_EINTERNAL, "device check " + std::to_string(c.check[0]) + " failed at index " +
+                               std::to_string(c.check[1]) + " (value " + std::to_string(c.check[2]) + ")");
     if (c.err & 1u) fail(RN_EINVAL, "a node id of R or S is >= n");
     if (c.err & 2u) fail(RN_EINVAL, "R or S repeats an id, or R and S overlap");
 }
@@ -1308,6 +1385,7 @@ void run_join(const DeviceGraph &g, Workspace *ws, const EngineConfig &cfg, uint
     const uint32_t T = cfg.tile_width ? cfg.tile_width : 32;
     if (T != 32 && T != 64 && T != 128) fail(RN_EINVAL, "tile width must be 32, 64 or 128");
     const uint32_t delta = choose_delta(cfg, median_w);
+    std::lock_guard<std::mutex> device_lock(ws->sh->mu);
     *stats = rn_query_stats{};
     stats->tile_width = T;
     stats->delta = delta;
@@ -1340,7 +1418,7 @@ void run_join(const DeviceGraph &g, Workspace *ws, const EngineConfig &cfg, uint
     a.src = ws->rsorted;
     a.bound = theta;
     a.delta = delta;
-    a.slab = ws->slab;
+    a.slab = ws->sh->slab;
     a.vbits = vbits;
     a.tile_src = tile_src;
     a.ctl = ws->ctl;
@@ -1661,6 +1739,7 @@ void run_kcp(const DeviceGraph &g, Workspace *ws, const EngineConfig &cfg, uint3
     const uint32_t T = cfg.tile_width ? cfg.tile_width : 32;
     if (T != 32 && T != 64 && T != 128) fail(RN_EINVAL, "tile width must be 32, 64 or 128");
     const uint32_t delta = choose_delta(cfg, median_w);
+    std::lock_guard<std::mutex> device_lock(ws->sh->mu);
     *stats = rn_query_stats{};
     stats->tile_width = T;
     stats->delta = delta;
@@ -1693,7 +1772,7 @@ void run_kcp(const DeviceGraph &g, Workspace *ws, const EngineConfig &cfg, uint3
     a.iperm = g.iperm;
     a.sbits = ws->sbits;
     a.delta = delta;
-    a.slab = ws->slab;
+    a.slab = ws->sh->slab;
     a.vbits = vbits;
     a.tile_src = tile_src;
     a.ctl = ws->ctl;
@@ -1785,5 +1864,526 @@ void run_kcp(const DeviceGraph &g, Workspace *ws, const EngineConfig &cfg, uint3
     stats->device_ms = ms;
     stats->search_ms = sms;
 }
+
+// ------------------------------------------------------------------- batch ----
+// Many independent theta-joins (their own graphs, sets and thetas) searched by one
+// persistent launch per block shape and tile width.  The batch's graphs are copied into
+// one disjoint union (node ids and arc positions shifted per instance, plus one
+// isolated pad node), so the search runs exactly as for a single query on that graph:
+// every instance's R list, in internal ids, is padded with the pad node to whole tiles,
+// and per-tile tables give each tile its instance's theta, bucket width and index.
+// Pairs are sorted by (u, v) in union ids, which puts every instance's pairs together in
+// (u, v) order; a last kernel shifts them back to the instance's own ids.  After a first
+// eager run fixes the counts, the run (clears, searches, sort) is captured in a CUDA
+// graph and replayed; a replay that does not reproduce the counts falls back to an
+// eager run.  An autotuner picks, per size class of instance, the tile width, the
+// bucket width and the block shape from per-instance SM cycles measured in the kernel.
+
+// Copy one instance's graph into the union: nodes shifted by node_off, arcs by arc_off.
+__global__ void k_union_graph(const uint32_t *__restrict__ row_ptr, const uint2 *__restrict__ adj,
+                              const uint32_t *__restrict__ iperm, uint32_t n, uint32_t arcs, uint32_t node_off,
+                              uint32_t arc_off, uint32_t *u_row_ptr, uint2 *u_adj, uint32_t *u_iperm) {
+    const uint32_t m = max(n, arcs);
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < m; i += gridDim.x * blockDim.x) {
+        if (i < n) {
+            u_row_ptr[node_off + i] = row_ptr[i] + arc_off;
+            u_iperm[node_off + i] = iperm[i] + node_off;
+        }
+        if (i < arcs) {
+            const uint2 e = adj[i];
+            u_adj[arc_off + i] = make_uint2(e.x + node_off, e.y);
+        }
+    }
+}
+
+// Shift every pair back to its instance's ids: pair p belongs to the instance i with
+// pair_off[i] <= p < pair_off[i+1].
+__global__ void k_localize(uint32_t *u, uint32_t *v, uint64_t n, const unsigned long long *__restrict__ pair_off,
+                           const uint32_t *__restrict__ node_off, uint32_t nq) {
+    for (uint64_t p = uint64_t(blockIdx.x) * blockDim.x + threadIdx.x; p < n; p += uint64_t(gridDim.x) * blockDim.x) {
+        uint32_t lo = 0, hi = nq - 1;
+        while (lo < hi) {
+            const uint32_t mid = (lo + hi + 1) >> 1;
+            if (pair_off[mid] <= p) lo = mid;
+            else hi = mid - 1;
+        }
+        u[p] -= node_off[lo];
+        v[p] -= node_off[lo];
+    }
+}
+
+namespace {
+
+struct BatchPlan {
+    uint32_t T = 32;
+    bool wide = false;
+    uint32_t delta_mult = 4;  // bucket width in median arc weights
+    uint32_t src_div = 1;     // sources per tile = T / src_div
+};
+
+// Size class of an instance for the autotuner: log2 of its node count and of |R|.
+uint32_t size_class(uint32_t n, uint32_t nR) { return (bits_for(n) << 8) | bits_for(std::max<uint32_t>(nR, 1)); }
+
+std::mutex g_tune_mu;
+std::map<uint32_t, BatchPlan> g_tune_cache;  // size class -> tuned plan, for the process
+
+}  // namespace
+
+struct Batch {
+    int device = 0;
+    uint32_t nq = 0, n_u = 0, pad = 0, vbits = 1;
+    uint64_t arcs_u = 0;
+    std::vector<uint32_t> n, nR, theta, median_w, cls, node_off;
+    std::vector<std::vector<uint32_t>> rint;  // per instance: R in union internal ids, ascending
+    std::vector<BatchPlan> plan;
+    DeviceGraph ug;  // the union graph (row_ptr, adj, iperm)
+    uint32_t *sbits = nullptr, *node_off_d = nullptr;
+    Workspace *ws = nullptr;  // control block, retry lists, events of the batch
+    cudaStream_t stream = nullptr;
+    unsigned long long *inst_pairs = nullptr, *inst_cycles = nullptr, *pair_off_d = nullptr;
+    struct Group {
+        uint32_t T = 32, tile_src = 32, nsrc = 0, tiles = 0;
+        bool wide = false;
+        uint32_t *src = nullptr, *tbound = nullptr, *tdelta = nullptr, *tinst = nullptr;
+    };
+    std::vector<Group> groups;
+    uint64_t pair_cap = 0;
+    unsigned long long *keyA = nullptr, *keyB = nullptr;
+    uint32_t *valA = nullptr, *valB = nullptr, *hist = nullptr;
+    size_t hist_cap = 0;
+    uint32_t *out_u = nullptr, *out_v = nullptr, *out_d = nullptr;
+    uint64_t out_cap = 0;
+    std::vector<uint64_t> cnt, off;  // per instance: pairs and their first index
+    uint64_t total = 0;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    uint64_t exec_pairs = 0;
+    rn_batch_stats stats{};
+};
+
+static void batch_drop_graph(Batch *b) {
+    if (b->exec) cudaGraphExecDestroy(b->exec);
+    if (b->graph) cudaGraphDestroy(b->graph);
+    b->exec = nullptr;
+    b->graph = nullptr;
+}
+
+static void batch_free_groups(Batch *b) {
+    for (auto &g : b->groups)
+        for (void *p : {(void *)g.src, (void *)g.tbound, (void *)g.tdelta, (void *)g.tinst}) device_free(p);
+    b->groups.clear();
+}
+
+void batch_destroy(Batch *b) {
+    if (!b) return;
+    batch_drop_graph(b);
+    batch_free_groups(b);
+    for (void *p : {(void *)b->sbits, (void *)b->node_off_d, (void *)b->inst_pairs, (void *)b->inst_cycles,
+                    (void *)b->pair_off_d, (void *)b->keyA, (void *)b->keyB, (void *)b->valA, (void *)b->valB,
+                    (void *)b->hist, (void *)b->out_u, (void *)b->out_v, (void *)b->out_d,
+                    (void *)b->ug.row_ptr, (void *)b->ug.adj, (void *)b->ug.iperm})
+        device_free(p);
+    if (b->stream) cudaStreamDestroy(b->stream);
+    workspace_destroy(b->ws);
+    delete b;
+}
+
+template <class T>
+static T *upload_vec(const std::vector<T> &v) {
+    T *p = (T *)device_alloc(std::max<size_t>(v.size(), 1) * sizeof(T));
+    if (!v.empty()) RN_CUDA(cudaMemcpy(p, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice));
+    return p;
+}
+
+// Group the instances by (tile width, block shape, sources per tile) and upload each
+// group's padded source list and per-tile tables.
+static void batch_layout(Batch *b) {
+    batch_drop_graph(b);
+    batch_free_groups(b);
+    std::map<std::tuple<uint32_t, bool, uint32_t>, std::vector<uint32_t>> by;
+    for (uint32_t i = 0; i < b->nq; i++)
+        by[std::make_tuple(b->plan[i].T, b->plan[i].wide, b->plan[i].src_div)].push_back(i);
+    uint64_t tiles = 0;
+    for (auto &kv : by) {
+        Batch::Group g;
+        g.T = std::get<0>(kv.first);
+        g.wide = std::get<1>(kv.first);
+        g.tile_src = std::max<uint32_t>(1, g.T / std::get<2>(kv.first));
+        std::vector<uint32_t> src, tb, td, ti;
+        for (uint32_t i : kv.second) {
+            const auto &r = b->rint[i];
+            const uint32_t nt = uint32_t((r.size() + g.tile_src - 1) / g.tile_src);
+            src.insert(src.end(), r.begin(), r.end());
+            src.resize(src.size() + size_t(nt) * g.tile_src - r.size(), b->pad);  // pad to whole tiles
+            const uint32_t delta = std::max<uint32_t>(1, b->plan[i].delta_mult * b->median_w[i]);
+            for (uint32_t t = 0; t < nt; t++) {
+                tb.push_back(b->theta[i]);
+                td.push_back(delta);
+                ti.push_back(i);
+            }
+        }
+        if (src.size() > 0xFFFFFFFFull) fail(RN_EINVAL, "batch too large: more than 2^32 - 1 sources");
+        // every tile lies inside one instance and every source inside the union
+        if (src.size() != size_t(tb.size()) * g.tile_src || td.size() != tb.size() || ti.size() != tb.size())
+            fail(RN_EINTERNAL, "batch layout: tile tables do not match the source list");
+        for (uint32_t x : src)
+            if (x >= b->n_u) fail(RN_EINTERNAL, "batch layout: source outside the union graph");
+        g.nsrc = uint32_t(src.size());
+        g.tiles = uint32_t(tb.size());
+        g.src = upload_vec(src);
+        g.tbound = upload_vec(tb);
+        g.tdelta = upload_vec(td);
+        g.tinst = upload_vec(ti);
+        tiles += g.tiles;
+        b->groups.push_back(g);
+    }
+    RN_CUDA(cudaDeviceSynchronize());  // the batch's stream does not wait for these copies
+    ensure_u32(&b->ws->failed, &b->ws->failed_cap, uint32_t(std::max<uint64_t>(tiles, 1)));
+    ensure_u32(&b->ws->failed2, &b->ws->failed2_cap, uint32_t(std::max<uint64_t>(tiles, 1)));
+    b->stats.tiles = tiles;
+    b->stats.groups = uint32_t(b->groups.size());
+}
+
+static void batch_reserve_pairs(Batch *b, uint64_t want) {
+    if (b->pair_cap >= want) return;
+    want = std::max<uint64_t>(want, 1 << 16);
+    for (void **p : {(void **)&b->keyA, (void **)&b->keyB, (void **)&b->valA, (void **)&b->valB}) {
+        device_free(*p);
+        *p = nullptr;
+    }
+    b->pair_cap = 0;
+    b->keyA = (unsigned long long *)device_alloc(want * 8);
+    b->keyB = (unsigned long long *)device_alloc(want * 8);
+    b->valA = (uint32_t *)device_alloc(want * 4);
+    b->valB = (uint32_t *)device_alloc(want * 4);
+    b->pair_cap = want;
+    batch_drop_graph(b);
+}
+
+static SearchArgs batch_args(Batch *b, const Batch::Group &g) {
+    SearchArgs a{};
+    a.row_ptr = b->ug.row_ptr;
+    a.adj = reinterpret_cast<const uint2 *>(b->ug.adj);
+    a.iperm = b->ug.iperm;
+    a.sbits = b->sbits;
+    a.src = g.src;
+    a.tile_src = g.tile_src;
+    a.nR_fixed = g.nsrc;
+    a.tile_bound = g.tbound;
+    a.tile_delta = g.tdelta;
+    a.tile_inst = g.tinst;
+    a.inst_pairs = b->inst_pairs;
+    a.inst_cycles = b->inst_cycles;
+    a.vbits = b->vbits;
+    a.ctl = b->ws->ctl;
+    a.out_key = b->keyA;
+    a.out_d = b->valA;
+    a.out_cap = b->pair_cap;
+    return a;
+}
+
+static void batch_clear(Batch *b, cudaStream_t st) {
+    RN_CUDA(cudaMemsetAsync(b->ws->ctl, 0, sizeof(Control), st));
+    RN_CUDA(cudaMemsetAsync(b->inst_pairs, 0, size_t(b->nq) * 8, st));
+    RN_CUDA(cudaMemsetAsync(b->inst_cycles, 0, size_t(b->nq) * 8, st));
+}
+
+// Sort `total` pairs by (u, v) into the result arrays and shift them to instance ids.
+static void batch_finish(Batch *b, uint64_t total, cudaStream_t st) {
+    if (!total) return;
+    if (total > 0xFFFFFFFFull) fail(RN_EINVAL, "more than 2^32 - 1 result pairs in the batch");
+    const uint32_t nblocks = uint32_t((total + RS_TILE - 1) / RS_TILE);
+    unsigned long long *ki = b->keyA, *ko = b->keyB;
+    uint32_t *vi = b->valA, *vo = b->valB;
+    for (uint32_t sh = 0; sh < 2 * b->vbits; sh += 8) {
+        const bool last = sh + 8 >= 2 * b->vbits;
+        k_rs_hist<<<nblocks, RS_THREADS, 0, st>>>(ki, vi, total, int(sh), b->hist, nblocks);
+        k_rs_scan<<<1, 1024, 0, st>>>(b->hist, nblocks * 256);
+        k_rs_scatter<<<nblocks, RS_THREADS, 0, st>>>(ki, vi, ko, vo, total, int(sh), b->hist, nblocks,
+                                                     last ? b->out_u : nullptr, last ? b->out_v : nullptr,
+                                                     last ? b->out_d : nullptr, b->vbits);
+        std::swap(ki, ko);
+        std::swap(vi, vo);
+    }
+    const uint32_t grid = uint32_t(std::min<uint64_t>((total + 255) / 256, uint64_t(b->ws->num_sms) * 8));
+    k_localize<<<grid, 256, 0, st>>>(b->out_u, b->out_v, total, b->pair_off_d, b->node_off_d, b->nq);
+    RN_CUDA(cudaGetLastError());
+}
+
+static void batch_counts(Batch *b, cudaStream_t st) {
+    std::vector<unsigned long long> c(b->nq);
+    RN_CUDA(cudaMemcpyAsync(c.data(), b->inst_pairs, size_t(b->nq) * 8, cudaMemcpyDeviceToHost, st));
+    RN_CUDA(cudaStreamSynchronize(st));
+    b->cnt.assign(c.begin(), c.end());
+    b->off.assign(b->nq + 1, 0);
+    for (uint32_t i = 0; i < b->nq; i++) b->off[i + 1] = b->off[i] + b->cnt[i];
+}
+
+// A full run with host checks between steps: retries of overflowed tiles, growth of
+// the pair buffer.  Returns the number of retried tiles.
+static uint64_t batch_run_eager(Batch *b, cudaStream_t st) {
+    for (;;) {
+        batch_clear(b, st);
+        uint64_t retried = 0;
+        Control c{};
+        for (const auto &g : b->groups) {
+            RN_CUDA(cudaMemsetAsync(&b->ws->ctl->tile_next, 0, 8, st));  // tile_next, n_failed
+            c = search_all(b->ug, b->ws, g.T, batch_args(b, g), g.tiles, st, &retried, g.wide);
+            check_control(c);
+        }
+        b->stats.retried_tiles = retried;
+        if (c.pairs > b->pair_cap) {
+            batch_reserve_pairs(b, c.pairs + c.pairs / 8);
+            continue;
+        }
+        b->total = c.pairs;
+        batch_counts(b, st);
+        if (b->off[b->nq] != b->total) fail(RN_EINTERNAL, "batch pair counts do not add up");
+        if (b->out_cap < b->total) {
+            for (void **p : {(void **)&b->out_u, (void **)&b->out_v, (void **)&b->out_d}) {
+                device_free(*p);
+                *p = nullptr;
+            }
+            b->out_cap = std::max<uint64_t>(b->total, 1024);
+            b->out_u = (uint32_t *)device_alloc(b->out_cap * 4);
+            b->out_v = (uint32_t *)device_alloc(b->out_cap * 4);
+            b->out_d = (uint32_t *)device_alloc(b->out_cap * 4);
+            batch_drop_graph(b);
+        }
+        const uint32_t nblocks = uint32_t((b->total + RS_TILE - 1) / RS_TILE);
+        if (b->hist_cap < uint64_t(nblocks) * 256 + 256) {
+            device_free(b->hist);
+            b->hist = nullptr;
+            b->hist_cap = uint64_t(nblocks) * 256 + 256;
+            b->hist = (uint32_t *)device_alloc(b->hist_cap * 4);
+            batch_drop_graph(b);
+        }
+        std::vector<unsigned long long> po(b->off.begin(), b->off.end());
+        RN_CUDA(cudaMemcpyAsync(b->pair_off_d, po.data(), po.size() * 8, cudaMemcpyHostToDevice, st));
+        batch_finish(b, b->total, st);
+        RN_CUDA(cudaStreamSynchronize(st));  // po is a host temporary
+        b->stats.eager_runs++;
+        return retried;
+    }
+}
+
+// The capturable sequence: clears, one launch per group, sort and shift.
+static void batch_record(Batch *b, cudaStream_t st) {
+    batch_clear(b, st);
+    const uint32_t grid_max = uint32_t(b->ws->num_sms) * CTAS_PER_SM;
+    for (const auto &g : b->groups) {
+        RN_CUDA(cudaMemsetAsync(&b->ws->ctl->tile_next, 0, 8, st));
+        SearchArgs a = batch_args(b, g);
+        a.slab = b->ws->sh->slab;
+        a.failed = b->ws->failed;
+        a.ntiles = g.tiles;
+        const uint32_t H = g.wide ? SMEM_HW : SMEM_H;
+        a.H = H;
+        a.hshift = 32 - bits_for(H);
+        a.max_fill = H * 7 / 8;
+        const uint32_t grid = std::max<uint32_t>(1, std::min(g.tiles, g.wide ? uint32_t(b->ws->num_sms) : grid_max));
+        if (g.tiles) search(g.T, g.wide ? Shape::Wide : Shape::Narrow, a, grid, st);
+    }
+    batch_finish(b, b->exec_pairs, st);
+}
+
+// One run: a graph replay when the last eager run needed no retries, else eager.
+void batch_run(Batch *b, void *user_stream, bool use_graph) {
+    std::lock_guard<std::mutex> device_lock(b->ws->sh->mu);
+    cudaStream_t st = b->stream;
+    if (user_stream) {
+        RN_CUDA(cudaEventRecord(b->ws->ev0, (cudaStream_t)user_stream));
+        RN_CUDA(cudaStreamWaitEvent(st, b->ws->ev0, 0));
+    }
+    ensure_slab(b->ws);
+    RN_CUDA(cudaEventRecord(b->ws->ev0, st));
+    bool done = false;
+    if (use_graph && b->exec) {
+        RN_CUDA(cudaGraphLaunch(b->exec, st));
+        const Control c = read_control(b->ws, st);
+        b->stats.graph_runs++;
+        if (!c.err && !c.n_failed && c.pairs == b->exec_pairs) {
+            b->total = c.pairs;
+            done = true;
+        } else {
+            batch_drop_graph(b);  // the replay did not reproduce the eager run: run eagerly
+        }
+    }
+    if (!done) {
+        b->ws->launches = 0;
+        const uint64_t retried = batch_run_eager(b, st);
+        const uint32_t passes = (2 * b->vbits + 7) / 8;
+        b->stats.launches_per_run = b->ws->launches + 3 * passes + 1;
+        if (use_graph && !retried && !b->exec) {
+            b->exec_pairs = b->total;
+            RN_CUDA(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+            try {
+                batch_record(b, st);
+            } catch (...) {
+                cudaGraph_t g = nullptr;
+                cudaStreamEndCapture(st, &g);
+                if (g) cudaGraphDestroy(g);
+                throw;
+            }
+            RN_CUDA(cudaStreamEndCapture(st, &b->graph));
+            RN_CUDA(cudaGraphInstantiate(&b->exec, b->graph, 0));
+        }
+    }
+    RN_CUDA(cudaEventRecord(b->ws->ev1, st));
+    RN_CUDA(cudaEventSynchronize(b->ws->ev1));
+    float ms = 0;
+    RN_CUDA(cudaEventElapsedTime(&ms, b->ws->ev0, b->ws->ev1));
+    b->stats.device_ms = ms;
+    b->stats.pairs = b->total;
+    if (user_stream) {
+        RN_CUDA(cudaEventRecord(b->ws->ev1, st));
+        RN_CUDA(cudaStreamWaitEvent((cudaStream_t)user_stream, b->ws->ev1, 0));
+    }
+}
+
+// Autotuner: run the whole batch once per candidate plan, read every instance's SM
+// cycles, and give each size class the candidate with the least total cycles.
+void batch_tune(Batch *b) {
+    static const BatchPlan cands[] = {
+        {32, false, 2, 1}, {32, false, 4, 1}, {32, false, 8, 1}, {32, false, 4, 2},
+        {32, true, 4, 1},  {64, false, 4, 1}, {64, true, 4, 1},  {128, true, 4, 1},
+    };
+    const size_t nc = sizeof(cands) / sizeof(cands[0]);
+    std::map<uint32_t, std::vector<double>> cost;  // class -> cost per candidate
+    {
+        std::lock_guard<std::mutex> device_lock(b->ws->sh->mu);
+        ensure_slab(b->ws);
+        for (size_t c = 0; c < nc; c++) {
+            for (uint32_t i = 0; i < b->nq; i++) b->plan[i] = cands[c];
+            batch_layout(b);
+            batch_run_eager(b, b->stream);
+            std::vector<unsigned long long> cyc(b->nq);
+            RN_CUDA(cudaMemcpy(cyc.data(), b->inst_cycles, size_t(b->nq) * 8, cudaMemcpyDeviceToHost));
+            for (uint32_t i = 0; i < b->nq; i++) {
+                auto &v = cost[b->cls[i]];
+                if (v.empty()) v.assign(nc, 0.0);
+                v[c] += double(cyc[i]);
+            }
+        }
+    }
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    for (auto &kv : cost) {
+        size_t best = 0;
+        for (size_t c = 1; c < nc; c++)
+            if (kv.second[c] < kv.second[best]) best = c;
+        g_tune_cache[kv.first] = cands[best];
+    }
+    for (uint32_t i = 0; i < b->nq; i++) b->plan[i] = g_tune_cache[b->cls[i]];
+    batch_layout(b);
+    b->stats.tuned = 1;
+    b->stats.candidates = uint32_t(nc);
+}
+
+Batch *batch_create(const std::vector<const DeviceGraph *> &graphs, const std::vector<const std::vector<uint32_t> *> &perms,
+                    const std::vector<uint32_t> &median_w, const std::vector<const uint32_t *> &R,
+                    const std::vector<uint32_t> &nR, const std::vector<const uint32_t *> &S,
+                    const std::vector<uint32_t> &nS, const std::vector<uint32_t> &theta) {
+    Batch *b = new Batch();
+    try {
+        b->nq = uint32_t(graphs.size());
+        RN_CUDA(cudaGetDevice(&b->device));
+        b->nR = nR;
+        b->median_w = median_w;
+        b->n.resize(b->nq);
+        b->theta.resize(b->nq);
+        b->cls.resize(b->nq);
+        b->node_off.assign(b->nq + 1, 0);
+        b->plan.assign(b->nq, BatchPlan{});
+        uint64_t nsum = 0, asum = 0;
+        for (uint32_t i = 0; i < b->nq; i++) {
+            b->n[i] = graphs[i]->n;
+            b->theta[i] = theta[i] == RN_INF ? RN_THETA_MAX : theta[i];
+            if (b->theta[i] > RN_THETA_MAX) fail(RN_EINVAL, "theta must be <= 2^31 or RN_INF");
+            b->cls[i] = size_class(b->n[i], nR[i]);
+            b->node_off[i] = uint32_t(nsum);
+            nsum += graphs[i]->n;
+            asum += graphs[i]->arcs;
+            if (nsum + 1 >= 0xFFFFFFFFull || asum >= 0xFFFFFFFFull)
+                fail(RN_EINVAL, "batch too large: more than 2^32 - 2 nodes or arcs in all");
+        }
+        b->node_off[b->nq] = uint32_t(nsum);
+        b->pad = uint32_t(nsum);
+        b->n_u = uint32_t(nsum + 1);
+        b->arcs_u = asum;
+        b->vbits = bits_for(b->n_u);
+        {
+            std::lock_guard<std::mutex> lk(g_tune_mu);
+            for (uint32_t i = 0; i < b->nq; i++) {
+                auto it = g_tune_cache.find(b->cls[i]);
+                if (it != g_tune_cache.end()) b->plan[i] = it->second;
+            }
+        }
+        DeviceGraph capg{};
+        capg.n = b->n_u;
+        b->ws = workspace_create(capg);
+        RN_CUDA(cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking));
+        // the union graph
+        b->ug.n = b->n_u;
+        b->ug.arcs = asum;
+        b->ug.row_ptr = (uint32_t *)device_alloc((size_t(b->n_u) + 1) * 4);
+        b->ug.adj = (uint32_t *)device_alloc(std::max<uint64_t>(asum, 1) * 8);
+        b->ug.iperm = (uint32_t *)device_alloc(size_t(b->n_u) * 4);
+        uint64_t aoff = 0;
+        for (uint32_t i = 0; i < b->nq; i++) {
+            const DeviceGraph &g = *graphs[i];
+            const uint32_t m = std::max<uint32_t>(g.n, uint32_t(g.arcs));
+            const uint32_t grid = std::max<uint32_t>(1, std::min<uint32_t>((m + 255) / 256, 1024));
+            k_union_graph<<<grid, 256, 0, b->stream>>>(g.row_ptr, reinterpret_cast<const uint2 *>(g.adj), g.iperm, g.n,
+                                                        uint32_t(g.arcs), b->node_off[i], uint32_t(aoff), b->ug.row_ptr,
+                                                        reinterpret_cast<uint2 *>(b->ug.adj), b->ug.iperm);
+            aoff += g.arcs;
+        }
+        RN_CUDA(cudaGetLastError());
+        const uint32_t tail_rp[2] = {uint32_t(asum), uint32_t(asum)};  // the pad node: no arcs
+        RN_CUDA(cudaMemcpyAsync(b->ug.row_ptr + b->pad, tail_rp, 8, cudaMemcpyHostToDevice, b->stream));
+        RN_CUDA(cudaMemcpyAsync(b->ug.iperm + b->pad, &b->pad, 4, cudaMemcpyHostToDevice, b->stream));
+        RN_CUDA(cudaStreamSynchronize(b->stream));
+        // sets, in union internal ids: R lists (sorted, per instance) and the S bitmap
+        std::vector<uint32_t> sb((b->n_u + 31) / 32, 0);
+        b->rint.resize(b->nq);
+        for (uint32_t i = 0; i < b->nq; i++) {
+            const std::vector<uint32_t> &perm = *perms[i];
+            auto &r = b->rint[i];
+            r.resize(nR[i]);
+            for (uint32_t j = 0; j < nR[i]; j++) r[j] = perm[R[i][j]] + b->node_off[i];
+            std::sort(r.begin(), r.end());
+            for (uint32_t j = 0; j < nS[i]; j++) {
+                const uint32_t x = perm[S[i][j]] + b->node_off[i];
+                sb[x >> 5] |= 1u << (x & 31);
+            }
+        }
+        b->sbits = upload_vec(sb);
+        b->node_off_d = upload_vec(b->node_off);
+        b->inst_pairs = (unsigned long long *)device_alloc(size_t(b->nq) * 8);
+        b->inst_cycles = (unsigned long long *)device_alloc(size_t(b->nq) * 8);
+        b->pair_off_d = (unsigned long long *)device_alloc((size_t(b->nq) + 1) * 8);
+        uint64_t totR = 0;
+        for (uint32_t x : nR) totR += x;
+        batch_reserve_pairs(b, std::max<uint64_t>(totR * 64, 1 << 16));
+        b->stats.instances = b->nq;
+        batch_layout(b);
+    } catch (...) {
+        batch_destroy(b);
+        throw;
+    }
+    return b;
+}
+
+void batch_pairs_dev(const Batch *b, uint32_t i, const uint32_t **u, const uint32_t **v, const uint32_t **d,
+                     uint64_t *n) {
+    if (i >= b->nq) fail(RN_EINVAL, "instance index out of range");
+    if (b->cnt.empty()) fail(RN_EINVAL, "the batch has not run yet");
+    *n = b->cnt[i];
+    *u = b->out_u + b->off[i];
+    *v = b->out_v + b->off[i];
+    *d = b->out_d + b->off[i];
+}
+
+const rn_batch_stats &batch_stats(const Batch *b) { return b->stats; }
 
 }  // namespace rn

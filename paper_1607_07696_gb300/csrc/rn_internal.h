@@ -81,6 +81,21 @@ void run_join_noalloc(const DeviceGraph &g, uint32_t median_w, const uint32_t *d
                       const uint32_t *dS, uint32_t nS, uint32_t theta, uint32_t *out_u, uint32_t *out_v,
                       uint32_t *out_d, uint64_t out_cap, uint64_t *n_out, void *stream);
 
+// Batches of joins (rn_engine.cu).
+struct Batch;
+// graphs[i] with host permutation perms[i] (original -> internal id); R and S host
+// arrays already validated.
+Batch *batch_create(const std::vector<const DeviceGraph *> &graphs, const std::vector<const std::vector<uint32_t> *> &perms,
+                    const std::vector<uint32_t> &median_w, const std::vector<const uint32_t *> &R,
+                    const std::vector<uint32_t> &nR, const std::vector<const uint32_t *> &S,
+                    const std::vector<uint32_t> &nS, const std::vector<uint32_t> &theta);
+void batch_tune(Batch *b);
+void batch_run(Batch *b, void *stream, bool use_graph);
+void batch_pairs_dev(const Batch *b, uint32_t i, const uint32_t **u, const uint32_t **v, const uint32_t **d,
+                     uint64_t *n);
+const rn_batch_stats &batch_stats(const Batch *b);
+void batch_destroy(Batch *b);
+
 void upload_graph(const HostGraph &g, const std::vector<uint32_t> &perm,
                   const std::vector<uint32_t> &iperm, DeviceGraph *out);
 void free_graph(DeviceGraph *g);

@@ -272,3 +272,37 @@ def c3_road_clustered(theta: int | None = None, k: int | None = None,
 
 def log_uniform(rng: np.random.Generator, lo: float, hi: float, size=None):
     return np.exp(rng.uniform(math.log(lo), math.log(hi), size=size))
+
+
+@dataclass
+class BatchSpec:
+    """One instance of the batched workload, before its graph is generated."""
+
+    n: int
+    m: int
+    graph_seed: int
+    nR: int
+    nS: int
+    set_seed: int
+    matches: float  # target S-matches per R node (theta is calibrated for it)
+
+
+def c4_batch_specs(count: int = 512, seed: int = BASE_SEED + 3) -> list[BatchSpec]:
+    """512 joins of uneven size: n log-uniform in [1k, 50k] nodes, m = 2.77 n edges (the
+    road-like generator), |R| and |S| log-uniform in [64, 4096] independently, each capped
+    at n / 3, and a target of 5 to 200 S-matches per R node, log-uniform."""
+    rng = np.random.default_rng(seed)
+    specs = []
+    for i in range(count):
+        n = int(round(log_uniform(rng, 1_000, 50_000)))
+        nR = int(min(round(log_uniform(rng, 64, 4096)), n // 3))
+        nS = int(min(round(log_uniform(rng, 64, 4096)), n // 3))
+        matches = float(log_uniform(rng, 5, 200))
+        specs.append(BatchSpec(n, int(round(2.77 * n)), seed + 1 + i, nR, nS, seed + 100_000 + i, matches))
+    return specs
+
+
+def c4_instance(spec: BatchSpec) -> tuple[EdgeList, np.ndarray, np.ndarray]:
+    g = road_graph(spec.n, spec.m, spec.graph_seed)
+    R, S = disjoint_sets(g.n, spec.nR, spec.nS, spec.set_seed)
+    return g, R, S

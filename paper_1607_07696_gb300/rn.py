@@ -65,6 +65,22 @@ class rn_query_stats(C.Structure):
                 ("cycles_step_a", C.c_uint64), ("round_arcs", C.c_uint64)]
 
 
+class rn_query(C.Structure):
+    _fields_ = [("g", C.c_void_p), ("R", C.POINTER(C.c_uint32)), ("nR", C.c_uint32),
+                ("S", C.POINTER(C.c_uint32)), ("nS", C.c_uint32), ("theta", C.c_uint32)]
+
+
+class rn_batch_config(C.Structure):
+    _fields_ = [("autotune", C.c_uint32), ("use_graph", C.c_uint32)]
+
+
+class rn_batch_stats(C.Structure):
+    _fields_ = [("instances", C.c_uint32), ("groups", C.c_uint32), ("tiles", C.c_uint64),
+                ("retried_tiles", C.c_uint64), ("pairs", C.c_uint64), ("eager_runs", C.c_uint32),
+                ("graph_runs", C.c_uint32), ("launches_per_run", C.c_uint32), ("tuned", C.c_uint32),
+                ("candidates", C.c_uint32), ("device_ms", C.c_double)]
+
+
 # Every symbol include/rn.h declares, with its ctypes signature (restype, argtypes).
 _P32 = C.POINTER(C.c_uint32)
 _G = C.c_void_p
@@ -88,6 +104,15 @@ SIGNATURES = {
                          C.POINTER(rn_pairs)]),
     "rn_kcp_dev": (C.c_int, [_G, C.c_void_p, C.c_uint32, C.c_void_p, C.c_uint32, C.c_uint64,
                              C.c_uint32, C.POINTER(rn_dpairs), C.c_void_p]),
+    "rn_batch_create": (C.c_int, [C.POINTER(rn_query), C.c_uint32, C.POINTER(rn_batch_config),
+                                  C.POINTER(C.c_void_p)]),
+    "rn_batch_run": (C.c_int, [C.c_void_p, C.c_void_p]),
+    "rn_batch_pairs": (C.c_int, [C.c_void_p, C.c_uint32, C.POINTER(rn_pairs)]),
+    "rn_batch_pairs_dev": (C.c_int, [C.c_void_p, C.c_uint32, C.POINTER(C.c_void_p), C.POINTER(C.c_void_p),
+                                     C.POINTER(C.c_void_p), C.POINTER(C.c_uint64)]),
+    "rn_batch_stats_get": (C.c_int, [C.c_void_p, C.POINTER(rn_batch_stats)]),
+    "rn_batch_free": (None, [C.c_void_p]),
+    "rn_join_batch": (C.c_int, [C.POINTER(rn_query), C.c_uint32, C.POINTER(rn_pairs)]),
     "rn_pairs_free": (None, [C.POINTER(rn_pairs)]),
     "rn_dpairs_free": (None, [C.POINTER(rn_dpairs)]),
     "rn_last_error": (C.c_char_p, []),
@@ -308,3 +333,72 @@ def rn_last_query_stats() -> dict:
 
 def rn_version() -> str:
     return lib().rn_version().decode()
+
+
+def _queries(queries):
+    """queries: (Graph, R, S, theta) tuples -> (ctypes array, arrays kept alive)."""
+    keep = []
+    arr = (rn_query * len(queries))()
+    for i, (g, R, S, theta) in enumerate(queries):
+        r, s_ = _u32(R), _u32(S)
+        keep += [r, s_]
+        arr[i].g = g.handle
+        arr[i].R = _p32(r)
+        arr[i].nR = len(r)
+        arr[i].S = _p32(s_)
+        arr[i].nS = len(s_)
+        arr[i].theta = int(theta)
+    return arr, keep
+
+
+class Batch:
+    """Owner of an ``rn_batch*`` (a prepared batch of theta-joins)."""
+
+    def __init__(self, handle: int, graphs):
+        self.handle = C.c_void_p(handle)
+        self.graphs = graphs  # the graphs must outlive the batch
+
+    def __del__(self):
+        h = getattr(self, "handle", None)
+        if h and h.value and _lib is not None:
+            _lib.rn_batch_free(h)
+            self.handle = None
+
+
+def rn_batch_create(queries, autotune: bool = False, use_graph: bool = True) -> Batch:
+    arr, _keep = _queries(queries)
+    cfg = rn_batch_config(int(bool(autotune)), int(bool(use_graph)))
+    out = C.c_void_p()
+    _check(lib().rn_batch_create(arr, len(queries), C.byref(cfg), C.byref(out)))
+    return Batch(out.value, [q[0] for q in queries])
+
+
+def rn_batch_run(b: Batch, stream=None) -> None:
+    _check(lib().rn_batch_run(b.handle, _stream_ptr(stream)))
+
+
+def rn_batch_pairs(b: Batch, i: int):
+    p = rn_pairs()
+    _check(lib().rn_batch_pairs(b.handle, int(i), C.byref(p)))
+    return _take_pairs(p)
+
+
+def rn_batch_pairs_dev(b: Batch, i: int):
+    """(u, v, d) device addresses and the count of instance i's pairs (owned by the batch)."""
+    u, v, d, n = C.c_void_p(), C.c_void_p(), C.c_void_p(), C.c_uint64()
+    _check(lib().rn_batch_pairs_dev(b.handle, int(i), C.byref(u), C.byref(v), C.byref(d), C.byref(n)))
+    return u.value, v.value, d.value, int(n.value)
+
+
+def rn_batch_stats_get(b: Batch) -> dict:
+    st = rn_batch_stats()
+    _check(lib().rn_batch_stats_get(b.handle, C.byref(st)))
+    return {f: getattr(st, f) for f, _ in rn_batch_stats._fields_}
+
+
+def rn_join_batch(queries):
+    """One call: every query's (u, v, d) host arrays, in query order."""
+    arr, _keep = _queries(queries)
+    outs = (rn_pairs * len(queries))()
+    _check(lib().rn_join_batch(arr, len(queries), outs))
+    return [_take_pairs(outs[i]) for i in range(len(queries))]
