@@ -49,6 +49,7 @@ def parse():
     ap.add_argument("--delta", type=int, default=0)
     ap.add_argument("--tile-sources", type=int, default=0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-batch", action="store_true", help="skip the 512-instance batched leg")
     return ap.parse_args()
 
 
@@ -179,6 +180,86 @@ def cpu_baseline(w, spec, sample_sources: int = 1500) -> dict:
 
 
 # ------------------------------------------------------------------- engine ----
+
+def batch_leg(rn, steps: int, warmup: int, stream, flush) -> dict:
+    """512 independent theta-joins (1k-50k-node graphs, uneven |R| and |S|, per-instance
+    theta): pairs/s of the whole batch run as one autotuned, graph-replayed batch, as a
+    batch with the default plan, and as 512 plain one-query calls in a row, all with the
+    sets already in device memory and L2 flushed before every timed run."""
+    import numpy as np
+    import torch
+
+    from paper_1607_07696_gb300 import inputs as I
+
+    specs = I.c4_batch_specs()
+    thetas = WORKLOADS["batch512"]["theta"]
+    qs, dev = [], []
+    for sp, th in zip(specs, thetas):
+        e, R, S = I.c4_instance(sp)
+        g = rn.rn_graph_load(e.src, e.dst, e.w, e.n)
+        qs.append((g, R, S, th))
+        dev.append((torch.as_tensor(R.astype(np.int32), device="cuda"),
+                    torch.as_tensor(S.astype(np.int32), device="cuda")))
+
+    def timed(fn) -> float:
+        for _ in range(warmup):
+            fn()
+        torch.cuda.synchronize()
+        ms = []
+        for i in range(steps):
+            with torch.cuda.stream(stream):
+                flush.fill_(i & 0xFF)
+                a = torch.cuda.Event(enable_timing=True)
+                b = torch.cuda.Event(enable_timing=True)
+                a.record(stream)
+                fn()
+                b.record(stream)
+            b.synchronize()
+            ms.append(a.elapsed_time(b))
+        return statistics.median(ms)
+
+    out = rn.DevicePairs()
+    plain_pairs = [0]
+
+    def plain():
+        tot = 0
+        for (g, R, S, th), (dR, dS) in zip(qs, dev):
+            tot += rn.rn_distance_join_dev(g, dR, dS, th, out, stream)
+        plain_pairs[0] = tot
+
+    plain_ms = timed(plain)
+    plain_launches = 0
+    for (g, R, S, th), (dR, dS) in zip(qs[:1], dev[:1]):
+        rn.rn_distance_join_dev(g, dR, dS, th, out, stream)
+        plain_launches = rn.rn_last_query_stats()["launches"] * len(qs)
+
+    b0 = rn.rn_batch_create(qs)
+    default_ms = timed(lambda: rn.rn_batch_run(b0, stream))
+    s0 = rn.rn_batch_stats_get(b0)
+    t0 = time.perf_counter()
+    b1 = rn.rn_batch_create(qs, autotune=True)
+    rn.rn_batch_run(b1, stream)
+    tune_s = time.perf_counter() - t0
+    tuned_ms = timed(lambda: rn.rn_batch_run(b1, stream))
+    s1 = rn.rn_batch_stats_get(b1)
+    pairs = int(s1["pairs"])
+    assert pairs == plain_pairs[0] == int(s0["pairs"]), "batched and plain pair counts differ"
+    res = {
+        "workload": "batch512: 512 theta-joins, n 1k-50k log-uniform, |R|,|S| 64-4096",
+        "instances": len(qs), "nodes": int(sum(q[0].n for q in qs)), "pairs": pairs,
+        "unit": UNIT,
+        "batched": pairs / (tuned_ms / 1e3), "batched_ms": tuned_ms,
+        "batched_default_plan": pairs / (default_ms / 1e3), "batched_default_ms": default_ms,
+        "plain": pairs / (plain_ms / 1e3), "plain_ms": plain_ms,
+        "batched_vs_plain": plain_ms / tuned_ms,
+        "tiles": int(s1["tiles"]), "groups": int(s1["groups"]), "graph_runs": int(s1["graph_runs"]),
+        "launches_per_run": int(s1["launches_per_run"]), "plain_launches": int(plain_launches),
+        "autotune_s": tune_s, "default_plan_groups": int(s0["groups"]),
+        "tuned": {1: "one plan for all", 2: "plan per size class"}.get(int(s1["tuned"]), "no"),
+    }
+    del b0, b1
+    return res
+
 
 def run_engine(args):
     import numpy as np
@@ -315,6 +396,8 @@ def run_engine(args):
                    "cycles_emission": stats["cycles_emission"],
                    "cycles_step_a": stats["cycles_step_a"], "round_arcs": stats["round_arcs"]},
     }
+    if not args.no_batch and world == 1:
+        line["batched"] = batch_leg(rn, max(3, args.steps // 2), 3, stream, flush)
     if not args.no_cpu_baseline and world == 1:
         line["cpu_baseline"] = cpu_baseline(w, spec)
     print(json.dumps(line), flush=True)

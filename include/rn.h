@@ -93,6 +93,11 @@ typedef struct {
     uint32_t leaf_size;   /* recursive-bisection leaf size used by RN_REORDER */
     float alpha;          /* smoothing parameter of the bisection (Eq. 1-2), in [0, 1];
                              negative selects the default, 0.5 */
+    uint32_t map_slots;   /* slots of the first slot map every tile is searched with: 0 or
+                             8192 starts with narrow blocks (shared-memory map), 16384 with
+                             wide blocks, a larger power of two with a global-memory map of
+                             that size (for queries whose balls are known to be large);
+                             tiles that overflow are searched again with larger maps */
 } rn_config;
 
 /* Graph facts, filled by rn_graph_info. */
@@ -129,6 +134,8 @@ typedef struct {
     uint64_t cycles_rounds, cycles_boundaries, cycles_emission;
     uint64_t cycles_step_a; /* part of cycles_rounds spent taking items and their offsets */
     uint64_t round_arcs;    /* arcs of the scanned items, over all rounds */
+    uint64_t max_ball;      /* largest union ball (slots) of a tile that completed */
+    double retry_ms;        /* time of the launches that searched overflowed tiles again */
 } rn_query_stats;
 
 /*
@@ -236,10 +243,12 @@ typedef struct {
 typedef struct rn_batch rn_batch;
 
 typedef struct {
-    uint32_t autotune;  /* 1: before the first run, time every candidate plan (tile width,
-                           bucket width, block shape) on the batch and keep, per size class
-                           of instance (log2 n, log2 |R|), the one with the least SM cycles;
-                           plans are remembered for later batches of the process */
+    uint32_t autotune;  /* 1: before the first run, run the batch under every candidate
+                           plan (tile width, bucket width, sources per tile); give each size
+                           class of instance (log2 n, log2 |R|, log2 of theta in median arc
+                           weights) the candidate with the least SM cycles, and keep that mix
+                           if the batch runs faster with it than with the best single
+                           candidate; plans are remembered for later batches of the process */
     uint32_t use_graph; /* 1: after the first (eager) run, capture the whole batch in a CUDA
                            graph and replay it on later runs */
 } rn_batch_config;
@@ -247,7 +256,10 @@ typedef struct {
 typedef struct {
     uint32_t instances, groups;  /* groups: launches of one block shape and tile width */
     uint64_t tiles, retried_tiles, pairs;
-    uint32_t eager_runs, graph_runs, launches_per_run, tuned, candidates;
+    uint32_t eager_runs, graph_runs, launches_per_run;
+    uint32_t tuned;              /* 0: not tuned; 1: one candidate plan for every instance;
+                                    2: a plan per size class of instance */
+    uint32_t candidates;         /* batch runs the tuning took */
     double device_ms;            /* last run, CUDA events on the batch's stream */
 } rn_batch_stats;
 

@@ -131,6 +131,10 @@ void apply_config(rn_graph *g, const rn_config *cfg) {
         if (cfg->tile_width) c.tile_width = cfg->tile_width;
         c.tile_src = cfg->tile_sources;
         c.delta = cfg->delta;
+        const uint32_t ms = cfg->map_slots;
+        if (ms && (ms < 8192 || (ms & (ms - 1)) || ms > (1u << 30)))
+            rn::fail(RN_EINVAL, "map_slots must be 0 or a power of two in [8192, 2^30]");
+        c.map_slots = ms;
     }
     g->cfg = c;
 }

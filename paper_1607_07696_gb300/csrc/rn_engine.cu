@@ -25,6 +25,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <chrono>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -149,6 +150,7 @@ struct Control {
     unsigned long long rounds, round_items, boundaries;
     unsigned long long cyc_round, cyc_bound, cyc_emit;
     unsigned long long cyc_stepA, round_arcs;
+    uint32_t max_fill;  // largest union ball (slots) of a completed tile
     uint32_t check[4];  // first failed device-side check of the batch path: code, index, value
 };
 
@@ -206,6 +208,12 @@ struct Workspace {
     uint32_t *hist = nullptr;
     size_t hist_cap = 0;
     cudaEvent_t ev0 = nullptr, ev1 = nullptr, evs0 = nullptr, evs1 = nullptr;
+    cudaEvent_t evr = nullptr;  // end of the last retry launch
+    float retry_ms = 0;
+    // a workspace may own its global-map buffer instead of using the device's
+    bool own_gmap_enabled = false, own_gmap_moved = false;
+    uint32_t *own_gmap = nullptr;
+    size_t own_gmap_bytes = 0;
     uint32_t launches = 0;  // kernels launched by the current query
     int blocks_per_sm = 0;  // occupancy of the shared-map search kernel
     uint64_t bytes = 0;
@@ -236,6 +244,7 @@ Workspace *workspace_create(const DeviceGraph &g) {
         RN_CUDA(cudaEventCreate(&ws->ev1));
         RN_CUDA(cudaEventCreate(&ws->evs0));
         RN_CUDA(cudaEventCreate(&ws->evs1));
+        RN_CUDA(cudaEventCreate(&ws->evr));
     } catch (...) {
         workspace_destroy(ws);
         throw;
@@ -264,6 +273,8 @@ void workspace_destroy(Workspace *ws) {
     if (ws->ev1) cudaEventDestroy(ws->ev1);
     if (ws->evs0) cudaEventDestroy(ws->evs0);
     if (ws->evs1) cudaEventDestroy(ws->evs1);
+    if (ws->evr) cudaEventDestroy(ws->evr);
+    device_free(ws->own_gmap);
     delete ws;
 }
 
@@ -408,6 +419,7 @@ struct SearchArgs {
     uint32_t nR_fixed;
     unsigned long long *inst_pairs;
     unsigned long long *inst_cycles;
+    uint32_t *inst_ball;  // per instance: largest union ball of a completed tile
 };
 
 // What a block needs to know about the tile it searches.
@@ -756,52 +768,43 @@ __global__ void __launch_bounds__(THREADS, (THREADS == NARROW ? CTAS_PER_SM : 1)
                         s_mark = t;
                         s_tel[T_ARCS] += total;
                     }
-                    // -- step B: one thread per arc of the staged items, two arcs in flight
-                    // (warp-uniform trip count, so the ballots below see every lane)
-                    for (uint32_t g0 = tid & ~31u; g0 < total; g0 += 2 * SEARCH_THREADS) {
-                        uint32_t item[2], hy[2], w[2];
-                        bool push[2] = {false, false};
-#pragma unroll
-                        for (int u = 0; u < 2; u++) {
-                            const uint32_t gi = g0 + lane + u * SEARCH_THREADS;
-                            hy[u] = EMPTY;
-                            w[u] = 0;
-                            item[u] = 0;
-                            if (gi >= total) continue;
+                    // -- step B: one thread per arc of the staged items, in chunks of 32 arcs
+                    // per warp (warp-uniform trip count, so the ballots below see every
+                    // lane).  A thread takes its arc's item, head and weight, prunes it
+                    // against the item's least dirty value, finds the head's slot, then
+                    // relaxes the item's dirty lane-groups into that slot, G at a time.
+                    // (One warp per arc across the row, with coalesced row loads, measured
+                    // slower: the round is bound by chains of dependent L2 round trips,
+                    // which serialising a warp's arcs lengthens.)
+                    for (uint32_t c0 = warp * 32; c0 < total; c0 += SEARCH_THREADS) {
+                        const uint32_t gi = c0 + lane;
+                        uint32_t item = 0, hy = EMPTY, w = 0;
+                        bool push = false;
+                        if (gi < total) {
                             uint32_t lo = 0, hi = nc - 1;  // last item whose arcs start at or before gi
                             while (lo < hi) {
                                 const uint32_t mid = (lo + hi + 1) >> 1;
                                 if (it_off[mid] <= gi) lo = mid;
                                 else hi = mid - 1;
                             }
-                            item[u] = lo;
+                            item = lo;
                             const uint2 arc = __ldg(&adj[it_beg[lo] + (gi - it_off[lo])]);
-                            w[u] = arc.y;
-                            hy[u] = arc.x;  // the head node until its slot is known
+                            w = arc.y;
+                            if (it_dmin[lo] + w <= bound) hy = arc.x;  // the head node until its slot is known
                         }
-                        uint32_t inserted = 0;
-#pragma unroll
-                        for (int u = 0; u < 2; u++) {
-                            if (hy[u] == EMPTY) continue;
-                            if (it_dmin[item[u]] + w[u] > bound) {
-                                hy[u] = EMPTY;
-                                continue;
-                            }
-                            bool ins;
-                            hy[u] = find_or_insert_nf(hkeys, a.H, a.hshift, hy[u], &ins);
-                            if (hy[u] == EMPTY) s_fail = 1;
-                            inserted += ins;
+                        bool ins = false;
+                        if (hy != EMPTY) {
+                            hy = find_or_insert_nf(hkeys, a.H, a.hshift, hy, &ins);
+                            if (hy == EMPTY) s_fail = 1;
                         }
-                        inserted = __reduce_add_sync(FULL, inserted);
+                        const uint32_t inserted = __popc(__ballot_sync(FULL, ins));
                         if (lane == 0 && inserted && atomicAdd(&s_fill, inserted) + inserted > a.max_fill)
                             s_fail = 1;
-#pragma unroll
-                        for (int u = 0; u < 2; u++) {
-                            if (hy[u] == EMPTY) continue;
-                            const uint32_t *xrow = slab + size_t(it_x[item[u]]) * T;
-                            uint32_t *yrow = slab + size_t(hy[u]) * T;
+                        if (hy != EMPTY) {
+                            const uint32_t *xrow = slab + size_t(it_x[item]) * T;
+                            uint32_t *yrow = slab + size_t(hy) * T;
                             uint32_t imask = 0, imin = INF;
-                            for (uint32_t m = it_mask[item[u]]; m;) {
+                            for (uint32_t m = it_mask[item]; m;) {
                                 uint32_t jj[G];
                                 Row<L> dv[G], cv[G];
 #pragma unroll
@@ -822,7 +825,7 @@ __global__ void __launch_bounds__(THREADS, (THREADS == NARROW ? CTAS_PER_SM : 1)
 #pragma unroll
                                     for (int q = 0; q < L; q++) {
                                         if (dv[k].x[q] == INF) continue;
-                                        const uint32_t d = dv[k].x[q] + w[u];
+                                        const uint32_t d = dv[k].x[q] + w;
                                         if (d <= bound && d < cv[k].x[q]) {
                                             atomicMin(yrow + jj[k] * L + q, d);
                                             imin = min(imin, d);
@@ -832,13 +835,12 @@ __global__ void __launch_bounds__(THREADS, (THREADS == NARROW ? CTAS_PER_SM : 1)
                                 }
                             }
                             if (imask) {
-                                atomicOr(&dmask[hy[u]], imask);
-                                const uint32_t old = atomicMin(&prio[hy[u]], imin);
-                                push[u] = imin < tau && (old == INF || old >= tau);
+                                atomicOr(&dmask[hy], imask);
+                                const uint32_t old = atomicMin(&prio[hy], imin);
+                                push = imin < tau && (old == INF || old >= tau);
                             }
                         }
-#pragma unroll
-                        for (int u = 0; u < 2; u++) warp_push(push[u], hy[u], &s_nnext, qnext, QCAP);
+                        warp_push(push, hy, &s_nnext, qnext, QCAP);
                     }
                     __syncthreads();
                     if (tid == 0) {
@@ -990,7 +992,13 @@ __global__ void __launch_bounds__(THREADS, (THREADS == NARROW ? CTAS_PER_SM : 1)
             const long long t = clock64();
             s_tel[T_EMIT] += t - s_mark;
             s_mark = t;
-            if (a.inst_cycles) atomicAdd(&a.inst_cycles[s_cx.inst], (unsigned long long)(t - s_tile0));
+            // cycles weighted by the block's share of an SM (a wide block holds it alone)
+            if (a.inst_cycles)
+                atomicAdd(&a.inst_cycles[s_cx.inst], (unsigned long long)(t - s_tile0) * (THREADS / NARROW));
+            if (ok) {
+                atomicMax(&a.ctl->max_fill, s_fill);
+                if (a.inst_ball) atomicMax(&a.inst_ball[s_cx.inst], s_fill);
+            }
         }
     }
     my_slots = __reduce_add_sync(FULL, my_slots);
@@ -1222,37 +1230,81 @@ static Control read_control(Workspace *ws, cudaStream_t st) {
     return *ws->ctl_host;
 }
 
-// Search every tile with narrow blocks (8192-slot shared maps, two per SM), then
-// search the tiles whose union ball overflowed again: with wide blocks (16384-slot
-// shared maps), then with global maps four times larger each time.  The map never
-// needs more than the next power of two >= 2n slots, where it cannot overflow.
+// Slots of the first map of a search: 8192 (narrow blocks, shared memory), 16384 (wide
+// blocks, shared memory) or a larger power of two (global memory), never more than the
+// largest map the graph can need.
+static uint64_t first_map(uint32_t want, uint64_t hcap) {
+    if (want <= SMEM_H) return SMEM_H;
+    uint64_t H = 1;
+    while (H < want) H <<= 1;
+    H = std::min<uint64_t>(H, hcap);
+    return H <= SMEM_HW ? SMEM_HW : H;
+}
+
+// One launch with global-memory slot maps of H slots over n tiles (tile_list, or all).
+// The maps and slab regions come from the device's retry buffer, or from the
+// workspace's own buffer when it has one (a batch, whose captured CUDA graph must keep
+// its addresses).
+static void launch_gmap(const DeviceGraph &g, Workspace *ws, uint32_t T, SearchArgs r, uint64_t H, uint32_t n,
+                        cudaStream_t st) {
+    (void)g;
+    const size_t per_block = (3 * H + H * T) * 4;
+    const size_t budget = size_t(8) << 30;
+    const uint32_t rgrid =
+        uint32_t(std::max<size_t>(1, std::min<size_t>({size_t(n), size_t(ws->num_sms), budget / per_block})));
+    uint32_t **buf = ws->own_gmap_enabled ? &ws->own_gmap : &ws->sh->gretry;
+    size_t *bytes = ws->own_gmap_enabled ? &ws->own_gmap_bytes : &ws->sh->gretry_bytes;
+    if (*bytes < per_block * rgrid) {
+        device_free(*buf);
+        *buf = nullptr;
+        *bytes = 0;
+        *buf = (uint32_t *)device_alloc(per_block * rgrid);
+        *bytes = per_block * rgrid;
+        ws->own_gmap_moved = true;
+    }
+    RN_CUDA(cudaMemsetAsync(*buf, 0xFF, per_block * rgrid, st));  // rows INF
+    r.gmap = *buf;
+    r.slab = *buf + size_t(rgrid) * 3 * H;
+    r.H = uint32_t(H);
+    r.hshift = 32 - bits_for(uint32_t(H));
+    r.max_fill = uint32_t(H * 7 / 8);
+    search(T, Shape::WideGlobal, r, rgrid, st);
+}
+
+// Search every tile with the first map (by default narrow blocks: 8192-slot shared
+// maps, two per SM), then search the tiles whose union ball overflowed again: with wide
+// blocks (16384-slot shared maps), then with global maps four times larger each time.
+// The map never needs more than the next power of two >= 2n slots, where it cannot
+// overflow.
 static Control search_all(const DeviceGraph &g, Workspace *ws, uint32_t T, SearchArgs a,
-                          uint32_t ntiles, cudaStream_t st, uint64_t *retried, bool wide = false) {
+                          uint32_t ntiles, cudaStream_t st, uint64_t *retried, uint32_t map_slots = 0) {
     const uint32_t grid_max = uint32_t(ws->num_sms) * CTAS_PER_SM;
     a.slab = ws->sh->slab;
     if (ntiles && (!a.src || !a.slab || !a.sbits || !a.out_key || !a.out_d || !a.row_ptr || !a.adj || !a.ctl))
         fail(RN_EINTERNAL, "tile search without its buffers");
+    uint64_t hcap = 1;
+    while (hcap < 2ull * g.n) hcap <<= 1;
+    uint64_t H = first_map(map_slots, hcap);
     a.gmap = nullptr;
     a.tile_list = nullptr;
     a.ntiles = ntiles;
-    const uint32_t H0 = wide ? SMEM_HW : SMEM_H;
-    a.H = H0;
-    a.hshift = 32 - bits_for(H0);
-    a.max_fill = H0 * 7 / 8;
     a.failed = ws->failed;
-    a.slab = ws->sh->slab;
+    if (H <= SMEM_HW) {
+        a.H = uint32_t(H);
+        a.hshift = 32 - bits_for(uint32_t(H));
+        a.max_fill = uint32_t(H * 7 / 8);
+    }
     RN_CUDA(cudaEventRecord(ws->evs0, st));
     if (ntiles) {
-        if (wide) search(T, Shape::Wide, a, std::max<uint32_t>(1, std::min(ntiles, uint32_t(ws->num_sms))), st);
-        else search(T, Shape::Narrow, a, std::max<uint32_t>(1, std::min(ntiles, grid_max)), st);
+        if (H == SMEM_H) search(T, Shape::Narrow, a, std::max<uint32_t>(1, std::min(ntiles, grid_max)), st);
+        else if (H == SMEM_HW) search(T, Shape::Wide, a, std::max<uint32_t>(1, std::min(ntiles, uint32_t(ws->num_sms))), st);
+        else launch_gmap(g, ws, T, a, H, ntiles, st);
         ws->launches++;
-        ws->blocks_per_sm = T == 32 ? search_occupancy<1>() : T == 64 ? search_occupancy<2>() : search_occupancy<4>();
+        ws->blocks_per_sm = H > SMEM_H ? 1 : T == 32 ? search_occupancy<1>() : T == 64 ? search_occupancy<2>() : search_occupancy<4>();
     }
     RN_CUDA(cudaEventRecord(ws->evs1, st));
     Control c = read_control(ws, st);
-    uint64_t hcap = 1;
-    while (hcap < 2ull * g.n) hcap <<= 1;
-    uint64_t H = H0;
+    ws->retry_ms = 0;
     uint32_t *list = ws->failed, *next = ws->failed2;
     while (c.n_failed && !c.err) {
         if (H >= hcap) fail(RN_EINTERNAL, "slot map overflowed at its largest size");
@@ -1273,28 +1325,14 @@ static Control search_all(const DeviceGraph &g, Workspace *ws, uint32_t T, Searc
             search(T, Shape::Wide, r, std::min<uint32_t>(nf, uint32_t(ws->num_sms)), st);
         } else {
             H = std::min<uint64_t>(H * 4, hcap);
-            const size_t per_block = (3 * H + H * T) * 4;
-            const size_t budget = size_t(8) << 30;
-            const uint32_t rgrid =
-                uint32_t(std::max<size_t>(1, std::min<size_t>({size_t(nf), size_t(ws->num_sms), budget / per_block})));
-            DeviceShared *sh = ws->sh;
-            if (sh->gretry_bytes < per_block * rgrid) {
-                device_free(sh->gretry);
-                sh->gretry = nullptr;
-                sh->gretry_bytes = 0;
-                sh->gretry = (uint32_t *)device_alloc(per_block * rgrid);
-                sh->gretry_bytes = per_block * rgrid;
-            }
-            RN_CUDA(cudaMemsetAsync(sh->gretry, 0xFF, per_block * rgrid, st));  // rows INF
-            r.gmap = sh->gretry;
-            r.slab = sh->gretry + size_t(rgrid) * 3 * H;
-            r.H = uint32_t(H);
-            r.hshift = 32 - bits_for(uint32_t(H));
-            r.max_fill = uint32_t(H * 7 / 8);
-            search(T, Shape::WideGlobal, r, rgrid, st);
+            launch_gmap(g, ws, T, r, H, nf, st);
         }
         ws->launches++;
+        RN_CUDA(cudaEventRecord(ws->evr, st));
         c = read_control(ws, st);
+        float ms = 0;
+        RN_CUDA(cudaEventElapsedTime(&ms, ws->evs1, ws->evr));
+        ws->retry_ms = ms;
         std::swap(list, next);  // this launch's failures are the next launch's tiles
     }
     return c;
@@ -1426,7 +1464,7 @@ void run_join(const DeviceGraph &g, Workspace *ws, const EngineConfig &cfg, uint
     a.out_d = ws->valA;
     a.out_cap = ws->pair_cap;
     uint64_t retried = 0;
-    Control c = search_all(g, ws, T, a, ntiles, st, &retried);
+    Control c = search_all(g, ws, T, a, ntiles, st, &retried, cfg.map_slots);
     check_control(c);
     if (c.pairs > ws->pair_cap) {
         // the pair buffer was too small: grow it and search again (same result)
@@ -1436,7 +1474,7 @@ void run_join(const DeviceGraph &g, Workspace *ws, const EngineConfig &cfg, uint
         a.out_key = ws->keyA;
         a.out_d = ws->valA;
         a.out_cap = ws->pair_cap;
-        c = search_all(g, ws, T, a, ntiles, st, &retried);
+        c = search_all(g, ws, T, a, ntiles, st, &retried, cfg.map_slots);
         check_control(c);
         if (c.pairs > ws->pair_cap) fail(RN_EINTERNAL, "pair count changed between passes");
     }
@@ -1473,6 +1511,8 @@ void run_join(const DeviceGraph &g, Workspace *ws, const EngineConfig &cfg, uint
     stats->cycles_emission = c.cyc_emit;
     stats->cycles_step_a = c.cyc_stepA;
     stats->round_arcs = c.round_arcs;
+    stats->max_ball = c.max_fill;
+    stats->retry_ms = ws->retry_ms;
 }
 
 // ------------------------------------------------- join without allocation ----
@@ -1797,7 +1837,7 @@ void run_kcp(const DeviceGraph &g, Workspace *ws, const EngineConfig &cfg, uint3
         a.out_key = ws->keyA;
         a.out_d = ws->valA;
         a.out_cap = ws->pair_cap;
-        c = search_all(g, ws, T, a, ntiles, st, &retried);
+        c = search_all(g, ws, T, a, ntiles, st, &retried, cfg.map_slots);
         check_control(c);
         if (c.pairs > ws->pair_cap) {  // the candidate buffer was too small: same pass again
             ensure_pairs(ws, c.pairs + c.pairs / 4);
@@ -1867,17 +1907,22 @@ void run_kcp(const DeviceGraph &g, Workspace *ws, const EngineConfig &cfg, uint3
 
 // ------------------------------------------------------------------- batch ----
 // Many independent theta-joins (their own graphs, sets and thetas) searched by one
-// persistent launch per block shape and tile width.  The batch's graphs are copied into
-// one disjoint union (node ids and arc positions shifted per instance, plus one
-// isolated pad node), so the search runs exactly as for a single query on that graph:
-// every instance's R list, in internal ids, is padded with the pad node to whole tiles,
-// and per-tile tables give each tile its instance's theta, bucket width and index.
-// Pairs are sorted by (u, v) in union ids, which puts every instance's pairs together in
-// (u, v) order; a last kernel shifts them back to the instance's own ids.  After a first
-// eager run fixes the counts, the run (clears, searches, sort) is captured in a CUDA
-// graph and replayed; a replay that does not reproduce the counts falls back to an
-// eager run.  An autotuner picks, per size class of instance, the tile width, the
-// bucket width and the block shape from per-instance SM cycles measured in the kernel.
+// persistent launch per (tile width, first map, sources per tile) group.  The batch's
+// graphs are copied into one disjoint union (node ids and arc positions shifted per
+// instance, plus one isolated pad node), so the search runs exactly as for a single
+// query on that graph: every instance's R list, in internal ids, is padded with the pad
+// node to whole tiles, and per-tile tables give each tile its instance's theta, bucket
+// width and index.  Pairs are sorted by (u, v) in union ids, which puts every instance's
+// pairs together in (u, v) order; a last kernel shifts them back to the instance's ids.
+//
+// The first map of an instance's tiles follows the largest union ball its tiles reached
+// in an earlier run (a shared-memory map when it fits, else a global map of the right
+// size), so tiles whose balls are known to be large are not first searched with maps
+// they overflow.  Once a run needs no retry, the whole run (clears, searches, sort) is
+// captured in a CUDA graph and replayed; a replay that does not reproduce the counts
+// falls back to an eager run.  An autotuner picks, per size class of instance, the tile
+// width, the bucket width and the sources per tile from per-instance SM cycles measured
+// in the kernel.
 
 // Copy one instance's graph into the union: nodes shifted by node_off, arcs by arc_off.
 __global__ void k_union_graph(const uint32_t *__restrict__ row_ptr, const uint2 *__restrict__ adj,
@@ -1916,13 +1961,28 @@ namespace {
 
 struct BatchPlan {
     uint32_t T = 32;
-    bool wide = false;
     uint32_t delta_mult = 4;  // bucket width in median arc weights
     uint32_t src_div = 1;     // sources per tile = T / src_div
 };
 
-// Size class of an instance for the autotuner: log2 of its node count and of |R|.
-uint32_t size_class(uint32_t n, uint32_t nR) { return (bits_for(n) << 8) | bits_for(std::max<uint32_t>(nR, 1)); }
+// Size class of an instance for the autotuner: log2 of its node count, of |R| and of
+// theta in median arc weights (the hop radius of a search, which sets its ball).
+uint32_t size_class(uint32_t n, uint32_t nR, uint32_t theta, uint32_t median_w) {
+    const uint64_t hops = uint64_t(theta) / std::max<uint32_t>(1, median_w);
+    return (bits_for(n) << 16) | (bits_for(std::max<uint32_t>(nR, 1)) << 8) |
+           bits_for(uint32_t(std::min<uint64_t>(hops + 1, 1u << 20)));
+}
+
+// First map for tiles whose union ball reached `ball` slots: the narrow shared map
+// while it holds the ball with some room, then the wide one, then a global map.
+uint32_t map_for_ball(uint32_t ball) {
+    const uint64_t need = uint64_t(ball) * 8 / 7 + uint64_t(ball) / 8 + 1;
+    if (need <= SMEM_H) return SMEM_H;
+    if (need <= SMEM_HW) return SMEM_HW;
+    uint64_t H = SMEM_HW * 2;
+    while (H < need) H <<= 1;
+    return uint32_t(std::min<uint64_t>(H, 1u << 30));
+}
 
 std::mutex g_tune_mu;
 std::map<uint32_t, BatchPlan> g_tune_cache;  // size class -> tuned plan, for the process
@@ -1936,14 +1996,19 @@ struct Batch {
     std::vector<uint32_t> n, nR, theta, median_w, cls, node_off;
     std::vector<std::vector<uint32_t>> rint;  // per instance: R in union internal ids, ascending
     std::vector<BatchPlan> plan;
+    std::vector<uint32_t> map;       // per instance: slots of the first map
+    std::vector<uint32_t> ball;      // per instance: largest union ball seen under plan[i].T
+    std::vector<uint32_t> ball_T;    // the tile width ball[i] was measured with (0: none)
+    std::vector<double> tile_cost;   // per instance: SM cycles of one of its tiles, last run
+    bool costs_known = false;        // tile_cost holds measurements (else a size proxy)
+    bool laid_out_by_cost = false;   // the layout used measured costs
     DeviceGraph ug;  // the union graph (row_ptr, adj, iperm)
-    uint32_t *sbits = nullptr, *node_off_d = nullptr;
-    Workspace *ws = nullptr;  // control block, retry lists, events of the batch
+    uint32_t *sbits = nullptr, *node_off_d = nullptr, *inst_ball = nullptr;
+    Workspace *ws = nullptr;  // control block, retry lists, global maps, events of the batch
     cudaStream_t stream = nullptr;
     unsigned long long *inst_pairs = nullptr, *inst_cycles = nullptr, *pair_off_d = nullptr;
     struct Group {
-        uint32_t T = 32, tile_src = 32, nsrc = 0, tiles = 0;
-        bool wide = false;
+        uint32_t T = 32, map = SMEM_H, tile_src = 32, nsrc = 0, tiles = 0;
         uint32_t *src = nullptr, *tbound = nullptr, *tdelta = nullptr, *tinst = nullptr;
     };
     std::vector<Group> groups;
@@ -1976,12 +2041,13 @@ static void batch_free_groups(Batch *b) {
 
 void batch_destroy(Batch *b) {
     if (!b) return;
+    if (b->stream) cudaStreamSynchronize(b->stream);
     batch_drop_graph(b);
     batch_free_groups(b);
-    for (void *p : {(void *)b->sbits, (void *)b->node_off_d, (void *)b->inst_pairs, (void *)b->inst_cycles,
-                    (void *)b->pair_off_d, (void *)b->keyA, (void *)b->keyB, (void *)b->valA, (void *)b->valB,
-                    (void *)b->hist, (void *)b->out_u, (void *)b->out_v, (void *)b->out_d,
-                    (void *)b->ug.row_ptr, (void *)b->ug.adj, (void *)b->ug.iperm})
+    for (void *p : {(void *)b->sbits, (void *)b->node_off_d, (void *)b->inst_ball, (void *)b->inst_pairs,
+                    (void *)b->inst_cycles, (void *)b->pair_off_d, (void *)b->keyA, (void *)b->keyB,
+                    (void *)b->valA, (void *)b->valB, (void *)b->hist, (void *)b->out_u, (void *)b->out_v,
+                    (void *)b->out_d, (void *)b->ug.row_ptr, (void *)b->ug.adj, (void *)b->ug.iperm})
         device_free(p);
     if (b->stream) cudaStreamDestroy(b->stream);
     workspace_destroy(b->ws);
@@ -1995,19 +2061,42 @@ static T *upload_vec(const std::vector<T> &v) {
     return p;
 }
 
-// Group the instances by (tile width, block shape, sources per tile) and upload each
+// First maps from the balls measured under each instance's current tile width.
+static bool batch_adapt_maps(Batch *b) {
+    bool changed = false;
+    for (uint32_t i = 0; i < b->nq; i++) {
+        const uint32_t m = b->ball_T[i] == b->plan[i].T ? map_for_ball(b->ball[i]) : SMEM_H;
+        if (m != b->map[i]) changed = true;
+        b->map[i] = m;
+    }
+    return changed;
+}
+
+// Group the instances by (tile width, first map, sources per tile) and upload each
 // group's padded source list and per-tile tables.
 static void batch_layout(Batch *b) {
     batch_drop_graph(b);
     batch_free_groups(b);
-    std::map<std::tuple<uint32_t, bool, uint32_t>, std::vector<uint32_t>> by;
+    std::map<std::tuple<uint32_t, uint32_t, uint32_t>, std::vector<uint32_t>> by;
     for (uint32_t i = 0; i < b->nq; i++)
-        by[std::make_tuple(b->plan[i].T, b->plan[i].wide, b->plan[i].src_div)].push_back(i);
-    uint64_t tiles = 0;
+        by[std::make_tuple(b->plan[i].T, b->map[i], b->plan[i].src_div)].push_back(i);
+    // longest tiles first, in every group and across groups (the persistent blocks then
+    // end together instead of waiting on a few long tiles popped last)
+    std::vector<std::pair<double, std::vector<uint32_t>>> order;
     for (auto &kv : by) {
+        auto &v = kv.second;
+        std::stable_sort(v.begin(), v.end(), [&](uint32_t x, uint32_t y) { return b->tile_cost[x] > b->tile_cost[y]; });
+        order.emplace_back(b->tile_cost[v.front()], v);
+    }
+    std::stable_sort(order.begin(), order.end(), [](const auto &x, const auto &y) { return x.first > y.first; });
+    uint64_t tiles = 0;
+    for (auto &ov : order) {
+        const auto &first = ov.second.front();
+        const std::pair<std::tuple<uint32_t, uint32_t, uint32_t>, std::vector<uint32_t>> kv{
+            std::make_tuple(b->plan[first].T, b->map[first], b->plan[first].src_div), ov.second};
         Batch::Group g;
         g.T = std::get<0>(kv.first);
-        g.wide = std::get<1>(kv.first);
+        g.map = std::get<1>(kv.first);
         g.tile_src = std::max<uint32_t>(1, g.T / std::get<2>(kv.first));
         std::vector<uint32_t> src, tb, td, ti;
         for (uint32_t i : kv.second) {
@@ -2074,6 +2163,7 @@ static SearchArgs batch_args(Batch *b, const Batch::Group &g) {
     a.tile_inst = g.tinst;
     a.inst_pairs = b->inst_pairs;
     a.inst_cycles = b->inst_cycles;
+    a.inst_ball = b->inst_ball;
     a.vbits = b->vbits;
     a.ctl = b->ws->ctl;
     a.out_key = b->keyA;
@@ -2086,6 +2176,7 @@ static void batch_clear(Batch *b, cudaStream_t st) {
     RN_CUDA(cudaMemsetAsync(b->ws->ctl, 0, sizeof(Control), st));
     RN_CUDA(cudaMemsetAsync(b->inst_pairs, 0, size_t(b->nq) * 8, st));
     RN_CUDA(cudaMemsetAsync(b->inst_cycles, 0, size_t(b->nq) * 8, st));
+    RN_CUDA(cudaMemsetAsync(b->inst_ball, 0, size_t(b->nq) * 4, st));
 }
 
 // Sort `total` pairs by (u, v) into the result arrays and shift them to instance ids.
@@ -2110,25 +2201,62 @@ static void batch_finish(Batch *b, uint64_t total, cudaStream_t st) {
     RN_CUDA(cudaGetLastError());
 }
 
+// Per-instance pair counts and offsets, and the balls of the run.
 static void batch_counts(Batch *b, cudaStream_t st) {
-    std::vector<unsigned long long> c(b->nq);
+    std::vector<unsigned long long> c(b->nq), cyc(b->nq);
+    std::vector<uint32_t> ball(b->nq);
     RN_CUDA(cudaMemcpyAsync(c.data(), b->inst_pairs, size_t(b->nq) * 8, cudaMemcpyDeviceToHost, st));
+    RN_CUDA(cudaMemcpyAsync(cyc.data(), b->inst_cycles, size_t(b->nq) * 8, cudaMemcpyDeviceToHost, st));
+    RN_CUDA(cudaMemcpyAsync(ball.data(), b->inst_ball, size_t(b->nq) * 4, cudaMemcpyDeviceToHost, st));
     RN_CUDA(cudaStreamSynchronize(st));
+    for (uint32_t i = 0; i < b->nq; i++) {
+        const uint32_t ts = std::max<uint32_t>(1, b->plan[i].T / b->plan[i].src_div);
+        const uint32_t nt = (b->nR[i] + ts - 1) / ts;
+        b->tile_cost[i] = nt ? double(cyc[i]) / nt : 0.0;
+    }
+    b->costs_known = true;
     b->cnt.assign(c.begin(), c.end());
     b->off.assign(b->nq + 1, 0);
-    for (uint32_t i = 0; i < b->nq; i++) b->off[i + 1] = b->off[i] + b->cnt[i];
+    for (uint32_t i = 0; i < b->nq; i++) {
+        b->off[i + 1] = b->off[i] + b->cnt[i];
+        if (b->ball_T[i] != b->plan[i].T) {
+            b->ball_T[i] = b->plan[i].T;
+            b->ball[i] = 0;
+        }
+        b->ball[i] = std::max(b->ball[i], ball[i]);
+    }
+}
+
+// The first launch of one group (the capturable part of its search).
+static void batch_launch_group(Batch *b, const Batch::Group &g, cudaStream_t st) {
+    if (!g.tiles) return;
+    SearchArgs a = batch_args(b, g);
+    a.slab = b->ws->sh->slab;
+    a.failed = b->ws->failed;
+    a.ntiles = g.tiles;
+    if (g.map > SMEM_HW) {
+        launch_gmap(b->ug, b->ws, g.T, a, g.map, g.tiles, st);
+        return;
+    }
+    a.H = g.map;
+    a.hshift = 32 - bits_for(g.map);
+    a.max_fill = g.map * 7 / 8;
+    const uint32_t grid_max = uint32_t(b->ws->num_sms) * CTAS_PER_SM;
+    if (g.map == SMEM_H) search(g.T, Shape::Narrow, a, std::max<uint32_t>(1, std::min(g.tiles, grid_max)), st);
+    else search(g.T, Shape::Wide, a, std::max<uint32_t>(1, std::min(g.tiles, uint32_t(b->ws->num_sms))), st);
 }
 
 // A full run with host checks between steps: retries of overflowed tiles, growth of
 // the pair buffer.  Returns the number of retried tiles.
 static uint64_t batch_run_eager(Batch *b, cudaStream_t st) {
+    b->ws->own_gmap_moved = false;
     for (;;) {
         batch_clear(b, st);
         uint64_t retried = 0;
         Control c{};
         for (const auto &g : b->groups) {
             RN_CUDA(cudaMemsetAsync(&b->ws->ctl->tile_next, 0, 8, st));  // tile_next, n_failed
-            c = search_all(b->ug, b->ws, g.T, batch_args(b, g), g.tiles, st, &retried, g.wide);
+            c = search_all(b->ug, b->ws, g.T, batch_args(b, g), g.tiles, st, &retried, g.map);
             check_control(c);
         }
         b->stats.retried_tiles = retried;
@@ -2158,6 +2286,7 @@ static uint64_t batch_run_eager(Batch *b, cudaStream_t st) {
             b->hist = (uint32_t *)device_alloc(b->hist_cap * 4);
             batch_drop_graph(b);
         }
+        if (b->ws->own_gmap_moved) batch_drop_graph(b);
         std::vector<unsigned long long> po(b->off.begin(), b->off.end());
         RN_CUDA(cudaMemcpyAsync(b->pair_off_d, po.data(), po.size() * 8, cudaMemcpyHostToDevice, st));
         batch_finish(b, b->total, st);
@@ -2170,24 +2299,15 @@ static uint64_t batch_run_eager(Batch *b, cudaStream_t st) {
 // The capturable sequence: clears, one launch per group, sort and shift.
 static void batch_record(Batch *b, cudaStream_t st) {
     batch_clear(b, st);
-    const uint32_t grid_max = uint32_t(b->ws->num_sms) * CTAS_PER_SM;
     for (const auto &g : b->groups) {
         RN_CUDA(cudaMemsetAsync(&b->ws->ctl->tile_next, 0, 8, st));
-        SearchArgs a = batch_args(b, g);
-        a.slab = b->ws->sh->slab;
-        a.failed = b->ws->failed;
-        a.ntiles = g.tiles;
-        const uint32_t H = g.wide ? SMEM_HW : SMEM_H;
-        a.H = H;
-        a.hshift = 32 - bits_for(H);
-        a.max_fill = H * 7 / 8;
-        const uint32_t grid = std::max<uint32_t>(1, std::min(g.tiles, g.wide ? uint32_t(b->ws->num_sms) : grid_max));
-        if (g.tiles) search(g.T, g.wide ? Shape::Wide : Shape::Narrow, a, grid, st);
+        batch_launch_group(b, g, st);
     }
     batch_finish(b, b->exec_pairs, st);
 }
 
-// One run: a graph replay when the last eager run needed no retries, else eager.
+// One run: a graph replay when the last eager run needed no retries, else eager.  An
+// eager run with retries sets the instances' first maps from the balls it measured.
 void batch_run(Batch *b, void *user_stream, bool use_graph) {
     std::lock_guard<std::mutex> device_lock(b->ws->sh->mu);
     cudaStream_t st = b->stream;
@@ -2214,7 +2334,12 @@ void batch_run(Batch *b, void *user_stream, bool use_graph) {
         const uint64_t retried = batch_run_eager(b, st);
         const uint32_t passes = (2 * b->vbits + 7) / 8;
         b->stats.launches_per_run = b->ws->launches + 3 * passes + 1;
-        if (use_graph && !retried && !b->exec) {
+        if (retried || !b->laid_out_by_cost) {
+            // the next run starts with fitting maps and the measured tile order
+            batch_adapt_maps(b);
+            batch_layout(b);
+            b->laid_out_by_cost = true;
+        } else if (use_graph && !b->exec) {
             b->exec_pairs = b->total;
             RN_CUDA(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
             try {
@@ -2241,22 +2366,43 @@ void batch_run(Batch *b, void *user_stream, bool use_graph) {
     }
 }
 
-// Autotuner: run the whole batch once per candidate plan, read every instance's SM
-// cycles, and give each size class the candidate with the least total cycles.
+// Autotuner.  Every candidate plan (tile width, bucket width, sources per tile) is run
+// on the whole batch, each instance with first maps fitted to its measured balls and
+// tiles ordered longest first; the run's wall time and every instance's SM cycles
+// (weighted by the share of an SM its blocks hold) are recorded.  Each size class then
+// takes the candidate with the least cycles; that mixed plan is kept if the batch runs
+// faster with it than with the best single candidate, else the best single candidate
+// is.  The default plan is a candidate, so tuning never loses to it on the batch it
+// was tuned on.  The chosen plan of each size class is remembered for the process.
+static double batch_time_eager(Batch *b) {
+    batch_adapt_maps(b);
+    batch_layout(b);
+    if (batch_run_eager(b, b->stream)) {  // overflowed: refit the maps, run again
+        batch_adapt_maps(b);
+        batch_layout(b);
+        batch_run_eager(b, b->stream);
+    }
+    batch_layout(b);  // measured tile order
+    const auto t0 = std::chrono::steady_clock::now();
+    batch_run_eager(b, b->stream);
+    return std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+}
+
 void batch_tune(Batch *b) {
     static const BatchPlan cands[] = {
-        {32, false, 2, 1}, {32, false, 4, 1}, {32, false, 8, 1}, {32, false, 4, 2},
-        {32, true, 4, 1},  {64, false, 4, 1}, {64, true, 4, 1},  {128, true, 4, 1},
+        {32, 4, 1}, {32, 8, 1}, {32, 16, 1}, {32, 4, 2}, {64, 4, 1}, {64, 8, 1}, {128, 4, 1}, {128, 8, 1},
     };
     const size_t nc = sizeof(cands) / sizeof(cands[0]);
-    std::map<uint32_t, std::vector<double>> cost;  // class -> cost per candidate
+    std::map<uint32_t, std::vector<double>> cost;  // class -> cycles per candidate
+    std::vector<double> wall(nc);
+    std::vector<BatchPlan> mixed(b->nq);
+    double wall_mixed = 0;
     {
         std::lock_guard<std::mutex> device_lock(b->ws->sh->mu);
         ensure_slab(b->ws);
         for (size_t c = 0; c < nc; c++) {
             for (uint32_t i = 0; i < b->nq; i++) b->plan[i] = cands[c];
-            batch_layout(b);
-            batch_run_eager(b, b->stream);
+            wall[c] = batch_time_eager(b);
             std::vector<unsigned long long> cyc(b->nq);
             RN_CUDA(cudaMemcpy(cyc.data(), b->inst_cycles, size_t(b->nq) * 8, cudaMemcpyDeviceToHost));
             for (uint32_t i = 0; i < b->nq; i++) {
@@ -2265,18 +2411,30 @@ void batch_tune(Batch *b) {
                 v[c] += double(cyc[i]);
             }
         }
+        std::map<uint32_t, size_t> pick;
+        for (auto &kv : cost) {
+            size_t best = 0;
+            for (size_t c = 1; c < nc; c++)
+                if (kv.second[c] < kv.second[best]) best = c;
+            pick[kv.first] = best;
+        }
+        for (uint32_t i = 0; i < b->nq; i++) mixed[i] = b->plan[i] = cands[pick[b->cls[i]]];
+        wall_mixed = batch_time_eager(b);
     }
-    std::lock_guard<std::mutex> lk(g_tune_mu);
-    for (auto &kv : cost) {
-        size_t best = 0;
-        for (size_t c = 1; c < nc; c++)
-            if (kv.second[c] < kv.second[best]) best = c;
-        g_tune_cache[kv.first] = cands[best];
+    const size_t best = size_t(std::min_element(wall.begin(), wall.end()) - wall.begin());
+    const bool use_mixed = wall_mixed < wall[best];
+    {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        for (uint32_t i = 0; i < b->nq; i++) {
+            b->plan[i] = use_mixed ? mixed[i] : cands[best];
+            g_tune_cache[b->cls[i]] = b->plan[i];
+        }
     }
-    for (uint32_t i = 0; i < b->nq; i++) b->plan[i] = g_tune_cache[b->cls[i]];
+    batch_adapt_maps(b);
     batch_layout(b);
-    b->stats.tuned = 1;
-    b->stats.candidates = uint32_t(nc);
+    b->laid_out_by_cost = false;  // costs of the chosen plan are measured by the next run
+    b->stats.tuned = use_mixed ? 2 : 1;
+    b->stats.candidates = uint32_t(nc + 1);
 }
 
 Batch *batch_create(const std::vector<const DeviceGraph *> &graphs, const std::vector<const std::vector<uint32_t> *> &perms,
@@ -2294,12 +2452,17 @@ Batch *batch_create(const std::vector<const DeviceGraph *> &graphs, const std::v
         b->cls.resize(b->nq);
         b->node_off.assign(b->nq + 1, 0);
         b->plan.assign(b->nq, BatchPlan{});
+        b->map.assign(b->nq, SMEM_H);
+        b->ball.assign(b->nq, 0);
+        b->ball_T.assign(b->nq, 0);
+        b->tile_cost.resize(b->nq);
+        for (uint32_t i = 0; i < b->nq; i++) b->tile_cost[i] = double(graphs[i]->n);  // until measured
         uint64_t nsum = 0, asum = 0;
         for (uint32_t i = 0; i < b->nq; i++) {
             b->n[i] = graphs[i]->n;
             b->theta[i] = theta[i] == RN_INF ? RN_THETA_MAX : theta[i];
             if (b->theta[i] > RN_THETA_MAX) fail(RN_EINVAL, "theta must be <= 2^31 or RN_INF");
-            b->cls[i] = size_class(b->n[i], nR[i]);
+            b->cls[i] = size_class(b->n[i], nR[i], b->theta[i], median_w[i]);
             b->node_off[i] = uint32_t(nsum);
             nsum += graphs[i]->n;
             asum += graphs[i]->arcs;
@@ -2321,6 +2484,7 @@ Batch *batch_create(const std::vector<const DeviceGraph *> &graphs, const std::v
         DeviceGraph capg{};
         capg.n = b->n_u;
         b->ws = workspace_create(capg);
+        b->ws->own_gmap_enabled = true;
         RN_CUDA(cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking));
         // the union graph
         b->ug.n = b->n_u;
@@ -2361,6 +2525,7 @@ Batch *batch_create(const std::vector<const DeviceGraph *> &graphs, const std::v
         b->node_off_d = upload_vec(b->node_off);
         b->inst_pairs = (unsigned long long *)device_alloc(size_t(b->nq) * 8);
         b->inst_cycles = (unsigned long long *)device_alloc(size_t(b->nq) * 8);
+        b->inst_ball = (uint32_t *)device_alloc(size_t(b->nq) * 4);
         b->pair_off_d = (unsigned long long *)device_alloc((size_t(b->nq) + 1) * 8);
         uint64_t totR = 0;
         for (uint32_t x : nR) totR += x;

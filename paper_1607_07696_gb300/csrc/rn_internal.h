@@ -66,6 +66,7 @@ struct EngineConfig {
     uint32_t tile_width = 32;
     uint32_t tile_src = 0;  // sources per tile; 0: spread over whole waves of blocks
     uint32_t delta = 0;     // 0: derive from the weights
+    uint32_t map_slots = 0; // first slot map: 0 / 8192 narrow, 16384 wide, larger: global
 };
 
 void run_join(const DeviceGraph &g, Workspace *ws, const EngineConfig &cfg, uint32_t median_w,

@@ -43,7 +43,7 @@ class rn_dpairs(C.Structure):
 
 class rn_config(C.Structure):
     _fields_ = [("tile_width", C.c_uint32), ("tile_sources", C.c_uint32), ("delta", C.c_uint32),
-                ("leaf_size", C.c_uint32), ("alpha", C.c_float)]
+                ("leaf_size", C.c_uint32), ("alpha", C.c_float), ("map_slots", C.c_uint32)]
 
 
 class rn_graph_stats(C.Structure):
@@ -62,7 +62,8 @@ class rn_query_stats(C.Structure):
                 ("search_ms", C.c_double), ("rounds", C.c_uint64), ("round_items", C.c_uint64),
                 ("boundaries", C.c_uint64), ("cycles_rounds", C.c_uint64),
                 ("cycles_boundaries", C.c_uint64), ("cycles_emission", C.c_uint64),
-                ("cycles_step_a", C.c_uint64), ("round_arcs", C.c_uint64)]
+                ("cycles_step_a", C.c_uint64), ("round_arcs", C.c_uint64), ("max_ball", C.c_uint64),
+                ("retry_ms", C.c_double)]
 
 
 class rn_query(C.Structure):
@@ -181,6 +182,7 @@ def _config(cfg: dict | None):
     c.delta = int(cfg.get("delta", 0))
     c.leaf_size = int(cfg.get("leaf_size", 0))
     c.alpha = float(cfg.get("alpha", -1.0))
+    c.map_slots = int(cfg.get("map_slots", 0))
     return C.byref(c)
 
 
@@ -354,9 +356,8 @@ def _queries(queries):
 class Batch:
     """Owner of an ``rn_batch*`` (a prepared batch of theta-joins)."""
 
-    def __init__(self, handle: int, graphs):
+    def __init__(self, handle: int):
         self.handle = C.c_void_p(handle)
-        self.graphs = graphs  # the graphs must outlive the batch
 
     def __del__(self):
         h = getattr(self, "handle", None)
@@ -370,7 +371,7 @@ def rn_batch_create(queries, autotune: bool = False, use_graph: bool = True) -> 
     cfg = rn_batch_config(int(bool(autotune)), int(bool(use_graph)))
     out = C.c_void_p()
     _check(lib().rn_batch_create(arr, len(queries), C.byref(cfg), C.byref(out)))
-    return Batch(out.value, [q[0] for q in queries])
+    return Batch(out.value)
 
 
 def rn_batch_run(b: Batch, stream=None) -> None:

@@ -208,3 +208,28 @@ def test_road1070k_join_sampled(rn, oracle):
     ref = og.join(sample, w.S, theta)
     m = np.isin(u, sample)
     assert_same((u[m], v[m], d[m]), ref, "road1070k sampled sources")
+
+
+@pytest.mark.parametrize("T,slots", [(32, 16384), (32, 65536), (64, 1 << 17), (128, 65536)])
+def test_first_map_size(rn, oracle, T, slots):
+    # unbounded search: every tile's ball is the whole 20k-node graph, larger than both
+    # shared maps; a first map of 16384 slots overflows and is retried, a global first
+    # map large enough is not
+    e = I.road_graph(20_000, 55_400, 51)
+    g = load(rn, e, cfg={"tile_width": T, "map_slots": slots})
+    R, S = I.disjoint_sets(e.n, 300, 1500, 52)
+    ref = oracle.graph(e.n, e.src, e.dst, e.w).join(R, S, rn.RN_THETA_MAX)
+    assert_same(dev_join(rn, g, R, S, rn.RN_INF), ref, f"T={T} first map {slots}")
+    st = rn.rn_last_query_stats()
+    import scipy.sparse as sp
+    from scipy.sparse.csgraph import connected_components
+
+    _, comp = connected_components(sp.coo_matrix((np.ones(e.m), (e.src, e.dst)), shape=(e.n, e.n)),
+                                   directed=False)
+    size = int(np.bincount(comp)[comp[R]].max())  # the largest component holding a source
+    assert size <= st["max_ball"] <= e.n
+    assert st["retried_tiles"] > 0 or slots * 7 // 8 >= st["max_ball"]
+    if slots * 7 // 8 < size:
+        assert st["retried_tiles"] > 0
+    with pytest.raises(rn.RNError):
+        load(rn, e, cfg={"map_slots": 5000})
