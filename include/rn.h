@@ -290,6 +290,72 @@ void rn_batch_free(rn_batch *b);
  * outs[0..nq) (free each with rn_pairs_free), free the batch. */
 rn_status rn_join_batch(const rn_query *q, uint32_t nq, rn_pairs *outs);
 
+/* ------------------------------------------------------------------ serving ---- */
+
+/* One request to a server: a theta-join (k = 0, as rn_distance_join) or the k closest
+ * pairs within theta (k >= 1, as rn_kcp).  R and S are host arrays, copied by
+ * rn_serve_submit. */
+typedef struct {
+    const uint32_t *R;
+    uint32_t nR;
+    const uint32_t *S;
+    uint32_t nS;
+    uint32_t theta;
+    uint64_t k;
+} rn_request;
+
+typedef struct rn_server rn_server;
+
+/* Zero in any field chooses the default. */
+typedef struct {
+    uint64_t slab_bytes;  /* the distance-slab arena, the admission budget: a request holds
+                             one region of 4 MiB per search block while it runs (default
+                             2 GiB) */
+    uint32_t workers;     /* requests on the device at once, at most (default 8) */
+    uint32_t max_blocks;  /* search blocks (slab regions) of one request, >= 2 (default 64) */
+} rn_serve_config;
+
+typedef struct {
+    uint64_t submitted, completed, failed, pending, running;
+    uint64_t pairs;               /* pairs returned by completed requests */
+    uint64_t slab_bytes, slab_bytes_in_use, slab_bytes_peak;
+    uint32_t workers, max_running;/* max_running: most requests on the device at once */
+    double p50_ms, p99_ms, max_ms, mean_ms;  /* latency, submit to result ready, over the
+                                                requests completed since the last reset */
+    double mean_queue_ms;         /* submit to admission */
+    double busy_s;                /* wall time with at least one request running */
+    double span_s;                /* first submit to last completion */
+} rn_serve_stats;
+
+/*
+ * rn_serve_create -- a server of distance joins and k-closest-pairs requests over one
+ * resident graph (the queries of Section 1 and Algorithm 2, answered as by
+ * rn_distance_join and rn_kcp).  Requests are admitted first come, first served as soon
+ * as a worker and enough contiguous slab regions are free (a request of |R| sources
+ * takes min(max_blocks, max(2, ceil(|R| / tile width))) regions); every admitted request
+ * runs at once on its own stream with its own slab regions, so requests that arrive
+ * while others run overlap with them on the device.  A request's result is the same as
+ * the query run alone.  The graph must outlive the server; its own queries (rn_*_join,
+ * rn_kcp) may run beside the server's.  RN_EINVAL for bad sizes, RN_ENOMEM when the
+ * arena cannot be allocated.
+ */
+rn_status rn_serve_create(const rn_graph *g, const rn_serve_config *cfg, rn_server **out);
+/* Queue one request; *ticket identifies it to rn_serve_wait.  RN_EINVAL for a bad
+ * request (as rn_distance_join / rn_kcp), found before it is queued. */
+rn_status rn_serve_submit(rn_server *s, const rn_request *q, uint64_t *ticket);
+/* Wait up to timeout_ms (0: do not wait; 0xFFFFFFFF: no limit) for a request; on
+ * success its pairs go to *out (free with rn_pairs_free) and the ticket is spent.
+ * RN_ETIMEOUT if it is not done in time (the ticket stays valid); RN_EINVAL for an
+ * unknown or spent ticket; otherwise the request's own status. */
+rn_status rn_serve_wait(rn_server *s, uint64_t ticket, uint32_t timeout_ms, rn_pairs *out);
+rn_status rn_serve_stats_get(rn_server *s, rn_serve_stats *out);
+/* Start a new measurement window: latency samples, counters of completed requests,
+ * busy time and span restart (pending and running requests are kept). */
+rn_status rn_serve_reset_stats(rn_server *s);
+/* Stop the server: running requests finish, queued ones are dropped, uncollected
+ * results freed. */
+void rn_serve_destroy(rn_server *s);
+
 void rn_pairs_free(rn_pairs *p);
 void rn_dpairs_free(rn_dpairs *p);
 

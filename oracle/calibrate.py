@@ -42,17 +42,40 @@ def theta_for_matches(g: O.OGraph, R, S, t: int, sample: int) -> tuple[int, list
     return int(np.median(ds)), ds
 
 
-def main() -> None:
-    """Recompute every stored workload parameter (about half a minute)."""
+def main(parts: list[str] | None = None) -> None:
+    """Recompute the stored workload parameters: every part (a few minutes), or only the
+    parts named (grid, road264k, road1070k, batch, serve)."""
     o = O.default()
     out = {}
     t0 = time.time()
+    want = (lambda name: not parts or name in parts)
+    if want("grid"):
+        _grid(o, out)
+    if want("road264k"):
+        _road264k(o, out, t0)
+    if want("road1070k"):
+        _road1070k(o, out, t0)
+    if want("batch"):
+        _batch(o, out, t0)
+    if want("serve"):
+        _serve(o, out, t0)
+    os.makedirs(os.path.dirname(OUT), exist_ok=True)
+    old = json.load(open(OUT)) if os.path.exists(OUT) else {}
+    old.update(out)
+    with open(OUT, "w") as f:
+        json.dump(old, f, indent=1, sort_keys=True)
+        f.write("\n")
+
+
+def _grid(o, out) -> None:
     w = I.c1_grid_join()
     g = o.graph(w.graph.n, w.graph.src, w.graph.dst, w.graph.w)
     full = g.join(w.R, w.S, w.theta)
     out["grid4096_theta1500"] = {"theta": 1500, "pairs": len(full), "alg_arcs": full.arcs,
                                  "graph": graph_digest(w.graph)}
 
+
+def _road264k(o, out, t0) -> None:
     w = I.c2_road_join(None)
     g = o.graph(w.graph.n, w.graph.src, w.graph.dst, w.graph.w)
     th, _ = theta_for_matches(g, w.R, w.S, 50, 256)
@@ -64,6 +87,8 @@ def main() -> None:
                             "graph": graph_digest(w.graph)}
     print("road264k_join theta", th, f"{time.time() - t0:.1f}s", flush=True)
 
+
+def _road1070k(o, out, t0) -> None:
     w = I.c3_road_clustered()
     g = o.graph(w.graph.n, w.graph.src, w.graph.dst, w.graph.w)
     th, _ = theta_for_matches(g, w.R, w.S, 50, 256)
@@ -71,6 +96,8 @@ def main() -> None:
                                   "k": [100, 10_000, 1_000_000], "graph": graph_digest(w.graph)}
     print("road1070k_clustered theta", th, f"{time.time() - t0:.1f}s", flush=True)
 
+
+def _batch(o, out, t0) -> None:
     # the batch: theta per instance for its target matches per R node (32 sampled R);
     # an instance whose sampled sources reach fewer S nodes than the target gets the
     # largest distance its samples reached
@@ -91,13 +118,24 @@ def main() -> None:
     out["batch512"] = {"theta": thetas, "sample": 32, "graph_wsum": digests}
     print("batch512", len(thetas), f"{time.time() - t0:.1f}s", flush=True)
 
-    os.makedirs(os.path.dirname(OUT), exist_ok=True)
-    old = json.load(open(OUT)) if os.path.exists(OUT) else {}
-    old.update(out)
-    with open(OUT, "w") as f:
-        json.dump(old, f, indent=1, sort_keys=True)
-        f.write("\n")
+
+def _serve(o, out, t0) -> None:
+    # serving: ball growth of the 6M-node graph, nodes within theta ~ c * theta^2, from
+    # the oracle's distances of 32 sampled sources at radii holding 1k..50k nodes
+    e = I.c5_serve_graph()
+    g = o.graph(e.n, e.src, e.dst, e.w)
+    rng = np.random.default_rng(I.BASE_SEED + 6)
+    ratios = []
+    for u in rng.choice(e.n, size=32, replace=False):
+        dist, _ = g.sssp(int(u), 3_000_000)
+        d = np.sort(dist[dist <= 3_000_000].astype(np.float64))
+        for b in (1_000, 2_000, 4_000, 8_000, 16_000, 32_000, 50_000):
+            if len(d) > b and d[b - 1] > 0:
+                ratios.append(b / d[b - 1] ** 2)
+    out["serve6m"] = {"ball_coeff": float(np.median(ratios)), "samples": len(ratios),
+                      "graph": graph_digest(e)}
+    print("serve6m ball_coeff", out["serve6m"]["ball_coeff"], f"{time.time() - t0:.1f}s", flush=True)
 
 
 if __name__ == "__main__":
-    main()
+    main(sys.argv[1:])

@@ -12,6 +12,34 @@
 
 #include "rn_internal.h"
 
+namespace rn {
+
+// Device pairs -> host arrays owned by the library (rn_pairs_free releases them).
+void to_host_pairs(const rn_dpairs &d, rn_pairs *out, void *stream) {
+    cudaStream_t st = (cudaStream_t)stream;
+    out->n = d.n;
+    size_t b = std::max<uint64_t>(d.n, 1) * 4;
+    out->u = (uint32_t *)std::malloc(b);
+    out->v = (uint32_t *)std::malloc(b);
+    out->d = (uint32_t *)std::malloc(b);
+    if (!out->u || !out->v || !out->d) {
+        rn_pairs_free(out);
+        fail(RN_ENOMEM, "host result allocation failed");
+    }
+    if (d.n) {
+        cudaMemcpyAsync(out->u, d.u, d.n * 4, cudaMemcpyDeviceToHost, st);
+        cudaMemcpyAsync(out->v, d.v, d.n * 4, cudaMemcpyDeviceToHost, st);
+        cudaMemcpyAsync(out->d, d.d, d.n * 4, cudaMemcpyDeviceToHost, st);
+        cudaError_t e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess) {
+            rn_pairs_free(out);
+            fail(RN_ECUDA, std::string("copying pairs to the host: ") + cudaGetErrorString(e));
+        }
+    }
+}
+
+}  // namespace rn
+
 namespace {
 
 thread_local std::string g_last_error;
@@ -70,27 +98,6 @@ void ensure(uint32_t **p, uint32_t *cap, uint32_t want) {
     *p = (uint32_t *)rn::device_alloc(size_t(*cap) * 4);
 }
 
-void to_host_pairs(const rn_dpairs &d, rn_pairs *out, cudaStream_t st) {
-    out->n = d.n;
-    size_t b = std::max<uint64_t>(d.n, 1) * 4;
-    out->u = (uint32_t *)std::malloc(b);
-    out->v = (uint32_t *)std::malloc(b);
-    out->d = (uint32_t *)std::malloc(b);
-    if (!out->u || !out->v || !out->d) {
-        rn_pairs_free(out);
-        rn::fail(RN_ENOMEM, "host result allocation failed");
-    }
-    if (d.n) {
-        cudaMemcpyAsync(out->u, d.u, d.n * 4, cudaMemcpyDeviceToHost, st);
-        cudaMemcpyAsync(out->v, d.v, d.n * 4, cudaMemcpyDeviceToHost, st);
-        cudaMemcpyAsync(out->d, d.d, d.n * 4, cudaMemcpyDeviceToHost, st);
-        cudaError_t e = cudaStreamSynchronize(st);
-        if (e != cudaSuccess) {
-            rn_pairs_free(out);
-            rn::fail(RN_ECUDA, std::string("copying pairs to the host: ") + cudaGetErrorString(e));
-        }
-    }
-}
 
 }  // namespace
 
@@ -296,7 +303,7 @@ rn_status rn_distance_join(const rn_graph *cg, const uint32_t *R, uint32_t nR, c
         rn_query_stats st{};
         rn::run_join(g->dev, g->ws, g->cfg, g->info.median_weight, hs.dR, nR, hs.dS, nS, theta, &hs.res,
                      (void *)hs.stream, &st);
-        to_host_pairs(hs.res, out, (cudaStream_t)hs.stream);
+        rn::to_host_pairs(hs.res, out, hs.stream);
         g_last_stats = st;
         g_have_stats = true;
     });
@@ -337,7 +344,7 @@ rn_status rn_kcp(const rn_graph *cg, const uint32_t *R, uint32_t nR, const uint3
         rn_query_stats st{};
         rn::run_kcp(g->dev, g->ws, g->cfg, g->info.median_weight, hs.dR, nR, hs.dS, nS, k, theta, &hs.res,
                     (void *)hs.stream, &st);
-        to_host_pairs(hs.res, out, (cudaStream_t)hs.stream);
+        rn::to_host_pairs(hs.res, out, hs.stream);
         g_last_stats = st;
         g_have_stats = true;
     });
@@ -418,7 +425,7 @@ rn_status rn_batch_pairs(const rn_batch *h, uint32_t i, rn_pairs *out) {
         uint64_t n = 0;
         rn::batch_pairs_dev(h->b, i, &u, &v, &d, &n);
         rn_dpairs view{const_cast<uint32_t *>(u), const_cast<uint32_t *>(v), const_cast<uint32_t *>(d), n, n};
-        to_host_pairs(view, out, nullptr);
+        rn::to_host_pairs(view, out, nullptr);
     });
 }
 
@@ -452,7 +459,7 @@ rn_status rn_join_batch(const rn_query *q, uint32_t nq, rn_pairs *outs) {
                 uint64_t n = 0;
                 rn::batch_pairs_dev(h.b, i, &u, &v, &d, &n);
                 rn_dpairs view{const_cast<uint32_t *>(u), const_cast<uint32_t *>(v), const_cast<uint32_t *>(d), n, n};
-                to_host_pairs(view, &outs[i], nullptr);
+                rn::to_host_pairs(view, &outs[i], nullptr);
             }
         } catch (...) {
             for (uint32_t i = 0; i < nq; i++) rn_pairs_free(&outs[i]);
@@ -463,6 +470,64 @@ rn_status rn_join_batch(const rn_query *q, uint32_t nq, rn_pairs *outs) {
         rn::batch_destroy(h.b);
         h.b = nullptr;
     });
+}
+
+struct rn_server {
+    rn::Server *s = nullptr;
+    uint32_t n = 0;
+};
+
+rn_status rn_serve_create(const rn_graph *g, const rn_serve_config *cfg, rn_server **out) {
+    return guarded([&] {
+        if (!g || !out) rn::fail(RN_EINVAL, "null argument");
+        *out = nullptr;
+        rn_serve_config c{};
+        if (cfg) c = *cfg;
+        auto h = std::make_unique<rn_server>();
+        h->n = g->dev.n;
+        h->s = rn::server_create(g, c.slab_bytes, c.workers, c.max_blocks);
+        *out = h.release();
+    });
+}
+
+rn_status rn_serve_submit(rn_server *h, const rn_request *q, uint64_t *ticket) {
+    return guarded([&] {
+        if (!h || !h->s || !q || !ticket) rn::fail(RN_EINVAL, "null argument");
+        check_theta(q->theta);
+        check_sets_host(h->n, q->R, q->nR, q->S, q->nS);
+        *ticket = rn::server_submit(h->s, q->R, q->nR, q->S, q->nS, q->theta, q->k);
+    });
+}
+
+rn_status rn_serve_wait(rn_server *h, uint64_t ticket, uint32_t timeout_ms, rn_pairs *out) {
+    return guarded([&] {
+        if (!h || !h->s || !out) rn::fail(RN_EINVAL, "null argument");
+        *out = rn_pairs{};
+        rn::server_wait(h->s, ticket, timeout_ms, out);
+    });
+}
+
+rn_status rn_serve_stats_get(rn_server *h, rn_serve_stats *out) {
+    return guarded([&] {
+        if (!h || !h->s || !out) rn::fail(RN_EINVAL, "null argument");
+        rn::server_stats(h->s, out);
+    });
+}
+
+rn_status rn_serve_reset_stats(rn_server *h) {
+    return guarded([&] {
+        if (!h || !h->s) rn::fail(RN_EINVAL, "null argument");
+        rn::server_reset_stats(h->s);
+    });
+}
+
+void rn_serve_destroy(rn_server *h) {
+    if (!h) return;
+    try {
+        rn::server_destroy(h->s);
+    } catch (...) {
+    }
+    delete h;
 }
 
 void rn_pairs_free(rn_pairs *p) {

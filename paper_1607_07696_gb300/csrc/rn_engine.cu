@@ -181,7 +181,8 @@ struct DeviceShared {
     std::mutex mu;
     uint32_t *slab = nullptr;
     size_t slab_bytes = 0;
-    uint32_t slab_ctas = 0;
+    uint32_t slab_ctas = 0;   // narrow-block regions the slab holds
+    bool external = false;    // the slab belongs to someone else (a server's arena)
     uint32_t *gretry = nullptr;
     size_t gretry_bytes = 0;
 };
@@ -208,6 +209,7 @@ struct Workspace {
     uint32_t *hist = nullptr;
     size_t hist_cap = 0;
     cudaEvent_t ev0 = nullptr, ev1 = nullptr, evs0 = nullptr, evs1 = nullptr;
+    DeviceShared *own_sh = nullptr;  // a slab of its own (workspace_set_slab), else null
     cudaEvent_t evr = nullptr;  // end of the last retry launch
     float retry_ms = 0;
     // a workspace may own its global-map buffer instead of using the device's
@@ -275,10 +277,30 @@ void workspace_destroy(Workspace *ws) {
     if (ws->evs1) cudaEventDestroy(ws->evs1);
     if (ws->evr) cudaEventDestroy(ws->evr);
     device_free(ws->own_gmap);
+    if (ws->own_sh) {
+        device_free(ws->own_sh->gretry);
+        delete ws->own_sh;
+    }
     delete ws;
 }
 
 uint64_t workspace_bytes(const Workspace *ws) { return ws ? ws->bytes : 0; }
+
+size_t slab_region_bytes() { return size_t(SMEM_H) * 128 * 4; }
+
+// Give the workspace a slab of its own: `regions` narrow-block regions (at least two,
+// so a wide block fits) at `slab`, which the caller owns and keeps every row of at INF
+// between queries (the search leaves the rows it used at INF).  Its queries then need
+// no device-wide lock and may overlap with other workspaces' queries on the device.
+void workspace_set_slab(Workspace *ws, uint32_t *slab, uint32_t regions) {
+    if (regions < 2 || !slab) fail(RN_EINVAL, "a workspace slab needs at least two regions");
+    if (!ws->own_sh) ws->own_sh = new DeviceShared();
+    ws->own_sh->external = true;
+    ws->own_sh->slab = slab;
+    ws->own_sh->slab_ctas = regions;
+    ws->own_sh->slab_bytes = size_t(regions) * slab_region_bytes();
+    ws->sh = ws->own_sh;
+}
 
 template <class T>
 static void grow(Workspace *ws, T **p, uint64_t *cap, uint64_t want, uint64_t elem) {
@@ -1250,8 +1272,8 @@ static void launch_gmap(const DeviceGraph &g, Workspace *ws, uint32_t T, SearchA
     (void)g;
     const size_t per_block = (3 * H + H * T) * 4;
     const size_t budget = size_t(8) << 30;
-    const uint32_t rgrid =
-        uint32_t(std::max<size_t>(1, std::min<size_t>({size_t(n), size_t(ws->num_sms), budget / per_block})));
+    const uint32_t rgrid = uint32_t(std::max<size_t>(
+        1, std::min<size_t>({size_t(n), size_t(ws->num_sms), size_t(ws->sh->slab_ctas), budget / per_block})));
     uint32_t **buf = ws->own_gmap_enabled ? &ws->own_gmap : &ws->sh->gretry;
     size_t *bytes = ws->own_gmap_enabled ? &ws->own_gmap_bytes : &ws->sh->gretry_bytes;
     if (*bytes < per_block * rgrid) {
@@ -1278,7 +1300,9 @@ static void launch_gmap(const DeviceGraph &g, Workspace *ws, uint32_t T, SearchA
 // overflow.
 static Control search_all(const DeviceGraph &g, Workspace *ws, uint32_t T, SearchArgs a,
                           uint32_t ntiles, cudaStream_t st, uint64_t *retried, uint32_t map_slots = 0) {
-    const uint32_t grid_max = uint32_t(ws->num_sms) * CTAS_PER_SM;
+    // narrow blocks: one slab region each; wide blocks: two regions each
+    const uint32_t grid_max = ws->sh->slab_ctas;
+    const uint32_t grid_wide = std::max<uint32_t>(1, std::min<uint32_t>(grid_max / 2, uint32_t(ws->num_sms)));
     a.slab = ws->sh->slab;
     if (ntiles && (!a.src || !a.slab || !a.sbits || !a.out_key || !a.out_d || !a.row_ptr || !a.adj || !a.ctl))
         fail(RN_EINTERNAL, "tile search without its buffers");
@@ -1297,7 +1321,7 @@ static Control search_all(const DeviceGraph &g, Workspace *ws, uint32_t T, Searc
     RN_CUDA(cudaEventRecord(ws->evs0, st));
     if (ntiles) {
         if (H == SMEM_H) search(T, Shape::Narrow, a, std::max<uint32_t>(1, std::min(ntiles, grid_max)), st);
-        else if (H == SMEM_HW) search(T, Shape::Wide, a, std::max<uint32_t>(1, std::min(ntiles, uint32_t(ws->num_sms))), st);
+        else if (H == SMEM_HW) search(T, Shape::Wide, a, std::max<uint32_t>(1, std::min(ntiles, grid_wide)), st);
         else launch_gmap(g, ws, T, a, H, ntiles, st);
         ws->launches++;
         ws->blocks_per_sm = H > SMEM_H ? 1 : T == 32 ? search_occupancy<1>() : T == 64 ? search_occupancy<2>() : search_occupancy<4>();
@@ -1317,12 +1341,12 @@ static Control search_all(const DeviceGraph &g, Workspace *ws, uint32_t T, Searc
         r.failed = next;
         if (H == SMEM_H) {
             // wide blocks reuse the slab: it holds grid_max regions of SMEM_H rows,
-            // that is num_sms regions of SMEM_HW rows
+            // that is grid_max / 2 regions of SMEM_HW rows
             H = SMEM_HW;
             r.H = SMEM_HW;
             r.hshift = 32 - bits_for(SMEM_HW);
             r.max_fill = SMEM_HW * 7 / 8;
-            search(T, Shape::Wide, r, std::min<uint32_t>(nf, uint32_t(ws->num_sms)), st);
+            search(T, Shape::Wide, r, std::min<uint32_t>(nf, grid_wide), st);
         } else {
             H = std::min<uint64_t>(H * 4, hcap);
             launch_gmap(g, ws, T, r, H, nf, st);
@@ -1374,6 +1398,10 @@ static void ensure_pairs(Workspace *ws, uint64_t want) {
 static void ensure_slab(Workspace *ws) {
     const uint32_t grid_max = uint32_t(ws->num_sms) * CTAS_PER_SM;
     DeviceShared *sh = ws->sh;
+    if (sh->external) {
+        if (!sh->slab || sh->slab_ctas < 2) fail(RN_EINTERNAL, "workspace slab not set");
+        return;
+    }
     if (sh->slab && sh->slab_ctas >= grid_max) return;
     device_free(sh->slab);
     sh->slab = nullptr;
@@ -1434,7 +1462,8 @@ void run_join(const DeviceGraph &g, Workspace *ws, const EngineConfig &cfg, uint
     prep_sets(g, ws, dR, nR, dS, nS, st);
     // sources per tile: as many as fit a row, but spread so the tiles fill the resident
     // blocks in whole waves (a last wave of a few tiles would double the search time)
-    const uint32_t grid_max = uint32_t(ws->num_sms) * CTAS_PER_SM;
+    ensure_slab(ws);
+    const uint32_t grid_max = ws->sh->slab_ctas;  // resident narrow blocks the slab serves
     uint32_t tile_src = T;
     if (nR) {
         const uint64_t waves = (uint64_t(nR) + uint64_t(T) * grid_max - 1) / (uint64_t(T) * grid_max);
@@ -1444,7 +1473,6 @@ void run_join(const DeviceGraph &g, Workspace *ws, const EngineConfig &cfg, uint
     const uint32_t ntiles = (nR + tile_src - 1) / tile_src;
     ensure_u32(&ws->failed, &ws->failed_cap, std::max<uint32_t>(ntiles, 1));
     ensure_u32(&ws->failed2, &ws->failed2_cap, std::max<uint32_t>(ntiles, 1));
-    ensure_slab(ws);
     ensure_pairs(ws, std::max<uint64_t>(ws->pair_cap, uint64_t(nR) * 64));
 
     const uint32_t vbits = bits_for(g.n);
@@ -1786,7 +1814,8 @@ void run_kcp(const DeviceGraph &g, Workspace *ws, const EngineConfig &cfg, uint3
     ws->launches = 0;
     RN_CUDA(cudaEventRecord(ws->ev0, st));
 
-    const uint32_t grid_max = uint32_t(ws->num_sms) * CTAS_PER_SM;
+    ensure_slab(ws);
+    const uint32_t grid_max = ws->sh->slab_ctas;  // resident narrow blocks the slab serves
     uint32_t tile_src = T;
     if (nR) {
         const uint64_t waves = (uint64_t(nR) + uint64_t(T) * grid_max - 1) / (uint64_t(T) * grid_max);
@@ -1796,7 +1825,6 @@ void run_kcp(const DeviceGraph &g, Workspace *ws, const EngineConfig &cfg, uint3
     const uint32_t ntiles = (nR + tile_src - 1) / tile_src;
     ensure_u32(&ws->failed, &ws->failed_cap, std::max<uint32_t>(ntiles, 1));
     ensure_u32(&ws->failed2, &ws->failed2_cap, std::max<uint32_t>(ntiles, 1));
-    ensure_slab(ws);
     ensure_pairs(ws, std::max<uint64_t>(ws->pair_cap, std::min<uint64_t>(k + (k >> 2) + 4096, uint64_t(nR) * 64 + 4096)));
     if (!ws->kcp) {
         ws->kcp = (uint32_t *)device_alloc((KCP_BINS + 16) * 4 + sizeof(SelState));

@@ -97,6 +97,24 @@ void batch_pairs_dev(const Batch *b, uint32_t i, const uint32_t **u, const uint3
 const rn_batch_stats &batch_stats(const Batch *b);
 void batch_destroy(Batch *b);
 
+// Workspaces with a slab of their own (servers, rn_engine.cu).
+size_t slab_region_bytes();
+void workspace_set_slab(Workspace *ws, uint32_t *slab, uint32_t regions);
+
+// Request servers (rn_serve.cpp): the graph must outlive its server.
+struct Server;
+Server *server_create(const rn_graph *g, uint64_t slab_bytes, uint32_t workers, uint32_t max_blocks);
+uint64_t server_submit(Server *s, const uint32_t *R, uint32_t nR, const uint32_t *S, uint32_t nS, uint32_t theta,
+                       uint64_t k);
+// Throws Error(RN_ETIMEOUT) when not done in time, or the request's own error.
+void server_wait(Server *s, uint64_t ticket, uint32_t timeout_ms, rn_pairs *out);
+void server_stats(Server *s, rn_serve_stats *out);
+void server_reset_stats(Server *s);
+void server_destroy(Server *s);
+
+// Device pairs -> library-owned host pairs (rn_pairs_free releases them).
+void to_host_pairs(const rn_dpairs &d, rn_pairs *out, void *stream);
+
 void upload_graph(const HostGraph &g, const std::vector<uint32_t> &perm,
                   const std::vector<uint32_t> &iperm, DeviceGraph *out);
 void free_graph(DeviceGraph *g);

@@ -1,0 +1,340 @@
+// rn_serve.cpp -- serving distance joins and k-closest-pairs requests over one resident
+// graph with continuous batching.
+//
+// A server owns an arena of distance-slab regions (the admission budget) and a pool of
+// worker threads, each with its own engine workspace and CUDA stream.  Requests queue
+// first come, first served; the head of the queue is admitted as soon as a worker is
+// idle and enough contiguous slab regions are free.  An admitted request runs the
+// engine's whole query (set preparation, tile search, emission, sort; for k closest
+// pairs the radius passes and the select) on its worker's stream, with a search grid of
+// as many blocks as it holds regions, so the kernels of every running request share the
+// device: a request that arrives while others run starts at once if it fits, and its
+// work overlaps theirs.  No kernel waits on another or on the host; the overlap comes
+// from independent streams only.  A request's result does not depend on what else runs:
+// it is computed by the same kernels on its own buffers.
+#include <algorithm>
+#include <chrono>
+#include <condition_variable>
+#include <deque>
+#include <memory>
+#include <thread>
+#include <unordered_map>
+
+#include <cuda_runtime.h>
+
+#include "rn_internal.h"
+
+namespace rn {
+
+namespace {
+
+using Clock = std::chrono::steady_clock;
+
+double ms_between(Clock::time_point a, Clock::time_point b) {
+    return std::chrono::duration<double, std::milli>(b - a).count();
+}
+
+struct Request {
+    uint64_t ticket = 0;
+    std::vector<uint32_t> R, S;
+    uint32_t theta = 0;
+    uint64_t k = 0;
+    uint32_t units = 0, unit_off = 0;
+    Clock::time_point t_submit, t_admit, t_done;
+    bool done = false;
+    rn_status status = RN_OK;
+    std::string err;
+    rn_pairs out{};
+};
+
+struct Worker {
+    Workspace *ws = nullptr;
+    cudaStream_t stream = nullptr;
+    uint32_t *dR = nullptr, *dS = nullptr;
+    uint32_t capR = 0, capS = 0;
+    rn_dpairs res{};
+    std::thread th;
+};
+
+void check(cudaError_t e, const char *what) {
+    if (e != cudaSuccess)
+        fail(e == cudaErrorMemoryAllocation ? RN_ENOMEM : RN_ECUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+void ensure_u32(uint32_t **p, uint32_t *cap, uint32_t want) {
+    if (*p && *cap >= want) return;
+    device_free(*p);
+    *p = nullptr;
+    *cap = std::max<uint32_t>(want, 4096);
+    *p = (uint32_t *)device_alloc(size_t(*cap) * 4);
+}
+
+}  // namespace
+
+struct Server {
+    const rn_graph *g = nullptr;
+    int device = 0;
+    uint32_t tile_width = 32, max_blocks = 64;
+    uint32_t *arena = nullptr;
+    uint32_t units_total = 0;
+    size_t unit_words = 0;
+    std::vector<uint8_t> unit_busy;
+    std::vector<Worker> workers;
+
+    std::mutex mu;
+    std::condition_variable cv_work, cv_done;
+    std::deque<std::shared_ptr<Request>> pending;
+    std::unordered_map<uint64_t, std::shared_ptr<Request>> reqs;
+    uint64_t next_ticket = 1;
+    bool stop = false;
+
+    // statistics of the current window
+    uint64_t submitted = 0, completed = 0, failed = 0, pairs = 0;
+    uint32_t running = 0, max_running = 0, units_in_use = 0, units_peak = 0;
+    std::vector<double> latency_ms;
+    double queue_ms = 0, busy_s = 0;
+    bool have_first = false;
+    Clock::time_point first_submit, last_done, busy_since;
+
+    // First fit of n contiguous free regions; false if none.
+    bool fit(uint32_t n, uint32_t *off) const {
+        uint32_t run = 0;
+        for (uint32_t i = 0; i < units_total; i++) {
+            run = unit_busy[i] ? 0 : run + 1;
+            if (run == n) {
+                *off = i + 1 - n;
+                return true;
+            }
+        }
+        return false;
+    }
+
+    void loop(Worker *w);
+    void execute(Worker *w, Request *q);
+};
+
+void Server::execute(Worker *w, Request *q) {
+    const rn_graph *G = g;
+    workspace_set_slab(w->ws, arena + size_t(q->unit_off) * unit_words, q->units);
+    const uint32_t nR = uint32_t(q->R.size()), nS = uint32_t(q->S.size());
+    ensure_u32(&w->dR, &w->capR, std::max<uint32_t>(nR, 1));
+    ensure_u32(&w->dS, &w->capS, std::max<uint32_t>(nS, 1));
+    if (nR) copy_to_device(w->dR, q->R.data(), size_t(nR) * 4, w->stream);
+    if (nS) copy_to_device(w->dS, q->S.data(), size_t(nS) * 4, w->stream);
+    rn_query_stats st{};
+    if (q->k == 0)
+        run_join(G->dev, w->ws, G->cfg, G->info.median_weight, w->dR, nR, w->dS, nS, q->theta, &w->res, w->stream,
+                 &st);
+    else
+        run_kcp(G->dev, w->ws, G->cfg, G->info.median_weight, w->dR, nR, w->dS, nS, q->k, q->theta, &w->res,
+                w->stream, &st);
+    to_host_pairs(w->res, &q->out, w->stream);
+}
+
+void Server::loop(Worker *w) {
+    cudaSetDevice(device);  // the current device is per host thread
+    for (;;) {
+        std::shared_ptr<Request> q;
+        {
+            std::unique_lock<std::mutex> lk(mu);
+            uint32_t off = 0;
+            cv_work.wait(lk, [&] { return stop || (!pending.empty() && fit(pending.front()->units, &off)); });
+            if (stop) return;
+            q = pending.front();
+            pending.pop_front();
+            q->unit_off = off;
+            for (uint32_t i = 0; i < q->units; i++) unit_busy[off + i] = 1;
+            units_in_use += q->units;
+            units_peak = std::max(units_peak, units_in_use);
+            q->t_admit = Clock::now();
+            if (running++ == 0) busy_since = q->t_admit;
+            max_running = std::max(max_running, running);
+        }
+        try {
+            execute(w, q.get());
+        } catch (const Error &e) {
+            q->status = e.status;
+            q->err = e.msg;
+        } catch (const std::bad_alloc &) {
+            q->status = RN_ENOMEM;
+            q->err = "host allocation failed";
+        } catch (const std::exception &e) {
+            q->status = RN_EINTERNAL;
+            q->err = e.what();
+        }
+        {
+            std::lock_guard<std::mutex> lk(mu);
+            for (uint32_t i = 0; i < q->units; i++) unit_busy[q->unit_off + i] = 0;
+            units_in_use -= q->units;
+            q->t_done = Clock::now();
+            q->done = true;
+            if (--running == 0) busy_s += ms_between(busy_since, q->t_done) / 1e3;
+            last_done = q->t_done;
+            if (q->status == RN_OK) {
+                completed++;
+                pairs += q->out.n;
+                latency_ms.push_back(ms_between(q->t_submit, q->t_done));
+                queue_ms += ms_between(q->t_submit, q->t_admit);
+            } else {
+                failed++;
+            }
+        }
+        cv_done.notify_all();
+        cv_work.notify_all();
+    }
+}
+
+Server *server_create(const rn_graph *g, uint64_t slab_bytes, uint32_t workers, uint32_t max_blocks) {
+    auto s = std::make_unique<Server>();
+    s->g = g;
+    s->device = g->device;
+    check(cudaSetDevice(g->device), "cudaSetDevice");
+    s->tile_width = g->cfg.tile_width ? g->cfg.tile_width : 32;
+    s->max_blocks = max_blocks ? max_blocks : 64;
+    if (s->max_blocks < 2) fail(RN_EINVAL, "max_blocks must be >= 2");
+    const uint32_t nworkers = workers ? workers : 8;
+    if (nworkers > 256) fail(RN_EINVAL, "at most 256 workers");
+    const size_t region = slab_region_bytes();
+    const uint64_t bytes = slab_bytes ? slab_bytes : (uint64_t(2) << 30);
+    s->units_total = uint32_t(std::min<uint64_t>(bytes / region, 1u << 20));
+    if (s->units_total < s->max_blocks)
+        fail(RN_EINVAL, "slab_bytes must hold max_blocks regions of " + std::to_string(region) + " bytes");
+    s->unit_words = region / 4;
+    s->unit_busy.assign(s->units_total, 0);
+    s->arena = (uint32_t *)device_alloc(size_t(s->units_total) * region);
+    check(cudaMemset(s->arena, 0xFF, size_t(s->units_total) * region), "cudaMemset");  // every row INF
+    check(cudaDeviceSynchronize(), "cudaDeviceSynchronize");  // before any worker's stream uses it
+    s->workers.resize(nworkers);
+    try {
+        for (auto &w : s->workers) {
+            w.ws = workspace_create(g->dev);
+            check(cudaStreamCreateWithFlags(&w.stream, cudaStreamNonBlocking), "cudaStreamCreateWithFlags");
+        }
+        for (auto &w : s->workers) {
+            Worker *wp = &w;
+            Server *sp = s.get();
+            w.th = std::thread([sp, wp] { sp->loop(wp); });
+        }
+    } catch (...) {
+        server_destroy(s.release());
+        throw;
+    }
+    return s.release();
+}
+
+uint64_t server_submit(Server *s, const uint32_t *R, uint32_t nR, const uint32_t *S, uint32_t nS, uint32_t theta,
+                       uint64_t k) {
+    auto q = std::make_shared<Request>();
+    q->R.assign(R, R + nR);
+    q->S.assign(S, S + nS);
+    q->theta = theta;
+    q->k = k;
+    const uint32_t T = s->tile_width;
+    q->units = std::min<uint32_t>(s->max_blocks, std::max<uint32_t>(2, (nR + T - 1) / T));
+    {
+        std::lock_guard<std::mutex> lk(s->mu);
+        if (s->stop) fail(RN_ECANCELLED, "the server is stopping");
+        q->ticket = s->next_ticket++;
+        q->t_submit = Clock::now();
+        if (!s->have_first) {
+            s->first_submit = q->t_submit;
+            s->have_first = true;
+        }
+        s->submitted++;
+        s->reqs[q->ticket] = q;
+        s->pending.push_back(q);
+    }
+    s->cv_work.notify_all();
+    return q->ticket;
+}
+
+void server_wait(Server *s, uint64_t ticket, uint32_t timeout_ms, rn_pairs *out) {
+    std::shared_ptr<Request> q;
+    {
+        std::unique_lock<std::mutex> lk(s->mu);
+        auto it = s->reqs.find(ticket);
+        if (it == s->reqs.end()) fail(RN_EINVAL, "unknown ticket (never issued, or already collected)");
+        q = it->second;
+        auto ready = [&] { return q->done; };
+        if (timeout_ms == 0xFFFFFFFFu) s->cv_done.wait(lk, ready);
+        else if (!s->cv_done.wait_for(lk, std::chrono::milliseconds(timeout_ms), ready))
+            fail(RN_ETIMEOUT, "request " + std::to_string(ticket) + " not done within " + std::to_string(timeout_ms) +
+                                  " ms");
+        s->reqs.erase(ticket);
+    }
+    if (q->status != RN_OK) fail(q->status, q->err);
+    *out = q->out;
+    q->out = rn_pairs{};
+}
+
+void server_stats(Server *s, rn_serve_stats *out) {
+    std::lock_guard<std::mutex> lk(s->mu);
+    rn_serve_stats r{};
+    r.submitted = s->submitted;
+    r.completed = s->completed;
+    r.failed = s->failed;
+    r.pending = s->pending.size();
+    r.running = s->running;
+    r.pairs = s->pairs;
+    const uint64_t region = slab_region_bytes();
+    r.slab_bytes = uint64_t(s->units_total) * region;
+    r.slab_bytes_in_use = uint64_t(s->units_in_use) * region;
+    r.slab_bytes_peak = uint64_t(s->units_peak) * region;
+    r.workers = uint32_t(s->workers.size());
+    r.max_running = s->max_running;
+    if (!s->latency_ms.empty()) {
+        std::vector<double> l = s->latency_ms;
+        std::sort(l.begin(), l.end());
+        auto pct = [&](double p) { return l[std::min<size_t>(l.size() - 1, size_t(p * double(l.size() - 1) + 0.5))]; };
+        r.p50_ms = pct(0.50);
+        r.p99_ms = pct(0.99);
+        r.max_ms = l.back();
+        double sum = 0;
+        for (double x : l) sum += x;
+        r.mean_ms = sum / double(l.size());
+        r.mean_queue_ms = s->queue_ms / double(l.size());
+    }
+    r.busy_s = s->busy_s;
+    if (s->running) r.busy_s += ms_between(s->busy_since, Clock::now()) / 1e3;
+    if (s->have_first && s->completed + s->failed) r.span_s = ms_between(s->first_submit, s->last_done) / 1e3;
+    *out = r;
+}
+
+void server_reset_stats(Server *s) {
+    std::lock_guard<std::mutex> lk(s->mu);
+    s->submitted = s->pending.size() + s->running;
+    s->completed = s->failed = s->pairs = 0;
+    s->max_running = s->running;
+    s->units_peak = s->units_in_use;
+    s->latency_ms.clear();
+    s->queue_ms = 0;
+    s->busy_s = 0;
+    if (s->running) s->busy_since = Clock::now();
+    s->have_first = false;
+}
+
+void server_destroy(Server *s) {
+    if (!s) return;
+    {
+        std::lock_guard<std::mutex> lk(s->mu);
+        s->stop = true;
+        s->pending.clear();
+    }
+    s->cv_work.notify_all();
+    for (auto &w : s->workers)
+        if (w.th.joinable()) w.th.join();
+    for (auto &kv : s->reqs) rn_pairs_free(&kv.second->out);
+    s->reqs.clear();
+    for (auto &w : s->workers) {
+        if (w.stream) cudaStreamSynchronize(w.stream);
+        workspace_destroy(w.ws);
+        device_free(w.dR);
+        device_free(w.dS);
+        dpairs_release(&w.res);
+        if (w.stream) cudaStreamDestroy(w.stream);
+    }
+    device_free(s->arena);
+    delete s;
+}
+
+}  // namespace rn

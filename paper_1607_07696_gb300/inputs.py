@@ -88,7 +88,7 @@ def _knn_table(xy: np.ndarray, k: int) -> np.ndarray:
     from scipy.spatial import cKDTree
 
     n = len(xy)
-    _, idx = cKDTree(xy).query(xy, k=min(k + 1, n))
+    _, idx = cKDTree(xy).query(xy, k=min(k + 1, n), workers=-1)  # per-point results: thread-count independent
     return np.asarray(idx).reshape(n, -1)[:, 1:]
 
 
@@ -100,7 +100,9 @@ def _knn_edges(idx: np.ndarray, k: int) -> np.ndarray:
     keep = src != dst
     a = np.minimum(src[keep], dst[keep])
     b = np.maximum(src[keep], dst[keep])
-    key = np.unique(a * n + b)
+    key = a * n + b
+    key.sort()
+    key = key[np.concatenate(([True], key[1:] != key[:-1]))] if len(key) else key
     return np.stack([key // n, key % n], axis=1)
 
 
@@ -120,8 +122,13 @@ def road_graph(n: int, m: int, seed: int, wmax: int = 10_000) -> EdgeList:
     d = xy[e[:, 0]] - xy[e[:, 1]]
     length = np.sqrt(d[:, 0] * d[:, 0] + d[:, 1] * d[:, 1])
     if len(e) > m:
-        order = np.lexsort((e[:, 1], e[:, 0], length))
-        sel = np.sort(order[:m])
+        # the m first edges in (length, a, b) order: every edge shorter than the m-th
+        # length, then the ties at that length by (a, b)
+        cut = np.partition(length, m - 1)[m - 1]
+        short = np.nonzero(length < cut)[0]
+        tie = np.nonzero(length == cut)[0]
+        tie = tie[np.lexsort((e[tie, 1], e[tie, 0]))][:m - len(short)]
+        sel = np.sort(np.concatenate([short, tie]))
         e, length = e[sel], length[sel]
     lmax = float(length.max()) if len(length) else 1.0
     w = np.clip(np.rint(wmax * length / lmax), 1, wmax)
@@ -306,3 +313,57 @@ def c4_instance(spec: BatchSpec) -> tuple[EdgeList, np.ndarray, np.ndarray]:
     g = road_graph(spec.n, spec.m, spec.graph_seed)
     R, S = disjoint_sets(g.n, spec.nR, spec.nS, spec.set_seed)
     return g, R, S
+
+
+# ---------------------------------------------------------------- serving ----
+
+C5_N, C5_M = 6_000_000, 14_000_000
+C5_BALL_CAP = 16_384  # largest expected ball (nodes) a join request is calibrated for
+
+
+def c5_serve_graph(seed: int = BASE_SEED + 4) -> EdgeList:
+    """The resident graph of the serving workload: the road-like generator at 6M nodes,
+    14M edges."""
+    return road_graph(C5_N, C5_M, seed)
+
+
+@dataclass
+class ServeRequest:
+    """One request of the serving stream: a theta-join (k = 0) or k closest pairs."""
+
+    R: np.ndarray
+    S: np.ndarray
+    theta: int
+    k: int
+    matches: float  # target S-matches per R node of a join (0 for k closest pairs)
+
+
+def c5_requests(n: int, count: int, ball_coeff: float, seed: int = BASE_SEED + 5,
+                join_frac: float = 0.7) -> list[ServeRequest]:
+    """The mixed request stream: 70% theta-joins, 30% k closest pairs; |R| and |S|
+    log-uniform in [100, 20000] (disjoint uniform nodes), k log-uniform in [10, 1e5].  A
+    join's theta targets log-uniform [5, 200] S-matches per R node: the expected ball
+    holding that many S nodes is matches * n / |S| nodes (capped at C5_BALL_CAP), and a
+    ball of b nodes has radius sqrt(b / ball_coeff) (the graph's measured ball growth,
+    about ball_coeff * theta^2 nodes within theta).  k closest pairs run unbounded."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for i in range(count):
+        nR = int(round(log_uniform(rng, 100, 20_000)))
+        nS = int(round(log_uniform(rng, 100, 20_000)))
+        R, S = disjoint_sets(n, nR, nS, seed + 1 + i)
+        if rng.random() < join_frac:
+            matches = float(log_uniform(rng, 5, 200))
+            ball = min(matches * n / nS, C5_BALL_CAP)
+            theta = int(round(np.sqrt(ball / ball_coeff)))
+            out.append(ServeRequest(R, S, theta, 0, matches))
+        else:
+            k = int(round(log_uniform(rng, 10, 100_000)))
+            out.append(ServeRequest(R, S, 0xFFFFFFFF, min(k, nR * nS), 0.0))
+    return out
+
+
+def poisson_arrivals(count: int, rate: float, seed: int) -> np.ndarray:
+    """Arrival times (s) of a Poisson stream of the given rate (per second)."""
+    rng = np.random.default_rng(seed)
+    return np.cumsum(rng.exponential(1.0 / rate, size=count))

@@ -82,6 +82,25 @@ class rn_batch_stats(C.Structure):
                 ("candidates", C.c_uint32), ("device_ms", C.c_double)]
 
 
+class rn_request(C.Structure):
+    _fields_ = [("R", C.POINTER(C.c_uint32)), ("nR", C.c_uint32), ("S", C.POINTER(C.c_uint32)),
+                ("nS", C.c_uint32), ("theta", C.c_uint32), ("k", C.c_uint64)]
+
+
+class rn_serve_config(C.Structure):
+    _fields_ = [("slab_bytes", C.c_uint64), ("workers", C.c_uint32), ("max_blocks", C.c_uint32)]
+
+
+class rn_serve_stats(C.Structure):
+    _fields_ = [("submitted", C.c_uint64), ("completed", C.c_uint64), ("failed", C.c_uint64),
+                ("pending", C.c_uint64), ("running", C.c_uint64), ("pairs", C.c_uint64),
+                ("slab_bytes", C.c_uint64), ("slab_bytes_in_use", C.c_uint64),
+                ("slab_bytes_peak", C.c_uint64), ("workers", C.c_uint32), ("max_running", C.c_uint32),
+                ("p50_ms", C.c_double), ("p99_ms", C.c_double), ("max_ms", C.c_double),
+                ("mean_ms", C.c_double), ("mean_queue_ms", C.c_double), ("busy_s", C.c_double),
+                ("span_s", C.c_double)]
+
+
 # Every symbol include/rn.h declares, with its ctypes signature (restype, argtypes).
 _P32 = C.POINTER(C.c_uint32)
 _G = C.c_void_p
@@ -114,6 +133,12 @@ SIGNATURES = {
     "rn_batch_stats_get": (C.c_int, [C.c_void_p, C.POINTER(rn_batch_stats)]),
     "rn_batch_free": (None, [C.c_void_p]),
     "rn_join_batch": (C.c_int, [C.POINTER(rn_query), C.c_uint32, C.POINTER(rn_pairs)]),
+    "rn_serve_create": (C.c_int, [_G, C.POINTER(rn_serve_config), C.POINTER(C.c_void_p)]),
+    "rn_serve_submit": (C.c_int, [C.c_void_p, C.POINTER(rn_request), C.POINTER(C.c_uint64)]),
+    "rn_serve_wait": (C.c_int, [C.c_void_p, C.c_uint64, C.c_uint32, C.POINTER(rn_pairs)]),
+    "rn_serve_stats_get": (C.c_int, [C.c_void_p, C.POINTER(rn_serve_stats)]),
+    "rn_serve_reset_stats": (C.c_int, [C.c_void_p]),
+    "rn_serve_destroy": (None, [C.c_void_p]),
     "rn_pairs_free": (None, [C.POINTER(rn_pairs)]),
     "rn_dpairs_free": (None, [C.POINTER(rn_dpairs)]),
     "rn_last_error": (C.c_char_p, []),
@@ -403,3 +428,58 @@ def rn_join_batch(queries):
     outs = (rn_pairs * len(queries))()
     _check(lib().rn_join_batch(arr, len(queries), outs))
     return [_take_pairs(outs[i]) for i in range(len(queries))]
+
+
+# ------------------------------------------------------------------ serving ----
+
+WAIT_FOREVER = 0xFFFFFFFF
+
+
+class Server:
+    """Owner of an ``rn_server*`` over one graph (kept alive as long as the server)."""
+
+    def __init__(self, handle: int, graph: Graph):
+        self.handle = C.c_void_p(handle)
+        self.graph = graph
+
+    def close(self) -> None:
+        h = getattr(self, "handle", None)
+        if h and h.value and _lib is not None:
+            _lib.rn_serve_destroy(h)
+        self.handle = None
+
+    def __del__(self):
+        self.close()
+
+
+def rn_serve_create(g: Graph, slab_bytes: int = 0, workers: int = 0, max_blocks: int = 0) -> Server:
+    cfg = rn_serve_config(int(slab_bytes), int(workers), int(max_blocks))
+    out = C.c_void_p()
+    _check(lib().rn_serve_create(g.handle, C.byref(cfg), C.byref(out)))
+    return Server(out.value, g)
+
+
+def rn_serve_submit(srv: Server, R, S, theta: int = RN_INF, k: int = 0) -> int:
+    """Queue a theta-join (k = 0) or a k-closest-pairs request; returns its ticket."""
+    r, s = _u32(R), _u32(S)
+    q = rn_request(_p32(r), len(r), _p32(s), len(s), int(theta), int(k))
+    t = C.c_uint64()
+    _check(lib().rn_serve_submit(srv.handle, C.byref(q), C.byref(t)))
+    return int(t.value)
+
+
+def rn_serve_wait(srv: Server, ticket: int, timeout_ms: int = WAIT_FOREVER):
+    """The request's (u, v, d) once done (the GIL is released while waiting)."""
+    p = rn_pairs()
+    _check(lib().rn_serve_wait(srv.handle, int(ticket), int(timeout_ms), C.byref(p)))
+    return _take_pairs(p)
+
+
+def rn_serve_stats_get(srv: Server) -> dict:
+    st = rn_serve_stats()
+    _check(lib().rn_serve_stats_get(srv.handle, C.byref(st)))
+    return {name: getattr(st, name) for name, _ in rn_serve_stats._fields_}
+
+
+def rn_serve_reset_stats(srv: Server) -> None:
+    _check(lib().rn_serve_reset_stats(srv.handle))

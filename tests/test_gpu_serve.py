@@ -1,0 +1,159 @@
+"""Serving: theta-joins and k-closest-pairs requests admitted by slab memory and run
+concurrently over one resident graph.  Every request's result must be the same in the
+mix as alone (bit-exact: the same triples in the same order) and, on samples, the same
+as the CPU oracle's.
+"""
+import threading
+
+import numpy as np
+import pytest
+
+from paper_1607_07696_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def rn():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    from paper_1607_07696_gb300 import build as B
+
+    B.build()
+    from paper_1607_07696_gb300 import rn as RN
+
+    return RN
+
+
+@pytest.fixture(scope="module")
+def world(rn):
+    e = I.road_graph(200_000, 554_000, 61)
+    g = rn.rn_graph_load(e.src, e.dst, e.w, e.n)
+    return e, g
+
+
+def mixed_requests(n, count, seed):
+    """Joins and k-closest-pairs requests of uneven sizes (|R|, |S| 20..3000)."""
+    rng = np.random.default_rng(seed)
+    reqs = []
+    for i in range(count):
+        nR = int(round(I.log_uniform(rng, 20, 3000)))
+        nS = int(round(I.log_uniform(rng, 20, 3000)))
+        R, S = I.disjoint_sets(n, nR, nS, seed * 1000 + i)
+        if rng.random() < 0.7:
+            reqs.append((R, S, int(rng.choice([0, 20_000, 80_000, 150_000, 300_000])), 0))
+        else:
+            theta = int(rng.choice([0xFFFFFFFF, 0xFFFFFFFF, 200_000]))
+            reqs.append((R, S, theta, int(round(I.log_uniform(rng, 1, 50_000)))))
+    return reqs
+
+
+def alone(rn, g, req):
+    R, S, theta, k = req
+    return rn.rn_distance_join(g, R, S, theta) if k == 0 else rn.rn_kcp(g, R, S, k, theta)
+
+
+def same(a, b):
+    return len(a[0]) == len(b[0]) and all(np.array_equal(x, y) for x, y in zip(a, b))
+
+
+def test_mix_equals_alone_and_oracle(rn, oracle, world):
+    e, g = world
+    reqs = mixed_requests(e.n, 48, 7)
+    srv = rn.rn_serve_create(g, slab_bytes=256 << 20, workers=6, max_blocks=16)
+    tickets = [rn.rn_serve_submit(srv, R, S, theta, k) for (R, S, theta, k) in reqs]
+    got = [rn.rn_serve_wait(srv, t) for t in tickets]
+    st = rn.rn_serve_stats_get(srv)
+    assert st["completed"] == len(reqs) and st["failed"] == 0
+    assert st["max_running"] >= 2, "requests never overlapped"
+    assert st["slab_bytes_peak"] <= st["slab_bytes"]
+    assert st["pairs"] == sum(len(x[0]) for x in got)
+    assert 0 < st["p50_ms"] <= st["p99_ms"] <= st["max_ms"]
+    for i, req in enumerate(reqs):
+        assert same(got[i], alone(rn, g, req)), f"request {i} differs from the same query alone"
+    og = oracle.graph(e.n, e.src, e.dst, e.w)
+    for i in (0, 5, 11, 17, 23, 40):
+        R, S, theta, k = reqs[i]
+        th = min(theta, rn.RN_THETA_MAX)
+        ref = og.join(R, S, th) if k == 0 else og.kcp(R, S, k, th)
+        u, v, d = got[i]
+        assert np.array_equal(u, ref.u) and np.array_equal(v, ref.v) and np.array_equal(d.astype(np.uint64), ref.d), \
+            f"request {i} differs from the oracle"
+    srv.close()
+
+
+def test_small_budget_queues_and_threads(rn, world):
+    # two regions per request, four regions in all, three workers: at most two requests
+    # fit at once, the rest queue; waits come from several threads
+    e, g = world
+    reqs = mixed_requests(e.n, 24, 8)
+    srv = rn.rn_serve_create(g, slab_bytes=4 * (4 << 20), workers=3, max_blocks=2)
+    tickets = [rn.rn_serve_submit(srv, R, S, theta, k) for (R, S, theta, k) in reqs]
+    got = [None] * len(reqs)
+    errors = []
+
+    def waiter(idx):
+        try:
+            for i in idx:
+                got[i] = rn.rn_serve_wait(srv, tickets[i])
+        except Exception as ex:  # noqa: BLE001 - reported below
+            errors.append(ex)
+
+    ths = [threading.Thread(target=waiter, args=(list(range(j, len(reqs), 4)),)) for j in range(4)]
+    for t in ths:
+        t.start()
+    for t in ths:
+        t.join()
+    assert not errors, errors
+    st = rn.rn_serve_stats_get(srv)
+    assert st["max_running"] <= 2 and st["slab_bytes_peak"] <= st["slab_bytes"] == 16 << 20
+    for i, req in enumerate(reqs):
+        assert same(got[i], alone(rn, g, req)), f"request {i}"
+    srv.close()
+
+
+def test_tickets_timeouts_and_errors(rn, world):
+    e, g = world
+    srv = rn.rn_serve_create(g, workers=2, max_blocks=8)
+    R, S = I.disjoint_sets(e.n, 3000, 3000, 3)
+    t_big = [rn.rn_serve_submit(srv, R, S, 300_000) for _ in range(6)]
+    try:
+        rn.rn_serve_wait(srv, t_big[-1], 0)  # may already be done
+    except rn.RNError as ex:
+        assert ex.status == rn.RN_ETIMEOUT
+    ref = rn.rn_distance_join(g, R, S, 300_000)
+    for t in t_big:
+        assert same(rn.rn_serve_wait(srv, t), ref)
+    with pytest.raises(rn.RNError) as ex:
+        rn.rn_serve_wait(srv, t_big[0])  # spent
+    assert ex.value.status == rn.RN_EINVAL
+    with pytest.raises(rn.RNError) as ex:
+        rn.rn_serve_wait(srv, 10**9)  # never issued
+    assert ex.value.status == rn.RN_EINVAL
+    with pytest.raises(rn.RNError) as ex:
+        rn.rn_serve_submit(srv, [1, 2], [2, 3], 100)  # R and S overlap
+    assert ex.value.status == rn.RN_EINVAL and "both R and S" in str(ex.value)
+    with pytest.raises(rn.RNError) as ex:
+        rn.rn_serve_submit(srv, [1], [e.n], 100)  # id >= n
+    assert ex.value.status == rn.RN_EINVAL
+    # empty sets are valid requests with empty results
+    assert len(rn.rn_serve_wait(srv, rn.rn_serve_submit(srv, [], [5], 100))[0]) == 0
+    assert len(rn.rn_serve_wait(srv, rn.rn_serve_submit(srv, [5], [], 100, k=3))[0]) == 0
+    rn.rn_serve_reset_stats(srv)
+    st = rn.rn_serve_stats_get(srv)
+    assert st["completed"] == 0 and st["p50_ms"] == 0
+    with pytest.raises(rn.RNError):
+        rn.rn_serve_create(g, slab_bytes=4 << 20, max_blocks=8)  # budget below one request
+    srv.close()
+
+
+def test_destroy_with_queued_requests(rn, world):
+    e, g = world
+    srv = rn.rn_serve_create(g, workers=2, max_blocks=4)
+    R, S = I.disjoint_sets(e.n, 2000, 2000, 4)
+    for _ in range(20):
+        rn.rn_serve_submit(srv, R, S, 150_000)
+    srv.close()  # running requests finish, queued ones are dropped
+    u, v, d = rn.rn_distance_join(g, R[:50], S, 150_000)  # the graph still answers
+    assert len(u) == len(rn.rn_distance_join(g, R[:50], S, 150_000)[0])
