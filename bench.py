@@ -50,6 +50,8 @@ def parse():
     ap.add_argument("--tile-sources", type=int, default=0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batch", action="store_true", help="skip the 512-instance batched leg")
+    ap.add_argument("--no-serve", action="store_true", help="skip the serving leg")
+    ap.add_argument("--serve-requests", type=int, default=300)
     return ap.parse_args()
 
 
@@ -261,6 +263,99 @@ def batch_leg(rn, steps: int, warmup: int, stream, flush) -> dict:
     return res
 
 
+def serve_leg(rn, count: int) -> dict:
+    """Serving on the 6M-node graph: a stream of 70% theta-joins and 30% k-closest-pairs
+    requests (|R|, |S| 100-20000).  Saturated throughput (every request submitted at
+    once), then Poisson arrivals at 50% and 90% of that rate with p50/p99 latency
+    (submit to host result), then the same requests one at a time through the plain
+    host calls.  Latencies and rates are host wall clock: inputs start and results end
+    in host memory."""
+    import threading
+
+    from paper_1607_07696_gb300 import inputs as I
+
+    spec = WORKLOADS["serve6m"]
+    e = I.c5_serve_graph()
+    t0 = time.perf_counter()
+    g = rn.rn_graph_load(e.src, e.dst, e.w, e.n)
+    load_s = time.perf_counter() - t0
+    reqs = I.c5_requests(e.n, count, spec["ball_coeff"])
+    srv = rn.rn_serve_create(g)
+    for r in reqs[:8]:  # warm-up: every worker's buffers
+        rn.rn_serve_wait(srv, rn.rn_serve_submit(srv, r.R, r.S, r.theta, r.k))
+
+    def run_stream(arrivals):
+        rn.rn_serve_reset_stats(srv)
+        tickets = [None] * count
+        ready = threading.Semaphore(0)
+
+        def submitter():
+            start = time.perf_counter()
+            for i, r in enumerate(reqs):
+                if arrivals is not None:
+                    delay = start + arrivals[i] - time.perf_counter()
+                    if delay > 0:
+                        time.sleep(delay)
+                tickets[i] = rn.rn_serve_submit(srv, r.R, r.S, r.theta, r.k)
+                ready.release()
+
+        failure = []
+
+        def guarded_submitter():
+            try:
+                submitter()
+            except BaseException as ex:  # noqa: BLE001 - re-raised in the main thread
+                failure.append(ex)
+                for _ in range(count):
+                    ready.release()
+
+        th = threading.Thread(target=guarded_submitter)
+        t0 = time.perf_counter()
+        th.start()
+        npairs = []
+        for i in range(count):
+            ready.acquire()
+            if failure:
+                th.join()
+                raise failure[0]
+            npairs.append(len(rn.rn_serve_wait(srv, tickets[i])[0]))
+        wall = time.perf_counter() - t0
+        th.join()
+        st = rn.rn_serve_stats_get(srv)
+        return wall, st, npairs
+
+    print(f"serve: graph loaded in {load_s:.1f}s, {count} requests", file=sys.stderr, flush=True)
+    wall, st, served_pairs = run_stream(None)
+    print(f"serve: saturated {count / wall:.1f} q/s", file=sys.stderr, flush=True)
+    sat = count / wall
+    phases = {"saturated": {"offered_qps": None, "qps": sat, "p50_ms": st["p50_ms"], "p99_ms": st["p99_ms"],
+                            "max_running": st["max_running"], "slab_peak_mb": st["slab_bytes_peak"] / 2**20}}
+    for frac in (0.5, 0.9):
+        arr = I.poisson_arrivals(count, frac * sat, seed=int(frac * 100))
+        wall, st, _ = run_stream(arr)
+        phases[f"poisson_{int(frac * 100)}pct"] = {
+            "offered_qps": frac * sat, "qps": count / wall, "p50_ms": st["p50_ms"], "p99_ms": st["p99_ms"],
+            "mean_queue_ms": st["mean_queue_ms"], "max_running": st["max_running"]}
+    srv.close()
+    # the plain form: one query per call, one after the other
+    t0 = time.perf_counter()
+    plain_pairs = []
+    for r in reqs:
+        out = rn.rn_distance_join(g, r.R, r.S, r.theta) if r.k == 0 else rn.rn_kcp(g, r.R, r.S, r.k, r.theta)
+        plain_pairs.append(len(out[0]))
+    plain_s = time.perf_counter() - t0
+    assert plain_pairs == served_pairs, "served and plain pair counts differ"
+    joins = [r for r in reqs if r.k == 0]
+    return {
+        "workload": "serve6m: 6M-node road-like graph, 70% theta-joins / 30% kCP, |R|,|S| 100-20000, "
+                    f"k 10-1e5, {count} requests",
+        "unit": "queries/s", "requests": count, "joins": len(joins), "pairs": int(sum(served_pairs)),
+        "served_qps": sat, "plain_qps": count / plain_s, "served_vs_plain": sat / (count / plain_s),
+        "phases": phases, "graph_load_s": load_s,
+        "config": {"workers": 8, "max_blocks": 64, "slab_mb": 2048},
+    }
+
+
 def run_engine(args):
     import numpy as np
     import torch
@@ -398,6 +493,8 @@ def run_engine(args):
     }
     if not args.no_batch and world == 1:
         line["batched"] = batch_leg(rn, max(3, args.steps // 2), 3, stream, flush)
+    if not args.no_serve and world == 1:
+        line["served"] = serve_leg(rn, args.serve_requests)
     if not args.no_cpu_baseline and world == 1:
         line["cpu_baseline"] = cpu_baseline(w, spec)
     print(json.dumps(line), flush=True)

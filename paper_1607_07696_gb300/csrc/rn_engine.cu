@@ -195,7 +195,7 @@ struct Workspace {
     uint32_t *block_sums = nullptr;
     uint32_t *rsorted = nullptr;
     uint32_t rsorted_cap = 0;
-    uint32_t *failed = nullptr, *failed2 = nullptr;  // tiles to search again (ping-pong)
+    uint4 *failed = nullptr, *failed2 = nullptr;  // source ranges whose map overflowed, to search again
     uint32_t failed_cap = 0, failed2_cap = 0;
     Control *ctl = nullptr;
     Control *ctl_host = nullptr;  // pinned
@@ -408,8 +408,9 @@ struct SearchArgs {
     const uint32_t *__restrict__ iperm;
     const uint32_t *__restrict__ sbits;
     const uint32_t *__restrict__ src;       // R, internal ids, ascending
-    const uint32_t *__restrict__ tile_list; // tiles to search (retry), or null: all
-    uint32_t ntiles;                        // entries of tile_list, or tiles of R
+    const uint4 *__restrict__ range_list;   // retry: (first source, count, -, -) of each
+                                            // range to search, or null: every tile of R
+    uint32_t ntiles;                        // entries of range_list, or tiles of R
     uint32_t tile_src;                      // sources per tile (<= T; lanes beyond stay INF)
     uint32_t bound;                         // theta
     uint32_t delta;
@@ -418,7 +419,8 @@ struct SearchArgs {
     uint32_t H, hshift, max_fill;
     uint32_t vbits;                         // key = (u << vbits) | v
     Control *ctl;
-    uint32_t *failed;
+    uint4 *failed;                          // ranges whose slot map overflowed: (first,
+                                            // count, bucket end reached, slots filled)
     unsigned long long *out_key;
     uint32_t *out_d;
     uint64_t out_cap;
@@ -452,7 +454,8 @@ struct TileCtx {
     const uint32_t *sbits;
     const uint32_t *src;
     unsigned long long key_prefix;
-    uint32_t local, nR, tile_src, bound, delta, inst;
+    uint32_t first, cnt;  // sources src[first .. first + cnt) of this tile (or part of one)
+    uint32_t bound, delta, inst;
 };
 
 constexpr uint32_t KCP_BINS = 2048;
@@ -660,7 +663,7 @@ __global__ void __launch_bounds__(THREADS, (THREADS == NARROW ? CTAS_PER_SM : 1)
     if (__ldcg(&a.ctl->err)) return;
     const uint32_t nR1 = a.nR_fixed ? a.nR_fixed : __ldcg(&a.ctl->r_count);  // sources
     const uint32_t all_tiles = (nR1 + a.tile_src - 1) / a.tile_src;
-    const uint32_t ntiles = a.tile_list ? a.ntiles : all_tiles;
+    const uint32_t ntiles = a.range_list ? a.ntiles : all_tiles;
 
 
     for (;;) {
@@ -681,8 +684,19 @@ __global__ void __launch_bounds__(THREADS, (THREADS == NARROW ? CTAS_PER_SM : 1)
         __syncthreads();
         const uint32_t ti = s_tile;
         if (ti >= ntiles) break;
-        const uint32_t tile = a.tile_list ? a.tile_list[ti] : ti;
-        if (tile >= all_tiles) continue;  // defensive: never index past R
+        // this block's sources: tile ti, or the ti-th range of a retry (a whole tile or a
+        // part of one); the tile it lies in names its per-tile table entries
+        uint32_t first, cnt;
+        if (a.range_list) {
+            const uint4 r = a.range_list[ti];
+            first = r.x;
+            cnt = r.y;
+        } else {
+            first = ti * a.tile_src;
+            cnt = first < nR1 ? min(a.tile_src, nR1 - first) : 0u;
+        }
+        if (cnt == 0 || cnt > a.tile_src || first >= nR1 || cnt > nR1 - first) continue;  // never past R
+        const uint32_t tile = first / a.tile_src;
         if (tid == 0) {
             TileCtx c;
             c.row_ptr = a.row_ptr;
@@ -690,12 +704,11 @@ __global__ void __launch_bounds__(THREADS, (THREADS == NARROW ? CTAS_PER_SM : 1)
             c.iperm = a.iperm;
             c.sbits = a.sbits;
             c.src = a.src;
-            c.nR = nR1;
-            c.tile_src = a.tile_src;
+            c.first = first;
+            c.cnt = cnt;
             c.bound = a.tile_bound ? a.tile_bound[tile]
                                    : (a.theta_live ? min(a.bound, __ldcg(a.theta_live)) : a.bound);
             c.delta = a.tile_delta ? a.tile_delta[tile] : a.delta;
-            c.local = tile;
             c.inst = a.tile_inst ? a.tile_inst[tile] : 0u;
             c.key_prefix = 0;
             s_cx = c;
@@ -706,12 +719,11 @@ __global__ void __launch_bounds__(THREADS, (THREADS == NARROW ? CTAS_PER_SM : 1)
         const uint2 *adj = s_cx.adj;
         const uint32_t bound = s_cx.bound;  // this tile's bound, the same for every thread
         const uint64_t delta = s_cx.delta;
-        const uint32_t first = s_cx.local * s_cx.tile_src;
-        const uint32_t tsz = min(s_cx.tile_src, s_cx.nR - first);
+        const uint32_t tsz = s_cx.cnt;
 
         // sources: lane t of every row belongs to R node first + t, at distance 0
         if (tid < tsz) {
-            const uint32_t y = s_cx.src[first + tid];
+            const uint32_t y = s_cx.src[s_cx.first + tid];
             src_orig[tid] = s_cx.iperm[y];
             const uint32_t h = find_or_insert(hkeys, a.H, a.hshift, y, &s_fill, a.max_fill, &s_fail);
             __stcg(&slab[size_t(h) * T + tid], 0u);
@@ -996,7 +1008,8 @@ __global__ void __launch_bounds__(THREADS, (THREADS == NARROW ? CTAS_PER_SM : 1)
                 }
             }
         } else if (tid == 0) {
-            a.failed[atomicAdd(&a.ctl->n_failed, 1u)] = tile;
+            a.failed[atomicAdd(&a.ctl->n_failed, 1u)] =
+                make_uint4(s_cx.first, s_cx.cnt, uint32_t(min(tau, uint64_t(0xFFFFFFFFu))), s_fill);
         }
         // ---- leave the region clean (every row INF) for the next tile
         for (uint32_t c = warp * 32; c < a.H; c += SEARCH_WARPS * 32) {
@@ -1277,11 +1290,13 @@ static void launch_gmap(const DeviceGraph &g, Workspace *ws, uint32_t T, SearchA
     uint32_t **buf = ws->own_gmap_enabled ? &ws->own_gmap : &ws->sh->gretry;
     size_t *bytes = ws->own_gmap_enabled ? &ws->own_gmap_bytes : &ws->sh->gretry_bytes;
     if (*bytes < per_block * rgrid) {
+        // grow with room to spare: freeing device memory synchronises the whole device
+        const size_t want = std::max(per_block * rgrid, std::min(*bytes * 2, budget));
         device_free(*buf);
         *buf = nullptr;
         *bytes = 0;
-        *buf = (uint32_t *)device_alloc(per_block * rgrid);
-        *bytes = per_block * rgrid;
+        *buf = (uint32_t *)device_alloc(want);
+        *bytes = want;
         ws->own_gmap_moved = true;
     }
     RN_CUDA(cudaMemsetAsync(*buf, 0xFF, per_block * rgrid, st));  // rows INF
@@ -1294,70 +1309,163 @@ static void launch_gmap(const DeviceGraph &g, Workspace *ws, uint32_t T, SearchA
 }
 
 // Search every tile with the first map (by default narrow blocks: 8192-slot shared
-// maps, two per SM), then search the tiles whose union ball overflowed again: with wide
-// blocks (16384-slot shared maps), then with global maps four times larger each time.
-// The map never needs more than the next power of two >= 2n slots, where it cannot
-// overflow.
+// maps, two per SM), then search again the source ranges whose union ball overflowed.
+// An overflowed range reports the bucket end tau it reached and its fill; in a road
+// network a ball grows about as the square of its radius, so its whole union ball is
+// estimated as fill * (bound / tau)^2.  A range whose sources lie far apart in the
+// locality order (balls nearly disjoint: a sparse R on a large graph) is cut once into
+// as many parts as that estimate asks, each searched again with the same shared map.
+// A range of nearby sources (overlapping balls, which cutting would not shrink), and
+// every part that still overflows, goes to the map its estimate fits (wide blocks with
+// 16384-slot shared maps, else a global map), growing four times on each further
+// overflow.  The map never needs more than the next power of two >= 2n slots, where it
+// cannot overflow.
+constexpr uint32_t SPARSE_GAP = 2048;  // mean internal-id gap of sources with disjoint balls
+
+static void ensure_ranges(uint4 **p, uint32_t *cap, uint32_t want) {
+    if (*p && *cap >= want) return;
+    device_free(*p);
+    *p = nullptr;
+    *cap = std::max<uint32_t>(want, 1024);
+    *p = (uint4 *)device_alloc(size_t(*cap) * 16);
+}
+
+static std::vector<uint4> read_ranges(const uint4 *d, uint32_t n, cudaStream_t st) {
+    std::vector<uint4> h(n);
+    if (n) {
+        RN_CUDA(cudaMemcpyAsync(h.data(), d, size_t(n) * 16, cudaMemcpyDeviceToHost, st));
+        RN_CUDA(cudaStreamSynchronize(st));
+    }
+    return h;
+}
+
+// Slots a map needs for an estimated ball: room to spare below its 7/8 fill limit.
+static uint64_t map_for(uint64_t ball, uint64_t hcap) {
+    const uint64_t need = ball + ball / 7 + ball / 4 + 1;
+    if (need <= SMEM_H) return SMEM_H;
+    if (need <= SMEM_HW) return SMEM_HW;
+    uint64_t H = SMEM_HW * 2;
+    while (H < need && H < hcap) H <<= 1;
+    return std::min(H, hcap);
+}
+
 static Control search_all(const DeviceGraph &g, Workspace *ws, uint32_t T, SearchArgs a,
-                          uint32_t ntiles, cudaStream_t st, uint64_t *retried, uint32_t map_slots = 0) {
+                          uint32_t ntiles, cudaStream_t st, uint64_t *retried, uint32_t map_slots = 0,
+                          bool split = true) {
     // narrow blocks: one slab region each; wide blocks: two regions each
     const uint32_t grid_max = ws->sh->slab_ctas;
     const uint32_t grid_wide = std::max<uint32_t>(1, std::min<uint32_t>(grid_max / 2, uint32_t(ws->num_sms)));
     a.slab = ws->sh->slab;
-    if (ntiles && (!a.src || !a.slab || !a.sbits || !a.out_key || !a.out_d || !a.row_ptr || !a.adj || !a.ctl))
+    if (ntiles && (!a.src || !a.slab || !a.sbits || !a.out_key || !a.out_d || !a.row_ptr || !a.adj || !a.ctl ||
+                   !ws->failed || !ws->failed2))
         fail(RN_EINTERNAL, "tile search without its buffers");
     uint64_t hcap = 1;
     while (hcap < 2ull * g.n) hcap <<= 1;
-    uint64_t H = first_map(map_slots, hcap);
+    const uint64_t H0 = first_map(map_slots, hcap);
     a.gmap = nullptr;
-    a.tile_list = nullptr;
+    a.range_list = nullptr;
     a.ntiles = ntiles;
     a.failed = ws->failed;
-    if (H <= SMEM_HW) {
-        a.H = uint32_t(H);
-        a.hshift = 32 - bits_for(uint32_t(H));
-        a.max_fill = uint32_t(H * 7 / 8);
-    }
+    auto set_shared = [](SearchArgs &x, uint32_t h) {
+        x.gmap = nullptr;
+        x.H = h;
+        x.hshift = 32 - bits_for(h);
+        x.max_fill = h * 7 / 8;
+    };
+    // one launch over n ranges (or every tile) with a map of h slots
+    auto launch = [&](SearchArgs &x, uint64_t h, uint32_t n) {
+        if (h == SMEM_H) {
+            set_shared(x, SMEM_H);
+            search(T, Shape::Narrow, x, std::max<uint32_t>(1, std::min(n, grid_max)), st);
+        } else if (h == SMEM_HW) {
+            set_shared(x, SMEM_HW);
+            search(T, Shape::Wide, x, std::max<uint32_t>(1, std::min(n, grid_wide)), st);
+        } else {
+            launch_gmap(g, ws, T, x, h, n, st);
+        }
+        ws->launches++;
+    };
     RN_CUDA(cudaEventRecord(ws->evs0, st));
     if (ntiles) {
-        if (H == SMEM_H) search(T, Shape::Narrow, a, std::max<uint32_t>(1, std::min(ntiles, grid_max)), st);
-        else if (H == SMEM_HW) search(T, Shape::Wide, a, std::max<uint32_t>(1, std::min(ntiles, grid_wide)), st);
-        else launch_gmap(g, ws, T, a, H, ntiles, st);
-        ws->launches++;
-        ws->blocks_per_sm = H > SMEM_H ? 1 : T == 32 ? search_occupancy<1>() : T == 64 ? search_occupancy<2>() : search_occupancy<4>();
+        launch(a, H0, ntiles);
+        ws->blocks_per_sm = H0 > SMEM_H ? 1 : T == 32 ? search_occupancy<1>() : T == 64 ? search_occupancy<2>() : search_occupancy<4>();
     }
     RN_CUDA(cudaEventRecord(ws->evs1, st));
     Control c = read_control(ws, st);
     ws->retry_ms = 0;
-    uint32_t *list = ws->failed, *next = ws->failed2;
-    while (c.n_failed && !c.err) {
-        if (H >= hcap) fail(RN_EINTERNAL, "slot map overflowed at its largest size");
-        const uint32_t nf = c.n_failed;
-        *retried += nf;
+    if (!c.n_failed || c.err) return c;
+    // relaunch `ranges` with a map of h slots; the ranges that overflow again come back
+    auto relaunch = [&](const std::vector<uint4> &ranges, uint64_t h) {
+        const uint32_t n = uint32_t(ranges.size());
+        ensure_ranges(&ws->failed, &ws->failed_cap, n);
+        ensure_ranges(&ws->failed2, &ws->failed2_cap, n);
+        RN_CUDA(cudaMemcpyAsync(ws->failed2, ranges.data(), size_t(n) * 16, cudaMemcpyHostToDevice, st));
         RN_CUDA(cudaMemsetAsync(&ws->ctl->tile_next, 0, 8, st));  // tile_next, n_failed
         SearchArgs r = a;
-        r.tile_list = list;
-        r.ntiles = nf;
-        r.failed = next;
-        if (H == SMEM_H) {
-            // wide blocks reuse the slab: it holds grid_max regions of SMEM_H rows,
-            // that is grid_max / 2 regions of SMEM_HW rows
-            H = SMEM_HW;
-            r.H = SMEM_HW;
-            r.hshift = 32 - bits_for(SMEM_HW);
-            r.max_fill = SMEM_HW * 7 / 8;
-            search(T, Shape::Wide, r, std::min<uint32_t>(nf, grid_wide), st);
-        } else {
-            H = std::min<uint64_t>(H * 4, hcap);
-            launch_gmap(g, ws, T, r, H, nf, st);
-        }
-        ws->launches++;
+        r.range_list = ws->failed2;
+        r.ntiles = n;
+        r.failed = ws->failed;
+        launch(r, h, n);
+        *retried += n;
         RN_CUDA(cudaEventRecord(ws->evr, st));
         c = read_control(ws, st);
         float ms = 0;
         RN_CUDA(cudaEventElapsedTime(&ms, ws->evs1, ws->evr));
         ws->retry_ms = ms;
-        std::swap(list, next);  // this launch's failures are the next launch's tiles
+        return c.err ? std::vector<uint4>() : read_ranges(ws->failed, c.n_failed, st);
+    };
+    // estimated union ball of an overflowed range (at least what it filled, at most n)
+    auto estimate = [&](const uint4 &f) {
+        const double r = double(a.bound) / double(std::max<uint32_t>(f.z, 1));
+        const double e = double(std::max<uint32_t>(f.w, 1)) * std::min(r * r, 1e12);
+        return uint64_t(std::min<double>(std::max<double>(e, f.w), double(g.n)));
+    };
+    std::vector<uint4> over = read_ranges(ws->failed, c.n_failed, st);
+    // ranges waiting for a larger map, by the map size they go to next
+    std::map<uint64_t, std::vector<uint4>> grow;
+    auto to_grow = [&](const uint4 &f, uint64_t failed_at) {
+        const uint64_t h = std::max(map_for(estimate(f), hcap), failed_at == SMEM_H ? uint64_t(SMEM_HW)
+                                                                                     : std::min(failed_at * 4, hcap));
+        if (failed_at >= hcap) fail(RN_EINTERNAL, "slot map overflowed at its largest size");
+        grow[h].push_back(make_uint4(f.x, f.y, 0, 0));
+    };
+    if (split && H0 <= SMEM_HW) {
+        // the sources of the overflowed ranges, to see how far apart they lie
+        std::vector<uint32_t> src(std::max<uint32_t>(a.nR_fixed ? a.nR_fixed : c.r_count, 1));
+        RN_CUDA(cudaMemcpyAsync(src.data(), a.src, src.size() * 4, cudaMemcpyDeviceToHost, st));
+        RN_CUDA(cudaStreamSynchronize(st));
+        // parts go to wide blocks, sized to fill about 60% of their map: sources of one
+        // tile cost little more than one (its rounds are bound by latency, not by the
+        // sources it carries), so fewer, fuller parts beat many small ones
+        const double room = double(SMEM_HW) * 7 / 8 * 0.6;
+        std::vector<uint4> parts;
+        for (const uint4 &f : over) {
+            const bool sparse = f.y >= 2 && f.x + f.y <= src.size() &&
+                                double(src[f.x + f.y - 1] - src[f.x]) / double(f.y - 1) >= SPARSE_GAP;
+            const uint32_t np = sparse ? uint32_t(std::min<double>(f.y, std::ceil(double(estimate(f)) / room))) : 1;
+            if (np < 2) {
+                to_grow(f, H0);
+                continue;
+            }
+            const uint32_t part = (f.y + np - 1) / np;
+            for (uint32_t j = 0; j * part < f.y; j++)
+                parts.push_back(make_uint4(f.x + j * part, std::min(part, f.y - j * part), 0, 0));
+        }
+        if (!parts.empty()) {
+            const uint64_t hp = std::max<uint64_t>(H0, std::min<uint64_t>(SMEM_HW, hcap));
+            for (const uint4 &f : relaunch(parts, hp)) to_grow(f, hp);
+            if (c.err) return c;
+        }
+    } else {
+        for (const uint4 &f : over) to_grow(f, H0);
+    }
+    while (!grow.empty()) {
+        const uint64_t h = grow.begin()->first;
+        std::vector<uint4> ranges;
+        ranges.swap(grow.begin()->second);
+        grow.erase(grow.begin());
+        for (const uint4 &f : relaunch(ranges, h)) to_grow(f, h);
+        if (c.err) return c;
     }
     return c;
 }
@@ -1410,6 +1518,18 @@ static void ensure_slab(Workspace *ws) {
     RN_CUDA(cudaMemset(sh->slab, 0xFF, sh->slab_bytes));  // every row INF
     RN_CUDA(cudaDeviceSynchronize());  // before any search on a stream of its own
     sh->slab_ctas = grid_max;
+}
+
+// Grow the workspace's buffers now for queries of up to max_r sources and max_pairs
+// pairs (raw pairs and their sort), so such queries allocate and free nothing later:
+// freeing device memory synchronises the whole device, which would stall every other
+// stream's work.
+void workspace_reserve(Workspace *ws, uint32_t max_r, uint64_t max_pairs) {
+    ensure_u32(&ws->rsorted, &ws->rsorted_cap, std::max<uint32_t>(max_r, 1));
+    ensure_ranges(&ws->failed, &ws->failed_cap, std::max<uint32_t>(max_r, 1));
+    ensure_ranges(&ws->failed2, &ws->failed2_cap, std::max<uint32_t>(max_r, 1));
+    ensure_pairs(ws, max_pairs);
+    grow(ws, &ws->hist, &ws->hist_cap, (max_pairs + RS_TILE - 1) / RS_TILE * 256 + 256, 4);
 }
 
 // a2: validate R and S on the device, build the S membership bitmap and the list of R
@@ -1471,8 +1591,8 @@ void run_join(const DeviceGraph &g, Workspace *ws, const EngineConfig &cfg, uint
         if (cfg.tile_src) tile_src = std::min(cfg.tile_src, T);
     }
     const uint32_t ntiles = (nR + tile_src - 1) / tile_src;
-    ensure_u32(&ws->failed, &ws->failed_cap, std::max<uint32_t>(ntiles, 1));
-    ensure_u32(&ws->failed2, &ws->failed2_cap, std::max<uint32_t>(ntiles, 1));
+    ensure_ranges(&ws->failed, &ws->failed_cap, std::max<uint32_t>(ntiles, 1));
+    ensure_ranges(&ws->failed2, &ws->failed2_cap, std::max<uint32_t>(ntiles, 1));
     ensure_pairs(ws, std::max<uint64_t>(ws->pair_cap, uint64_t(nR) * 64));
 
     const uint32_t vbits = bits_for(g.n);
@@ -1608,7 +1728,10 @@ void run_join_noalloc(const DeviceGraph &g, uint32_t median_w, const uint32_t *d
     uint32_t *used_bits = base + NA_BITS, *rbits = used_bits + na_round(NA_NWORDS),
              *sbits = rbits + na_round(NA_NWORDS);
     uint32_t *bsums = base + NA_BSUMS, *rsorted = base + NA_RSORT;
-    uint32_t *failed = base + NA_FAIL, *failed2 = failed + na_round(NA_MAX_R);
+    // the failed-range lists: NA_MAX_R words, NA_MAX_R / 4 ranges each (a launch has at
+    // most 2048 tiles)
+    uint4 *failed = reinterpret_cast<uint4 *>(base + NA_FAIL);
+    uint4 *failed2 = reinterpret_cast<uint4 *>(base + NA_FAIL + na_round(NA_MAX_R));
     unsigned long long *keyA = reinterpret_cast<unsigned long long *>(base + NA_KEYS);
     unsigned long long *keyB = reinterpret_cast<unsigned long long *>(base + NA_KEYS + na_round(2 * size_t(NA_MAX_PAIRS)));
     uint32_t *valA = base + NA_VALS, *valB = valA + na_round(NA_MAX_PAIRS);
@@ -1664,7 +1787,7 @@ void run_join_noalloc(const DeviceGraph &g, uint32_t median_w, const uint32_t *d
         // wide blocks: the slab holds NA_BLOCKS / 2 regions of SMEM_HW rows
         RN_CUDA(cudaMemsetAsync(&ctl->tile_next, 0, 8, st));
         SearchArgs r = a;
-        r.tile_list = failed;
+        r.range_list = failed;
         r.ntiles = c.n_failed;
         r.failed = failed2;
         r.H = SMEM_HW;
@@ -1823,8 +1946,8 @@ void run_kcp(const DeviceGraph &g, Workspace *ws, const EngineConfig &cfg, uint3
         if (cfg.tile_src) tile_src = std::min(cfg.tile_src, T);
     }
     const uint32_t ntiles = (nR + tile_src - 1) / tile_src;
-    ensure_u32(&ws->failed, &ws->failed_cap, std::max<uint32_t>(ntiles, 1));
-    ensure_u32(&ws->failed2, &ws->failed2_cap, std::max<uint32_t>(ntiles, 1));
+    ensure_ranges(&ws->failed, &ws->failed_cap, std::max<uint32_t>(ntiles, 1));
+    ensure_ranges(&ws->failed2, &ws->failed2_cap, std::max<uint32_t>(ntiles, 1));
     ensure_pairs(ws, std::max<uint64_t>(ws->pair_cap, std::min<uint64_t>(k + (k >> 2) + 4096, uint64_t(nR) * 64 + 4096)));
     if (!ws->kcp) {
         ws->kcp = (uint32_t *)device_alloc((KCP_BINS + 16) * 4 + sizeof(SelState));
@@ -2155,8 +2278,8 @@ static void batch_layout(Batch *b) {
         b->groups.push_back(g);
     }
     RN_CUDA(cudaDeviceSynchronize());  // the batch's stream does not wait for these copies
-    ensure_u32(&b->ws->failed, &b->ws->failed_cap, uint32_t(std::max<uint64_t>(tiles, 1)));
-    ensure_u32(&b->ws->failed2, &b->ws->failed2_cap, uint32_t(std::max<uint64_t>(tiles, 1)));
+    ensure_ranges(&b->ws->failed, &b->ws->failed_cap, uint32_t(std::max<uint64_t>(tiles, 1)));
+    ensure_ranges(&b->ws->failed2, &b->ws->failed2_cap, uint32_t(std::max<uint64_t>(tiles, 1)));
     b->stats.tiles = tiles;
     b->stats.groups = uint32_t(b->groups.size());
 }
@@ -2284,7 +2407,7 @@ static uint64_t batch_run_eager(Batch *b, cudaStream_t st) {
         Control c{};
         for (const auto &g : b->groups) {
             RN_CUDA(cudaMemsetAsync(&b->ws->ctl->tile_next, 0, 8, st));  // tile_next, n_failed
-            c = search_all(b->ug, b->ws, g.T, batch_args(b, g), g.tiles, st, &retried, g.map);
+            c = search_all(b->ug, b->ws, g.T, batch_args(b, g), g.tiles, st, &retried, g.map, false);
             check_control(c);
         }
         b->stats.retried_tiles = retried;

@@ -100,6 +100,7 @@ void batch_destroy(Batch *b);
 // Workspaces with a slab of their own (servers, rn_engine.cu).
 size_t slab_region_bytes();
 void workspace_set_slab(Workspace *ws, uint32_t *slab, uint32_t regions);
+void workspace_reserve(Workspace *ws, uint32_t max_r, uint64_t max_pairs);
 
 // Request servers (rn_serve.cpp): the graph must outlive its server.
 struct Server;

@@ -208,6 +208,11 @@ Server *server_create(const rn_graph *g, uint64_t slab_bytes, uint32_t workers, 
     try {
         for (auto &w : s->workers) {
             w.ws = workspace_create(g->dev);
+            // requests up to 32768 sources and 2^22 pairs then allocate nothing
+            workspace_reserve(w.ws, 1u << 15, uint64_t(1) << 22);
+            ensure_u32(&w.dR, &w.capR, 1u << 15);
+            ensure_u32(&w.dS, &w.capS, 1u << 15);
+            dpairs_reserve(&w.res, uint64_t(1) << 22);
             check(cudaStreamCreateWithFlags(&w.stream, cudaStreamNonBlocking), "cudaStreamCreateWithFlags");
         }
         for (auto &w : s->workers) {

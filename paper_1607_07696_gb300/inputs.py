@@ -318,7 +318,7 @@ def c4_instance(spec: BatchSpec) -> tuple[EdgeList, np.ndarray, np.ndarray]:
 # ---------------------------------------------------------------- serving ----
 
 C5_N, C5_M = 6_000_000, 14_000_000
-C5_BALL_CAP = 16_384  # largest expected ball (nodes) a join request is calibrated for
+C5_BALL_CAP = 4_096  # largest expected ball (nodes per source) a request is sized for
 
 
 def c5_serve_graph(seed: int = BASE_SEED + 4) -> EdgeList:
@@ -343,9 +343,13 @@ def c5_requests(n: int, count: int, ball_coeff: float, seed: int = BASE_SEED + 5
     """The mixed request stream: 70% theta-joins, 30% k closest pairs; |R| and |S|
     log-uniform in [100, 20000] (disjoint uniform nodes), k log-uniform in [10, 1e5].  A
     join's theta targets log-uniform [5, 200] S-matches per R node: the expected ball
-    holding that many S nodes is matches * n / |S| nodes (capped at C5_BALL_CAP), and a
-    ball of b nodes has radius sqrt(b / ball_coeff) (the graph's measured ball growth,
-    about ball_coeff * theta^2 nodes within theta).  k closest pairs run unbounded."""
+    holding that many S nodes is matches * n / |S| nodes, and a ball of b nodes has
+    radius sqrt(b / ball_coeff) (the graph's measured ball growth, about
+    ball_coeff * theta^2 nodes within theta).  k closest pairs run unbounded.  Either
+    kind is sized so the expected ball of one source stays within C5_BALL_CAP nodes: a
+    join's target lowered to what such a ball holds (theta at the cap's radius), k to
+    at most |R| * |S| * C5_BALL_CAP / n (without the cap, small sets with a large
+    target make single requests search the whole graph from every source)."""
     rng = np.random.default_rng(seed)
     out = []
     for i in range(count):
@@ -359,7 +363,8 @@ def c5_requests(n: int, count: int, ball_coeff: float, seed: int = BASE_SEED + 5
             out.append(ServeRequest(R, S, theta, 0, matches))
         else:
             k = int(round(log_uniform(rng, 10, 100_000)))
-            out.append(ServeRequest(R, S, 0xFFFFFFFF, min(k, nR * nS), 0.0))
+            k = max(1, min(k, int(nR * nS * C5_BALL_CAP / n)))
+            out.append(ServeRequest(R, S, 0xFFFFFFFF, k, 0.0))
     return out
 
 
