@@ -150,6 +150,9 @@ struct Control {
     unsigned long long rounds, round_items, boundaries;
     unsigned long long cyc_round, cyc_bound, cyc_emit;
     unsigned long long cyc_stepA, round_arcs;
+    // balance of step B: dirty lane-groups of the scanned items; per lane, batches of G
+    // groups it relaxed; per warp chunk, its slowest lane's batches
+    unsigned long long dirty_groups, lane_batches, lane_batches_max;
     uint32_t max_fill;  // largest union ball (slots) of a completed tile
     uint32_t check[4];  // first failed device-side check of the batch path: code, index, value
 };
@@ -651,10 +654,10 @@ __global__ void __launch_bounds__(THREADS, (THREADS == NARROW ? CTAS_PER_SM : 1)
     const uint32_t tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     uint32_t *slab = a.slab + size_t(blockIdx.x) * a.H * T;
     __shared__ TileCtx s_cx;
-    uint32_t my_scans = 0, my_slots = 0, my_arcs = 0;
+    uint32_t my_scans = 0, my_slots = 0, my_arcs = 0, my_dirty = 0;
     // telemetry, kept by thread 0 in shared memory: rounds, round items, boundaries,
     // round arcs, cycles in step A, step B, boundaries, emission; clock marks
-    enum { T_ROUNDS, T_ITEMS, T_BOUNDS, T_ARCS, T_STEPA, T_STEPB, T_BOUND, T_EMIT, T_N };
+    enum { T_ROUNDS, T_ITEMS, T_BOUNDS, T_ARCS, T_STEPA, T_STEPB, T_BOUND, T_EMIT, T_BSUM, T_BMAX, T_N };
     __shared__ unsigned long long s_tel[T_N];
     __shared__ long long s_mark, s_tile0;
     if (tid < T_N) s_tel[tid] = 0;
@@ -765,6 +768,7 @@ __global__ void __launch_bounds__(THREADS, (THREADS == NARROW ? CTAS_PER_SM : 1)
                         if (p != INF) mask = atomicExch(&dmask[x], 0u);
                         if (mask) {
                             my_scans++;
+                            my_dirty += __popc(mask);
                             const uint32_t y0 = hkeys[x];
                             beg = __ldg(&row_ptr[y0]);
                             deg = __ldg(&row_ptr[y0 + 1]) - beg;
@@ -834,6 +838,14 @@ __global__ void __launch_bounds__(THREADS, (THREADS == NARROW ? CTAS_PER_SM : 1)
                         const uint32_t inserted = __popc(__ballot_sync(FULL, ins));
                         if (lane == 0 && inserted && atomicAdd(&s_fill, inserted) + inserted > a.max_fill)
                             s_fail = 1;
+                        {
+                            const uint32_t nb = hy != EMPTY ? (__popc(it_mask[item]) + G - 1) / G : 0u;
+                            const uint32_t bmax = __reduce_max_sync(FULL, nb), bsum = __reduce_add_sync(FULL, nb);
+                            if (lane == 0 && bmax) {
+                                atomicAdd(&s_tel[T_BSUM], (unsigned long long)bsum);
+                                atomicAdd(&s_tel[T_BMAX], (unsigned long long)bmax);
+                            }
+                        }
                         if (hy != EMPTY) {
                             const uint32_t *xrow = slab + size_t(it_x[item]) * T;
                             uint32_t *yrow = slab + size_t(hy) * T;
@@ -1039,8 +1051,10 @@ __global__ void __launch_bounds__(THREADS, (THREADS == NARROW ? CTAS_PER_SM : 1)
     my_slots = __reduce_add_sync(FULL, my_slots);
     my_arcs = __reduce_add_sync(FULL, my_arcs);
     my_scans = __reduce_add_sync(FULL, my_scans);
+    my_dirty = __reduce_add_sync(FULL, my_dirty);
     if (lane == 0) {
         atomicAdd(&a.ctl->scans, (unsigned long long)my_scans);
+        atomicAdd(&a.ctl->dirty_groups, (unsigned long long)my_dirty);
         atomicAdd(&a.ctl->slots, (unsigned long long)my_slots);
         atomicAdd(&a.ctl->slot_arcs, (unsigned long long)my_arcs);
     }
@@ -1053,6 +1067,8 @@ __global__ void __launch_bounds__(THREADS, (THREADS == NARROW ? CTAS_PER_SM : 1)
         atomicAdd(&a.ctl->round_arcs, s_tel[T_ARCS]);
         atomicAdd(&a.ctl->cyc_bound, s_tel[T_BOUND]);
         atomicAdd(&a.ctl->cyc_emit, s_tel[T_EMIT]);
+        atomicAdd(&a.ctl->lane_batches, s_tel[T_BSUM]);
+        atomicAdd(&a.ctl->lane_batches_max, s_tel[T_BMAX]);
     }
 }
 
@@ -1660,6 +1676,9 @@ void run_join(const DeviceGraph &g, Workspace *ws, const EngineConfig &cfg, uint
     stats->cycles_step_a = c.cyc_stepA;
     stats->round_arcs = c.round_arcs;
     stats->max_ball = c.max_fill;
+    stats->dirty_groups = c.dirty_groups;
+    stats->lane_batches = c.lane_batches;
+    stats->lane_batches_max = c.lane_batches_max;
     stats->retry_ms = ws->retry_ms;
 }
 
