@@ -418,12 +418,9 @@ def run_engine(args):
     total_ms = sum(times)
     pairs_all = npairs
     if dist:
-        t = torch.tensor([total_ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
-        pc = torch.tensor([float(npairs)], device="cuda")
-        dist.all_reduce(pc, op=dist.ReduceOp.SUM)
-        pairs_all = int(pc.item())
+        from paper_1607_07696_gb300 import shard
+
+        total_ms, pairs_all = shard.job_time_and_pairs(total_ms, npairs, device="cuda")
     value = pairs_all * args.steps / (total_ms / 1e3)
 
     # end to end through the host-buffer call: R, S in pinned memory, pairs to the host
