@@ -137,8 +137,6 @@ typedef struct {
     uint64_t max_ball;      /* largest union ball (slots) of a tile that completed */
     double retry_ms;        /* time of the launches that searched overflowed tiles again */
     uint64_t dirty_groups;  /* dirty lane-groups of the scanned items, over all rounds */
-    uint64_t lane_batches;  /* edge relaxation: batches of dirty lane-groups, over all lanes */
-    uint64_t lane_batches_max; /* the same, counting each warp's slowest lane for the warp */
 } rn_query_stats;
 
 /*

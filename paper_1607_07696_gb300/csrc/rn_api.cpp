@@ -70,19 +70,34 @@ rn_status guarded(F &&f) {
 
 // Host-side check of R and S (ids < n, no repeats, disjoint), for a precise message
 // before anything reaches the device.
+// The marks live in a per-thread array reused across calls and cleared entry by entry
+// afterwards, so a check costs O(|R| + |S|), not O(n).
 void check_sets_host(uint32_t n, const uint32_t *R, uint32_t nR, const uint32_t *S, uint32_t nS) {
     if ((nR && !R) || (nS && !S)) rn::fail(RN_EINVAL, "null R or S with a non-zero size");
-    std::vector<uint8_t> mark(n, 0);
+    thread_local std::vector<uint8_t> mark;
+    if (mark.size() < n) mark.assign(n, 0);
+    struct Clear {  // leave the marks at zero however the check ends
+        const uint32_t *R, *S;
+        uint32_t nR, nS, n;
+        ~Clear() {
+            for (uint32_t i = 0; i < nR; i++)
+                if (R[i] < n) mark[R[i]] = 0;
+            for (uint32_t i = 0; i < nS; i++)
+                if (S[i] < n) mark[S[i]] = 0;
+        }
+    } clear{R, S, 0, 0, n};
     for (uint32_t i = 0; i < nR; i++) {
         if (R[i] >= n) rn::fail(RN_EINVAL, "R[" + std::to_string(i) + "] >= n");
         if (mark[R[i]]) rn::fail(RN_EINVAL, "R repeats node " + std::to_string(R[i]));
         mark[R[i]] = 1;
+        clear.nR = i + 1;
     }
     for (uint32_t i = 0; i < nS; i++) {
         if (S[i] >= n) rn::fail(RN_EINVAL, "S[" + std::to_string(i) + "] >= n");
         if (mark[S[i]] == 2) rn::fail(RN_EINVAL, "S repeats node " + std::to_string(S[i]));
         if (mark[S[i]] == 1) rn::fail(RN_EINVAL, "node " + std::to_string(S[i]) + " is in both R and S");
         mark[S[i]] = 2;
+        clear.nS = i + 1;
     }
 }
 

@@ -150,9 +150,7 @@ struct Control {
     unsigned long long rounds, round_items, boundaries;
     unsigned long long cyc_round, cyc_bound, cyc_emit;
     unsigned long long cyc_stepA, round_arcs;
-    // balance of step B: dirty lane-groups of the scanned items; per lane, batches of G
-    // groups it relaxed; per warp chunk, its slowest lane's batches
-    unsigned long long dirty_groups, lane_batches, lane_batches_max;
+    unsigned long long dirty_groups;  // dirty lane-groups of the scanned items
     uint32_t max_fill;  // largest union ball (slots) of a completed tile
     uint32_t check[4];  // first failed device-side check of the batch path: code, index, value
 };
@@ -657,7 +655,7 @@ __global__ void __launch_bounds__(THREADS, (THREADS == NARROW ? CTAS_PER_SM : 1)
     uint32_t my_scans = 0, my_slots = 0, my_arcs = 0, my_dirty = 0;
     // telemetry, kept by thread 0 in shared memory: rounds, round items, boundaries,
     // round arcs, cycles in step A, step B, boundaries, emission; clock marks
-    enum { T_ROUNDS, T_ITEMS, T_BOUNDS, T_ARCS, T_STEPA, T_STEPB, T_BOUND, T_EMIT, T_BSUM, T_BMAX, T_N };
+    enum { T_ROUNDS, T_ITEMS, T_BOUNDS, T_ARCS, T_STEPA, T_STEPB, T_BOUND, T_EMIT, T_N };
     __shared__ unsigned long long s_tel[T_N];
     __shared__ long long s_mark, s_tile0;
     if (tid < T_N) s_tel[tid] = 0;
@@ -773,7 +771,14 @@ __global__ void __launch_bounds__(THREADS, (THREADS == NARROW ? CTAS_PER_SM : 1)
                             beg = __ldg(&row_ptr[y0]);
                             deg = __ldg(&row_ptr[y0 + 1]) - beg;
                             const uint32_t *xrow = slab + size_t(x) * T;
-                            for (uint32_t m = mask; m;) {
+                            uint32_t m = mask;
+                            if ((m & (m - 1)) == 0) {  // one dirty lane-group (m != 0 here)
+                                const Row<L> r = load_row<L>(xrow + (__ffs(m) - 1) * L);
+#pragma unroll
+                                for (int q = 0; q < L; q++) dmin = min(dmin, r.x[q]);
+                                m = 0;
+                            }
+                            while (m) {
                                 Row<L> r[G];
 #pragma unroll
                                 for (int k = 0; k < G; k++) {
@@ -838,19 +843,33 @@ __global__ void __launch_bounds__(THREADS, (THREADS == NARROW ? CTAS_PER_SM : 1)
                         const uint32_t inserted = __popc(__ballot_sync(FULL, ins));
                         if (lane == 0 && inserted && atomicAdd(&s_fill, inserted) + inserted > a.max_fill)
                             s_fail = 1;
-                        {
-                            const uint32_t nb = hy != EMPTY ? (__popc(it_mask[item]) + G - 1) / G : 0u;
-                            const uint32_t bmax = __reduce_max_sync(FULL, nb), bsum = __reduce_add_sync(FULL, nb);
-                            if (lane == 0 && bmax) {
-                                atomicAdd(&s_tel[T_BSUM], (unsigned long long)bsum);
-                                atomicAdd(&s_tel[T_BMAX], (unsigned long long)bmax);
-                            }
-                        }
                         if (hy != EMPTY) {
                             const uint32_t *xrow = slab + size_t(it_x[item]) * T;
                             uint32_t *yrow = slab + size_t(hy) * T;
                             uint32_t imask = 0, imin = INF;
-                            for (uint32_t m = it_mask[item]; m;) {
+                            uint32_t m = it_mask[item];
+                            if (m && (m & (m - 1)) == 0) {
+                                // one dirty lane-group (the common case): no batching; with
+                                // one lane per group its value is the item's least dirty
+                                // value, read in step A (a value lowered since marks the row
+                                // dirty again, so it is relaxed in a later round)
+                                const uint32_t j = __ffs(m) - 1;
+                                Row<L> dv;
+                                if constexpr (L == 1) dv.x[0] = it_dmin[item];
+                                else dv = load_row<L>(xrow + j * L);
+                                const Row<L> cv = load_row<L>(yrow + j * L);
+#pragma unroll
+                                for (int q = 0; q < L; q++) {
+                                    const uint32_t d = dv.x[q] + w;
+                                    if (dv.x[q] != INF && d <= bound && d < cv.x[q]) {
+                                        atomicMin(yrow + j * L + q, d);
+                                        imin = min(imin, d);
+                                        imask = 1u << j;
+                                    }
+                                }
+                                m = 0;
+                            }
+                            while (m) {
                                 uint32_t jj[G];
                                 Row<L> dv[G], cv[G];
 #pragma unroll
@@ -1067,8 +1086,6 @@ __global__ void __launch_bounds__(THREADS, (THREADS == NARROW ? CTAS_PER_SM : 1)
         atomicAdd(&a.ctl->round_arcs, s_tel[T_ARCS]);
         atomicAdd(&a.ctl->cyc_bound, s_tel[T_BOUND]);
         atomicAdd(&a.ctl->cyc_emit, s_tel[T_EMIT]);
-        atomicAdd(&a.ctl->lane_batches, s_tel[T_BSUM]);
-        atomicAdd(&a.ctl->lane_batches_max, s_tel[T_BMAX]);
     }
 }
 
@@ -1677,8 +1694,6 @@ void run_join(const DeviceGraph &g, Workspace *ws, const EngineConfig &cfg, uint
     stats->round_arcs = c.round_arcs;
     stats->max_ball = c.max_fill;
     stats->dirty_groups = c.dirty_groups;
-    stats->lane_batches = c.lane_batches;
-    stats->lane_batches_max = c.lane_batches_max;
     stats->retry_ms = ws->retry_ms;
 }
 

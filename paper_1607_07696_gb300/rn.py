@@ -63,8 +63,7 @@ class rn_query_stats(C.Structure):
                 ("boundaries", C.c_uint64), ("cycles_rounds", C.c_uint64),
                 ("cycles_boundaries", C.c_uint64), ("cycles_emission", C.c_uint64),
                 ("cycles_step_a", C.c_uint64), ("round_arcs", C.c_uint64), ("max_ball", C.c_uint64),
-                ("retry_ms", C.c_double), ("dirty_groups", C.c_uint64), ("lane_batches", C.c_uint64),
-                ("lane_batches_max", C.c_uint64)]
+                ("retry_ms", C.c_double), ("dirty_groups", C.c_uint64)]
 
 
 class rn_query(C.Structure):
@@ -263,18 +262,36 @@ def rn_graph_set_config(g: Graph, cfg: dict | None) -> None:
     _check(lib().rn_graph_set_config(g.handle, _config(cfg)))
 
 
+class _PairsOwner:
+    """Holds library-owned result buffers (an ``rn_pairs``) until no array views them."""
+
+    def __init__(self, p: rn_pairs):
+        self.p = p
+
+    def __del__(self):
+        if _lib is not None and getattr(self, "p", None) is not None:
+            _lib.rn_pairs_free(C.byref(self.p))
+            self.p = None
+
+
+class _View:
+    """numpy array interface over one of the buffers, keeping their owner alive."""
+
+    def __init__(self, owner: _PairsOwner, ptr, n: int):
+        self.owner = owner
+        self.__array_interface__ = {"shape": (n,), "typestr": "<u4", "version": 3,
+                                    "data": (C.cast(ptr, C.c_void_p).value, False)}
+
+
 def _take_pairs(p: rn_pairs):
+    """(u, v, d) numpy views of the library's result buffers (no copy); the buffers are
+    freed when the last of the three arrays is gone."""
     n = int(p.n)
-    try:
-        if n == 0:
-            z = np.zeros(0, np.uint32)
-            return z, z.copy(), z.copy()
-        u = np.ctypeslib.as_array(p.u, shape=(n,)).copy()
-        v = np.ctypeslib.as_array(p.v, shape=(n,)).copy()
-        d = np.ctypeslib.as_array(p.d, shape=(n,)).copy()
-        return u, v, d
-    finally:
-        lib().rn_pairs_free(C.byref(p))
+    owner = _PairsOwner(p)
+    if n == 0:
+        z = np.zeros(0, np.uint32)
+        return z, z.copy(), z.copy()
+    return tuple(np.asarray(_View(owner, ptr, n)) for ptr in (p.u, p.v, p.d))
 
 
 def rn_distance_join(g: Graph, R, S, theta: int):
