@@ -564,7 +564,8 @@ __device__ __forceinline__ uint32_t find_or_insert(uint32_t *hkeys, uint32_t H, 
 }
 
 // Exclusive prefix sum of v over the block; *total receives the sum.  All threads call;
-// warp_buf must hold THREADS / 32 + 1 words.
+// warp_buf must hold THREADS / 32 + 1 words, and the caller puts a barrier between this
+// call and the next write to warp_buf (the next call, or any other use).
 template <int THREADS>
 __device__ __forceinline__ uint32_t block_exclusive_scan(uint32_t v, uint32_t *warp_buf, uint32_t *total) {
     constexpr int SEARCH_WARPS = THREADS / 32;
@@ -591,7 +592,6 @@ __device__ __forceinline__ uint32_t block_exclusive_scan(uint32_t v, uint32_t *w
     __syncthreads();
     const uint32_t r = warp_buf[warp] + x - v;
     *total = warp_buf[SEARCH_WARPS];
-    __syncthreads();
     return r;
 }
 
@@ -645,7 +645,7 @@ __global__ void __launch_bounds__(THREADS, (THREADS == NARROW ? CTAS_PER_SM : 1)
     uint32_t *it_off = it_beg + ICAP;  // arc offset in the step,
     uint32_t *it_dmin = it_off + ICAP; // least dirty value
     __shared__ uint32_t src_orig[T];
-    __shared__ uint32_t s_tile, s_ncur, s_nnext, s_fill, s_fail, s_stop, s_minp;
+    __shared__ uint32_t s_tile, s_ncur, s_nnext, s_fill, s_fail, s_minp;
     __shared__ uint32_t s_warp[SEARCH_WARPS + 1];
     __shared__ unsigned long long s_base;
 
@@ -679,7 +679,6 @@ __global__ void __launch_bounds__(THREADS, (THREADS == NARROW ? CTAS_PER_SM : 1)
             s_nnext = 0;
             s_fill = 0;
             s_fail = 0;
-            s_stop = 0;
         }
         if (tid < T) src_orig[tid] = 0;
         __syncthreads();
@@ -737,20 +736,21 @@ __global__ void __launch_bounds__(THREADS, (THREADS == NARROW ? CTAS_PER_SM : 1)
         if (tau > uint64_t(bound) + 1) tau = uint64_t(bound) + 1;
 
         for (;;) {
-            // ---- rounds of the current bucket: relax the near queue until it drains
+            // ---- rounds of the current bucket: relax the near queue until it drains.
+            // Every thread reads the queue count and the fail flag right after the
+            // barrier that ends the step writing them (the sources or the collect step
+            // here; step B below), so every thread takes the same decision; the count
+            // is reset only after the next barrier (the scan's), when all have read it.
+            __syncthreads();
+            uint32_t ncur = min(s_ncur, QCAP);
+            bool stop = s_fail;
             for (;;) {
-                // s_ncur and s_stop are written only by thread 0 after the barrier that
-                // ends a round (or by the collect step before this barrier), and read
-                // here by all threads before the next round's barrier: every thread
-                // takes the same decision.
-                __syncthreads();
-                const uint32_t ncur = min(s_ncur, QCAP);
                 if (tid == 0) {
                     const long long t = clock64();
                     s_tel[T_BOUND] += t - s_mark;
                     s_mark = t;
                 }
-                if (ncur == 0 || s_stop) break;
+                if (ncur == 0 || stop) break;
                 if (tid == 0) {
                     s_tel[T_ROUNDS]++;
                     s_tel[T_ITEMS] += ncur;
@@ -803,6 +803,7 @@ __global__ void __launch_bounds__(THREADS, (THREADS == NARROW ? CTAS_PER_SM : 1)
                     }
                     uint32_t total;
                     const uint32_t off = block_exclusive_scan<THREADS>(deg, s_warp, &total);
+                    if (tid == 0 && c0 == 0) s_nnext = 0;  // every thread has read the last count
                     if (tid < nc) it_off[tid] = off;
                     __syncthreads();
                     if (tid == 0) {
@@ -914,19 +915,17 @@ __global__ void __launch_bounds__(THREADS, (THREADS == NARROW ? CTAS_PER_SM : 1)
                         s_mark = t;
                     }
                 }
-                if (tid == 0) {
-                    s_ncur = s_nnext;
-                    s_nnext = 0;
-                    s_stop = s_fail;
-                }
+                ncur = min(s_nnext, QCAP);  // after step B's closing barrier
+                stop = s_fail;
                 uint32_t *t = qcur;
                 qcur = qnext;
                 qnext = t;
             }
-            if (s_fail) break;
+            if (stop) break;
             // ---- the near queue is empty: find the smallest pending priority
             if (tid == 0) {
                 s_minp = INF;
+                s_ncur = 0;  // the collect step counts from zero (read before the barrier above)
                 s_tel[T_BOUNDS]++;
             }
             __syncthreads();
