@@ -101,6 +101,11 @@ class Oracle:
                            C.c_uint32, C.c_uint64, C.c_uint64, C.POINTER(_Pairs)]
         L.og_pairs_free.argtypes = [C.POINTER(_Pairs)]
         L.og_floyd_warshall.argtypes = [C.c_void_p, C.POINTER(C.c_uint64)]
+        # points on edges: arrays of (a, b, t) uint32 triples
+        L.og_join_points.argtypes = [C.c_void_p, C.POINTER(C.c_uint32), C.c_uint32, C.POINTER(C.c_uint32),
+                                     C.c_uint32, C.c_uint64, C.POINTER(_Pairs)]
+        L.og_kcp_points.argtypes = [C.c_void_p, C.POINTER(C.c_uint32), C.c_uint32, C.POINTER(C.c_uint32),
+                                    C.c_uint32, C.c_uint64, C.c_uint64, C.POINTER(_Pairs)]
 
     def graph(self, n: int, src, dst, w, undirected: bool = True) -> "OGraph":
         return OGraph(self, n, src, dst, w, undirected)
@@ -178,10 +183,27 @@ class OGraph:
         return self._pairs(self.o.lib.og_kcp_bruteforce, _ptr(r, C.c_uint32), len(r),
                            _ptr(s, C.c_uint32), len(s), int(k), int(theta))
 
+    def join_points(self, R, S, theta: int) -> Pairs:
+        """Join of points on edges: R, S are (count, 3) arrays of (a, b, t); pairs are
+        (index in R, index in S, distance)."""
+        r, s = _points(R), _points(S)
+        return self._pairs(self.o.lib.og_join_points, _ptr(r, C.c_uint32), len(r), _ptr(s, C.c_uint32),
+                           len(s), int(theta))
+
+    def kcp_points(self, R, S, k: int, theta: int = THETA_MAX) -> Pairs:
+        r, s = _points(R), _points(S)
+        return self._pairs(self.o.lib.og_kcp_points, _ptr(r, C.c_uint32), len(r), _ptr(s, C.c_uint32),
+                           len(s), int(k), int(theta))
+
     def floyd_warshall(self) -> np.ndarray:
         D = np.zeros(self.n * self.n, np.uint64)
         self.o.lib.og_floyd_warshall(self.h, _ptr(D, C.c_uint64))
         return D.reshape(self.n, self.n)
+
+
+def _points(P) -> np.ndarray:
+    a = np.ascontiguousarray(np.asarray(P, dtype=np.uint32).reshape(-1, 3))
+    return a if len(a) else np.zeros((1, 3), np.uint32)[:0]
 
 
 _default: Oracle | None = None

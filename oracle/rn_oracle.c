@@ -29,6 +29,12 @@
  *   - weights lie in [1, 2^24) and theta in [0, 2^31]; distances are kept in 64 bits
  *     here so no sum can wrap.
  *
+ * Points on edges (Section 1: objects moving on an edge are searched from the two ends
+ * of their edge, at their distances from those ends): a point on the undirected edge
+ * {a, b} at distance t from a; its distance to a node x is the better of
+ * t + dist(a, x) and (w - t) + dist(b, x), w the edge's weight; two points on the same
+ * edge may also meet along it, at the difference of their positions.
+ *
  * Parity pins (tests, run without a GPU): Floyd-Warshall brute force on tiny graphs,
  * closed-form distances on grids, paths and stars, the transpose symmetry of the join
  * on undirected graphs, monotonicity in theta and k, and kCP against its own
@@ -466,4 +472,136 @@ int og_floyd_warshall(const og_graph *g, uint64_t *D) {
             }
         }
     return OG_OK;
+}
+
+/* ------------------------------------------------------------ points on edges ---- */
+
+/* A point on the undirected edge {a, b}, at distance t from a, 0 <= t <= w(a, b) (the
+ * least weight among parallel a-b edges). */
+typedef struct {
+    uint32_t a, b, t;
+} og_point;
+
+/* The least weight of an arc a -> b, or OG_INF if there is none. */
+static uint64_t arc_weight(const og_graph *g, uint32_t a, uint32_t b) {
+    uint64_t best = OG_INF;
+    for (uint64_t e = g->off[a]; e < g->off[a + 1]; e++)
+        if (g->to[e] == b && g->w[e] < best) best = g->w[e];
+    return best;
+}
+
+static int check_points(const og_graph *g, const og_point *P, uint32_t nP, uint64_t *w) {
+    for (uint32_t i = 0; i < nP; i++) {
+        if (P[i].a >= g->n || P[i].b >= g->n || P[i].a == P[i].b) return OG_EINVAL;
+        uint64_t wab = arc_weight(g, P[i].a, P[i].b), wba = arc_weight(g, P[i].b, P[i].a);
+        if (wab == OG_INF || wab != wba || P[i].t > wab) return OG_EINVAL; /* an undirected edge */
+        w[i] = wab;
+    }
+    return OG_OK;
+}
+
+/* Bounded search from a point: Dijkstra seeded at a with t and at b with w - t (seeds
+ * above the bound are left out), otherwise as og_sssp. */
+static int sssp_point(const og_graph *g, og_point p, uint64_t w, uint64_t bound, uint64_t *dist) {
+    for (uint32_t x = 0; x < g->n; x++) dist[x] = OG_INF;
+    uint8_t *done = (uint8_t *)calloc(g->n, 1);
+    og_heap h = {0};
+    if (!done) return OG_ENOMEM;
+    int rc = OG_OK;
+    const uint32_t seed[2] = {p.a, p.b};
+    const uint64_t sd[2] = {p.t, w - p.t};
+    for (int i = 0; i < 2 && rc == OG_OK; i++) {
+        if (sd[i] > bound || sd[i] >= dist[seed[i]]) continue;
+        dist[seed[i]] = sd[i];
+        rc = heap_push(&h, sd[i], seed[i]);
+    }
+    while (rc == OG_OK && h.len > 0) {
+        og_item it = heap_pop(&h);
+        if (done[it.node] || it.key != dist[it.node]) continue;
+        if (it.key > bound) break;
+        done[it.node] = 1;
+        for (uint64_t e = g->off[it.node]; e < g->off[it.node + 1]; e++) {
+            uint64_t nd = it.key + g->w[e];
+            uint32_t y = g->to[e];
+            if (nd > bound) continue;
+            if (nd < dist[y]) {
+                dist[y] = nd;
+                rc = heap_push(&h, nd, y);
+                if (rc) break;
+            }
+        }
+    }
+    for (uint32_t x = 0; x < g->n; x++)
+        if (!done[x]) dist[x] = OG_INF;
+    free(done);
+    free(h.a);
+    return rc;
+}
+
+/* theta-join of points: every (i, j), R[i] to S[j] within theta, with its distance,
+ * sorted by (i, j).  The distance from R[i] to S[j] on edge {c, e} at s from c is the
+ * least of dist(R[i], c) + s and dist(R[i], e) + (w - s), and, when both lie on the
+ * same edge, the gap between their positions along it. */
+int og_join_points(const og_graph *g, const og_point *R, uint32_t nR, const og_point *S, uint32_t nS,
+                   uint64_t theta, og_pairs *out) {
+    memset(out, 0, sizeof(*out));
+    if (theta > OG_THETA_MAX) return OG_EINVAL;
+    uint64_t *wR = (uint64_t *)malloc(((size_t)nR + 1) * sizeof(uint64_t));
+    uint64_t *wS = (uint64_t *)malloc(((size_t)nS + 1) * sizeof(uint64_t));
+    uint64_t *dist = (uint64_t *)malloc(((size_t)g->n + 1) * sizeof(uint64_t));
+    uint64_t cap = 1024, n = 0;
+    og_triple *t = (og_triple *)malloc(cap * sizeof(og_triple));
+    int rc = (!wR || !wS || !dist || !t) ? OG_ENOMEM : OG_OK;
+    if (rc == OG_OK) rc = check_points(g, R, nR, wR);
+    if (rc == OG_OK) rc = check_points(g, S, nS, wS);
+    for (uint32_t i = 0; i < nR && rc == OG_OK; i++) {
+        rc = sssp_point(g, R[i], wR[i], theta, dist);
+        for (uint32_t j = 0; j < nS && rc == OG_OK; j++) {
+            const og_point q = S[j];
+            uint64_t d = OG_INF;
+            if (dist[q.a] != OG_INF) d = dist[q.a] + q.t;
+            if (dist[q.b] != OG_INF && dist[q.b] + (wS[j] - q.t) < d) d = dist[q.b] + (wS[j] - q.t);
+            if (q.a == R[i].a && q.b == R[i].b) {
+                uint64_t gap = q.t > R[i].t ? q.t - R[i].t : R[i].t - q.t;
+                if (gap < d) d = gap;
+            } else if (q.a == R[i].b && q.b == R[i].a) {
+                uint64_t pos = wS[j] - q.t; /* S[j]'s distance from R[i].a */
+                uint64_t gap = pos > R[i].t ? pos - R[i].t : R[i].t - pos;
+                if (gap < d) d = gap;
+            }
+            if (d > theta) continue;
+            if (n == cap) {
+                og_triple *nt = (og_triple *)realloc(t, 2 * cap * sizeof(og_triple));
+                if (!nt) { rc = OG_ENOMEM; break; }
+                t = nt;
+                cap *= 2;
+            }
+            t[n].u = i; t[n].v = j; t[n].d = d; n++;
+        }
+    }
+    if (rc == OG_OK) {
+        qsort(t, n, sizeof(og_triple), cmp_uv);
+        rc = store_pairs(t, n, out);
+    }
+    free(t); free(dist); free(wR); free(wS);
+    return rc;
+}
+
+/* k closest pairs of points within theta, by its definition: the whole join, sorted by
+ * (d, i, j), cut to the first k. */
+int og_kcp_points(const og_graph *g, const og_point *R, uint32_t nR, const og_point *S, uint32_t nS,
+                  uint64_t k, uint64_t theta, og_pairs *out) {
+    if (k == 0) return OG_EINVAL;
+    og_pairs all;
+    int rc = og_join_points(g, R, nR, S, nS, theta, &all);
+    memset(out, 0, sizeof(*out));
+    if (rc) return rc;
+    og_triple *t = (og_triple *)malloc((all.n ? all.n : 1) * sizeof(og_triple));
+    if (!t) { og_pairs_free(&all); return OG_ENOMEM; }
+    for (uint64_t i = 0; i < all.n; i++) { t[i].u = all.u[i]; t[i].v = all.v[i]; t[i].d = all.d[i]; }
+    qsort(t, all.n, sizeof(og_triple), cmp_duv);
+    rc = store_pairs(t, all.n < k ? all.n : k, out);
+    free(t);
+    og_pairs_free(&all);
+    return rc;
 }

@@ -17,6 +17,10 @@ What pins what:
 * Input rules: ids out of range, repeated ids, R and S overlapping, bad weights.
 * Edge-list cleaning: self-loops dropped and parallel edges reduced to their least
   weight (checked against a numpy reduction of the same edge list).
+* Points on edges (Section 1: objects moving on edges): the join and kCP of points equal
+  the node search on the graph subdivided at the points (an independent formulation:
+  new nodes on chains of shorter edges, the node search itself pinned above); points on
+  a path are at the gap between their positions; a point at a node is that node.
 """
 from __future__ import annotations
 
@@ -214,5 +218,106 @@ def pin_cleaning(o, seeds=range(10)):
             "multigraph join != cleaned graph join"
 
 
+def least_weights(e):
+    """The least weight of every undirected edge {p < q} of an edge list."""
+    best = {}
+    for a, b, w in zip(e.src.tolist(), e.dst.tolist(), e.w.tolist()):
+        if a != b:
+            k = (min(a, b), max(a, b))
+            best[k] = min(best.get(k, 1 << 40), w)
+    return best
+
+
+def subdivide(n, best, points):
+    """The graph subdivided at the points: every edge carrying points becomes a chain
+    through one new node per distinct inner position (a point at an end is that end).
+    Returns (node count, src, dst, w, node of every point)."""
+    on = {}
+    for i, (a, b, t) in enumerate(points):
+        k = (min(a, b), max(a, b))
+        on.setdefault(k, []).append((t if a == k[0] else best[k] - t, i))
+    src, dst, w = [], [], []
+    for (p, q), ww in best.items():
+        if (p, q) not in on:
+            src.append(p), dst.append(q), w.append(ww)
+    node = [0] * len(points)
+    nxt = n
+    for (p, q), lst in on.items():
+        W = best[(p, q)]
+        at = {0: p, W: q}
+        for pos in sorted({pos for pos, _ in lst}):
+            if pos not in at:
+                at[pos] = nxt
+                nxt += 1
+        chain = sorted(at.items())
+        for (p0, n0), (p1, n1) in zip(chain, chain[1:]):
+            src.append(n0), dst.append(n1), w.append(p1 - p0)
+        for pos, i in lst:
+            node[i] = at[pos]
+    return nxt, np.array(src, np.uint32), np.array(dst, np.uint32), np.array(w, np.uint32), node
+
+
+def random_points(rng, best, count):
+    """Points on random edges: at either end, or anywhere, named from either end."""
+    keys = list(best)
+    out = []
+    for _ in range(count):
+        p, q = keys[rng.integers(len(keys))]
+        W = best[(p, q)]
+        t = int(rng.choice([0, W, rng.integers(0, W + 1), rng.integers(0, W + 1)]))
+        out.append((p, q, t) if rng.random() < 0.5 else (q, p, W - t))
+    return out
+
+
+def points_by_subdivision(o, e, R, S, theta):
+    """(i, j, d) of the points join, from node searches on the subdivided graph."""
+    best = least_weights(e)
+    m, src, dst, w, node = subdivide(e.n, best, list(R) + list(S))
+    g = o.graph(m, src, dst, w)
+    rows = []
+    for i in range(len(R)):
+        dist, _ = g.sssp(node[i], theta)
+        for j in range(len(S)):
+            d = dist[node[len(R) + j]]
+            if d != INF64:
+                rows.append((i, j, int(d)))
+    return rows
+
+
+def pin_points(o, seeds=range(6)):
+    for seed in seeds:
+        rng = np.random.default_rng(900 + seed)
+        n = int(rng.integers(30, 300))
+        e = I.road_graph(n, int(2.77 * n), 950 + seed)
+        best = least_weights(e)
+        pts = random_points(rng, best, int(rng.integers(2, 30)))
+        k = list(best)[0]
+        pts += [pts[0], pts[1]] + [(k[0], k[1], t) for t in (0, 1, best[k] // 2, best[k])]
+        pts += [(k[1], k[0], best[k] // 3)]
+        R, S = pts[: len(pts) // 2], pts[len(pts) // 2:]
+        og = o.graph(e.n, e.src, e.dst, e.w)
+        for theta in (0, int(np.median(e.w)) * 3, THETA_MAX):
+            got = og.join_points(R, S, theta)
+            ref = points_by_subdivision(o, e, R, S, theta)
+            assert list(zip(got.u.tolist(), got.v.tolist(), got.d.tolist())) == ref, f"points seed {seed}"
+            refk = sorted(ref, key=lambda r: (r[2], r[0], r[1]))
+            for kk in (1, 5, len(ref) + 3):
+                gk = og.kcp_points(R, S, kk, theta)
+                assert list(zip(gk.u.tolist(), gk.v.tolist(), gk.d.tolist())) == refk[:kk]
+    # points on a path: distance = gap between positions along the line
+    w = [2, 3, 5, 7]
+    e = I.path_graph(w)
+    og = o.graph(e.n, e.src, e.dst, e.w)
+    start = np.concatenate([[0], np.cumsum(w)])
+    pts, pos = [], []
+    for i, wi in enumerate(w):
+        for t in range(0, wi + 1):
+            pts.append((i, i + 1, t) if t % 2 else (i + 1, i, wi - t))
+            pos.append(int(start[i]) + t)
+    got = og.join_points(pts, pts, THETA_MAX)
+    assert len(got) == len(pts) ** 2
+    assert all(int(d) == abs(pos[i] - pos[j]) for i, j, d in zip(got.u, got.v, got.d))
+
+
 ALL_PINS = [pin_fw_random, pin_closed_forms, pin_invariants, pin_triangle, pin_validation,
-            pin_cleaning]
+            pin_cleaning, pin_points]

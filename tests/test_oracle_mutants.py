@@ -43,13 +43,25 @@ MUTANTS = {
     "dropped_weight": ("            uint64_t nd = it.key + g->w[e];\n            uint32_t y = g->to[e];\n            if (nd > bound) continue;\n            if (nd < dist[y]) {\n                dist[y] = nd;\n                rc = heap_push(&h, nd, y);\n                if (rc) break;\n            }\n        }\n    }\n    /* nodes",
                        "            uint64_t nd = it.key + 1;\n            uint32_t y = g->to[e];\n            if (nd > bound) continue;\n            if (nd < dist[y]) {\n                dist[y] = nd;\n                rc = heap_push(&h, nd, y);\n                if (rc) break;\n            }\n        }\n    }\n    /* nodes"),
     # the join sorted (v, u)
-    "join_sorted_vu": ("        qsort(t, n, sizeof(og_triple), cmp_uv);", "        qsort(t, n, sizeof(og_triple), cmp_duv);"),
+    "join_sorted_vu": ("        qsort(t, n, sizeof(og_triple), cmp_uv);\n        uint64_t arcs = out->arcs;",
+                       "        qsort(t, n, sizeof(og_triple), cmp_duv);\n        uint64_t arcs = out->arcs;"),
     # overlap of R and S no longer rejected
     "overlap_accepted": ("        if (S[i] >= n || mark[S[i]]) { free(mark); return OG_EINVAL; }",
                          "        if (S[i] >= n || mark[S[i]] == 2) { free(mark); return OG_EINVAL; }"),
     # emits a pair for every reached node, not only members of S
     "emit_non_members": ("            if (!inS[x] || dist[x] == OG_INF) continue;",
                          "            if (dist[x] == OG_INF) continue;"),
+    # points: the meeting of two points along their shared edge forgotten
+    "points_no_same_edge": ("                uint64_t gap = q.t > R[i].t ? q.t - R[i].t : R[i].t - q.t;\n                if (gap < d) d = gap;\n",
+                            ""),
+    # points: the search seeded at the far end with t instead of w - t
+    "points_far_seed": ("    const uint64_t sd[2] = {p.t, w - p.t};", "    const uint64_t sd[2] = {p.t, p.t};"),
+    # points: an S point reached from its far end at t instead of w - t
+    "points_far_offset": ("if (dist[q.b] != OG_INF && dist[q.b] + (wS[j] - q.t) < d) d = dist[q.b] + (wS[j] - q.t);",
+                          "if (dist[q.b] != OG_INF && dist[q.b] + q.t < d) d = dist[q.b] + q.t;"),
+    # points: on a shared edge named the other way round, the position not mirrored
+    "points_unmirrored": ("                uint64_t pos = wS[j] - q.t; /* S[j]'s distance from R[i].a */",
+                          "                uint64_t pos = q.t; /* S[j]'s distance from R[i].a */"),
     # Floyd-Warshall with the intermediate loop in the middle
     "fw_loop_order": ("    for (uint32_t m = 0; m < n; m++)\n        for (uint32_t i = 0; i < n; i++) {",
                       "    for (uint32_t i = 0; i < n; i++)\n        for (uint32_t m = 0; m < n; m++) {"),
