@@ -227,6 +227,31 @@ rn_status rn_kcp(const rn_graph *g, const uint32_t *R, uint32_t nR, const uint32
 rn_status rn_kcp_dev(const rn_graph *g, const uint32_t *dR, uint32_t nR, const uint32_t *dS,
                      uint32_t nS, uint64_t k, uint32_t theta, rn_dpairs *out, rn_stream stream);
 
+/* ---------------------------------------------------------- points on edges ---- */
+
+/* A point on the undirected edge {a, b} at distance t from a (0 <= t <= w, w the edge's
+ * weight): an object on the road between two nodes (Section 1: objects moving on edges
+ * are searched from the two ends of their edge). */
+typedef struct {
+    uint32_t a, b, t;
+} rn_point;
+
+/*
+ * rn_distance_join_points -- the theta-join of points: every (i, j) with the network
+ * distance from R[i] to S[j] <= theta, as (u = i, v = j, d), sorted by (u, v).  The
+ * distance runs from a point through either end of its edge (or along the edge, for two
+ * points on the same edge).  R and S are host arrays of points, which may coincide.
+ * RN_EINVAL if a point's {a, b} is not an undirected edge of the graph (both arcs, one
+ * weight), a == b, an id is >= n, or t exceeds the edge's weight.  The graph is
+ * subdivided at the points for the query (a device copy of the graph plus two arcs per
+ * point), then searched as rn_distance_join searches.
+ */
+rn_status rn_distance_join_points(const rn_graph *g, const rn_point *R, uint32_t nR, const rn_point *S, uint32_t nS,
+                                  uint32_t theta, rn_pairs *out);
+/* k closest pairs of points within theta, sorted by (d, u, v); u, v index R and S. */
+rn_status rn_kcp_points(const rn_graph *g, const rn_point *R, uint32_t nR, const rn_point *S, uint32_t nS,
+                        uint64_t k, uint32_t theta, rn_pairs *out);
+
 /* ------------------------------------------------------------------ batches ---- */
 
 /* One theta-join of a batch.  R and S are host arrays and g a loaded graph, read only by

@@ -237,6 +237,7 @@ void rn_graph_free(rn_graph *g) {
     if (!g) return;
     try {
         drop_scratch(g);
+        rn::points_destroy(g->points);
         rn::workspace_destroy(g->ws);
         rn::free_graph(&g->dev);
     } catch (...) {
@@ -362,6 +363,50 @@ rn_status rn_kcp(const rn_graph *cg, const uint32_t *R, uint32_t nR, const uint3
         rn::to_host_pairs(hs.res, out, hs.stream);
         g_last_stats = st;
         g_have_stats = true;
+    });
+}
+
+namespace {
+
+void check_points_host(uint32_t n, const rn_point *P, uint32_t nP, const char *name) {
+    if (nP && !P) rn::fail(RN_EINVAL, std::string("null ") + name + " with a non-zero size");
+    for (uint32_t i = 0; i < nP; i++) {
+        if (P[i].a >= n || P[i].b >= n)
+            rn::fail(RN_EINVAL, std::string(name) + "[" + std::to_string(i) + "]: an end id is >= n");
+        if (P[i].a == P[i].b) rn::fail(RN_EINVAL, std::string(name) + "[" + std::to_string(i) + "]: a == b");
+    }
+}
+
+void points_query(const rn_graph *cg, const rn_point *R, uint32_t nR, const rn_point *S, uint32_t nS, uint64_t k,
+                  uint32_t theta, rn_pairs *out) {
+    if (!cg || !out) rn::fail(RN_EINVAL, "null argument");
+    *out = rn_pairs{};
+    check_theta(theta);
+    rn_graph *g = const_cast<rn_graph *>(cg);
+    check_points_host(g->dev.n, R, nR, "R");
+    check_points_host(g->dev.n, S, nS, "S");
+    std::lock_guard<std::mutex> lk(g->mu);
+    rn::HostScratch &hs = scratch_of(g);
+    rn_query_stats st{};
+    rn::run_points(g->dev, g->perm, &g->points, g->cfg, g->info.median_weight, R, nR, S, nS, k, theta, &hs.res,
+                   hs.stream, &st);
+    rn::to_host_pairs(hs.res, out, hs.stream);
+    g_last_stats = st;
+    g_have_stats = true;
+}
+
+}  // namespace
+
+rn_status rn_distance_join_points(const rn_graph *g, const rn_point *R, uint32_t nR, const rn_point *S, uint32_t nS,
+                                  uint32_t theta, rn_pairs *out) {
+    return guarded([&] { points_query(g, R, nR, S, nS, 0, theta, out); });
+}
+
+rn_status rn_kcp_points(const rn_graph *g, const rn_point *R, uint32_t nR, const rn_point *S, uint32_t nS,
+                        uint64_t k, uint32_t theta, rn_pairs *out) {
+    return guarded([&] {
+        if (k == 0) rn::fail(RN_EINVAL, "k must be >= 1");
+        points_query(g, R, nR, S, nS, k, theta, out);
     });
 }
 

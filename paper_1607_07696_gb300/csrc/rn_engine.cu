@@ -2089,6 +2089,227 @@ void run_kcp(const DeviceGraph &g, Workspace *ws, const EngineConfig &cfg, uint3
     stats->search_ms = sms;
 }
 
+// ------------------------------------------------------------ points on edges ----
+// Joins and k closest pairs of points that lie on edges (objects moving on the road
+// network, searched from the two ends of their edge: Section 1).  The query runs the
+// ordinary engine over the graph subdivided at its points: every point becomes a node,
+// and every edge {p, q} that carries points becomes a chain p - o_1 - ... - o_k - q with
+// links of the positions' differences (a point at an end, or two points at one
+// position, give links of weight 0).  The subdivided graph is built on the device for
+// each query: a copy of the graph's arrays, the two arcs p->q and q->p turned into the
+// chain's first and last links, and two arcs per point node; the point nodes' output
+// ids are their indices in R and S.  R's points are numbered in the order of their
+// edges' internal ids, so a tile's sources lie near each other.
+
+// For each undirected edge {p, q} (p < q, internal ids): the positions of the arcs
+// p->q and q->p in adj and their weights, EMPTY where there is no such arc.
+__global__ void k_edge_find(const uint32_t *__restrict__ row_ptr, const uint2 *__restrict__ adj,
+                            const uint2 *__restrict__ keys, uint32_t nkeys, uint4 *out) {
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < nkeys; i += gridDim.x * blockDim.x) {
+        const uint2 k = keys[i];
+        uint4 r = make_uint4(EMPTY, EMPTY, EMPTY, EMPTY);
+        for (uint32_t e = row_ptr[k.x]; e < row_ptr[k.x + 1]; e++)
+            if (adj[e].x == k.y && (r.x == EMPTY || adj[e].y < r.z)) {
+                r.x = e;
+                r.z = adj[e].y;
+            }
+        for (uint32_t e = row_ptr[k.y]; e < row_ptr[k.y + 1]; e++)
+            if (adj[e].x == k.x && (r.y == EMPTY || adj[e].y < r.w)) {
+                r.y = e;
+                r.w = adj[e].y;
+            }
+        out[i] = r;
+    }
+}
+
+// adj[pos] = (target, weight) for every patch (pos, target, weight).
+__global__ void k_patch_arcs(uint2 *adj, const uint4 *__restrict__ patches, uint32_t n, uint64_t arcs) {
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const uint4 pt = patches[i];
+        if (pt.x < arcs) adj[pt.x] = make_uint2(pt.y, pt.z);
+    }
+}
+
+struct PointsState {
+    DeviceGraph aug;
+    uint64_t cap_nodes = 0, cap_arcs = 0;
+    Workspace *ws = nullptr;  // bitmaps sized for cap_nodes
+    uint32_t *ids = nullptr;  // R ids then S ids (the point nodes)
+    uint32_t cap_ids = 0;
+    uint2 *keys = nullptr;
+    uint4 *found = nullptr, *patches = nullptr;
+    uint32_t cap_keys = 0;
+};
+
+void points_destroy(PointsState *ps) {
+    if (!ps) return;
+    for (void *p : {(void *)ps->aug.row_ptr, (void *)ps->aug.adj, (void *)ps->aug.perm, (void *)ps->aug.iperm,
+                    (void *)ps->ids, (void *)ps->keys, (void *)ps->found, (void *)ps->patches})
+        device_free(p);
+    workspace_destroy(ps->ws);
+    delete ps;
+}
+
+// Build the subdivided graph for the points in ps->aug (grow-only buffers).
+static void points_graph(const DeviceGraph &g, const std::vector<uint32_t> &perm, const rn_point *R, uint32_t nR,
+                         const rn_point *S, uint32_t nS, PointsState *ps, cudaStream_t st) {
+    const uint32_t np = nR + nS;
+    const uint64_t n_aug = uint64_t(g.n) + np, arcs_aug = g.arcs + 2ull * np;
+    if (n_aug >= 0xFFFFFFFFull || arcs_aug >= 0xFFFFFFFFull) fail(RN_EINVAL, "too many points for this graph");
+    struct P {
+        uint32_t p, q, pos_raw, from_p, idx;  // edge {p < q}; t from a; a == p?; index in R ++ S
+    };
+    std::vector<P> pts(np);
+    for (uint32_t i = 0; i < np; i++) {
+        const rn_point &x = i < nR ? R[i] : S[i - nR];
+        const uint32_t a = perm[x.a], b = perm[x.b];
+        pts[i] = {std::min(a, b), std::max(a, b), x.t, a < b ? 1u : 0u, i};
+    }
+    // the distinct edges, and their arcs on the device
+    std::vector<uint32_t> order(np);
+    for (uint32_t i = 0; i < np; i++) order[i] = i;
+    std::sort(order.begin(), order.end(), [&](uint32_t x, uint32_t y) {
+        return pts[x].p != pts[y].p ? pts[x].p < pts[y].p : pts[x].q != pts[y].q ? pts[x].q < pts[y].q : x < y;
+    });
+    std::vector<uint2> keys;
+    std::vector<uint32_t> key_of(np);
+    for (uint32_t j = 0; j < np; j++) {
+        const P &x = pts[order[j]];
+        if (keys.empty() || keys.back().x != x.p || keys.back().y != x.q) keys.push_back(make_uint2(x.p, x.q));
+        key_of[order[j]] = uint32_t(keys.size() - 1);
+    }
+    const uint32_t nk = uint32_t(keys.size());
+    if (ps->cap_keys < std::max<uint32_t>(nk, 1)) {
+        for (void **q : {(void **)&ps->keys, (void **)&ps->found, (void **)&ps->patches}) {
+            device_free(*q);
+            *q = nullptr;
+        }
+        ps->cap_keys = std::max<uint32_t>(nk, 1024);
+        ps->keys = (uint2 *)device_alloc(size_t(ps->cap_keys) * 8);
+        ps->found = (uint4 *)device_alloc(size_t(ps->cap_keys) * 16);
+        ps->patches = (uint4 *)device_alloc(size_t(ps->cap_keys) * 2 * 16);
+    }
+    std::vector<uint4> found(nk);
+    if (nk) {
+        RN_CUDA(cudaMemcpyAsync(ps->keys, keys.data(), size_t(nk) * 8, cudaMemcpyHostToDevice, st));
+        k_edge_find<<<std::min<uint32_t>((nk + 255) / 256, 1024), 256, 0, st>>>(
+            g.row_ptr, reinterpret_cast<const uint2 *>(g.adj), ps->keys, nk, ps->found);
+        RN_CUDA(cudaGetLastError());
+        RN_CUDA(cudaMemcpyAsync(found.data(), ps->found, size_t(nk) * 16, cudaMemcpyDeviceToHost, st));
+        RN_CUDA(cudaStreamSynchronize(st));
+    }
+    // positions from p, checked against the edge
+    std::vector<uint32_t> pos(np);
+    for (uint32_t i = 0; i < np; i++) {
+        const uint4 f = found[key_of[i]];
+        const rn_point &x = i < nR ? R[i] : S[i - nR];
+        const std::string who = (i < nR ? "R[" + std::to_string(i) : "S[" + std::to_string(i - nR)) + "]";
+        if (f.x == EMPTY || f.y == EMPTY || f.z != f.w)
+            fail(RN_EINVAL, who + ": {" + std::to_string(x.a) + ", " + std::to_string(x.b) + "} is not an undirected edge");
+        if (pts[i].pos_raw > f.z) fail(RN_EINVAL, who + ": t is longer than its edge");
+        pos[i] = pts[i].from_p ? pts[i].pos_raw : f.z - pts[i].pos_raw;
+    }
+    // node ids: R points in the order of their edges (locality), then S points
+    std::vector<uint32_t> node(np), rank_ids(np);
+    {
+        uint32_t nextR = 0, nextS = 0;
+        for (uint32_t j = 0; j < np; j++) {
+            const uint32_t i = order[j];
+            if (i < nR) node[i] = g.n + nextR++;
+        }
+        for (uint32_t i = nR; i < np; i++) node[i] = g.n + nR + nextS++;
+        for (uint32_t i = 0; i < np; i++) rank_ids[node[i] - g.n] = i < nR ? i : i - nR;
+    }
+    // chains: per edge, its points by position (then index), links between neighbours
+    std::vector<uint32_t> tail(2 * size_t(np) * 2);  // object rows: (col, w) x 2 per point node
+    std::vector<uint4> patches;
+    patches.reserve(2 * size_t(nk));
+    std::sort(order.begin(), order.end(), [&](uint32_t x, uint32_t y) {
+        if (key_of[x] != key_of[y]) return key_of[x] < key_of[y];
+        return pos[x] != pos[y] ? pos[x] < pos[y] : x < y;
+    });
+    for (uint32_t j = 0; j < np;) {
+        uint32_t e = j;
+        while (e < np && key_of[order[e]] == key_of[order[j]]) e++;
+        const uint32_t k = key_of[order[j]];
+        const uint4 f = found[k];
+        const uint32_t p = keys[k].x, q = keys[k].y, w = f.z;
+        for (uint32_t c = j; c < e; c++) {
+            const uint32_t i = order[c], me = node[i] - g.n;
+            const uint32_t prev = c == j ? p : node[order[c - 1]], prev_pos = c == j ? 0 : pos[order[c - 1]];
+            const uint32_t next = c + 1 == e ? q : node[order[c + 1]], next_pos = c + 1 == e ? w : pos[order[c + 1]];
+            tail[4 * size_t(me) + 0] = prev;
+            tail[4 * size_t(me) + 1] = pos[i] - prev_pos;
+            tail[4 * size_t(me) + 2] = next;
+            tail[4 * size_t(me) + 3] = next_pos - pos[i];
+        }
+        patches.push_back(make_uint4(f.x, node[order[j]], pos[order[j]], 0));            // p -> o_1
+        patches.push_back(make_uint4(f.y, node[order[e - 1]], w - pos[order[e - 1]], 0));  // q -> o_k
+        j = e;
+    }
+    // the subdivided graph's arrays
+    if (ps->cap_nodes < n_aug || ps->cap_arcs < arcs_aug) {
+        for (void **q : {(void **)&ps->aug.row_ptr, (void **)&ps->aug.adj, (void **)&ps->aug.perm, (void **)&ps->aug.iperm}) {
+            device_free(*q);
+            *q = nullptr;
+        }
+        ps->cap_nodes = n_aug + n_aug / 4;
+        ps->cap_arcs = arcs_aug + arcs_aug / 4;
+        ps->aug.row_ptr = (uint32_t *)device_alloc((ps->cap_nodes + 1) * 4);
+        ps->aug.adj = (uint32_t *)device_alloc(ps->cap_arcs * 8);
+        ps->aug.perm = (uint32_t *)device_alloc(ps->cap_nodes * 4);
+        ps->aug.iperm = (uint32_t *)device_alloc(ps->cap_nodes * 4);
+        workspace_destroy(ps->ws);
+        ps->ws = nullptr;
+        DeviceGraph capg{};
+        capg.n = uint32_t(ps->cap_nodes);
+        ps->ws = workspace_create(capg);
+    }
+    ps->aug.n = uint32_t(n_aug);
+    ps->aug.arcs = arcs_aug;
+    std::vector<uint32_t> rp_tail(np), perm_tail(np);
+    for (uint32_t i = 0; i < np; i++) {
+        rp_tail[i] = uint32_t(g.arcs + 2ull * (i + 1));  // row_ptr[n + 1 + i]
+        perm_tail[i] = g.n + i;                          // the point nodes are named by themselves
+    }
+    RN_CUDA(cudaMemcpyAsync(ps->aug.row_ptr, g.row_ptr, (size_t(g.n) + 1) * 4, cudaMemcpyDeviceToDevice, st));
+    RN_CUDA(cudaMemcpyAsync(ps->aug.adj, g.adj, g.arcs * 8, cudaMemcpyDeviceToDevice, st));
+    RN_CUDA(cudaMemcpyAsync(ps->aug.perm, g.perm, size_t(g.n) * 4, cudaMemcpyDeviceToDevice, st));
+    RN_CUDA(cudaMemcpyAsync(ps->aug.iperm, g.iperm, size_t(g.n) * 4, cudaMemcpyDeviceToDevice, st));
+    if (np) {
+        RN_CUDA(cudaMemcpyAsync(ps->aug.row_ptr + g.n + 1, rp_tail.data(), size_t(np) * 4, cudaMemcpyHostToDevice, st));
+        RN_CUDA(cudaMemcpyAsync(ps->aug.adj + 2 * g.arcs, tail.data(), size_t(np) * 16, cudaMemcpyHostToDevice, st));
+        RN_CUDA(cudaMemcpyAsync(ps->aug.perm + g.n, perm_tail.data(), size_t(np) * 4, cudaMemcpyHostToDevice, st));
+        RN_CUDA(cudaMemcpyAsync(ps->aug.iperm + g.n, rank_ids.data(), size_t(np) * 4, cudaMemcpyHostToDevice, st));
+        RN_CUDA(cudaMemcpyAsync(ps->patches, patches.data(), patches.size() * 16, cudaMemcpyHostToDevice, st));
+        k_patch_arcs<<<std::min<uint32_t>((uint32_t(patches.size()) + 255) / 256, 1024), 256, 0, st>>>(
+            reinterpret_cast<uint2 *>(ps->aug.adj), ps->patches, uint32_t(patches.size()), g.arcs);
+        RN_CUDA(cudaGetLastError());
+    }
+    // the query's sets: the point nodes
+    if (ps->cap_ids < std::max<uint32_t>(np, 1)) {
+        device_free(ps->ids);
+        ps->ids = nullptr;
+        ps->cap_ids = std::max<uint32_t>(np, 1024);
+        ps->ids = (uint32_t *)device_alloc(size_t(ps->cap_ids) * 4);
+    }
+    if (np) RN_CUDA(cudaMemcpyAsync(ps->ids, perm_tail.data(), size_t(np) * 4, cudaMemcpyHostToDevice, st));
+    RN_CUDA(cudaStreamSynchronize(st));  // the host vectors above are temporaries
+}
+
+void run_points(const DeviceGraph &g, const std::vector<uint32_t> &perm, PointsState **state, const EngineConfig &cfg,
+                uint32_t median_w, const rn_point *R, uint32_t nR, const rn_point *S, uint32_t nS, uint64_t k,
+                uint32_t theta, rn_dpairs *out, void *stream, rn_query_stats *stats) {
+    if (!*state) *state = new PointsState();
+    PointsState *ps = *state;
+    cudaStream_t st = (cudaStream_t)stream;
+    points_graph(g, perm, R, nR, S, nS, ps, st);
+    if (k == 0)
+        run_join(ps->aug, ps->ws, cfg, median_w, ps->ids, nR, ps->ids + nR, nS, theta, out, stream, stats);
+    else
+        run_kcp(ps->aug, ps->ws, cfg, median_w, ps->ids, nR, ps->ids + nR, nS, k, theta, out, stream, stats);
+}
+
 // ------------------------------------------------------------------- batch ----
 // Many independent theta-joins (their own graphs, sets and thetas) searched by one
 // persistent launch per (tile width, first map, sources per tile) group.  The batch's

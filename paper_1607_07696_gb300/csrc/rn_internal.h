@@ -102,6 +102,14 @@ size_t slab_region_bytes();
 void workspace_set_slab(Workspace *ws, uint32_t *slab, uint32_t regions);
 void workspace_reserve(Workspace *ws, uint32_t max_r, uint64_t max_pairs);
 
+// Queries over points on edges (rn_engine.cu): the graph subdivided at the points, then
+// the ordinary join (k = 0) or k closest pairs.  perm: host original -> internal ids.
+struct PointsState;
+void run_points(const DeviceGraph &g, const std::vector<uint32_t> &perm, PointsState **state, const EngineConfig &cfg,
+                uint32_t median_w, const rn_point *R, uint32_t nR, const rn_point *S, uint32_t nS, uint64_t k,
+                uint32_t theta, rn_dpairs *out, void *stream, rn_query_stats *stats);
+void points_destroy(PointsState *ps);
+
 // Request servers (rn_serve.cpp): the graph must outlive its server.
 struct Server;
 Server *server_create(const rn_graph *g, uint64_t slab_bytes, uint32_t workers, uint32_t max_blocks);
@@ -148,5 +156,6 @@ struct rn_graph {
     std::vector<uint32_t> perm;  // host copy: original -> internal
     std::mutex mu;
     rn::HostScratch hs;
+    rn::PointsState *points = nullptr;  // buffers of point queries, grown as needed
     int device = 0;
 };

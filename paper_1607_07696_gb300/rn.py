@@ -82,6 +82,10 @@ class rn_batch_stats(C.Structure):
                 ("candidates", C.c_uint32), ("device_ms", C.c_double)]
 
 
+class rn_point(C.Structure):
+    _fields_ = [("a", C.c_uint32), ("b", C.c_uint32), ("t", C.c_uint32)]
+
+
 class rn_request(C.Structure):
     _fields_ = [("R", C.POINTER(C.c_uint32)), ("nR", C.c_uint32), ("S", C.POINTER(C.c_uint32)),
                 ("nS", C.c_uint32), ("theta", C.c_uint32), ("k", C.c_uint64)]
@@ -139,6 +143,10 @@ SIGNATURES = {
     "rn_serve_stats_get": (C.c_int, [C.c_void_p, C.POINTER(rn_serve_stats)]),
     "rn_serve_reset_stats": (C.c_int, [C.c_void_p]),
     "rn_serve_destroy": (None, [C.c_void_p]),
+    "rn_distance_join_points": (C.c_int, [_G, C.POINTER(rn_point), C.c_uint32, C.POINTER(rn_point), C.c_uint32,
+                                          C.c_uint32, C.POINTER(rn_pairs)]),
+    "rn_kcp_points": (C.c_int, [_G, C.POINTER(rn_point), C.c_uint32, C.POINTER(rn_point), C.c_uint32, C.c_uint64,
+                                C.c_uint32, C.POINTER(rn_pairs)]),
     "rn_pairs_free": (None, [C.POINTER(rn_pairs)]),
     "rn_dpairs_free": (None, [C.POINTER(rn_dpairs)]),
     "rn_last_error": (C.c_char_p, []),
@@ -501,3 +509,33 @@ def rn_serve_stats_get(srv: Server) -> dict:
 
 def rn_serve_reset_stats(srv: Server) -> None:
     _check(lib().rn_serve_reset_stats(srv.handle))
+
+
+# ------------------------------------------------------------- points on edges ----
+
+def _points(P) -> np.ndarray:
+    a = np.asarray(P, dtype=np.int64).reshape(-1, 3)
+    if a.size and (a.min() < 0 or a.max() > 0xFFFFFFFF):
+        raise ValueError("point fields must fit in uint32")
+    return np.ascontiguousarray(a.astype(np.uint32))
+
+
+def _pp(a: np.ndarray):
+    return a.ctypes.data_as(C.POINTER(rn_point))
+
+
+def rn_distance_join_points(g: Graph, R, S, theta: int):
+    """Points as (count, 3) arrays of (a, b, t): the point on edge {a, b} at distance t
+    from a.  Returns (u, v, d) with u, v indices into R and S, sorted by (u, v)."""
+    r, s = _points(R), _points(S)
+    p = rn_pairs()
+    _check(lib().rn_distance_join_points(g.handle, _pp(r), len(r), _pp(s), len(s), int(theta), C.byref(p)))
+    return _take_pairs(p)
+
+
+def rn_kcp_points(g: Graph, R, S, k: int, theta: int = RN_INF):
+    """k closest pairs of points, sorted by (d, u, v); u, v index R and S."""
+    r, s = _points(R), _points(S)
+    p = rn_pairs()
+    _check(lib().rn_kcp_points(g.handle, _pp(r), len(r), _pp(s), len(s), int(k), int(theta), C.byref(p)))
+    return _take_pairs(p)
