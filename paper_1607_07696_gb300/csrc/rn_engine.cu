@@ -1153,6 +1153,76 @@ __global__ void k_rs_scan(uint32_t *hist, uint32_t total) {
     }
 }
 
+// Large histograms are scanned by many blocks: each block scans a chunk of SCAN_CHUNK
+// entries in place and leaves the chunk's total, one block scans the totals, and every
+// chunk adds its offset.  A histogram buffer of n entries holds the chunk totals after
+// them (hist_words gives the size).
+constexpr uint32_t SCAN_CHUNK = 8192;  // 1024 threads x 8 entries
+__host__ __device__ constexpr uint64_t hist_words(uint64_t entries) {
+    return entries + (entries + SCAN_CHUNK - 1) / SCAN_CHUNK + 64;
+}
+
+__global__ void __launch_bounds__(1024) k_scan_chunks(uint32_t *a, uint32_t total, uint32_t *sums) {
+    __shared__ uint32_t warp_sum[32];
+    const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const uint32_t base = blockIdx.x * SCAN_CHUNK + threadIdx.x * 8;
+    uint32_t v[8], s = 0;
+#pragma unroll
+    for (int k = 0; k < 8; k++) {
+        v[k] = base + k < total ? a[base + k] : 0u;
+        s += v[k];
+    }
+    uint32_t x = s;  // inclusive scan of the threads' sums over the warp
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t t = __shfl_up_sync(FULL, x, o);
+        if (lane >= uint32_t(o)) x += t;
+    }
+    if (lane == 31) warp_sum[warp] = x;
+    __syncthreads();
+    if (warp == 0) {
+        const uint32_t wv = warp_sum[lane];
+        uint32_t y = wv;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t t = __shfl_up_sync(FULL, y, o);
+            if (lane >= uint32_t(o)) y += t;
+        }
+        warp_sum[lane] = y - wv;
+    }
+    __syncthreads();
+    uint32_t run = warp_sum[warp] + x - s;
+#pragma unroll
+    for (int k = 0; k < 8; k++) {
+        if (base + k < total) a[base + k] = run;
+        run += v[k];
+    }
+    if (threadIdx.x == 1023) sums[blockIdx.x] = run;
+}
+
+__global__ void __launch_bounds__(1024) k_scan_add(uint32_t *a, uint32_t total, const uint32_t *__restrict__ sums) {
+    const uint32_t add = sums[blockIdx.x];
+    const uint32_t base = blockIdx.x * SCAN_CHUNK + threadIdx.x * 8;
+#pragma unroll
+    for (int k = 0; k < 8; k++)
+        if (base + k < total) a[base + k] += add;
+}
+
+// Exclusive scan of hist[0, total) in place; hist holds hist_words(total) entries.
+// Returns the kernels launched.
+static uint32_t scan_hist(uint32_t *hist, uint32_t total, cudaStream_t st) {
+    if (total <= 2 * SCAN_CHUNK) {
+        k_rs_scan<<<1, 1024, 0, st>>>(hist, total);
+        return 1;
+    }
+    const uint32_t nb = (total + SCAN_CHUNK - 1) / SCAN_CHUNK;
+    uint32_t *sums = hist + total;
+    k_scan_chunks<<<nb, 1024, 0, st>>>(hist, total, sums);
+    k_rs_scan<<<1, 1024, 0, st>>>(sums, nb);
+    k_scan_add<<<nb, 1024, 0, st>>>(hist, total, sums);
+    return 3;
+}
+
 // Scatter pass.  With out_u != null the pass is the last one of a join sort and writes
 // the struct-of-arrays result (u = key >> vbits, v = key & mask, d = value) directly.
 __global__ void k_rs_scatter(const unsigned long long *__restrict__ kin, const uint32_t *__restrict__ vin,
@@ -1214,13 +1284,13 @@ static void radix_sort_to_pairs(Workspace *ws, uint64_t n, const std::vector<int
     if (n == 0) return;
     if (n > 0xFFFFFFFFull) fail(RN_EINVAL, "more than 2^32 - 1 result pairs");
     const uint32_t nblocks = uint32_t((n + RS_TILE - 1) / RS_TILE);
-    grow(ws, &ws->hist, &ws->hist_cap, uint64_t(nblocks) * 256, 4);
+    grow(ws, &ws->hist, &ws->hist_cap, hist_words(uint64_t(nblocks) * 256), 4);
     unsigned long long *ki = ws->keyA, *ko = ws->keyB;
     uint32_t *vi = ws->valA, *vo = ws->valB;
     for (size_t p = 0; p < shifts.size(); p++) {
         const bool last = p + 1 == shifts.size();
         k_rs_hist<<<nblocks, RS_THREADS, 0, st>>>(ki, vi, n, shifts[p], ws->hist, nblocks);
-        k_rs_scan<<<1, 1024, 0, st>>>(ws->hist, nblocks * 256);
+        ws->launches += scan_hist(ws->hist, nblocks * 256, st) - 1;
         k_rs_scatter<<<nblocks, RS_THREADS, 0, st>>>(ki, vi, ko, vo, n, shifts[p], ws->hist, nblocks,
                                                      last ? out->u : nullptr, last ? out->v : nullptr,
                                                      last ? out->d : nullptr, vbits);
@@ -1561,7 +1631,7 @@ void workspace_reserve(Workspace *ws, uint32_t max_r, uint64_t max_pairs) {
     ensure_ranges(&ws->failed, &ws->failed_cap, std::max<uint32_t>(max_r, 1));
     ensure_ranges(&ws->failed2, &ws->failed2_cap, std::max<uint32_t>(max_r, 1));
     ensure_pairs(ws, max_pairs);
-    grow(ws, &ws->hist, &ws->hist_cap, (max_pairs + RS_TILE - 1) / RS_TILE * 256 + 256, 4);
+    grow(ws, &ws->hist, &ws->hist_cap, hist_words((max_pairs + RS_TILE - 1) / RS_TILE * 256), 4);
 }
 
 // a2: validate R and S on the device, build the S membership bitmap and the list of R
@@ -2594,7 +2664,7 @@ static void batch_finish(Batch *b, uint64_t total, cudaStream_t st) {
     for (uint32_t sh = 0; sh < 2 * b->vbits; sh += 8) {
         const bool last = sh + 8 >= 2 * b->vbits;
         k_rs_hist<<<nblocks, RS_THREADS, 0, st>>>(ki, vi, total, int(sh), b->hist, nblocks);
-        k_rs_scan<<<1, 1024, 0, st>>>(b->hist, nblocks * 256);
+        scan_hist(b->hist, nblocks * 256, st);
         k_rs_scatter<<<nblocks, RS_THREADS, 0, st>>>(ki, vi, ko, vo, total, int(sh), b->hist, nblocks,
                                                      last ? b->out_u : nullptr, last ? b->out_v : nullptr,
                                                      last ? b->out_d : nullptr, b->vbits);
@@ -2684,10 +2754,10 @@ static uint64_t batch_run_eager(Batch *b, cudaStream_t st) {
             batch_drop_graph(b);
         }
         const uint32_t nblocks = uint32_t((b->total + RS_TILE - 1) / RS_TILE);
-        if (b->hist_cap < uint64_t(nblocks) * 256 + 256) {
+        if (b->hist_cap < hist_words(uint64_t(nblocks) * 256)) {
             device_free(b->hist);
             b->hist = nullptr;
-            b->hist_cap = uint64_t(nblocks) * 256 + 256;
+            b->hist_cap = hist_words(uint64_t(nblocks) * 256);
             b->hist = (uint32_t *)device_alloc(b->hist_cap * 4);
             batch_drop_graph(b);
         }
@@ -2738,7 +2808,8 @@ void batch_run(Batch *b, void *user_stream, bool use_graph) {
         b->ws->launches = 0;
         const uint64_t retried = batch_run_eager(b, st);
         const uint32_t passes = (2 * b->vbits + 7) / 8;
-        b->stats.launches_per_run = b->ws->launches + 3 * passes + 1;
+        const uint64_t entries = (b->total + RS_TILE - 1) / RS_TILE * 256;
+        b->stats.launches_per_run = b->ws->launches + passes * (entries <= 2 * SCAN_CHUNK ? 3 : 5) + 1;
         if (retried || !b->laid_out_by_cost) {
             // the next run starts with fitting maps and the measured tile order
             batch_adapt_maps(b);

@@ -114,3 +114,35 @@ def test_batch512_alone_and_in_the_mix(rn, oracle):
         if i in check:
             ref = oracle.graph(e.n, e.src, e.dst, e.w).join(R, S, th)
             assert same(got, ref), f"instance {i} differs from the oracle"
+
+
+def test_batch_edge_cases(rn, oracle):
+    # empty sets, theta 0 and unbounded, one-node and two-node graphs, a graph shared by
+    # several instances, an instance whose every source overflows the shared map
+    big = I.road_graph(30_000, 83_100, 91)
+    gb = rn.rn_graph_load(big.src, big.dst, big.w, big.n)
+    tiny = I.path_graph([5])
+    gt = rn.rn_graph_load(tiny.src, tiny.dst, tiny.w, tiny.n)
+    one = I.random_graph(1, 0, 1)
+    g1 = rn.rn_graph_load(one.src, one.dst, one.w, one.n)
+    Rb, Sb = I.disjoint_sets(big.n, 300, 500, 92)
+    inst = [
+        (big, gb, Rb, Sb, 40_000),
+        (big, gb, Rb[:0], Sb, 40_000),        # no sources
+        (big, gb, Rb[:7], Sb[:0], 40_000),    # no targets
+        (big, gb, Rb[:50], Sb, 0),            # theta 0: nothing (sets are disjoint)
+        (big, gb, Rb[:40], Sb, rn.RN_INF),    # unbounded: whole-graph balls
+        (tiny, gt, np.array([0]), np.array([1]), 5),
+        (tiny, gt, np.array([1]), np.array([0]), 4),
+        (one, g1, np.array([0]), np.array([], dtype=np.int64), 3),
+    ]
+    b = rn.rn_batch_create([(g, R, S, th) for (e, g, R, S, th) in inst])
+    for run in range(3):
+        rn.rn_batch_run(b)
+        for i, (e, g, R, S, th) in enumerate(inst):
+            ref = oracle.graph(e.n, e.src, e.dst, e.w).join(R, S, min(th, rn.RN_THETA_MAX))
+            assert same(rn.rn_batch_pairs(b, i), ref), f"run {run} instance {i}"
+    with pytest.raises(rn.RNError):
+        rn.rn_batch_pairs(b, len(inst))
+    with pytest.raises(rn.RNError):
+        rn.rn_batch_create([])
