@@ -100,6 +100,14 @@ typedef struct {
                              tiles that overflow are searched again with larger maps */
 } rn_config;
 
+/* An edge list in host memory (library-owned arrays: free with rn_edges_free). */
+typedef struct {
+    uint32_t n;      /* nodes */
+    uint32_t flags;  /* RN_UNDIRECTED | RN_REORDER, as the file asks the graph to be loaded */
+    uint64_t m;      /* edges */
+    uint32_t *src, *dst, *w;
+} rn_edges;
+
 /* Graph facts, filled by rn_graph_info. */
 typedef struct {
     uint32_t n;
@@ -169,6 +177,22 @@ rn_status rn_bisection_order(const uint32_t *src, const uint32_t *dst, const uin
 rn_status rn_graph_permutation(const rn_graph *g, uint32_t *perm);
 /* Change the knobs of later queries (tile_width, delta); NULL restores the defaults. */
 rn_status rn_graph_set_config(rn_graph *g, const rn_config *cfg);
+
+/*
+ * Graph files.  Two formats are read, told apart by their first bytes:
+ *   .rng  the engine's binary edge list, little-endian: "RNG1", u32 n, u32 flags,
+ *         u64 m, then u32 src[m], u32 dst[m], u32 w[m] (written by rn_graph_write_file);
+ *   .gr   DIMACS shortest-path text: "c" comment lines, "p sp n m", then m lines
+ *         "a u v w" with 1-based ids, one arc each (flags RN_REORDER).
+ * rn_file_read parses a file into host arrays; rn_graph_load_file reads it and loads the
+ * graph as rn_graph_load would with the file's flags and default knobs.  RN_EINVAL for a
+ * missing, truncated or malformed file (the message names the line or the field).
+ */
+rn_status rn_file_read(const char *path, rn_edges *out);
+void rn_edges_free(rn_edges *e);
+rn_status rn_graph_load_file(const char *path, rn_graph **out);
+rn_status rn_graph_write_file(const char *path, const uint32_t *src, const uint32_t *dst, const uint32_t *w,
+                              uint64_t m, uint32_t n, uint32_t flags);
 
 /*
  * rn_distance_join -- all (u in R, v in S) with dist(u, v) <= theta, sorted by (u, v)

@@ -22,7 +22,7 @@ LIB = os.path.join(PKG, "librn.so")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 COMMON = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-I", INCLUDE, "-I", CSRC]
-SOURCES = ["rn_engine.cu", "rn_graph.cpp", "rn_api.cpp", "rn_serve.cpp"]
+SOURCES = ["rn_engine.cu", "rn_graph.cpp", "rn_api.cpp", "rn_serve.cpp", "rn_file.cpp"]
 
 
 def nvcc() -> str:

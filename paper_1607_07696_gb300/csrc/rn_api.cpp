@@ -245,6 +245,55 @@ void rn_graph_free(rn_graph *g) {
     delete g;
 }
 
+rn_status rn_file_read(const char *path, rn_edges *out) {
+    return guarded([&] {
+        if (!out) rn::fail(RN_EINVAL, "null output");
+        *out = rn_edges{};
+        rn::EdgeFile f;
+        rn::read_edge_file(path, &f);
+        const size_t m = f.src.size(), b = std::max<size_t>(m, 1) * 4;
+        out->src = (uint32_t *)std::malloc(b);
+        out->dst = (uint32_t *)std::malloc(b);
+        out->w = (uint32_t *)std::malloc(b);
+        if (!out->src || !out->dst || !out->w) {
+            rn_edges_free(out);
+            rn::fail(RN_ENOMEM, "host allocation failed");
+        }
+        if (m) {
+            std::memcpy(out->src, f.src.data(), m * 4);
+            std::memcpy(out->dst, f.dst.data(), m * 4);
+            std::memcpy(out->w, f.w.data(), m * 4);
+        }
+        out->n = f.n;
+        out->flags = f.flags;
+        out->m = m;
+    });
+}
+
+void rn_edges_free(rn_edges *e) {
+    if (!e) return;
+    std::free(e->src);
+    std::free(e->dst);
+    std::free(e->w);
+    *e = rn_edges{};
+}
+
+rn_status rn_graph_load_file(const char *path, rn_graph **out) {
+    rn::EdgeFile f;
+    rn_status st = guarded([&] {
+        if (!out) rn::fail(RN_EINVAL, "null output");
+        *out = nullptr;
+        rn::read_edge_file(path, &f);
+    });
+    if (st != RN_OK) return st;
+    return rn_graph_load(f.src.data(), f.dst.data(), f.w.data(), f.src.size(), f.n, f.flags, nullptr, out);
+}
+
+rn_status rn_graph_write_file(const char *path, const uint32_t *src, const uint32_t *dst, const uint32_t *w,
+                              uint64_t m, uint32_t n, uint32_t flags) {
+    return guarded([&] { rn::write_edge_file(path, n, m, src, dst, w, flags); });
+}
+
 rn_status rn_graph_info(const rn_graph *g, rn_graph_stats *out) {
     return guarded([&] {
         if (!g || !out) rn::fail(RN_EINVAL, "null argument");

@@ -102,6 +102,15 @@ size_t slab_region_bytes();
 void workspace_set_slab(Workspace *ws, uint32_t *slab, uint32_t regions);
 void workspace_reserve(Workspace *ws, uint32_t max_r, uint64_t max_pairs);
 
+// Graph files (rn_file.cpp): the .rng binary edge list and DIMACS .gr text.
+struct EdgeFile {
+    uint32_t n = 0, flags = 0;
+    std::vector<uint32_t> src, dst, w;
+};
+void read_edge_file(const char *path, EdgeFile *out);
+void write_edge_file(const char *path, uint32_t n, uint64_t m, const uint32_t *src, const uint32_t *dst,
+                     const uint32_t *w, uint32_t flags);
+
 // Queries over points on edges (rn_engine.cu): the graph subdivided at the points, then
 // the ordinary join (k = 0) or k closest pairs.  perm: host original -> internal ids.
 struct PointsState;

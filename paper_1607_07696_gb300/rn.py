@@ -82,6 +82,11 @@ class rn_batch_stats(C.Structure):
                 ("candidates", C.c_uint32), ("device_ms", C.c_double)]
 
 
+class rn_edges(C.Structure):
+    _fields_ = [("n", C.c_uint32), ("flags", C.c_uint32), ("m", C.c_uint64), ("src", C.POINTER(C.c_uint32)),
+                ("dst", C.POINTER(C.c_uint32)), ("w", C.POINTER(C.c_uint32))]
+
+
 class rn_point(C.Structure):
     _fields_ = [("a", C.c_uint32), ("b", C.c_uint32), ("t", C.c_uint32)]
 
@@ -147,6 +152,10 @@ SIGNATURES = {
                                           C.c_uint32, C.POINTER(rn_pairs)]),
     "rn_kcp_points": (C.c_int, [_G, C.POINTER(rn_point), C.c_uint32, C.POINTER(rn_point), C.c_uint32, C.c_uint64,
                                 C.c_uint32, C.POINTER(rn_pairs)]),
+    "rn_file_read": (C.c_int, [C.c_char_p, C.POINTER(rn_edges)]),
+    "rn_edges_free": (None, [C.POINTER(rn_edges)]),
+    "rn_graph_load_file": (C.c_int, [C.c_char_p, C.POINTER(C.c_void_p)]),
+    "rn_graph_write_file": (C.c_int, [C.c_char_p, _P32, _P32, _P32, C.c_uint64, C.c_uint32, C.c_uint32]),
     "rn_pairs_free": (None, [C.POINTER(rn_pairs)]),
     "rn_dpairs_free": (None, [C.POINTER(rn_dpairs)]),
     "rn_last_error": (C.c_char_p, []),
@@ -539,3 +548,32 @@ def rn_kcp_points(g: Graph, R, S, k: int, theta: int = RN_INF):
     p = rn_pairs()
     _check(lib().rn_kcp_points(g.handle, _pp(r), len(r), _pp(s), len(s), int(k), int(theta), C.byref(p)))
     return _take_pairs(p)
+
+
+# ------------------------------------------------------------------ graph files ----
+
+def rn_file_read(path: str):
+    """(n, flags, src, dst, w) of a .rng or DIMACS .gr file (host arrays, copied)."""
+    e = rn_edges()
+    _check(lib().rn_file_read(os.fsencode(path), C.byref(e)))
+    try:
+        m = int(e.m)
+        arrs = [np.ctypeslib.as_array(p, shape=(max(m, 1),))[:m].copy() for p in (e.src, e.dst, e.w)]
+        return int(e.n), int(e.flags), arrs[0], arrs[1], arrs[2]
+    finally:
+        lib().rn_edges_free(C.byref(e))
+
+
+def rn_graph_load_file(path: str) -> Graph:
+    out = C.c_void_p()
+    _check(lib().rn_graph_load_file(os.fsencode(path), C.byref(out)))
+    g = Graph(out.value, 0)
+    g.n = int(rn_graph_info(g)["n"])
+    return g
+
+
+def rn_graph_write_file(path: str, src, dst, w, n: int, flags: int = RN_UNDIRECTED | RN_REORDER) -> None:
+    s, d, ww = _u32(src), _u32(dst), _u32(w)
+    if not (len(s) == len(d) == len(ww)):
+        raise ValueError("edge arrays differ in length")
+    _check(lib().rn_graph_write_file(os.fsencode(path), _p32(s), _p32(d), _p32(ww), len(s), int(n), int(flags)))
