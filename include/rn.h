@@ -409,6 +409,21 @@ void rn_serve_destroy(rn_server *s);
 void rn_pairs_free(rn_pairs *p);
 void rn_dpairs_free(rn_dpairs *p);
 
+/*
+ * rn_set_allocator -- take the library's device memory from the caller's allocator (for
+ * instance a framework's caching allocator) instead of cudaMalloc/cudaFree: both
+ * functions, or both NULL to go back to cudaMalloc.  alloc(bytes, ctx) returns device
+ * memory of the current device, aligned to 256 bytes and ready for use on any stream
+ * (the library runs its work on streams of its own), or NULL (RN_ENOMEM); free(ptr, ctx)
+ * takes it back.  Every block is returned to the allocator that made it, even after the
+ * hook changes; the library frees a block only when none of its work uses it any more.
+ * Applies to allocations made after the call, from any thread.  The no-alloc join
+ * allocates nothing either way.
+ */
+typedef void *(*rn_alloc_fn)(size_t bytes, void *ctx);
+typedef void (*rn_free_fn)(void *ptr, void *ctx);
+rn_status rn_set_allocator(rn_alloc_fn alloc, rn_free_fn free, void *ctx);
+
 /* Message of the calling thread's last failure ("" if none).  Valid until the next call. */
 const char *rn_last_error(void);
 /* Counters of the calling thread's last successful query. */

@@ -245,6 +245,10 @@ void rn_graph_free(rn_graph *g) {
     delete g;
 }
 
+rn_status rn_set_allocator(rn_alloc_fn alloc, rn_free_fn free, void *ctx) {
+    return guarded([&] { rn::set_allocator(alloc, free, ctx); });
+}
+
 rn_status rn_file_read(const char *path, rn_edges *out) {
     return guarded([&] {
         if (!out) rn::fail(RN_EINVAL, "null output");

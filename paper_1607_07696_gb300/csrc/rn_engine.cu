@@ -33,6 +33,7 @@
 #include <mutex>
 #include <string>
 #include <tuple>
+#include <unordered_map>
 
 #include "rn_internal.h"
 
@@ -54,14 +55,65 @@ constexpr unsigned FULL = 0xFFFFFFFFu;
 
 // ------------------------------------------------------------------ memory ----
 
+// Device memory comes from cudaMalloc, or from the caller's allocator when one is set
+// (rn_set_allocator).  Every block made through a hook remembers that hook, so it goes
+// back to the allocator that made it even if the hook changes later.  The library frees
+// a block only when none of its work still uses it.
+namespace {
+struct Hook {
+    rn_alloc_fn alloc = nullptr;
+    rn_free_fn free = nullptr;
+    void *ctx = nullptr;
+};
+std::mutex g_alloc_mu;
+Hook g_hook;
+std::unordered_map<void *, Hook> g_hooked;
+}  // namespace
+
+void set_allocator(rn_alloc_fn alloc, rn_free_fn free, void *ctx) {
+    if (!alloc != !free) fail(RN_EINVAL, "give both allocator functions, or neither");
+    std::lock_guard<std::mutex> lk(g_alloc_mu);
+    g_hook = Hook{alloc, free, ctx};
+}
+
 void *device_alloc(size_t bytes) {
-    void *p = nullptr;
-    RN_CUDA(cudaMalloc(&p, bytes ? bytes : 16));
+    Hook h;
+    {
+        std::lock_guard<std::mutex> lk(g_alloc_mu);
+        h = g_hook;
+    }
+    if (!bytes) bytes = 16;
+    if (!h.alloc) {
+        void *p = nullptr;
+        RN_CUDA(cudaMalloc(&p, bytes));
+        return p;
+    }
+    void *p = h.alloc(bytes, h.ctx);
+    if (!p) fail(RN_ENOMEM, "the allocator hook returned no memory for " + std::to_string(bytes) + " bytes");
+    if (reinterpret_cast<uintptr_t>(p) % 256) {
+        h.free(p, h.ctx);
+        fail(RN_EINVAL, "the allocator hook returned memory not aligned to 256 bytes");
+    }
+    std::lock_guard<std::mutex> lk(g_alloc_mu);
+    g_hooked[p] = h;
     return p;
 }
 
 void device_free(void *p) {
-    if (p) cudaFree(p);
+    if (!p) return;
+    Hook h;
+    bool hooked = false;
+    {
+        std::lock_guard<std::mutex> lk(g_alloc_mu);
+        auto it = g_hooked.find(p);
+        if (it != g_hooked.end()) {
+            h = it->second;
+            hooked = true;
+            g_hooked.erase(it);
+        }
+    }
+    if (hooked) h.free(p, h.ctx);
+    else cudaFree(p);
 }
 
 void copy_to_host(void *dst, const void *src, size_t bytes, void *stream) {

@@ -140,6 +140,7 @@ void dpairs_reserve(rn_dpairs *p, uint64_t cap);
 void dpairs_release(rn_dpairs *p);
 void copy_to_host(void *dst, const void *src, size_t bytes, void *stream);
 void copy_to_device(void *dst, const void *src, size_t bytes, void *stream);
+void set_allocator(rn_alloc_fn alloc, rn_free_fn free, void *ctx);
 void *device_alloc(size_t bytes);
 void device_free(void *p);
 void stream_sync(void *stream);

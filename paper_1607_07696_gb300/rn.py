@@ -156,6 +156,7 @@ SIGNATURES = {
     "rn_edges_free": (None, [C.POINTER(rn_edges)]),
     "rn_graph_load_file": (C.c_int, [C.c_char_p, C.POINTER(C.c_void_p)]),
     "rn_graph_write_file": (C.c_int, [C.c_char_p, _P32, _P32, _P32, C.c_uint64, C.c_uint32, C.c_uint32]),
+    "rn_set_allocator": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p]),
     "rn_pairs_free": (None, [C.POINTER(rn_pairs)]),
     "rn_dpairs_free": (None, [C.POINTER(rn_dpairs)]),
     "rn_last_error": (C.c_char_p, []),
@@ -577,3 +578,48 @@ def rn_graph_write_file(path: str, src, dst, w, n: int, flags: int = RN_UNDIRECT
     if not (len(s) == len(d) == len(ww)):
         raise ValueError("edge arrays differ in length")
     _check(lib().rn_graph_write_file(os.fsencode(path), _p32(s), _p32(d), _p32(ww), len(s), int(n), int(flags)))
+
+
+# ------------------------------------------------------------- allocator hook ----
+
+_ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p)
+_FREE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_void_p)
+_torch_hooks = []  # every hook made: blocks made through one still call it when freed
+_torch_hook_open = True
+
+
+def use_torch_allocator(enable: bool = True) -> None:
+    """Take the engine's device memory from torch's caching allocator (enable=True) or
+    from cudaMalloc again (False).  Blocks already made keep going back to the allocator
+    that made them."""
+    import atexit
+
+    import torch
+
+    if not enable:
+        _check(lib().rn_set_allocator(None, None, None))
+        return
+
+    def alloc(nbytes, ctx):
+        try:
+            dev = torch.cuda.current_device()
+            stream = torch.cuda.default_stream(dev)
+            p = torch.cuda.caching_allocator_alloc(int(nbytes), dev, stream)
+            stream.synchronize()  # the block may have been in use on that stream until now
+            return p
+        except Exception:  # noqa: BLE001 - reported to the engine as no memory
+            return None
+
+    def free(ptr, ctx):
+        if _torch_hook_open:
+            torch.cuda.caching_allocator_delete(int(ptr))
+
+    if not _torch_hooks:
+        def _close():
+            global _torch_hook_open
+            _torch_hook_open = False  # no calls into torch while the interpreter exits
+
+        atexit.register(_close)
+    hook = (_ALLOC_FN(alloc), _FREE_FN(free))
+    _torch_hooks.append(hook)
+    _check(lib().rn_set_allocator(C.cast(hook[0], C.c_void_p), C.cast(hook[1], C.c_void_p), None))
