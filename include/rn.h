@@ -367,6 +367,7 @@ typedef struct {
 
 typedef struct {
     uint64_t submitted, completed, failed, pending, running;
+    uint64_t cancelled;           /* taken off the queue by rn_serve_cancel */
     uint64_t pairs;               /* pairs returned by completed requests */
     uint64_t slab_bytes, slab_bytes_in_use, slab_bytes_peak;
     uint32_t workers, max_running;/* max_running: most requests on the device at once */
@@ -398,6 +399,10 @@ rn_status rn_serve_submit(rn_server *s, const rn_request *q, uint64_t *ticket);
  * RN_ETIMEOUT if it is not done in time (the ticket stays valid); RN_EINVAL for an
  * unknown or spent ticket; otherwise the request's own status. */
 rn_status rn_serve_wait(rn_server *s, uint64_t ticket, uint32_t timeout_ms, rn_pairs *out);
+/* Take a queued request off the queue: its wait then returns RN_ECANCELLED.  RN_EBUSY
+ * if it is already running or finished (it is never interrupted on the device);
+ * RN_EINVAL for an unknown ticket. */
+rn_status rn_serve_cancel(rn_server *s, uint64_t ticket);
 rn_status rn_serve_stats_get(rn_server *s, rn_serve_stats *out);
 /* Start a new measurement window: latency samples, counters of completed requests,
  * busy time and span restart (pending and running requests are kept). */

@@ -620,6 +620,13 @@ rn_status rn_serve_wait(rn_server *h, uint64_t ticket, uint32_t timeout_ms, rn_p
     });
 }
 
+rn_status rn_serve_cancel(rn_server *h, uint64_t ticket) {
+    return guarded([&] {
+        if (!h || !h->s) rn::fail(RN_EINVAL, "null argument");
+        rn::server_cancel(h->s, ticket);
+    });
+}
+
 rn_status rn_serve_stats_get(rn_server *h, rn_serve_stats *out) {
     return guarded([&] {
         if (!h || !h->s || !out) rn::fail(RN_EINVAL, "null argument");

@@ -126,6 +126,7 @@ uint64_t server_submit(Server *s, const uint32_t *R, uint32_t nR, const uint32_t
                        uint64_t k);
 // Throws Error(RN_ETIMEOUT) when not done in time, or the request's own error.
 void server_wait(Server *s, uint64_t ticket, uint32_t timeout_ms, rn_pairs *out);
+void server_cancel(Server *s, uint64_t ticket);
 void server_stats(Server *s, rn_serve_stats *out);
 void server_reset_stats(Server *s);
 void server_destroy(Server *s);

@@ -89,7 +89,7 @@ struct Server {
     bool stop = false;
 
     // statistics of the current window
-    uint64_t submitted = 0, completed = 0, failed = 0, pairs = 0;
+    uint64_t submitted = 0, completed = 0, failed = 0, cancelled = 0, pairs = 0;
     uint32_t running = 0, max_running = 0, units_in_use = 0, units_peak = 0;
     std::vector<double> latency_ms;
     double queue_ms = 0, busy_s = 0;
@@ -272,12 +272,34 @@ void server_wait(Server *s, uint64_t ticket, uint32_t timeout_ms, rn_pairs *out)
     q->out = rn_pairs{};
 }
 
+// Cancel a queued request: it leaves the queue and its wait returns RN_ECANCELLED.  A
+// request already on the device runs to the end (no kernel is interrupted): RN_EBUSY.
+void server_cancel(Server *s, uint64_t ticket) {
+    {
+        std::lock_guard<std::mutex> lk(s->mu);
+        auto it = s->reqs.find(ticket);
+        if (it == s->reqs.end()) fail(RN_EINVAL, "unknown ticket (never issued, or already collected)");
+        std::shared_ptr<Request> q = it->second;
+        if (q->done) fail(RN_EBUSY, "request " + std::to_string(ticket) + " has already finished");
+        auto pos = std::find(s->pending.begin(), s->pending.end(), q);
+        if (pos == s->pending.end()) fail(RN_EBUSY, "request " + std::to_string(ticket) + " is running");
+        s->pending.erase(pos);
+        q->status = RN_ECANCELLED;
+        q->err = "request " + std::to_string(ticket) + " was cancelled";
+        q->done = true;
+        s->cancelled++;
+    }
+    s->cv_done.notify_all();
+    s->cv_work.notify_all();  // the next request may fit now
+}
+
 void server_stats(Server *s, rn_serve_stats *out) {
     std::lock_guard<std::mutex> lk(s->mu);
     rn_serve_stats r{};
     r.submitted = s->submitted;
     r.completed = s->completed;
     r.failed = s->failed;
+    r.cancelled = s->cancelled;
     r.pending = s->pending.size();
     r.running = s->running;
     r.pairs = s->pairs;
@@ -308,7 +330,7 @@ void server_stats(Server *s, rn_serve_stats *out) {
 void server_reset_stats(Server *s) {
     std::lock_guard<std::mutex> lk(s->mu);
     s->submitted = s->pending.size() + s->running;
-    s->completed = s->failed = s->pairs = 0;
+    s->completed = s->failed = s->cancelled = s->pairs = 0;
     s->max_running = s->running;
     s->units_peak = s->units_in_use;
     s->latency_ms.clear();

@@ -102,7 +102,7 @@ class rn_serve_config(C.Structure):
 
 class rn_serve_stats(C.Structure):
     _fields_ = [("submitted", C.c_uint64), ("completed", C.c_uint64), ("failed", C.c_uint64),
-                ("pending", C.c_uint64), ("running", C.c_uint64), ("pairs", C.c_uint64),
+                ("pending", C.c_uint64), ("running", C.c_uint64), ("cancelled", C.c_uint64), ("pairs", C.c_uint64),
                 ("slab_bytes", C.c_uint64), ("slab_bytes_in_use", C.c_uint64),
                 ("slab_bytes_peak", C.c_uint64), ("workers", C.c_uint32), ("max_running", C.c_uint32),
                 ("p50_ms", C.c_double), ("p99_ms", C.c_double), ("max_ms", C.c_double),
@@ -145,6 +145,7 @@ SIGNATURES = {
     "rn_serve_create": (C.c_int, [_G, C.POINTER(rn_serve_config), C.POINTER(C.c_void_p)]),
     "rn_serve_submit": (C.c_int, [C.c_void_p, C.POINTER(rn_request), C.POINTER(C.c_uint64)]),
     "rn_serve_wait": (C.c_int, [C.c_void_p, C.c_uint64, C.c_uint32, C.POINTER(rn_pairs)]),
+    "rn_serve_cancel": (C.c_int, [C.c_void_p, C.c_uint64]),
     "rn_serve_stats_get": (C.c_int, [C.c_void_p, C.POINTER(rn_serve_stats)]),
     "rn_serve_reset_stats": (C.c_int, [C.c_void_p]),
     "rn_serve_destroy": (None, [C.c_void_p]),
@@ -509,6 +510,10 @@ def rn_serve_wait(srv: Server, ticket: int, timeout_ms: int = WAIT_FOREVER):
     p = rn_pairs()
     _check(lib().rn_serve_wait(srv.handle, int(ticket), int(timeout_ms), C.byref(p)))
     return _take_pairs(p)
+
+
+def rn_serve_cancel(srv: Server, ticket: int) -> None:
+    _check(lib().rn_serve_cancel(srv.handle, int(ticket)))
 
 
 def rn_serve_stats_get(srv: Server) -> dict:

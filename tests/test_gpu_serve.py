@@ -157,3 +157,52 @@ def test_destroy_with_queued_requests(rn, world):
     srv.close()  # running requests finish, queued ones are dropped
     u, v, d = rn.rn_distance_join(g, R[:50], S, 150_000)  # the graph still answers
     assert len(u) == len(rn.rn_distance_join(g, R[:50], S, 150_000)[0])
+
+
+def test_cancel_and_admission_oom(rn, world):
+    e, g = world
+    srv = rn.rn_serve_create(g, workers=1, max_blocks=4)
+    R, S = I.disjoint_sets(e.n, 2000, 2000, 5)
+    tickets = [rn.rn_serve_submit(srv, R, S, 150_000) for _ in range(6)]
+    # once the one worker has taken the first request, it is running or done; the last
+    # is still queued behind four others
+    import time
+
+    t0 = time.time()
+    while time.time() - t0 < 10:
+        st = rn.rn_serve_stats_get(srv)
+        if st["running"] or st["completed"]:
+            break
+        time.sleep(0.0005)
+    with pytest.raises(rn.RNError) as ex:
+        rn.rn_serve_cancel(srv, tickets[0])
+    assert ex.value.status == rn.RN_EBUSY
+    rn.rn_serve_cancel(srv, tickets[-1])
+    with pytest.raises(rn.RNError) as ex:
+        rn.rn_serve_wait(srv, tickets[-1])
+    assert ex.value.status == rn.RN_ECANCELLED
+    ref = rn.rn_distance_join(g, R, S, 150_000)
+    for t in tickets[:-1]:
+        assert same(rn.rn_serve_wait(srv, t), ref)
+    st = rn.rn_serve_stats_get(srv)
+    assert st["cancelled"] == 1 and st["completed"] == 5
+    with pytest.raises(rn.RNError) as ex:
+        rn.rn_serve_cancel(srv, 10**9)
+    assert ex.value.status == rn.RN_EINVAL
+    srv.close()
+    # an allocator with no memory left: the server cannot be made (RN_ENOMEM), nothing leaks
+    import ctypes as C
+
+    nomem = rn._ALLOC_FN(lambda n, ctx: None)
+    free = rn._FREE_FN(lambda p, ctx: None)
+    rn._check(rn.lib().rn_set_allocator(C.cast(nomem, C.c_void_p), C.cast(free, C.c_void_p), None))
+    try:
+        with pytest.raises(rn.RNError) as ex:
+            rn.rn_serve_create(g, workers=2, max_blocks=4)
+        assert ex.value.status == rn.RN_ENOMEM
+    finally:
+        rn._check(rn.lib().rn_set_allocator(None, None, None))
+    srv = rn.rn_serve_create(g, workers=2, max_blocks=4)  # and works again afterwards
+    assert same(rn.rn_serve_wait(srv, rn.rn_serve_submit(srv, R[:10], S, 150_000)),
+                rn.rn_distance_join(g, R[:10], S, 150_000))
+    srv.close()
