@@ -336,6 +336,12 @@ rn_status rn_batch_pairs_dev(const rn_batch *b, uint32_t i, const uint32_t **u, 
                              const uint32_t **d, uint64_t *n);
 rn_status rn_batch_stats_get(const rn_batch *b, rn_batch_stats *out);
 void rn_batch_free(rn_batch *b);
+/* The autotuner's plans (per size class: tile width, bucket width, sources per tile) to a
+ * text file, and back: a loaded file is merged into the process's plans, which later
+ * batches use without tuning.  *classes receives how many plans the file held.  RN_EINVAL
+ * for a file that cannot be written, opened or parsed. */
+rn_status rn_tune_cache_save(const char *path);
+rn_status rn_tune_cache_load(const char *path, uint32_t *classes);
 /* One call: create a batch (no autotuning), run it once, copy every instance's pairs to
  * outs[0..nq) (free each with rn_pairs_free), free the batch. */
 rn_status rn_join_batch(const rn_query *q, uint32_t nq, rn_pairs *outs);
@@ -428,6 +434,9 @@ void rn_dpairs_free(rn_dpairs *p);
 typedef void *(*rn_alloc_fn)(size_t bytes, void *ctx);
 typedef void (*rn_free_fn)(void *ptr, void *ctx);
 rn_status rn_set_allocator(rn_alloc_fn alloc, rn_free_fn free, void *ctx);
+
+/* Per-query stats are also appended as JSON lines to the file named by the environment
+ * variable RN_STATS_LOG, when it is set (read once per process). */
 
 /* Message of the calling thread's last failure ("" if none).  Valid until the next call. */
 const char *rn_last_error(void);

@@ -3,9 +3,11 @@
 // catches everything; no exception crosses the ABI.
 #include <algorithm>
 #include <chrono>
+#include <cstdio>
 #include <cstdlib>
 #include <cstring>
 #include <memory>
+#include <mutex>
 #include <new>
 
 #include <cuda_runtime.h>
@@ -65,6 +67,31 @@ rn_status guarded(F &&f) {
         return set_error(RN_EINTERNAL, e.what());
     } catch (...) {
         return set_error(RN_EINTERNAL, "unknown failure");
+    }
+}
+
+// Per-query stats as JSON lines: when the environment names a file in RN_STATS_LOG,
+// every successful query appends one line to it.
+void log_stats(const char *kind, const rn_query_stats &st) {
+    static const char *path = std::getenv("RN_STATS_LOG");
+    if (!path || !*path) return;
+    static std::mutex mu;
+    char line[1024];
+    std::snprintf(line, sizeof line,
+                  "{\"query\": \"%s\", \"pairs\": %llu, \"tiles\": %llu, \"tile_width\": %u, "
+                  "\"tile_sources\": %u, \"delta\": %u, \"theta_final\": %u, \"passes\": %u, "
+                  "\"retried_tiles\": %llu, \"slots\": %llu, \"slot_arcs\": %llu, \"scans\": %llu, "
+                  "\"rounds\": %llu, \"max_ball\": %llu, \"launches\": %u, \"device_ms\": %.4f, "
+                  "\"search_ms\": %.4f, \"retry_ms\": %.4f}\n",
+                  kind, (unsigned long long)st.pairs, (unsigned long long)st.tiles, st.tile_width, st.tile_sources,
+                  st.delta, st.theta_final, st.passes, (unsigned long long)st.retried_tiles,
+                  (unsigned long long)st.slots, (unsigned long long)st.slot_arcs, (unsigned long long)st.scans,
+                  (unsigned long long)st.rounds, (unsigned long long)st.max_ball, st.launches, st.device_ms,
+                  st.search_ms, st.retry_ms);
+    std::lock_guard<std::mutex> lk(mu);
+    if (std::FILE *f = std::fopen(path, "a")) {
+        std::fputs(line, f);
+        std::fclose(f);
     }
 }
 
@@ -334,6 +361,7 @@ rn_status rn_distance_join_dev(const rn_graph *cg, const uint32_t *dR, uint32_t 
         rn::run_join(g->dev, g->ws, g->cfg, g->info.median_weight, dR, nR, dS, nS, theta, out,
                      (void *)stream, &st);
         g_last_stats = st;
+        log_stats("join", st);
         g_have_stats = true;
     });
 }
@@ -374,6 +402,7 @@ rn_status rn_distance_join(const rn_graph *cg, const uint32_t *R, uint32_t nR, c
                      (void *)hs.stream, &st);
         rn::to_host_pairs(hs.res, out, hs.stream);
         g_last_stats = st;
+        log_stats("join", st);
         g_have_stats = true;
     });
 }
@@ -391,6 +420,7 @@ rn_status rn_kcp_dev(const rn_graph *cg, const uint32_t *dR, uint32_t nR, const 
         rn::run_kcp(g->dev, g->ws, g->cfg, g->info.median_weight, dR, nR, dS, nS, k, theta, out,
                     (void *)stream, &st);
         g_last_stats = st;
+        log_stats("kcp", st);
         g_have_stats = true;
     });
 }
@@ -415,6 +445,7 @@ rn_status rn_kcp(const rn_graph *cg, const uint32_t *R, uint32_t nR, const uint3
                     (void *)hs.stream, &st);
         rn::to_host_pairs(hs.res, out, hs.stream);
         g_last_stats = st;
+        log_stats("kcp", st);
         g_have_stats = true;
     });
 }
@@ -445,6 +476,7 @@ void points_query(const rn_graph *cg, const rn_point *R, uint32_t nR, const rn_p
                    hs.stream, &st);
     rn::to_host_pairs(hs.res, out, hs.stream);
     g_last_stats = st;
+    log_stats(k ? "kcp_points" : "join_points", st);
     g_have_stats = true;
 }
 
@@ -556,6 +588,17 @@ void rn_batch_free(rn_batch *h) {
     } catch (...) {
     }
     delete h;
+}
+
+rn_status rn_tune_cache_save(const char *path) {
+    return guarded([&] { rn::tune_cache_save(path); });
+}
+
+rn_status rn_tune_cache_load(const char *path, uint32_t *classes) {
+    return guarded([&] {
+        const uint32_t n = rn::tune_cache_load(path);
+        if (classes) *classes = n;
+    });
 }
 
 rn_status rn_join_batch(const rn_query *q, uint32_t nq, rn_pairs *outs) {

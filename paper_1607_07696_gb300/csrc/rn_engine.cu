@@ -1726,6 +1726,7 @@ void run_join(const DeviceGraph &g, Workspace *ws, const EngineConfig &cfg, uint
     if (T != 32 && T != 64 && T != 128) fail(RN_EINVAL, "tile width must be 32, 64 or 128");
     const uint32_t delta = choose_delta(cfg, median_w);
     std::lock_guard<std::mutex> device_lock(ws->sh->mu);
+    Range range("rn.join");
     *stats = rn_query_stats{};
     stats->tile_width = T;
     stats->delta = delta;
@@ -1766,7 +1767,11 @@ void run_join(const DeviceGraph &g, Workspace *ws, const EngineConfig &cfg, uint
     a.out_d = ws->valA;
     a.out_cap = ws->pair_cap;
     uint64_t retried = 0;
-    Control c = search_all(g, ws, T, a, ntiles, st, &retried, cfg.map_slots);
+    Control c;
+    {
+        Range r("rn.search");
+        c = search_all(g, ws, T, a, ntiles, st, &retried, cfg.map_slots);
+    }
     check_control(c);
     if (c.pairs > ws->pair_cap) {
         // the pair buffer was too small: grow it and search again (same result)
@@ -1783,6 +1788,7 @@ void run_join(const DeviceGraph &g, Workspace *ws, const EngineConfig &cfg, uint
     const uint64_t np = c.pairs;
 
     // a5: canonical order by (u, v), written straight into the caller's buffers
+    Range rsort("rn.sort");
     dpairs_reserve(out, np);
     std::vector<int> shifts;
     for (uint32_t sh = 0; sh < 2 * vbits; sh += 8) shifts.push_back(int(sh));
@@ -2086,6 +2092,7 @@ void run_kcp(const DeviceGraph &g, Workspace *ws, const EngineConfig &cfg, uint3
     if (T != 32 && T != 64 && T != 128) fail(RN_EINVAL, "tile width must be 32, 64 or 128");
     const uint32_t delta = choose_delta(cfg, median_w);
     std::lock_guard<std::mutex> device_lock(ws->sh->mu);
+    Range range("rn.kcp");
     *stats = rn_query_stats{};
     stats->tile_width = T;
     stats->delta = delta;
@@ -2425,7 +2432,10 @@ void run_points(const DeviceGraph &g, const std::vector<uint32_t> &perm, PointsS
     if (!*state) *state = new PointsState();
     PointsState *ps = *state;
     cudaStream_t st = (cudaStream_t)stream;
-    points_graph(g, perm, R, nR, S, nS, ps, st);
+    {
+        Range r("rn.points.subdivide");
+        points_graph(g, perm, R, nR, S, nS, ps, st);
+    }
     if (k == 0)
         run_join(ps->aug, ps->ws, cfg, median_w, ps->ids, nR, ps->ids + nR, nS, theta, out, stream, stats);
     else
@@ -2515,6 +2525,56 @@ std::mutex g_tune_mu;
 std::map<uint32_t, BatchPlan> g_tune_cache;  // size class -> tuned plan, for the process
 
 }  // namespace
+
+// The tuned plans as text, one "class T delta_mult src_div" line per size class (class =
+// log2 n << 16 | log2 |R| << 8 | log2 hops), after a "rn-tune 1" line.
+void tune_cache_save(const char *path) {
+    if (!path) fail(RN_EINVAL, "null path");
+    std::string text = "rn-tune 1\n";
+    {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        for (const auto &kv : g_tune_cache)
+            text += std::to_string(kv.first) + " " + std::to_string(kv.second.T) + " " +
+                    std::to_string(kv.second.delta_mult) + " " + std::to_string(kv.second.src_div) + "\n";
+    }
+    std::FILE *f = std::fopen(path, "w");
+    if (!f) fail(RN_EINVAL, std::string(path) + ": cannot create");
+    const bool ok = std::fputs(text.c_str(), f) >= 0;
+    if ((std::fclose(f) != 0) || !ok) fail(RN_EINVAL, std::string(path) + ": write failed");
+}
+
+// Merge the plans of a saved cache into the process's (later batches use them).
+uint32_t tune_cache_load(const char *path) {
+    if (!path) fail(RN_EINVAL, "null path");
+    std::FILE *f = std::fopen(path, "r");
+    if (!f) fail(RN_EINVAL, std::string(path) + ": cannot open");
+    std::map<uint32_t, BatchPlan> plans;
+    char line[256];
+    int lineno = 0;
+    bool ok = true;
+    std::string why;
+    while (ok && std::fgets(line, sizeof line, f)) {
+        lineno++;
+        if (lineno == 1) {
+            ok = std::strncmp(line, "rn-tune 1", 9) == 0;
+            why = "not a tune cache";
+            continue;
+        }
+        unsigned long cls = 0, T = 0, dm = 0, sd = 0;
+        if (std::sscanf(line, "%lu %lu %lu %lu", &cls, &T, &dm, &sd) != 4 || (T != 32 && T != 64 && T != 128) ||
+            dm < 1 || dm > 1024 || sd < 1 || sd > T || cls > 0xFFFFFFFFul) {
+            ok = false;
+            why = "line " + std::to_string(lineno) + " is not 'class T delta_mult src_div'";
+            break;
+        }
+        plans[uint32_t(cls)] = BatchPlan{uint32_t(T), uint32_t(dm), uint32_t(sd)};
+    }
+    std::fclose(f);
+    if (!ok || lineno == 0) fail(RN_EINVAL, std::string(path) + ": " + (lineno ? why : "empty file"));
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    for (const auto &kv : plans) g_tune_cache[kv.first] = kv.second;
+    return uint32_t(plans.size());
+}
 
 struct Batch {
     int device = 0;
@@ -2837,6 +2897,7 @@ static void batch_record(Batch *b, cudaStream_t st) {
 // eager run with retries sets the instances' first maps from the balls it measured.
 void batch_run(Batch *b, void *user_stream, bool use_graph) {
     std::lock_guard<std::mutex> device_lock(b->ws->sh->mu);
+    Range range("rn.batch.run");
     cudaStream_t st = b->stream;
     if (user_stream) {
         RN_CUDA(cudaEventRecord(b->ws->ev0, (cudaStream_t)user_stream));
@@ -2917,6 +2978,7 @@ static double batch_time_eager(Batch *b) {
 }
 
 void batch_tune(Batch *b) {
+    Range range("rn.batch.tune");
     static const BatchPlan cands[] = {
         {32, 4, 1}, {32, 8, 1}, {32, 16, 1}, {32, 4, 2}, {64, 4, 1}, {64, 8, 1}, {128, 4, 1}, {128, 8, 1},
     };

@@ -9,7 +9,18 @@
 
 #include "rn.h"
 
+#include <nvtx3/nvToolsExt.h>
+
 namespace rn {
+
+// A named NVTX range over a scope (query phases show up by name in Nsight timelines and
+// ncu range filters; without a tool attached the calls do nothing).
+struct Range {
+    explicit Range(const char *name) { nvtxRangePushA(name); }
+    ~Range() { nvtxRangePop(); }
+    Range(const Range &) = delete;
+    Range &operator=(const Range &) = delete;
+};
 
 // Every internal failure is thrown as an Error and turned into an rn_status at the ABI.
 struct Error {
@@ -96,6 +107,8 @@ void batch_pairs_dev(const Batch *b, uint32_t i, const uint32_t **u, const uint3
                      uint64_t *n);
 const rn_batch_stats &batch_stats(const Batch *b);
 void batch_destroy(Batch *b);
+void tune_cache_save(const char *path);
+uint32_t tune_cache_load(const char *path);
 
 // Workspaces with a slab of their own (servers, rn_engine.cu).
 size_t slab_region_bytes();

@@ -114,6 +114,7 @@ struct Server {
 };
 
 void Server::execute(Worker *w, Request *q) {
+    Range range(q->k ? "rn.serve.kcp" : "rn.serve.join");
     const rn_graph *G = g;
     workspace_set_slab(w->ws, arena + size_t(q->unit_off) * unit_words, q->units);
     const uint32_t nR = uint32_t(q->R.size()), nS = uint32_t(q->S.size());

@@ -158,6 +158,8 @@ SIGNATURES = {
     "rn_graph_load_file": (C.c_int, [C.c_char_p, C.POINTER(C.c_void_p)]),
     "rn_graph_write_file": (C.c_int, [C.c_char_p, _P32, _P32, _P32, C.c_uint64, C.c_uint32, C.c_uint32]),
     "rn_set_allocator": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p]),
+    "rn_tune_cache_save": (C.c_int, [C.c_char_p]),
+    "rn_tune_cache_load": (C.c_int, [C.c_char_p, C.POINTER(C.c_uint32)]),
     "rn_pairs_free": (None, [C.POINTER(rn_pairs)]),
     "rn_dpairs_free": (None, [C.POINTER(rn_dpairs)]),
     "rn_last_error": (C.c_char_p, []),
@@ -628,3 +630,13 @@ def use_torch_allocator(enable: bool = True) -> None:
     hook = (_ALLOC_FN(alloc), _FREE_FN(free))
     _torch_hooks.append(hook)
     _check(lib().rn_set_allocator(C.cast(hook[0], C.c_void_p), C.cast(hook[1], C.c_void_p), None))
+
+
+def rn_tune_cache_save(path: str) -> None:
+    _check(lib().rn_tune_cache_save(os.fsencode(path)))
+
+
+def rn_tune_cache_load(path: str) -> int:
+    n = C.c_uint32()
+    _check(lib().rn_tune_cache_load(os.fsencode(path), C.byref(n)))
+    return int(n.value)

@@ -71,3 +71,27 @@ def test_hook_rules(rn):
         assert ex.value.status == rn.RN_ENOMEM
     finally:
         rn._check(rn.lib().rn_set_allocator(None, None, None))
+
+
+def test_stats_log(rn, tmp_path):
+    import json
+    import os
+    import subprocess
+    import sys
+
+    log = tmp_path / "stats.jsonl"
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    code = (
+        "import sys; sys.path.insert(0, %r)\n"
+        "from paper_1607_07696_gb300 import inputs as I, rn\n"
+        "e = I.road_graph(5000, 13850, 3); g = rn.rn_graph_load(e.src, e.dst, e.w, e.n)\n"
+        "R, S = I.disjoint_sets(e.n, 100, 200, 4)\n"
+        "u, v, d = rn.rn_distance_join(g, R, S, 30000); k = rn.rn_kcp(g, R, S, 50)\n"
+        "print(len(u))\n" % root)
+    env = dict(os.environ, RN_STATS_LOG=str(log))
+    out = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True, timeout=600)
+    assert out.returncode == 0, out.stderr
+    lines = [json.loads(x) for x in log.read_text().splitlines()]
+    assert [x["query"] for x in lines] == ["join", "kcp"]
+    assert lines[0]["pairs"] == int(out.stdout.strip()) and lines[1]["pairs"] == 50
+    assert all(x["device_ms"] > 0 and x["tiles"] > 0 for x in lines)
