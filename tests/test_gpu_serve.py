@@ -206,3 +206,28 @@ def test_cancel_and_admission_oom(rn, world):
     assert same(rn.rn_serve_wait(srv, rn.rn_serve_submit(srv, R[:10], S, 150_000)),
                 rn.rn_distance_join(g, R[:10], S, 150_000))
     srv.close()
+
+
+def test_serve6m_requests_against_oracle(rn, oracle):
+    """Requests of the serving stream on its own 6M-node graph: the small ones (|R| <= 250,
+    joins and k closest pairs) served in a mix, each equal to the oracle's answer."""
+    import json
+    import os
+
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    spec = json.load(open(os.path.join(root, "tests", "golden", "workloads.json")))["serve6m"]
+    e = I.c5_serve_graph()
+    g = rn.rn_graph_load(e.src, e.dst, e.w, e.n)
+    reqs = I.c5_requests(e.n, 300, spec["ball_coeff"])
+    small = [r for r in reqs if len(r.R) <= 250]
+    pick = [r for r in small if r.k == 0][:4] + [r for r in small if r.k][:3]
+    srv = rn.rn_serve_create(g)
+    tickets = [rn.rn_serve_submit(srv, r.R, r.S, r.theta, r.k) for r in pick]
+    og = oracle.graph(e.n, e.src, e.dst, e.w)
+    for i, (r, t) in enumerate(zip(pick, tickets)):
+        u, v, d = rn.rn_serve_wait(srv, t)
+        th = min(r.theta, rn.RN_THETA_MAX)
+        ref = og.join(r.R, r.S, th) if r.k == 0 else og.kcp(r.R, r.S, r.k, th)
+        assert np.array_equal(u, ref.u) and np.array_equal(v, ref.v) and np.array_equal(d.astype(np.uint64), ref.d), \
+            f"request {i} (k = {r.k}) differs from the oracle"
+    srv.close()
