@@ -45,20 +45,28 @@ def _headers() -> list[str]:
     return hs
 
 
-def build(verbose: bool = False, force: bool = False) -> str:
-    """Compile every translation unit that changed and link librn.so; returns its path."""
-    os.makedirs(BUILD, exist_ok=True)
+CHECKS_LIB = os.path.join(PKG, "librn_checks.so")
+
+
+def build(verbose: bool = False, force: bool = False, checks: bool = False) -> str:
+    """Compile every translation unit that changed and link librn.so; returns its path.
+    checks=True builds librn_checks.so instead: the same engine with device bounds
+    checks compiled in (-DRN_CHECKS; a failed check is reported as RN_EINTERNAL)."""
+    out_dir = os.path.join(BUILD, "checks") if checks else BUILD
+    lib_path = CHECKS_LIB if checks else LIB
+    os.makedirs(out_dir, exist_ok=True)
     cc = nvcc()
     headers = _headers()
     jobs = []
     objs = []
     for src in SOURCES:
         path = os.path.join(CSRC, src)
-        obj = os.path.join(BUILD, src + ".o")
+        obj = os.path.join(out_dir, src + ".o")
         objs.append(obj)
         if force or _stale(obj, [path, *headers]):
             extra = ["-Xptxas", "-v"] if (verbose and src.endswith(".cu")) else []
-            jobs.append([cc, *ARCH, *COMMON, *extra, "-c", path, "-o", obj])
+            defs = ["-DRN_CHECKS"] if checks else []
+            jobs.append([cc, *ARCH, *COMMON, *defs, *extra, "-c", path, "-o", obj])
 
     def run(cmd):
         r = subprocess.run(cmd, capture_output=True, text=True)
@@ -70,11 +78,11 @@ def build(verbose: bool = False, force: bool = False) -> str:
         for out in ex.map(run, jobs):
             if verbose and out:
                 print(out, file=sys.stderr)
-    if force or jobs or _stale(LIB, objs):
-        tmp = LIB + f".tmp{os.getpid()}"
+    if force or jobs or _stale(lib_path, objs):
+        tmp = lib_path + f".tmp{os.getpid()}"
         run([cc, *ARCH, "-shared", "-o", tmp, *objs, "-lpthread"])
-        os.replace(tmp, LIB)
-    return LIB
+        os.replace(tmp, lib_path)
+    return lib_path
 
 
 if __name__ == "__main__":

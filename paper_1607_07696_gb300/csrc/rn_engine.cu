@@ -215,6 +215,15 @@ __device__ __forceinline__ void record_check(Control *ctl, uint32_t code, uint32
     }
 }
 
+// Bounds checks of the debug build (-DRN_CHECKS): a failed check records the first bad
+// index in the control block (the host reports RN_EINTERNAL) and the access it guards is
+// skipped; in the normal build a check is the constant false and compiles away.
+#ifdef RN_CHECKS
+#define RN_BAD(cond, code, idx, val) (!(cond) && (record_check(a.ctl, (code), uint32_t(idx), uint32_t(val)), true))
+#else
+#define RN_BAD(cond, code, idx, val) false
+#endif
+
 // Two block shapes: NARROW blocks (512 threads, an 8192-slot shared map, two blocks per
 // SM) search every tile first; WIDE blocks (1024 threads, a 16384-slot map, one block
 // per SM) search again the tiles whose union ball overflowed, and run the global-map
@@ -471,6 +480,8 @@ struct SearchArgs {
     uint32_t *gmap;                         // global slot maps (2 H words per block), or null
     uint32_t H, hshift, max_fill;
     uint32_t vbits;                         // key = (u << vbits) | v
+    uint32_t n_nodes;                       // the graph's nodes and arcs (bounds checks)
+    uint64_t n_arcs;
     Control *ctl;
     uint4 *failed;                          // ranges whose slot map overflowed: (first,
                                             // count, bucket end reached, slots filled)
@@ -776,12 +787,16 @@ __global__ void __launch_bounds__(THREADS, (THREADS == NARROW ? CTAS_PER_SM : 1)
         // sources: lane t of every row belongs to R node first + t, at distance 0
         if (tid < tsz) {
             const uint32_t y = s_cx.src[s_cx.first + tid];
-            src_orig[tid] = s_cx.iperm[y];
-            const uint32_t h = find_or_insert(hkeys, a.H, a.hshift, y, &s_fill, a.max_fill, &s_fail);
-            __stcg(&slab[size_t(h) * T + tid], 0u);
-            atomicOr(&dmask[h], 1u << (tid / L));
-            prio[h] = 0;
-            qa[atomicAdd(&s_ncur, 1u)] = h;
+            if (!RN_BAD(y < a.n_nodes, 1, s_cx.first + tid, y)) {
+                src_orig[tid] = s_cx.iperm[y];
+                const uint32_t h = find_or_insert(hkeys, a.H, a.hshift, y, &s_fill, a.max_fill, &s_fail);
+                if (!RN_BAD(h < a.H, 2, tid, h)) {
+                    __stcg(&slab[size_t(h) * T + tid], 0u);
+                    atomicOr(&dmask[h], 1u << (tid / L));
+                    prio[h] = 0;
+                    qa[atomicAdd(&s_ncur, 1u)] = h;
+                }
+            }
         }
         uint32_t *qcur = qa, *qnext = qb;
         uint64_t tau = delta;  // end (exclusive) of the current bucket
@@ -814,14 +829,17 @@ __global__ void __launch_bounds__(THREADS, (THREADS == NARROW ? CTAS_PER_SM : 1)
                     if (tid < nc) {
                         const uint32_t x = qcur[c0 + tid];
                         uint32_t mask = 0, beg = 0, dmin = INF;
-                        const uint32_t p = atomicExch(&prio[x], INF);
+                        const bool bad_x = RN_BAD(x < a.H, 3, c0 + tid, x);
+                        const uint32_t p = bad_x ? INF : atomicExch(&prio[x], INF);
                         if (p != INF) mask = atomicExch(&dmask[x], 0u);
+                        if (mask && RN_BAD(hkeys[x] < a.n_nodes, 4, x, hkeys[x])) mask = 0;
                         if (mask) {
                             my_scans++;
                             my_dirty += __popc(mask);
                             const uint32_t y0 = hkeys[x];
                             beg = __ldg(&row_ptr[y0]);
                             deg = __ldg(&row_ptr[y0 + 1]) - beg;
+                            if (RN_BAD(uint64_t(beg) + deg <= a.n_arcs, 5, y0, beg)) deg = 0;
                             const uint32_t *xrow = slab + size_t(x) * T;
                             uint32_t m = mask;
                             if ((m & (m - 1)) == 0) {  // one dirty lane-group (m != 0 here)
@@ -884,14 +902,19 @@ __global__ void __launch_bounds__(THREADS, (THREADS == NARROW ? CTAS_PER_SM : 1)
                                 else hi = mid - 1;
                             }
                             item = lo;
-                            const uint2 arc = __ldg(&adj[it_beg[lo] + (gi - it_off[lo])]);
-                            w = arc.y;
-                            if (it_dmin[lo] + w <= bound) hy = arc.x;  // the head node until its slot is known
+                            const uint32_t ai = it_beg[lo] + (gi - it_off[lo]);
+                            if (!RN_BAD(ai < a.n_arcs, 6, gi, ai)) {
+                                const uint2 arc = __ldg(&adj[ai]);
+                                w = arc.y;
+                                if (it_dmin[lo] + w <= bound) hy = arc.x;  // the head node until its slot is known
+                                if (hy != EMPTY && RN_BAD(hy < a.n_nodes, 7, ai, hy)) hy = EMPTY;
+                            }
                         }
                         bool ins = false;
                         if (hy != EMPTY) {
                             hy = find_or_insert_nf(hkeys, a.H, a.hshift, hy, &ins);
                             if (hy == EMPTY) s_fail = 1;
+                            else if (RN_BAD(hy < a.H, 8, gi, hy)) hy = EMPTY;
                         }
                         const uint32_t inserted = __popc(__ballot_sync(FULL, ins));
                         if (lane == 0 && inserted && atomicAdd(&s_fill, inserted) + inserted > a.max_fill)
@@ -1011,7 +1034,8 @@ __global__ void __launch_bounds__(THREADS, (THREADS == NARROW ? CTAS_PER_SM : 1)
             uint32_t cnt = 0;
             for (uint32_t c = warp * 32; c < a.H; c += SEARCH_WARPS * 32) {
                 const uint32_t yl = hkeys[c + lane];
-                const bool in_s = yl != EMPTY && ((__ldg(&s_cx.sbits[yl >> 5]) >> (yl & 31)) & 1u);
+                const bool in_s = yl != EMPTY && !RN_BAD(yl < a.n_nodes, 9, c + lane, yl) &&
+                                  ((__ldg(&s_cx.sbits[yl >> 5]) >> (yl & 31)) & 1u);
                 for (uint32_t b = __ballot_sync(FULL, in_s); b; b &= b - 1) {
                     const uint32_t h = c + __ffs(b) - 1;
                     const Row<L> r = load_row<L>(slab + size_t(h) * T + lane * L);
@@ -1035,7 +1059,8 @@ __global__ void __launch_bounds__(THREADS, (THREADS == NARROW ? CTAS_PER_SM : 1)
             unsigned long long pos = s_base + s_warp[warp];
             for (uint32_t c = warp * 32; c < a.H; c += SEARCH_WARPS * 32) {
                 const uint32_t yl = hkeys[c + lane];
-                const bool in_s = yl != EMPTY && ((__ldg(&s_cx.sbits[yl >> 5]) >> (yl & 31)) & 1u);
+                const bool in_s = yl != EMPTY && !RN_BAD(yl < a.n_nodes, 9, c + lane, yl) &&
+                                  ((__ldg(&s_cx.sbits[yl >> 5]) >> (yl & 31)) & 1u);
                 for (uint32_t b = __ballot_sync(FULL, in_s); b; b &= b - 1) {
                     const uint32_t src_lane = __ffs(b) - 1;
                     const uint32_t h = c + src_lane;
@@ -1510,6 +1535,8 @@ static Control search_all(const DeviceGraph &g, Workspace *ws, uint32_t T, Searc
     const uint32_t grid_max = ws->sh->slab_ctas;
     const uint32_t grid_wide = std::max<uint32_t>(1, std::min<uint32_t>(grid_max / 2, uint32_t(ws->num_sms)));
     a.slab = ws->sh->slab;
+    a.n_nodes = g.n;
+    a.n_arcs = g.arcs;
     if (ntiles && (!a.src || !a.slab || !a.sbits || !a.out_key || !a.out_d || !a.row_ptr || !a.adj || !a.ctl ||
                    !ws->failed || !ws->failed2))
         fail(RN_EINTERNAL, "tile search without its buffers");
@@ -1940,6 +1967,8 @@ void run_join_noalloc(const DeviceGraph &g, uint32_t median_w, const uint32_t *d
     a.hshift = 32 - bits_for(SMEM_H);
     a.max_fill = SMEM_H * 7 / 8;
     a.failed = failed;
+    a.n_nodes = g.n;
+    a.n_arcs = g.arcs;
     if (ntiles) search(T, Shape::Narrow, a, std::min(ntiles, NA_BLOCKS), st);
     Control c;
     RN_CUDA(cudaMemcpyAsync(&c, ctl, sizeof(Control), cudaMemcpyDeviceToHost, st));
@@ -2821,6 +2850,8 @@ static void batch_launch_group(Batch *b, const Batch::Group &g, cudaStream_t st)
     a.slab = b->ws->sh->slab;
     a.failed = b->ws->failed;
     a.ntiles = g.tiles;
+    a.n_nodes = b->ug.n;
+    a.n_arcs = b->ug.arcs;
     if (g.map > SMEM_HW) {
         launch_gmap(b->ug, b->ws, g.T, a, g.map, g.tiles, st);
         return;

@@ -13,7 +13,8 @@ from dataclasses import dataclass
 
 import numpy as np
 
-LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "librn.so")
+# RN_LIBRARY may name another build of the engine (the bounds-checked librn_checks.so)
+LIB_PATH = os.environ.get("RN_LIBRARY") or os.path.join(os.path.dirname(os.path.abspath(__file__)), "librn.so")
 
 RN_OK, RN_EINVAL, RN_ENOMEM, RN_ECUDA, RN_ETIMEOUT = 0, 1, 2, 3, 4
 RN_ECANCELLED, RN_EBUSY, RN_EINTERNAL, RN_ENOTIMPL = 5, 6, 7, 8
