@@ -395,7 +395,7 @@ def serve_leg(rn, count: int) -> dict:
         "unit": "queries/s", "requests": count, "joins": len(joins), "pairs": int(sum(served_pairs)),
         "served_qps": sat, "plain_qps": count / plain_s, "served_vs_plain": sat / (count / plain_s),
         "phases": phases, "graph_load_s": load_s,
-        "config": {"workers": 8, "max_blocks": 64, "slab_mb": 2048},
+        "config": {"workers": 8, "max_blocks": "one per SM", "slab_mb": 4096},
     }
 
 

@@ -366,9 +366,10 @@ typedef struct rn_server rn_server;
 typedef struct {
     uint64_t slab_bytes;  /* the distance-slab arena, the admission budget: a request holds
                              one region of 4 MiB per search block while it runs (default
-                             2 GiB) */
+                             4 GiB) */
     uint32_t workers;     /* requests on the device at once, at most (default 8) */
-    uint32_t max_blocks;  /* search blocks (slab regions) of one request, >= 2 (default 64) */
+    uint32_t max_blocks;  /* search blocks (slab regions) of one request, >= 2 (default: the
+                             device's SM count) */
 } rn_serve_config;
 
 typedef struct {

@@ -191,12 +191,16 @@ Server *server_create(const rn_graph *g, uint64_t slab_bytes, uint32_t workers, 
     s->device = g->device;
     check(cudaSetDevice(g->device), "cudaSetDevice");
     s->tile_width = g->cfg.tile_width ? g->cfg.tile_width : 32;
-    s->max_blocks = max_blocks ? max_blocks : 64;
+    int sms = 0;
+    check(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, g->device), "cudaDeviceGetAttribute");
+    // by default a request may spread over one block per SM: its sources then sit a few to
+    // a tile, whose union balls fit the shared maps, and a few requests still share the GPU
+    s->max_blocks = max_blocks ? max_blocks : uint32_t(std::max(sms, 2));
     if (s->max_blocks < 2) fail(RN_EINVAL, "max_blocks must be >= 2");
     const uint32_t nworkers = workers ? workers : 8;
     if (nworkers > 256) fail(RN_EINVAL, "at most 256 workers");
     const size_t region = slab_region_bytes();
-    const uint64_t bytes = slab_bytes ? slab_bytes : (uint64_t(2) << 30);
+    const uint64_t bytes = slab_bytes ? slab_bytes : (uint64_t(4) << 30);
     s->units_total = uint32_t(std::min<uint64_t>(bytes / region, 1u << 20));
     if (s->units_total < s->max_blocks)
         fail(RN_EINVAL, "slab_bytes must hold max_blocks regions of " + std::to_string(region) + " bytes");
