@@ -690,6 +690,7 @@ __global__ void __launch_bounds__(THREADS, (THREADS == NARROW ? CTAS_PER_SM : 1)
     constexpr int SEARCH_WARPS = THREADS / 32;
     constexpr uint32_t QCAP = qcap_of(THREADS);
     constexpr uint32_t ICAP = icap_of(THREADS);
+    constexpr uint32_t ICAP_POW2 = 1u << (31 - __builtin_clz(ICAP));  // the largest power of two <= ICAP
     extern __shared__ uint32_t smem[];
     uint32_t *hkeys, *qa;
     if constexpr (GMAP) {
@@ -895,12 +896,12 @@ __global__ void __launch_bounds__(THREADS, (THREADS == NARROW ? CTAS_PER_SM : 1)
                         uint32_t item = 0, hy = EMPTY, w = 0;
                         bool push = false;
                         if (gi < total) {
-                            uint32_t lo = 0, hi = nc - 1;  // last item whose arcs start at or before gi
-                            while (lo < hi) {
-                                const uint32_t mid = (lo + hi + 1) >> 1;
-                                if (it_off[mid] <= gi) lo = mid;
-                                else hi = mid - 1;
-                            }
+                            // the last item whose arcs start at or before gi: a branchless
+                            // search by powers of two below ICAP (it_off is non-decreasing)
+                            uint32_t lo = 0;
+#pragma unroll
+                            for (uint32_t step = ICAP_POW2; step; step >>= 1)
+                                if (lo + step < nc && it_off[lo + step] <= gi) lo += step;
                             item = lo;
                             const uint32_t ai = it_beg[lo] + (gi - it_off[lo]);
                             if (!RN_BAD(ai < a.n_arcs, 6, gi, ai)) {
