@@ -176,6 +176,8 @@ rn_status rn_bisection_order(const uint32_t *src, const uint32_t *dst, const uin
 /* Copy the relabelling out: perm[orig] = internal id (n entries). */
 rn_status rn_graph_permutation(const rn_graph *g, uint32_t *perm);
 /* Change the knobs of later queries (tile_width, delta); NULL restores the defaults. */
+/* Change a graph's knobs for its later queries (servers keep the knobs they were made
+ * with). */
 rn_status rn_graph_set_config(rn_graph *g, const rn_config *cfg);
 
 /*
@@ -335,6 +337,7 @@ rn_status rn_batch_pairs(const rn_batch *b, uint32_t i, rn_pairs *out);
 rn_status rn_batch_pairs_dev(const rn_batch *b, uint32_t i, const uint32_t **u, const uint32_t **v,
                              const uint32_t **d, uint64_t *n);
 rn_status rn_batch_stats_get(const rn_batch *b, rn_batch_stats *out);
+/* A batch runs one rn_batch_run at a time; no call on it may overlap rn_batch_free. */
 void rn_batch_free(rn_batch *b);
 /* The autotuner's plans (per size class: tile width, bucket width, sources per tile) to a
  * text file, and back: a loaded file is merged into the process's plans, which later
@@ -415,7 +418,7 @@ rn_status rn_serve_stats_get(rn_server *s, rn_serve_stats *out);
  * busy time and span restart (pending and running requests are kept). */
 rn_status rn_serve_reset_stats(rn_server *s);
 /* Stop the server: running requests finish, queued ones are dropped, uncollected
- * results freed. */
+ * results freed.  No other call on this server may run while it is destroyed. */
 void rn_serve_destroy(rn_server *s);
 
 void rn_pairs_free(rn_pairs *p);

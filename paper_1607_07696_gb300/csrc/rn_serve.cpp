@@ -73,6 +73,7 @@ void ensure_u32(uint32_t **p, uint32_t *cap, uint32_t want) {
 
 struct Server {
     const rn_graph *g = nullptr;
+    EngineConfig cfg;  // the graph's knobs when the server was made (a later change does not race)
     int device = 0;
     uint32_t tile_width = 32, max_blocks = 64;
     uint32_t *arena = nullptr;
@@ -124,10 +125,10 @@ void Server::execute(Worker *w, Request *q) {
     if (nS) copy_to_device(w->dS, q->S.data(), size_t(nS) * 4, w->stream);
     rn_query_stats st{};
     if (q->k == 0)
-        run_join(G->dev, w->ws, G->cfg, G->info.median_weight, w->dR, nR, w->dS, nS, q->theta, &w->res, w->stream,
+        run_join(G->dev, w->ws, cfg, G->info.median_weight, w->dR, nR, w->dS, nS, q->theta, &w->res, w->stream,
                  &st);
     else
-        run_kcp(G->dev, w->ws, G->cfg, G->info.median_weight, w->dR, nR, w->dS, nS, q->k, q->theta, &w->res,
+        run_kcp(G->dev, w->ws, cfg, G->info.median_weight, w->dR, nR, w->dS, nS, q->k, q->theta, &w->res,
                 w->stream, &st);
     to_host_pairs(w->res, &q->out, w->stream);
 }
@@ -188,9 +189,13 @@ void Server::loop(Worker *w) {
 Server *server_create(const rn_graph *g, uint64_t slab_bytes, uint32_t workers, uint32_t max_blocks) {
     auto s = std::make_unique<Server>();
     s->g = g;
+    {
+        std::lock_guard<std::mutex> lk(const_cast<rn_graph *>(g)->mu);
+        s->cfg = g->cfg;
+    }
     s->device = g->device;
     check(cudaSetDevice(g->device), "cudaSetDevice");
-    s->tile_width = g->cfg.tile_width ? g->cfg.tile_width : 32;
+    s->tile_width = s->cfg.tile_width ? s->cfg.tile_width : 32;
     int sms = 0;
     check(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, g->device), "cudaDeviceGetAttribute");
     // by default a request may spread over one block per SM: its sources then sit a few to
