@@ -40,7 +40,7 @@ PROFILE = os.path.join(ROOT, "profiles", "tile_search_road264k.json")
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="engine", choices=["engine", "reference"])
     ap.add_argument("--workload", default="road264k_join",
@@ -93,7 +93,7 @@ class ClockSampler:
     def __enter__(self):
         try:
             self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
-                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                          "--format=csv,noheader,nounits", "-lms", "50"],
                                          stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.t = threading.Thread(target=self._read, daemon=True)
             self.t.start()
@@ -471,7 +471,7 @@ def run_engine(args):
     Sh = torch.as_tensor(w.S.astype(np.int32)).pin_memory().numpy()
     rn.rn_distance_join(g, Rh, Sh, theta)  # warm the host path's buffers
     e2e_t = []
-    for i in range(max(3, args.steps // 2)):
+    for i in range(min(50, max(3, args.steps // 2))):
         flush.fill_(i & 0xFF)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
@@ -532,9 +532,9 @@ def run_engine(args):
                    "cycles_step_a": stats["cycles_step_a"], "round_arcs": stats["round_arcs"]},
     }
     if args.workload == "road264k_join" and world == 1:
-        line["join_1m"] = join_1m_leg(rn, max(3, args.steps // 2), stream, flush, peak)
+        line["join_1m"] = join_1m_leg(rn, min(50, max(3, args.steps // 2)), stream, flush, peak)
     if not args.no_batch and world == 1:
-        line["batched"] = batch_leg(rn, max(3, args.steps // 2), 3, stream, flush)
+        line["batched"] = batch_leg(rn, 5, 3, stream, flush)
     if not args.no_serve and world == 1:
         line["served"] = serve_leg(rn, args.serve_requests)
     if not args.no_cpu_baseline and world == 1:
@@ -555,7 +555,7 @@ def run_reference(args):
 
     w, spec = make_workload(args.workload, 0)
     og = O.default().graph(w.graph.n, w.graph.src, w.graph.dst, w.graph.w)
-    per_step = 400
+    per_step = max(10, min(400, 20000 // max(1, args.steps)))  # about 20,000 sources in all
     theta = spec["theta"]
     nR = len(w.R)
     for i in range(args.warmup):
