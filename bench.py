@@ -306,6 +306,42 @@ def join_1m_leg(rn, steps: int, stream, flush, peak: float) -> dict:
                          "frac": alg / (sm / 1e3) / 1e9 / peak, "alg_bytes_per_launch": alg}}
 
 
+def kcp_1m_leg(rn, steps: int, stream, flush) -> dict:
+    """k closest pairs on the 1.07M-node graph with 50,000 + 50,000 clustered sets, for
+    k = 100, 10^4 and 10^6 (unbounded theta): device time per query (sets in device
+    memory, L2 flushed), the radius passes it took and the k-th distance."""
+    import numpy as np
+    import torch
+
+    from paper_1607_07696_gb300 import inputs as I
+
+    w = I.c3_road_clustered()
+    e = w.graph
+    g = rn.rn_graph_load(e.src, e.dst, e.w, e.n)
+    dR = torch.as_tensor(w.R.astype(np.int32), device="cuda")
+    dS = torch.as_tensor(w.S.astype(np.int32), device="cuda")
+    out = rn.DevicePairs()
+    res = {"workload": "road1070k_kcp: 1.07M nodes, |R| = |S| = 50,000 clustered, theta unbounded"}
+    for k in (100, 10_000, 1_000_000):
+        for _ in range(2):
+            rn.rn_kcp_dev(g, dR, dS, k, rn.RN_INF, out, stream)
+        ms = []
+        for i in range(steps):
+            with torch.cuda.stream(stream):
+                flush.fill_(i & 0xFF)
+                a = torch.cuda.Event(enable_timing=True)
+                b = torch.cuda.Event(enable_timing=True)
+                a.record(stream)
+                n = rn.rn_kcp_dev(g, dR, dS, k, rn.RN_INF, out, stream)
+                b.record(stream)
+            b.synchronize()
+            ms.append(a.elapsed_time(b))
+        st = rn.rn_last_query_stats()
+        res[f"k={k}"] = {"ms": statistics.median(ms), "pairs": int(n), "passes": st["passes"],
+                         "kth_distance": st["theta_final"], "launches": st["launches"]}
+    return res
+
+
 def serve_leg(rn, count: int) -> dict:
     """Serving on the 6M-node graph: a stream of 70% theta-joins and 30% k-closest-pairs
     requests (|R|, |S| 100-20000).  Saturated throughput (every request submitted at
@@ -533,6 +569,7 @@ def run_engine(args):
     }
     if args.workload == "road264k_join" and world == 1:
         line["join_1m"] = join_1m_leg(rn, min(50, max(3, args.steps // 2)), stream, flush, peak)
+        line["kcp_1m"] = kcp_1m_leg(rn, min(10, max(3, args.steps // 2)), stream, flush)
     if not args.no_batch and world == 1:
         line["batched"] = batch_leg(rn, 5, 3, stream, flush)
     if not args.no_serve and world == 1:
