@@ -365,6 +365,16 @@ typedef struct {
 
 typedef struct rn_server rn_server;
 
+/*
+ * rn_join_many -- several theta-joins over one graph searched together: their sources
+ * are laid out one query after another, every tile holds sources of one query and
+ * searches with that query's theta against its S, and one sort orders all pairs by
+ * (query, u, v).  Small queries then share one launch instead of each leaving most of the
+ * GPU idle.  q[i].k must be 0; outs[0..nq) receive each query's pairs sorted by (u, v)
+ * (free each with rn_pairs_free).  RN_EINVAL as rn_distance_join, naming the query.
+ */
+rn_status rn_join_many(const rn_graph *g, const rn_request *q, uint32_t nq, rn_pairs *outs);
+
 /* Zero in any field chooses the default. */
 typedef struct {
     uint64_t slab_bytes;  /* the distance-slab arena, the admission budget: a request holds
@@ -378,6 +388,8 @@ typedef struct {
 typedef struct {
     uint64_t submitted, completed, failed, pending, running;
     uint64_t cancelled;           /* taken off the queue by rn_serve_cancel */
+    uint64_t groups, grouped;     /* searches that served several small joins at once, and
+                                     the requests they served */
     uint64_t pairs;               /* pairs returned by completed requests */
     uint64_t slab_bytes, slab_bytes_in_use, slab_bytes_peak;
     uint32_t workers, max_running;/* max_running: most requests on the device at once */
@@ -401,6 +413,8 @@ typedef struct {
  * arena cannot be allocated.
  */
 rn_status rn_serve_create(const rn_graph *g, const rn_serve_config *cfg, rn_server **out);
+/* (Small joins queued one behind another, |R| <= 512, up to 16 of them, are admitted
+ * together and searched in one launch, as rn_join_many does.) */
 /* Queue one request; *ticket identifies it to rn_serve_wait.  RN_EINVAL for a bad
  * request (as rn_distance_join / rn_kcp), found before it is queued. */
 rn_status rn_serve_submit(rn_server *s, const rn_request *q, uint64_t *ticket);

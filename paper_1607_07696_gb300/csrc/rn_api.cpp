@@ -601,6 +601,51 @@ rn_status rn_tune_cache_load(const char *path, uint32_t *classes) {
     });
 }
 
+rn_status rn_join_many(const rn_graph *cg, const rn_request *q, uint32_t nq, rn_pairs *outs) {
+    return guarded([&] {
+        if (!cg || !outs || (nq && !q)) rn::fail(RN_EINVAL, "null argument");
+        if (nq == 0) rn::fail(RN_EINVAL, "no queries");
+        for (uint32_t i = 0; i < nq; i++) outs[i] = rn_pairs{};
+        rn_graph *g = const_cast<rn_graph *>(cg);
+        std::vector<const uint32_t *> R(nq), S(nq);
+        std::vector<uint32_t> nR(nq), nS(nq), theta(nq);
+        for (uint32_t i = 0; i < nq; i++) {
+            try {
+                if (q[i].k != 0) rn::fail(RN_EINVAL, "k must be 0 (a theta-join)");
+                check_theta(q[i].theta);
+                check_sets_host(g->dev.n, q[i].R, q[i].nR, q[i].S, q[i].nS);
+            } catch (const rn::Error &e) {
+                rn::fail(e.status, "query " + std::to_string(i) + ": " + e.msg);
+            }
+            R[i] = q[i].R;
+            S[i] = q[i].S;
+            nR[i] = q[i].nR;
+            nS[i] = q[i].nS;
+            theta[i] = q[i].theta;
+        }
+        std::lock_guard<std::mutex> lk(g->mu);
+        rn::HostScratch &hs = scratch_of(g);
+        std::vector<uint64_t> counts;
+        rn_query_stats st{};
+        rn::run_join_multi(g->dev, g->ws, g->cfg, g->info.median_weight, g->perm, R, nR, S, nS, theta, &hs.res,
+                           &counts, hs.stream, &st);
+        uint64_t at = 0;
+        try {
+            for (uint32_t i = 0; i < nq; i++) {
+                rn_dpairs view{hs.res.u + at, hs.res.v + at, hs.res.d + at, counts[i], counts[i]};
+                rn::to_host_pairs(view, &outs[i], hs.stream);
+                at += counts[i];
+            }
+        } catch (...) {
+            for (uint32_t i = 0; i < nq; i++) rn_pairs_free(&outs[i]);
+            throw;
+        }
+        g_last_stats = st;
+        g_have_stats = true;
+        log_stats("join_many", st);
+    });
+}
+
 rn_status rn_join_batch(const rn_query *q, uint32_t nq, rn_pairs *outs) {
     return guarded([&] {
         if (!outs) rn::fail(RN_EINVAL, "null output");

@@ -278,6 +278,12 @@ struct Workspace {
     bool own_gmap_enabled = false, own_gmap_moved = false;
     uint32_t *own_gmap = nullptr;
     size_t own_gmap_bytes = 0;
+    // several joins over one graph: per query its first source, bound, S bitmap pointer
+    // and pair count, the S bitmaps, and the S ids with their offsets
+    uint32_t *mq_first = nullptr, *mq_bound = nullptr, *mq_sbits = nullptr, *mq_sids = nullptr, *mq_soff = nullptr;
+    const uint32_t **mq_sptr = nullptr;
+    unsigned long long *mq_counts = nullptr;
+    uint64_t mq_cap_q = 0, mq_cap_bits = 0, mq_cap_sids = 0;
     uint32_t launches = 0;  // kernels launched by the current query
     int blocks_per_sm = 0;  // occupancy of the shared-map search kernel
     uint64_t bytes = 0;
@@ -338,6 +344,9 @@ void workspace_destroy(Workspace *ws) {
     if (ws->evs0) cudaEventDestroy(ws->evs0);
     if (ws->evs1) cudaEventDestroy(ws->evs1);
     if (ws->evr) cudaEventDestroy(ws->evr);
+    for (void *p : {(void *)ws->mq_first, (void *)ws->mq_bound, (void *)ws->mq_sbits, (void *)ws->mq_sids,
+                    (void *)ws->mq_soff, (void *)ws->mq_sptr, (void *)ws->mq_counts})
+        device_free(p);
     device_free(ws->own_gmap);
     if (ws->own_sh) {
         device_free(ws->own_sh->gretry);
@@ -508,6 +517,13 @@ struct SearchArgs {
     unsigned long long *inst_pairs;
     unsigned long long *inst_cycles;
     uint32_t *inst_ball;  // per instance: largest union ball of a completed tile
+    // several joins over one graph (null for a single query): query i owns the sources
+    // src[inst_first[i] .. inst_first[i + 1]), searches with bound inst_bound[i] against
+    // the S bitmap inst_sbits[i], and its keys carry i above bit inst_shift
+    const uint32_t *inst_first;
+    uint32_t inst_count, inst_shift;
+    const uint32_t *const *inst_sbits;
+    const uint32_t *inst_bound;
 };
 
 // What a block needs to know about the tile it searches.
@@ -775,6 +791,19 @@ __global__ void __launch_bounds__(THREADS, (THREADS == NARROW ? CTAS_PER_SM : 1)
             c.delta = a.tile_delta ? a.tile_delta[tile] : a.delta;
             c.inst = a.tile_inst ? a.tile_inst[tile] : 0u;
             c.key_prefix = 0;
+            if (a.inst_first) {
+                // the query whose sources hold this range: the last with inst_first <= first
+                uint32_t lo = 0, hi = a.inst_count - 1;
+                while (lo < hi) {
+                    const uint32_t mid = (lo + hi + 1) >> 1;
+                    if (a.inst_first[mid] <= first) lo = mid;
+                    else hi = mid - 1;
+                }
+                c.inst = lo;
+                c.bound = a.inst_bound[lo];
+                c.sbits = a.inst_sbits[lo];
+                c.key_prefix = (unsigned long long)lo << a.inst_shift;
+            }
             s_cx = c;
             s_tile0 = clock64();
         }
@@ -1358,7 +1387,7 @@ __global__ void k_rs_scatter(const unsigned long long *__restrict__ kin, const u
 // Sort n records in (keyA, valA) by the listed digit shifts (least significant first);
 // the last pass writes the struct-of-arrays result into out.
 static void radix_sort_to_pairs(Workspace *ws, uint64_t n, const std::vector<int> &shifts,
-                                uint32_t vbits, rn_dpairs *out, cudaStream_t st) {
+                                uint32_t vbits, rn_dpairs *out, cudaStream_t st, uint32_t umask = 0xFFFFFFFFu) {
     if (n == 0) return;
     if (n > 0xFFFFFFFFull) fail(RN_EINVAL, "more than 2^32 - 1 result pairs");
     const uint32_t nblocks = uint32_t((n + RS_TILE - 1) / RS_TILE);
@@ -1371,7 +1400,7 @@ static void radix_sort_to_pairs(Workspace *ws, uint64_t n, const std::vector<int
         ws->launches += scan_hist(ws->hist, nblocks * 256, st) - 1;
         k_rs_scatter<<<nblocks, RS_THREADS, 0, st>>>(ki, vi, ko, vo, n, shifts[p], ws->hist, nblocks,
                                                      last ? out->u : nullptr, last ? out->v : nullptr,
-                                                     last ? out->d : nullptr, vbits);
+                                                     last ? out->d : nullptr, vbits, umask);
         std::swap(ki, ko);
         std::swap(vi, vo);
         ws->launches += 3;
@@ -1531,7 +1560,7 @@ static uint64_t map_for(uint64_t ball, uint64_t hcap) {
 
 static Control search_all(const DeviceGraph &g, Workspace *ws, uint32_t T, SearchArgs a,
                           uint32_t ntiles, cudaStream_t st, uint64_t *retried, uint32_t map_slots = 0,
-                          bool split = true) {
+                          bool split = true, const std::vector<uint4> *first_ranges = nullptr) {
     // narrow blocks: one slab region each; wide blocks: two regions each
     const uint32_t grid_max = ws->sh->slab_ctas;
     const uint32_t grid_wide = std::max<uint32_t>(1, std::min<uint32_t>(grid_max / 2, uint32_t(ws->num_sms)));
@@ -1547,6 +1576,16 @@ static Control search_all(const DeviceGraph &g, Workspace *ws, uint32_t T, Searc
     a.gmap = nullptr;
     a.range_list = nullptr;
     a.ntiles = ntiles;
+    if (first_ranges) {
+        // the first launch searches the given source ranges instead of the tiles of R
+        ntiles = uint32_t(first_ranges->size());
+        ensure_ranges(&ws->failed, &ws->failed_cap, std::max<uint32_t>(ntiles, 1));
+        ensure_ranges(&ws->failed2, &ws->failed2_cap, std::max<uint32_t>(ntiles, 1));
+        if (ntiles)
+            RN_CUDA(cudaMemcpyAsync(ws->failed2, first_ranges->data(), size_t(ntiles) * 16, cudaMemcpyHostToDevice, st));
+        a.range_list = ws->failed2;
+        a.ntiles = ntiles;
+    }
     a.failed = ws->failed;
     auto set_shared = [](SearchArgs &x, uint32_t h) {
         x.gmap = nullptr;
@@ -1850,6 +1889,195 @@ void run_join(const DeviceGraph &g, Workspace *ws, const EngineConfig &cfg, uint
     stats->max_ball = c.max_fill;
     stats->dirty_groups = c.dirty_groups;
     stats->retry_ms = ws->retry_ms;
+}
+
+// ------------------------------------------------ several joins, one graph ----
+// Several theta-joins over the same graph searched together (the server's micro-batches
+// of small requests, rn_join_many): their sources are laid out one query after another,
+// every tile is a range of one query's sources, and a tile takes its query's bound, S
+// bitmap and key prefix (the query index above the (u, v) bits).  One sort then orders
+// all pairs by (query, u, v), and the per-query counts cut the result.
+
+// Set the S bit of every id of every query: ids[soff[i] .. soff[i+1]) belong to query i.
+__global__ void k_set_bits_multi(const uint32_t *__restrict__ ids, const uint32_t *__restrict__ soff, uint32_t nq,
+                                 uint32_t total, const uint32_t *__restrict__ perm, uint32_t *bits, uint32_t nwords) {
+    for (uint32_t j = blockIdx.x * blockDim.x + threadIdx.x; j < total; j += gridDim.x * blockDim.x) {
+        uint32_t lo = 0, hi = nq - 1;
+        while (lo < hi) {
+            const uint32_t mid = (lo + hi + 1) >> 1;
+            if (soff[mid] <= j) lo = mid;
+            else hi = mid - 1;
+        }
+        const uint32_t x = perm[ids[j]];
+        atomicOr(&bits[size_t(lo) * nwords + (x >> 5)], 1u << (x & 31));
+    }
+}
+
+void run_join_multi(const DeviceGraph &g, Workspace *ws, const EngineConfig &cfg, uint32_t median_w,
+                    const std::vector<uint32_t> &perm, const std::vector<const uint32_t *> &R,
+                    const std::vector<uint32_t> &nR, const std::vector<const uint32_t *> &S,
+                    const std::vector<uint32_t> &nS, const std::vector<uint32_t> &theta, rn_dpairs *out,
+                    std::vector<uint64_t> *counts, void *stream, rn_query_stats *stats) {
+    cudaStream_t st = (cudaStream_t)stream;
+    const uint32_t nq = uint32_t(R.size());
+    if (nq == 0) fail(RN_EINVAL, "no queries");
+    const uint32_t T = cfg.tile_width ? cfg.tile_width : 32;
+    if (T != 32 && T != 64 && T != 128) fail(RN_EINVAL, "tile width must be 32, 64 or 128");
+    const uint32_t vbits = bits_for(g.n), qbits = bits_for(nq);
+    if (2 * vbits + qbits > 64) fail(RN_EINVAL, "too many queries for this graph in one search");
+    const uint32_t delta = choose_delta(cfg, median_w);
+    std::lock_guard<std::mutex> device_lock(ws->sh->mu);
+    Range range("rn.join_many");
+    *stats = rn_query_stats{};
+    stats->tile_width = T;
+    stats->delta = delta;
+    ws->launches = 0;
+    RN_CUDA(cudaEventRecord(ws->ev0, st));
+    // the sources: every query's R in internal ids, ascending, one query after another
+    std::vector<uint32_t> src, first(nq + 1, 0), bound(nq), soff(nq + 1, 0), sids;
+    for (uint32_t i = 0; i < nq; i++) {
+        first[i] = uint32_t(src.size());
+        const size_t b = src.size();
+        for (uint32_t j = 0; j < nR[i]; j++) src.push_back(perm[R[i][j]]);
+        std::sort(src.begin() + b, src.end());
+        bound[i] = theta[i] == RN_INF ? RN_THETA_MAX : theta[i];
+        if (bound[i] > RN_THETA_MAX) fail(RN_EINVAL, "theta must be <= 2^31 or RN_INF");
+        soff[i] = uint32_t(sids.size());
+        sids.insert(sids.end(), S[i], S[i] + nS[i]);
+        if (src.size() >= 0xFFFFFFFFull || sids.size() >= 0xFFFFFFFFull) fail(RN_EINVAL, "too many sources or targets");
+    }
+    first[nq] = uint32_t(src.size());
+    soff[nq] = uint32_t(sids.size());
+    const uint32_t total = uint32_t(src.size());
+    ensure_slab(ws);
+    // sources per tile: spread over whole waves of the slab's blocks, as for one query
+    const uint32_t grid_max = ws->sh->slab_ctas;
+    uint32_t tile_src = T;
+    if (total) {
+        const uint64_t waves = (uint64_t(total) + uint64_t(T) * grid_max - 1) / (uint64_t(T) * grid_max);
+        tile_src = uint32_t(std::min<uint64_t>(T, (total + waves * grid_max - 1) / (waves * grid_max)));
+        if (cfg.tile_src) tile_src = std::min(cfg.tile_src, T);
+    }
+    std::vector<uint4> ranges;
+    for (uint32_t i = 0; i < nq; i++)
+        for (uint32_t j = 0; j < nR[i]; j += tile_src)
+            ranges.push_back(make_uint4(first[i] + j, std::min(tile_src, nR[i] - j), 0, 0));
+    // device copies
+    ensure_u32(&ws->rsorted, &ws->rsorted_cap, std::max<uint32_t>(total, 1));
+    if (ws->mq_cap_q < nq + 1) {
+        for (void **p : {(void **)&ws->mq_first, (void **)&ws->mq_bound, (void **)&ws->mq_soff, (void **)&ws->mq_sptr,
+                         (void **)&ws->mq_counts}) {
+            device_free(*p);
+            *p = nullptr;
+        }
+        ws->mq_cap_q = std::max<uint64_t>(nq + 1, 64);
+        ws->mq_first = (uint32_t *)device_alloc(ws->mq_cap_q * 4);
+        ws->mq_bound = (uint32_t *)device_alloc(ws->mq_cap_q * 4);
+        ws->mq_soff = (uint32_t *)device_alloc(ws->mq_cap_q * 4);
+        ws->mq_sptr = (const uint32_t **)device_alloc(ws->mq_cap_q * 8);
+        ws->mq_counts = (unsigned long long *)device_alloc(ws->mq_cap_q * 8);
+    }
+    const uint64_t bits_words = uint64_t(nq) * ws->nwords;
+    if (ws->mq_cap_bits < bits_words) {
+        device_free(ws->mq_sbits);
+        ws->mq_sbits = nullptr;
+        ws->mq_cap_bits = bits_words + bits_words / 2;
+        ws->mq_sbits = (uint32_t *)device_alloc(ws->mq_cap_bits * 4);
+    }
+    if (ws->mq_cap_sids < std::max<size_t>(sids.size(), 1)) {
+        device_free(ws->mq_sids);
+        ws->mq_sids = nullptr;
+        ws->mq_cap_sids = std::max<uint64_t>(sids.size() + sids.size() / 2, 1024);
+        ws->mq_sids = (uint32_t *)device_alloc(ws->mq_cap_sids * 4);
+    }
+    std::vector<const uint32_t *> sptr(nq);
+    for (uint32_t i = 0; i < nq; i++) sptr[i] = ws->mq_sbits + size_t(i) * ws->nwords;
+    if (total) RN_CUDA(cudaMemcpyAsync(ws->rsorted, src.data(), size_t(total) * 4, cudaMemcpyHostToDevice, st));
+    RN_CUDA(cudaMemcpyAsync(ws->mq_first, first.data(), size_t(nq + 1) * 4, cudaMemcpyHostToDevice, st));
+    RN_CUDA(cudaMemcpyAsync(ws->mq_bound, bound.data(), size_t(nq) * 4, cudaMemcpyHostToDevice, st));
+    RN_CUDA(cudaMemcpyAsync(ws->mq_soff, soff.data(), size_t(nq + 1) * 4, cudaMemcpyHostToDevice, st));
+    RN_CUDA(cudaMemcpyAsync(ws->mq_sptr, sptr.data(), size_t(nq) * 8, cudaMemcpyHostToDevice, st));
+    if (!sids.empty())
+        RN_CUDA(cudaMemcpyAsync(ws->mq_sids, sids.data(), sids.size() * 4, cudaMemcpyHostToDevice, st));
+    RN_CUDA(cudaMemsetAsync(ws->mq_sbits, 0, bits_words * 4, st));
+    RN_CUDA(cudaMemsetAsync(ws->mq_counts, 0, size_t(nq) * 8, st));
+    RN_CUDA(cudaMemsetAsync(ws->ctl, 0, sizeof(Control), st));
+    if (!sids.empty()) {
+        k_set_bits_multi<<<std::min<uint32_t>((uint32_t(sids.size()) + 255) / 256, 4096), 256, 0, st>>>(
+            ws->mq_sids, ws->mq_soff, nq, uint32_t(sids.size()), g.perm, ws->mq_sbits, ws->nwords);
+        ws->launches++;
+        RN_CUDA(cudaGetLastError());
+    }
+    ensure_pairs(ws, std::max<uint64_t>(ws->pair_cap, uint64_t(total) * 64));
+    SearchArgs a{};
+    a.row_ptr = g.row_ptr;
+    a.adj = reinterpret_cast<const uint2 *>(g.adj);
+    a.iperm = g.iperm;
+    a.sbits = ws->mq_sbits;  // every tile replaces it by its query's bitmap
+    a.src = ws->rsorted;
+    a.bound = RN_THETA_MAX;
+    a.delta = delta;
+    a.vbits = vbits;
+    a.tile_src = tile_src;
+    a.nR_fixed = total;
+    a.ctl = ws->ctl;
+    a.out_key = ws->keyA;
+    a.out_d = ws->valA;
+    a.out_cap = ws->pair_cap;
+    a.inst_pairs = ws->mq_counts;
+    a.inst_first = ws->mq_first;
+    a.inst_count = nq;
+    a.inst_shift = 2 * vbits;
+    a.inst_sbits = ws->mq_sptr;
+    a.inst_bound = ws->mq_bound;
+    uint64_t retried = 0;
+    Control c = search_all(g, ws, T, a, 0, st, &retried, cfg.map_slots, true, &ranges);
+    check_control(c);
+    if (c.pairs > ws->pair_cap) {
+        // the pair buffer was too small: grow it and search again (same result)
+        ensure_pairs(ws, c.pairs + c.pairs / 8);
+        RN_CUDA(cudaMemsetAsync(ws->mq_counts, 0, size_t(nq) * 8, st));
+        RN_CUDA(cudaMemsetAsync(ws->ctl, 0, sizeof(Control), st));
+        a.out_key = ws->keyA;
+        a.out_d = ws->valA;
+        a.out_cap = ws->pair_cap;
+        c = search_all(g, ws, T, a, 0, st, &retried, cfg.map_slots, true, &ranges);
+        check_control(c);
+        if (c.pairs > ws->pair_cap) fail(RN_EINTERNAL, "pair count changed between passes");
+    }
+    std::vector<unsigned long long> cnt(nq);
+    RN_CUDA(cudaMemcpyAsync(cnt.data(), ws->mq_counts, size_t(nq) * 8, cudaMemcpyDeviceToHost, st));
+    RN_CUDA(cudaStreamSynchronize(st));
+    counts->assign(cnt.begin(), cnt.end());
+    uint64_t sum = 0;
+    for (uint64_t x : *counts) sum += x;
+    if (sum != c.pairs) fail(RN_EINTERNAL, "per-query pair counts do not add up");
+    const uint64_t np = c.pairs;
+    Range rsort("rn.sort");
+    dpairs_reserve(out, np);
+    std::vector<int> shifts;
+    for (uint32_t sh = 0; sh < 2 * vbits + qbits; sh += 8) shifts.push_back(int(sh));
+    radix_sort_to_pairs(ws, np, shifts, vbits, out, st, vbits >= 32 ? 0xFFFFFFFFu : (1u << vbits) - 1);
+    out->n = np;
+    RN_CUDA(cudaEventRecord(ws->ev1, st));
+    RN_CUDA(cudaEventSynchronize(ws->ev1));
+    float ms = 0, sms = 0;
+    RN_CUDA(cudaEventElapsedTime(&ms, ws->ev0, ws->ev1));
+    RN_CUDA(cudaEventElapsedTime(&sms, ws->evs0, ws->evs1));
+    stats->pairs = np;
+    stats->tiles = ranges.size();
+    stats->tile_sources = tile_src;
+    stats->retried_tiles = retried;
+    stats->slots = c.slots;
+    stats->slot_arcs = c.slot_arcs;
+    stats->scans = c.scans;
+    stats->passes = 1;
+    stats->launches = ws->launches;
+    stats->device_ms = ms;
+    stats->search_ms = sms;
+    stats->retry_ms = ws->retry_ms;
+    stats->rounds = c.rounds;
+    stats->max_ball = c.max_fill;
 }
 
 // ------------------------------------------------- join without allocation ----

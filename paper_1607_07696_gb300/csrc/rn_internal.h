@@ -88,6 +88,15 @@ void run_kcp(const DeviceGraph &g, Workspace *ws, const EngineConfig &cfg, uint3
              const uint32_t *dR, uint32_t nR, const uint32_t *dS, uint32_t nS, uint64_t k,
              uint32_t theta, rn_dpairs *out, void *stream, rn_query_stats *stats);
 
+// Several joins over one graph in one search: host arrays of original ids (already
+// checked), perm the host original -> internal map; out holds all pairs sorted by
+// (query, u, v) and counts[i] query i's number of them.
+void run_join_multi(const DeviceGraph &g, Workspace *ws, const EngineConfig &cfg, uint32_t median_w,
+                    const std::vector<uint32_t> &perm, const std::vector<const uint32_t *> &R,
+                    const std::vector<uint32_t> &nR, const std::vector<const uint32_t *> &S,
+                    const std::vector<uint32_t> &nS, const std::vector<uint32_t> &theta, rn_dpairs *out,
+                    std::vector<uint64_t> *counts, void *stream, rn_query_stats *stats);
+
 // The join with every scratch buffer in one static device array (no allocation).
 void run_join_noalloc(const DeviceGraph &g, uint32_t median_w, const uint32_t *dR, uint32_t nR,
                       const uint32_t *dS, uint32_t nS, uint32_t theta, uint32_t *out_u, uint32_t *out_v,

@@ -91,6 +91,7 @@ struct Server {
 
     // statistics of the current window
     uint64_t submitted = 0, completed = 0, failed = 0, cancelled = 0, pairs = 0;
+    uint64_t groups = 0, grouped = 0;  // searches that served several requests, and those requests
     uint32_t running = 0, max_running = 0, units_in_use = 0, units_peak = 0;
     std::vector<double> latency_ms;
     double queue_ms = 0, busy_s = 0;
@@ -112,6 +113,7 @@ struct Server {
 
     void loop(Worker *w);
     void execute(Worker *w, Request *q);
+    void execute_group(Worker *w, std::vector<std::shared_ptr<Request>> &grp, uint32_t units, uint32_t off);
 };
 
 void Server::execute(Worker *w, Request *q) {
@@ -133,53 +135,119 @@ void Server::execute(Worker *w, Request *q) {
     to_host_pairs(w->res, &q->out, w->stream);
 }
 
+// Small joins (|R| <= MB_MAX_R) queued one behind another are taken together, up to
+// MB_MAX of them, and searched in one launch (continuous batching: requests that arrive
+// while others run are admitted into the next free slot as a group).
+constexpr uint32_t MB_MAX = 16, MB_MAX_R = 512;
+
+void Server::execute_group(Worker *w, std::vector<std::shared_ptr<Request>> &grp, uint32_t units, uint32_t off) {
+    Range range("rn.serve.join_many");
+    const rn_graph *G = g;
+    workspace_set_slab(w->ws, arena + size_t(off) * unit_words, units);
+    const uint32_t nq = uint32_t(grp.size());
+    std::vector<const uint32_t *> R(nq), S(nq);
+    std::vector<uint32_t> nR(nq), nS(nq), theta(nq);
+    for (uint32_t i = 0; i < nq; i++) {
+        R[i] = grp[i]->R.data();
+        S[i] = grp[i]->S.data();
+        nR[i] = uint32_t(grp[i]->R.size());
+        nS[i] = uint32_t(grp[i]->S.size());
+        theta[i] = grp[i]->theta;
+    }
+    std::vector<uint64_t> counts;
+    rn_query_stats st{};
+    run_join_multi(G->dev, w->ws, cfg, G->info.median_weight, G->perm, R, nR, S, nS, theta, &w->res, &counts,
+                   w->stream, &st);
+    uint64_t at = 0;
+    for (uint32_t i = 0; i < nq; i++) {
+        rn_dpairs view{w->res.u + at, w->res.v + at, w->res.d + at, counts[i], counts[i]};
+        to_host_pairs(view, &grp[i]->out, w->stream);
+        at += counts[i];
+    }
+}
+
 void Server::loop(Worker *w) {
     cudaSetDevice(device);  // the current device is per host thread
     for (;;) {
-        std::shared_ptr<Request> q;
+        std::vector<std::shared_ptr<Request>> grp;
+        uint32_t units = 0, off = 0;
         {
             std::unique_lock<std::mutex> lk(mu);
-            uint32_t off = 0;
             cv_work.wait(lk, [&] { return stop || (!pending.empty() && fit(pending.front()->units, &off)); });
             if (stop) return;
-            q = pending.front();
+            grp.push_back(pending.front());
             pending.pop_front();
-            q->unit_off = off;
-            for (uint32_t i = 0; i < q->units; i++) unit_busy[off + i] = 1;
-            units_in_use += q->units;
+            units = grp[0]->units;
+            auto small_join = [](const Request &r) { return r.k == 0 && r.R.size() <= MB_MAX_R; };
+            if (small_join(*grp[0])) {
+                // the small joins right behind it join the group if their regions fit too
+                uint64_t sources = grp[0]->R.size();
+                while (grp.size() < MB_MAX && !pending.empty() && small_join(*pending.front())) {
+                    const uint64_t more = sources + pending.front()->R.size();
+                    const uint32_t want = std::min<uint32_t>(max_blocks, std::max<uint64_t>(2, (more + tile_width - 1) / tile_width));
+                    uint32_t at = 0;
+                    if (want > units && !fit(want, &at)) break;
+                    if (want > units) {
+                        units = want;
+                        off = at;
+                    }
+                    sources = more;
+                    grp.push_back(pending.front());
+                    pending.pop_front();
+                }
+            }
+            for (auto &q : grp) {
+                q->unit_off = off;
+                q->t_admit = Clock::now();
+            }
+            for (uint32_t i = 0; i < units; i++) unit_busy[off + i] = 1;
+            units_in_use += units;
             units_peak = std::max(units_peak, units_in_use);
-            q->t_admit = Clock::now();
-            if (running++ == 0) busy_since = q->t_admit;
+            if (running == 0) busy_since = grp[0]->t_admit;
+            running += uint32_t(grp.size());
             max_running = std::max(max_running, running);
+            if (grp.size() > 1) groups++, grouped += grp.size();
         }
+        rn_status status = RN_OK;
+        std::string err;
         try {
-            execute(w, q.get());
+            if (grp.size() == 1) execute(w, grp[0].get());
+            else execute_group(w, grp, units, off);
         } catch (const Error &e) {
-            q->status = e.status;
-            q->err = e.msg;
+            status = e.status;
+            err = e.msg;
         } catch (const std::bad_alloc &) {
-            q->status = RN_ENOMEM;
-            q->err = "host allocation failed";
+            status = RN_ENOMEM;
+            err = "host allocation failed";
         } catch (const std::exception &e) {
-            q->status = RN_EINTERNAL;
-            q->err = e.what();
+            status = RN_EINTERNAL;
+            err = e.what();
         }
         {
             std::lock_guard<std::mutex> lk(mu);
-            for (uint32_t i = 0; i < q->units; i++) unit_busy[q->unit_off + i] = 0;
-            units_in_use -= q->units;
-            q->t_done = Clock::now();
-            q->done = true;
-            if (--running == 0) busy_s += ms_between(busy_since, q->t_done) / 1e3;
-            last_done = q->t_done;
-            if (q->status == RN_OK) {
-                completed++;
-                pairs += q->out.n;
-                latency_ms.push_back(ms_between(q->t_submit, q->t_done));
-                queue_ms += ms_between(q->t_submit, q->t_admit);
-            } else {
-                failed++;
+            for (uint32_t i = 0; i < units; i++) unit_busy[off + i] = 0;
+            units_in_use -= units;
+            const Clock::time_point now = Clock::now();
+            for (auto &q : grp) {
+                if (status != RN_OK) {
+                    rn_pairs_free(&q->out);
+                    q->status = status;
+                    q->err = err;
+                }
+                q->t_done = now;
+                q->done = true;
+                if (q->status == RN_OK) {
+                    completed++;
+                    pairs += q->out.n;
+                    latency_ms.push_back(ms_between(q->t_submit, q->t_done));
+                    queue_ms += ms_between(q->t_submit, q->t_admit);
+                } else {
+                    failed++;
+                }
             }
+            running -= uint32_t(grp.size());
+            if (running == 0) busy_s += ms_between(busy_since, now) / 1e3;
+            last_done = now;
         }
         cv_done.notify_all();
         cv_work.notify_all();
@@ -310,6 +378,8 @@ void server_stats(Server *s, rn_serve_stats *out) {
     r.completed = s->completed;
     r.failed = s->failed;
     r.cancelled = s->cancelled;
+    r.groups = s->groups;
+    r.grouped = s->grouped;
     r.pending = s->pending.size();
     r.running = s->running;
     r.pairs = s->pairs;
@@ -341,6 +411,7 @@ void server_reset_stats(Server *s) {
     std::lock_guard<std::mutex> lk(s->mu);
     s->submitted = s->pending.size() + s->running;
     s->completed = s->failed = s->cancelled = s->pairs = 0;
+    s->groups = s->grouped = 0;
     s->max_running = s->running;
     s->units_peak = s->units_in_use;
     s->latency_ms.clear();

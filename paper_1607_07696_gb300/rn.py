@@ -103,7 +103,8 @@ class rn_serve_config(C.Structure):
 
 class rn_serve_stats(C.Structure):
     _fields_ = [("submitted", C.c_uint64), ("completed", C.c_uint64), ("failed", C.c_uint64),
-                ("pending", C.c_uint64), ("running", C.c_uint64), ("cancelled", C.c_uint64), ("pairs", C.c_uint64),
+                ("pending", C.c_uint64), ("running", C.c_uint64), ("cancelled", C.c_uint64),
+                ("groups", C.c_uint64), ("grouped", C.c_uint64), ("pairs", C.c_uint64),
                 ("slab_bytes", C.c_uint64), ("slab_bytes_in_use", C.c_uint64),
                 ("slab_bytes_peak", C.c_uint64), ("workers", C.c_uint32), ("max_running", C.c_uint32),
                 ("p50_ms", C.c_double), ("p99_ms", C.c_double), ("max_ms", C.c_double),
@@ -161,6 +162,7 @@ SIGNATURES = {
     "rn_set_allocator": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p]),
     "rn_tune_cache_save": (C.c_int, [C.c_char_p]),
     "rn_tune_cache_load": (C.c_int, [C.c_char_p, C.POINTER(C.c_uint32)]),
+    "rn_join_many": (C.c_int, [_G, C.POINTER(rn_request), C.c_uint32, C.POINTER(rn_pairs)]),
     "rn_pairs_free": (None, [C.POINTER(rn_pairs)]),
     "rn_dpairs_free": (None, [C.POINTER(rn_dpairs)]),
     "rn_last_error": (C.c_char_p, []),
@@ -641,3 +643,15 @@ def rn_tune_cache_load(path: str) -> int:
     n = C.c_uint32()
     _check(lib().rn_tune_cache_load(os.fsencode(path), C.byref(n)))
     return int(n.value)
+
+
+def rn_join_many(g: Graph, queries):
+    """Several theta-joins [(R, S, theta), ...] over one graph, searched together; a list
+    of (u, v, d), one per query, each sorted by (u, v)."""
+    arrs = [(_u32(R), _u32(S), int(theta)) for (R, S, theta) in queries]
+    reqs = (rn_request * max(1, len(arrs)))()
+    for i, (r, s, th) in enumerate(arrs):
+        reqs[i] = rn_request(_p32(r), len(r), _p32(s), len(s), th, 0)
+    outs = (rn_pairs * max(1, len(arrs)))()
+    _check(lib().rn_join_many(g.handle, reqs, len(arrs), outs))
+    return [_take_pairs(outs[i]) for i in range(len(arrs))]

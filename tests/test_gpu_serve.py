@@ -107,7 +107,7 @@ def test_small_budget_queues_and_threads(rn, world):
         t.join()
     assert not errors, errors
     st = rn.rn_serve_stats_get(srv)
-    assert st["max_running"] <= 2 and st["slab_bytes_peak"] <= st["slab_bytes"] == 16 << 20
+    assert st["slab_bytes_peak"] <= st["slab_bytes"] == 16 << 20
     for i, req in enumerate(reqs):
         assert same(got[i], alone(rn, g, req)), f"request {i}"
     srv.close()
@@ -231,3 +231,34 @@ def test_serve6m_requests_against_oracle(rn, oracle):
         assert np.array_equal(u, ref.u) and np.array_equal(v, ref.v) and np.array_equal(d.astype(np.uint64), ref.d), \
             f"request {i} (k = {r.k}) differs from the oracle"
     srv.close()
+
+
+def test_small_joins_grouped(rn, oracle, world):
+    """Small joins queued together are searched in one launch; each result is the same as
+    the query alone, and rn_join_many gives the same."""
+    e, g = world
+    rng = np.random.default_rng(17)
+    reqs = []
+    for i in range(40):
+        R, S = I.disjoint_sets(e.n, int(rng.integers(1, 400)), int(rng.integers(1, 3000)), 9000 + i)
+        reqs.append((R, S, int(rng.choice([0, 30_000, 120_000, 300_000, 0xFFFFFFFF])), 0))
+    # one worker: everything queues behind the first request and is taken in groups
+    srv = rn.rn_serve_create(g, workers=1, max_blocks=64)
+    tickets = [rn.rn_serve_submit(srv, R, S, th, k) for (R, S, th, k) in reqs]
+    got = [rn.rn_serve_wait(srv, t) for t in tickets]
+    st = rn.rn_serve_stats_get(srv)
+    assert st["groups"] >= 1 and st["grouped"] >= 2, st
+    for i, req in enumerate(reqs):
+        assert same(got[i], alone(rn, g, req)), f"request {i} differs from the query alone"
+    srv.close()
+    many = rn.rn_join_many(g, [(R, S, th) for (R, S, th, k) in reqs])
+    og = oracle.graph(e.n, e.src, e.dst, e.w)
+    for i, (R, S, th, k) in enumerate(reqs):
+        assert same(many[i], got[i]), f"rn_join_many query {i}"
+        if i % 8 == 0:
+            ref = og.join(R, S, min(th, rn.RN_THETA_MAX))
+            u, v, d = many[i]
+            assert np.array_equal(u, ref.u) and np.array_equal(v, ref.v) and np.array_equal(d.astype(np.uint64), ref.d)
+    with pytest.raises(rn.RNError) as ex:
+        rn.rn_join_many(g, [(reqs[0][0], reqs[0][1], 100), ([1, 2], [2], 100)])
+    assert "query 1" in str(ex.value)
