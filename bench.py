@@ -34,7 +34,7 @@ METRIC = "join pairs/s"
 UNIT = "pairs/s"
 WORKLOADS = json.load(open(os.path.join(ROOT, "tests", "golden", "workloads.json")))
 ENGINE_SRC = os.path.join(ROOT, "paper_1607_07696_gb300", "csrc", "rn_engine.cu")
-PROFILE = os.path.join(ROOT, "profiles", "tile_search_road264k.json")
+PROFILE = os.path.join(ROOT, "profiles", "search_road264k.json")
 
 
 def parse():
@@ -148,21 +148,36 @@ def graph_digest(e) -> dict:
             "xsum": int((e.src.astype(np.uint64) * 3 + e.dst.astype(np.uint64)).sum())}
 
 
+def algorithmic_bytes(st: dict, pairs: int) -> float:
+    """Bytes the search must move, summed over tiles (a source alone is a tile of one
+    lane): 8 per reached node (CSR offsets) and per arc leaving it (column, weight), 8
+    per node and lane (its distance written, then read at emission), a bit per node (S
+    membership) and 12 per pair."""
+    return (8 * st["slots"] + 8 * st["slot_arcs"] + 8 * st["slot_lanes"] + st["slots"] / 8
+            + 12 * pairs)
+
+
+def search_kernel(st: dict) -> str:
+    return "k_source_search" if st["tile_width"] == 1 else "k_tile_search"
+
+
 def engine_hash() -> str:
-    """Hash of the tile-search section of the engine source (the profiled kernel)."""
+    """Hash of the search sections of the engine source (tile and source search, the
+    profiled kernels)."""
     src = open(ENGINE_SRC).read()
     a = src.index("// ------------------------------------------------------------ tile search ----")
     b = src.index("// ------------------------------------------------------------- radix sort ----")
     return hashlib.sha256(src[a:b].encode()).hexdigest()[:16]
 
 
-def profiled_traffic(workload: str):
-    """DRAM bytes per launch of the tile search from the committed ncu summary, or None
-    when there is none or the kernel source changed since it was taken."""
+def profiled_traffic(workload: str, kernel: str):
+    """DRAM bytes per launch of the search kernel from the committed ncu summary, or None
+    when there is none, it covers another kernel or the kernel source changed since."""
     if not os.path.exists(PROFILE):
         return None
     p = json.load(open(PROFILE))
-    if p.get("workload") != workload or p.get("engine_sha") != engine_hash():
+    if (p.get("workload") != workload or p.get("engine_sha") != engine_hash()
+            or not str(p.get("kernel", "")).startswith(kernel)):
         return None
     return p.get("dram_bytes_per_launch")
 
@@ -295,8 +310,7 @@ def join_1m_leg(rn, steps: int, stream, flush, peak: float) -> dict:
         ms.append(a.elapsed_time(b))
         st = rn.rn_last_query_stats()
         search.append(st["search_ms"] + st["retry_ms"])
-    T = st["tile_width"]
-    alg = 8 * st["slots"] + 8 * st["slot_arcs"] + 8 * T * st["slots"] + st["slots"] / 8 + 12 * n
+    alg = algorithmic_bytes(st, n)
     sm = statistics.mean(search)
     return {"workload": "road1070k_join: 1.07M nodes, 2.7M edges, |R| = |S| = 50,000 clustered",
             "theta": theta, "pairs": int(n), "value": n / (statistics.median(ms) / 1e3), "unit": UNIT,
@@ -521,8 +535,7 @@ def run_engine(args):
             dist.destroy_process_group()
         return
     T = stats["tile_width"]
-    alg_bytes = (8 * stats["slots"] + 8 * stats["slot_arcs"] + 8 * T * stats["slots"]
-                 + stats["slots"] / 8 + 12 * npairs)
+    alg_bytes = algorithmic_bytes(stats, npairs)
     smean = statistics.mean(search_ms)
     achieved = alg_bytes / (smean / 1e3) / 1e9
     peak, peak_kind = measured_peak_gbs()
@@ -554,8 +567,8 @@ def run_engine(args):
                 "d2h_bytes_per_step": 12 * npairs},
         "gpu_launches": int(stats["launches"]) * args.steps,
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                     "frac": achieved / peak, "traffic": profiled_traffic(args.workload),
-                     "kernel": "k_tile_search", "peak_kind": peak_kind,
+                     "frac": achieved / peak, "traffic": profiled_traffic(args.workload, search_kernel(stats)),
+                     "kernel": search_kernel(stats), "peak_kind": peak_kind,
                      "search_ms": smean, "alg_bytes_per_launch": alg_bytes},
         "clocks": clk.summary(),
         "engine": {"reorder_ms": info["reorder_ms"], "slots": stats["slots"],

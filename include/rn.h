@@ -85,8 +85,14 @@ typedef struct {
 
 /* Engine knobs.  Zero in any field means "choose automatically". */
 typedef struct {
-    uint32_t tile_width;  /* lanes of a slab row, the most sources one thread block
-                             searches together: 32, 64 or 128 */
+    uint32_t tile_width;  /* 1: every source searched by one warp with its ball in a
+                             shared-memory map (sources whose ball outgrows the largest
+                             warp map, 8192 slots, go to the tile search of width 32);
+                             32, 64 or 128: lanes of a slab row, the most sources one
+                             thread block searches together; 0: the warp search while the
+                             balls met so far, scaled to the query's bound, fit a warp
+                             map, else tiles of 32 (k closest pairs and batches always
+                             run tiles, 32 wide unless set) */
     uint32_t tile_sources;/* sources per tile, <= tile_width; 0 spreads R over whole
                              waves of resident blocks */
     uint32_t delta;       /* bucket width of the delta-stepping search, in weight units */
@@ -145,6 +151,8 @@ typedef struct {
     uint64_t max_ball;      /* largest union ball (slots) of a tile that completed */
     double retry_ms;        /* time of the launches that searched overflowed tiles again */
     uint64_t dirty_groups;  /* dirty lane-groups of the scanned items, over all rounds */
+    uint64_t slot_lanes;    /* sum over tiles of slots times the tile's lanes (tile_width
+                               1: the sum of the sources' balls) */
 } rn_query_stats;
 
 /*

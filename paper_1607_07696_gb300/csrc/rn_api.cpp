@@ -175,8 +175,8 @@ uint32_t median_weight(const rn::HostGraph &g) {
 void apply_config(rn_graph *g, const rn_config *cfg) {
     rn::EngineConfig c;
     if (cfg) {
-        if (cfg->tile_width && cfg->tile_width != 32 && cfg->tile_width != 64 && cfg->tile_width != 128)
-            rn::fail(RN_EINVAL, "tile_width must be 0, 32, 64 or 128");
+        if (cfg->tile_width > 1 && cfg->tile_width != 32 && cfg->tile_width != 64 && cfg->tile_width != 128)
+            rn::fail(RN_EINVAL, "tile_width must be 0, 1, 32, 64 or 128");
         if (cfg->tile_width) c.tile_width = cfg->tile_width;
         c.tile_src = cfg->tile_sources;
         c.delta = cfg->delta;

@@ -204,7 +204,10 @@ struct Control {
     unsigned long long cyc_stepA, round_arcs;
     unsigned long long dirty_groups;  // dirty lane-groups of the scanned items
     uint32_t max_fill;  // largest union ball (slots) of a completed tile
-    uint32_t check[4];  // first failed device-side check of the batch path: code, index, value
+    uint32_t check[4];  // first failed device-side check: code, index, value
+    unsigned long long slot_lanes;  // sum over tiles of slots times the tile's lanes
+    uint32_t src_max_ball;          // largest ball of a source the warp search completed
+    uint32_t pad_;
 };
 
 // Record the first failed device-side check (the access it guarded is skipped).
@@ -284,6 +287,10 @@ struct Workspace {
     const uint32_t **mq_sptr = nullptr;
     unsigned long long *mq_counts = nullptr;
     uint64_t mq_cap_q = 0, mq_cap_bits = 0, mq_cap_sids = 0;
+    // the largest source ball the last warp search met (or estimated, for sources
+    // whose map overflowed) and its bound: predicts the next query's balls
+    double ball_max = 0;
+    uint32_t ball_theta = 0;
     uint32_t launches = 0;  // kernels launched by the current query
     int blocks_per_sm = 0;  // occupancy of the shared-map search kernel
     uint64_t bytes = 0;
@@ -1181,6 +1188,7 @@ __global__ void __launch_bounds__(THREADS, (THREADS == NARROW ? CTAS_PER_SM : 1)
         atomicAdd(&a.ctl->scans, (unsigned long long)my_scans);
         atomicAdd(&a.ctl->dirty_groups, (unsigned long long)my_dirty);
         atomicAdd(&a.ctl->slots, (unsigned long long)my_slots);
+        atomicAdd(&a.ctl->slot_lanes, (unsigned long long)my_slots * T);
         atomicAdd(&a.ctl->slot_arcs, (unsigned long long)my_arcs);
     }
     if (tid == 0) {
@@ -1192,6 +1200,387 @@ __global__ void __launch_bounds__(THREADS, (THREADS == NARROW ? CTAS_PER_SM : 1)
         atomicAdd(&a.ctl->round_arcs, s_tel[T_ARCS]);
         atomicAdd(&a.ctl->cyc_bound, s_tel[T_BOUND]);
         atomicAdd(&a.ctl->cyc_emit, s_tel[T_EMIT]);
+    }
+}
+
+// ----------------------------------------------------------- source search ----
+// One warp searches one source at a time (persistent: warps pop sources from the work
+// counter).  The source's ball lives in a map of MS slots in shared memory that only this
+// warp touches:
+//   key[h]   node id (SK_NODE bits) and four flags: SK_SEEN (its arcs were relaxed at
+//            least once), SK_IN_S (the node is in S, read at that first scan), SK_DIRTY
+//            (its distance improved since its arcs were last relaxed), SK_QUEUED (in the
+//            near queue, or claimed for it); SK_EMPTY when free;
+//   dist[h]  tentative distance, INF when free.
+// Delta-stepping with one lane of distances: a round takes up to 64 near-queue items (two
+// per lane), clears their flags and reads their distance and CSR range, lays their arcs
+// out with a warp prefix sum, then relaxes 128 arcs at a time (four per lane): every arc
+// load, then every first probe, then every atomicMin on dist,
+// then on improvements every flag update is issued before the results are used, so their
+// latencies overlap; a slot is pushed when it enters the near queue.  When the
+// queue drains, one pass over the map takes the least pending distance and collects the
+// slots of the next bucket.  There is no block barrier: lanes synchronise with __syncwarp,
+// and a round waits on two dependent L2 round trips (CSR offsets, then arcs).
+//
+// A source whose ball outgrows 7/8 of the map stops and reports (source, bound, bucket end
+// reached, slots filled); the host searches it again with a larger map or with the tile
+// search.
+constexpr uint32_t SK_NODE = 0x0FFFFFFFu;
+constexpr uint32_t SK_EMPTY = SK_NODE;
+constexpr uint32_t SK_IN_S = 0x10000000u;
+constexpr uint32_t SK_SEEN = 0x20000000u;
+constexpr uint32_t SK_DIRTY = 0x40000000u;
+constexpr uint32_t SK_QUEUED = 0x80000000u;
+constexpr uint32_t SRC_BLOCK_SMEM = 73728;  // shared memory of one block: three per SM
+constexpr uint32_t SRC_BLOCKS_PER_SM = 3;
+constexpr uint32_t SRC_MS_MIN = 1024, SRC_MS_MAX = 8192;
+__host__ __device__ constexpr uint32_t log2u(uint32_t x) { return x <= 1 ? 0 : 1 + log2u(x >> 1); }
+__host__ __device__ constexpr uint32_t src_qcap(uint32_t ms) { return ms / 8; }
+__host__ __device__ constexpr uint32_t src_words(uint32_t ms) { return 2 * ms + 2 * src_qcap(ms); }
+__host__ __device__ constexpr uint32_t src_warps(uint32_t ms) { return SRC_BLOCK_SMEM / (4 * src_words(ms)); }
+
+// Slot of node y in a warp map of MS slots, probing from slot h on (linear probing) and
+// inserting y if absent; EMPTY when the map is full.
+template <uint32_t MS>
+__device__ __forceinline__ uint32_t src_slot(uint32_t *key, uint32_t y, uint32_t h, bool *inserted) {
+    volatile uint32_t *vk = key;
+    *inserted = false;
+    for (uint32_t probe = 0; probe < MS; probe++) {
+        const uint32_t k = vk[h];
+        if ((k & SK_NODE) == y) return h;
+        if (k == SK_EMPTY) {
+            const uint32_t prev = atomicCAS(&key[h], SK_EMPTY, y);
+            if (prev == SK_EMPTY) {
+                *inserted = true;
+                return h;
+            }
+            if ((prev & SK_NODE) == y) return h;
+        }
+        h = (h + 1) & (MS - 1);
+    }
+    return EMPTY;
+}
+
+__device__ __forceinline__ unsigned long long warp_sum64(unsigned long long v) {
+#pragma unroll
+    for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(FULL, v, o);
+    return v;
+}
+
+template <uint32_t MS>
+__global__ void __launch_bounds__(src_warps(MS) * 32, SRC_BLOCKS_PER_SM) k_source_search(SearchArgs a) {
+    constexpr uint32_t QS = src_qcap(MS);
+    constexpr int AP = 4;  // arcs per lane in flight
+    extern __shared__ uint32_t smem[];
+    const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const uint32_t lt = (1u << lane) - 1;
+    uint32_t *key = smem + warp * src_words(MS);
+    uint32_t *dist = key + MS;
+    uint32_t *qa = dist + MS, *qb = qa + QS;
+    for (uint32_t h = lane; h < MS; h += 32) {
+        key[h] = SK_EMPTY;
+        dist[h] = INF;
+    }
+    __syncwarp();
+    if (__ldcg(&a.ctl->err)) return;
+    const uint32_t nR1 = a.nR_fixed ? a.nR_fixed : __ldcg(&a.ctl->r_count);
+    const uint32_t nitems = a.range_list ? a.ntiles : nR1;
+    // per lane: items scanned, their arcs, arcs of first scans; per warp (every lane the
+    // same): rounds, bucket boundaries, slots of completed sources, SM cycles by phase
+    unsigned long long n_scans = 0, n_arcs = 0, n_slot_arcs = 0;
+    unsigned long long n_rounds = 0, n_bounds = 0, n_slots = 0;
+    unsigned long long cyc_round = 0, cyc_bound = 0, cyc_emit = 0;
+    uint32_t max_ball = 0;
+    long long t_mark = clock64();
+
+    for (;;) {
+        uint32_t item = 0;
+        if (lane == 0) item = atomicAdd(&a.ctl->tile_next, 1u);
+        item = __shfl_sync(FULL, item, 0);
+        if (item >= nitems) break;
+        const uint32_t si = a.range_list ? a.range_list[item].x : item;
+        if (si >= nR1) continue;  // never past R
+        uint32_t bound = a.bound;
+        const uint32_t *sbits = a.sbits;
+        unsigned long long prefix = 0;
+        uint32_t inst = 0;
+        if (a.inst_first) {
+            // the query whose sources hold si: the last with inst_first <= si
+            uint32_t lo = 0, hi = a.inst_count - 1;
+            while (lo < hi) {
+                const uint32_t mid = (lo + hi + 1) >> 1;
+                if (a.inst_first[mid] <= si) lo = mid;
+                else hi = mid - 1;
+            }
+            inst = lo;
+            bound = a.inst_bound[lo];
+            sbits = a.inst_sbits[lo];
+            prefix = (unsigned long long)lo << a.inst_shift;
+        }
+        const uint32_t y0 = a.src[si];
+        if (RN_BAD(y0 < a.n_nodes, 11, si, y0)) continue;
+        const unsigned long long u = __ldg(&a.iperm[y0]);
+        const uint64_t delta = a.delta;
+        // the source, at distance 0, is the only item of the near queue
+        if (lane == 0) {
+            const uint32_t h = (y0 * 0x9E3779B1u) >> (32 - log2u(MS));
+            key[h] = y0 | SK_DIRTY | SK_QUEUED;
+            dist[h] = 0;
+            qa[0] = h;
+        }
+        __syncwarp();
+        uint32_t *qcur = qa, *qnext = qb;
+        uint32_t ncur = 1, fill = 1;
+        bool fail = false;
+        uint64_t tau = delta < uint64_t(bound) + 1 ? delta : uint64_t(bound) + 1;  // end of the bucket
+
+        // collect: least distance m of the dirty slots; those below lim go to the near
+        // queue (as many as fit: the rest stay dirty for the next pass), every other
+        // slot loses a stale queued flag (one whose push found the queue full)
+        auto collect = [&](uint64_t lim, uint32_t *m) {
+            uint32_t nq = 0;
+#pragma unroll 4
+            for (uint32_t c = 0; c < MS; c += 32) {
+                const uint32_t h = c + lane;
+                const uint32_t k = key[h];
+                const bool dirty = (k & SK_DIRTY) != 0;  // SK_EMPTY carries no flag
+                const uint32_t d = dirty ? dist[h] : INF;
+                *m = min(*m, d);
+                const bool take = dirty && d < lim;
+                const uint32_t b = __ballot_sync(FULL, take);
+                const uint32_t qi = nq + __popc(b & lt);
+                const bool queued = take && qi < QS;
+                if (queued) qcur[qi] = h;
+                nq += __popc(b);
+                const uint32_t nk = queued ? (k | SK_QUEUED) : (k & ~SK_QUEUED);
+                if (nk != k) key[h] = nk;
+            }
+            return nq;
+        };
+
+        for (;;) {
+            // ---- rounds of the current bucket
+            while (ncur && !fail) {
+                n_rounds++;
+                uint32_t nnext = 0;
+                for (uint32_t c0 = 0; c0 < ncur && !fail; c0 += 64) {
+                    // step A: items c0 + 2 lane and c0 + 2 lane + 1
+                    uint32_t beg[2], deg[2], dv[2];
+#pragma unroll
+                    for (int t = 0; t < 2; t++) {
+                        const uint32_t j = c0 + 2 * lane + t;
+                        beg[t] = 0;
+                        deg[t] = 0;
+                        dv[t] = INF;
+                        if (j < ncur) {
+                            const uint32_t x = qcur[j];
+                            if (!RN_BAD(x < MS, 12, j, x)) {
+                                const uint32_t k = key[x];
+                                const uint32_t y = k & SK_NODE;
+                                if (!RN_BAD(y < a.n_nodes, 13, x, y)) {
+                                    dv[t] = dist[x];
+                                    beg[t] = __ldg(&a.row_ptr[y]);
+                                    deg[t] = __ldg(&a.row_ptr[y + 1]) - beg[t];
+                                    uint32_t in_s = k & SK_IN_S;
+                                    if (!(k & SK_SEEN)) {  // first scan: S membership, arcs
+                                        in_s = ((__ldg(&sbits[y >> 5]) >> (y & 31)) & 1u) ? SK_IN_S : 0u;
+                                        n_slot_arcs += deg[t];
+                                    }
+                                    key[x] = y | SK_SEEN | in_s;
+                                    if (RN_BAD(uint64_t(beg[t]) + deg[t] <= a.n_arcs, 14, y, beg[t])) deg[t] = 0;
+                                    n_scans++;
+                                    n_arcs += deg[t];
+                                }
+                            }
+                        }
+                    }
+                    const uint32_t mine = deg[0] + deg[1];
+                    uint32_t incl = mine;
+#pragma unroll
+                    for (int o = 1; o < 32; o <<= 1) {
+                        const uint32_t t = __shfl_up_sync(FULL, incl, o);
+                        if (lane >= uint32_t(o)) incl += t;
+                    }
+                    const uint32_t total = __shfl_sync(FULL, incl, 31);
+                    const uint32_t ex = incl - mine;  // first arc of this lane's items
+                    __syncwarp();                     // flags cleared before any relaxation
+                    // step B: arcs b0 .. b0 + 127, arc g of lane l's items when
+                    // ex[l] <= g < ex[l] + deg[l][0] + deg[l][1] (lanes past the items
+                    // have ex = total)
+                    for (uint32_t b0 = 0; b0 < total && !fail; b0 += 32 * AP) {
+                        uint32_t y[AP], nd[AP];
+#pragma unroll
+                        for (int k = 0; k < AP; k++) {
+                            const uint32_t gi = b0 + 32 * k + lane;
+                            uint32_t l = 0;
+#pragma unroll
+                            for (uint32_t s = 16; s; s >>= 1)
+                                if (__shfl_sync(FULL, ex, l + s) <= gi) l += s;
+                            const uint32_t o = gi - __shfl_sync(FULL, ex, l);
+                            const uint32_t d0 = __shfl_sync(FULL, deg[0], l);
+                            const uint32_t bb0 = __shfl_sync(FULL, beg[0], l);
+                            const uint32_t bb1 = __shfl_sync(FULL, beg[1], l);
+                            const uint32_t v0 = __shfl_sync(FULL, dv[0], l);
+                            const uint32_t v1 = __shfl_sync(FULL, dv[1], l);
+                            const bool second = o >= d0;
+                            const uint32_t ai = second ? bb1 + (o - d0) : bb0 + o;
+                            nd[k] = INF;
+                            y[k] = 0;
+                            if (gi < total && !RN_BAD(ai < a.n_arcs, 15, gi, ai)) {
+                                const uint2 arc = __ldg(&a.adj[ai]);
+                                y[k] = arc.x;
+                                nd[k] = (second ? v1 : v0) + arc.y;  // <= bound + 2^24: no overflow
+                            }
+                        }
+                        // every probe, then every atomic, of the batch issued back to back
+                        // (their latencies overlap instead of adding up arc after arc)
+                        uint32_t h[AP], kv[AP];
+#pragma unroll
+                        for (int k = 0; k < AP; k++) {
+                            if (nd[k] <= bound && RN_BAD(y[k] < a.n_nodes, 16, b0 + 32 * k + lane, y[k])) nd[k] = INF;
+                            h[k] = (y[k] * 0x9E3779B1u) >> (32 - log2u(MS));
+                            kv[k] = nd[k] <= bound ? ((volatile uint32_t *)key)[h[k]] : 0u;
+                        }
+                        uint32_t ins_count = 0;
+                        bool full = false;
+#pragma unroll
+                        for (int k = 0; k < AP; k++) {
+                            bool ins = false;
+                            if (nd[k] > bound) h[k] = EMPTY;
+                            else if ((kv[k] & SK_NODE) != y[k]) h[k] = src_slot<MS>(key, y[k], h[k], &ins);
+                            ins_count += ins;
+                            full |= nd[k] <= bound && h[k] == EMPTY;
+                        }
+                        fill += __reduce_add_sync(FULL, ins_count);  // once per batch
+                        uint32_t old[AP];
+#pragma unroll
+                        for (int k = 0; k < AP; k++) old[k] = h[k] != EMPTY ? atomicMin(&dist[h[k]], nd[k]) : 0u;
+                        uint32_t kf[AP];
+#pragma unroll
+                        for (int k = 0; k < AP; k++)
+                            kf[k] = h[k] != EMPTY && nd[k] < old[k]
+                                        ? atomicOr(&key[h[k]], nd[k] < tau ? (SK_DIRTY | SK_QUEUED) : SK_DIRTY)
+                                        : SK_QUEUED;
+#pragma unroll
+                        for (int k = 0; k < AP; k++) {
+                            const bool push = h[k] != EMPTY && nd[k] < old[k] && nd[k] < tau && !(kf[k] & SK_QUEUED);
+                            const uint32_t pb = __ballot_sync(FULL, push);
+                            if (push) {
+                                const uint32_t qi = nnext + __popc(pb & lt);
+                                if (qi < QS) qnext[qi] = h[k];
+                            }
+                            nnext += __popc(pb);
+                        }
+                        if (__any_sync(FULL, full) || fill > a.max_fill) fail = true;
+                    }
+                    __syncwarp();  // this step's relaxations before the next step's scans
+                }
+                ncur = min(nnext, QS);
+                uint32_t *t = qcur;
+                qcur = qnext;
+                qnext = t;
+            }
+            if (lane == 0) {
+                const long long t = clock64();
+                cyc_round += t - t_mark;
+                t_mark = t;
+            }
+            if (fail) break;
+            // ---- the near queue is empty: the next bucket
+            n_bounds++;
+            const uint64_t top = uint64_t(bound) + 1;
+            const uint64_t tau2 = tau + delta < top ? tau + delta : top;
+            uint32_t m = INF;
+            uint32_t nq = collect(tau2, &m);
+            m = __reduce_min_sync(FULL, m);
+            if (m == INF) break;  // nothing pending: the search is complete
+            if (m >= tau2) {
+                // no pending slot in the next bucket: skip to the one holding m
+                const uint64_t t = (uint64_t(m) / delta + 1) * delta;
+                tau = t < top ? t : top;
+                uint32_t m2 = INF;
+                nq = collect(tau, &m2);
+            } else {
+                tau = tau2;
+            }
+            ncur = min(nq, QS);
+            __syncwarp();
+            if (lane == 0) {
+                const long long t = clock64();
+                cyc_bound += t - t_mark;
+                t_mark = t;
+            }
+        }
+
+        // ---- emission: every slot of an S node (all lie within the bound), then the map
+        // is left clean for the next source
+        uint32_t *hits = qa;  // the queues are free: one ballot word per 32 slots
+        if (!fail) {
+            uint32_t cnt = 0;
+#pragma unroll 8
+            for (uint32_t c = 0; c < MS; c += 32) {
+                const uint32_t b = __ballot_sync(FULL, (key[c + lane] & SK_IN_S) != 0u);  // never on SK_EMPTY
+                if (lane == 0) hits[c >> 5] = b;
+                cnt += __popc(b);
+            }
+            unsigned long long base = 0;
+            if (lane == 0 && cnt) {
+                base = atomicAdd(&a.ctl->pairs, (unsigned long long)cnt);
+                if (a.inst_pairs) atomicAdd(&a.inst_pairs[inst], (unsigned long long)cnt);
+            }
+            base = __shfl_sync(FULL, base, 0);
+            __syncwarp();
+            unsigned long long pos = base;
+            for (uint32_t c = 0; c < MS; c += 32) {
+                const uint32_t b = hits[c >> 5];
+                if ((b >> lane) & 1u) {
+                    const unsigned long long idx = pos + __popc(b & lt);
+                    const uint32_t y = key[c + lane] & SK_NODE;
+                    if (idx < a.out_cap && !RN_BAD(y < a.n_nodes, 17, c + lane, y)) {
+                        a.out_key[idx] = prefix | (u << a.vbits) | (unsigned long long)__ldg(&a.iperm[y]);
+                        a.out_d[idx] = dist[c + lane];
+                    }
+                }
+                pos += __popc(b);
+                key[c + lane] = SK_EMPTY;
+                dist[c + lane] = INF;
+            }
+            n_slots += fill;
+            max_ball = max(max_ball, fill);
+        } else {
+            if (lane == 0)
+                a.failed[atomicAdd(&a.ctl->n_failed, 1u)] =
+                    make_uint4(si, bound, uint32_t(tau < 0xFFFFFFFFull ? tau : 0xFFFFFFFFull), fill);
+            for (uint32_t h = lane; h < MS; h += 32) {
+                key[h] = SK_EMPTY;
+                dist[h] = INF;
+            }
+        }
+        __syncwarp();
+        if (lane == 0) {
+            const long long t = clock64();
+            cyc_emit += t - t_mark;
+            t_mark = t;
+        }
+    }
+    n_scans = warp_sum64(n_scans);
+    n_arcs = warp_sum64(n_arcs);
+    n_slot_arcs = warp_sum64(n_slot_arcs);
+    if (lane == 0) {
+        atomicAdd(&a.ctl->scans, n_scans);
+        atomicAdd(&a.ctl->dirty_groups, n_scans);
+        atomicAdd(&a.ctl->round_items, n_scans);
+        atomicAdd(&a.ctl->round_arcs, n_arcs);
+        atomicAdd(&a.ctl->slot_arcs, n_slot_arcs);
+        atomicAdd(&a.ctl->slots, n_slots);
+        atomicAdd(&a.ctl->slot_lanes, n_slots);
+        atomicAdd(&a.ctl->rounds, n_rounds);
+        atomicAdd(&a.ctl->boundaries, n_bounds);
+        atomicAdd(&a.ctl->cyc_round, cyc_round);
+        atomicAdd(&a.ctl->cyc_bound, cyc_bound);
+        atomicAdd(&a.ctl->cyc_emit, cyc_emit);
+        atomicMax(&a.ctl->max_fill, max_ball);
+        atomicMax(&a.ctl->src_max_ball, max_ball);
     }
 }
 
@@ -1560,7 +1949,8 @@ static uint64_t map_for(uint64_t ball, uint64_t hcap) {
 
 static Control search_all(const DeviceGraph &g, Workspace *ws, uint32_t T, SearchArgs a,
                           uint32_t ntiles, cudaStream_t st, uint64_t *retried, uint32_t map_slots = 0,
-                          bool split = true, const std::vector<uint4> *first_ranges = nullptr) {
+                          bool split = true, const std::vector<uint4> *first_ranges = nullptr,
+                          bool timed = true) {
     // narrow blocks: one slab region each; wide blocks: two regions each
     const uint32_t grid_max = ws->sh->slab_ctas;
     const uint32_t grid_wide = std::max<uint32_t>(1, std::min<uint32_t>(grid_max / 2, uint32_t(ws->num_sms)));
@@ -1606,14 +1996,15 @@ static Control search_all(const DeviceGraph &g, Workspace *ws, uint32_t T, Searc
         }
         ws->launches++;
     };
-    RN_CUDA(cudaEventRecord(ws->evs0, st));
+    if (timed) RN_CUDA(cudaEventRecord(ws->evs0, st));
     if (ntiles) {
         launch(a, H0, ntiles);
-        ws->blocks_per_sm = H0 > SMEM_H ? 1 : T == 32 ? search_occupancy<1>() : T == 64 ? search_occupancy<2>() : search_occupancy<4>();
+        if (timed)
+            ws->blocks_per_sm = H0 > SMEM_H ? 1 : T == 32 ? search_occupancy<1>() : T == 64 ? search_occupancy<2>() : search_occupancy<4>();
     }
-    RN_CUDA(cudaEventRecord(ws->evs1, st));
+    if (timed) RN_CUDA(cudaEventRecord(ws->evs1, st));
     Control c = read_control(ws, st);
-    ws->retry_ms = 0;
+    if (timed) ws->retry_ms = 0;
     if (!c.n_failed || c.err) return c;
     // relaunch `ranges` with a map of h slots; the ranges that overflow again come back
     auto relaunch = [&](const std::vector<uint4> &ranges, uint64_t h) {
@@ -1688,6 +2079,180 @@ static Control search_all(const DeviceGraph &g, Workspace *ws, uint32_t T, Searc
         for (const uint4 &f : relaunch(ranges, h)) to_grow(f, h);
         if (c.err) return c;
     }
+    return c;
+}
+
+// ---------------------------------------------------- source search, host side ----
+
+template <uint32_t MS>
+static void launch_source(const SearchArgs &a, uint32_t grid, cudaStream_t st) {
+    constexpr uint32_t smem = src_warps(MS) * src_words(MS) * 4;
+    static std::once_flag once;
+    std::call_once(once, [&] {
+        RN_CUDA(cudaFuncSetAttribute(k_source_search<MS>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)));
+        RN_CUDA(cudaFuncSetAttribute(k_source_search<MS>, cudaFuncAttributePreferredSharedMemoryCarveout, 100));
+    });
+    k_source_search<MS><<<grid, src_warps(MS) * 32, smem, st>>>(a);
+    RN_CUDA(cudaGetLastError());
+}
+
+// One warp-search launch over `items` sources with maps of ms slots: at most three
+// blocks per SM the slab's regions stand for (two regions per SM), fewer for few sources.
+static void source_launch(uint32_t ms, SearchArgs a, uint32_t items, Workspace *ws, cudaStream_t st) {
+    a.H = ms;
+    a.hshift = 32 - log2u(ms);
+    a.max_fill = ms * 7 / 8;
+    a.gmap = nullptr;
+    const uint32_t per_block = src_warps(ms);
+    const uint32_t resident = std::max<uint32_t>(1, ws->sh->slab_ctas * SRC_BLOCKS_PER_SM / CTAS_PER_SM);
+    const uint32_t grid = std::max<uint32_t>(1, std::min<uint32_t>((items + per_block - 1) / per_block, resident));
+    switch (ms) {
+        case 1024: launch_source<1024>(a, grid, st); break;
+        case 2048: launch_source<2048>(a, grid, st); break;
+        case 4096: launch_source<4096>(a, grid, st); break;
+        case 8192: launch_source<8192>(a, grid, st); break;
+        default: fail(RN_EINTERNAL, "warp map size must be 1024 .. 8192");
+    }
+    ws->launches++;
+}
+
+// Slots a warp map of ms slots is expected to hold with room to spare below its 7/8 limit.
+static double src_fit(uint32_t ms) { return double(ms) * 7 / 8 / 1.1; }
+
+// The largest source ball expected at bound theta from the last warp search on this
+// workspace (balls grow about as the square of the radius), 0 when there was none.
+static double predicted_ball(const Workspace *ws, uint32_t theta) {
+    if (!ws->ball_theta) return 0;
+    const double r = double(theta) / double(ws->ball_theta);
+    return double(ws->ball_max) * r * r;
+}
+
+// Whether a join runs the warp-per-source search: always for tile width 1, never for
+// 32, 64 or 128 or an explicit first map; by default while the balls seen on this
+// workspace, scaled to this bound, fit the largest warp map.
+static bool use_source_search(const DeviceGraph &g, const Workspace *ws, const EngineConfig &cfg, uint32_t theta) {
+    if (g.n >= SK_NODE) return false;
+    if (cfg.tile_width == 1) return true;
+    if (cfg.tile_width || cfg.map_slots) return false;
+    return predicted_ball(ws, theta) <= src_fit(SRC_MS_MAX);
+}
+
+// First warp map: the smallest that holds the predicted ball, 2048 slots with no history.
+static uint32_t source_first_map(const Workspace *ws, uint32_t theta) {
+    const double b = predicted_ball(ws, theta);
+    if (b <= 0) return 2048;
+    for (uint32_t ms = SRC_MS_MIN; ms <= SRC_MS_MAX; ms *= 2)
+        if (b <= src_fit(ms)) return ms;
+    return SRC_MS_MAX;
+}
+
+// Search sources 0 .. nsrc-1 with warp maps of ms0 slots, then the sources whose ball
+// overflowed: with the smallest warp map their estimated ball fits (fill * (bound /
+// tau)^2, as for tiles), and past the largest warp map with the tile search of width T,
+// as ranges of consecutive sources of one query (inst_first: the first source of every
+// query, empty for a single query).  Remembers the largest ball seen, for the next
+// query's choice of path and map.
+static Control source_search_all(const DeviceGraph &g, Workspace *ws, SearchArgs a, uint32_t nsrc, uint32_t ms0,
+                                 uint32_t T, uint32_t theta, const std::vector<uint32_t> &inst_first,
+                                 cudaStream_t st, uint64_t *retried) {
+    a.n_nodes = g.n;
+    a.n_arcs = g.arcs;
+    a.range_list = nullptr;
+    a.ntiles = nsrc;
+    if (nsrc && (!a.src || (!a.sbits && !a.inst_sbits) || !a.out_key || !a.out_d || !a.row_ptr || !a.adj || !a.ctl))
+        fail(RN_EINTERNAL, "source search without its buffers");
+    ensure_ranges(&ws->failed, &ws->failed_cap, std::max<uint32_t>(nsrc, 1));
+    ensure_ranges(&ws->failed2, &ws->failed2_cap, std::max<uint32_t>(nsrc, 1));
+    a.failed = ws->failed;
+    RN_CUDA(cudaEventRecord(ws->evs0, st));
+    if (nsrc) source_launch(ms0, a, nsrc, ws, st);
+    RN_CUDA(cudaEventRecord(ws->evs1, st));
+    Control c = read_control(ws, st);
+    ws->retry_ms = 0;
+    ws->blocks_per_sm = int(SRC_BLOCKS_PER_SM);
+    double ball = c.src_max_ball;
+    auto learn = [&] {
+        if (nsrc && ball >= 64) {  // a handful of nodes says little about the growth
+            ws->ball_theta = std::max<uint32_t>(theta, 1);
+            ws->ball_max = ball;
+        }
+    };
+    if (!c.n_failed || c.err || c.check[0]) {
+        learn();
+        return c;
+    }
+    auto estimate = [&](const uint4 &f) {
+        const double r = double(f.y) / double(std::max<uint32_t>(f.z, 1));
+        const double e = double(std::max<uint32_t>(f.w, 1)) * std::min(r * r, 1e12);
+        return std::min<double>(std::max<double>(e, f.w), double(g.n));
+    };
+    std::map<uint32_t, std::vector<uint4>> grow;  // warp map -> sources (index, bound, est, -)
+    std::vector<uint4> to_tiles;
+    double tile_est = 0;
+    auto route = [&](const uint4 &f, uint32_t failed_at) {
+        const double e = estimate(f);
+        ball = std::max(ball, e);
+        uint32_t ms = failed_at * 2;
+        while (ms <= SRC_MS_MAX && e > src_fit(ms)) ms *= 2;
+        if (ms <= SRC_MS_MAX) {
+            grow[ms].push_back(make_uint4(f.x, 0, 0, 0));
+        } else {
+            to_tiles.push_back(f);
+            tile_est = std::max(tile_est, e);
+        }
+    };
+    for (const uint4 &f : read_ranges(ws->failed, c.n_failed, st)) route(f, ms0);
+    while (!grow.empty()) {
+        const uint32_t ms = grow.begin()->first;
+        std::vector<uint4> items;
+        items.swap(grow.begin()->second);
+        grow.erase(grow.begin());
+        const uint32_t n = uint32_t(items.size());
+        RN_CUDA(cudaMemcpyAsync(ws->failed2, items.data(), size_t(n) * 16, cudaMemcpyHostToDevice, st));
+        RN_CUDA(cudaMemsetAsync(&ws->ctl->tile_next, 0, 8, st));  // tile_next, n_failed
+        SearchArgs r = a;
+        r.range_list = ws->failed2;
+        r.ntiles = n;
+        source_launch(ms, r, n, ws, st);
+        *retried += n;
+        c = read_control(ws, st);
+        if (c.err || c.check[0]) return c;
+        ball = std::max<double>(ball, c.src_max_ball);
+        for (const uint4 &f : read_ranges(ws->failed, c.n_failed, st)) route(f, ms);
+    }
+    if (!to_tiles.empty()) {
+        // consecutive sources of one query become ranges of up to T sources each
+        std::sort(to_tiles.begin(), to_tiles.end(), [](const uint4 &x, const uint4 &y) { return x.x < y.x; });
+        auto query_of = [&](uint32_t si) {
+            return inst_first.empty()
+                       ? 0u
+                       : uint32_t(std::upper_bound(inst_first.begin(), inst_first.end(), si) - inst_first.begin());
+        };
+        std::vector<uint4> ranges;
+        for (const uint4 &f : to_tiles) {
+            if (!ranges.empty()) {
+                uint4 &b = ranges.back();
+                if (b.x + b.y == f.x && b.y < T && query_of(b.x) == query_of(f.x)) {
+                    b.y++;
+                    continue;
+                }
+            }
+            ranges.push_back(make_uint4(f.x, 1, 0, 0));
+        }
+        RN_CUDA(cudaMemsetAsync(&ws->ctl->tile_next, 0, 8, st));
+        SearchArgs t = a;
+        t.tile_src = T;
+        uint64_t want = uint64_t(tile_est) * 2;  // the union of a few neighbours' balls
+        c = search_all(g, ws, T, t, 0, st, retried, uint32_t(std::min<uint64_t>(want, 1u << 30)), true, &ranges,
+                       false);
+        *retried += ranges.size();
+    }
+    RN_CUDA(cudaEventRecord(ws->evr, st));
+    RN_CUDA(cudaEventSynchronize(ws->evr));
+    float ms = 0;
+    RN_CUDA(cudaEventElapsedTime(&ms, ws->evs1, ws->evr));
+    ws->retry_ms = ms;
+    learn();
     return c;
 }
 
@@ -1789,13 +2354,14 @@ void run_join(const DeviceGraph &g, Workspace *ws, const EngineConfig &cfg, uint
     cudaStream_t st = (cudaStream_t)stream;
     if (theta == RN_INF) theta = RN_THETA_MAX;
     if (theta > RN_THETA_MAX) fail(RN_EINVAL, "theta must be <= 2^31 or RN_INF");
-    const uint32_t T = cfg.tile_width ? cfg.tile_width : 32;
-    if (T != 32 && T != 64 && T != 128) fail(RN_EINVAL, "tile width must be 32, 64 or 128");
+    const uint32_t T = cfg.tile_width > 1 ? cfg.tile_width : 32;  // the tile search's width
+    if (T != 32 && T != 64 && T != 128) fail(RN_EINVAL, "tile width must be 1, 32, 64 or 128");
     const uint32_t delta = choose_delta(cfg, median_w);
     std::lock_guard<std::mutex> device_lock(ws->sh->mu);
     Range range("rn.join");
     *stats = rn_query_stats{};
-    stats->tile_width = T;
+    const bool by_source = use_source_search(g, ws, cfg, theta);
+    stats->tile_width = by_source ? 1 : T;
     stats->delta = delta;
     stats->theta_final = theta;
     ws->launches = 0;
@@ -1812,10 +2378,12 @@ void run_join(const DeviceGraph &g, Workspace *ws, const EngineConfig &cfg, uint
         tile_src = uint32_t(std::min<uint64_t>(T, (nR + waves * grid_max - 1) / (waves * grid_max)));
         if (cfg.tile_src) tile_src = std::min(cfg.tile_src, T);
     }
+    if (by_source) tile_src = 1;
     const uint32_t ntiles = (nR + tile_src - 1) / tile_src;
     ensure_ranges(&ws->failed, &ws->failed_cap, std::max<uint32_t>(ntiles, 1));
     ensure_ranges(&ws->failed2, &ws->failed2_cap, std::max<uint32_t>(ntiles, 1));
     ensure_pairs(ws, std::max<uint64_t>(ws->pair_cap, uint64_t(nR) * 64));
+    const uint32_t ms0 = by_source ? source_first_map(ws, theta) : 0;
 
     const uint32_t vbits = bits_for(g.n);
     SearchArgs a{};
@@ -1834,10 +2402,15 @@ void run_join(const DeviceGraph &g, Workspace *ws, const EngineConfig &cfg, uint
     a.out_d = ws->valA;
     a.out_cap = ws->pair_cap;
     uint64_t retried = 0;
+    const std::vector<uint32_t> one_query;
+    auto search_pass = [&] {
+        return by_source ? source_search_all(g, ws, a, nR, ms0, T, theta, one_query, st, &retried)
+                         : search_all(g, ws, T, a, ntiles, st, &retried, cfg.map_slots);
+    };
     Control c;
     {
         Range r("rn.search");
-        c = search_all(g, ws, T, a, ntiles, st, &retried, cfg.map_slots);
+        c = search_pass();
     }
     check_control(c);
     if (c.pairs > ws->pair_cap) {
@@ -1848,7 +2421,7 @@ void run_join(const DeviceGraph &g, Workspace *ws, const EngineConfig &cfg, uint
         a.out_key = ws->keyA;
         a.out_d = ws->valA;
         a.out_cap = ws->pair_cap;
-        c = search_all(g, ws, T, a, ntiles, st, &retried, cfg.map_slots);
+        c = search_pass();
         check_control(c);
         if (c.pairs > ws->pair_cap) fail(RN_EINTERNAL, "pair count changed between passes");
     }
@@ -1889,6 +2462,7 @@ void run_join(const DeviceGraph &g, Workspace *ws, const EngineConfig &cfg, uint
     stats->max_ball = c.max_fill;
     stats->dirty_groups = c.dirty_groups;
     stats->retry_ms = ws->retry_ms;
+    stats->slot_lanes = c.slot_lanes;
 }
 
 // ------------------------------------------------ several joins, one graph ----
@@ -1921,15 +2495,18 @@ void run_join_multi(const DeviceGraph &g, Workspace *ws, const EngineConfig &cfg
     cudaStream_t st = (cudaStream_t)stream;
     const uint32_t nq = uint32_t(R.size());
     if (nq == 0) fail(RN_EINVAL, "no queries");
-    const uint32_t T = cfg.tile_width ? cfg.tile_width : 32;
-    if (T != 32 && T != 64 && T != 128) fail(RN_EINVAL, "tile width must be 32, 64 or 128");
+    const uint32_t T = cfg.tile_width > 1 ? cfg.tile_width : 32;  // the tile search's width
+    if (T != 32 && T != 64 && T != 128) fail(RN_EINVAL, "tile width must be 1, 32, 64 or 128");
     const uint32_t vbits = bits_for(g.n), qbits = bits_for(nq);
     if (2 * vbits + qbits > 64) fail(RN_EINVAL, "too many queries for this graph in one search");
     const uint32_t delta = choose_delta(cfg, median_w);
     std::lock_guard<std::mutex> device_lock(ws->sh->mu);
     Range range("rn.join_many");
     *stats = rn_query_stats{};
-    stats->tile_width = T;
+    uint32_t max_bound = 0;
+    for (uint32_t t : theta) max_bound = std::max(max_bound, std::min(t, RN_THETA_MAX));
+    const bool by_source = use_source_search(g, ws, cfg, max_bound);
+    stats->tile_width = by_source ? 1 : T;
     stats->delta = delta;
     ws->launches = 0;
     RN_CUDA(cudaEventRecord(ws->ev0, st));
@@ -1958,6 +2535,8 @@ void run_join_multi(const DeviceGraph &g, Workspace *ws, const EngineConfig &cfg
         tile_src = uint32_t(std::min<uint64_t>(T, (total + waves * grid_max - 1) / (waves * grid_max)));
         if (cfg.tile_src) tile_src = std::min(cfg.tile_src, T);
     }
+    if (by_source) tile_src = 1;
+    const uint32_t ms0 = by_source ? source_first_map(ws, max_bound) : 0;
     std::vector<uint4> ranges;
     for (uint32_t i = 0; i < nq; i++)
         for (uint32_t j = 0; j < nR[i]; j += tile_src)
@@ -2031,7 +2610,11 @@ void run_join_multi(const DeviceGraph &g, Workspace *ws, const EngineConfig &cfg
     a.inst_sbits = ws->mq_sptr;
     a.inst_bound = ws->mq_bound;
     uint64_t retried = 0;
-    Control c = search_all(g, ws, T, a, 0, st, &retried, cfg.map_slots, true, &ranges);
+    auto search_pass = [&] {
+        return by_source ? source_search_all(g, ws, a, total, ms0, T, max_bound, first, st, &retried)
+                         : search_all(g, ws, T, a, 0, st, &retried, cfg.map_slots, true, &ranges);
+    };
+    Control c = search_pass();
     check_control(c);
     if (c.pairs > ws->pair_cap) {
         // the pair buffer was too small: grow it and search again (same result)
@@ -2041,7 +2624,7 @@ void run_join_multi(const DeviceGraph &g, Workspace *ws, const EngineConfig &cfg
         a.out_key = ws->keyA;
         a.out_d = ws->valA;
         a.out_cap = ws->pair_cap;
-        c = search_all(g, ws, T, a, 0, st, &retried, cfg.map_slots, true, &ranges);
+        c = search_pass();
         check_control(c);
         if (c.pairs > ws->pair_cap) fail(RN_EINTERNAL, "pair count changed between passes");
     }
@@ -2078,6 +2661,7 @@ void run_join_multi(const DeviceGraph &g, Workspace *ws, const EngineConfig &cfg
     stats->retry_ms = ws->retry_ms;
     stats->rounds = c.rounds;
     stats->max_ball = c.max_fill;
+    stats->slot_lanes = c.slot_lanes;
 }
 
 // ------------------------------------------------- join without allocation ----
@@ -2346,7 +2930,7 @@ void run_kcp(const DeviceGraph &g, Workspace *ws, const EngineConfig &cfg, uint3
     if (k == 0) fail(RN_EINVAL, "k must be >= 1");
     if (theta == RN_INF) theta = RN_THETA_MAX;
     if (theta > RN_THETA_MAX) fail(RN_EINVAL, "theta must be <= 2^31 or RN_INF");
-    const uint32_t T = cfg.tile_width ? cfg.tile_width : 32;
+    const uint32_t T = cfg.tile_width > 1 ? cfg.tile_width : 32;
     if (T != 32 && T != 64 && T != 128) fail(RN_EINVAL, "tile width must be 32, 64 or 128");
     const uint32_t delta = choose_delta(cfg, median_w);
     std::lock_guard<std::mutex> device_lock(ws->sh->mu);

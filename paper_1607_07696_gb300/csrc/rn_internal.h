@@ -74,7 +74,7 @@ void workspace_destroy(Workspace *ws);
 uint64_t workspace_bytes(const Workspace *ws);
 
 struct EngineConfig {
-    uint32_t tile_width = 32;
+    uint32_t tile_width = 0;  // 0: choose; 1: one warp per source; 32, 64, 128: tiles
     uint32_t tile_src = 0;  // sources per tile; 0: spread over whole waves of blocks
     uint32_t delta = 0;     // 0: derive from the weights
     uint32_t map_slots = 0; // first slot map: 0 / 8192 narrow, 16384 wide, larger: global

@@ -263,7 +263,7 @@ Server *server_create(const rn_graph *g, uint64_t slab_bytes, uint32_t workers, 
     }
     s->device = g->device;
     check(cudaSetDevice(g->device), "cudaSetDevice");
-    s->tile_width = s->cfg.tile_width ? s->cfg.tile_width : 32;
+    s->tile_width = s->cfg.tile_width > 1 ? s->cfg.tile_width : 32;
     int sms = 0;
     check(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, g->device), "cudaDeviceGetAttribute");
     // by default a request may spread over one block per SM: its sources then sit a few to

@@ -64,7 +64,7 @@ class rn_query_stats(C.Structure):
                 ("boundaries", C.c_uint64), ("cycles_rounds", C.c_uint64),
                 ("cycles_boundaries", C.c_uint64), ("cycles_emission", C.c_uint64),
                 ("cycles_step_a", C.c_uint64), ("round_arcs", C.c_uint64), ("max_ball", C.c_uint64),
-                ("retry_ms", C.c_double), ("dirty_groups", C.c_uint64)]
+                ("retry_ms", C.c_double), ("dirty_groups", C.c_uint64), ("slot_lanes", C.c_uint64)]
 
 
 class rn_query(C.Structure):

@@ -26,11 +26,16 @@ done = 0
 for seed in range(4):
     e = I.road_graph(3000 + 7000 * seed, int(2.77 * (3000 + 7000 * seed)), 300 + seed)
     og = o.graph(e.n, e.src, e.dst, e.w)
-    for T in (32, 64, 128):
+    for T in (1, 32, 64, 128):  # 1: one warp per source
         g = rn.rn_graph_load(e.src, e.dst, e.w, e.n, cfg={"tile_width": T})
         R, S = I.disjoint_sets(e.n, 400, 600, 400 + seed)
         for theta in (20_000, rn.RN_INF):  # unbounded: every tile overflows and is retried
             assert same(rn.rn_distance_join(g, R, S, theta), og.join(R, S, min(theta, rn.RN_THETA_MAX)))
+            done += 1
+        if T == 1:  # several joins in one warp search, then in the tile search
+            qs = [(R[:150], S[:200], 20_000), (R[150:], S[200:], 9_000), (R[150:170], S, rn.RN_INF)]
+            for got, (r, s, th) in zip(rn.rn_join_many(g, qs), qs):
+                assert same(got, og.join(r, s, min(th, rn.RN_THETA_MAX)))
             done += 1
         assert same(rn.rn_kcp(g, R, S, 300), og.kcp(R, S, 300)); done += 1
         best = pins.least_weights(e)
@@ -62,4 +67,4 @@ def test_checked_build_runs_clean():
     r = subprocess.run([sys.executable, "-c", "ROOT = %r\n" % ROOT + SCRIPT], env=env, capture_output=True,
                        text=True, timeout=1200)
     assert r.returncode == 0, (r.stdout + r.stderr)[-4000:]
-    assert "checked 48" in r.stdout
+    assert "checked 68" in r.stdout

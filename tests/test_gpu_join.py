@@ -54,7 +54,7 @@ def load(rn, e, flags=None, cfg=None):
     return rn.rn_graph_load(e.src, e.dst, e.w, e.n, flags=flags, cfg=cfg)
 
 
-@pytest.mark.parametrize("T", [32, 64, 128])
+@pytest.mark.parametrize("T", [1, 32, 64, 128])
 def test_grid4096_full(rn, oracle, T):
     w = I.c1_grid_join()
     e = w.graph
@@ -64,6 +64,7 @@ def test_grid4096_full(rn, oracle, T):
     assert_same(rn.rn_distance_join(g, w.R, w.S, w.theta), ref, f"grid T={T} host")
     st = rn.rn_last_query_stats()
     assert st["pairs"] == len(ref) and st["tile_width"] == T
+    assert st["slot_lanes"] == (st["slots"] if T == 1 else None) or T > 1
 
 
 @pytest.mark.parametrize("T,ts", [(32, 1), (32, 7), (64, 33), (128, 100), (32, 32)])
@@ -91,7 +92,7 @@ def test_random_small(rn, oracle, seed):
     directed = seed % 4 == 3
     reorder = seed % 5 != 4
     flags = (0 if directed else rn.RN_UNDIRECTED) | (rn.RN_REORDER if reorder else 0)
-    T = [32, 64, 128][seed % 3]
+    T = [1, 32, 64, 128][seed % 4]
     cfg = {"tile_width": T, "delta": int(rng.choice([0, 1, 50, 1 << 20]))}
     g = load(rn, e, flags, cfg)
     og = oracle.graph(n, e.src, e.dst, e.w, undirected=not directed)
@@ -233,3 +234,31 @@ def test_first_map_size(rn, oracle, T, slots):
         assert st["retried_tiles"] > 0
     with pytest.raises(rn.RNError):
         load(rn, e, cfg={"map_slots": 5000})
+
+
+def test_source_search_routes(rn, oracle):
+    """The warp-per-source search: sources whose ball outgrows a 2048-slot warp map are
+    searched again with a larger warp map, those past the largest (8192) with the tile
+    search; the default path follows the balls met so far."""
+    e = I.road_graph(40_000, 110_800, 61)
+    og = oracle.graph(e.n, e.src, e.dst, e.w)
+    R, S = I.disjoint_sets(e.n, 300, 3000, 62)
+    D = np.sort(og.sssp(int(R[0]))[0])
+    for ball, routed in ((3000, "warp"), (20_000, "tiles")):
+        theta = int(D[ball])
+        g = load(rn, e, cfg={"tile_width": 1})
+        assert_same(dev_join(rn, g, R, S, theta), og.join(R, S, theta), f"ball ~{ball}")
+        st = rn.rn_last_query_stats()
+        assert st["tile_width"] == 1 and st["retried_tiles"] > 0, st
+        assert st["max_ball"] > 1792
+    # default path: an unbounded query meets balls of the whole graph, so the same bound
+    # goes to tiles next time, while a small one stays with the warp search
+    g = load(rn, e)
+    ref = og.join(R[:40], S, rn.RN_THETA_MAX)
+    for i in range(2):
+        assert_same(dev_join(rn, g, R[:40], S, rn.RN_INF), ref, f"unbounded {i}")
+        assert rn.rn_last_query_stats()["tile_width"] == (1 if i == 0 else 32)
+    theta = int(D[500])
+    assert_same(dev_join(rn, g, R, S, theta), og.join(R, S, theta), "small after unbounded")
+    st = rn.rn_last_query_stats()
+    assert st["tile_width"] == 1 and st["slot_lanes"] == st["slots"]
