@@ -95,7 +95,8 @@ typedef struct {
                              run tiles, 32 wide unless set) */
     uint32_t tile_sources;/* sources per tile, <= tile_width; 0 spreads R over whole
                              waves of resident blocks */
-    uint32_t delta;       /* bucket width of the delta-stepping search, in weight units */
+    uint32_t delta;       /* bucket width of the delta-stepping search, in weight units;
+                             0: 16 median arc weights for the warp search, 4 for tiles */
     uint32_t leaf_size;   /* recursive-bisection leaf size used by RN_REORDER */
     float alpha;          /* smoothing parameter of the bisection (Eq. 1-2), in [0, 1];
                              negative selects the default, 0.5 */

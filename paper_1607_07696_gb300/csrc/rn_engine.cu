@@ -207,7 +207,7 @@ struct Control {
     uint32_t check[4];  // first failed device-side check: code, index, value
     unsigned long long slot_lanes;  // sum over tiles of slots times the tile's lanes
     uint32_t src_max_ball;          // largest ball of a source the warp search completed
-    uint32_t pad_;
+    uint32_t max_seg;               // most pairs one source emitted in the warp search
 };
 
 // Record the first failed device-side check (the access it guarded is skipped).
@@ -291,6 +291,11 @@ struct Workspace {
     // whose map overflowed) and its bound: predicts the next query's balls
     double ball_max = 0;
     uint32_t ball_theta = 0;
+    // warp search: per source its first pair and pair count; whether the last search
+    // handed sources to the tile search (their pairs are then not in segments)
+    uint2 *seg = nullptr;
+    uint32_t seg_cap = 0;
+    bool src_tiles = false;
     uint32_t launches = 0;  // kernels launched by the current query
     int blocks_per_sm = 0;  // occupancy of the shared-map search kernel
     uint64_t bytes = 0;
@@ -355,6 +360,7 @@ void workspace_destroy(Workspace *ws) {
                     (void *)ws->mq_soff, (void *)ws->mq_sptr, (void *)ws->mq_counts})
         device_free(p);
     device_free(ws->own_gmap);
+    device_free(ws->seg);
     if (ws->own_sh) {
         device_free(ws->own_sh->gretry);
         delete ws->own_sh;
@@ -399,9 +405,10 @@ static void grow(Workspace *ws, T **p, uint64_t *cap, uint64_t want, uint64_t el
 // Mark one set: reject ids >= n and ids already marked (a repeat, or an id of R met
 // again in S: the sets must be disjoint), and set the membership bit of the internal
 // id.
+// set_bits marks internal ids, or original ids with by_orig.
 __global__ void k_mark_set(const uint32_t *__restrict__ ids, uint32_t cnt, uint32_t n,
                            const uint32_t *__restrict__ perm, uint32_t *used_bits,
-                           uint32_t *set_bits, Control *ctl) {
+                           uint32_t *set_bits, Control *ctl, bool by_orig) {
     for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < cnt; i += gridDim.x * blockDim.x) {
         uint32_t id = ids[i];
         if (id >= n) {
@@ -414,7 +421,7 @@ __global__ void k_mark_set(const uint32_t *__restrict__ ids, uint32_t cnt, uint3
             atomicOr(&ctl->err, 2u);
             continue;
         }
-        uint32_t in = perm[id];
+        const uint32_t in = by_orig ? id : perm[id];
         atomicOr(&set_bits[in >> 5], 1u << (in & 31));
     }
 }
@@ -531,6 +538,8 @@ struct SearchArgs {
     uint32_t inst_count, inst_shift;
     const uint32_t *const *inst_sbits;
     const uint32_t *inst_bound;
+    // warp search: seg[si] = (first pair, pair count) of source si, or null
+    uint2 *seg;
 };
 
 // What a block needs to know about the tile it searches.
@@ -1290,7 +1299,7 @@ __global__ void __launch_bounds__(src_warps(MS) * 32, SRC_BLOCKS_PER_SM) k_sourc
     unsigned long long n_scans = 0, n_arcs = 0, n_slot_arcs = 0;
     unsigned long long n_rounds = 0, n_bounds = 0, n_slots = 0;
     unsigned long long cyc_round = 0, cyc_bound = 0, cyc_emit = 0;
-    uint32_t max_ball = 0;
+    uint32_t max_ball = 0, max_seg = 0;
     long long t_mark = clock64();
 
     for (;;) {
@@ -1528,6 +1537,8 @@ __global__ void __launch_bounds__(src_warps(MS) * 32, SRC_BLOCKS_PER_SM) k_sourc
                 base = atomicAdd(&a.ctl->pairs, (unsigned long long)cnt);
                 if (a.inst_pairs) atomicAdd(&a.inst_pairs[inst], (unsigned long long)cnt);
             }
+            if (lane == 0 && a.seg) a.seg[si] = make_uint2(uint32_t(base), cnt);
+            max_seg = max(max_seg, cnt);
             base = __shfl_sync(FULL, base, 0);
             __syncwarp();
             unsigned long long pos = base;
@@ -1581,8 +1592,105 @@ __global__ void __launch_bounds__(src_warps(MS) * 32, SRC_BLOCKS_PER_SM) k_sourc
         atomicAdd(&a.ctl->cyc_emit, cyc_emit);
         atomicMax(&a.ctl->max_fill, max_ball);
         atomicMax(&a.ctl->src_max_ball, max_ball);
+        atomicMax(&a.ctl->max_seg, max_seg);
     }
 }
+
+// ------------------------------------------------- order without a sort ----
+// The warp search writes every source's pairs contiguously (seg[si] = first pair, count);
+// with the sources in increasing original id, the (u, v) order is the sources' segments
+// one after another, each sorted by v.  So a join's canonical order (Section 4's result
+// sorted by (u, v)) needs a scan of the counts and one placement pass, in which a warp
+// sorts one segment of up to 256 pairs in registers (bitonic network) and writes it.
+
+__global__ void k_seg_counts(const uint2 *__restrict__ seg, uint32_t n, uint32_t *cnt) {
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) cnt[i] = seg[i].y;
+}
+
+// Ascending bitonic sort of the warp's 32 E values, element lane * E + e in x[e].
+template <int E>
+__device__ __forceinline__ void warp_bitonic(unsigned long long (&x)[E], uint32_t lane) {
+#pragma unroll
+    for (uint32_t k = 2; k <= 32u * E; k <<= 1) {
+#pragma unroll
+        for (uint32_t j = k >> 1; j > 0; j >>= 1) {
+            if (j >= uint32_t(E)) {  // partner in lane ^ (j / E), same register
+                const uint32_t lj = j / E;
+                const bool lower = (lane & lj) == 0;
+#pragma unroll
+                for (int e = 0; e < E; e++) {
+                    const unsigned long long p = __shfl_xor_sync(FULL, x[e], lj);
+                    const bool up = ((lane * E + e) & k) == 0;
+                    x[e] = (lower == up) ? (x[e] < p ? x[e] : p) : (x[e] < p ? p : x[e]);
+                }
+            } else {  // partner in this lane, register e ^ j
+#pragma unroll
+                for (int e = 0; e < E; e++) {
+                    if ((e & j) == 0) {
+                        const bool up = ((lane * E + e) & k) == 0;
+                        const unsigned long long lo = x[e], hi = x[e ^ j];
+                        if ((lo > hi) == up) {
+                            x[e] = hi;
+                            x[e ^ j] = lo;
+                        }
+                    }
+                }
+            }
+        }
+    }
+}
+
+template <int E>
+__device__ __forceinline__ void place_segment(uint32_t lane, uint32_t base, uint32_t cnt, uint32_t o, uint32_t u,
+                                              const unsigned long long *__restrict__ key,
+                                              const uint32_t *__restrict__ val, unsigned long long vmask,
+                                              uint32_t *out_u, uint32_t *out_v, uint32_t *out_d) {
+    unsigned long long x[E];
+#pragma unroll
+    for (int e = 0; e < E; e++) {
+        const uint32_t i = lane * E + e;
+        x[e] = i < cnt ? ((key[base + i] & vmask) << 32) | val[base + i] : ~0ull;  // v, then d
+    }
+    warp_bitonic<E>(x, lane);
+#pragma unroll
+    for (int e = 0; e < E; e++) {
+        const uint32_t i = lane * E + e;
+        if (i < cnt) {
+            out_u[o + i] = u;
+            out_v[o + i] = uint32_t(x[e] >> 32);
+            out_d[o + i] = uint32_t(x[e]);
+        }
+    }
+}
+
+// One warp per source: its segment, sorted by v, at its offset off[si] of the result.
+__global__ void k_place(const uint2 *__restrict__ seg, const uint32_t *__restrict__ off, uint32_t n,
+                        const unsigned long long *__restrict__ key, const uint32_t *__restrict__ val, uint32_t vbits,
+                        uint32_t umask, uint32_t *out_u, uint32_t *out_v, uint32_t *out_d) {
+    const uint32_t lane = threadIdx.x & 31;
+    const uint32_t warps = gridDim.x * (blockDim.x / 32);
+    const unsigned long long vmask = (1ull << vbits) - 1;
+    for (uint32_t si = blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5); si < n; si += warps) {
+        const uint2 sg = seg[si];
+        const uint32_t cnt = sg.y;
+        if (!cnt) continue;
+        const uint32_t u = uint32_t(key[sg.x] >> vbits) & umask;
+        const uint32_t o = off[si];
+        if (cnt <= 32) place_segment<1>(lane, sg.x, cnt, o, u, key, val, vmask, out_u, out_v, out_d);
+        else if (cnt <= 64) place_segment<2>(lane, sg.x, cnt, o, u, key, val, vmask, out_u, out_v, out_d);
+        else if (cnt <= 128) place_segment<4>(lane, sg.x, cnt, o, u, key, val, vmask, out_u, out_v, out_d);
+        else place_segment<8>(lane, sg.x, cnt, o, u, key, val, vmask, out_u, out_v, out_d);
+    }
+}
+
+// Replace the original ids of list[0, min(cap, r_count)) by internal ids.
+__global__ void k_to_internal(uint32_t *list, uint32_t cap, const uint32_t *__restrict__ perm,
+                              const Control *__restrict__ ctl) {
+    const uint32_t n = min(cap, ctl->r_count);
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) list[i] = perm[list[i]];
+}
+
+constexpr uint32_t PLACE_MAX = 256;  // longest segment k_place sorts
 
 // ------------------------------------------------------------- radix sort ----
 // LSD radix sort of (64-bit key, 32-bit value) records, 8 bits per pass.  Stable within
@@ -2096,6 +2204,25 @@ static void launch_source(const SearchArgs &a, uint32_t grid, cudaStream_t st) {
     RN_CUDA(cudaGetLastError());
 }
 
+template <uint32_t MS>
+static int source_occupancy() {
+    int b = 0;
+    RN_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_source_search<MS>, src_warps(MS) * 32,
+                                                          src_warps(MS) * src_words(MS) * 4));
+    return b;
+}
+
+// Resident warp-search blocks per SM with maps of ms slots (after the first launch set
+// the kernel's shared-memory limit).
+static int source_blocks_per_sm(uint32_t ms) {
+    switch (ms) {
+        case 1024: return source_occupancy<1024>();
+        case 2048: return source_occupancy<2048>();
+        case 4096: return source_occupancy<4096>();
+        default: return source_occupancy<8192>();
+    }
+}
+
 // One warp-search launch over `items` sources with maps of ms slots: at most three
 // blocks per SM the slab's regions stand for (two regions per SM), fewer for few sources.
 static void source_launch(uint32_t ms, SearchArgs a, uint32_t items, Workspace *ws, cudaStream_t st) {
@@ -2169,7 +2296,8 @@ static Control source_search_all(const DeviceGraph &g, Workspace *ws, SearchArgs
     RN_CUDA(cudaEventRecord(ws->evs1, st));
     Control c = read_control(ws, st);
     ws->retry_ms = 0;
-    ws->blocks_per_sm = int(SRC_BLOCKS_PER_SM);
+    ws->src_tiles = false;
+    ws->blocks_per_sm = nsrc ? source_blocks_per_sm(ms0) : 0;
     double ball = c.src_max_ball;
     auto learn = [&] {
         if (nsrc && ball >= 64) {  // a handful of nodes says little about the growth
@@ -2220,6 +2348,7 @@ static Control source_search_all(const DeviceGraph &g, Workspace *ws, SearchArgs
         ball = std::max<double>(ball, c.src_max_ball);
         for (const uint4 &f : read_ranges(ws->failed, c.n_failed, st)) route(f, ms);
     }
+    ws->src_tiles = !to_tiles.empty();
     if (!to_tiles.empty()) {
         // consecutive sources of one query become ranges of up to T sources each
         std::sort(to_tiles.begin(), to_tiles.end(), [](const uint4 &x, const uint4 &y) { return x.x < y.x; });
@@ -2256,12 +2385,49 @@ static Control source_search_all(const DeviceGraph &g, Workspace *ws, SearchArgs
     return c;
 }
 
-// Bucket width: four median arc weights unless configured.  Wider buckets mean fewer
-// rounds (each round is a few memory round trips for the whole block) at the price of
-// some relaxations redone inside a bucket.
-static uint32_t choose_delta(const EngineConfig &cfg, uint32_t median_w) {
+// Per-source segments of the warp search for nsrc sources, cleared on the stream.
+static uint2 *ensure_segments(Workspace *ws, uint32_t nsrc, cudaStream_t st) {
+    if (!ws->seg || ws->seg_cap < nsrc) {
+        device_free(ws->seg);
+        ws->seg = nullptr;
+        ws->seg_cap = std::max<uint32_t>(nsrc, 1024);
+        ws->seg = (uint2 *)device_alloc(size_t(ws->seg_cap) * 8);
+    }
+    if (nsrc) RN_CUDA(cudaMemsetAsync(ws->seg, 0, size_t(nsrc) * 8, st));
+    return ws->seg;
+}
+
+// Whether the pairs of the last warp search can be ordered by placement (every source's
+// pairs in one segment of at most PLACE_MAX, all written).
+static bool can_place(const Workspace *ws, const Control &c) {
+    return !ws->src_tiles && c.max_seg <= PLACE_MAX && c.pairs <= ws->pair_cap && c.pairs < 0xFFFFFFFFull;
+}
+
+// The canonical order by placement: offsets from the segments' counts (source order is
+// the output order), then one warp per segment.
+static void place_pairs(Workspace *ws, uint32_t nsrc, uint32_t vbits, uint32_t umask, rn_dpairs *out,
+                        cudaStream_t st) {
+    if (!nsrc) return;
+    grow(ws, &ws->hist, &ws->hist_cap, hist_words(nsrc), 4);
+    const uint32_t nb = std::min<uint32_t>((nsrc + 255) / 256, 4096);
+    k_seg_counts<<<nb, 256, 0, st>>>(ws->seg, nsrc, ws->hist);
+    ws->launches += 1 + scan_hist(ws->hist, nsrc, st);
+    k_place<<<std::min<uint32_t>((nsrc + 7) / 8, 8192), 256, 0, st>>>(ws->seg, ws->hist, nsrc, ws->keyA, ws->valA,
+                                                                       vbits, umask, out->u, out->v, out->d);
+    ws->launches++;
+    RN_CUDA(cudaGetLastError());
+}
+
+// Bucket width unless configured: four median arc weights for the tile search, sixteen
+// for the warp search.  Wider buckets mean fewer rounds and bucket boundaries at the price
+// of some relaxations redone inside a bucket; a warp's boundary is a pass over its whole
+// map, so the warp search gains from wider buckets (measured on road-like graphs: 4, 8,
+// 16, 32 medians gave 1.51, 1.43, 1.42, 1.55 ms on the 264k join and 3.31, 2.82, 2.69,
+// 2.64 ms on the 1.07M one).
+static uint32_t choose_delta(const EngineConfig &cfg, uint32_t median_w, bool by_source = false) {
     if (cfg.delta) return cfg.delta;
-    return std::max<uint32_t>(1, 4 * median_w);
+    const uint64_t d = uint64_t(by_source ? 16 : 4) * median_w;
+    return uint32_t(std::max<uint64_t>(1, std::min<uint64_t>(d, RN_THETA_MAX)));
 }
 
 static void ensure_u32(uint32_t **p, uint32_t *cap, uint32_t want) {
@@ -2320,23 +2486,29 @@ void workspace_reserve(Workspace *ws, uint32_t max_r, uint64_t max_pairs) {
 
 // a2: validate R and S on the device, build the S membership bitmap and the list of R
 // nodes in increasing internal id (so consecutive sources are graph neighbours).
+// by_orig: R in increasing original id instead (each source alone, so the order of
+// sources need not follow the graph; it is the output order).
 static void prep_sets(const DeviceGraph &g, Workspace *ws, const uint32_t *dR, uint32_t nR,
-                      const uint32_t *dS, uint32_t nS, cudaStream_t st) {
+                      const uint32_t *dS, uint32_t nS, cudaStream_t st, bool by_orig = false) {
     RN_CUDA(cudaMemsetAsync(ws->used_bits, 0, size_t(ws->nwords) * 4, st));
     RN_CUDA(cudaMemsetAsync(ws->rbits, 0, size_t(ws->nwords) * 4, st));
     RN_CUDA(cudaMemsetAsync(ws->sbits, 0, size_t(ws->nwords) * 4, st));
     RN_CUDA(cudaMemsetAsync(ws->ctl, 0, sizeof(Control), st));
     if (nR)
         k_mark_set<<<std::min<uint32_t>((nR + 255) / 256, 4096), 256, 0, st>>>(dR, nR, g.n, g.perm, ws->used_bits,
-                                                                               ws->rbits, ws->ctl);
+                                                                               ws->rbits, ws->ctl, by_orig);
     if (nS)
         k_mark_set<<<std::min<uint32_t>((nS + 255) / 256, 4096), 256, 0, st>>>(dS, nS, g.n, g.perm, ws->used_bits,
-                                                                               ws->sbits, ws->ctl);
+                                                                               ws->sbits, ws->ctl, false);
     ensure_u32(&ws->rsorted, &ws->rsorted_cap, std::max<uint32_t>(nR, 1));
     const uint32_t nblocks = (ws->nwords + 1023) / 1024;
     k_bits_count<<<nblocks, 1024, 0, st>>>(ws->rbits, ws->nwords, ws->block_sums);
     k_bits_compact<<<nblocks, 1024, 0, st>>>(ws->rbits, ws->nwords, ws->block_sums, nblocks, ws->rsorted, ws->ctl);
     ws->launches += (nR ? 1 : 0) + (nS ? 1 : 0) + 2;
+    if (by_orig && nR) {
+        k_to_internal<<<std::min<uint32_t>((nR + 255) / 256, 4096), 256, 0, st>>>(ws->rsorted, nR, g.perm, ws->ctl);
+        ws->launches++;
+    }
     RN_CUDA(cudaGetLastError());
 }
 
@@ -2356,18 +2528,20 @@ void run_join(const DeviceGraph &g, Workspace *ws, const EngineConfig &cfg, uint
     if (theta > RN_THETA_MAX) fail(RN_EINVAL, "theta must be <= 2^31 or RN_INF");
     const uint32_t T = cfg.tile_width > 1 ? cfg.tile_width : 32;  // the tile search's width
     if (T != 32 && T != 64 && T != 128) fail(RN_EINVAL, "tile width must be 1, 32, 64 or 128");
-    const uint32_t delta = choose_delta(cfg, median_w);
     std::lock_guard<std::mutex> device_lock(ws->sh->mu);
     Range range("rn.join");
     *stats = rn_query_stats{};
     const bool by_source = use_source_search(g, ws, cfg, theta);
+    // the warp search's segments give the output order when sources run in output order
+    const bool place = by_source && g.iperm_inverts_perm;
+    const uint32_t delta = choose_delta(cfg, median_w, by_source);
     stats->tile_width = by_source ? 1 : T;
     stats->delta = delta;
     stats->theta_final = theta;
     ws->launches = 0;
     RN_CUDA(cudaEventRecord(ws->ev0, st));
 
-    prep_sets(g, ws, dR, nR, dS, nS, st);
+    prep_sets(g, ws, dR, nR, dS, nS, st, place);
     // sources per tile: as many as fit a row, but spread so the tiles fill the resident
     // blocks in whole waves (a last wave of a few tiles would double the search time)
     ensure_slab(ws);
@@ -2401,6 +2575,7 @@ void run_join(const DeviceGraph &g, Workspace *ws, const EngineConfig &cfg, uint
     a.out_key = ws->keyA;
     a.out_d = ws->valA;
     a.out_cap = ws->pair_cap;
+    a.seg = place ? ensure_segments(ws, nR, st) : nullptr;
     uint64_t retried = 0;
     const std::vector<uint32_t> one_query;
     auto search_pass = [&] {
@@ -2416,23 +2591,29 @@ void run_join(const DeviceGraph &g, Workspace *ws, const EngineConfig &cfg, uint
     if (c.pairs > ws->pair_cap) {
         // the pair buffer was too small: grow it and search again (same result)
         ensure_pairs(ws, c.pairs + c.pairs / 8);
-        prep_sets(g, ws, dR, nR, dS, nS, st);
+        prep_sets(g, ws, dR, nR, dS, nS, st, place);
         a.src = ws->rsorted;
         a.out_key = ws->keyA;
         a.out_d = ws->valA;
         a.out_cap = ws->pair_cap;
+        a.seg = place ? ensure_segments(ws, nR, st) : nullptr;
         c = search_pass();
         check_control(c);
         if (c.pairs > ws->pair_cap) fail(RN_EINTERNAL, "pair count changed between passes");
     }
     const uint64_t np = c.pairs;
 
-    // a5: canonical order by (u, v), written straight into the caller's buffers
+    // a5: canonical order by (u, v), written straight into the caller's buffers: by
+    // placing the warp search's per-source segments, else by a radix sort of all pairs
     Range rsort("rn.sort");
     dpairs_reserve(out, np);
-    std::vector<int> shifts;
-    for (uint32_t sh = 0; sh < 2 * vbits; sh += 8) shifts.push_back(int(sh));
-    radix_sort_to_pairs(ws, np, shifts, vbits, out, st);
+    if (place && can_place(ws, c)) {
+        place_pairs(ws, nR, vbits, 0xFFFFFFFFu, out, st);
+    } else {
+        std::vector<int> shifts;
+        for (uint32_t sh = 0; sh < 2 * vbits; sh += 8) shifts.push_back(int(sh));
+        radix_sort_to_pairs(ws, np, shifts, vbits, out, st);
+    }
     out->n = np;
     RN_CUDA(cudaEventRecord(ws->ev1, st));
     RN_CUDA(cudaEventSynchronize(ws->ev1));
@@ -2499,13 +2680,13 @@ void run_join_multi(const DeviceGraph &g, Workspace *ws, const EngineConfig &cfg
     if (T != 32 && T != 64 && T != 128) fail(RN_EINVAL, "tile width must be 1, 32, 64 or 128");
     const uint32_t vbits = bits_for(g.n), qbits = bits_for(nq);
     if (2 * vbits + qbits > 64) fail(RN_EINVAL, "too many queries for this graph in one search");
-    const uint32_t delta = choose_delta(cfg, median_w);
     std::lock_guard<std::mutex> device_lock(ws->sh->mu);
     Range range("rn.join_many");
     *stats = rn_query_stats{};
     uint32_t max_bound = 0;
     for (uint32_t t : theta) max_bound = std::max(max_bound, std::min(t, RN_THETA_MAX));
     const bool by_source = use_source_search(g, ws, cfg, max_bound);
+    const uint32_t delta = choose_delta(cfg, median_w, by_source);
     stats->tile_width = by_source ? 1 : T;
     stats->delta = delta;
     ws->launches = 0;
@@ -2515,8 +2696,15 @@ void run_join_multi(const DeviceGraph &g, Workspace *ws, const EngineConfig &cfg
     for (uint32_t i = 0; i < nq; i++) {
         first[i] = uint32_t(src.size());
         const size_t b = src.size();
-        for (uint32_t j = 0; j < nR[i]; j++) src.push_back(perm[R[i][j]]);
-        std::sort(src.begin() + b, src.end());
+        if (by_source && g.iperm_inverts_perm) {
+            // each source alone: in increasing original id, the output order
+            std::vector<uint32_t> r(R[i], R[i] + nR[i]);
+            std::sort(r.begin(), r.end());
+            for (uint32_t x : r) src.push_back(perm[x]);
+        } else {
+            for (uint32_t j = 0; j < nR[i]; j++) src.push_back(perm[R[i][j]]);
+            std::sort(src.begin() + b, src.end());  // graph neighbours share tiles
+        }
         bound[i] = theta[i] == RN_INF ? RN_THETA_MAX : theta[i];
         if (bound[i] > RN_THETA_MAX) fail(RN_EINVAL, "theta must be <= 2^31 or RN_INF");
         soff[i] = uint32_t(sids.size());
@@ -2609,6 +2797,8 @@ void run_join_multi(const DeviceGraph &g, Workspace *ws, const EngineConfig &cfg
     a.inst_shift = 2 * vbits;
     a.inst_sbits = ws->mq_sptr;
     a.inst_bound = ws->mq_bound;
+    const bool place = by_source && g.iperm_inverts_perm;
+    a.seg = place ? ensure_segments(ws, total, st) : nullptr;
     uint64_t retried = 0;
     auto search_pass = [&] {
         return by_source ? source_search_all(g, ws, a, total, ms0, T, max_bound, first, st, &retried)
@@ -2624,6 +2814,7 @@ void run_join_multi(const DeviceGraph &g, Workspace *ws, const EngineConfig &cfg
         a.out_key = ws->keyA;
         a.out_d = ws->valA;
         a.out_cap = ws->pair_cap;
+        a.seg = place ? ensure_segments(ws, total, st) : nullptr;
         c = search_pass();
         check_control(c);
         if (c.pairs > ws->pair_cap) fail(RN_EINTERNAL, "pair count changed between passes");
@@ -2638,9 +2829,14 @@ void run_join_multi(const DeviceGraph &g, Workspace *ws, const EngineConfig &cfg
     const uint64_t np = c.pairs;
     Range rsort("rn.sort");
     dpairs_reserve(out, np);
-    std::vector<int> shifts;
-    for (uint32_t sh = 0; sh < 2 * vbits + qbits; sh += 8) shifts.push_back(int(sh));
-    radix_sort_to_pairs(ws, np, shifts, vbits, out, st, vbits >= 32 ? 0xFFFFFFFFu : (1u << vbits) - 1);
+    const uint32_t umask = vbits >= 32 ? 0xFFFFFFFFu : (1u << vbits) - 1;
+    if (place && can_place(ws, c)) {
+        place_pairs(ws, total, vbits, umask, out, st);  // sources in (query, u) order
+    } else {
+        std::vector<int> shifts;
+        for (uint32_t sh = 0; sh < 2 * vbits + qbits; sh += 8) shifts.push_back(int(sh));
+        radix_sort_to_pairs(ws, np, shifts, vbits, out, st, umask);
+    }
     out->n = np;
     RN_CUDA(cudaEventRecord(ws->ev1, st));
     RN_CUDA(cudaEventSynchronize(ws->ev1));
@@ -2749,9 +2945,9 @@ void run_join_noalloc(const DeviceGraph &g, uint32_t median_w, const uint32_t *d
     RN_CUDA(cudaMemsetAsync(sbits, 0, size_t(nwords) * 4, st));
     RN_CUDA(cudaMemsetAsync(slab, 0xFF, size_t(NA_BLOCKS) * SMEM_H * 32 * 4, st));
     if (nR)
-        k_mark_set<<<std::min<uint32_t>((nR + 255) / 256, 4096), 256, 0, st>>>(dR, nR, g.n, g.perm, used_bits, rbits, ctl);
+        k_mark_set<<<std::min<uint32_t>((nR + 255) / 256, 4096), 256, 0, st>>>(dR, nR, g.n, g.perm, used_bits, rbits, ctl, false);
     if (nS)
-        k_mark_set<<<std::min<uint32_t>((nS + 255) / 256, 4096), 256, 0, st>>>(dS, nS, g.n, g.perm, used_bits, sbits, ctl);
+        k_mark_set<<<std::min<uint32_t>((nS + 255) / 256, 4096), 256, 0, st>>>(dS, nS, g.n, g.perm, used_bits, sbits, ctl, false);
     k_bits_count<<<nblocks, 1024, 0, st>>>(rbits, nwords, bsums);
     k_bits_compact<<<nblocks, 1024, 0, st>>>(rbits, nwords, bsums, nblocks, rsorted, ctl);
     RN_CUDA(cudaGetLastError());
@@ -3245,6 +3441,7 @@ static void points_graph(const DeviceGraph &g, const std::vector<uint32_t> &perm
     }
     RN_CUDA(cudaMemcpyAsync(ps->aug.row_ptr, g.row_ptr, (size_t(g.n) + 1) * 4, cudaMemcpyDeviceToDevice, st));
     RN_CUDA(cudaMemcpyAsync(ps->aug.adj, g.adj, g.arcs * 8, cudaMemcpyDeviceToDevice, st));
+    ps->aug.iperm_inverts_perm = false;  // a point node's output id is its index in R or S
     RN_CUDA(cudaMemcpyAsync(ps->aug.perm, g.perm, size_t(g.n) * 4, cudaMemcpyDeviceToDevice, st));
     RN_CUDA(cudaMemcpyAsync(ps->aug.iperm, g.iperm, size_t(g.n) * 4, cudaMemcpyDeviceToDevice, st));
     if (np) {

@@ -60,6 +60,7 @@ struct DeviceGraph {
     uint32_t *adj = nullptr;      // 2 * arcs: (col, w) interleaved, 8-byte aligned
     uint32_t *perm = nullptr;     // original id -> internal id
     uint32_t *iperm = nullptr;    // internal id -> original id
+    bool iperm_inverts_perm = true;  // false when output ids are not the input ids (points)
 };
 
 struct Workspace;  // device scratch owned by a graph (rn_engine.cu)

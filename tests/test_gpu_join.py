@@ -188,6 +188,9 @@ def test_road264k_full(rn, oracle):
     got = dev_join(rn, g, w.R, w.S, w.theta)
     assert_same(got, ref, "road264k")
     assert_same(rn.rn_distance_join(g, w.R, w.S, w.theta), ref, "road264k host")
+    st = rn.rn_last_query_stats()
+    # the warp search's segments are placed in order (no 40-bit radix sort of all pairs)
+    assert st["tile_width"] == 1 and st["launches"] < 16, st["launches"]
 
 
 def test_road1070k_join_sampled(rn, oracle):
@@ -262,3 +265,24 @@ def test_source_search_routes(rn, oracle):
     assert_same(dev_join(rn, g, R, S, theta), og.join(R, S, theta), "small after unbounded")
     st = rn.rn_last_query_stats()
     assert st["tile_width"] == 1 and st["slot_lanes"] == st["slots"]
+
+
+def test_long_segments_sorted(rn, oracle):
+    """Sources with more than 256 pairs each (S dense around them): the warp search's
+    segments are too long to place, and the pairs are radix sorted instead."""
+    e = I.road_graph(30_000, 83_100, 71)
+    og = oracle.graph(e.n, e.src, e.dst, e.w)
+    R, S = I.disjoint_sets(e.n, 200, 20_000, 72)
+    D = np.sort(og.sssp(int(R[0]))[0])
+    theta = int(D[1200])  # balls of ~1,200 nodes, two thirds of them in S
+    g = load(rn, e)
+    ref = og.join(R, S, theta)
+    assert_same(dev_join(rn, g, R, S, theta), ref, "dense S")
+    st = rn.rn_last_query_stats()
+    assert st["tile_width"] == 1 and st["launches"] > 16, st["launches"]
+    # and both orders agree with the tile search's
+    gt = load(rn, e, cfg={"tile_width": 32})
+    assert_same(dev_join(rn, gt, R, S, theta), ref, "dense S, tiles")
+    small = S[:500]
+    assert_same(dev_join(rn, g, R, small, theta), og.join(R, small, theta), "sparse S, placed")
+    assert rn.rn_last_query_stats()["launches"] < 16
