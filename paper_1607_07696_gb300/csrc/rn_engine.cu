@@ -2223,15 +2223,17 @@ static int source_blocks_per_sm(uint32_t ms) {
     }
 }
 
-// One warp-search launch over `items` sources with maps of ms slots: at most three
-// blocks per SM the slab's regions stand for (two regions per SM), fewer for few sources.
+// One warp-search launch over `items` sources with maps of ms slots: a block per
+// src_warps sources up to three blocks per SM of the device.  The warp search uses no slab,
+// so a server's request is not held to the slab regions it was given (those serve its
+// tile fallback): its blocks share the SMs with the other requests' as they free up.
 static void source_launch(uint32_t ms, SearchArgs a, uint32_t items, Workspace *ws, cudaStream_t st) {
     a.H = ms;
     a.hshift = 32 - log2u(ms);
     a.max_fill = ms * 7 / 8;
     a.gmap = nullptr;
     const uint32_t per_block = src_warps(ms);
-    const uint32_t resident = std::max<uint32_t>(1, ws->sh->slab_ctas * SRC_BLOCKS_PER_SM / CTAS_PER_SM);
+    const uint32_t resident = std::max<uint32_t>(1, uint32_t(ws->num_sms) * SRC_BLOCKS_PER_SM);
     const uint32_t grid = std::max<uint32_t>(1, std::min<uint32_t>((items + per_block - 1) / per_block, resident));
     switch (ms) {
         case 1024: launch_source<1024>(a, grid, st); break;
