@@ -1541,20 +1541,39 @@ __global__ void __launch_bounds__(src_warps(MS) * 32, SRC_BLOCKS_PER_SM) k_sourc
             max_seg = max(max_seg, cnt);
             base = __shfl_sync(FULL, base, 0);
             __syncwarp();
+            // four chunks of 32 slots at a time, every output-id load issued before the
+            // first write (so their latencies overlap)
             unsigned long long pos = base;
-            for (uint32_t c = 0; c < MS; c += 32) {
-                const uint32_t b = hits[c >> 5];
-                if ((b >> lane) & 1u) {
-                    const unsigned long long idx = pos + __popc(b & lt);
-                    const uint32_t y = key[c + lane] & SK_NODE;
-                    if (idx < a.out_cap && !RN_BAD(y < a.n_nodes, 17, c + lane, y)) {
-                        a.out_key[idx] = prefix | (u << a.vbits) | (unsigned long long)__ldg(&a.iperm[y]);
-                        a.out_d[idx] = dist[c + lane];
+            for (uint32_t c = 0; c < MS; c += 128) {
+                uint32_t b[4], dd[4], v[4];
+#pragma unroll
+                for (int q = 0; q < 4; q++) {
+                    const uint32_t h = c + 32 * q + lane;
+                    b[q] = hits[h >> 5];
+                    dd[q] = 0;
+                    v[q] = 0;
+                    if ((b[q] >> lane) & 1u) {
+                        const uint32_t y = key[h] & SK_NODE;
+                        if (!RN_BAD(y < a.n_nodes, 17, h, y)) {
+                            dd[q] = dist[h];
+                            v[q] = __ldg(&a.iperm[y]);
+                        }
                     }
                 }
-                pos += __popc(b);
-                key[c + lane] = SK_EMPTY;
-                dist[c + lane] = INF;
+#pragma unroll
+                for (int q = 0; q < 4; q++) {
+                    const uint32_t h = c + 32 * q + lane;
+                    if ((b[q] >> lane) & 1u) {
+                        const unsigned long long idx = pos + __popc(b[q] & lt);
+                        if (idx < a.out_cap) {
+                            a.out_key[idx] = prefix | (u << a.vbits) | (unsigned long long)v[q];
+                            a.out_d[idx] = dd[q];
+                        }
+                    }
+                    pos += __popc(b[q]);
+                    key[h] = SK_EMPTY;
+                    dist[h] = INF;
+                }
             }
             n_slots += fill;
             max_ball = max(max_ball, fill);
