@@ -289,7 +289,7 @@ struct Workspace {
     uint64_t mq_cap_q = 0, mq_cap_bits = 0, mq_cap_sids = 0;
     // the largest source ball the last warp search met (or estimated, for sources
     // whose map overflowed) and its bound: predicts the next query's balls
-    double ball_max = 0;
+    double ball_max = 0, ball_mean = 0;
     uint32_t ball_theta = 0;
     // warp search: per source its first pair and pair count; whether the last search
     // handed sources to the tile search (their pairs are then not in segments)
@@ -2285,12 +2285,19 @@ static bool use_source_search(const DeviceGraph &g, const Workspace *ws, const E
     return predicted_ball(ws, theta) <= src_fit(SRC_MS_MAX);
 }
 
-// First warp map: the smallest that holds the predicted ball, 2048 slots with no history.
+// First warp map: the smallest whose 7/8 holds 1.3 times the predicted mean ball and
+// nearly the predicted largest (up to 15% over: the few sources that overflow are searched
+// again with a larger map, while a smaller map fits twice as many warps on an SM); 2048
+// slots with no history.
 static uint32_t source_first_map(const Workspace *ws, uint32_t theta) {
     const double b = predicted_ball(ws, theta);
     if (b <= 0) return 2048;
-    for (uint32_t ms = SRC_MS_MIN; ms <= SRC_MS_MAX; ms *= 2)
-        if (b <= src_fit(ms)) return ms;
+    const double r = double(theta) / double(ws->ball_theta);
+    const double mean = ws->ball_mean * r * r;
+    for (uint32_t ms = SRC_MS_MIN; ms <= SRC_MS_MAX; ms *= 2) {
+        const double room = double(ms) * 7 / 8;
+        if (mean > 0 ? (mean * 1.3 <= room && b <= room * 1.15) : b <= src_fit(ms)) return ms;
+    }
     return SRC_MS_MAX;
 }
 
@@ -2320,10 +2327,13 @@ static Control source_search_all(const DeviceGraph &g, Workspace *ws, SearchArgs
     ws->src_tiles = false;
     ws->blocks_per_sm = nsrc ? source_blocks_per_sm(ms0) : 0;
     double ball = c.src_max_ball;
+    // mean ball of the sources the first pass completed (0 when none did)
+    const double mean = nsrc > c.n_failed ? double(c.slots) / double(nsrc - c.n_failed) : 0.0;
     auto learn = [&] {
         if (nsrc && ball >= 64) {  // a handful of nodes says little about the growth
             ws->ball_theta = std::max<uint32_t>(theta, 1);
             ws->ball_max = ball;
+            ws->ball_mean = mean;
         }
     };
     if (!c.n_failed || c.err || c.check[0]) {
