@@ -2513,6 +2513,12 @@ void workspace_reserve(Workspace *ws, uint32_t max_r, uint64_t max_pairs) {
     ensure_ranges(&ws->failed2, &ws->failed2_cap, std::max<uint32_t>(max_r, 1));
     ensure_pairs(ws, max_pairs);
     grow(ws, &ws->hist, &ws->hist_cap, hist_words((max_pairs + RS_TILE - 1) / RS_TILE * 256), 4);
+    if (!ws->seg || ws->seg_cap < max_r) {  // the warp search's per-source segments
+        device_free(ws->seg);
+        ws->seg = nullptr;
+        ws->seg_cap = std::max<uint32_t>(max_r, 1024);
+        ws->seg = (uint2 *)device_alloc(size_t(ws->seg_cap) * 8);
+    }
 }
 
 // a2: validate R and S on the device, build the S membership bitmap and the list of R
