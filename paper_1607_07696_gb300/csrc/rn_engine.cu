@@ -2305,8 +2305,8 @@ static uint32_t source_first_map(const Workspace *ws, uint32_t theta) {
 // overflowed: with the smallest warp map their estimated ball fits (fill * (bound /
 // tau)^2, as for tiles), and past the largest warp map with the tile search of width T,
 // as ranges of consecutive sources of one query (inst_first: the first source of every
-// query, empty for a single query).  Remembers the largest ball seen, for the next
-// query's choice of path and map.
+// query, empty for a single query).  Remembers the largest and the mean ball seen, for
+// the next query's choice of path and map.
 static Control source_search_all(const DeviceGraph &g, Workspace *ws, SearchArgs a, uint32_t nsrc, uint32_t ms0,
                                  uint32_t T, uint32_t theta, const std::vector<uint32_t> &inst_first,
                                  cudaStream_t st, uint64_t *retried) {
@@ -2345,7 +2345,7 @@ static Control source_search_all(const DeviceGraph &g, Workspace *ws, SearchArgs
         const double e = double(std::max<uint32_t>(f.w, 1)) * std::min(r * r, 1e12);
         return std::min<double>(std::max<double>(e, f.w), double(g.n));
     };
-    std::map<uint32_t, std::vector<uint4>> grow;  // warp map -> sources (index, bound, est, -)
+    std::map<uint32_t, std::vector<uint4>> grow;  // warp map -> its sources (index, 0, 0, 0)
     std::vector<uint4> to_tiles;
     double tile_est = 0;
     auto route = [&](const uint4 &f, uint32_t failed_at) {
