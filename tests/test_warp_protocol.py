@@ -142,3 +142,47 @@ def test_protocol_matches_dijkstra(oracle, seed):
                         continue
                     assert got == ref, (seed, int(s), bound, delta, qs)
     assert runs - overflow > runs // 2
+
+
+def warp_bitonic_model(vals, E):
+    """The placement's in-register sort (`warp_bitonic<E>`): 32 lanes of E values, element
+    lane * E + e in register e; partners at distance j >= E sit in lane ^ (j / E) (a
+    shuffle), closer ones in register e ^ j of the same lane."""
+    x = [[vals[lane * E + e] for e in range(E)] for lane in range(32)]
+    k = 2
+    while k <= 32 * E:
+        j = k >> 1
+        while j > 0:
+            if j >= E:
+                lj = j // E
+                partner = [[x[lane ^ lj][e] for e in range(E)] for lane in range(32)]  # shfl_xor
+                for lane in range(32):
+                    lower = (lane & lj) == 0
+                    for e in range(E):
+                        up = ((lane * E + e) & k) == 0
+                        p = partner[lane][e]
+                        x[lane][e] = min(x[lane][e], p) if lower == up else max(x[lane][e], p)
+            else:
+                for lane in range(32):
+                    for e in range(E):
+                        if e & j == 0:
+                            up = ((lane * E + e) & k) == 0
+                            lo, hi = x[lane][e], x[lane][e ^ j]
+                            if (lo > hi) == up:
+                                x[lane][e], x[lane][e ^ j] = hi, lo
+            j >>= 1
+        k <<= 1
+    return [x[lane][e] for lane in range(32) for e in range(E)]
+
+
+@pytest.mark.parametrize("E", [1, 2, 4, 8])
+def test_placement_network_sorts(E):
+    rng = np.random.default_rng(E)
+    pad = (1 << 64) - 1
+    for cnt in sorted({1, 2, 31, 32, 33, 16 * E + 3, 32 * E - 1, 32 * E}):
+        if cnt > 32 * E:
+            continue
+        for _ in range(5):
+            v = rng.choice(1 << 40, size=cnt, replace=False).tolist()
+            vals = v + [pad] * (32 * E - cnt)
+            assert warp_bitonic_model(vals, E)[:cnt] == sorted(v), (E, cnt)
