@@ -129,10 +129,11 @@ typedef struct {
 /* Counters of the calling thread's last query (rn_last_query_stats). */
 typedef struct {
     uint64_t pairs;         /* pairs returned */
-    uint64_t tiles;         /* source tiles searched */
-    uint64_t retried_tiles; /* tiles searched again with a larger slab after an overflow */
+    uint64_t tiles;         /* source tiles searched (sources, for the warp search) */
+    uint64_t retried_tiles; /* tiles (or sources) searched again with a larger map after an
+                               overflow */
     uint64_t scans;         /* slab rows scanned (a node's arcs relaxed for a whole tile) */
-    uint32_t tile_width;
+    uint32_t tile_width;    /* 1: the warp search ran; else the tile search's width */
     uint32_t tile_sources;  /* sources per tile */
     uint32_t delta;
     uint32_t passes;        /* search passes (k closest pairs widens its radius by passes) */
