@@ -1,9 +1,9 @@
 #!/usr/bin/env python
 """Benchmark of the theta-join engine on the 264k-node road-like workload.
 
-One step = one whole query: validate R and S, build the S bitmap, sort R into tiles,
-search every tile (delta-stepping over the distance slab), emit the pairs within theta,
-sort them by (u, v).  The headline ``value`` is join pairs/s with R and S already in
+One step = one whole query: validate R and S, build the S bitmap, list R, search every
+source (by default one warp per source, delta-stepping in a shared-memory map), emit the
+pairs within theta and put them in (u, v) order.  The headline ``value`` is join pairs/s with R and S already in
 device memory (CUDA events on the query stream, L2 flushed between steps); ``e2e`` is
 the same metric through the host-buffer call, with the copies of R and S to the device
 and of the pairs back to the host inside the timed region.
