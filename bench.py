@@ -1,19 +1,23 @@
 #!/usr/bin/env python
-"""Benchmark of the theta-join engine on the 264k-node road-like workload.
+"""Benchmark of the theta-join engine on the 1.07M-node road-like workload.
 
 One step = one whole query: validate R and S, build the S bitmap, list R, search every
 source (by default one warp per source, delta-stepping in a shared-memory map), emit the
-pairs within theta and put them in (u, v) order.  The headline ``value`` is join pairs/s with R and S already in
-device memory (CUDA events on the query stream, L2 flushed between steps); ``e2e`` is
-the same metric through the host-buffer call, with the copies of R and S to the device
-and of the pairs back to the host inside the timed region.
+pairs within theta and put them in (u, v) order.  The workload is the 1.07M-node,
+2.7M-edge road-like graph with 50,000 + 50,000 clustered R and S nodes and theta for
+about 50 S-matches per R node (2.8M pairs).  The headline ``value`` is join pairs/s
+with R and S already in device memory (CUDA events on the query stream, L2 flushed
+between steps); ``e2e`` is the same metric through the host-buffer call, with the
+copies of R and S to the device and of the pairs back to the host inside the timed
+region.  Secondary legs: the 264k-node join, k closest pairs on the 1.07M-node graph,
+512 batched joins against plain calls, and a served request stream.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl engine|reference]
 
 Under torchrun (N > 1) every rank joins its own R and S (same sizes, other seeds) over
 the same graph -- weak scaling with no collective on the data path; rank 0 prints the
-line, with the slowest rank's time.  ``--impl reference`` times the CPU oracle on the
-host (the paper publishes no code and no absolute numbers to compare against).
+line, with the slowest rank's time.  ``--impl reference`` times the CPU oracle on every
+host core (the paper publishes no code and no absolute numbers to compare against).
 """
 from __future__ import annotations
 
@@ -34,7 +38,8 @@ METRIC = "join pairs/s"
 UNIT = "pairs/s"
 WORKLOADS = json.load(open(os.path.join(ROOT, "tests", "golden", "workloads.json")))
 ENGINE_SRC = os.path.join(ROOT, "paper_1607_07696_gb300", "csrc", "rn_engine.cu")
-PROFILE = os.path.join(ROOT, "profiles", "search_road264k.json")
+PROFILES = {"road264k_join": os.path.join(ROOT, "profiles", "search_road264k.json"),
+            "road1070k_join": os.path.join(ROOT, "profiles", "search_road1070k.json")}
 
 
 def parse():
@@ -43,7 +48,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="engine", choices=["engine", "reference"])
-    ap.add_argument("--workload", default="road264k_join",
+    ap.add_argument("--workload", default="road1070k_join",
                     choices=["road264k_join", "grid4096_theta1500", "road1070k_join"])
     ap.add_argument("--tile-width", type=int, default=0)
     ap.add_argument("--delta", type=int, default=0)
@@ -51,7 +56,9 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batch", action="store_true", help="skip the 512-instance batched leg")
     ap.add_argument("--no-serve", action="store_true", help="skip the serving leg")
-    ap.add_argument("--serve-requests", type=int, default=300)
+    ap.add_argument("--serve-requests", type=int, default=2000)
+    ap.add_argument("--no-legs", action="store_true",
+                    help="only the headline workload: no secondary legs and no CPU baseline")
     return ap.parse_args()
 
 
@@ -73,6 +80,8 @@ def make_workload(name: str, rank: int):
     spec = dict(WORKLOADS["road1070k_clustered"])
     w = I.c3_road_clustered(theta=spec["theta_join"])
     spec["theta"] = spec["theta_join"]
+    if rank:
+        w.R, w.S = I.clustered_sets(w.graph.xy, len(w.R), len(w.S), I.BASE_SEED + 3000 + 7919 * rank)
     return w, spec
 
 
@@ -170,30 +179,58 @@ def engine_hash() -> str:
     return hashlib.sha256(src[a:b].encode()).hexdigest()[:16]
 
 
-def profiled_traffic(workload: str, kernel: str):
-    """DRAM bytes per launch of the search kernel from the committed ncu summary, or None
-    when there is none, it covers another kernel or the kernel source changed since."""
-    if not os.path.exists(PROFILE):
+def profile_of(workload: str, kernel: str):
+    """The committed ncu summary of the search kernel on this workload, or None when there
+    is none, it covers another kernel or the kernel source changed since."""
+    path = PROFILES.get(workload)
+    if not path or not os.path.exists(path):
         return None
-    p = json.load(open(PROFILE))
+    p = json.load(open(path))
     if (p.get("workload") != workload or p.get("engine_sha") != engine_hash()
             or not str(p.get("kernel", "")).startswith(kernel)):
         return None
-    return p.get("dram_bytes_per_launch")
+    return p
 
 
-def cpu_baseline(w, spec, sample_sources: int = 1500) -> dict:
-    """The CPU oracle, as it stands, on the first sources of R (single thread)."""
+def roofline(st: dict, pairs: int, search_ms: float, workload: str, peak: float, peak_kind: str) -> dict:
+    """HBM roofline of the search kernel: algorithmic bytes per launch over its CUDA-event
+    time, against the measured copy bandwidth; beside it, from the committed ncu summary
+    of the same kernel and workload (when current), its DRAM traffic per launch and its
+    L2 traffic per launch over the same time against the L2 peak ncu reports."""
+    alg = algorithmic_bytes(st, pairs)
+    achieved = alg / (search_ms / 1e3) / 1e9
+    kernel = search_kernel(st)
+    prof = profile_of(workload, kernel)
+    out = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+           "traffic": prof.get("dram_bytes_per_launch") if prof else None, "kernel": kernel,
+           "peak_kind": peak_kind, "search_ms": search_ms, "alg_bytes_per_launch": alg}
+    if prof and prof.get("l2_bytes_per_launch") and prof.get("l2_peak_gbs"):
+        l2 = prof["l2_bytes_per_launch"] / (search_ms / 1e3) / 1e9
+        out["l2"] = {"achieved": l2, "peak": prof["l2_peak_gbs"], "unit": "GB/s",
+                     "frac": l2 / prof["l2_peak_gbs"], "bytes_per_launch": prof["l2_bytes_per_launch"],
+                     "peak_kind": "ncu lts__t_bytes peak"}
+    return out
+
+
+def cpu_baseline(w, spec) -> dict:
+    """The CPU oracle, as it stands, on the whole workload: its per-source searches on
+    every host core (R in chunks, one search state per thread), then on one core."""
     from oracle import oracle as O
 
     og = O.default().graph(w.graph.n, w.graph.src, w.graph.dst, w.graph.w)
-    R = w.R[:sample_sources]
+    cores = O.host_cores()
     t0 = time.perf_counter()
-    p = og.join(R, w.S, spec["theta"])
+    p = og.join_mt(w.R, w.S, spec["theta"], cores)
     dt = time.perf_counter() - t0
-    return {"value": len(p) / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"{len(R)} of {len(w.R)} R sources against all {len(w.S)} S nodes, "
-                      f"theta {spec['theta']}, {dt:.1f} s, {len(p)} pairs"}
+    t0 = time.perf_counter()
+    p1 = og.join(w.R, w.S, spec["theta"])
+    dt1 = time.perf_counter() - t0
+    assert len(p1) == len(p), "threaded and single-thread oracle disagree"
+    return {"value": len(p) / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"the whole workload: all {len(w.R)} R sources against all {len(w.S)} S nodes, "
+                      f"theta {spec['theta']}, {len(p)} pairs; {dt:.2f} s on {cores} threads, "
+                      f"{dt1:.2f} s on one",
+            "single_core_value": len(p1) / dt1, "cpu_model": O.cpu_model()}
 
 
 # ------------------------------------------------------------------- engine ----
@@ -278,23 +315,21 @@ def batch_leg(rn, steps: int, warmup: int, stream, flush) -> dict:
     return res
 
 
-def join_1m_leg(rn, steps: int, stream, flush, peak: float) -> dict:
-    """The theta-join on the 1.07M-node road-like graph with 50,000 + 50,000 clustered
-    sets (theta for about 50 S-matches per R node): pairs/s with device buffers and L2
-    flushed, and the search's roofline against the same measured HBM peak."""
+def join_264k_leg(rn, steps: int, stream, flush, peak: float, peak_kind: str) -> dict:
+    """The theta-join on the 264k-node road-like graph with 10,000 + 10,000 uniform sets
+    (theta for about 50 S-matches per R node): pairs/s with device buffers and L2
+    flushed, GTEPS, and the search's roofline against the same measured HBM peak."""
     import numpy as np
     import torch
 
-    from paper_1607_07696_gb300 import inputs as I
-
-    spec = WORKLOADS["road1070k_clustered"]
-    w = I.c3_road_clustered()
+    spec = WORKLOADS["road264k_join"]
+    w, _ = make_workload("road264k_join", 0)
     e = w.graph
     g = rn.rn_graph_load(e.src, e.dst, e.w, e.n)
     dR = torch.as_tensor(w.R.astype(np.int32), device="cuda")
     dS = torch.as_tensor(w.S.astype(np.int32), device="cuda")
     out = rn.DevicePairs()
-    theta = spec["theta_join"]
+    theta = spec["theta"]
     for _ in range(3):
         rn.rn_distance_join_dev(g, dR, dS, theta, out, stream)
     ms, search = [], []
@@ -310,14 +345,12 @@ def join_1m_leg(rn, steps: int, stream, flush, peak: float) -> dict:
         ms.append(a.elapsed_time(b))
         st = rn.rn_last_query_stats()
         search.append(st["search_ms"] + st["retry_ms"])
-    alg = algorithmic_bytes(st, n)
-    sm = statistics.mean(search)
-    return {"workload": "road1070k_join: 1.07M nodes, 2.7M edges, |R| = |S| = 50,000 clustered",
-            "theta": theta, "pairs": int(n), "value": n / (statistics.median(ms) / 1e3), "unit": UNIT,
-            "ms_per_join": statistics.median(ms), "search_ms": sm, "tiles": st["tiles"],
-            "retried_tiles": st["retried_tiles"],
-            "roofline": {"bound": "hbm", "achieved": alg / (sm / 1e3) / 1e9, "peak": peak, "unit": "GB/s",
-                         "frac": alg / (sm / 1e3) / 1e9 / peak, "alg_bytes_per_launch": alg}}
+    med = statistics.median(ms)
+    return {"workload": "road264k_join: 264k nodes, 730k edges, |R| = |S| = 10,000 uniform",
+            "theta": theta, "pairs": int(n), "value": n / (med / 1e3), "unit": UNIT,
+            "ms_per_join": med, "gteps": spec["alg_arcs"] / (med / 1e3) / 1e9,
+            "launches": int(st["launches"]), "retried_tiles": st["retried_tiles"],
+            "roofline": roofline(st, n, statistics.mean(search), "road264k_join", peak, peak_kind)}
 
 
 def kcp_1m_leg(rn, steps: int, stream, flush) -> dict:
@@ -535,9 +568,7 @@ def run_engine(args):
             dist.destroy_process_group()
         return
     T = stats["tile_width"]
-    alg_bytes = algorithmic_bytes(stats, npairs)
     smean = statistics.mean(search_ms)
-    achieved = alg_bytes / (smean / 1e3) / 1e9
     peak, peak_kind = measured_peak_gbs()
     line = {
         "metric": METRIC,
@@ -566,10 +597,7 @@ def run_engine(args):
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 4 * (len(w.R) + len(w.S)),
                 "d2h_bytes_per_step": 12 * npairs},
         "gpu_launches": int(stats["launches"]) * args.steps,
-        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                     "frac": achieved / peak, "traffic": profiled_traffic(args.workload, search_kernel(stats)),
-                     "kernel": search_kernel(stats), "peak_kind": peak_kind,
-                     "search_ms": smean, "alg_bytes_per_launch": alg_bytes},
+        "roofline": roofline(stats, npairs, smean, args.workload, peak, peak_kind),
         "clocks": clk.summary(),
         "engine": {"reorder_ms": info["reorder_ms"], "slots": stats["slots"],
                    "slot_arcs": stats["slot_arcs"], "scans": stats["scans"],
@@ -580,14 +608,16 @@ def run_engine(args):
                    "cycles_emission": stats["cycles_emission"],
                    "cycles_step_a": stats["cycles_step_a"], "round_arcs": stats["round_arcs"]},
     }
-    if args.workload == "road264k_join" and world == 1:
-        line["join_1m"] = join_1m_leg(rn, min(50, max(3, args.steps // 2)), stream, flush, peak)
+    legs = world == 1 and not args.no_legs
+    if legs and args.workload != "road264k_join":
+        line["join_264k"] = join_264k_leg(rn, min(50, max(3, args.steps // 2)), stream, flush, peak, peak_kind)
+    if legs:
         line["kcp_1m"] = kcp_1m_leg(rn, min(10, max(3, args.steps // 2)), stream, flush)
-    if not args.no_batch and world == 1:
+    if legs and not args.no_batch:
         line["batched"] = batch_leg(rn, 5, 3, stream, flush)
-    if not args.no_serve and world == 1:
+    if legs and not args.no_serve:
         line["served"] = serve_leg(rn, args.serve_requests)
-    if not args.no_cpu_baseline and world == 1:
+    if legs and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(w, spec)
     print(json.dumps(line), flush=True)
     if dist:
@@ -597,7 +627,9 @@ def run_engine(args):
 # ---------------------------------------------------------------- reference ----
 
 def run_reference(args):
-    """The CPU oracle timed on the host cores, on bounded samples of the same workload."""
+    """The CPU oracle timed on every host core (its per-source searches on one thread per
+    core), each step a bounded sample of the same workload: a run of consecutive R
+    sources against all of S."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
@@ -605,17 +637,18 @@ def run_reference(args):
 
     w, spec = make_workload(args.workload, 0)
     og = O.default().graph(w.graph.n, w.graph.src, w.graph.dst, w.graph.w)
-    per_step = max(10, min(400, 20000 // max(1, args.steps)))  # about 20,000 sources in all
-    theta = spec["theta"]
+    cores = O.host_cores()
     nR = len(w.R)
+    per_step = max(100, min(nR, 100_000 // max(1, args.steps)))  # about 100,000 sources in all
+    theta = spec["theta"]
     for i in range(args.warmup):
-        og.join(w.R[:50], w.S, theta)
+        og.join_mt(w.R[:200], w.S, theta, cores)
     total_pairs, total_s = 0, 0.0
     for i in range(args.steps):
-        lo = (i * per_step) % max(1, nR - per_step)
+        lo = (i * per_step) % max(1, nR - per_step + 1)
         R = w.R[lo:lo + per_step]
         t0 = time.perf_counter()
-        p = og.join(R, w.S, theta)
+        p = og.join_mt(R, w.S, theta, cores)
         total_s += time.perf_counter() - t0
         total_pairs += len(p)
     value = total_pairs / total_s
@@ -626,10 +659,11 @@ def run_reference(args):
         "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
         "impl": "reference",
         "config": {"workload": args.workload, "n": w.graph.n, "m": w.graph.m, "nR": nR,
-                   "nS": len(w.S), "theta": theta},
-        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                   "nS": len(w.S), "theta": theta, "parallelism": f"{cores} host threads",
+                   "l2": "CPU: inputs resident in host memory"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
                          "sample": f"each step: {per_step} of {nR} R sources against all "
-                                   f"{len(w.S)} S nodes"},
+                                   f"{len(w.S)} S nodes", "cpu_model": O.cpu_model()},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)

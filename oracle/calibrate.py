@@ -92,7 +92,9 @@ def _road1070k(o, out, t0) -> None:
     w = I.c3_road_clustered()
     g = o.graph(w.graph.n, w.graph.src, w.graph.dst, w.graph.w)
     th, _ = theta_for_matches(g, w.R, w.S, 50, 256)
+    full = g.join_mt(w.R, w.S, th, O.host_cores())
     out["road1070k_clustered"] = {"theta_join": th, "matches_per_u": 50, "sample": 256,
+                                  "pairs": len(full), "alg_arcs": full.arcs,
                                   "k": [100, 10_000, 1_000_000], "graph": graph_digest(w.graph)}
     print("road1070k_clustered theta", th, f"{time.time() - t0:.1f}s", flush=True)
 

@@ -62,7 +62,7 @@ def build(src: str = SRC, out: str = LIB_PATH, extra: tuple[str, ...] = ()) -> s
     if os.path.exists(out) and src == SRC and os.path.getmtime(out) >= os.path.getmtime(src):
         return out
     tmp = out + f".tmp{os.getpid()}"
-    cmd = ["gcc", "-O2", "-std=c11", "-shared", "-fPIC", "-o", tmp, src, *extra]
+    cmd = ["gcc", "-O2", "-std=c11", "-shared", "-fPIC", "-pthread", "-o", tmp, src, *extra]
     subprocess.run(cmd, check=True)
     os.replace(tmp, out)
     return out
@@ -99,6 +99,10 @@ class Oracle:
         for fn in (L.og_kcp, L.og_kcp_bruteforce):
             fn.argtypes = [C.c_void_p, C.POINTER(C.c_uint32), C.c_uint32, C.POINTER(C.c_uint32),
                            C.c_uint32, C.c_uint64, C.c_uint64, C.POINTER(_Pairs)]
+        L.og_join_mt.argtypes = [C.c_void_p, C.POINTER(C.c_uint32), C.c_uint32, C.POINTER(C.c_uint32),
+                                 C.c_uint32, C.c_uint64, C.c_uint32, C.POINTER(_Pairs)]
+        L.og_kcp_mt.argtypes = [C.c_void_p, C.POINTER(C.c_uint32), C.c_uint32, C.POINTER(C.c_uint32),
+                                C.c_uint32, C.c_uint64, C.c_uint64, C.c_uint32, C.POINTER(_Pairs)]
         L.og_pairs_free.argtypes = [C.POINTER(_Pairs)]
         L.og_floyd_warshall.argtypes = [C.c_void_p, C.POINTER(C.c_uint64)]
         # points on edges: arrays of (a, b, t) uint32 triples
@@ -178,6 +182,36 @@ class OGraph:
         return self._pairs(self.o.lib.og_kcp, _ptr(r, C.c_uint32), len(r), _ptr(s, C.c_uint32),
                            len(s), int(k), int(theta))
 
+    def join_mt(self, R, S, theta: int, threads: int) -> Pairs:
+        """The join of ``join`` searched on ``threads`` host threads (same pairs, same order)."""
+        r, s = _u32(R), _u32(S)
+        return self._pairs(self.o.lib.og_join_mt, _ptr(r, C.c_uint32), len(r), _ptr(s, C.c_uint32),
+                           len(s), int(theta), int(threads))
+
+    def kcp_mt(self, R, S, k: int, theta: int = THETA_MAX, threads: int = 1) -> Pairs:
+        """kCP of ``kcp`` searched on ``threads`` host threads sharing one bound."""
+        r, s = _u32(R), _u32(S)
+        return self._pairs(self.o.lib.og_kcp_mt, _ptr(r, C.c_uint32), len(r), _ptr(s, C.c_uint32),
+                           len(s), int(k), int(theta), int(threads))
+
+    def kcp_by_join(self, R, S, k: int, theta: int = THETA_MAX, threads: int = 1,
+                    probe: int | None = None) -> Pairs:
+        """kCP by its definition: the first k of all pairs within theta in (d, u, v)
+        order.  The join is computed at a probe bound, doubled until it holds k pairs or
+        reaches theta: once the join within the probe holds k pairs, no pair beyond the
+        probe can be among the first k, so the answer is the first k of that join."""
+        if k < 1:
+            raise OracleError(OG_EINVAL, "kcp_by_join")
+        theta = int(theta)
+        b = theta if probe is None else max(1, min(int(probe), theta))
+        while True:
+            p = self.join_mt(R, S, b, threads)
+            if len(p) >= k or b >= theta:
+                break
+            b = min(theta, 2 * b)
+        order = np.lexsort((p.v, p.u, p.d))[:k]
+        return Pairs(p.u[order], p.v[order], p.d[order], p.arcs)
+
     def kcp_bruteforce(self, R, S, k: int, theta: int = THETA_MAX) -> Pairs:
         r, s = _u32(R), _u32(S)
         return self._pairs(self.o.lib.og_kcp_bruteforce, _ptr(r, C.c_uint32), len(r),
@@ -204,6 +238,34 @@ class OGraph:
 def _points(P) -> np.ndarray:
     a = np.ascontiguousarray(np.asarray(P, dtype=np.uint32).reshape(-1, 3))
     return a if len(a) else np.zeros((1, 3), np.uint32)[:0]
+
+
+def host_cores() -> int:
+    """Cores this process may run on (its CPU affinity)."""
+    try:
+        return len(os.sched_getaffinity(0))
+    except (AttributeError, OSError):
+        return os.cpu_count() or 1
+
+
+def cpu_model() -> str:
+    """The host CPU's model name, from /proc/cpuinfo (x86: "model name"; Arm: the
+    implementer and part numbers when no name is given)."""
+    try:
+        txt = open("/proc/cpuinfo").read()
+    except OSError:
+        return "unknown"
+    fields = {}
+    for line in txt.splitlines():
+        if ":" in line:
+            k, v = line.split(":", 1)
+            fields.setdefault(k.strip().lower(), v.strip())
+    for key in ("model name", "cpu model", "hardware"):
+        if fields.get(key):
+            return fields[key]
+    if "cpu part" in fields:
+        return f"Arm implementer {fields.get('cpu implementer', '?')} part {fields['cpu part']}"
+    return "unknown"
 
 
 _default: Oracle | None = None

@@ -43,6 +43,8 @@
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
+#include <stdatomic.h>
+#include <pthread.h>
 
 #define OG_OK 0
 #define OG_EINVAL 1
@@ -184,41 +186,101 @@ static og_item heap_pop(og_heap *h) {
 
 /* --------------------------------------------------------- bounded Dijkstra ---- */
 
-/* Shortest distances from src, bounded: a node is reached only through paths whose
- * every prefix costs <= bound (a path cost above the bound ends the search, as in
- * Algorithm 4).  dist[] receives OG_INF for nodes beyond the bound or unreachable.
- * *arcs (if not NULL) is incremented by the out-degree of every settled node: the
- * arcs a plain per-source search must look at. */
-int og_sssp(const og_graph *g, uint32_t src, uint64_t bound, uint64_t *dist, uint64_t *arcs) {
-    if (src >= g->n) return OG_EINVAL;
-    for (uint32_t x = 0; x < g->n; x++) dist[x] = OG_INF;
-    uint8_t *done = (uint8_t *)calloc(g->n, 1);
-    og_heap h = {0};
-    if (!done) return OG_ENOMEM;
-    dist[src] = 0;
-    int rc = heap_push(&h, 0, src);
-    while (rc == OG_OK && h.len > 0) {
-        og_item it = heap_pop(&h);
-        if (done[it.node] || it.key != dist[it.node]) continue; /* stale entry */
+/* The state of one bounded search, reused from source to source.  At rest dist[] is
+ * OG_INF and done[] is 0 for every node; a search lists in seen[] every node it gave a
+ * finite distance (each once), and state_clear puts back only those, so a search costs
+ * what its ball costs instead of a pass over all n nodes. */
+typedef struct {
+    uint32_t n;
+    uint64_t *dist;
+    uint8_t *done;
+    uint32_t *seen;
+    uint64_t nseen;
+    og_heap h;
+} og_state;
+
+static void state_free(og_state *s) {
+    free(s->dist);
+    free(s->done);
+    free(s->seen);
+    free(s->h.a);
+    memset(s, 0, sizeof(*s));
+}
+
+static int state_init(og_state *s, uint32_t n) {
+    memset(s, 0, sizeof(*s));
+    s->n = n;
+    s->dist = (uint64_t *)malloc(((size_t)n + 1) * sizeof(uint64_t));
+    s->done = (uint8_t *)calloc((size_t)n + 1, 1);
+    s->seen = (uint32_t *)malloc(((size_t)n + 1) * sizeof(uint32_t));
+    if (!s->dist || !s->done || !s->seen) { state_free(s); return OG_ENOMEM; }
+    for (uint32_t x = 0; x < n; x++) s->dist[x] = OG_INF;
+    return OG_OK;
+}
+
+/* Back to rest: every node the last search reached gets OG_INF and not-done again. */
+static void state_clear(og_state *s) {
+    for (uint64_t i = 0; i < s->nseen; i++) {
+        s->dist[s->seen[i]] = OG_INF;
+        s->done[s->seen[i]] = 0;
+    }
+    s->nseen = 0;
+    s->h.len = 0;
+}
+
+/* A tentative distance d for node x (smaller than its current one), queued in the heap. */
+static int state_reach(og_state *s, uint32_t x, uint64_t d) {
+    if (s->dist[x] == OG_INF) s->seen[s->nseen++] = x;
+    s->dist[x] = d;
+    return heap_push(&s->h, d, x);
+}
+
+/* The settled distance of x after a search: OG_INF when x lies beyond the bound or was
+ * never reached. */
+static uint64_t state_dist(const og_state *s, uint32_t x) { return s->done[x] ? s->dist[x] : OG_INF; }
+
+/* Bounded Dijkstra from nseeds seeds (node seed[i] at distance sd[i]; a seed above the
+ * bound is left out): a node is settled only through paths whose every prefix costs
+ * <= bound -- a path cost above the bound ends the search, as in Algorithm 4.  The
+ * state must be at rest.  *arcs (if not NULL) grows by the out-degree of every settled
+ * node: the arcs a plain per-source search must look at. */
+static int search_seeds(const og_graph *g, og_state *s, int nseeds, const uint32_t *seed,
+                        const uint64_t *sd, uint64_t bound, uint64_t *arcs) {
+    int rc = OG_OK;
+    for (int i = 0; i < nseeds && rc == OG_OK; i++) {
+        if (sd[i] > bound || sd[i] >= s->dist[seed[i]]) continue;
+        rc = state_reach(s, seed[i], sd[i]);
+    }
+    while (rc == OG_OK && s->h.len > 0) {
+        og_item it = heap_pop(&s->h);
+        if (s->done[it.node] || it.key != s->dist[it.node]) continue; /* stale entry */
         if (it.key > bound) break;
-        done[it.node] = 1;
+        s->done[it.node] = 1;
         if (arcs) *arcs += g->off[it.node + 1] - g->off[it.node];
         for (uint64_t e = g->off[it.node]; e < g->off[it.node + 1]; e++) {
             uint64_t nd = it.key + g->w[e];
             uint32_t y = g->to[e];
             if (nd > bound) continue;
-            if (nd < dist[y]) {
-                dist[y] = nd;
-                rc = heap_push(&h, nd, y);
+            if (nd < s->dist[y]) {
+                rc = state_reach(s, y, nd);
                 if (rc) break;
             }
         }
     }
-    /* nodes that were reached but never settled lie beyond the bound */
-    for (uint32_t x = 0; x < g->n; x++)
-        if (!done[x]) dist[x] = OG_INF;
-    free(done);
-    free(h.a);
+    return rc;
+}
+
+/* Shortest distances from src, bounded as above, into dist[0 .. n): OG_INF for nodes
+ * beyond the bound or unreachable. */
+int og_sssp(const og_graph *g, uint32_t src, uint64_t bound, uint64_t *dist, uint64_t *arcs) {
+    if (src >= g->n) return OG_EINVAL;
+    og_state s;
+    int rc = state_init(&s, g->n);
+    if (rc) return rc;
+    const uint64_t zero = 0;
+    rc = search_seeds(g, &s, 1, &src, &zero, bound, arcs);
+    for (uint32_t x = 0; x < g->n; x++) dist[x] = state_dist(&s, x);
+    state_free(&s);
     return rc;
 }
 
@@ -287,6 +349,36 @@ static int check_sets(uint32_t n, const uint32_t *R, uint32_t nR, const uint32_t
     return OG_OK;
 }
 
+/* A growable list of triples. */
+typedef struct {
+    og_triple *a;
+    uint64_t n, cap;
+} og_list;
+
+static int list_add(og_list *l, uint32_t u, uint32_t v, uint64_t d) {
+    if (l->n == l->cap) {
+        uint64_t nc = l->cap ? 2 * l->cap : 1024;
+        og_triple *na = (og_triple *)realloc(l->a, nc * sizeof(og_triple));
+        if (!na) return OG_ENOMEM;
+        l->a = na;
+        l->cap = nc;
+    }
+    l->a[l->n].u = u; l->a[l->n].v = v; l->a[l->n].d = d; l->n++;
+    return OG_OK;
+}
+
+/* The pairs of one source u: every member of S its search settled (all lie within the
+ * bound), appended to l in the order reached. */
+static int emit_source(const og_state *s, const uint8_t *inS, uint32_t u, og_list *l) {
+    for (uint64_t i = 0; i < s->nseen; i++) {
+        uint32_t x = s->seen[i];
+        if (!inS[x] || !s->done[x]) continue;
+        int rc = list_add(l, u, x, s->dist[x]);
+        if (rc) return rc;
+    }
+    return OG_OK;
+}
+
 /* theta-join: one bounded search from every u in R (Section 4, local processing: a
  * best-first search from each element of R that tests every reached node for
  * membership in S), every pair with dist <= theta, sorted by (u, v). */
@@ -297,30 +389,23 @@ int og_join(const og_graph *g, const uint32_t *R, uint32_t nR, const uint32_t *S
     uint8_t *inS = NULL;
     int rc = check_sets(g->n, R, nR, S, nS, &inS);
     if (rc) return rc;
-    uint64_t *dist = (uint64_t *)malloc(((size_t)g->n + 1) * sizeof(uint64_t));
-    uint64_t cap = 1024, n = 0;
-    og_triple *t = (og_triple *)malloc(cap * sizeof(og_triple));
-    if (!dist || !t) { free(dist); free(t); free(inS); return OG_ENOMEM; }
+    og_state s;
+    og_list l = {0};
+    rc = state_init(&s, g->n);
+    const uint64_t zero = 0;
     for (uint32_t i = 0; i < nR && rc == OG_OK; i++) {
-        rc = og_sssp(g, R[i], theta, dist, &out->arcs);
-        for (uint32_t x = 0; x < g->n && rc == OG_OK; x++) {
-            if (!inS[x] || dist[x] == OG_INF) continue;
-            if (n == cap) {
-                og_triple *nt = (og_triple *)realloc(t, 2 * cap * sizeof(og_triple));
-                if (!nt) { rc = OG_ENOMEM; break; }
-                t = nt;
-                cap *= 2;
-            }
-            t[n].u = R[i]; t[n].v = x; t[n].d = dist[x]; n++;
-        }
+        rc = search_seeds(g, &s, 1, &R[i], &zero, theta, &out->arcs);
+        if (rc == OG_OK) rc = emit_source(&s, inS, R[i], &l);
+        state_clear(&s);
     }
     if (rc == OG_OK) {
-        qsort(t, n, sizeof(og_triple), cmp_uv);
+        if (l.n) qsort(l.a, l.n, sizeof(og_triple), cmp_uv);
         uint64_t arcs = out->arcs;
-        rc = store_pairs(t, n, out);
+        rc = store_pairs(l.a, l.n, out);
         out->arcs = arcs;
     }
-    free(t); free(dist); free(inS);
+    state_free(&s);
+    free(l.a); free(inS);
     return rc;
 }
 
@@ -364,11 +449,66 @@ static void kheap_offer(og_kheap *h, og_triple c) {
     }
 }
 
+/* The bound of kCP's local search: theta, lowered to the d of the worst held pair once k
+ * pairs are held (Algorithm 3's global threshold), and to *shared when several threads
+ * search (each publishes its own k-th best; any thread's k-th best is an upper bound on
+ * the global k-th distance). */
+static uint64_t kcp_bound(uint64_t theta, const og_kheap *kh, _Atomic uint64_t *shared) {
+    uint64_t bound = theta;
+    if (kh->len == kh->k && kh->a[0].d < bound) bound = kh->a[0].d;
+    if (shared) {
+        uint64_t b = atomic_load_explicit(shared, memory_order_relaxed);
+        if (b < bound) bound = b;
+    }
+    return bound;
+}
+
+/* Lower *shared to b (when given). */
+static void publish_bound(_Atomic uint64_t *shared, uint64_t b) {
+    if (!shared) return;
+    uint64_t cur = atomic_load_explicit(shared, memory_order_relaxed);
+    while (b < cur && !atomic_compare_exchange_weak_explicit(shared, &cur, b, memory_order_relaxed,
+                                                             memory_order_relaxed)) {
+    }
+}
+
+/* kCP's local search from u (Section 4): best-first, bounded by kcp_bound; every settled
+ * member of S is offered to the k best held.  A node is dropped only when its cost is
+ * greater than the bound, so pairs tied with the k-th survive for the (d, u, v)
+ * tie-break.  The state must be at rest and is left for the caller to clear. */
+static int kcp_source(const og_graph *g, og_state *s, const uint8_t *inS, uint32_t u, uint64_t theta,
+                      og_kheap *kh, uint64_t *arcs, _Atomic uint64_t *shared) {
+    int rc = state_reach(s, u, 0);
+    while (rc == OG_OK && s->h.len > 0) {
+        og_item it = heap_pop(&s->h);
+        if (s->done[it.node] || it.key != s->dist[it.node]) continue;
+        uint64_t bound = kcp_bound(theta, kh, shared);
+        if (it.key > bound) break; /* kcp: cut at the bound */
+        s->done[it.node] = 1;
+        *arcs += g->off[it.node + 1] - g->off[it.node];
+        if (inS[it.node]) {
+            og_triple c;
+            c.d = it.key; c.u = u; c.v = it.node;
+            kheap_offer(kh, c);
+            if (kh->len == kh->k) publish_bound(shared, kh->a[0].d);
+            bound = kcp_bound(theta, kh, shared);
+        }
+        for (uint64_t e = g->off[it.node]; e < g->off[it.node + 1]; e++) {
+            uint64_t nd = it.key + g->w[e];
+            uint32_t y = g->to[e];
+            if (nd > bound) continue;
+            if (nd < s->dist[y]) {
+                rc = state_reach(s, y, nd);
+                if (rc) break;
+            }
+        }
+    }
+    return rc;
+}
+
 /* kCP, the paper's local search with a shrinking bound: from every u in R a
  * best-first search whose bound is min(theta, d of the worst held pair once k pairs are
- * held) (Section 4; the global threshold of Algorithm 3).  A node is dropped only when
- * its cost is greater than the bound, so pairs tied with the k-th survive for the
- * (d, u, v) tie-break.  Result sorted by (d, u, v). */
+ * held) (Section 4; the global threshold of Algorithm 3).  Result sorted by (d, u, v). */
 int og_kcp(const og_graph *g, const uint32_t *R, uint32_t nR, const uint32_t *S, uint32_t nS,
            uint64_t k, uint64_t theta, og_pairs *out) {
     memset(out, 0, sizeof(*out));
@@ -380,50 +520,21 @@ int og_kcp(const og_graph *g, const uint32_t *R, uint32_t nR, const uint32_t *S,
     og_kheap kh = {0};
     kh.k = k;
     kh.a = (og_triple *)malloc((hcap ? hcap : 1) * sizeof(og_triple));
-    uint64_t *dist = (uint64_t *)malloc(((size_t)g->n + 1) * sizeof(uint64_t));
-    uint8_t *done = (uint8_t *)malloc(g->n ? g->n : 1);
-    og_heap h = {0};
-    if (!kh.a || !dist || !done) { rc = OG_ENOMEM; goto out; }
+    og_state s;
+    rc = state_init(&s, g->n);
+    if (rc == OG_OK && !kh.a) rc = OG_ENOMEM;
     for (uint32_t i = 0; i < nR && rc == OG_OK; i++) {
-        uint32_t u = R[i];
-        for (uint32_t x = 0; x < g->n; x++) { dist[x] = OG_INF; done[x] = 0; }
-        h.len = 0;
-        dist[u] = 0;
-        rc = heap_push(&h, 0, u);
-        while (rc == OG_OK && h.len > 0) {
-            og_item it = heap_pop(&h);
-            if (done[it.node] || it.key != dist[it.node]) continue;
-            uint64_t bound = theta;
-            if (kh.len == kh.k && kh.a[0].d < bound) bound = kh.a[0].d;
-            if (it.key > bound) break;
-            done[it.node] = 1;
-            out->arcs += g->off[it.node + 1] - g->off[it.node];
-            if (inS[it.node]) {
-                og_triple c;
-                c.d = it.key; c.u = u; c.v = it.node;
-                kheap_offer(&kh, c);
-                if (kh.len == kh.k && kh.a[0].d < bound) bound = kh.a[0].d;
-            }
-            for (uint64_t e = g->off[it.node]; e < g->off[it.node + 1]; e++) {
-                uint64_t nd = it.key + g->w[e];
-                uint32_t y = g->to[e];
-                if (nd > bound) continue;
-                if (nd < dist[y]) {
-                    dist[y] = nd;
-                    rc = heap_push(&h, nd, y);
-                    if (rc) break;
-                }
-            }
-        }
+        rc = kcp_source(g, &s, inS, R[i], theta, &kh, &out->arcs, NULL);
+        state_clear(&s);
     }
     if (rc == OG_OK) {
-        qsort(kh.a, kh.len, sizeof(og_triple), cmp_duv);
+        if (kh.len) qsort(kh.a, kh.len, sizeof(og_triple), cmp_duv);
         uint64_t arcs = out->arcs;
         rc = store_pairs(kh.a, kh.len, out);
         out->arcs = arcs;
     }
-out:
-    free(kh.a); free(dist); free(done); free(h.a); free(inS);
+    state_free(&s);
+    free(kh.a); free(inS);
     return rc;
 }
 
@@ -445,6 +556,192 @@ int og_kcp_bruteforce(const og_graph *g, const uint32_t *R, uint32_t nR, const u
     rc = store_pairs(t, keep, out);
     out->arcs = arcs;
     free(t);
+    return rc;
+}
+
+/* ------------------------------------------------------- all host cores ---- */
+
+/* The same per-source searches on several threads, to time the oracle on every core of
+ * a host.  R is taken in increasing id and cut into chunks of consecutive sources; a
+ * thread takes the next chunk, searches its sources one after another with a state of
+ * its own, and sorts the chunk's pairs by (u, v), so the chunks' lists laid end to end
+ * are the join in (u, v) order.  For kCP every thread keeps its own k best and the
+ * threads share one bound (see kcp_bound); the k best of all threads' k best are the
+ * answer, since every pair of the global k best is among its own thread's k best. */
+
+#define OG_CHUNK 16
+
+static int cmp_u32(const void *pa, const void *pb) {
+    uint32_t x = *(const uint32_t *)pa, y = *(const uint32_t *)pb;
+    return x < y ? -1 : x > y;
+}
+
+typedef struct {
+    const og_graph *g;
+    const uint32_t *R; /* ascending */
+    uint32_t nR;
+    const uint8_t *inS;
+    uint64_t theta, k;
+    _Atomic uint64_t next;  /* next chunk to take */
+    _Atomic uint64_t bound; /* kCP: the least k-th best published by any thread */
+    _Atomic int rc;
+    og_list *chunk;         /* join: per chunk its pairs */
+    og_kheap *held;         /* kCP: per thread its k best */
+    uint64_t *arcs;         /* per thread */
+} og_job;
+
+typedef struct {
+    og_job *job;
+    uint32_t t;
+} og_worker;
+
+static void *join_worker(void *arg) {
+    og_worker *w = (og_worker *)arg;
+    og_job *j = w->job;
+    og_state s;
+    int rc = state_init(&s, j->g->n);
+    const uint64_t zero = 0, nchunks = ((uint64_t)j->nR + OG_CHUNK - 1) / OG_CHUNK;
+    while (rc == OG_OK && atomic_load(&j->rc) == OG_OK) {
+        uint64_t c = atomic_fetch_add(&j->next, 1);
+        if (c >= nchunks) break;
+        og_list *l = &j->chunk[c];
+        for (uint64_t i = c * OG_CHUNK; i < (c + 1) * OG_CHUNK && i < j->nR && rc == OG_OK; i++) {
+            rc = search_seeds(j->g, &s, 1, &j->R[i], &zero, j->theta, &j->arcs[w->t]);
+            if (rc == OG_OK) rc = emit_source(&s, j->inS, j->R[i], l);
+            state_clear(&s);
+        }
+        if (rc == OG_OK && l->n) qsort(l->a, l->n, sizeof(og_triple), cmp_uv);
+    }
+    state_free(&s);
+    if (rc) atomic_store(&j->rc, rc);
+    return NULL;
+}
+
+static void *kcp_worker(void *arg) {
+    og_worker *w = (og_worker *)arg;
+    og_job *j = w->job;
+    og_state s;
+    int rc = state_init(&s, j->g->n);
+    const uint64_t nchunks = ((uint64_t)j->nR + OG_CHUNK - 1) / OG_CHUNK;
+    while (rc == OG_OK && atomic_load(&j->rc) == OG_OK) {
+        uint64_t c = atomic_fetch_add(&j->next, 1);
+        if (c >= nchunks) break;
+        for (uint64_t i = c * OG_CHUNK; i < (c + 1) * OG_CHUNK && i < j->nR && rc == OG_OK; i++) {
+            rc = kcp_source(j->g, &s, j->inS, j->R[i], j->theta, &j->held[w->t], &j->arcs[w->t], &j->bound);
+            state_clear(&s);
+        }
+    }
+    state_free(&s);
+    if (rc) atomic_store(&j->rc, rc);
+    return NULL;
+}
+
+/* Run fn on nthreads threads (at least one) over the job. */
+static int run_threads(og_job *j, uint32_t nthreads, void *(*fn)(void *)) {
+    pthread_t *tid = (pthread_t *)calloc(nthreads, sizeof(pthread_t));
+    og_worker *wk = (og_worker *)calloc(nthreads, sizeof(og_worker));
+    uint8_t *started = (uint8_t *)calloc(nthreads, 1);
+    if (!tid || !wk || !started) { free(tid); free(wk); free(started); return OG_ENOMEM; }
+    for (uint32_t t = 0; t < nthreads; t++) {
+        wk[t].job = j;
+        wk[t].t = t;
+        started[t] = pthread_create(&tid[t], NULL, fn, &wk[t]) == 0;
+    }
+    uint32_t ran = 0;
+    for (uint32_t t = 0; t < nthreads; t++)
+        if (started[t]) { pthread_join(tid[t], NULL); ran++; }
+    if (ran == 0) fn(&wk[0]); /* no thread could be started: run here */
+    free(tid); free(wk); free(started);
+    return atomic_load(&j->rc);
+}
+
+static int job_init(og_job *j, const og_graph *g, const uint32_t *R, uint32_t nR, const uint8_t *inS,
+                    uint64_t theta, uint64_t k, uint32_t nthreads, uint32_t **Rsorted) {
+    memset(j, 0, sizeof(*j));
+    uint32_t *r = (uint32_t *)malloc(((size_t)nR + 1) * sizeof(uint32_t));
+    j->arcs = (uint64_t *)calloc(nthreads, sizeof(uint64_t));
+    if (!r || !j->arcs) { free(r); free(j->arcs); return OG_ENOMEM; }
+    if (nR) memcpy(r, R, (size_t)nR * sizeof(uint32_t));
+    qsort(r, nR, sizeof(uint32_t), cmp_u32);
+    j->g = g; j->R = r; j->nR = nR; j->inS = inS; j->theta = theta; j->k = k;
+    atomic_init(&j->next, 0);
+    atomic_init(&j->bound, theta);
+    atomic_init(&j->rc, OG_OK);
+    *Rsorted = r;
+    return OG_OK;
+}
+
+/* The theta-join of og_join on nthreads threads: the same pairs in the same order. */
+int og_join_mt(const og_graph *g, const uint32_t *R, uint32_t nR, const uint32_t *S, uint32_t nS,
+               uint64_t theta, uint32_t nthreads, og_pairs *out) {
+    memset(out, 0, sizeof(*out));
+    if (theta > OG_THETA_MAX) return OG_EINVAL;
+    if (nthreads == 0) nthreads = 1;
+    uint8_t *inS = NULL;
+    int rc = check_sets(g->n, R, nR, S, nS, &inS);
+    if (rc) return rc;
+    og_job j;
+    uint32_t *r = NULL;
+    rc = job_init(&j, g, R, nR, inS, theta, 0, nthreads, &r);
+    const uint64_t nchunks = ((uint64_t)nR + OG_CHUNK - 1) / OG_CHUNK;
+    if (rc == OG_OK) {
+        j.chunk = (og_list *)calloc(nchunks ? nchunks : 1, sizeof(og_list));
+        if (!j.chunk) rc = OG_ENOMEM;
+    }
+    if (rc == OG_OK) rc = run_threads(&j, nthreads, join_worker);
+    if (rc == OG_OK) {
+        og_list all = {0};
+        for (uint64_t c = 0; c < nchunks && rc == OG_OK; c++)
+            for (uint64_t i = 0; i < j.chunk[c].n && rc == OG_OK; i++)
+                rc = list_add(&all, j.chunk[c].a[i].u, j.chunk[c].a[i].v, j.chunk[c].a[i].d);
+        if (rc == OG_OK) rc = store_pairs(all.a, all.n, out);
+        for (uint32_t t = 0; t < nthreads; t++) out->arcs += j.arcs[t];
+        free(all.a);
+    }
+    if (j.chunk)
+        for (uint64_t c = 0; c < nchunks; c++) free(j.chunk[c].a);
+    free(j.chunk); free(j.arcs); free(r); free(inS);
+    return rc;
+}
+
+/* kCP of og_kcp on nthreads threads: the same k pairs in the same (d, u, v) order. */
+int og_kcp_mt(const og_graph *g, const uint32_t *R, uint32_t nR, const uint32_t *S, uint32_t nS,
+              uint64_t k, uint64_t theta, uint32_t nthreads, og_pairs *out) {
+    memset(out, 0, sizeof(*out));
+    if (theta > OG_THETA_MAX || k == 0) return OG_EINVAL;
+    if (nthreads == 0) nthreads = 1;
+    uint8_t *inS = NULL;
+    int rc = check_sets(g->n, R, nR, S, nS, &inS);
+    if (rc) return rc;
+    og_job j;
+    uint32_t *r = NULL;
+    rc = job_init(&j, g, R, nR, inS, theta, k, nthreads, &r);
+    const uint64_t hcap = k < (uint64_t)nR * nS ? k : (uint64_t)nR * nS;
+    if (rc == OG_OK) {
+        j.held = (og_kheap *)calloc(nthreads, sizeof(og_kheap));
+        if (!j.held) rc = OG_ENOMEM;
+        for (uint32_t t = 0; t < nthreads && rc == OG_OK; t++) {
+            j.held[t].k = k;
+            j.held[t].a = (og_triple *)malloc((hcap ? hcap : 1) * sizeof(og_triple));
+            if (!j.held[t].a) rc = OG_ENOMEM;
+        }
+    }
+    if (rc == OG_OK) rc = run_threads(&j, nthreads, kcp_worker);
+    if (rc == OG_OK) {
+        og_list all = {0};
+        for (uint32_t t = 0; t < nthreads && rc == OG_OK; t++)
+            for (uint64_t i = 0; i < j.held[t].len && rc == OG_OK; i++)
+                rc = list_add(&all, j.held[t].a[i].u, j.held[t].a[i].v, j.held[t].a[i].d);
+        if (rc == OG_OK) {
+            if (all.n) qsort(all.a, all.n, sizeof(og_triple), cmp_duv);
+            rc = store_pairs(all.a, all.n < k ? all.n : k, out);
+        }
+        for (uint32_t t = 0; t < nthreads; t++) out->arcs += j.arcs[t];
+        free(all.a);
+    }
+    if (j.held)
+        for (uint32_t t = 0; t < nthreads; t++) free(j.held[t].a);
+    free(j.held); free(j.arcs); free(r); free(inS);
     return rc;
 }
 
@@ -501,41 +798,11 @@ static int check_points(const og_graph *g, const og_point *P, uint32_t nP, uint6
 }
 
 /* Bounded search from a point: Dijkstra seeded at a with t and at b with w - t (seeds
- * above the bound are left out), otherwise as og_sssp. */
-static int sssp_point(const og_graph *g, og_point p, uint64_t w, uint64_t bound, uint64_t *dist) {
-    for (uint32_t x = 0; x < g->n; x++) dist[x] = OG_INF;
-    uint8_t *done = (uint8_t *)calloc(g->n, 1);
-    og_heap h = {0};
-    if (!done) return OG_ENOMEM;
-    int rc = OG_OK;
+ * above the bound are left out), otherwise as og_sssp.  The state must be at rest. */
+static int sssp_point(const og_graph *g, og_state *s, og_point p, uint64_t w, uint64_t bound) {
     const uint32_t seed[2] = {p.a, p.b};
     const uint64_t sd[2] = {p.t, w - p.t};
-    for (int i = 0; i < 2 && rc == OG_OK; i++) {
-        if (sd[i] > bound || sd[i] >= dist[seed[i]]) continue;
-        dist[seed[i]] = sd[i];
-        rc = heap_push(&h, sd[i], seed[i]);
-    }
-    while (rc == OG_OK && h.len > 0) {
-        og_item it = heap_pop(&h);
-        if (done[it.node] || it.key != dist[it.node]) continue;
-        if (it.key > bound) break;
-        done[it.node] = 1;
-        for (uint64_t e = g->off[it.node]; e < g->off[it.node + 1]; e++) {
-            uint64_t nd = it.key + g->w[e];
-            uint32_t y = g->to[e];
-            if (nd > bound) continue;
-            if (nd < dist[y]) {
-                dist[y] = nd;
-                rc = heap_push(&h, nd, y);
-                if (rc) break;
-            }
-        }
-    }
-    for (uint32_t x = 0; x < g->n; x++)
-        if (!done[x]) dist[x] = OG_INF;
-    free(done);
-    free(h.a);
-    return rc;
+    return search_seeds(g, s, 2, seed, sd, bound, NULL);
 }
 
 /* theta-join of points: every (i, j), R[i] to S[j] within theta, with its distance,
@@ -548,19 +815,21 @@ int og_join_points(const og_graph *g, const og_point *R, uint32_t nR, const og_p
     if (theta > OG_THETA_MAX) return OG_EINVAL;
     uint64_t *wR = (uint64_t *)malloc(((size_t)nR + 1) * sizeof(uint64_t));
     uint64_t *wS = (uint64_t *)malloc(((size_t)nS + 1) * sizeof(uint64_t));
-    uint64_t *dist = (uint64_t *)malloc(((size_t)g->n + 1) * sizeof(uint64_t));
     uint64_t cap = 1024, n = 0;
     og_triple *t = (og_triple *)malloc(cap * sizeof(og_triple));
-    int rc = (!wR || !wS || !dist || !t) ? OG_ENOMEM : OG_OK;
+    og_state st;
+    int rc = (!wR || !wS || !t) ? OG_ENOMEM : state_init(&st, g->n);
+    const int have_state = (wR && wS && t && rc == OG_OK);
     if (rc == OG_OK) rc = check_points(g, R, nR, wR);
     if (rc == OG_OK) rc = check_points(g, S, nS, wS);
     for (uint32_t i = 0; i < nR && rc == OG_OK; i++) {
-        rc = sssp_point(g, R[i], wR[i], theta, dist);
+        rc = sssp_point(g, &st, R[i], wR[i], theta);
         for (uint32_t j = 0; j < nS && rc == OG_OK; j++) {
             const og_point q = S[j];
+            const uint64_t da = state_dist(&st, q.a), db = state_dist(&st, q.b);
             uint64_t d = OG_INF;
-            if (dist[q.a] != OG_INF) d = dist[q.a] + q.t;
-            if (dist[q.b] != OG_INF && dist[q.b] + (wS[j] - q.t) < d) d = dist[q.b] + (wS[j] - q.t);
+            if (da != OG_INF) d = da + q.t;
+            if (db != OG_INF && db + (wS[j] - q.t) < d) d = db + (wS[j] - q.t);
             if (q.a == R[i].a && q.b == R[i].b) {
                 uint64_t gap = q.t > R[i].t ? q.t - R[i].t : R[i].t - q.t;
                 if (gap < d) d = gap;
@@ -578,12 +847,14 @@ int og_join_points(const og_graph *g, const og_point *R, uint32_t nR, const og_p
             }
             t[n].u = i; t[n].v = j; t[n].d = d; n++;
         }
+        state_clear(&st);
     }
     if (rc == OG_OK) {
         qsort(t, n, sizeof(og_triple), cmp_uv);
         rc = store_pairs(t, n, out);
     }
-    free(t); free(dist); free(wR); free(wS);
+    if (have_state) state_free(&st);
+    free(t); free(wR); free(wS);
     return rc;
 }
 

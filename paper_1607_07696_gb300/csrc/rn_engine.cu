@@ -1938,11 +1938,21 @@ static size_t search_smem(uint32_t H, bool gmap, int threads) {
     return (gmap ? 0 : size_t(H) * 12) + size_t(qcap_of(threads)) * 8 + size_t(icap_of(threads)) * 20;
 }
 
+// A kernel's attributes (its dynamic shared-memory limit, the carveout) belong to the
+// device that was current when they were set, so every kernel sets them once per device.
+constexpr int MAX_DEVICES = 64;
+static int attr_device() {
+    int d = 0;
+    RN_CUDA(cudaGetDevice(&d));
+    if (d < 0 || d >= MAX_DEVICES) fail(RN_EINVAL, "device ordinal out of range");
+    return d;
+}
+
 template <int L, bool GMAP, int THREADS>
 static void launch_search(const SearchArgs &a, uint32_t grid, cudaStream_t st) {
     const size_t smem = search_smem(a.H, GMAP, THREADS);
-    static std::once_flag once;
-    std::call_once(once, [&] {
+    static std::once_flag once[MAX_DEVICES];
+    std::call_once(once[attr_device()], [&] {
         RN_CUDA(cudaFuncSetAttribute(k_tile_search<L, GMAP, THREADS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                      int(search_smem(THREADS == NARROW ? SMEM_H : SMEM_HW, GMAP, THREADS))));
         RN_CUDA(cudaFuncSetAttribute(k_tile_search<L, GMAP, THREADS>,
@@ -2214,8 +2224,8 @@ static Control search_all(const DeviceGraph &g, Workspace *ws, uint32_t T, Searc
 template <uint32_t MS>
 static void launch_source(const SearchArgs &a, uint32_t grid, cudaStream_t st) {
     constexpr uint32_t smem = src_warps(MS) * src_words(MS) * 4;
-    static std::once_flag once;
-    std::call_once(once, [&] {
+    static std::once_flag once[MAX_DEVICES];
+    std::call_once(once[attr_device()], [&] {
         RN_CUDA(cudaFuncSetAttribute(k_source_search<MS>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)));
         RN_CUDA(cudaFuncSetAttribute(k_source_search<MS>, cudaFuncAttributePreferredSharedMemoryCarveout, 100));
     });

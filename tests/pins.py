@@ -69,10 +69,14 @@ def pin_fw_random(o, seeds=range(60)):
             want = sorted(_fw_pairs(D, R, S, theta))
             got = g.join(R, S, theta).triples()
             assert got == want, f"seed {seed} theta {theta}: join != brute force"
+            got = g.join_mt(R, S, theta, threads=1 + seed % 4).triples()
+            assert got == want, f"seed {seed} theta {theta}: threaded join != brute force"
             byd = sorted(want, key=lambda t: (t[2], t[0], t[1]))
             for k in sorted({1, 2, 3, max(1, len(byd)), len(byd) + 1, max(1, len(byd) // 2)}):
                 kc = g.kcp(R, S, k, theta).triples()
                 assert kc == byd[:k], f"seed {seed} theta {theta} k {k}: kcp != brute force"
+                kc = g.kcp_mt(R, S, k, theta, threads=1 + seed % 4).triples()
+                assert kc == byd[:k], f"seed {seed} theta {theta} k {k}: threaded kcp != brute force"
 
 
 def pin_closed_forms(o):
@@ -137,15 +141,22 @@ def pin_invariants(o, n=3000, seed=7):
         t = g.join(S, R, theta).triples()
         assert sorted((v, u, d) for (u, v, d) in t) == j, "join not its own transpose"
         assert all(d <= theta for (_, _, d) in j), "pair beyond theta"
+        assert g.join_mt(R, S, theta, threads=5).triples() == j, "threaded join differs"
     full = sorted(g.join(R, S, THETA_MAX).triples(), key=lambda t: (t[2], t[0], t[1]))
     last = []
     for k in (1, 2, 5, 50, 51, 400, len(full), len(full) + 7):
         kc = g.kcp(R, S, k).triples()
         assert kc == full[:k], f"kcp k={k} != first k of the sorted join"
         assert kc[: len(last)] == last, "kcp not a prefix in k"
+        assert g.kcp_mt(R, S, k, threads=3).triples() == kc, f"threaded kcp k={k} differs"
         last = kc
     kb = g.kcp_bruteforce(R, S, 77, 9000).triples()
     assert g.kcp(R, S, 77, 9000).triples() == kb, "kcp with theta != brute force"
+    # kCP through a join at a doubled probe bound: the first k of the sorted join
+    for k, probe in ((1, 1), (50, 300), (400, 2000), (len(full) + 7, 5)):
+        got = g.kcp_by_join(R, S, k, probe=probe, threads=2).triples()
+        assert got == full[:k], f"kcp by join k={k} probe {probe}"
+    assert g.kcp_by_join(R, S, 77, 9000, probe=100).triples() == kb, "kcp by join with theta"
 
 
 def pin_triangle(o, seeds=range(8)):

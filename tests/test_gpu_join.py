@@ -2,7 +2,7 @@
 
 Distances are integers, so the bar is equality of every (u, v, d) triple and of the
 order (sorted by (u, v)).  Sizes run from a handful of nodes to the 264k-node road-like
-workload in full, and the 1.07M-node clustered workload on sampled sources.
+workload and the 1.07M-node clustered workload in full.
 """
 import json
 import os
@@ -193,25 +193,22 @@ def test_road264k_full(rn, oracle):
     assert st["tile_width"] == 1 and st["launches"] < 16, st["launches"]
 
 
-def test_road1070k_join_sampled(rn, oracle):
+def test_road1070k_join_full(rn, oracle):
+    """The 1.07M-node join (50,000 + 50,000 clustered nodes, theta for about 50 matches
+    per source) in full: every one of the 2.8M pairs equal to the oracle's, searched on
+    every host core."""
+    from oracle import oracle as O
+
     spec = WORKLOADS["road1070k_clustered"]
     w = I.c3_road_clustered()
     e = w.graph
     g = load(rn, e)
     theta = spec["theta_join"]
-    u, v, d = dev_join(rn, g, w.R, w.S, theta)
-    # properties that hold at any size
-    assert np.all(d <= theta)
-    key = u.astype(np.uint64) << np.uint64(32) | v.astype(np.uint64)
-    assert np.all(key[1:] > key[:-1]), "not strictly sorted by (u, v)"
-    assert np.isin(u, w.R).all() and np.isin(v, w.S).all()
-    # every pair of 300 sampled sources, against the oracle one source at a time
-    rng = np.random.default_rng(5)
-    sample = np.sort(rng.choice(w.R, size=300, replace=False))
-    og = oracle.graph(e.n, e.src, e.dst, e.w)
-    ref = og.join(sample, w.S, theta)
-    m = np.isin(u, sample)
-    assert_same((u[m], v[m], d[m]), ref, "road1070k sampled sources")
+    got = dev_join(rn, g, w.R, w.S, theta)
+    ref = oracle.graph(e.n, e.src, e.dst, e.w).join_mt(w.R, w.S, theta, O.host_cores())
+    assert len(ref) > 2_000_000
+    assert_same(got, ref, "road1070k")
+    assert_same(rn.rn_distance_join(g, w.R, w.S, theta), ref, "road1070k host")
 
 
 @pytest.mark.parametrize("T,slots", [(32, 16384), (32, 65536), (64, 1 << 17), (128, 65536)])
@@ -286,3 +283,22 @@ def test_long_segments_sorted(rn, oracle):
     small = S[:500]
     assert_same(dev_join(rn, g, R, small, theta), og.join(R, small, theta), "sparse S, placed")
     assert rn.rn_last_query_stats()["launches"] < 16
+
+
+def test_second_device(rn, oracle):
+    """A graph loaded on a second GPU after a query on the first: every search kernel
+    sets its shared-memory limit on each device it runs on, so both devices' joins (warp
+    search and tile search) equal the oracle."""
+    import torch
+
+    if torch.cuda.device_count() < 2:
+        pytest.skip("needs two GPUs")
+    e = I.road_graph(30_000, 83_100, 81)
+    R, S = I.disjoint_sets(e.n, 400, 2000, 82)
+    ref = oracle.graph(e.n, e.src, e.dst, e.w).join(R, S, 60_000)
+    for dev in (0, 1):
+        with torch.cuda.device(dev):
+            for T in (1, 32):
+                g = load(rn, e, cfg={"tile_width": T})
+                assert_same(rn.rn_distance_join(g, R, S, 60_000), ref, f"device {dev} T={T}")
+                assert rn.rn_last_query_stats()["blocks_per_sm"] >= 1

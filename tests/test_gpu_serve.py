@@ -208,29 +208,44 @@ def test_cancel_and_admission_oom(rn, world):
     srv.close()
 
 
-def test_serve6m_requests_against_oracle(rn, oracle):
-    """Requests of the serving stream on its own 6M-node graph: the small ones (|R| <= 250,
-    joins and k closest pairs) served in a mix, each equal to the oracle's answer."""
+SERVE_CHECKED = 600  # leading requests of the benchmark's 2,000-request stream
+
+
+def test_serve6m_stream_against_oracle(rn, oracle):
+    """The serving benchmark's request stream on its 6M-node graph: its first 600
+    requests (joins and k closest pairs, |R| and |S| 100-20,000) submitted at once, as the
+    saturated phase does, and every answer equal to the oracle's, element by element.
+    The oracle answers joins with its per-source searches on every host core, and k
+    closest pairs by their definition (the first k of the sorted join within a bound
+    doubled until it holds k pairs, starting from the radius the graph's measured ball
+    growth gives)."""
     import json
     import os
+
+    from oracle import oracle as O
 
     root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
     spec = json.load(open(os.path.join(root, "tests", "golden", "workloads.json")))["serve6m"]
     e = I.c5_serve_graph()
     g = rn.rn_graph_load(e.src, e.dst, e.w, e.n)
-    reqs = I.c5_requests(e.n, 300, spec["ball_coeff"])
-    small = [r for r in reqs if len(r.R) <= 250]
-    pick = [r for r in small if r.k == 0][:4] + [r for r in small if r.k][:3]
+    reqs = I.c5_requests(e.n, 2000, spec["ball_coeff"])[:SERVE_CHECKED]
+    for a, b in zip(reqs, I.c5_requests(e.n, SERVE_CHECKED, spec["ball_coeff"])):
+        assert np.array_equal(a.R, b.R) and np.array_equal(a.S, b.S) and (a.theta, a.k) == (b.theta, b.k)
     srv = rn.rn_serve_create(g)
-    tickets = [rn.rn_serve_submit(srv, r.R, r.S, r.theta, r.k) for r in pick]
-    og = oracle.graph(e.n, e.src, e.dst, e.w)
-    for i, (r, t) in enumerate(zip(pick, tickets)):
-        u, v, d = rn.rn_serve_wait(srv, t)
-        th = min(r.theta, rn.RN_THETA_MAX)
-        ref = og.join(r.R, r.S, th) if r.k == 0 else og.kcp(r.R, r.S, r.k, th)
-        assert np.array_equal(u, ref.u) and np.array_equal(v, ref.v) and np.array_equal(d.astype(np.uint64), ref.d), \
-            f"request {i} (k = {r.k}) differs from the oracle"
+    tickets = [rn.rn_serve_submit(srv, r.R, r.S, r.theta, r.k) for r in reqs]
+    got = [rn.rn_serve_wait(srv, t) for t in tickets]
     srv.close()
+    og = oracle.graph(e.n, e.src, e.dst, e.w)
+    cores = O.host_cores()
+    for i, (r, (u, v, d)) in enumerate(zip(reqs, got)):
+        th = min(r.theta, rn.RN_THETA_MAX)
+        if r.k == 0:
+            ref = og.join_mt(r.R, r.S, th, cores)
+        else:
+            ball = max(64.0, r.k * e.n / (len(r.R) * len(r.S)))
+            ref = og.kcp_by_join(r.R, r.S, r.k, th, cores, probe=int(np.sqrt(ball / spec["ball_coeff"])))
+        assert np.array_equal(u, ref.u) and np.array_equal(v, ref.v) and np.array_equal(d.astype(np.uint64), ref.d), \
+            f"request {i} (|R| {len(r.R)}, |S| {len(r.S)}, k = {r.k}) differs from the oracle"
 
 
 def test_small_joins_grouped(rn, oracle, world):

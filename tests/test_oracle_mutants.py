@@ -14,12 +14,12 @@ from oracle import oracle as O
 
 MUTANTS = {
     # the theta cut becomes exclusive (Abstract: dist <= theta is inclusive)
-    "strict_theta_cut": ("            if (nd > bound) continue;\n            if (nd < dist[y]) {\n"
-                         "                dist[y] = nd;\n                rc = heap_push(&h, nd, y);\n"
-                         "                if (rc) break;\n            }\n        }\n    }\n    /* nodes",
-                         "            if (nd >= bound) continue;\n            if (nd < dist[y]) {\n"
-                         "                dist[y] = nd;\n                rc = heap_push(&h, nd, y);\n"
-                         "                if (rc) break;\n            }\n        }\n    }\n    /* nodes"),
+    "strict_theta_cut": ("            if (nd > bound) continue;\n            if (nd < s->dist[y]) {\n"
+                         "                rc = state_reach(s, y, nd);\n                if (rc) break;\n"
+                         "            }\n        }\n    }\n    return rc;\n}\n\n/* Shortest distances",
+                         "            if (nd >= bound) continue;\n            if (nd < s->dist[y]) {\n"
+                         "                rc = state_reach(s, y, nd);\n                if (rc) break;\n"
+                         "            }\n        }\n    }\n    return rc;\n}\n\n/* Shortest distances"),
     # parallel edges keep their largest weight instead of the least
     "multi_edge_max": ("if (x->w != y->w) return x->w < y->w ? -1 : 1;",
                        "if (x->w != y->w) return x->w > y->w ? -1 : 1;"),
@@ -31,34 +31,45 @@ MUTANTS = {
     # kCP keeps the worse candidate
     "kcp_keep_worse": ("} else if (trip_less(&c, &h->a[0])) {", "} else if (trip_less(&h->a[0], &c)) {"),
     # kCP tightens its bound before k pairs are held
-    "kcp_early_bound": ("            if (kh.len == kh.k && kh.a[0].d < bound) bound = kh.a[0].d;\n            if (it.key > bound) break;",
-                        "            if (kh.len > 0 && kh.a[0].d < bound) bound = kh.a[0].d;\n            if (it.key > bound) break;"),
+    "kcp_early_bound": ("    if (kh->len == kh->k && kh->a[0].d < bound) bound = kh->a[0].d;\n    if (shared) {",
+                        "    if (kh->len > 0 && kh->a[0].d < bound) bound = kh->a[0].d;\n    if (shared) {"),
     # kCP prunes ties at the bound
-    "kcp_prune_ties": ("            if (it.key > bound) break;\n            done[it.node] = 1;\n            out->arcs",
-                       "            if (it.key >= bound && kh.len == kh.k) break;\n            done[it.node] = 1;\n            out->arcs"),
+    "kcp_prune_ties": ("        if (it.key > bound) break; /* kcp: cut at the bound */",
+                       "        if (it.key >= bound && kh->len == kh->k) break; /* kcp: cut at the bound */"),
     # heap pops the larger child: not a min-heap any more
     "heap_wrong_child": ("if (c + 1 < h->len && h->a[c + 1].key < h->a[c].key) c++;",
                          "if (c + 1 < h->len && h->a[c + 1].key > h->a[c].key) c++;"),
     # a relaxation that forgets the arc weight
-    "dropped_weight": ("            uint64_t nd = it.key + g->w[e];\n            uint32_t y = g->to[e];\n            if (nd > bound) continue;\n            if (nd < dist[y]) {\n                dist[y] = nd;\n                rc = heap_push(&h, nd, y);\n                if (rc) break;\n            }\n        }\n    }\n    /* nodes",
-                       "            uint64_t nd = it.key + 1;\n            uint32_t y = g->to[e];\n            if (nd > bound) continue;\n            if (nd < dist[y]) {\n                dist[y] = nd;\n                rc = heap_push(&h, nd, y);\n                if (rc) break;\n            }\n        }\n    }\n    /* nodes"),
+    "dropped_weight": ("            uint64_t nd = it.key + g->w[e];\n            uint32_t y = g->to[e];\n            if (nd > bound) continue;\n            if (nd < s->dist[y]) {\n                rc = state_reach(s, y, nd);\n                if (rc) break;\n            }\n        }\n    }\n    return rc;\n}\n\n/* Shortest distances",
+                       "            uint64_t nd = it.key + 1;\n            uint32_t y = g->to[e];\n            if (nd > bound) continue;\n            if (nd < s->dist[y]) {\n                rc = state_reach(s, y, nd);\n                if (rc) break;\n            }\n        }\n    }\n    return rc;\n}\n\n/* Shortest distances"),
     # the join sorted (v, u)
-    "join_sorted_vu": ("        qsort(t, n, sizeof(og_triple), cmp_uv);\n        uint64_t arcs = out->arcs;",
-                       "        qsort(t, n, sizeof(og_triple), cmp_duv);\n        uint64_t arcs = out->arcs;"),
+    "join_sorted_vu": ("        if (l.n) qsort(l.a, l.n, sizeof(og_triple), cmp_uv);\n        uint64_t arcs = out->arcs;",
+                       "        if (l.n) qsort(l.a, l.n, sizeof(og_triple), cmp_duv);\n        uint64_t arcs = out->arcs;"),
     # overlap of R and S no longer rejected
     "overlap_accepted": ("        if (S[i] >= n || mark[S[i]]) { free(mark); return OG_EINVAL; }",
                          "        if (S[i] >= n || mark[S[i]] == 2) { free(mark); return OG_EINVAL; }"),
     # emits a pair for every reached node, not only members of S
-    "emit_non_members": ("            if (!inS[x] || dist[x] == OG_INF) continue;",
-                         "            if (dist[x] == OG_INF) continue;"),
+    "emit_non_members": ("        if (!inS[x] || !s->done[x]) continue;",
+                         "        if (!s->done[x]) continue;"),
+    # the sparse reset forgets the settled marks: the next source cannot settle them
+    "reset_keeps_done": ("        s->dist[s->seen[i]] = OG_INF;\n        s->done[s->seen[i]] = 0;\n",
+                         "        s->dist[s->seen[i]] = OG_INF;\n"),
+    # the sparse reset forgets the distances: the next source starts from stale ones
+    "reset_keeps_dist": ("        s->dist[s->seen[i]] = OG_INF;\n        s->done[s->seen[i]] = 0;\n",
+                         "        s->done[s->seen[i]] = 0;\n"),
+    # several threads: a chunk's pairs left unsorted before the chunks are laid end to end
+    "mt_chunk_unsorted": ("        if (rc == OG_OK && l->n) qsort(l->a, l->n, sizeof(og_triple), cmp_uv);\n", ""),
+    # several threads: kCP keeps every thread's k best instead of the k best of them all
+    "mt_kcp_no_cut": ("            rc = store_pairs(all.a, all.n < k ? all.n : k, out);",
+                      "            rc = store_pairs(all.a, all.n, out);"),
     # points: the meeting of two points along their shared edge forgotten
     "points_no_same_edge": ("                uint64_t gap = q.t > R[i].t ? q.t - R[i].t : R[i].t - q.t;\n                if (gap < d) d = gap;\n",
                             ""),
     # points: the search seeded at the far end with t instead of w - t
     "points_far_seed": ("    const uint64_t sd[2] = {p.t, w - p.t};", "    const uint64_t sd[2] = {p.t, p.t};"),
     # points: an S point reached from its far end at t instead of w - t
-    "points_far_offset": ("if (dist[q.b] != OG_INF && dist[q.b] + (wS[j] - q.t) < d) d = dist[q.b] + (wS[j] - q.t);",
-                          "if (dist[q.b] != OG_INF && dist[q.b] + q.t < d) d = dist[q.b] + q.t;"),
+    "points_far_offset": ("if (db != OG_INF && db + (wS[j] - q.t) < d) d = db + (wS[j] - q.t);",
+                          "if (db != OG_INF && db + q.t < d) d = db + q.t;"),
     # points: on a shared edge named the other way round, the position not mirrored
     "points_unmirrored": ("                uint64_t pos = wS[j] - q.t; /* S[j]'s distance from R[i].a */",
                           "                uint64_t pos = q.t; /* S[j]'s distance from R[i].a */"),
