@@ -90,16 +90,20 @@ typedef struct {
                              warp map, 8192 slots, go to the tile search of width 32);
                              32, 64 or 128: lanes of a slab row, the most sources one
                              thread block searches together; 0: the warp search while the
-                             balls met so far, scaled to the query's bound, fit a warp
-                             map, else tiles of 32 (k closest pairs and batches always
-                             run tiles, 32 wide unless set) */
+                             balls met so far, scaled to the query's bound (or, before any
+                             search, estimated from it), fit a warp map, else tiles of 32
+                             (k closest pairs decides so for each of its radius passes;
+                             batches run tiles, 32 wide unless set) */
     uint32_t tile_sources;/* sources per tile, <= tile_width; 0 spreads R over whole
                              waves of resident blocks */
     uint32_t delta;       /* bucket width of the delta-stepping search, in weight units;
                              0: 16 median arc weights for the warp search, 4 for tiles */
     uint32_t leaf_size;   /* recursive-bisection leaf size used by RN_REORDER */
     float alpha;          /* smoothing parameter of the bisection (Eq. 1-2), in [0, 1];
-                             negative selects the default, 0.5 */
+                             negative selects the default, 0.5 -- not the 0 of the
+                             paper's experiments (Table 1): at 0 the bisection of the
+                             road-like graphs is badly unbalanced (slower to build, less
+                             compact leaves); the order never changes a result */
     uint32_t map_slots;   /* slots of the first slot map every tile is searched with: 0 or
                              8192 starts with narrow blocks (shared-memory map), 16384 with
                              wide blocks, a larger power of two with a global-memory map of
@@ -143,7 +147,8 @@ typedef struct {
     uint64_t slots;         /* sum over tiles of the nodes the tile reached (its union ball) */
     uint64_t slot_arcs;     /* sum over tiles of the arcs leaving those nodes */
     double device_ms;       /* device time of the query, CUDA events on its stream */
-    double search_ms;       /* device time of the first tile-search launch, CUDA events */
+    double search_ms;       /* device time of the first search launch (warp or tile search),
+                               CUDA events */
     /* search telemetry, summed over blocks: relaxation rounds, queue items over all
        rounds, bucket boundaries, and SM cycles in rounds, boundaries and emission */
     uint64_t rounds, round_items, boundaries;
@@ -155,21 +160,29 @@ typedef struct {
     uint64_t dirty_groups;  /* dirty lane-groups of the scanned items, over all rounds */
     uint64_t slot_lanes;    /* sum over tiles of slots times the tile's lanes (tile_width
                                1: the sum of the sources' balls) */
+    uint64_t box_leaf_decided; /* queries in a rectangle: members of R and S kept or dropped
+                               by their leaf's bounding rectangle alone */
 } rn_query_stats;
 
 /*
  * rn_graph_load -- build a graph from an edge list and upload it to the current GPU.
  *   src, dst, w : m edges, host arrays, endpoints < n, weights in [1, 2^24).
  *   flags       : RN_UNDIRECTED and/or RN_REORDER.
+ *   xy          : node coordinates, host array of 2 n floats (x, y of node i at 2i,
+ *                 2i + 1), finite; may be NULL.  Only queries restricted to a rectangle
+ *                 (rn_distance_join_box, rn_kcp_box) read them.
  *   cfg         : may be NULL (defaults).
  * Self-loops are dropped and parallel arcs keep their least weight (neither changes a
  * distance).  With RN_REORDER the nodes are relabelled by the recursive two-seed
  * bisection of Section 3 (Algorithm 1, smoothed by Eq. 1-2) so that every partition of
- * the hierarchy is a contiguous id range; ids seen by the caller never change.
- * Returns RN_EINVAL for a bad endpoint, weight or flag, RN_ENOMEM / RN_ECUDA otherwise.
+ * the hierarchy is a contiguous id range; ids seen by the caller never change.  With xy
+ * the graph keeps each leaf partition's bounding rectangle (its MBR; without RN_REORDER
+ * the leaves are runs of leaf_size consecutive ids).
+ * Returns RN_EINVAL for a bad endpoint, weight, coordinate or flag, RN_ENOMEM / RN_ECUDA
+ * otherwise.
  */
 rn_status rn_graph_load(const uint32_t *src, const uint32_t *dst, const uint32_t *w, uint64_t m,
-                        uint32_t n, uint32_t flags, const rn_config *cfg, rn_graph **out);
+                        uint32_t n, uint32_t flags, const float *xy, const rn_config *cfg, rn_graph **out);
 void rn_graph_free(rn_graph *g);
 rn_status rn_graph_info(const rn_graph *g, rn_graph_stats *out);
 /*
@@ -185,9 +198,8 @@ rn_status rn_bisection_order(const uint32_t *src, const uint32_t *dst, const uin
                              uint32_t n, uint32_t flags, const rn_config *cfg, uint32_t *order);
 /* Copy the relabelling out: perm[orig] = internal id (n entries). */
 rn_status rn_graph_permutation(const rn_graph *g, uint32_t *perm);
-/* Change the knobs of later queries (tile_width, delta); NULL restores the defaults. */
-/* Change a graph's knobs for its later queries (servers keep the knobs they were made
- * with). */
+/* Change a graph's knobs for its later queries; NULL restores the defaults (servers keep
+ * the knobs they were made with). */
 rn_status rn_graph_set_config(rn_graph *g, const rn_config *cfg);
 
 /*
@@ -262,6 +274,30 @@ rn_status rn_kcp(const rn_graph *g, const uint32_t *R, uint32_t nR, const uint32
                  uint32_t nS, uint64_t k, uint32_t theta, rn_pairs *out);
 rn_status rn_kcp_dev(const rn_graph *g, const uint32_t *dR, uint32_t nR, const uint32_t *dS,
                      uint32_t nS, uint64_t k, uint32_t theta, rn_dpairs *out, rn_stream stream);
+
+/* ------------------------------------------------- queries in a rectangle ---- */
+
+#define RN_BOX_R 1u /* the rectangle restricts R */
+#define RN_BOX_S 2u /* the rectangle restricts S */
+
+/*
+ * rn_distance_join_box / rn_kcp_box -- the join (sorted by (u, v)) and k closest pairs
+ * (sorted by (d, u, v)) of rn_distance_join / rn_kcp over the members of R (which &
+ * RN_BOX_R) and of S (which & RN_BOX_S) whose node lies in the closed rectangle
+ * box[0] <= x <= box[2], box[1] <= y <= box[3] of the coordinates given to
+ * rn_graph_load; a set the flag leaves out is taken whole.  Geographically constrained
+ * queries, Section 2: processing is restricted to the partitions that satisfy the
+ * constraint by a comparison with each partition's MBR -- a leaf whose rectangle lies
+ * inside the box keeps all its members, one that misses it drops them, and only a leaf
+ * on the box's border tests its members one by one.  Distances remain network distances
+ * over the whole graph (a path may leave the rectangle).  Host arrays in, library-owned
+ * host pairs out.  RN_EINVAL as rn_distance_join / rn_kcp, and for a graph loaded without
+ * coordinates, a box with xmin > xmax or ymin > ymax (or a NaN bound), or an unknown flag.
+ */
+rn_status rn_distance_join_box(const rn_graph *g, const uint32_t *R, uint32_t nR, const uint32_t *S,
+                               uint32_t nS, uint32_t theta, const float box[4], uint32_t which, rn_pairs *out);
+rn_status rn_kcp_box(const rn_graph *g, const uint32_t *R, uint32_t nR, const uint32_t *S, uint32_t nS,
+                     uint64_t k, uint32_t theta, const float box[4], uint32_t which, rn_pairs *out);
 
 /* ---------------------------------------------------------- points on edges ---- */
 

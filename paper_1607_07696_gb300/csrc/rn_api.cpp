@@ -3,6 +3,7 @@
 // catches everything; no exception crosses the ABI.
 #include <algorithm>
 #include <chrono>
+#include <cmath>
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
@@ -204,24 +205,28 @@ rn_status rn_last_query_stats(rn_query_stats *out) {
 }
 
 rn_status rn_graph_load(const uint32_t *src, const uint32_t *dst, const uint32_t *w, uint64_t m,
-                        uint32_t n, uint32_t flags, const rn_config *cfg, rn_graph **out) {
+                        uint32_t n, uint32_t flags, const float *xy, const rn_config *cfg, rn_graph **out) {
     return guarded([&] {
         if (!out) rn::fail(RN_EINVAL, "null output");
         *out = nullptr;
         if (m && (!src || !dst || !w)) rn::fail(RN_EINVAL, "null edge arrays");
         if (flags & ~(RN_UNDIRECTED | RN_REORDER)) rn::fail(RN_EINVAL, "unknown flag");
+        if (xy)
+            for (uint64_t i = 0; i < 2ull * n; i++)
+                if (!std::isfinite(xy[i])) rn::fail(RN_EINVAL, "node coordinates must be finite");
         auto g = std::make_unique<rn_graph>();
         apply_config(g.get(), cfg);
         rn::HostGraph h = rn::build_csr(n, m, src, dst, w, (flags & RN_UNDIRECTED) != 0);
-        std::vector<uint32_t> order(n), perm(n);
+        std::vector<uint32_t> order(n), perm(n), leaves;
+        const uint32_t leaf = cfg && cfg->leaf_size ? cfg->leaf_size : 512;
         auto t0 = std::chrono::steady_clock::now();
         if (flags & RN_REORDER) {
-            uint32_t leaf = cfg && cfg->leaf_size ? cfg->leaf_size : 512;
             float alpha = (cfg && cfg->alpha >= 0.0f) ? cfg->alpha : 0.5f;
-            order = rn::bisection_order(h, leaf, alpha, (flags & RN_UNDIRECTED) != 0);
+            order = rn::bisection_order(h, leaf, alpha, (flags & RN_UNDIRECTED) != 0, &leaves);
             h = rn::relabel(h, order);
         } else {
             for (uint32_t i = 0; i < n; i++) order[i] = i;
+            for (uint32_t i = 0; i < n; i += std::max<uint32_t>(leaf, 2)) leaves.push_back(i);
         }
         auto t1 = std::chrono::steady_clock::now();
         for (uint32_t i = 0; i < n; i++) perm[order[i]] = i;
@@ -236,6 +241,7 @@ rn_status rn_graph_load(const uint32_t *src, const uint32_t *dst, const uint32_t
         cudaGetDevice(&g->device);
         rn::upload_graph(h, perm, order, &g->dev);
         try {
+            if (xy) rn::upload_geometry(xy, order, leaves, &g->dev);
             g->ws = rn::workspace_create(g->dev);
         } catch (...) {
             rn::free_graph(&g->dev);
@@ -265,6 +271,7 @@ void rn_graph_free(rn_graph *g) {
     try {
         drop_scratch(g);
         rn::points_destroy(g->points);
+        rn::box_destroy(g->box);
         rn::workspace_destroy(g->ws);
         rn::free_graph(&g->dev);
     } catch (...) {
@@ -317,7 +324,7 @@ rn_status rn_graph_load_file(const char *path, rn_graph **out) {
         rn::read_edge_file(path, &f);
     });
     if (st != RN_OK) return st;
-    return rn_graph_load(f.src.data(), f.dst.data(), f.w.data(), f.src.size(), f.n, f.flags, nullptr, out);
+    return rn_graph_load(f.src.data(), f.dst.data(), f.w.data(), f.src.size(), f.n, f.flags, nullptr, nullptr, out);
 }
 
 rn_status rn_graph_write_file(const char *path, const uint32_t *src, const uint32_t *dst, const uint32_t *w,
@@ -446,6 +453,37 @@ rn_status rn_kcp(const rn_graph *cg, const uint32_t *R, uint32_t nR, const uint3
         rn::to_host_pairs(hs.res, out, hs.stream);
         g_last_stats = st;
         log_stats("kcp", st);
+        g_have_stats = true;
+    });
+}
+
+rn_status rn_distance_join_box(const rn_graph *cg, const uint32_t *R, uint32_t nR, const uint32_t *S,
+                               uint32_t nS, uint32_t theta, const float box[4], uint32_t which, rn_pairs *out) {
+    return rn_kcp_box(cg, R, nR, S, nS, 0, theta, box, which, out);
+}
+
+rn_status rn_kcp_box(const rn_graph *cg, const uint32_t *R, uint32_t nR, const uint32_t *S, uint32_t nS,
+                     uint64_t k, uint32_t theta, const float box[4], uint32_t which, rn_pairs *out) {
+    return guarded([&] {
+        if (!cg || !out || !box) rn::fail(RN_EINVAL, "null argument");
+        *out = rn_pairs{};
+        check_theta(theta);
+        rn_graph *g = const_cast<rn_graph *>(cg);
+        check_sets_host(g->dev.n, R, nR, S, nS);
+        std::lock_guard<std::mutex> lk(g->mu);
+        rn::HostScratch &hs = scratch_of(g);
+        ensure(&hs.dR, &hs.capR, nR);
+        ensure(&hs.dS, &hs.capS, nS);
+        rn::copy_to_device(hs.dR, R, size_t(nR) * 4, hs.stream);
+        rn::copy_to_device(hs.dS, S, size_t(nS) * 4, hs.stream);
+        rn_query_stats st{};
+        uint64_t decided = 0;
+        rn::run_box(g->dev, g->ws, &g->box, g->cfg, g->info.median_weight, hs.dR, nR, hs.dS, nS, box, which, k,
+                    theta, &hs.res, (void *)hs.stream, &st, &decided);
+        rn::to_host_pairs(hs.res, out, hs.stream);
+        st.box_leaf_decided = decided;
+        g_last_stats = st;
+        log_stats(k ? "kcp_box" : "join_box", st);
         g_have_stats = true;
     });
 }

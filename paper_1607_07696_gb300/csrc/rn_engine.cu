@@ -182,7 +182,40 @@ void free_graph(DeviceGraph *g) {
     device_free(g->adj);
     device_free(g->perm);
     device_free(g->iperm);
+    device_free(g->xy);
+    device_free(g->leaf_start);
+    device_free(g->leaf_box);
     *g = DeviceGraph{};
+}
+
+void upload_geometry(const float *xy, const std::vector<uint32_t> &order, const std::vector<uint32_t> &leaf_starts,
+                     DeviceGraph *out) {
+    const uint32_t n = out->n;
+    std::vector<float2> pos(n);
+    for (uint32_t i = 0; i < n; i++) pos[i] = make_float2(xy[2 * size_t(order[i])], xy[2 * size_t(order[i]) + 1]);
+    std::vector<uint32_t> starts(leaf_starts);
+    if (starts.empty() || starts[0] != 0) starts.insert(starts.begin(), 0);
+    const uint32_t nl = n ? uint32_t(starts.size()) : 0;
+    starts.push_back(n);
+    std::vector<float4> box(std::max<uint32_t>(nl, 1));
+    for (uint32_t l = 0; l < nl; l++) {
+        float4 b = make_float4(INFINITY, INFINITY, -INFINITY, -INFINITY);
+        for (uint32_t i = starts[l]; i < starts[l + 1]; i++) {
+            b.x = std::min(b.x, pos[i].x);
+            b.y = std::min(b.y, pos[i].y);
+            b.z = std::max(b.z, pos[i].x);
+            b.w = std::max(b.w, pos[i].y);
+        }
+        box[l] = b;
+    }
+    out->xy = (float2 *)device_alloc(std::max<size_t>(n, 1) * sizeof(float2));
+    out->leaf_start = (uint32_t *)device_alloc(starts.size() * 4);
+    out->leaf_box = (float4 *)device_alloc(box.size() * sizeof(float4));
+    out->nleaves = nl;
+    if (n) RN_CUDA(cudaMemcpy(out->xy, pos.data(), size_t(n) * sizeof(float2), cudaMemcpyHostToDevice));
+    RN_CUDA(cudaMemcpy(out->leaf_start, starts.data(), starts.size() * 4, cudaMemcpyHostToDevice));
+    RN_CUDA(cudaMemcpy(out->leaf_box, box.data(), box.size() * sizeof(float4), cudaMemcpyHostToDevice));
+    RN_CUDA(cudaDeviceSynchronize());  // pageable copies done before any stream reads them
 }
 
 // ---------------------------------------------------------------- workspace ----
@@ -1276,6 +1309,48 @@ __device__ __forceinline__ unsigned long long warp_sum64(unsigned long long v) {
     return v;
 }
 
+// One warp: the first bin of the k-closest-pairs histogram where the cumulative count
+// reaches k, and the live bound lowered to that bin's upper edge.  Each lane sums its 64
+// consecutive bins (16 independent vector loads); the lane whose range holds the k-th
+// pair reads its bins again to find the bin.
+__device__ __forceinline__ void kcp_lower_bound(const SearchArgs &a, uint32_t lane) {
+    constexpr uint32_t PER = KCP_BINS / 32;
+    const uint4 *h4 = reinterpret_cast<const uint4 *>(a.kcp_hist) + lane * (PER / 4);
+    unsigned long long own = 0;
+#pragma unroll
+    for (uint32_t i = 0; i < PER / 4; i++) {
+        const uint4 q = __ldcg(&h4[i]);
+        own += (unsigned long long)q.x + q.y + q.z + q.w;
+    }
+    unsigned long long incl = own;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const unsigned long long t = __shfl_up_sync(FULL, incl, o);
+        if (lane >= uint32_t(o)) incl += t;
+    }
+    const uint32_t reach = __ballot_sync(FULL, incl >= a.kcp_k);
+    if (reach && lane == uint32_t(__ffs(reach) - 1)) {
+        unsigned long long cum = incl - own;
+        uint32_t bin = lane * PER + PER - 1;
+        for (uint32_t i = 0; i < PER / 4; i++) {
+            const uint4 q = __ldcg(&h4[i]);
+            const uint32_t c4[4] = {q.x, q.y, q.z, q.w};
+            bool found = false;
+#pragma unroll
+            for (uint32_t j = 0; j < 4; j++) {
+                cum += c4[j];
+                if (!found && cum >= a.kcp_k) {
+                    bin = lane * PER + 4 * i + j;
+                    found = true;
+                }
+            }
+            if (found) break;
+        }
+        const unsigned long long edge = ((unsigned long long)(bin + 1) << a.hist_shift) - 1;
+        atomicMin(a.theta_live, uint32_t(min(edge, 0xFFFFFFFFull)));
+    }
+}
+
 template <uint32_t MS>
 __global__ void __launch_bounds__(src_warps(MS) * 32, SRC_BLOCKS_PER_SM) k_source_search(SearchArgs a) {
     constexpr uint32_t QS = src_qcap(MS);
@@ -1300,6 +1375,7 @@ __global__ void __launch_bounds__(src_warps(MS) * 32, SRC_BLOCKS_PER_SM) k_sourc
     unsigned long long n_rounds = 0, n_bounds = 0, n_slots = 0;
     unsigned long long cyc_round = 0, cyc_bound = 0, cyc_emit = 0;
     uint32_t max_ball = 0, max_seg = 0;
+    const bool kcp = a.kcp_hist != nullptr;
     long long t_mark = clock64();
 
     for (;;) {
@@ -1326,6 +1402,9 @@ __global__ void __launch_bounds__(src_warps(MS) * 32, SRC_BLOCKS_PER_SM) k_sourc
             sbits = a.inst_sbits[lo];
             prefix = (unsigned long long)lo << a.inst_shift;
         }
+        // k closest pairs: the live k-th distance bound (Algorithm 3's global threshold)
+        // caps the source's bound, and is read again at every bucket boundary
+        if (kcp) bound = min(bound, __ldcg(a.theta_live));
         const uint32_t y0 = a.src[si];
         if (RN_BAD(y0 < a.n_nodes, 11, si, y0)) continue;
         const unsigned long long u = __ldg(&a.iperm[y0]);
@@ -1497,12 +1576,15 @@ __global__ void __launch_bounds__(src_warps(MS) * 32, SRC_BLOCKS_PER_SM) k_sourc
             if (fail) break;
             // ---- the near queue is empty: the next bucket
             n_bounds++;
+            if (kcp) bound = min(bound, __ldcg(a.theta_live));  // the same for every lane
             const uint64_t top = uint64_t(bound) + 1;
             const uint64_t tau2 = tau + delta < top ? tau + delta : top;
             uint32_t m = INF;
             uint32_t nq = collect(tau2, &m);
             m = __reduce_min_sync(FULL, m);
-            if (m == INF) break;  // nothing pending: the search is complete
+            // nothing pending within the bound: the search is complete (a bound lowered
+            // by k closest pairs leaves dirty slots above it, which are never taken)
+            if (m == INF || m > bound) break;
             if (m >= tau2) {
                 // no pending slot in the next bucket: skip to the one holding m
                 const uint64_t t = (uint64_t(m) / delta + 1) * delta;
@@ -1528,7 +1610,10 @@ __global__ void __launch_bounds__(src_warps(MS) * 32, SRC_BLOCKS_PER_SM) k_sourc
             uint32_t cnt = 0;
 #pragma unroll 8
             for (uint32_t c = 0; c < MS; c += 32) {
-                const uint32_t b = __ballot_sync(FULL, (key[c + lane] & SK_IN_S) != 0u);  // never on SK_EMPTY
+                // an S slot within the bound (a join's slots all are; k closest pairs may
+                // have lowered the bound below slots reached before)
+                const bool hit = (key[c + lane] & SK_IN_S) != 0u && (!kcp || dist[c + lane] <= bound);
+                const uint32_t b = __ballot_sync(FULL, hit);  // never on SK_EMPTY
                 if (lane == 0) hits[c >> 5] = b;
                 cnt += __popc(b);
             }
@@ -1569,11 +1654,19 @@ __global__ void __launch_bounds__(src_warps(MS) * 32, SRC_BLOCKS_PER_SM) k_sourc
                             a.out_key[idx] = prefix | (u << a.vbits) | (unsigned long long)v[q];
                             a.out_d[idx] = dd[q];
                         }
+                        if (kcp) atomicAdd(&a.kcp_hist[dd[q] >> a.hist_shift], 1u);
                     }
                     pos += __popc(b[q]);
                     key[h] = SK_EMPTY;
                     dist[h] = INF;
                 }
+            }
+            if (kcp && cnt) {
+                // the source's pairs are counted: once k pairs exist, lower the live bound
+                // to the edge of the first histogram bin where the pairs emitted so far
+                // reach k (exact, distinct pairs: the k-th distance cannot lie above it)
+                const unsigned long long emitted = __shfl_sync(FULL, base, 0) + cnt;
+                if (emitted >= a.kcp_k) kcp_lower_bound(a, lane);
             }
             n_slots += fill;
             max_ball = max(max_ball, fill);
@@ -2285,14 +2378,25 @@ static double predicted_ball(const Workspace *ws, uint32_t theta) {
     return double(ws->ball_max) * r * r;
 }
 
+// The ball of a source at bound theta on a graph with no search behind it yet: on a
+// planar road network the nodes within theta are about those within theta / w_med hops,
+// and a lattice holds 2 r^2 nodes within r hops; never more than the graph.
+static double first_ball_estimate(const DeviceGraph &g, uint32_t theta, uint32_t median_w) {
+    const double r = double(theta) / double(std::max<uint32_t>(median_w, 1));
+    return std::min(2.0 * r * r, double(g.n));
+}
+
 // Whether a join runs the warp-per-source search: always for tile width 1, never for
 // 32, 64 or 128 or an explicit first map; by default while the balls seen on this
-// workspace, scaled to this bound, fit the largest warp map.
-static bool use_source_search(const DeviceGraph &g, const Workspace *ws, const EngineConfig &cfg, uint32_t theta) {
+// workspace, scaled to this bound, fit the largest warp map (with no search behind the
+// workspace yet, while the ball estimated from the bound does).
+static bool use_source_search(const DeviceGraph &g, const Workspace *ws, const EngineConfig &cfg, uint32_t theta,
+                              uint32_t median_w) {
     if (g.n >= SK_NODE) return false;
     if (cfg.tile_width == 1) return true;
     if (cfg.tile_width || cfg.map_slots) return false;
-    return predicted_ball(ws, theta) <= src_fit(SRC_MS_MAX);
+    const double ball = ws->ball_theta ? predicted_ball(ws, theta) : first_ball_estimate(g, theta, median_w);
+    return ball <= src_fit(SRC_MS_MAX);
 }
 
 // First warp map: the smallest whose 7/8 holds 1.3 times the predicted mean ball and
@@ -2319,7 +2423,7 @@ static uint32_t source_first_map(const Workspace *ws, uint32_t theta) {
 // the next query's choice of path and map.
 static Control source_search_all(const DeviceGraph &g, Workspace *ws, SearchArgs a, uint32_t nsrc, uint32_t ms0,
                                  uint32_t T, uint32_t theta, const std::vector<uint32_t> &inst_first,
-                                 cudaStream_t st, uint64_t *retried) {
+                                 cudaStream_t st, uint64_t *retried, bool learn_balls = true) {
     a.n_nodes = g.n;
     a.n_arcs = g.arcs;
     a.range_list = nullptr;
@@ -2340,7 +2444,8 @@ static Control source_search_all(const DeviceGraph &g, Workspace *ws, SearchArgs
     // mean ball of the sources the first pass completed (0 when none did)
     const double mean = nsrc > c.n_failed ? double(c.slots) / double(nsrc - c.n_failed) : 0.0;
     auto learn = [&] {
-        if (nsrc && ball >= 64) {  // a handful of nodes says little about the growth
+        // (k closest pairs lowers its bound as it goes: its balls say nothing of theta)
+        if (learn_balls && nsrc && ball >= 64) {  // a handful of nodes says little about the growth
             ws->ball_theta = std::max<uint32_t>(theta, 1);
             ws->ball_max = ball;
             ws->ball_mean = mean;
@@ -2578,7 +2683,7 @@ void run_join(const DeviceGraph &g, Workspace *ws, const EngineConfig &cfg, uint
     std::lock_guard<std::mutex> device_lock(ws->sh->mu);
     Range range("rn.join");
     *stats = rn_query_stats{};
-    const bool by_source = use_source_search(g, ws, cfg, theta);
+    const bool by_source = use_source_search(g, ws, cfg, theta, median_w);
     // the warp search's segments give the output order when sources run in output order
     const bool place = by_source && g.iperm_inverts_perm;
     const uint32_t delta = choose_delta(cfg, median_w, by_source);
@@ -2732,7 +2837,7 @@ void run_join_multi(const DeviceGraph &g, Workspace *ws, const EngineConfig &cfg
     *stats = rn_query_stats{};
     uint32_t max_bound = 0;
     for (uint32_t t : theta) max_bound = std::max(max_bound, std::min(t, RN_THETA_MAX));
-    const bool by_source = use_source_search(g, ws, cfg, max_bound);
+    const bool by_source = use_source_search(g, ws, cfg, max_bound, median_w);
     const uint32_t delta = choose_delta(cfg, median_w, by_source);
     stats->tile_width = by_source ? 1 : T;
     stats->delta = delta;
@@ -3174,13 +3279,10 @@ void run_kcp(const DeviceGraph &g, Workspace *ws, const EngineConfig &cfg, uint3
     if (theta == RN_INF) theta = RN_THETA_MAX;
     if (theta > RN_THETA_MAX) fail(RN_EINVAL, "theta must be <= 2^31 or RN_INF");
     const uint32_t T = cfg.tile_width > 1 ? cfg.tile_width : 32;
-    if (T != 32 && T != 64 && T != 128) fail(RN_EINVAL, "tile width must be 32, 64 or 128");
-    const uint32_t delta = choose_delta(cfg, median_w);
+    if (T != 32 && T != 64 && T != 128) fail(RN_EINVAL, "tile width must be 1, 32, 64 or 128");
     std::lock_guard<std::mutex> device_lock(ws->sh->mu);
     Range range("rn.kcp");
     *stats = rn_query_stats{};
-    stats->tile_width = T;
-    stats->delta = delta;
     ws->launches = 0;
     RN_CUDA(cudaEventRecord(ws->ev0, st));
 
@@ -3193,8 +3295,8 @@ void run_kcp(const DeviceGraph &g, Workspace *ws, const EngineConfig &cfg, uint3
         if (cfg.tile_src) tile_src = std::min(cfg.tile_src, T);
     }
     const uint32_t ntiles = (nR + tile_src - 1) / tile_src;
-    ensure_ranges(&ws->failed, &ws->failed_cap, std::max<uint32_t>(ntiles, 1));
-    ensure_ranges(&ws->failed2, &ws->failed2_cap, std::max<uint32_t>(ntiles, 1));
+    ensure_ranges(&ws->failed, &ws->failed_cap, std::max<uint32_t>(std::max(ntiles, nR), 1));
+    ensure_ranges(&ws->failed2, &ws->failed2_cap, std::max<uint32_t>(std::max(ntiles, nR), 1));
     ensure_pairs(ws, std::max<uint64_t>(ws->pair_cap, std::min<uint64_t>(k + (k >> 2) + 4096, uint64_t(nR) * 64 + 4096)));
     if (!ws->kcp) {
         ws->kcp = (uint32_t *)device_alloc((KCP_BINS + 16) * 4 + sizeof(SelState));
@@ -3209,20 +3311,27 @@ void run_kcp(const DeviceGraph &g, Workspace *ws, const EngineConfig &cfg, uint3
     a.adj = reinterpret_cast<const uint2 *>(g.adj);
     a.iperm = g.iperm;
     a.sbits = ws->sbits;
-    a.delta = delta;
     a.slab = ws->sh->slab;
     a.vbits = vbits;
-    a.tile_src = tile_src;
     a.ctl = ws->ctl;
     a.kcp_hist = hist;
     a.theta_live = theta_live;
     a.kcp_k = k;
-    uint64_t tau = std::min<uint64_t>(theta, delta);
+    // the first radius: one bucket of the warp search (16 median weights) when its ball
+    // fits a warp map, else one bucket of the tile search (4 median weights)
+    const uint32_t delta_src = choose_delta(cfg, median_w, true);
+    uint64_t tau = std::min<uint64_t>(theta, delta_src);
+    if (!use_source_search(g, ws, cfg, uint32_t(tau), median_w))
+        tau = std::min<uint64_t>(theta, choose_delta(cfg, median_w, false));
     uint64_t retried = 0;
     uint32_t passes = 0;
     Control c{};
     unsigned long long scans = 0;
+    bool any_tiles = false;
     for (;;) {
+        // every pass takes the warp search while the balls at tau fit a warp map
+        const bool by_source = use_source_search(g, ws, cfg, uint32_t(tau), median_w);
+        const uint32_t delta = choose_delta(cfg, median_w, by_source);
         prep_sets(g, ws, dR, nR, dS, nS, st);
         a.src = ws->rsorted;  // prep_sets may have (re)allocated the R list
         RN_CUDA(cudaMemsetAsync(hist, 0, KCP_BINS * 4, st));
@@ -3231,11 +3340,21 @@ void run_kcp(const DeviceGraph &g, Workspace *ws, const EngineConfig &cfg, uint3
         uint32_t shift = 0;
         while ((tau >> shift) >= KCP_BINS) shift++;
         a.bound = uint32_t(tau);
+        a.delta = delta;
         a.hist_shift = shift;
         a.out_key = ws->keyA;
         a.out_d = ws->valA;
         a.out_cap = ws->pair_cap;
-        c = search_all(g, ws, T, a, ntiles, st, &retried, cfg.map_slots);
+        if (by_source) {
+            a.tile_src = 1;
+            a.seg = nullptr;
+            c = source_search_all(g, ws, a, nR, source_first_map(ws, uint32_t(tau)), T, uint32_t(tau), {}, st,
+                                  &retried, false);
+        } else {
+            a.tile_src = tile_src;
+            c = search_all(g, ws, T, a, ntiles, st, &retried, cfg.map_slots);
+        }
+        any_tiles |= !by_source;
         check_control(c);
         if (c.pairs > ws->pair_cap) {  // the candidate buffer was too small: same pass again
             ensure_pairs(ws, c.pairs + c.pairs / 4);
@@ -3243,12 +3362,14 @@ void run_kcp(const DeviceGraph &g, Workspace *ws, const EngineConfig &cfg, uint3
         }
         passes++;
         scans += c.scans;
+        stats->delta = delta;
         if (c.pairs >= k || tau >= theta) break;
         // widen: pairs grow about as tau^2 on a road network
         double f = c.pairs ? std::sqrt(double(k) / double(c.pairs)) * 1.25 : 4.0;
         f = std::max(f, 1.5);
         tau = std::min<uint64_t>(theta, uint64_t(double(tau) * f) + 1);
     }
+    stats->tile_width = any_tiles ? T : 1;
     const uint64_t m = c.pairs;
     uint64_t kept = m;
     uint32_t theta_k = uint32_t(tau);
@@ -3526,6 +3647,127 @@ void run_points(const DeviceGraph &g, const std::vector<uint32_t> &perm, PointsS
         run_join(ps->aug, ps->ws, cfg, median_w, ps->ids, nR, ps->ids + nR, nS, theta, out, stream, stats);
     else
         run_kcp(ps->aug, ps->ws, cfg, median_w, ps->ids, nR, ps->ids + nR, nS, k, theta, out, stream, stats);
+}
+
+// ----------------------------------------------------- queries in a rectangle ----
+// Geographically constrained queries (Section 2: processing is restricted to the
+// partitions that satisfy the constraint, by a comparison with each partition's MBR).
+// A member of R or S belongs to the query when its node lies in the closed rectangle
+// box = (xmin, ymin, xmax, ymax).  The members are filtered on the device leaf by leaf:
+// a leaf whose bounding rectangle lies inside the box keeps all its members, one that
+// misses the box drops them, and only a leaf that straddles the box's border tests each
+// member's own coordinates.  Distances are still network distances over the whole graph
+// (a path may leave the rectangle); only the sets are restricted.
+
+struct BoxState {
+    uint32_t *ids = nullptr;     // R survivors, then S survivors
+    uint32_t cap = 0;
+    unsigned long long *counts = nullptr;  // R kept, S kept, members decided by a whole leaf
+    unsigned long long *counts_host = nullptr;  // pinned
+};
+
+void box_destroy(BoxState *bs) {
+    if (!bs) return;
+    device_free(bs->ids);
+    device_free(bs->counts);
+    if (bs->counts_host) cudaFreeHost(bs->counts_host);
+    delete bs;
+}
+
+// Keep the ids (original node ids) whose node lies in the box, appending them to out
+// (order not kept: the query's preparation sorts its sets); counts[slot] gets the
+// survivors and counts[2] the members decided by their leaf's rectangle alone.  An id
+// >= n is kept, for the query's own validation to reject.
+__global__ void k_box_filter(const uint32_t *__restrict__ ids, uint32_t cnt, uint32_t n,
+                             const uint32_t *__restrict__ perm, const uint32_t *__restrict__ leaf_start,
+                             uint32_t nleaves, const float4 *__restrict__ leaf_box, const float2 *__restrict__ xy,
+                             float4 box, uint32_t *out, unsigned long long *counts, uint32_t slot) {
+    const uint32_t lane = threadIdx.x & 31;
+    for (uint32_t base = (blockIdx.x * blockDim.x + threadIdx.x) & ~31u; base < cnt; base += gridDim.x * blockDim.x) {
+        const uint32_t i = base + lane;
+        bool keep = false, whole = false;
+        if (i < cnt) {
+            const uint32_t id = ids[i];
+            if (id >= n) {
+                keep = true;
+            } else {
+                const uint32_t x = perm[id];
+                // the leaf holding x: the last leaf starting at or before x
+                uint32_t lo = 0, hi = nleaves - 1;
+                while (lo < hi) {
+                    const uint32_t mid = (lo + hi + 1) >> 1;
+                    if (leaf_start[mid] <= x) lo = mid;
+                    else hi = mid - 1;
+                }
+                const float4 b = leaf_box[lo];
+                if (b.x >= box.x && b.z <= box.z && b.y >= box.y && b.w <= box.w) {
+                    keep = whole = true;  // the leaf lies inside the box
+                } else if (b.z < box.x || b.x > box.z || b.w < box.y || b.y > box.w) {
+                    whole = true;  // the leaf misses the box
+                } else {
+                    const float2 q = xy[x];
+                    keep = q.x >= box.x && q.x <= box.z && q.y >= box.y && q.y <= box.w;
+                }
+            }
+        }
+        const uint32_t kb = __ballot_sync(FULL, keep);
+        const uint32_t wb = __ballot_sync(FULL, whole);
+        uint32_t at = 0;
+        if (lane == 0) {
+            if (kb) at = uint32_t(atomicAdd(&counts[slot], (unsigned long long)__popc(kb)));
+            if (wb) atomicAdd(&counts[2], (unsigned long long)__popc(wb));
+        }
+        at = __shfl_sync(FULL, at, 0);
+        if (keep) out[at + __popc(kb & ((1u << lane) - 1))] = ids[i];
+    }
+}
+
+void run_box(const DeviceGraph &g, Workspace *ws, BoxState **state, const EngineConfig &cfg, uint32_t median_w,
+             const uint32_t *dR, uint32_t nR, const uint32_t *dS, uint32_t nS, const float *box, uint32_t which,
+             uint64_t k, uint32_t theta, rn_dpairs *out, void *stream, rn_query_stats *stats, uint64_t *leaves_whole) {
+    cudaStream_t st = (cudaStream_t)stream;
+    if (!g.xy || !g.leaf_box) fail(RN_EINVAL, "the graph was loaded without node coordinates");
+    if (!(box[0] <= box[2] && box[1] <= box[3])) fail(RN_EINVAL, "the box must have xmin <= xmax and ymin <= ymax");
+    if (which & ~uint32_t(RN_BOX_R | RN_BOX_S)) fail(RN_EINVAL, "unknown box flag");
+    if (!*state) *state = new BoxState();
+    BoxState *bs = *state;
+    if (!bs->counts) {
+        bs->counts = (unsigned long long *)device_alloc(4 * 8);
+        RN_CUDA(cudaMallocHost(&bs->counts_host, 4 * 8));
+    }
+    const uint64_t want = uint64_t(nR) + nS;
+    if (bs->cap < want) {
+        device_free(bs->ids);
+        bs->ids = nullptr;
+        bs->cap = uint32_t(std::min<uint64_t>(std::max<uint64_t>(want + want / 4, 1024), 0xFFFFFFFFull));
+        bs->ids = (uint32_t *)device_alloc(size_t(bs->cap) * 4);
+    }
+    uint32_t *oR = bs->ids, *oS = bs->ids + nR;
+    const float4 b4 = make_float4(box[0], box[1], box[2], box[3]);
+    RN_CUDA(cudaMemsetAsync(bs->counts, 0, 4 * 8, st));
+    // a set the box does not restrict is copied whole
+    if (nR) {
+        if (which & RN_BOX_R)
+            k_box_filter<<<std::min<uint32_t>((nR + 255) / 256, 4096), 256, 0, st>>>(
+                dR, nR, g.n, g.perm, g.leaf_start, g.nleaves, g.leaf_box, g.xy, b4, oR, bs->counts, 0);
+        else
+            RN_CUDA(cudaMemcpyAsync(oR, dR, size_t(nR) * 4, cudaMemcpyDeviceToDevice, st));
+    }
+    if (nS) {
+        if (which & RN_BOX_S)
+            k_box_filter<<<std::min<uint32_t>((nS + 255) / 256, 4096), 256, 0, st>>>(
+                dS, nS, g.n, g.perm, g.leaf_start, g.nleaves, g.leaf_box, g.xy, b4, oS, bs->counts, 1);
+        else
+            RN_CUDA(cudaMemcpyAsync(oS, dS, size_t(nS) * 4, cudaMemcpyDeviceToDevice, st));
+    }
+    RN_CUDA(cudaGetLastError());
+    RN_CUDA(cudaMemcpyAsync(bs->counts_host, bs->counts, 4 * 8, cudaMemcpyDeviceToHost, st));
+    RN_CUDA(cudaStreamSynchronize(st));
+    const uint32_t kR = (which & RN_BOX_R) ? uint32_t(bs->counts_host[0]) : nR;
+    const uint32_t kS = (which & RN_BOX_S) ? uint32_t(bs->counts_host[1]) : nS;
+    *leaves_whole = bs->counts_host[2];
+    if (k) run_kcp(g, ws, cfg, median_w, oR, kR, oS, kS, k, theta, out, stream, stats);
+    else run_join(g, ws, cfg, median_w, oR, kR, oS, kS, theta, out, stream, stats);
 }
 
 // ------------------------------------------------------------------- batch ----

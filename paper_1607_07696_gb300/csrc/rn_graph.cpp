@@ -77,6 +77,8 @@ struct Bisector {
     std::vector<uint32_t> stamp;  // BFS visit stamps
     std::vector<uint8_t> side;    // 0 unassigned, 1 left cluster, 2 right cluster
     std::vector<uint32_t> order;  // output: internal id -> original id
+    std::mutex leaves_mu;
+    std::vector<uint32_t> leaves;  // output: first internal id of every leaf (any order)
     std::atomic<uint32_t> next_label{1};
     std::atomic<uint32_t> next_stamp{1};
 
@@ -160,6 +162,10 @@ struct Bisector {
         if (part.size() <= leaf) {
             std::sort(part.begin(), part.end());
             std::copy(part.begin(), part.end(), order.begin() + out_begin);
+            if (!part.empty()) {
+                std::lock_guard<std::mutex> lk(leaves_mu);
+                leaves.push_back(out_begin);
+            }
             return;
         }
         std::vector<uint32_t> vis;
@@ -214,7 +220,8 @@ struct Bisector {
 
 }  // namespace
 
-std::vector<uint32_t> bisection_order(const HostGraph &g0, uint32_t leaf_size, float alpha, bool symmetric) {
+std::vector<uint32_t> bisection_order(const HostGraph &g0, uint32_t leaf_size, float alpha, bool symmetric,
+                                      std::vector<uint32_t> *leaf_starts) {
     if (alpha < 0.0f || alpha > 1.0f) fail(RN_EINVAL, "alpha must lie in [0, 1]");
     // The partitioning looks at proximity only, so a directed graph is bisected through
     // its symmetrised form (every arc both ways, least weight kept).
@@ -235,6 +242,10 @@ std::vector<uint32_t> bisection_order(const HostGraph &g0, uint32_t leaf_size, f
     std::vector<uint32_t> all(g.n);
     for (uint32_t x = 0; x < g.n; x++) all[x] = x;
     b.run(std::move(all), 0, 0, 0);
+    if (leaf_starts) {
+        *leaf_starts = std::move(b.leaves);
+        std::sort(leaf_starts->begin(), leaf_starts->end());
+    }
     return std::move(b.order);
 }
 

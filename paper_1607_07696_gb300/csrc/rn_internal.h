@@ -7,6 +7,8 @@
 #include <string>
 #include <vector>
 
+#include <vector_types.h>
+
 #include "rn.h"
 
 #include <nvtx3/nvToolsExt.h>
@@ -46,8 +48,10 @@ HostGraph build_csr(uint32_t n, uint64_t m, const uint32_t *src, const uint32_t 
 
 // Recursive two-seed bisection (Algorithm 1 with the smoothing of Eq. 1-2).  Returns
 // order[i] = the original id placed at internal id i; every partition of the hierarchy
-// occupies a contiguous range of internal ids.
-std::vector<uint32_t> bisection_order(const HostGraph &g, uint32_t leaf_size, float alpha, bool symmetric);
+// occupies a contiguous range of internal ids.  leaf_starts (if given) receives the
+// first internal id of every leaf, ascending.
+std::vector<uint32_t> bisection_order(const HostGraph &g, uint32_t leaf_size, float alpha, bool symmetric,
+                                      std::vector<uint32_t> *leaf_starts = nullptr);
 
 // CSR of g relabelled so that internal id i is original node order[i].
 HostGraph relabel(const HostGraph &g, const std::vector<uint32_t> &order);
@@ -61,6 +65,13 @@ struct DeviceGraph {
     uint32_t *perm = nullptr;     // original id -> internal id
     uint32_t *iperm = nullptr;    // internal id -> original id
     bool iperm_inverts_perm = true;  // false when output ids are not the input ids (points)
+    // node coordinates (rn_graph_load's xy), or none: per node (x, y) by internal id, and
+    // the leaves of the partition -- leaf i holds internal ids [leaf_start[i],
+    // leaf_start[i + 1]) -- with their bounding rectangles (xmin, ymin, xmax, ymax)
+    float2 *xy = nullptr;
+    uint32_t nleaves = 0;
+    uint32_t *leaf_start = nullptr;  // nleaves + 1
+    float4 *leaf_box = nullptr;      // nleaves
 };
 
 struct Workspace;  // device scratch owned by a graph (rn_engine.cu)
@@ -159,6 +170,20 @@ void to_host_pairs(const rn_dpairs &d, rn_pairs *out, void *stream);
 
 void upload_graph(const HostGraph &g, const std::vector<uint32_t> &perm,
                   const std::vector<uint32_t> &iperm, DeviceGraph *out);
+// Upload node coordinates (original ids, 2 floats each) and the partition's leaves
+// (first internal id of each, ascending) with their bounding rectangles.
+void upload_geometry(const float *xy, const std::vector<uint32_t> &order, const std::vector<uint32_t> &leaf_starts,
+                     DeviceGraph *out);
+
+// Queries restricted to a rectangle (rn_engine.cu): the members of R (RN_BOX_R in which)
+// and of S (RN_BOX_S) outside box = (xmin, ymin, xmax, ymax) are dropped -- a whole leaf
+// at a time where its bounding rectangle lies inside or outside the box -- then the
+// ordinary join (k = 0) or k closest pairs runs on what is left.
+struct BoxState;
+void run_box(const DeviceGraph &g, Workspace *ws, BoxState **state, const EngineConfig &cfg, uint32_t median_w,
+             const uint32_t *dR, uint32_t nR, const uint32_t *dS, uint32_t nS, const float *box, uint32_t which,
+             uint64_t k, uint32_t theta, rn_dpairs *out, void *stream, rn_query_stats *stats, uint64_t *leaves_whole);
+void box_destroy(BoxState *bs);
 void free_graph(DeviceGraph *g);
 void dpairs_reserve(rn_dpairs *p, uint64_t cap);
 void dpairs_release(rn_dpairs *p);
@@ -191,5 +216,6 @@ struct rn_graph {
     std::mutex mu;
     rn::HostScratch hs;
     rn::PointsState *points = nullptr;  // buffers of point queries, grown as needed
+    rn::BoxState *box = nullptr;        // buffers of rectangle-restricted queries
     int device = 0;
 };

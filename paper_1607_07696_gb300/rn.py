@@ -64,7 +64,8 @@ class rn_query_stats(C.Structure):
                 ("boundaries", C.c_uint64), ("cycles_rounds", C.c_uint64),
                 ("cycles_boundaries", C.c_uint64), ("cycles_emission", C.c_uint64),
                 ("cycles_step_a", C.c_uint64), ("round_arcs", C.c_uint64), ("max_ball", C.c_uint64),
-                ("retry_ms", C.c_double), ("dirty_groups", C.c_uint64), ("slot_lanes", C.c_uint64)]
+                ("retry_ms", C.c_double), ("dirty_groups", C.c_uint64), ("slot_lanes", C.c_uint64),
+                ("box_leaf_decided", C.c_uint64)]
 
 
 class rn_query(C.Structure):
@@ -117,7 +118,7 @@ _P32 = C.POINTER(C.c_uint32)
 _G = C.c_void_p
 SIGNATURES = {
     "rn_graph_load": (C.c_int, [_P32, _P32, _P32, C.c_uint64, C.c_uint32, C.c_uint32,
-                                C.POINTER(rn_config), C.POINTER(C.c_void_p)]),
+                                C.POINTER(C.c_float), C.POINTER(rn_config), C.POINTER(C.c_void_p)]),
     "rn_graph_free": (None, [_G]),
     "rn_bisection_order": (C.c_int, [_P32, _P32, _P32, C.c_uint64, C.c_uint32, C.c_uint32,
                                      C.POINTER(rn_config), _P32]),
@@ -155,6 +156,10 @@ SIGNATURES = {
                                           C.c_uint32, C.POINTER(rn_pairs)]),
     "rn_kcp_points": (C.c_int, [_G, C.POINTER(rn_point), C.c_uint32, C.POINTER(rn_point), C.c_uint32, C.c_uint64,
                                 C.c_uint32, C.POINTER(rn_pairs)]),
+    "rn_distance_join_box": (C.c_int, [_G, _P32, C.c_uint32, _P32, C.c_uint32, C.c_uint32,
+                                       C.POINTER(C.c_float), C.c_uint32, C.POINTER(rn_pairs)]),
+    "rn_kcp_box": (C.c_int, [_G, _P32, C.c_uint32, _P32, C.c_uint32, C.c_uint64, C.c_uint32,
+                             C.POINTER(C.c_float), C.c_uint32, C.POINTER(rn_pairs)]),
     "rn_file_read": (C.c_int, [C.c_char_p, C.POINTER(rn_edges)]),
     "rn_edges_free": (None, [C.POINTER(rn_edges)]),
     "rn_graph_load_file": (C.c_int, [C.c_char_p, C.POINTER(C.c_void_p)]),
@@ -250,12 +255,19 @@ class Graph:
 
 
 def rn_graph_load(src, dst, w, n: int, flags: int = RN_UNDIRECTED | RN_REORDER,
-                  cfg: dict | None = None) -> Graph:
+                  cfg: dict | None = None, xy=None) -> Graph:
+    """Load a graph; xy (optional, n x 2) gives node coordinates for rectangle queries."""
     s, d, ww = _u32(src), _u32(dst), _u32(w)
     if not (len(s) == len(d) == len(ww)):
         raise ValueError("edge arrays differ in length")
+    pxy = None
+    if xy is not None:
+        xy = np.ascontiguousarray(np.asarray(xy, dtype=np.float32).reshape(-1, 2))
+        if len(xy) != int(n):
+            raise ValueError("xy needs one (x, y) per node")
+        pxy = xy.ctypes.data_as(C.POINTER(C.c_float))
     out = C.c_void_p()
-    _check(lib().rn_graph_load(_p32(s), _p32(d), _p32(ww), len(s), int(n), int(flags),
+    _check(lib().rn_graph_load(_p32(s), _p32(d), _p32(ww), len(s), int(n), int(flags), pxy,
                                _config(cfg), C.byref(out)))
     return Graph(out.value, int(n))
 
@@ -331,6 +343,35 @@ def rn_kcp(g: Graph, R, S, k: int, theta: int = RN_INF):
     r, s = _u32(R), _u32(S)
     p = rn_pairs()
     _check(lib().rn_kcp(g.handle, _p32(r), len(r), _p32(s), len(s), int(k), int(theta), C.byref(p)))
+    return _take_pairs(p)
+
+
+RN_BOX_R, RN_BOX_S = 1, 2
+
+
+def _box(box):
+    b = np.ascontiguousarray(np.asarray(box, dtype=np.float32).reshape(4))
+    return b, b.ctypes.data_as(C.POINTER(C.c_float))
+
+
+def rn_distance_join_box(g: Graph, R, S, theta: int, box, which: int = RN_BOX_R | RN_BOX_S):
+    """The join of the members of R and S (as ``which`` says) whose node lies in the closed
+    rectangle box = (xmin, ymin, xmax, ymax); (u, v, d) sorted by (u, v)."""
+    r, s = _u32(R), _u32(S)
+    b, pb = _box(box)
+    p = rn_pairs()
+    _check(lib().rn_distance_join_box(g.handle, _p32(r), len(r), _p32(s), len(s), int(theta), pb, int(which),
+                                      C.byref(p)))
+    return _take_pairs(p)
+
+
+def rn_kcp_box(g: Graph, R, S, k: int, theta: int = RN_INF, box=(0, 0, 0, 0), which: int = RN_BOX_R | RN_BOX_S):
+    """k closest pairs of the members of R and S in the rectangle; sorted by (d, u, v)."""
+    r, s = _u32(R), _u32(S)
+    b, pb = _box(box)
+    p = rn_pairs()
+    _check(lib().rn_kcp_box(g.handle, _p32(r), len(r), _p32(s), len(s), int(k), int(theta), pb, int(which),
+                            C.byref(p)))
     return _take_pairs(p)
 
 

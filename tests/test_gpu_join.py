@@ -251,13 +251,18 @@ def test_source_search_routes(rn, oracle):
         st = rn.rn_last_query_stats()
         assert st["tile_width"] == 1 and st["retried_tiles"] > 0, st
         assert st["max_ball"] > 1792
-    # default path: an unbounded query meets balls of the whole graph, so the same bound
-    # goes to tiles next time, while a small one stays with the warp search
+    # default path: with no search behind the graph, the ball is estimated from the bound
+    # (an unbounded one spans the graph: tiles from the first query on); a small bound
+    # stays with the warp search, and then its measured balls decide
     g = load(rn, e)
     ref = og.join(R[:40], S, rn.RN_THETA_MAX)
     for i in range(2):
         assert_same(dev_join(rn, g, R[:40], S, rn.RN_INF), ref, f"unbounded {i}")
-        assert rn.rn_last_query_stats()["tile_width"] == (1 if i == 0 else 32)
+        assert rn.rn_last_query_stats()["tile_width"] == 32
+    g = load(rn, e)
+    for i in range(2):
+        assert_same(dev_join(rn, g, R[:40], S, int(D[3000])), og.join(R[:40], S, int(D[3000])), f"small {i}")
+        assert rn.rn_last_query_stats()["tile_width"] == 1
     theta = int(D[500])
     assert_same(dev_join(rn, g, R, S, theta), og.join(R, S, theta), "small after unbounded")
     st = rn.rn_last_query_stats()

@@ -49,7 +49,7 @@ def assert_same(got, ref, what):
     assert np.array_equal(d.astype(np.uint64), ref.d), f"{what}: d differs"
 
 
-@pytest.mark.parametrize("seed", range(16))
+@pytest.mark.parametrize("seed", range(24))
 def test_random_small(rn, oracle, seed):
     rng = np.random.default_rng(500 + seed)
     n = int(rng.integers(10, 3000))
@@ -59,7 +59,9 @@ def test_random_small(rn, oracle, seed):
         e = I.random_graph(n, int(rng.integers(n, 3 * n)), seed, 1, int(rng.choice([3, 100, 5000])))
     directed = seed % 5 == 4
     flags = (0 if directed else rn.RN_UNDIRECTED) | rn.RN_REORDER
-    g = rn.rn_graph_load(e.src, e.dst, e.w, e.n, flags=flags, cfg={"tile_width": [32, 64, 128][seed % 3]})
+    # the warp search (1), tiles (32, 64, 128), or the default path (0)
+    T = [1, 32, 64, 128, 0, 1][seed % 6]
+    g = rn.rn_graph_load(e.src, e.dst, e.w, e.n, flags=flags, cfg={"tile_width": T})
     og = oracle.graph(e.n, e.src, e.dst, e.w, undirected=not directed)
     perm = rng.permutation(e.n)
     nR = int(rng.integers(1, e.n // 2))
@@ -70,12 +72,15 @@ def test_random_small(rn, oracle, seed):
         for theta in (rn.RN_INF, int(np.median(full.d)) if len(full) else 10):
             ref = og.kcp(R, S, k, min(theta, rn.RN_THETA_MAX))
             assert_same(dev_kcp(rn, g, R, S, k, theta), ref, f"seed {seed} k {k} theta {theta}")
+            if T in (1, 32, 64, 128):
+                assert rn.rn_last_query_stats()["tile_width"] == T
 
 
-def test_ties_on_a_uniform_grid(rn, oracle):
+@pytest.mark.parametrize("T", [1, 32])
+def test_ties_on_a_uniform_grid(rn, oracle, T):
     # every edge weight 1: distances are Manhattan, so ties at the k-th distance abound
     e = I.full_grid(60, 50, 1)
-    g = rn.rn_graph_load(e.src, e.dst, e.w, e.n)
+    g = rn.rn_graph_load(e.src, e.dst, e.w, e.n, cfg={"tile_width": T})
     og = oracle.graph(e.n, e.src, e.dst, e.w)
     R, S = I.disjoint_sets(e.n, 400, 600, 9)
     for k in (1, 2, 3, 50, 51, 777, 5000):
@@ -85,10 +90,11 @@ def test_ties_on_a_uniform_grid(rn, oracle):
     assert_same((u, v, d), og.kcp(R, S, 333), "host kcp")
 
 
-def test_grid4096(rn, oracle):
+@pytest.mark.parametrize("T", [0, 1, 32])
+def test_grid4096(rn, oracle, T):
     w = I.c1_grid_join()
     e = w.graph
-    g = rn.rn_graph_load(e.src, e.dst, e.w, e.n)
+    g = rn.rn_graph_load(e.src, e.dst, e.w, e.n, cfg={"tile_width": T})
     og = oracle.graph(e.n, e.src, e.dst, e.w)
     for k in (1, 10, 100, 1000, 6356, 20000):
         assert_same(dev_kcp(rn, g, w.R, w.S, k, rn.RN_INF), og.kcp(w.R, w.S, k), f"grid4096 k {k}")

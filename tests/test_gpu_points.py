@@ -29,7 +29,7 @@ def same(got, ref):
             and np.array_equal(d.astype(np.uint64), ref.d))
 
 
-@pytest.mark.parametrize("seed", range(10))
+@pytest.mark.parametrize("seed", range(14))
 def test_points_random(rn, oracle, seed):
     rng = np.random.default_rng(700 + seed)
     n = int(rng.integers(50, 4000))
@@ -43,7 +43,9 @@ def test_points_random(rn, oracle, seed):
     cut = int(rng.integers(1, len(pts)))
     R = [pts[i] for i in order[:cut]]
     S = [pts[i] for i in order[cut:]]
-    T = [32, 64, 128][seed % 3]
+    # tile widths 32, 64, 128, and the default path (0: the warp search while the balls
+    # fit a warp map)
+    T = [32, 64, 128, 0][seed % 4]
     g = rn.rn_graph_load(e.src, e.dst, e.w, e.n, cfg={"tile_width": T})
     og = oracle.graph(e.n, e.src, e.dst, e.w)
     med = int(np.median(e.w))

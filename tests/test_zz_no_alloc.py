@@ -75,3 +75,47 @@ def test_limits_are_rejected_clearly(rn):
     with pytest.raises(rn.RNError) as ex:  # 40 pairs do not fit 1 entry
         rn.rn_distance_join_noalloc(g, _dev(np.arange(0, 80, 2)), _dev([81]), 1000, z, z.clone(), z.clone())
     assert ex.value.status == rn.RN_EINVAL and "output" in str(ex.value)
+
+
+def test_tiles_that_outgrow_the_narrow_map(rn, oracle):
+    """Every source's ball holds more than 7/8 of the narrow blocks' 8,192-slot map, so
+    every tile of 32 sources overflows and is searched again by wide blocks (16,384
+    slots, the static slab cut into four wide regions); the graph's 12,000 nodes fit that
+    map, so every tile completes there.  Two calls in a row, each equal to the allocating
+    join."""
+    e = I.road_graph(12_000, 33_240, 91)
+    g = rn.rn_graph_load(e.src, e.dst, e.w, e.n)
+    R, S = I.disjoint_sets(e.n, 256, 1000, 92)
+    og = oracle.graph(e.n, e.src, e.dst, e.w)
+    theta = max(int(np.sort(og.sssp(int(u))[0])[7200]) for u in R)
+    for _ in range(2):
+        ref = _reference(rn, g, R, S, theta)
+        got = _noalloc(rn, g, R, S, theta, cap=len(ref[0]))
+        assert len(ref[0]) > 0
+        for x, y in zip(got, ref):
+            assert np.array_equal(x, y)
+
+
+def test_tiles_that_outgrow_the_wide_map_are_rejected(rn):
+    """Unbounded searches on a graph whose largest component exceeds the wide map: the
+    call reports RN_EINVAL naming the slab, and the next call still works."""
+    import scipy.sparse as sp
+    import torch
+    from scipy.sparse.csgraph import connected_components
+
+    e = I.road_graph(20_000, 55_400, 93)
+    _, comp = connected_components(sp.coo_matrix((np.ones(e.m), (e.src, e.dst)), shape=(e.n, e.n)),
+                                   directed=False)
+    big = np.bincount(comp)
+    assert big.max() > 16_384 * 7 // 8
+    R, S = I.disjoint_sets(e.n, 256, 1000, 94)
+    R = R[big[comp[R]] > 16_384 * 7 // 8]
+    g = rn.rn_graph_load(e.src, e.dst, e.w, e.n)
+    z = torch.zeros(1 << 19, dtype=torch.int32, device="cuda")
+    with pytest.raises(rn.RNError) as ex:
+        rn.rn_distance_join_noalloc(g, _dev(R), _dev(S), rn.RN_INF, z, z.clone(), z.clone())
+    assert ex.value.status == rn.RN_EINVAL and "slab" in str(ex.value)
+    ref = _reference(rn, g, R[:8], S, 20_000)
+    got = _noalloc(rn, g, R[:8], S, 20_000, cap=len(ref[0]) + 1)
+    for x, y in zip(got, ref):
+        assert np.array_equal(x, y)
