@@ -465,10 +465,11 @@ def serve_leg(rn, count: int) -> dict:
     srv.close()
     # the plain form: one query per call, one after the other
     t0 = time.perf_counter()
-    plain_pairs = []
+    plain_pairs, plain_dev_ms = [], 0.0
     for r in reqs:
         out = rn.rn_distance_join(g, r.R, r.S, r.theta) if r.k == 0 else rn.rn_kcp(g, r.R, r.S, r.k, r.theta)
         plain_pairs.append(len(out[0]))
+        plain_dev_ms += rn.rn_last_query_stats()["device_ms"]
     plain_s = time.perf_counter() - t0
     assert plain_pairs == served_pairs, "served and plain pair counts differ"
     joins = [r for r in reqs if r.k == 0]
@@ -477,6 +478,7 @@ def serve_leg(rn, count: int) -> dict:
                     f"k 10-1e5, {count} requests",
         "unit": "queries/s", "requests": count, "joins": len(joins), "pairs": int(sum(served_pairs)),
         "served_qps": sat, "plain_qps": count / plain_s, "served_vs_plain": sat / (count / plain_s),
+        "plain_device_s": plain_dev_ms / 1e3, "plain_wall_s": plain_s,
         "phases": phases, "graph_load_s": load_s,
         "config": {"workers": 8, "max_blocks": "one per SM", "slab_mb": 4096},
     }

@@ -1369,14 +1369,18 @@ __global__ void __launch_bounds__(src_warps(MS) * 32, SRC_BLOCKS_PER_SM) k_sourc
     if (__ldcg(&a.ctl->err)) return;
     const uint32_t nR1 = a.nR_fixed ? a.nR_fixed : __ldcg(&a.ctl->r_count);
     const uint32_t nitems = a.range_list ? a.ntiles : nR1;
-    // per lane: items scanned, their arcs, arcs of first scans; per warp (every lane the
-    // same): rounds, bucket boundaries, slots of completed sources, SM cycles by phase
-    unsigned long long n_scans = 0, n_arcs = 0, n_slot_arcs = 0;
-    unsigned long long n_rounds = 0, n_bounds = 0, n_slots = 0;
-    unsigned long long cyc_round = 0, cyc_bound = 0, cyc_emit = 0;
-    uint32_t max_ball = 0, max_seg = 0;
+    // telemetry, counted per source in 32-bit registers -- per lane: items scanned, their
+    // arcs, arcs of first scans; per warp (every lane the same): rounds, bucket boundaries,
+    // SM cycles by phase (32-bit clock differences) -- and added to the warp's 64-bit
+    // totals in shared memory when the source ends
+    enum { W_SCANS, W_ARCS, W_SLOT_ARCS, W_ROUNDS, W_BOUNDS, W_SLOTS, W_CYC_ROUND, W_CYC_BOUND, W_CYC_EMIT, W_N };
+    __shared__ unsigned long long s_tel[src_warps(MS)][W_N];
+    __shared__ uint32_t s_max[src_warps(MS)][2];  // largest completed ball, most pairs of a source
+    if (lane < W_N) s_tel[warp][lane] = 0;
+    if (lane < 2) s_max[warp][lane] = 0;
+    __syncwarp();
     const bool kcp = a.kcp_hist != nullptr;
-    long long t_mark = clock64();
+    uint32_t t_mark = uint32_t(clock());
 
     for (;;) {
         uint32_t item = 0;
@@ -1402,13 +1406,21 @@ __global__ void __launch_bounds__(src_warps(MS) * 32, SRC_BLOCKS_PER_SM) k_sourc
             sbits = a.inst_sbits[lo];
             prefix = (unsigned long long)lo << a.inst_shift;
         }
+        uint64_t delta = a.delta;
+        if (a.tile_bound) {  // a batch: the source's instance, its bound and bucket width
+            inst = a.tile_inst[si];
+            bound = a.tile_bound[si];
+            delta = a.tile_delta[si];
+        }
         // k closest pairs: the live k-th distance bound (Algorithm 3's global threshold)
         // caps the source's bound, and is read again at every bucket boundary
         if (kcp) bound = min(bound, __ldcg(a.theta_live));
         const uint32_t y0 = a.src[si];
         if (RN_BAD(y0 < a.n_nodes, 11, si, y0)) continue;
         const unsigned long long u = __ldg(&a.iperm[y0]);
-        const uint64_t delta = a.delta;
+        const uint32_t t_source = uint32_t(clock());
+        uint32_t n_scans = 0, n_arcs = 0, n_slot_arcs = 0, n_rounds = 0, n_bounds = 0;
+        uint32_t cyc_round = 0, cyc_bound = 0;
         // the source, at distance 0, is the only item of the near queue
         if (lane == 0) {
             const uint32_t h = (y0 * 0x9E3779B1u) >> (32 - log2u(MS));
@@ -1495,49 +1507,68 @@ __global__ void __launch_bounds__(src_warps(MS) * 32, SRC_BLOCKS_PER_SM) k_sourc
                     // step B: arcs b0 .. b0 + 127, arc g of lane l's items when
                     // ex[l] <= g < ex[l] + deg[l][0] + deg[l][1] (lanes past the items
                     // have ex = total)
+                    const uint32_t tau32 = uint32_t(tau);  // <= bound + 1 <= 2^31 + 1
                     for (uint32_t b0 = 0; b0 < total && !fail; b0 += 32 * AP) {
+                        // arc slots k of the batch that hold arcs (the same for every lane):
+                        // a round's last batch is often far from full
+                        const uint32_t nk = min(uint32_t(AP), (total - b0 + 31) / 32);
                         uint32_t y[AP], nd[AP];
 #pragma unroll
                         for (int k = 0; k < AP; k++) {
-                            const uint32_t gi = b0 + 32 * k + lane;
-                            uint32_t l = 0;
-#pragma unroll
-                            for (uint32_t s = 16; s; s >>= 1)
-                                if (__shfl_sync(FULL, ex, l + s) <= gi) l += s;
-                            const uint32_t o = gi - __shfl_sync(FULL, ex, l);
-                            const uint32_t d0 = __shfl_sync(FULL, deg[0], l);
-                            const uint32_t bb0 = __shfl_sync(FULL, beg[0], l);
-                            const uint32_t bb1 = __shfl_sync(FULL, beg[1], l);
-                            const uint32_t v0 = __shfl_sync(FULL, dv[0], l);
-                            const uint32_t v1 = __shfl_sync(FULL, dv[1], l);
-                            const bool second = o >= d0;
-                            const uint32_t ai = second ? bb1 + (o - d0) : bb0 + o;
                             nd[k] = INF;
                             y[k] = 0;
-                            if (gi < total && !RN_BAD(ai < a.n_arcs, 15, gi, ai)) {
-                                const uint2 arc = __ldg(&a.adj[ai]);
-                                y[k] = arc.x;
-                                nd[k] = (second ? v1 : v0) + arc.y;  // <= bound + 2^24: no overflow
+                            if (uint32_t(k) < nk) {
+                                const uint32_t gi = b0 + 32 * k + lane;
+                                uint32_t l = 0;
+#pragma unroll
+                                for (uint32_t s = 16; s; s >>= 1)
+                                    if (__shfl_sync(FULL, ex, l + s) <= gi) l += s;
+                                const uint32_t o = gi - __shfl_sync(FULL, ex, l);
+                                const uint32_t d0 = __shfl_sync(FULL, deg[0], l);
+                                const uint32_t bb0 = __shfl_sync(FULL, beg[0], l);
+                                const uint32_t bb1 = __shfl_sync(FULL, beg[1], l);
+                                const uint32_t v0 = __shfl_sync(FULL, dv[0], l);
+                                const uint32_t v1 = __shfl_sync(FULL, dv[1], l);
+                                const bool second = o >= d0;
+                                const uint32_t ai = second ? bb1 + (o - d0) : bb0 + o;
+                                if (gi < total && !RN_BAD(ai < a.n_arcs, 15, gi, ai)) {
+                                    const uint2 arc = __ldg(&a.adj[ai]);
+                                    y[k] = arc.x;
+                                    nd[k] = (second ? v1 : v0) + arc.y;  // <= bound + 2^24: no overflow
+                                }
                             }
                         }
-                        // every probe, then every atomic, of the batch issued back to back
+                        // every first probe, then every atomic, of the batch issued back to back
                         // (their latencies overlap instead of adding up arc after arc)
                         uint32_t h[AP], kv[AP];
 #pragma unroll
                         for (int k = 0; k < AP; k++) {
-                            if (nd[k] <= bound && RN_BAD(y[k] < a.n_nodes, 16, b0 + 32 * k + lane, y[k])) nd[k] = INF;
-                            h[k] = (y[k] * 0x9E3779B1u) >> (32 - log2u(MS));
-                            kv[k] = nd[k] <= bound ? ((volatile uint32_t *)key)[h[k]] : 0u;
+                            h[k] = EMPTY;
+                            kv[k] = 0u;
+                            if (uint32_t(k) < nk) {
+                                if (nd[k] <= bound && RN_BAD(y[k] < a.n_nodes, 16, b0 + 32 * k + lane, y[k])) nd[k] = INF;
+                                h[k] = (y[k] * 0x9E3779B1u) >> (32 - log2u(MS));
+                                kv[k] = nd[k] <= bound ? ((volatile uint32_t *)key)[h[k]] : 0u;
+                            }
                         }
                         uint32_t ins_count = 0;
                         bool full = false;
 #pragma unroll
                         for (int k = 0; k < AP; k++) {
-                            bool ins = false;
-                            if (nd[k] > bound) h[k] = EMPTY;
-                            else if ((kv[k] & SK_NODE) != y[k]) h[k] = src_slot<MS>(key, y[k], h[k], &ins);
-                            ins_count += ins;
-                            full |= nd[k] <= bound && h[k] == EMPTY;
+                            if (uint32_t(k) < nk) {
+                                bool ins = false;
+                                if (nd[k] > bound) {
+                                    h[k] = EMPTY;
+                                } else if ((kv[k] & SK_NODE) != y[k]) {
+                                    // the home slot holds another node (keys never leave the
+                                    // map during a search): probe on from the next slot; it was
+                                    // empty: probe from it (another lane may have taken it since)
+                                    const uint32_t h0 = kv[k] == SK_EMPTY ? h[k] : (h[k] + 1) & (MS - 1);
+                                    h[k] = src_slot<MS>(key, y[k], h0, &ins);
+                                }
+                                ins_count += ins;
+                                full |= nd[k] <= bound && h[k] == EMPTY;
+                            }
                         }
                         fill += __reduce_add_sync(FULL, ins_count);  // once per batch
                         uint32_t old[AP];
@@ -1547,17 +1578,19 @@ __global__ void __launch_bounds__(src_warps(MS) * 32, SRC_BLOCKS_PER_SM) k_sourc
 #pragma unroll
                         for (int k = 0; k < AP; k++)
                             kf[k] = h[k] != EMPTY && nd[k] < old[k]
-                                        ? atomicOr(&key[h[k]], nd[k] < tau ? (SK_DIRTY | SK_QUEUED) : SK_DIRTY)
+                                        ? atomicOr(&key[h[k]], nd[k] < tau32 ? (SK_DIRTY | SK_QUEUED) : SK_DIRTY)
                                         : SK_QUEUED;
 #pragma unroll
                         for (int k = 0; k < AP; k++) {
-                            const bool push = h[k] != EMPTY && nd[k] < old[k] && nd[k] < tau && !(kf[k] & SK_QUEUED);
-                            const uint32_t pb = __ballot_sync(FULL, push);
-                            if (push) {
-                                const uint32_t qi = nnext + __popc(pb & lt);
-                                if (qi < QS) qnext[qi] = h[k];
+                            if (uint32_t(k) < nk) {
+                                const bool push = h[k] != EMPTY && nd[k] < old[k] && nd[k] < tau32 && !(kf[k] & SK_QUEUED);
+                                const uint32_t pb = __ballot_sync(FULL, push);
+                                if (push) {
+                                    const uint32_t qi = nnext + __popc(pb & lt);
+                                    if (qi < QS) qnext[qi] = h[k];
+                                }
+                                nnext += __popc(pb);
                             }
-                            nnext += __popc(pb);
                         }
                         if (__any_sync(FULL, full) || fill > a.max_fill) fail = true;
                     }
@@ -1568,8 +1601,8 @@ __global__ void __launch_bounds__(src_warps(MS) * 32, SRC_BLOCKS_PER_SM) k_sourc
                 qcur = qnext;
                 qnext = t;
             }
-            if (lane == 0) {
-                const long long t = clock64();
+            {
+                const uint32_t t = uint32_t(clock());
                 cyc_round += t - t_mark;
                 t_mark = t;
             }
@@ -1596,8 +1629,8 @@ __global__ void __launch_bounds__(src_warps(MS) * 32, SRC_BLOCKS_PER_SM) k_sourc
             }
             ncur = min(nq, QS);
             __syncwarp();
-            if (lane == 0) {
-                const long long t = clock64();
+            {
+                const uint32_t t = uint32_t(clock());
                 cyc_bound += t - t_mark;
                 t_mark = t;
             }
@@ -1623,7 +1656,7 @@ __global__ void __launch_bounds__(src_warps(MS) * 32, SRC_BLOCKS_PER_SM) k_sourc
                 if (a.inst_pairs) atomicAdd(&a.inst_pairs[inst], (unsigned long long)cnt);
             }
             if (lane == 0 && a.seg) a.seg[si] = make_uint2(uint32_t(base), cnt);
-            max_seg = max(max_seg, cnt);
+            if (lane == 0) s_max[warp][1] = max(s_max[warp][1], cnt);
             base = __shfl_sync(FULL, base, 0);
             __syncwarp();
             // four chunks of 32 slots at a time, every output-id load issued before the
@@ -1668,8 +1701,11 @@ __global__ void __launch_bounds__(src_warps(MS) * 32, SRC_BLOCKS_PER_SM) k_sourc
                 const unsigned long long emitted = __shfl_sync(FULL, base, 0) + cnt;
                 if (emitted >= a.kcp_k) kcp_lower_bound(a, lane);
             }
-            n_slots += fill;
-            max_ball = max(max_ball, fill);
+            if (lane == 0) {
+                s_tel[warp][W_SLOTS] += fill;
+                s_max[warp][0] = max(s_max[warp][0], fill);
+                if (a.inst_ball) atomicMax(&a.inst_ball[inst], fill);
+            }
         } else {
             if (lane == 0)
                 a.failed[atomicAdd(&a.ctl->n_failed, 1u)] =
@@ -1680,31 +1716,46 @@ __global__ void __launch_bounds__(src_warps(MS) * 32, SRC_BLOCKS_PER_SM) k_sourc
             }
         }
         __syncwarp();
+        const uint32_t t_end = uint32_t(clock());
+        n_scans = __reduce_add_sync(FULL, n_scans);
+        n_arcs = __reduce_add_sync(FULL, n_arcs);
+        n_slot_arcs = __reduce_add_sync(FULL, n_slot_arcs);
         if (lane == 0) {
-            const long long t = clock64();
-            cyc_emit += t - t_mark;
-            t_mark = t;
+            unsigned long long *tel = s_tel[warp];
+            tel[W_SCANS] += n_scans;
+            tel[W_ARCS] += n_arcs;
+            tel[W_SLOT_ARCS] += n_slot_arcs;
+            tel[W_ROUNDS] += n_rounds;
+            tel[W_BOUNDS] += n_bounds;
+            tel[W_CYC_ROUND] += cyc_round;
+            tel[W_CYC_BOUND] += cyc_bound;
+            tel[W_CYC_EMIT] += t_end - t_mark;
+            // a batch: the instance's SM cycles, this warp holding one resident warp's
+            // share of its SM
+            if (a.inst_cycles)
+                atomicAdd(&a.inst_cycles[inst],
+                          (unsigned long long)(t_end - t_source) / (src_warps(MS) * SRC_BLOCKS_PER_SM));
         }
+        t_mark = t_end;
+        __syncwarp();
     }
-    n_scans = warp_sum64(n_scans);
-    n_arcs = warp_sum64(n_arcs);
-    n_slot_arcs = warp_sum64(n_slot_arcs);
     if (lane == 0) {
-        atomicAdd(&a.ctl->scans, n_scans);
-        atomicAdd(&a.ctl->dirty_groups, n_scans);
-        atomicAdd(&a.ctl->round_items, n_scans);
-        atomicAdd(&a.ctl->round_arcs, n_arcs);
-        atomicAdd(&a.ctl->slot_arcs, n_slot_arcs);
-        atomicAdd(&a.ctl->slots, n_slots);
-        atomicAdd(&a.ctl->slot_lanes, n_slots);
-        atomicAdd(&a.ctl->rounds, n_rounds);
-        atomicAdd(&a.ctl->boundaries, n_bounds);
-        atomicAdd(&a.ctl->cyc_round, cyc_round);
-        atomicAdd(&a.ctl->cyc_bound, cyc_bound);
-        atomicAdd(&a.ctl->cyc_emit, cyc_emit);
-        atomicMax(&a.ctl->max_fill, max_ball);
-        atomicMax(&a.ctl->src_max_ball, max_ball);
-        atomicMax(&a.ctl->max_seg, max_seg);
+        const unsigned long long *tel = s_tel[warp];
+        atomicAdd(&a.ctl->scans, tel[W_SCANS]);
+        atomicAdd(&a.ctl->dirty_groups, tel[W_SCANS]);
+        atomicAdd(&a.ctl->round_items, tel[W_SCANS]);
+        atomicAdd(&a.ctl->round_arcs, tel[W_ARCS]);
+        atomicAdd(&a.ctl->slot_arcs, tel[W_SLOT_ARCS]);
+        atomicAdd(&a.ctl->slots, tel[W_SLOTS]);
+        atomicAdd(&a.ctl->slot_lanes, tel[W_SLOTS]);
+        atomicAdd(&a.ctl->rounds, tel[W_ROUNDS]);
+        atomicAdd(&a.ctl->boundaries, tel[W_BOUNDS]);
+        atomicAdd(&a.ctl->cyc_round, tel[W_CYC_ROUND]);
+        atomicAdd(&a.ctl->cyc_bound, tel[W_CYC_BOUND]);
+        atomicAdd(&a.ctl->cyc_emit, tel[W_CYC_EMIT]);
+        atomicMax(&a.ctl->max_fill, s_max[warp][0]);
+        atomicMax(&a.ctl->src_max_ball, s_max[warp][0]);
+        atomicMax(&a.ctl->max_seg, s_max[warp][1]);
     }
 }
 
@@ -2503,9 +2554,11 @@ static Control source_search_all(const DeviceGraph &g, Workspace *ws, SearchArgs
                        ? 0u
                        : uint32_t(std::upper_bound(inst_first.begin(), inst_first.end(), si) - inst_first.begin());
         };
+        // (a batch's tables hold one entry per source: its sources go one per tile)
+        const bool per_source = a.tile_bound != nullptr;
         std::vector<uint4> ranges;
         for (const uint4 &f : to_tiles) {
-            if (!ranges.empty()) {
+            if (!ranges.empty() && !per_source) {
                 uint4 &b = ranges.back();
                 if (b.x + b.y == f.x && b.y < T && query_of(b.x) == query_of(f.x)) {
                     b.y++;
@@ -2516,7 +2569,7 @@ static Control source_search_all(const DeviceGraph &g, Workspace *ws, SearchArgs
         }
         RN_CUDA(cudaMemsetAsync(&ws->ctl->tile_next, 0, 8, st));
         SearchArgs t = a;
-        t.tile_src = T;
+        t.tile_src = per_source ? 1 : T;
         uint64_t want = uint64_t(tile_est) * 2;  // the union of a few neighbours' balls
         c = search_all(g, ws, T, t, 0, st, retried, uint32_t(std::min<uint64_t>(want, 1u << 30)), true, &ranges,
                        false);
@@ -3319,9 +3372,15 @@ void run_kcp(const DeviceGraph &g, Workspace *ws, const EngineConfig &cfg, uint3
     a.kcp_k = k;
     // the first radius: one bucket of the warp search (16 median weights) when its ball
     // fits a warp map, else one bucket of the tile search (4 median weights)
+    // a source's ball at the k-th distance holds about (k / |R|) (n / |S|) nodes (each
+    // source's share of the k pairs, one S node per n / |S| nodes): a warp's map passes at
+    // bucket boundaries and emission do not pay for balls of a few dozen nodes, which the
+    // tile search shares between the sources of a tile
+    const double kth_ball = nR && nS ? double(k) / nR * (double(g.n) / nS) : 0.0;
+    const bool warp_ok = cfg.tile_width == 1 || kth_ball >= 64.0;
     const uint32_t delta_src = choose_delta(cfg, median_w, true);
     uint64_t tau = std::min<uint64_t>(theta, delta_src);
-    if (!use_source_search(g, ws, cfg, uint32_t(tau), median_w))
+    if (!warp_ok || !use_source_search(g, ws, cfg, uint32_t(tau), median_w))
         tau = std::min<uint64_t>(theta, choose_delta(cfg, median_w, false));
     uint64_t retried = 0;
     uint32_t passes = 0;
@@ -3330,7 +3389,7 @@ void run_kcp(const DeviceGraph &g, Workspace *ws, const EngineConfig &cfg, uint3
     bool any_tiles = false;
     for (;;) {
         // every pass takes the warp search while the balls at tau fit a warp map
-        const bool by_source = use_source_search(g, ws, cfg, uint32_t(tau), median_w);
+        const bool by_source = warp_ok && use_source_search(g, ws, cfg, uint32_t(tau), median_w);
         const uint32_t delta = choose_delta(cfg, median_w, by_source);
         prep_sets(g, ws, dR, nR, dS, nS, st);
         a.src = ws->rsorted;  // prep_sets may have (re)allocated the R list
@@ -3825,10 +3884,23 @@ __global__ void k_localize(uint32_t *u, uint32_t *v, uint64_t n, const unsigned 
 namespace {
 
 struct BatchPlan {
-    uint32_t T = 32;
+    uint32_t T = 32;          // 1: the warp search; 32, 64, 128: tiles of that width
     uint32_t delta_mult = 4;  // bucket width in median arc weights
     uint32_t src_div = 1;     // sources per tile = T / src_div
 };
+
+constexpr BatchPlan WARP_PLAN{1, 16, 1}, TILE_PLAN{32, 4, 1};
+
+// Sources per tile of a plan (one for the warp search).
+uint32_t plan_tile_src(const BatchPlan &p) { return std::max<uint32_t>(1, p.T / p.src_div); }
+
+// The smallest warp map whose 7/8 holds a ball of `ball` nodes with room to spare, or 0
+// when even the largest does not.
+uint32_t warp_map_for_ball(double ball) {
+    for (uint32_t ms = SRC_MS_MIN; ms <= SRC_MS_MAX; ms *= 2)
+        if (ball <= src_fit(ms)) return ms;
+    return 0;
+}
 
 // Size class of an instance for the autotuner: log2 of its node count, of |R| and of
 // theta in median arc weights (the hop radius of a search, which sets its ball).
@@ -3889,7 +3961,7 @@ uint32_t tune_cache_load(const char *path) {
             continue;
         }
         unsigned long cls = 0, T = 0, dm = 0, sd = 0;
-        if (std::sscanf(line, "%lu %lu %lu %lu", &cls, &T, &dm, &sd) != 4 || (T != 32 && T != 64 && T != 128) ||
+        if (std::sscanf(line, "%lu %lu %lu %lu", &cls, &T, &dm, &sd) != 4 || (T != 1 && T != 32 && T != 64 && T != 128) ||
             dm < 1 || dm > 1024 || sd < 1 || sd > T || cls > 0xFFFFFFFFul) {
             ok = false;
             why = "line " + std::to_string(lineno) + " is not 'class T delta_mult src_div'";
@@ -3976,11 +4048,21 @@ static T *upload_vec(const std::vector<T> &v) {
     return p;
 }
 
-// First maps from the balls measured under each instance's current tile width.
+// First maps from the balls measured under each instance's current tile width: for the
+// warp search the smallest warp map its largest source ball fits (an instance whose balls
+// outgrow the largest warp map moves to tiles), for tiles the map of its largest union
+// ball.
 static bool batch_adapt_maps(Batch *b) {
     bool changed = false;
     for (uint32_t i = 0; i < b->nq; i++) {
-        const uint32_t m = b->ball_T[i] == b->plan[i].T ? map_for_ball(b->ball[i]) : SMEM_H;
+        const bool measured = b->ball_T[i] == b->plan[i].T;
+        if (b->plan[i].T == 1 && measured && !warp_map_for_ball(b->ball[i])) {
+            b->plan[i] = TILE_PLAN;
+            changed = true;
+        }
+        uint32_t m;
+        if (b->plan[i].T == 1) m = measured ? warp_map_for_ball(b->ball[i]) : 2048;
+        else m = b->ball_T[i] == b->plan[i].T ? map_for_ball(b->ball[i]) : SMEM_H;
         if (m != b->map[i]) changed = true;
         b->map[i] = m;
     }
@@ -4012,7 +4094,7 @@ static void batch_layout(Batch *b) {
         Batch::Group g;
         g.T = std::get<0>(kv.first);
         g.map = std::get<1>(kv.first);
-        g.tile_src = std::max<uint32_t>(1, g.T / std::get<2>(kv.first));
+        g.tile_src = plan_tile_src(b->plan[first]);
         std::vector<uint32_t> src, tb, td, ti;
         for (uint32_t i : kv.second) {
             const auto &r = b->rint[i];
@@ -4125,7 +4207,7 @@ static void batch_counts(Batch *b, cudaStream_t st) {
     RN_CUDA(cudaMemcpyAsync(ball.data(), b->inst_ball, size_t(b->nq) * 4, cudaMemcpyDeviceToHost, st));
     RN_CUDA(cudaStreamSynchronize(st));
     for (uint32_t i = 0; i < b->nq; i++) {
-        const uint32_t ts = std::max<uint32_t>(1, b->plan[i].T / b->plan[i].src_div);
+        const uint32_t ts = plan_tile_src(b->plan[i]);
         const uint32_t nt = (b->nR[i] + ts - 1) / ts;
         b->tile_cost[i] = nt ? double(cyc[i]) / nt : 0.0;
     }
@@ -4151,6 +4233,10 @@ static void batch_launch_group(Batch *b, const Batch::Group &g, cudaStream_t st)
     a.ntiles = g.tiles;
     a.n_nodes = b->ug.n;
     a.n_arcs = b->ug.arcs;
+    if (g.T == 1) {  // the warp search: one source per tile, a warp map of g.map slots
+        source_launch(g.map, a, g.nsrc, b->ws, st);
+        return;
+    }
     if (g.map > SMEM_HW) {
         launch_gmap(b->ug, b->ws, g.T, a, g.map, g.tiles, st);
         return;
@@ -4173,7 +4259,11 @@ static uint64_t batch_run_eager(Batch *b, cudaStream_t st) {
         Control c{};
         for (const auto &g : b->groups) {
             RN_CUDA(cudaMemsetAsync(&b->ws->ctl->tile_next, 0, 8, st));  // tile_next, n_failed
-            c = search_all(b->ug, b->ws, g.T, batch_args(b, g), g.tiles, st, &retried, g.map, false);
+            if (g.T == 1)
+                c = source_search_all(b->ug, b->ws, batch_args(b, g), g.nsrc, g.map, TILE_PLAN.T, RN_THETA_MAX, {},
+                                      st, &retried, false);
+            else
+                c = search_all(b->ug, b->ws, g.T, batch_args(b, g), g.tiles, st, &retried, g.map, false);
             check_control(c);
         }
         b->stats.retried_tiles = retried;
@@ -4310,7 +4400,7 @@ static double batch_time_eager(Batch *b) {
 void batch_tune(Batch *b) {
     Range range("rn.batch.tune");
     static const BatchPlan cands[] = {
-        {32, 4, 1}, {32, 8, 1}, {32, 16, 1}, {32, 4, 2}, {64, 4, 1}, {64, 8, 1}, {128, 4, 1}, {128, 8, 1},
+        {1, 16, 1}, {1, 8, 1}, {1, 32, 1}, {32, 4, 1}, {32, 8, 1}, {32, 4, 2}, {64, 4, 1}, {128, 4, 1},
     };
     const size_t nc = sizeof(cands) / sizeof(cands[0]);
     std::map<uint32_t, std::vector<double>> cost;  // class -> cycles per candidate
@@ -4371,7 +4461,7 @@ Batch *batch_create(const std::vector<const DeviceGraph *> &graphs, const std::v
         b->theta.resize(b->nq);
         b->cls.resize(b->nq);
         b->node_off.assign(b->nq + 1, 0);
-        b->plan.assign(b->nq, BatchPlan{});
+        b->plan.assign(b->nq, TILE_PLAN);
         b->map.assign(b->nq, SMEM_H);
         b->ball.assign(b->nq, 0);
         b->ball_T.assign(b->nq, 0);
@@ -4383,6 +4473,11 @@ Batch *batch_create(const std::vector<const DeviceGraph *> &graphs, const std::v
             b->theta[i] = theta[i] == RN_INF ? RN_THETA_MAX : theta[i];
             if (b->theta[i] > RN_THETA_MAX) fail(RN_EINVAL, "theta must be <= 2^31 or RN_INF");
             b->cls[i] = size_class(b->n[i], nR[i], b->theta[i], median_w[i]);
+            // the default plan: the warp search while the ball estimated from the bound
+            // fits a 2048-slot warp map (a dozen warps per SM or more), else tiles, whose
+            // sources share their searches' passes
+            if (graphs[i]->n < SK_NODE && first_ball_estimate(*graphs[i], b->theta[i], median_w[i]) <= src_fit(2048))
+                b->plan[i] = WARP_PLAN;
             b->node_off[i] = uint32_t(nsum);
             nsum += graphs[i]->n;
             asum += graphs[i]->arcs;
@@ -4451,6 +4546,10 @@ Batch *batch_create(const std::vector<const DeviceGraph *> &graphs, const std::v
         for (uint32_t x : nR) totR += x;
         batch_reserve_pairs(b, std::max<uint64_t>(totR * 64, 1 << 16));
         b->stats.instances = b->nq;
+        if (b->n_u >= SK_NODE)  // the warp search keys nodes in 28 bits
+            for (auto &p : b->plan)
+                if (p.T == 1) p = TILE_PLAN;
+        batch_adapt_maps(b);
         batch_layout(b);
     } catch (...) {
         batch_destroy(b);

@@ -125,6 +125,12 @@ def test_batch_edge_cases(rn, oracle):
     gt = rn.rn_graph_load(tiny.src, tiny.dst, tiny.w, tiny.n)
     one = I.random_graph(1, 0, 1)
     g1 = rn.rn_graph_load(one.src, one.dst, one.w, one.n)
+    # a random (non-planar) graph: a bound of a few median weights, whose ball the planar
+    # estimate puts within a warp map, reaches most of the graph -- the warp search's
+    # sources overflow, go to tiles one by one, and the instance moves to tiles
+    rnd = I.random_graph(20_000, 60_000, 95, 1, 100)
+    gr = rn.rn_graph_load(rnd.src, rnd.dst, rnd.w, rnd.n)
+    Rr, Sr = I.disjoint_sets(rnd.n, 64, 400, 96)
     Rb, Sb = I.disjoint_sets(big.n, 300, 500, 92)
     inst = [
         (big, gb, Rb, Sb, 40_000),
@@ -135,6 +141,7 @@ def test_batch_edge_cases(rn, oracle):
         (tiny, gt, np.array([0]), np.array([1]), 5),
         (tiny, gt, np.array([1]), np.array([0]), 4),
         (one, g1, np.array([0]), np.array([], dtype=np.int64), 3),
+        (rnd, gr, Rr, Sr, 8 * int(np.median(rnd.w))),
     ]
     b = rn.rn_batch_create([(g, R, S, th) for (e, g, R, S, th) in inst])
     for run in range(3):
