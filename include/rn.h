@@ -299,6 +299,42 @@ rn_status rn_distance_join_box(const rn_graph *g, const uint32_t *R, uint32_t nR
 rn_status rn_kcp_box(const rn_graph *g, const uint32_t *R, uint32_t nR, const uint32_t *S, uint32_t nS,
                      uint64_t k, uint32_t theta, const float box[4], uint32_t which, rn_pairs *out);
 
+/* ------------------------------------------------------ hierarchical variant ---- */
+
+/* Counters of the calling thread's last hierarchical query (rn_last_hier_stats). */
+typedef struct {
+    uint64_t parts;          /* parts of the hierarchy cut the query used */
+    uint64_t max_part;       /* nodes of its largest part */
+    uint64_t local_pairs;    /* pairs the local searches found inside their sources' parts */
+    uint64_t border_routes;  /* (source, border node) routes of the local searches */
+    uint64_t exit_routes;    /* distinct (source, far end of an exit arc) routes */
+    uint64_t exit_searches;  /* searches from the far ends of exit arcs */
+    uint64_t candidates;     /* pairs through exit arcs before each pair keeps its least distance */
+    double local_ms, exit_ms, combine_ms;  /* device time of the three phases (all passes) */
+} rn_hier_stats;
+
+/*
+ * rn_distance_join_hier / rn_kcp_hier -- the join and k closest pairs of
+ * rn_distance_join / rn_kcp (same results, same order, same errors), computed the way of
+ * the paper's hierarchical processing (Section 4, Algorithms 2-4) over the partition
+ * hierarchy of Algorithm 1: the hierarchy is cut into its coarsest parts of at most
+ * part_size nodes (0: its leaves; at least the load's leaf_size, at most 6516);
+ * every u in R is searched inside its own part only (local processing), which gives the
+ * pairs inside the part and the routes to the part's border nodes; each route is
+ * extended over the arcs that leave the part (cross-edges), one search runs from every
+ * far end of such an arc and its hits are shared by every u that reaches it (the reuse of
+ * the inside routes of Algorithm 4); every pair keeps its least distance.  The search
+ * from a far end is not confined to the neighbouring part (the listing's confinement can
+ * overstate a distance whose shortest path crosses a border twice), so the result is
+ * exact.  k closest pairs grow the radius until the join holds k pairs.  Host arrays in,
+ * library-owned host pairs out.  RN_EINVAL also for a part_size outside those limits.
+ */
+rn_status rn_distance_join_hier(const rn_graph *g, const uint32_t *R, uint32_t nR, const uint32_t *S,
+                                uint32_t nS, uint32_t theta, uint32_t part_size, rn_pairs *out);
+rn_status rn_kcp_hier(const rn_graph *g, const uint32_t *R, uint32_t nR, const uint32_t *S, uint32_t nS,
+                      uint64_t k, uint32_t theta, uint32_t part_size, rn_pairs *out);
+rn_status rn_last_hier_stats(rn_hier_stats *out);
+
 /* ---------------------------------------------------------- points on edges ---- */
 
 /* A point on the undirected edge {a, b} at distance t from a (0 <= t <= w, w the edge's

@@ -218,15 +218,31 @@ rn_status rn_graph_load(const uint32_t *src, const uint32_t *dst, const uint32_t
         apply_config(g.get(), cfg);
         rn::HostGraph h = rn::build_csr(n, m, src, dst, w, (flags & RN_UNDIRECTED) != 0);
         std::vector<uint32_t> order(n), perm(n), leaves;
-        const uint32_t leaf = cfg && cfg->leaf_size ? cfg->leaf_size : 512;
+        std::vector<uint64_t> parts;
+        const uint32_t leaf = std::max<uint32_t>(cfg && cfg->leaf_size ? cfg->leaf_size : 512, 2);
         auto t0 = std::chrono::steady_clock::now();
         if (flags & RN_REORDER) {
             float alpha = (cfg && cfg->alpha >= 0.0f) ? cfg->alpha : 0.5f;
-            order = rn::bisection_order(h, leaf, alpha, (flags & RN_UNDIRECTED) != 0, &leaves);
+            order = rn::bisection_order(h, leaf, alpha, (flags & RN_UNDIRECTED) != 0, &leaves, &parts);
             h = rn::relabel(h, order);
         } else {
+            // no bisection: the id ranges of a halving hierarchy stand for its parts
             for (uint32_t i = 0; i < n; i++) order[i] = i;
-            for (uint32_t i = 0; i < n; i += std::max<uint32_t>(leaf, 2)) leaves.push_back(i);
+            std::vector<std::pair<uint32_t, uint32_t>> todo;
+            if (n) todo.emplace_back(0, n);
+            while (!todo.empty()) {
+                const auto [b, sz] = todo.back();
+                todo.pop_back();
+                parts.push_back((uint64_t(b) << 32) | sz);
+                if (sz <= leaf) {
+                    leaves.push_back(b);
+                } else {
+                    todo.emplace_back(b, sz / 2);
+                    todo.emplace_back(b + sz / 2, sz - sz / 2);
+                }
+            }
+            std::sort(leaves.begin(), leaves.end());
+            std::sort(parts.begin(), parts.end());
         }
         auto t1 = std::chrono::steady_clock::now();
         for (uint32_t i = 0; i < n; i++) perm[order[i]] = i;
@@ -248,6 +264,8 @@ rn_status rn_graph_load(const uint32_t *src, const uint32_t *dst, const uint32_t
             throw;
         }
         g->perm = std::move(perm);
+        g->parts = std::move(parts);
+        g->leaf_size = leaf;
         *out = g.release();
     });
 }
@@ -272,6 +290,7 @@ void rn_graph_free(rn_graph *g) {
         drop_scratch(g);
         rn::points_destroy(g->points);
         rn::box_destroy(g->box);
+        rn::hier_destroy(g->hier);
         rn::workspace_destroy(g->ws);
         rn::free_graph(&g->dev);
     } catch (...) {
@@ -486,6 +505,79 @@ rn_status rn_kcp_box(const rn_graph *cg, const uint32_t *R, uint32_t nR, const u
         log_stats(k ? "kcp_box" : "join_box", st);
         g_have_stats = true;
     });
+}
+
+namespace {
+
+thread_local rn_hier_stats g_last_hier{};
+thread_local bool g_have_hier = false;
+
+// The coarsest parts of the partition hierarchy with at most part_size nodes (the leaves
+// for 0): their first internal ids, ascending; they cover every node once.
+std::vector<uint32_t> hierarchy_cut(const rn_graph *g, uint32_t part_size) {
+    const uint32_t P = part_size ? part_size : g->leaf_size;
+    if (P < g->leaf_size) rn::fail(RN_EINVAL, "part_size must be 0 or at least the graph's leaf size");
+    std::vector<uint64_t> parts(g->parts);
+    std::sort(parts.begin(), parts.end(), [](uint64_t a, uint64_t b) {
+        return (a >> 32) != (b >> 32) ? (a >> 32) < (b >> 32) : (a & 0xFFFFFFFFull) > (b & 0xFFFFFFFFull);
+    });
+    std::vector<uint32_t> starts;
+    uint64_t covered = 0;
+    for (uint64_t p : parts) {
+        const uint64_t b = p >> 32, sz = p & 0xFFFFFFFFull;
+        if (b >= covered && sz <= P) {
+            if (b != covered) rn::fail(RN_EINTERNAL, "the partition hierarchy leaves a gap");
+            starts.push_back(uint32_t(b));
+            covered = b + sz;
+        }
+    }
+    if (covered != g->dev.n) rn::fail(RN_EINTERNAL, "the partition hierarchy does not cover the graph");
+    if (starts.empty()) starts.push_back(0);
+    return starts;
+}
+
+void hier_query(const rn_graph *cg, const uint32_t *R, uint32_t nR, const uint32_t *S, uint32_t nS, uint64_t k,
+                uint32_t theta, uint32_t part_size, rn_pairs *out) {
+    if (!cg || !out) rn::fail(RN_EINVAL, "null argument");
+    *out = rn_pairs{};
+    check_theta(theta);
+    rn_graph *g = const_cast<rn_graph *>(cg);
+    check_sets_host(g->dev.n, R, nR, S, nS);
+    std::lock_guard<std::mutex> lk(g->mu);
+    const std::vector<uint32_t> cut = hierarchy_cut(g, part_size);
+    rn::HostScratch &hs = scratch_of(g);
+    rn_query_stats st{};
+    rn_hier_stats hst{};
+    rn::run_hier(g->dev, g->ws, &g->hier, g->cfg, g->info.median_weight, g->perm, cut, R, nR, S, nS, k, theta,
+                 &hs.res, (void *)hs.stream, &st, &hst);
+    rn::to_host_pairs(hs.res, out, hs.stream);
+    g_last_stats = st;
+    g_have_stats = true;
+    g_last_hier = hst;
+    g_have_hier = true;
+    log_stats(k ? "kcp_hier" : "join_hier", st);
+}
+
+}  // namespace
+
+rn_status rn_distance_join_hier(const rn_graph *g, const uint32_t *R, uint32_t nR, const uint32_t *S, uint32_t nS,
+                                uint32_t theta, uint32_t part_size, rn_pairs *out) {
+    return guarded([&] { hier_query(g, R, nR, S, nS, 0, theta, part_size, out); });
+}
+
+rn_status rn_kcp_hier(const rn_graph *g, const uint32_t *R, uint32_t nR, const uint32_t *S, uint32_t nS, uint64_t k,
+                      uint32_t theta, uint32_t part_size, rn_pairs *out) {
+    return guarded([&] {
+        if (k == 0) rn::fail(RN_EINVAL, "k must be >= 1");
+        hier_query(g, R, nR, S, nS, k, theta, part_size, out);
+    });
+}
+
+rn_status rn_last_hier_stats(rn_hier_stats *out) {
+    if (!out) return set_error(RN_EINVAL, "null output");
+    if (!g_have_hier) return set_error(RN_EINVAL, "no hierarchical query has completed on this thread");
+    *out = g_last_hier;
+    return RN_OK;
 }
 
 namespace {

@@ -573,6 +573,16 @@ struct SearchArgs {
     const uint32_t *inst_bound;
     // warp search: seg[si] = (first pair, pair count) of source si, or null
     uint2 *seg;
+    // the hierarchical variant's local searches: source si relaxes only arcs into its
+    // part, internal ids [src_range[si].x, src_range[si].y), and records a route
+    // (si << 32 | node, distance) to every border node of the part it settles (a node
+    // with an arc leaving its part: border_bits) in brd_key / brd_d
+    const uint2 *src_range;
+    const uint32_t *border_bits;
+    unsigned long long *brd_key;
+    uint32_t *brd_d;
+    uint64_t brd_cap;
+    unsigned long long *brd_count;
 };
 
 // What a block needs to know about the tile it searches.
@@ -1351,7 +1361,7 @@ __device__ __forceinline__ void kcp_lower_bound(const SearchArgs &a, uint32_t la
     }
 }
 
-template <uint32_t MS>
+template <uint32_t MS, bool HIER>
 __global__ void __launch_bounds__(src_warps(MS) * 32, SRC_BLOCKS_PER_SM) k_source_search(SearchArgs a) {
     constexpr uint32_t QS = src_qcap(MS);
     constexpr int AP = 4;  // arcs per lane in flight
@@ -1419,6 +1429,12 @@ __global__ void __launch_bounds__(src_warps(MS) * 32, SRC_BLOCKS_PER_SM) k_sourc
         if (RN_BAD(y0 < a.n_nodes, 11, si, y0)) continue;
         const unsigned long long u = __ldg(&a.iperm[y0]);
         const uint32_t t_source = uint32_t(clock());
+        uint32_t part_lo = 0, part_hi = 0xFFFFFFFFu;  // the hierarchical variant: the source's part
+        if (HIER) {
+            const uint2 r = a.src_range[si];
+            part_lo = r.x;
+            part_hi = r.y;
+        }
         uint32_t n_scans = 0, n_arcs = 0, n_slot_arcs = 0, n_rounds = 0, n_bounds = 0;
         uint32_t cyc_round = 0, cyc_bound = 0;
         // the source, at distance 0, is the only item of the near queue
@@ -1509,33 +1525,29 @@ __global__ void __launch_bounds__(src_warps(MS) * 32, SRC_BLOCKS_PER_SM) k_sourc
                     // have ex = total)
                     const uint32_t tau32 = uint32_t(tau);  // <= bound + 1 <= 2^31 + 1
                     for (uint32_t b0 = 0; b0 < total && !fail; b0 += 32 * AP) {
-                        // arc slots k of the batch that hold arcs (the same for every lane):
-                        // a round's last batch is often far from full
-                        const uint32_t nk = min(uint32_t(AP), (total - b0 + 31) / 32);
                         uint32_t y[AP], nd[AP];
 #pragma unroll
                         for (int k = 0; k < AP; k++) {
+                            const uint32_t gi = b0 + 32 * k + lane;
+                            uint32_t l = 0;
+#pragma unroll
+                            for (uint32_t s = 16; s; s >>= 1)
+                                if (__shfl_sync(FULL, ex, l + s) <= gi) l += s;
+                            const uint32_t o = gi - __shfl_sync(FULL, ex, l);
+                            const uint32_t d0 = __shfl_sync(FULL, deg[0], l);
+                            const uint32_t bb0 = __shfl_sync(FULL, beg[0], l);
+                            const uint32_t bb1 = __shfl_sync(FULL, beg[1], l);
+                            const uint32_t v0 = __shfl_sync(FULL, dv[0], l);
+                            const uint32_t v1 = __shfl_sync(FULL, dv[1], l);
+                            const bool second = o >= d0;
+                            const uint32_t ai = second ? bb1 + (o - d0) : bb0 + o;
                             nd[k] = INF;
                             y[k] = 0;
-                            if (uint32_t(k) < nk) {
-                                const uint32_t gi = b0 + 32 * k + lane;
-                                uint32_t l = 0;
-#pragma unroll
-                                for (uint32_t s = 16; s; s >>= 1)
-                                    if (__shfl_sync(FULL, ex, l + s) <= gi) l += s;
-                                const uint32_t o = gi - __shfl_sync(FULL, ex, l);
-                                const uint32_t d0 = __shfl_sync(FULL, deg[0], l);
-                                const uint32_t bb0 = __shfl_sync(FULL, beg[0], l);
-                                const uint32_t bb1 = __shfl_sync(FULL, beg[1], l);
-                                const uint32_t v0 = __shfl_sync(FULL, dv[0], l);
-                                const uint32_t v1 = __shfl_sync(FULL, dv[1], l);
-                                const bool second = o >= d0;
-                                const uint32_t ai = second ? bb1 + (o - d0) : bb0 + o;
-                                if (gi < total && !RN_BAD(ai < a.n_arcs, 15, gi, ai)) {
-                                    const uint2 arc = __ldg(&a.adj[ai]);
-                                    y[k] = arc.x;
-                                    nd[k] = (second ? v1 : v0) + arc.y;  // <= bound + 2^24: no overflow
-                                }
+                            if (gi < total && !RN_BAD(ai < a.n_arcs, 15, gi, ai)) {
+                                const uint2 arc = __ldg(&a.adj[ai]);
+                                y[k] = arc.x;
+                                nd[k] = (second ? v1 : v0) + arc.y;  // <= bound + 2^24: no overflow
+                                if (HIER && (arc.x < part_lo || arc.x >= part_hi)) nd[k] = INF;  // leaves the part
                             }
                         }
                         // every first probe, then every atomic, of the batch issued back to back
@@ -1543,32 +1555,26 @@ __global__ void __launch_bounds__(src_warps(MS) * 32, SRC_BLOCKS_PER_SM) k_sourc
                         uint32_t h[AP], kv[AP];
 #pragma unroll
                         for (int k = 0; k < AP; k++) {
-                            h[k] = EMPTY;
-                            kv[k] = 0u;
-                            if (uint32_t(k) < nk) {
-                                if (nd[k] <= bound && RN_BAD(y[k] < a.n_nodes, 16, b0 + 32 * k + lane, y[k])) nd[k] = INF;
-                                h[k] = (y[k] * 0x9E3779B1u) >> (32 - log2u(MS));
-                                kv[k] = nd[k] <= bound ? ((volatile uint32_t *)key)[h[k]] : 0u;
-                            }
+                            if (nd[k] <= bound && RN_BAD(y[k] < a.n_nodes, 16, b0 + 32 * k + lane, y[k])) nd[k] = INF;
+                            h[k] = (y[k] * 0x9E3779B1u) >> (32 - log2u(MS));
+                            kv[k] = nd[k] <= bound ? ((volatile uint32_t *)key)[h[k]] : 0u;
                         }
                         uint32_t ins_count = 0;
                         bool full = false;
 #pragma unroll
                         for (int k = 0; k < AP; k++) {
-                            if (uint32_t(k) < nk) {
-                                bool ins = false;
-                                if (nd[k] > bound) {
-                                    h[k] = EMPTY;
-                                } else if ((kv[k] & SK_NODE) != y[k]) {
-                                    // the home slot holds another node (keys never leave the
-                                    // map during a search): probe on from the next slot; it was
-                                    // empty: probe from it (another lane may have taken it since)
-                                    const uint32_t h0 = kv[k] == SK_EMPTY ? h[k] : (h[k] + 1) & (MS - 1);
-                                    h[k] = src_slot<MS>(key, y[k], h0, &ins);
-                                }
-                                ins_count += ins;
-                                full |= nd[k] <= bound && h[k] == EMPTY;
+                            bool ins = false;
+                            if (nd[k] > bound) {
+                                h[k] = EMPTY;
+                            } else if ((kv[k] & SK_NODE) != y[k]) {
+                                // the home slot holds another node (keys never leave the map
+                                // during a search): probe on from the next slot; it was empty:
+                                // probe from it (another lane may have taken it since)
+                                const uint32_t h0 = kv[k] == SK_EMPTY ? h[k] : (h[k] + 1) & (MS - 1);
+                                h[k] = src_slot<MS>(key, y[k], h0, &ins);
                             }
+                            ins_count += ins;
+                            full |= nd[k] <= bound && h[k] == EMPTY;
                         }
                         fill += __reduce_add_sync(FULL, ins_count);  // once per batch
                         uint32_t old[AP];
@@ -1582,15 +1588,13 @@ __global__ void __launch_bounds__(src_warps(MS) * 32, SRC_BLOCKS_PER_SM) k_sourc
                                         : SK_QUEUED;
 #pragma unroll
                         for (int k = 0; k < AP; k++) {
-                            if (uint32_t(k) < nk) {
-                                const bool push = h[k] != EMPTY && nd[k] < old[k] && nd[k] < tau32 && !(kf[k] & SK_QUEUED);
-                                const uint32_t pb = __ballot_sync(FULL, push);
-                                if (push) {
-                                    const uint32_t qi = nnext + __popc(pb & lt);
-                                    if (qi < QS) qnext[qi] = h[k];
-                                }
-                                nnext += __popc(pb);
+                            const bool push = h[k] != EMPTY && nd[k] < old[k] && nd[k] < tau32 && !(kf[k] & SK_QUEUED);
+                            const uint32_t pb = __ballot_sync(FULL, push);
+                            if (push) {
+                                const uint32_t qi = nnext + __popc(pb & lt);
+                                if (qi < QS) qnext[qi] = h[k];
                             }
+                            nnext += __popc(pb);
                         }
                         if (__any_sync(FULL, full) || fill > a.max_fill) fail = true;
                     }
@@ -1649,6 +1653,25 @@ __global__ void __launch_bounds__(src_warps(MS) * 32, SRC_BLOCKS_PER_SM) k_sourc
                 const uint32_t b = __ballot_sync(FULL, hit);  // never on SK_EMPTY
                 if (lane == 0) hits[c >> 5] = b;
                 cnt += __popc(b);
+            }
+            if (HIER) {
+                // the routes to the part's border nodes (the inside routes that the search
+                // from an exit arc's far end continues)
+#pragma unroll 4
+                for (uint32_t c = 0; c < MS; c += 32) {
+                    const uint32_t kk = key[c + lane];
+                    const uint32_t yy = kk & SK_NODE;
+                    const bool brd = kk != SK_EMPTY && ((__ldg(&a.border_bits[yy >> 5]) >> (yy & 31)) & 1u);
+                    const uint32_t bb = __ballot_sync(FULL, brd);
+                    if (!bb) continue;
+                    unsigned long long at = 0;
+                    if (lane == 0) at = atomicAdd(a.brd_count, (unsigned long long)__popc(bb));
+                    at = __shfl_sync(FULL, at, 0) + __popc(bb & lt);
+                    if (brd && at < a.brd_cap) {
+                        a.brd_key[at] = ((unsigned long long)si << 32) | yy;
+                        a.brd_d[at] = dist[c + lane];
+                    }
+                }
             }
             unsigned long long base = 0;
             if (lane == 0 && cnt) {
@@ -2044,6 +2067,28 @@ __global__ void k_rs_scatter(const unsigned long long *__restrict__ kin, const u
     }
 }
 
+// Sort n (key, value) records by the listed digit shifts (least significant first; a
+// shift >= 64 takes the value's bits), passing between (k0, v0) and (k1, v1); returns the
+// pair of buffers that holds the sorted records.
+static std::pair<unsigned long long *, uint32_t *> sort_kv(Workspace *ws, unsigned long long *k0, uint32_t *v0,
+                                                           unsigned long long *k1, uint32_t *v1, uint64_t n,
+                                                           const std::vector<int> &shifts, cudaStream_t st) {
+    if (n == 0) return {k0, v0};
+    if (n > 0xFFFFFFFFull) fail(RN_EINVAL, "more than 2^32 - 1 records to sort");
+    const uint32_t nblocks = uint32_t((n + RS_TILE - 1) / RS_TILE);
+    grow(ws, &ws->hist, &ws->hist_cap, hist_words(uint64_t(nblocks) * 256), 4);
+    for (int sh : shifts) {
+        k_rs_hist<<<nblocks, RS_THREADS, 0, st>>>(k0, v0, n, sh, ws->hist, nblocks);
+        ws->launches += scan_hist(ws->hist, nblocks * 256, st) + 2;
+        k_rs_scatter<<<nblocks, RS_THREADS, 0, st>>>(k0, v0, k1, v1, n, sh, ws->hist, nblocks, nullptr, nullptr,
+                                                     nullptr, 32);
+        std::swap(k0, k1);
+        std::swap(v0, v1);
+    }
+    RN_CUDA(cudaGetLastError());
+    return {k0, v0};
+}
+
 // Sort n records in (keyA, valA) by the listed digit shifts (least significant first);
 // the last pass writes the struct-of-arrays result into out.
 static void radix_sort_to_pairs(Workspace *ws, uint64_t n, const std::vector<int> &shifts,
@@ -2365,22 +2410,22 @@ static Control search_all(const DeviceGraph &g, Workspace *ws, uint32_t T, Searc
 
 // ---------------------------------------------------- source search, host side ----
 
-template <uint32_t MS>
+template <uint32_t MS, bool HIER = false>
 static void launch_source(const SearchArgs &a, uint32_t grid, cudaStream_t st) {
     constexpr uint32_t smem = src_warps(MS) * src_words(MS) * 4;
     static std::once_flag once[MAX_DEVICES];
     std::call_once(once[attr_device()], [&] {
-        RN_CUDA(cudaFuncSetAttribute(k_source_search<MS>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)));
-        RN_CUDA(cudaFuncSetAttribute(k_source_search<MS>, cudaFuncAttributePreferredSharedMemoryCarveout, 100));
+        RN_CUDA(cudaFuncSetAttribute(k_source_search<MS, HIER>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)));
+        RN_CUDA(cudaFuncSetAttribute(k_source_search<MS, HIER>, cudaFuncAttributePreferredSharedMemoryCarveout, 100));
     });
-    k_source_search<MS><<<grid, src_warps(MS) * 32, smem, st>>>(a);
+    k_source_search<MS, HIER><<<grid, src_warps(MS) * 32, smem, st>>>(a);
     RN_CUDA(cudaGetLastError());
 }
 
 template <uint32_t MS>
 static int source_occupancy() {
     int b = 0;
-    RN_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_source_search<MS>, src_warps(MS) * 32,
+    RN_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_source_search<MS, false>, src_warps(MS) * 32,
                                                           src_warps(MS) * src_words(MS) * 4));
     return b;
 }
@@ -2400,7 +2445,8 @@ static int source_blocks_per_sm(uint32_t ms) {
 // src_warps sources up to three blocks per SM of the device.  The warp search uses no slab,
 // so a server's request is not held to the slab regions it was given (those serve its
 // tile fallback): its blocks share the SMs with the other requests' as they free up.
-static void source_launch(uint32_t ms, SearchArgs a, uint32_t items, Workspace *ws, cudaStream_t st) {
+static void source_launch(uint32_t ms, SearchArgs a, uint32_t items, Workspace *ws, cudaStream_t st,
+                          bool hier = false) {
     a.H = ms;
     a.hshift = 32 - log2u(ms);
     a.max_fill = ms * 7 / 8;
@@ -2408,11 +2454,15 @@ static void source_launch(uint32_t ms, SearchArgs a, uint32_t items, Workspace *
     const uint32_t per_block = src_warps(ms);
     const uint32_t resident = std::max<uint32_t>(1, uint32_t(ws->num_sms) * SRC_BLOCKS_PER_SM);
     const uint32_t grid = std::max<uint32_t>(1, std::min<uint32_t>((items + per_block - 1) / per_block, resident));
-    switch (ms) {
-        case 1024: launch_source<1024>(a, grid, st); break;
-        case 2048: launch_source<2048>(a, grid, st); break;
-        case 4096: launch_source<4096>(a, grid, st); break;
-        case 8192: launch_source<8192>(a, grid, st); break;
+    switch (ms * 2 + (hier ? 1 : 0)) {
+        case 2048: launch_source<1024>(a, grid, st); break;
+        case 4096: launch_source<2048>(a, grid, st); break;
+        case 8192: launch_source<4096>(a, grid, st); break;
+        case 16384: launch_source<8192>(a, grid, st); break;
+        case 2049: launch_source<1024, true>(a, grid, st); break;
+        case 4097: launch_source<2048, true>(a, grid, st); break;
+        case 8193: launch_source<4096, true>(a, grid, st); break;
+        case 16385: launch_source<8192, true>(a, grid, st); break;
         default: fail(RN_EINTERNAL, "warp map size must be 1024 .. 8192");
     }
     ws->launches++;
@@ -3827,6 +3877,659 @@ void run_box(const DeviceGraph &g, Workspace *ws, BoxState **state, const Engine
     *leaves_whole = bs->counts_host[2];
     if (k) run_kcp(g, ws, cfg, median_w, oR, kR, oS, kS, k, theta, out, stream, stats);
     else run_join(g, ws, cfg, median_w, oR, kR, oS, kS, theta, out, stream, stats);
+}
+
+// ------------------------------------------------------ hierarchical variant ----
+// The paper's hierarchical processing (Section 4; Algorithms 2-4) on the GPU.  The graph's
+// partition hierarchy (Algorithm 1) is cut into parts of at most a given size (the
+// granularity the paper chooses by its degree of parallelism); then
+//   1. local processing: from every u in R a search confined to u's own part (no arc that
+//      leaves the part is relaxed), which gives the pairs inside the part and the routes
+//      from u to the part's border nodes ("inside routes": a border node has an arc that
+//      leaves its part);
+//   2. cross-edge expansion: each route (u, b, d) is extended over every arc b -> f that
+//      leaves u's part, giving (u, f, d + w); for every far end f one search runs (bounded
+//      by theta less the least such offset), and its S-hits are shared by every u that
+//      reaches f -- the reuse of the inside routes that Algorithm 4 makes;
+//   3. combination: every (u, f, off) with every hit (f, y, e) of f gives the candidate
+//      (u, y, off + e) within theta, and each pair keeps its least distance, merged with
+//      the local pairs (Algorithm 3 merging the partial results).
+// Exactness (a reading: the listing expands a cross-edge only inside the sibling partition,
+// which can overstate a distance whose shortest path crosses a border more than once):
+// here the search from f is not confined.  A shortest u -> y path either stays in u's part,
+// or leaves it a first time over some arc b -> f; its part before that arc lies inside the
+// part, so its length is at least d_part(u, b) + w(b, f) + d(f, y), which is a u -> y walk;
+// the least candidate is therefore dist(u, y).  k closest pairs take the join within a
+// radius grown until it holds k pairs (radius passes), then the first k in (d, u, v) order.
+
+struct HierState {
+    std::vector<uint32_t> cut;      // part starts the border bitmap below was built for
+    cudaEvent_t ev[2] = {nullptr, nullptr};
+    uint32_t *part_start = nullptr, *border = nullptr;
+    uint32_t cap_parts = 0, cap_border = 0;
+    struct Buf {
+        void *p = nullptr;
+        size_t bytes = 0;
+    };
+    std::map<std::string, Buf> bufs;
+    unsigned long long *count = nullptr, *count_host = nullptr;  // 4 device counters, pinned copy
+    template <class T>
+    T *get(const char *name, uint64_t n) {
+        Buf &b = bufs[name];
+        const size_t want = std::max<size_t>(size_t(n) * sizeof(T), 256);
+        if (b.bytes < want) {
+            device_free(b.p);
+            b.p = nullptr;
+            b.bytes = 0;
+            b.p = device_alloc(want + want / 4);
+            b.bytes = want + want / 4;
+        }
+        return static_cast<T *>(b.p);
+    }
+};
+
+void hier_destroy(HierState *h) {
+    if (!h) return;
+    device_free(h->part_start);
+    device_free(h->border);
+    for (auto &kv : h->bufs) device_free(kv.second.p);
+    device_free(h->count);
+    if (h->count_host) cudaFreeHost(h->count_host);
+    for (cudaEvent_t e : h->ev)
+        if (e) cudaEventDestroy(e);
+    delete h;
+}
+
+// The part of internal id x: the last part starting at or before it.
+__device__ __forceinline__ uint32_t part_of(const uint32_t *__restrict__ start, uint32_t nparts, uint32_t x) {
+    uint32_t lo = 0, hi = nparts - 1;
+    while (lo < hi) {
+        const uint32_t mid = (lo + hi + 1) >> 1;
+        if (start[mid] <= x) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
+// Border bitmap: node x is a border node when one of its arcs leaves its part.
+__global__ void k_border_bits(const uint32_t *__restrict__ row_ptr, const uint2 *__restrict__ adj, uint32_t n,
+                              const uint32_t *__restrict__ start, uint32_t nparts, uint32_t *bits) {
+    for (uint32_t x = blockIdx.x * blockDim.x + threadIdx.x; x < n; x += gridDim.x * blockDim.x) {
+        const uint32_t p = part_of(start, nparts, x);
+        const uint32_t lo = start[p], hi = p + 1 < nparts ? start[p + 1] : n;
+        bool out = false;
+        for (uint32_t e = row_ptr[x]; e < row_ptr[x + 1] && !out; e++) {
+            const uint32_t y = adj[e].x;
+            out = y < lo || y >= hi;
+        }
+        if (out) atomicOr(&bits[x >> 5], 1u << (x & 31));
+    }
+}
+
+// Extend every inside route (si << 32 | b, d) over the arcs b -> f that leave source si's
+// part: exit routes (orig(f) << 32 | si, d + w) within theta.  Warp-aggregated appends.
+__global__ void k_exit_expand(const unsigned long long *__restrict__ brd_key, const uint32_t *__restrict__ brd_d,
+                              uint64_t nb, const uint2 *__restrict__ src_range, const uint32_t *__restrict__ row_ptr,
+                              const uint2 *__restrict__ adj, const uint32_t *__restrict__ iperm, uint32_t theta,
+                              unsigned long long *ex_key, uint32_t *ex_d, uint64_t cap, unsigned long long *count) {
+    const uint32_t lane = threadIdx.x & 31;
+    for (uint64_t base = (uint64_t(blockIdx.x) * blockDim.x + threadIdx.x) & ~31ull; base < nb;
+         base += uint64_t(gridDim.x) * blockDim.x) {
+        const uint64_t i = base + lane;
+        uint32_t si = 0, x = 0, d = 0, e0 = 0, e1 = 0, c = 0;
+        uint2 r = make_uint2(0, 0);
+        if (i < nb) {
+            const unsigned long long kk = brd_key[i];
+            si = uint32_t(kk >> 32);
+            x = uint32_t(kk);
+            d = brd_d[i];
+            r = src_range[si];
+            e0 = row_ptr[x];
+            e1 = row_ptr[x + 1];
+            for (uint32_t e = e0; e < e1; e++) {
+                const uint2 a = adj[e];
+                c += (a.x < r.x || a.x >= r.y) && uint64_t(d) + a.y <= theta;
+            }
+        }
+        uint32_t incl = c;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t t = __shfl_up_sync(FULL, incl, o);
+            if (lane >= uint32_t(o)) incl += t;
+        }
+        unsigned long long at = 0;
+        if (lane == 31 && incl) at = atomicAdd(count, (unsigned long long)incl);
+        at = __shfl_sync(FULL, at, 31) + (incl - c);
+        for (uint32_t e = e0; e < e1 && c; e++) {
+            const uint2 a = adj[e];
+            if ((a.x < r.x || a.x >= r.y) && uint64_t(d) + a.y <= theta) {
+                if (at < cap) {
+                    ex_key[at] = ((unsigned long long)iperm[a.x] << 32) | si;
+                    ex_d[at] = d + a.y;
+                }
+                at++;
+            }
+        }
+    }
+}
+
+// Flags over records sorted by key: keep[i] = first of its key, head[i] = first of its
+// key's upper 32 bits (its far end f).
+__global__ void k_exit_flags(const unsigned long long *__restrict__ key, uint64_t m, uint32_t *keep, uint32_t *head) {
+    for (uint64_t i = uint64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < m; i += uint64_t(gridDim.x) * blockDim.x) {
+        const unsigned long long k = key[i];
+        const bool first = i == 0 || key[i - 1] != k;
+        keep[i] = first;
+        head[i] = first && (i == 0 || (key[i - 1] >> 32) != (k >> 32));
+    }
+}
+
+// Compact the kept exit routes (each (f, si) with its least offset: records sorted by key
+// then offset) into (j << 32 | si, off), j the index of far end f in f_list; f_list[j] =
+// orig(f), fmin[j] = its least offset (fmin starts at INF).
+__global__ void k_exit_compact(const unsigned long long *__restrict__ key, const uint32_t *__restrict__ d, uint64_t m,
+                               const uint32_t *__restrict__ keep, const uint32_t *__restrict__ keep_at,
+                               const uint32_t *__restrict__ head, const uint32_t *__restrict__ head_at,
+                               unsigned long long *e_key, uint32_t *e_off, uint32_t *f_list, uint32_t *fmin) {
+    for (uint64_t i = uint64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < m; i += uint64_t(gridDim.x) * blockDim.x) {
+        if (!keep[i]) continue;
+        const unsigned long long k = key[i];
+        const uint32_t j = head_at[i] + head[i] - 1;
+        if (head[i]) f_list[j] = uint32_t(k >> 32);
+        e_key[keep_at[i]] = ((unsigned long long)j << 32) | uint32_t(k);
+        e_off[keep_at[i]] = d[i];
+        atomicMin(&fmin[j], d[i]);
+    }
+}
+
+// Sources of the searches from the far ends: internal ids and per-source tables.
+__global__ void k_exit_sources(const uint32_t *__restrict__ f_list, const uint32_t *__restrict__ fmin, uint32_t nf,
+                               const uint32_t *__restrict__ perm, uint32_t theta, uint32_t delta, uint32_t *src,
+                               uint32_t *tb, uint32_t *td, uint32_t *ti) {
+    for (uint32_t j = blockIdx.x * blockDim.x + threadIdx.x; j < nf; j += gridDim.x * blockDim.x) {
+        src[j] = perm[f_list[j]];
+        tb[j] = theta - min(fmin[j], theta);
+        td[j] = delta;
+        ti[j] = 0;
+    }
+}
+
+// The hits of far end j: the run of sorted hit keys (orig(f) << vbits | v) with f_list[j].
+__global__ void k_hit_ranges(const unsigned long long *__restrict__ hkey, uint64_t nh,
+                             const uint32_t *__restrict__ f_list, uint32_t nf, uint32_t vbits, uint2 *range) {
+    for (uint32_t j = blockIdx.x * blockDim.x + threadIdx.x; j < nf; j += gridDim.x * blockDim.x) {
+        const unsigned long long lo_key = (unsigned long long)f_list[j] << vbits;
+        const unsigned long long hi_key = (unsigned long long)(f_list[j] + 1ull) << vbits;
+        uint64_t a = 0, b = nh;
+        while (a < b) {
+            const uint64_t mid = (a + b) >> 1;
+            if (hkey[mid] < lo_key) a = mid + 1;
+            else b = mid;
+        }
+        uint64_t c = a, e = nh;
+        while (c < e) {
+            const uint64_t mid = (c + e) >> 1;
+            if (hkey[mid] < hi_key) c = mid + 1;
+            else e = mid;
+        }
+        range[j] = make_uint2(uint32_t(a), uint32_t(c));
+    }
+}
+
+// Candidates: exit route (j << 32 | si, off) with every hit (f_j, v, e) of its far end,
+// (orig(u_si) << vbits | v, off + e) when within theta.  A warp per exit route.
+__global__ void k_hier_combine(const unsigned long long *__restrict__ e_key, const uint32_t *__restrict__ e_off,
+                               uint64_t ne, const uint2 *__restrict__ range, const unsigned long long *__restrict__ hkey,
+                               const uint32_t *__restrict__ hd, const uint32_t *__restrict__ src,
+                               const uint32_t *__restrict__ iperm, uint32_t theta, uint32_t vbits,
+                               unsigned long long *c_key, uint32_t *c_d, uint64_t cap, unsigned long long *count) {
+    const uint32_t lane = threadIdx.x & 31, lt = (1u << lane) - 1;
+    const uint64_t warps = uint64_t(gridDim.x) * (blockDim.x / 32);
+    const unsigned long long vmask = (1ull << vbits) - 1;
+    for (uint64_t i = uint64_t(blockIdx.x) * (blockDim.x / 32) + (threadIdx.x >> 5); i < ne; i += warps) {
+        const unsigned long long ek = e_key[i];
+        const uint32_t j = uint32_t(ek >> 32), si = uint32_t(ek), off = e_off[i];
+        const uint2 r = range[j];
+        const unsigned long long u = (unsigned long long)iperm[src[si]] << vbits;
+        for (uint32_t h0 = r.x; h0 < r.y; h0 += 32) {
+            const uint32_t h = h0 + lane;
+            const bool ok = h < r.y && uint64_t(off) + hd[h] <= theta;
+            const uint32_t b = __ballot_sync(FULL, ok);
+            if (!b) continue;
+            unsigned long long at = 0;
+            if (lane == 0) at = atomicAdd(count, (unsigned long long)__popc(b));
+            at = __shfl_sync(FULL, at, 0) + __popc(b & lt);
+            if (ok && at < cap) {
+                c_key[at] = u | (hkey[h] & vmask);
+                c_d[at] = off + hd[h];
+            }
+        }
+    }
+}
+
+// Flags of the first record of every key (records sorted by key, then distance).
+__global__ void k_first_of_key(const unsigned long long *__restrict__ key, uint64_t m, uint32_t *first) {
+    for (uint64_t i = uint64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < m; i += uint64_t(gridDim.x) * blockDim.x)
+        first[i] = i == 0 || key[i - 1] != key[i];
+}
+
+// The first (least-distance) record of every key, compacted in key order.
+__global__ void k_first_compact(const unsigned long long *__restrict__ key, const uint32_t *__restrict__ d, uint64_t m,
+                                const uint32_t *__restrict__ first, const uint32_t *__restrict__ at,
+                                unsigned long long *okey, uint32_t *od) {
+    for (uint64_t i = uint64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < m; i += uint64_t(gridDim.x) * blockDim.x) {
+        if (!first[i]) continue;
+        okey[at[i]] = key[i];
+        od[at[i]] = d[i];
+    }
+}
+
+// Records (key, d) to struct-of-arrays pairs (u = key >> vbits, v = the low bits, d).
+__global__ void k_split_pairs(const unsigned long long *__restrict__ key, const uint32_t *__restrict__ d, uint64_t n,
+                              uint32_t vbits, uint32_t *u, uint32_t *v, uint32_t *dd) {
+    const unsigned long long vmask = (1ull << vbits) - 1;
+    for (uint64_t i = uint64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += uint64_t(gridDim.x) * blockDim.x) {
+        u[i] = uint32_t(key[i] >> vbits);
+        v[i] = uint32_t(key[i] & vmask);
+        dd[i] = d[i];
+    }
+}
+
+namespace {
+
+uint32_t grid_of(const Workspace *ws, uint64_t n, uint32_t per = 256) {
+    return uint32_t(std::max<uint64_t>(1, std::min<uint64_t>((n + per - 1) / per, uint64_t(ws->num_sms) * 16)));
+}
+
+// Digit shifts of a radix sort over the key bits [lo, hi) and then the value bits [0, vhi)
+// (least significant first: values sort first when given first).
+void add_shifts(std::vector<int> *sh, uint32_t lo, uint32_t hi, int offset = 0) {
+    for (uint32_t b = lo; b < hi; b += 8) sh->push_back(offset + int(b));
+}
+
+}  // namespace
+
+
+void run_hier(const DeviceGraph &g, Workspace *ws, HierState **state, const EngineConfig &cfg, uint32_t median_w,
+              const std::vector<uint32_t> &perm, const std::vector<uint32_t> &part_start, const uint32_t *R,
+              uint32_t nR, const uint32_t *S, uint32_t nS, uint64_t k, uint32_t theta, rn_dpairs *out, void *stream,
+              rn_query_stats *stats, rn_hier_stats *hs) {
+    cudaStream_t st = (cudaStream_t)stream;
+    if (theta == RN_INF) theta = RN_THETA_MAX;
+    if (theta > RN_THETA_MAX) fail(RN_EINVAL, "theta must be <= 2^31 or RN_INF");
+    if (g.n >= SK_NODE) fail(RN_EINVAL, "the hierarchical variant takes graphs of fewer than 2^28 nodes");
+    if (part_start.empty() || part_start[0] != 0) fail(RN_EINTERNAL, "hierarchy cut does not start at node 0");
+    const uint32_t nparts = uint32_t(part_start.size());
+    uint32_t max_part = 0;
+    for (uint32_t p = 0; p < nparts; p++)
+        max_part = std::max(max_part, (p + 1 < nparts ? part_start[p + 1] : g.n) - part_start[p]);
+    // a local search never leaves its part: a warp map holding the largest part never overflows
+    uint32_t map_slots = 0;
+    for (uint32_t m = SRC_MS_MIN; m <= SRC_MS_MAX && !map_slots; m *= 2)
+        if (double(max_part) <= src_fit(m)) map_slots = m;
+    if (!map_slots) fail(RN_EINVAL, "the hierarchical variant takes parts of at most 6516 nodes");
+    std::lock_guard<std::mutex> device_lock(ws->sh->mu);
+    Range range("rn.hier");
+    *stats = rn_query_stats{};
+    *hs = rn_hier_stats{};
+    hs->parts = nparts;
+    ws->launches = 0;
+    if (!*state) *state = new HierState();
+    HierState *h = *state;
+    if (!h->count) {
+        h->count = (unsigned long long *)device_alloc(4 * 8);
+        RN_CUDA(cudaMallocHost(&h->count_host, 4 * 8));
+        RN_CUDA(cudaEventCreate(&h->ev[0]));
+        RN_CUDA(cudaEventCreate(&h->ev[1]));
+    }
+    RN_CUDA(cudaEventRecord(ws->ev0, st));
+    auto counts = [&] {
+        RN_CUDA(cudaMemcpyAsync(h->count_host, h->count, 4 * 8, cudaMemcpyDeviceToHost, st));
+        RN_CUDA(cudaStreamSynchronize(st));
+    };
+    double phase_ms[3] = {0, 0, 0};
+    auto mark = [&] { RN_CUDA(cudaEventRecord(h->ev[0], st)); };
+    auto lap = [&](int p) {
+        RN_CUDA(cudaEventRecord(h->ev[1], st));
+        RN_CUDA(cudaEventSynchronize(h->ev[1]));
+        float t = 0;
+        RN_CUDA(cudaEventElapsedTime(&t, h->ev[0], h->ev[1]));
+        phase_ms[p] += t;
+    };
+    // the border bitmap of this cut of the hierarchy (kept for the next query)
+    if (h->cut != part_start) {
+        const uint32_t nw = (g.n + 31) / 32;
+        if (h->cap_parts < nparts) {
+            device_free(h->part_start);
+            h->part_start = nullptr;
+            h->part_start = (uint32_t *)device_alloc(size_t(nparts) * 4);
+            h->cap_parts = nparts;
+        }
+        if (h->cap_border < std::max<uint32_t>(nw, 1)) {
+            device_free(h->border);
+            h->border = nullptr;
+            h->border = (uint32_t *)device_alloc(std::max<size_t>(nw, 1) * 4);
+            h->cap_border = std::max<uint32_t>(nw, 1);
+        }
+        RN_CUDA(cudaMemcpyAsync(h->part_start, part_start.data(), size_t(nparts) * 4, cudaMemcpyHostToDevice, st));
+        RN_CUDA(cudaMemsetAsync(h->border, 0, std::max<size_t>(nw, 1) * 4, st));
+        if (g.n)
+            k_border_bits<<<grid_of(ws, g.n), 256, 0, st>>>(g.row_ptr, reinterpret_cast<const uint2 *>(g.adj), g.n,
+                                                            h->part_start, nparts, h->border);
+        RN_CUDA(cudaGetLastError());
+        RN_CUDA(cudaStreamSynchronize(st));  // part_start is the caller's host vector
+        h->cut = part_start;
+        ws->launches++;
+    }
+    // sources: R in internal ids, ascending, each with its part's id range
+    std::vector<uint32_t> src(nR);
+    for (uint32_t j = 0; j < nR; j++) src[j] = perm[R[j]];
+    std::sort(src.begin(), src.end());
+    std::vector<uint2> rng(nR);
+    for (uint32_t j = 0; j < nR; j++) {
+        const uint32_t p = uint32_t(std::upper_bound(part_start.begin(), part_start.end(), src[j]) - part_start.begin()) - 1;
+        rng[j] = make_uint2(part_start[p], p + 1 < nparts ? part_start[p + 1] : g.n);
+    }
+    uint32_t *d_src = h->get<uint32_t>("src", nR);
+    uint2 *d_rng = h->get<uint2>("range", nR);
+    uint32_t *dR = h->get<uint32_t>("R", nR), *dS = h->get<uint32_t>("S", nS);
+    if (nR) {
+        RN_CUDA(cudaMemcpyAsync(d_src, src.data(), size_t(nR) * 4, cudaMemcpyHostToDevice, st));
+        RN_CUDA(cudaMemcpyAsync(d_rng, rng.data(), size_t(nR) * 8, cudaMemcpyHostToDevice, st));
+        RN_CUDA(cudaMemcpyAsync(dR, R, size_t(nR) * 4, cudaMemcpyHostToDevice, st));
+    }
+    if (nS) RN_CUDA(cudaMemcpyAsync(dS, S, size_t(nS) * 4, cudaMemcpyHostToDevice, st));
+    prep_sets(g, ws, dR, nR, dS, nS, st);  // validation and the S bitmap
+    check_control(read_control(ws, st));   // (host vectors above are copied by now)
+    ensure_ranges(&ws->failed, &ws->failed_cap, std::max<uint32_t>(nR, 1));
+    ensure_ranges(&ws->failed2, &ws->failed2_cap, std::max<uint32_t>(nR, 1));
+    const uint32_t vbits = bits_for(g.n);
+    const uint32_t delta = choose_delta(cfg, median_w, true);
+    uint64_t retried = 0;
+
+    // The join within bound bnd: every pair's least distance, sorted by (u, v), as records
+    // (orig(u) << vbits | orig(v), d) in (*ok, *od).
+    auto join_at = [&](uint32_t bnd, unsigned long long **ok, uint32_t **od) -> uint64_t {
+        const int dbits = int(bits_for(uint32_t(std::min<uint64_t>(bnd + 1ull, 0xFFFFFFFFull))));
+        // 1. local searches: pairs inside each source's part, routes to its border nodes
+        mark();
+        ensure_pairs(ws, std::max<uint64_t>(ws->pair_cap, uint64_t(nR) * 64));
+        uint64_t brd_cap = std::max<uint64_t>(uint64_t(nR) * 64, 1 << 16);
+        Control c{};
+        unsigned long long *brd_key = nullptr;
+        uint32_t *brd_d = nullptr;
+        for (;;) {
+            brd_key = h->get<unsigned long long>("brd_key", brd_cap);
+            brd_d = h->get<uint32_t>("brd_d", brd_cap);
+            RN_CUDA(cudaMemsetAsync(ws->ctl, 0, sizeof(Control), st));
+            RN_CUDA(cudaMemsetAsync(h->count, 0, 4 * 8, st));
+            SearchArgs a{};
+            a.row_ptr = g.row_ptr;
+            a.adj = reinterpret_cast<const uint2 *>(g.adj);
+            a.iperm = g.iperm;
+            a.sbits = ws->sbits;
+            a.src = d_src;
+            a.bound = bnd;
+            a.delta = delta;
+            a.vbits = vbits;
+            a.ctl = ws->ctl;
+            a.out_key = ws->keyA;
+            a.out_d = ws->valA;
+            a.out_cap = ws->pair_cap;
+            a.nR_fixed = nR;
+            a.ntiles = nR;
+            a.n_nodes = g.n;
+            a.n_arcs = g.arcs;
+            a.failed = ws->failed;
+            a.src_range = d_rng;
+            a.border_bits = h->border;
+            a.brd_key = brd_key;
+            a.brd_d = brd_d;
+            a.brd_cap = brd_cap;
+            a.brd_count = h->count;
+            if (nR) source_launch(map_slots, a, nR, ws, st, true);
+            c = read_control(ws, st);
+            counts();
+            check_control(c);
+            if (c.n_failed) fail(RN_EINTERNAL, "a local search outgrew a map that holds its part");
+            if (c.pairs > ws->pair_cap) {
+                ensure_pairs(ws, c.pairs + c.pairs / 4);
+                continue;
+            }
+            if (h->count_host[0] > brd_cap) {
+                brd_cap = h->count_host[0] + h->count_host[0] / 4;
+                continue;
+            }
+            break;
+        }
+        const uint64_t local = c.pairs, nb = h->count_host[0];
+        lap(0);
+        mark();
+        // 2. exit routes (orig(f) << 32 | si, off); each (f, si) keeps its least offset
+        uint64_t ex_cap = std::max<uint64_t>(nb * 3, 1 << 16), nx = 0;
+        unsigned long long *xk = nullptr;
+        uint32_t *xd = nullptr;
+        for (;;) {
+            xk = h->get<unsigned long long>("ex_key", ex_cap);
+            xd = h->get<uint32_t>("ex_d", ex_cap);
+            RN_CUDA(cudaMemsetAsync(h->count, 0, 4 * 8, st));
+            if (nb) {
+                k_exit_expand<<<grid_of(ws, nb), 256, 0, st>>>(brd_key, brd_d, nb, d_rng, g.row_ptr,
+                                                               reinterpret_cast<const uint2 *>(g.adj), g.iperm, bnd,
+                                                               xk, xd, ex_cap, h->count);
+                ws->launches++;
+            }
+            RN_CUDA(cudaGetLastError());
+            counts();
+            nx = h->count_host[0];
+            if (nx <= ex_cap) break;
+            ex_cap = nx + nx / 4;
+        }
+        unsigned long long *xk2 = h->get<unsigned long long>("ex_key2", nx);
+        uint32_t *xd2 = h->get<uint32_t>("ex_d2", nx);
+        std::vector<int> sh;
+        add_shifts(&sh, 0, uint32_t(dbits), 64);                      // offset
+        add_shifts(&sh, 0, bits_for(std::max<uint32_t>(nR, 2)));      // si
+        add_shifts(&sh, 32, 32 + vbits);                              // orig(f)
+        const auto xs = sort_kv(ws, xk, xd, xk2, xd2, nx, sh, st);
+        uint32_t *keep = h->get<uint32_t>("keep", nx + 1), *keep_at = h->get<uint32_t>("keep_at", hist_words(nx + 1));
+        uint32_t *head = h->get<uint32_t>("head", nx + 1), *head_at = h->get<uint32_t>("head_at", hist_words(nx + 1));
+        uint32_t ne = 0, nf = 0;
+        if (nx) {
+            k_exit_flags<<<grid_of(ws, nx), 256, 0, st>>>(xs.first, nx, keep, head);
+            RN_CUDA(cudaMemsetAsync(keep + nx, 0, 4, st));
+            RN_CUDA(cudaMemsetAsync(head + nx, 0, 4, st));
+            RN_CUDA(cudaMemcpyAsync(keep_at, keep, (nx + 1) * 4, cudaMemcpyDeviceToDevice, st));
+            RN_CUDA(cudaMemcpyAsync(head_at, head, (nx + 1) * 4, cudaMemcpyDeviceToDevice, st));
+            ws->launches += 1 + scan_hist(keep_at, uint32_t(nx + 1), st) + scan_hist(head_at, uint32_t(nx + 1), st);
+            uint32_t *tot = reinterpret_cast<uint32_t *>(h->count_host);
+            RN_CUDA(cudaMemcpyAsync(&tot[0], keep_at + nx, 4, cudaMemcpyDeviceToHost, st));
+            RN_CUDA(cudaMemcpyAsync(&tot[1], head_at + nx, 4, cudaMemcpyDeviceToHost, st));
+            RN_CUDA(cudaStreamSynchronize(st));
+            ne = tot[0];
+            nf = tot[1];
+        }
+        unsigned long long *ek = h->get<unsigned long long>("e_key", ne);
+        uint32_t *eo = h->get<uint32_t>("e_off", ne), *f_list = h->get<uint32_t>("f_list", nf);
+        uint32_t *fmin = h->get<uint32_t>("fmin", nf);
+        if (nx) {
+            RN_CUDA(cudaMemsetAsync(fmin, 0xFF, size_t(std::max<uint32_t>(nf, 1)) * 4, st));
+            k_exit_compact<<<grid_of(ws, nx), 256, 0, st>>>(xs.first, xs.second, nx, keep, keep_at, head, head_at, ek,
+                                                            eo, f_list, fmin);
+            ws->launches++;
+            RN_CUDA(cudaGetLastError());
+        }
+        // 3. one unconfined search from every far end f, bounded by theta less its least
+        // offset (source_search_all: larger maps, then tiles, for balls that outgrow a map)
+        uint32_t *fsrc = h->get<uint32_t>("f_src", nf), *tb = h->get<uint32_t>("f_tb", nf);
+        uint32_t *td = h->get<uint32_t>("f_td", nf), *ti = h->get<uint32_t>("f_ti", nf);
+        if (nf) {
+            k_exit_sources<<<grid_of(ws, nf), 256, 0, st>>>(f_list, fmin, nf, g.perm, bnd, delta, fsrc, tb, td, ti);
+            ws->launches++;
+        }
+        uint64_t hit_cap = std::max<uint64_t>(uint64_t(nf) * 32, 1 << 16), nh = 0;
+        unsigned long long *hk = nullptr;
+        uint32_t *hd = nullptr;
+        if (nf) ensure_slab(ws);  // the tile fallback of balls that outgrow a warp map
+        for (;;) {
+            hk = h->get<unsigned long long>("hit_key", hit_cap);
+            hd = h->get<uint32_t>("hit_d", hit_cap);
+            RN_CUDA(cudaMemsetAsync(ws->ctl, 0, sizeof(Control), st));
+            SearchArgs a{};
+            a.row_ptr = g.row_ptr;
+            a.adj = reinterpret_cast<const uint2 *>(g.adj);
+            a.iperm = g.iperm;
+            a.sbits = ws->sbits;
+            a.src = fsrc;
+            a.bound = bnd;
+            a.delta = delta;
+            a.vbits = vbits;
+            a.ctl = ws->ctl;
+            a.out_key = hk;
+            a.out_d = hd;
+            a.out_cap = hit_cap;
+            a.nR_fixed = nf;
+            a.tile_bound = tb;
+            a.tile_delta = td;
+            a.tile_inst = ti;
+            a.slab = ws->sh->slab;
+            const Control cc =
+                source_search_all(g, ws, a, nf, source_first_map(ws, bnd), 32, bnd, {}, st, &retried, false);
+            check_control(cc);
+            if (cc.pairs > hit_cap) {
+                hit_cap = cc.pairs + cc.pairs / 4;
+                continue;
+            }
+            nh = cc.pairs;
+            break;
+        }
+        unsigned long long *hk2 = h->get<unsigned long long>("hit_key2", nh);
+        uint32_t *hd2 = h->get<uint32_t>("hit_d2", nh);
+        sh.clear();
+        add_shifts(&sh, 0, 2 * vbits);
+        const auto hsrt = sort_kv(ws, hk, hd, hk2, hd2, nh, sh, st);
+        uint2 *fr = h->get<uint2>("f_range", nf);
+        if (nf) {
+            k_hit_ranges<<<grid_of(ws, nf), 256, 0, st>>>(hsrt.first, nh, f_list, nf, vbits, fr);
+            ws->launches++;
+        }
+        lap(1);
+        mark();
+        // 4. candidates through the exit arcs after the local pairs, then every pair's least
+        // distance (records sorted by (u, v) and distance; the first of each (u, v) kept)
+        uint64_t cap = std::max<uint64_t>(local + nh * 2, 1 << 16), m = 0;
+        unsigned long long *mk0 = nullptr;
+        uint32_t *md0 = nullptr;
+        for (;;) {
+            mk0 = h->get<unsigned long long>("m_key", cap);
+            md0 = h->get<uint32_t>("m_d", cap);
+            if (local > cap) {
+                cap = local + local / 4;
+                continue;
+            }
+            h->count_host[0] = local;
+            RN_CUDA(cudaMemcpyAsync(h->count, h->count_host, 8, cudaMemcpyHostToDevice, st));
+            if (local) {
+                RN_CUDA(cudaMemcpyAsync(mk0, ws->keyA, local * 8, cudaMemcpyDeviceToDevice, st));
+                RN_CUDA(cudaMemcpyAsync(md0, ws->valA, local * 4, cudaMemcpyDeviceToDevice, st));
+            }
+            if (ne) {
+                k_hier_combine<<<grid_of(ws, uint64_t(ne) * 32), 256, 0, st>>>(ek, eo, ne, fr, hsrt.first, hsrt.second,
+                                                                               d_src, g.iperm, bnd, vbits, mk0, md0,
+                                                                               cap, h->count);
+                ws->launches++;
+            }
+            RN_CUDA(cudaGetLastError());
+            counts();
+            m = h->count_host[0];
+            if (m <= cap) break;
+            cap = m + m / 4;
+        }
+        unsigned long long *mk1 = h->get<unsigned long long>("m_key2", m);
+        uint32_t *md1 = h->get<uint32_t>("m_d2", m);
+        sh.clear();
+        add_shifts(&sh, 0, uint32_t(dbits), 64);  // distance
+        add_shifts(&sh, 0, 2 * vbits);           // (u, v)
+        const auto msrt = sort_kv(ws, mk0, md0, mk1, md1, m, sh, st);
+        uint32_t *first = h->get<uint32_t>("first", m + 1), *first_at = h->get<uint32_t>("first_at", hist_words(m + 1));
+        unsigned long long *uk = h->get<unsigned long long>("u_key", m);
+        uint32_t *ud = h->get<uint32_t>("u_d", m);
+        uint64_t nu = 0;
+        if (m) {
+            k_first_of_key<<<grid_of(ws, m), 256, 0, st>>>(msrt.first, m, first);
+            RN_CUDA(cudaMemsetAsync(first + m, 0, 4, st));
+            RN_CUDA(cudaMemcpyAsync(first_at, first, (m + 1) * 4, cudaMemcpyDeviceToDevice, st));
+            ws->launches += 2 + scan_hist(first_at, uint32_t(m + 1), st);
+            k_first_compact<<<grid_of(ws, m), 256, 0, st>>>(msrt.first, msrt.second, m, first, first_at, uk, ud);
+            uint32_t *tot = reinterpret_cast<uint32_t *>(h->count_host);
+            RN_CUDA(cudaMemcpyAsync(&tot[0], first_at + m, 4, cudaMemcpyDeviceToHost, st));
+            RN_CUDA(cudaStreamSynchronize(st));
+            nu = tot[0];
+            RN_CUDA(cudaGetLastError());
+        }
+        lap(2);
+        hs->local_pairs = local;
+        hs->border_routes = nb;
+        hs->exit_routes = ne;
+        hs->exit_searches = nf;
+        hs->candidates = m - local;
+        *ok = uk;
+        *od = ud;
+        return nu;
+    };
+
+    unsigned long long *rk = nullptr;
+    uint32_t *rd = nullptr;
+    uint64_t np = 0;
+    uint32_t passes = 0;
+    if (k == 0) {
+        np = join_at(theta, &rk, &rd);
+        passes = 1;
+    } else {
+        // k closest pairs: the join within a radius grown until it holds k pairs (pairs
+        // grow about as the square of the radius on a road network), then the first k by
+        // (d, u, v)
+        uint64_t tau = std::min<uint64_t>(theta, std::max<uint32_t>(delta, 1));
+        for (;;) {
+            np = join_at(uint32_t(tau), &rk, &rd);
+            passes++;
+            if (np >= k || tau >= theta) break;
+            double f = np ? std::sqrt(double(k) / double(np)) * 1.25 : 4.0;
+            tau = std::min<uint64_t>(theta, uint64_t(double(tau) * std::max(f, 1.5)) + 1);
+        }
+        unsigned long long *sk = h->get<unsigned long long>("k_key", np);
+        uint32_t *sd = h->get<uint32_t>("k_d", np);
+        std::vector<int> sh;
+        add_shifts(&sh, 0, 2 * vbits);                                     // (u, v)
+        add_shifts(&sh, 0, bits_for(uint32_t(std::min<uint64_t>(tau + 1, 0xFFFFFFFFull))), 64);  // distance
+        const auto ks = sort_kv(ws, rk, rd, sk, sd, np, sh, st);
+        rk = ks.first;
+        rd = ks.second;
+        np = std::min<uint64_t>(np, k);
+    }
+    dpairs_reserve(out, np);
+    if (np) {
+        k_split_pairs<<<grid_of(ws, np), 256, 0, st>>>(rk, rd, np, vbits, out->u, out->v, out->d);
+        ws->launches++;
+        RN_CUDA(cudaGetLastError());
+    }
+    out->n = np;
+    RN_CUDA(cudaEventRecord(ws->ev1, st));
+    RN_CUDA(cudaEventSynchronize(ws->ev1));
+    float ms = 0;
+    RN_CUDA(cudaEventElapsedTime(&ms, ws->ev0, ws->ev1));
+    stats->pairs = np;
+    stats->tile_width = 1;
+    stats->delta = delta;
+    stats->passes = passes;
+    stats->theta_final = theta;
+    stats->launches = ws->launches;
+    stats->device_ms = ms;
+    stats->retried_tiles = retried;
+    hs->local_ms = phase_ms[0];
+    hs->exit_ms = phase_ms[1];
+    hs->combine_ms = phase_ms[2];
+    hs->max_part = max_part;
 }
 
 // ------------------------------------------------------------------- batch ----

@@ -79,6 +79,7 @@ struct Bisector {
     std::vector<uint32_t> order;  // output: internal id -> original id
     std::mutex leaves_mu;
     std::vector<uint32_t> leaves;  // output: first internal id of every leaf (any order)
+    std::vector<uint64_t> parts;   // output: every part of the hierarchy, (first id << 32) | size
     std::atomic<uint32_t> next_label{1};
     std::atomic<uint32_t> next_stamp{1};
 
@@ -159,6 +160,10 @@ struct Bisector {
     }
 
     void run(std::vector<uint32_t> part, uint32_t lbl, uint32_t out_begin, int depth) {
+        if (!part.empty()) {
+            std::lock_guard<std::mutex> lk(leaves_mu);
+            parts.push_back((uint64_t(out_begin) << 32) | part.size());
+        }
         if (part.size() <= leaf) {
             std::sort(part.begin(), part.end());
             std::copy(part.begin(), part.end(), order.begin() + out_begin);
@@ -221,7 +226,7 @@ struct Bisector {
 }  // namespace
 
 std::vector<uint32_t> bisection_order(const HostGraph &g0, uint32_t leaf_size, float alpha, bool symmetric,
-                                      std::vector<uint32_t> *leaf_starts) {
+                                      std::vector<uint32_t> *leaf_starts, std::vector<uint64_t> *parts) {
     if (alpha < 0.0f || alpha > 1.0f) fail(RN_EINVAL, "alpha must lie in [0, 1]");
     // The partitioning looks at proximity only, so a directed graph is bisected through
     // its symmetrised form (every arc both ways, least weight kept).
@@ -245,6 +250,10 @@ std::vector<uint32_t> bisection_order(const HostGraph &g0, uint32_t leaf_size, f
     if (leaf_starts) {
         *leaf_starts = std::move(b.leaves);
         std::sort(leaf_starts->begin(), leaf_starts->end());
+    }
+    if (parts) {
+        *parts = std::move(b.parts);
+        std::sort(parts->begin(), parts->end());
     }
     return std::move(b.order);
 }

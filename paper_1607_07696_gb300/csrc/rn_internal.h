@@ -49,9 +49,11 @@ HostGraph build_csr(uint32_t n, uint64_t m, const uint32_t *src, const uint32_t 
 // Recursive two-seed bisection (Algorithm 1 with the smoothing of Eq. 1-2).  Returns
 // order[i] = the original id placed at internal id i; every partition of the hierarchy
 // occupies a contiguous range of internal ids.  leaf_starts (if given) receives the
-// first internal id of every leaf, ascending.
+// first internal id of every leaf, ascending; parts (if given) every part of the
+// hierarchy, root and leaves included, as (first internal id << 32) | size, ascending.
 std::vector<uint32_t> bisection_order(const HostGraph &g, uint32_t leaf_size, float alpha, bool symmetric,
-                                      std::vector<uint32_t> *leaf_starts = nullptr);
+                                      std::vector<uint32_t> *leaf_starts = nullptr,
+                                      std::vector<uint64_t> *parts = nullptr);
 
 // CSR of g relabelled so that internal id i is original node order[i].
 HostGraph relabel(const HostGraph &g, const std::vector<uint32_t> &order);
@@ -180,10 +182,23 @@ void upload_geometry(const float *xy, const std::vector<uint32_t> &order, const 
 // at a time where its bounding rectangle lies inside or outside the box -- then the
 // ordinary join (k = 0) or k closest pairs runs on what is left.
 struct BoxState;
+struct HierState;
 void run_box(const DeviceGraph &g, Workspace *ws, BoxState **state, const EngineConfig &cfg, uint32_t median_w,
              const uint32_t *dR, uint32_t nR, const uint32_t *dS, uint32_t nS, const float *box, uint32_t which,
              uint64_t k, uint32_t theta, rn_dpairs *out, void *stream, rn_query_stats *stats, uint64_t *leaves_whole);
 void box_destroy(BoxState *bs);
+
+// The hierarchical variant (rn_engine.cu): searches local to the parts of a cut of the
+// partition hierarchy, searches from the far ends of the arcs that leave a part, and
+// their combination.  part_start: the first internal id of every part of the cut,
+// ascending, the first 0.  R and S: host arrays of original ids (checked); perm the host
+// original -> internal map.  k = 0: the join; else k closest pairs.
+struct HierState;
+void run_hier(const DeviceGraph &g, Workspace *ws, HierState **state, const EngineConfig &cfg, uint32_t median_w,
+              const std::vector<uint32_t> &perm, const std::vector<uint32_t> &part_start, const uint32_t *R,
+              uint32_t nR, const uint32_t *S, uint32_t nS, uint64_t k, uint32_t theta, rn_dpairs *out, void *stream,
+              rn_query_stats *stats, rn_hier_stats *hs);
+void hier_destroy(HierState *hs);
 void free_graph(DeviceGraph *g);
 void dpairs_reserve(rn_dpairs *p, uint64_t cap);
 void dpairs_release(rn_dpairs *p);
@@ -217,5 +232,8 @@ struct rn_graph {
     rn::HostScratch hs;
     rn::PointsState *points = nullptr;  // buffers of point queries, grown as needed
     rn::BoxState *box = nullptr;        // buffers of rectangle-restricted queries
+    rn::HierState *hier = nullptr;      // buffers of the hierarchical variant
+    std::vector<uint64_t> parts;        // the partition hierarchy: (first internal id << 32) | size
+    uint32_t leaf_size = 512;
     int device = 0;
 };

@@ -98,6 +98,13 @@ class rn_request(C.Structure):
                 ("nS", C.c_uint32), ("theta", C.c_uint32), ("k", C.c_uint64)]
 
 
+class rn_hier_stats(C.Structure):
+    _fields_ = [("parts", C.c_uint64), ("max_part", C.c_uint64), ("local_pairs", C.c_uint64),
+                ("border_routes", C.c_uint64), ("exit_routes", C.c_uint64), ("exit_searches", C.c_uint64),
+                ("candidates", C.c_uint64), ("local_ms", C.c_double), ("exit_ms", C.c_double),
+                ("combine_ms", C.c_double)]
+
+
 class rn_serve_config(C.Structure):
     _fields_ = [("slab_bytes", C.c_uint64), ("workers", C.c_uint32), ("max_blocks", C.c_uint32)]
 
@@ -172,6 +179,11 @@ SIGNATURES = {
     "rn_dpairs_free": (None, [C.POINTER(rn_dpairs)]),
     "rn_last_error": (C.c_char_p, []),
     "rn_last_query_stats": (C.c_int, [C.POINTER(rn_query_stats)]),
+    "rn_distance_join_hier": (C.c_int, [_G, _P32, C.c_uint32, _P32, C.c_uint32, C.c_uint32, C.c_uint32,
+                                        C.POINTER(rn_pairs)]),
+    "rn_kcp_hier": (C.c_int, [_G, _P32, C.c_uint32, _P32, C.c_uint32, C.c_uint64, C.c_uint32, C.c_uint32,
+                              C.POINTER(rn_pairs)]),
+    "rn_last_hier_stats": (C.c_int, [C.POINTER(rn_hier_stats)]),
     "rn_version": (C.c_char_p, []),
 }
 
@@ -439,6 +451,31 @@ def rn_last_query_stats() -> dict:
     st = rn_query_stats()
     _check(lib().rn_last_query_stats(C.byref(st)))
     return {f: getattr(st, f) for f, _ in rn_query_stats._fields_}
+
+
+def rn_distance_join_hier(g: Graph, R, S, theta: int, part_size: int = 0):
+    """The join by the hierarchical variant (parts of the partition hierarchy of at most
+    part_size nodes; 0: its leaves): the same (u, v, d), sorted by (u, v)."""
+    r, s = _u32(R), _u32(S)
+    p = rn_pairs()
+    _check(lib().rn_distance_join_hier(g.handle, _p32(r), len(r), _p32(s), len(s), int(theta), int(part_size),
+                                       C.byref(p)))
+    return _take_pairs(p)
+
+
+def rn_kcp_hier(g: Graph, R, S, k: int, theta: int = RN_INF, part_size: int = 0):
+    """k closest pairs by the hierarchical variant; sorted by (d, u, v)."""
+    r, s = _u32(R), _u32(S)
+    p = rn_pairs()
+    _check(lib().rn_kcp_hier(g.handle, _p32(r), len(r), _p32(s), len(s), int(k), int(theta), int(part_size),
+                             C.byref(p)))
+    return _take_pairs(p)
+
+
+def rn_last_hier_stats() -> dict:
+    st = rn_hier_stats()
+    _check(lib().rn_last_hier_stats(C.byref(st)))
+    return {f: getattr(st, f) for f, _ in rn_hier_stats._fields_}
 
 
 def rn_version() -> str:
