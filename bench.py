@@ -56,6 +56,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batch", action="store_true", help="skip the 512-instance batched leg")
     ap.add_argument("--no-serve", action="store_true", help="skip the serving leg")
+    ap.add_argument("--no-hier", action="store_true", help="skip the hierarchical-variant leg")
     ap.add_argument("--serve-requests", type=int, default=2000)
     ap.add_argument("--no-legs", action="store_true",
                     help="only the headline workload: no secondary legs and no CPU baseline")
@@ -353,6 +354,45 @@ def join_264k_leg(rn, steps: int, stream, flush, peak: float, peak_kind: str) ->
             "roofline": roofline(st, n, statistics.mean(search), "road264k_join", peak, peak_kind)}
 
 
+def hier_leg(rn, steps: int) -> dict:
+    """The hierarchical variant (searches local to the parts of the partition hierarchy,
+    the searches from the far ends of the arcs that leave a part shared by every source,
+    min-plus combination) on the 264k-node join, at several part sizes, beside the flat
+    warp search on the same graph: device time per join (CUDA events inside the query),
+    pairs/s and the phase counters; every result checked equal to the flat join's."""
+    import numpy as np
+
+    spec = WORKLOADS["road264k_join"]
+    w, _ = make_workload("road264k_join", 0)
+    e = w.graph
+    g = rn.rn_graph_load(e.src, e.dst, e.w, e.n)
+    theta = spec["theta"]
+    flat = rn.rn_distance_join(g, w.R, w.S, theta)
+    fl = []
+    for _ in range(steps):
+        rn.rn_distance_join(g, w.R, w.S, theta)
+        fl.append(rn.rn_last_query_stats()["device_ms"])
+    res = {"workload": "road264k_join: 264k nodes, |R| = |S| = 10,000 uniform, theta for ~50 matches",
+           "pairs": len(flat[0]), "unit": UNIT, "flat_ms": statistics.median(fl),
+           "flat": len(flat[0]) / (statistics.median(fl) / 1e3)}
+    for part in (0, 2048, 6000):
+        got = rn.rn_distance_join_hier(g, w.R, w.S, theta, part)
+        assert all(np.array_equal(x, y) for x, y in zip(got, flat)), f"hierarchical join (parts {part}) differs"
+        ms = []
+        for _ in range(steps):
+            rn.rn_distance_join_hier(g, w.R, w.S, theta, part)
+            ms.append(rn.rn_last_query_stats()["device_ms"])
+        hs = rn.rn_last_hier_stats()
+        med = statistics.median(ms)
+        res[f"parts_{part or 'leaves'}"] = {
+            "ms": med, "value": len(flat[0]) / (med / 1e3), "vs_flat": statistics.median(fl) / med,
+            "parts": hs["parts"], "max_part": hs["max_part"], "local_pairs": hs["local_pairs"],
+            "border_routes": hs["border_routes"], "exit_routes": hs["exit_routes"],
+            "exit_searches": hs["exit_searches"], "candidates": hs["candidates"],
+            "local_ms": hs["local_ms"], "exit_ms": hs["exit_ms"], "combine_ms": hs["combine_ms"]}
+    return res
+
+
 def kcp_1m_leg(rn, steps: int, stream, flush) -> dict:
     """k closest pairs on the 1.07M-node graph with 50,000 + 50,000 clustered sets, for
     k = 100, 10^4 and 10^6 (unbounded theta): device time per query (sets in device
@@ -615,6 +655,8 @@ def run_engine(args):
         line["join_264k"] = join_264k_leg(rn, min(50, max(3, args.steps // 2)), stream, flush, peak, peak_kind)
     if legs:
         line["kcp_1m"] = kcp_1m_leg(rn, min(10, max(3, args.steps // 2)), stream, flush)
+    if legs and not args.no_hier:
+        line["hierarchical"] = hier_leg(rn, 5)
     if legs and not args.no_batch:
         line["batched"] = batch_leg(rn, 5, 3, stream, flush)
     if legs and not args.no_serve:
