@@ -470,8 +470,8 @@ typedef struct {
 typedef struct {
     uint64_t submitted, completed, failed, pending, running;
     uint64_t cancelled;           /* taken off the queue by rn_serve_cancel */
-    uint64_t groups, grouped;     /* searches that served several small joins at once, and
-                                     the requests they served */
+    uint64_t groups, grouped;     /* searches that served several joins at once, and the
+                                     requests they served */
     uint64_t pairs;               /* pairs returned by completed requests */
     uint64_t slab_bytes, slab_bytes_in_use, slab_bytes_peak;
     uint32_t workers, max_running;/* max_running: most requests on the device at once */
@@ -495,8 +495,8 @@ typedef struct {
  * arena cannot be allocated.
  */
 rn_status rn_serve_create(const rn_graph *g, const rn_serve_config *cfg, rn_server **out);
-/* (Small joins queued one behind another, |R| <= 512, up to 16 of them, are admitted
- * together and searched in one launch, as rn_join_many does.) */
+/* (Joins queued one behind another, up to 64 of them and 32,768 sources in all, are
+ * admitted together and searched in one launch, as rn_join_many does.) */
 /* Queue one request; *ticket identifies it to rn_serve_wait.  RN_EINVAL for a bad
  * request (as rn_distance_join / rn_kcp), found before it is queued. */
 rn_status rn_serve_submit(rn_server *s, const rn_request *q, uint64_t *ticket);

@@ -117,7 +117,15 @@ def _batch(o, out, t0) -> None:
                 ds.append(int(p.d[-1]))
         thetas.append(int(np.median(ds)) if ds else far)
         digests.append(graph_digest(e)["wsum"])
-    out["batch512"] = {"theta": thetas, "sample": 32, "graph_wsum": digests}
+    # the batch's algorithmic arcs (GTEPS numerator): every instance's join at its theta
+    alg_arcs, pairs = 0, 0
+    for sp, th in zip(I.c4_batch_specs(), thetas):
+        e, R, S = I.c4_instance(sp)
+        p = o.graph(e.n, e.src, e.dst, e.w).join_mt(R, S, th, O.host_cores())
+        alg_arcs += p.arcs
+        pairs += len(p)
+    out["batch512"] = {"theta": thetas, "sample": 32, "graph_wsum": digests, "alg_arcs": alg_arcs,
+                       "pairs": pairs}
     print("batch512", len(thetas), f"{time.time() - t0:.1f}s", flush=True)
 
 

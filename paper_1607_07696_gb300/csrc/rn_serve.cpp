@@ -135,10 +135,11 @@ void Server::execute(Worker *w, Request *q) {
     to_host_pairs(w->res, &q->out, w->stream);
 }
 
-// Small joins (|R| <= MB_MAX_R) queued one behind another are taken together, up to
-// MB_MAX of them, and searched in one launch (continuous batching: requests that arrive
-// while others run are admitted into the next free slot as a group).
-constexpr uint32_t MB_MAX = 16, MB_MAX_R = 512;
+// Joins queued one behind another are taken together, up to MB_MAX of them and
+// MB_MAX_SOURCES sources in all (the sources a worker's buffers are reserved for), and
+// searched in one launch (continuous batching: requests that arrive while others run are
+// admitted into the next free slot as a group).
+constexpr uint32_t MB_MAX = 64, MB_MAX_SOURCES = 1u << 15;
 
 void Server::execute_group(Worker *w, std::vector<std::shared_ptr<Request>> &grp, uint32_t units, uint32_t off) {
     Range range("rn.serve.join_many");
@@ -178,12 +179,13 @@ void Server::loop(Worker *w) {
             grp.push_back(pending.front());
             pending.pop_front();
             units = grp[0]->units;
-            auto small_join = [](const Request &r) { return r.k == 0 && r.R.size() <= MB_MAX_R; };
-            if (small_join(*grp[0])) {
-                // the small joins right behind it join the group if their regions fit too
+            auto join = [](const Request &r) { return r.k == 0; };
+            if (join(*grp[0])) {
+                // the joins right behind it join the group while their sources and regions fit
                 uint64_t sources = grp[0]->R.size();
-                while (grp.size() < MB_MAX && !pending.empty() && small_join(*pending.front())) {
+                while (grp.size() < MB_MAX && !pending.empty() && join(*pending.front())) {
                     const uint64_t more = sources + pending.front()->R.size();
+                    if (more > MB_MAX_SOURCES) break;
                     const uint32_t want = std::min<uint32_t>(max_blocks, std::max<uint64_t>(2, (more + tile_width - 1) / tile_width));
                     uint32_t at = 0;
                     if (want > units && !fit(want, &at)) break;
