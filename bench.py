@@ -312,7 +312,9 @@ def batch_leg(rn, steps: int, warmup: int, stream, flush) -> dict:
         "tiles": int(s1["tiles"]), "groups": int(s1["groups"]), "graph_runs": int(s1["graph_runs"]),
         "launches_per_run": int(s1["launches_per_run"]), "plain_launches": int(plain_launches),
         "autotune_s": tune_s, "default_plan_groups": int(s0["groups"]),
-        "tuned": {1: "one plan for all", 2: "plan per size class"}.get(int(s1["tuned"]), "no"),
+        "tuned": {1: f"one plan for all (tile width {int(s1['plan_tile_width'])}, buckets of "
+                     f"{int(s1['plan_delta_mult'])} median weights)",
+                  2: "plan per size class"}.get(int(s1["tuned"]), "no"),
     }
     del b0, b1
     return res

@@ -92,8 +92,9 @@ typedef struct {
                              thread block searches together; 0: the warp search while the
                              balls met so far, scaled to the query's bound (or, before any
                              search, estimated from it), fit a warp map, else tiles of 32
-                             (k closest pairs decides so for each of its radius passes;
-                             batches run tiles, 32 wide unless set) */
+                             (k closest pairs decides so for each of its radius passes,
+                             and takes tiles when the balls at the k-th distance are tiny;
+                             a batch plans its instances itself) */
     uint32_t tile_sources;/* sources per tile, <= tile_width; 0 spreads R over whole
                              waves of resident blocks */
     uint32_t delta;       /* bucket width of the delta-stepping search, in weight units;
@@ -388,22 +389,26 @@ typedef struct {
 } rn_batch_config;
 
 typedef struct {
-    uint32_t instances, groups;  /* groups: launches of one block shape and tile width */
+    uint32_t instances, groups;  /* groups: launches of one plan (search, width or map, shape) */
     uint64_t tiles, retried_tiles, pairs;
     uint32_t eager_runs, graph_runs, launches_per_run;
     uint32_t tuned;              /* 0: not tuned; 1: one candidate plan for every instance;
                                     2: a plan per size class of instance */
     uint32_t candidates;         /* batch runs the tuning took */
     double device_ms;            /* last run, CUDA events on the batch's stream */
+    uint32_t plan_tile_width;    /* tuned = 1: the plan's tile width (1: the warp search) */
+    uint32_t plan_delta_mult;    /* tuned = 1: its bucket width in median arc weights */
 } rn_batch_stats;
 
 /*
  * rn_batch_create -- upload nq theta-joins (each as rn_distance_join, Section 4) for
  * batched execution.  The graphs are copied into one disjoint union on the device (node
- * ids shifted per instance), every instance's sources are padded to whole tiles, and the
- * (instance, source tile) work items are searched by one persistent launch per tile
- * width and block shape, each tile with its instance's theta; all pairs are sorted at
- * once, which groups them by instance in (u, v) order.  cfg may be NULL (no autotuning,
+ * ids shifted per instance).  An instance whose ball, estimated from its theta, fits a
+ * 2048-slot warp map is searched by the warp search (one source per warp, each source
+ * with its instance's theta and bucket width from per-source tables); the others have
+ * their sources padded to whole tiles for the tile search.  Every group of one plan
+ * (search, tile width or warp map, block shape) is one persistent launch; all pairs are
+ * sorted at once, which groups them by instance in (u, v) order.  cfg may be NULL (no autotuning,
  * CUDA graph on).  RN_EINVAL for a bad query (the message names its index), graphs on
  * other devices, or more than 2^32 - 2 nodes or arcs in all; RN_ENOMEM if device memory
  * runs out.
@@ -421,7 +426,8 @@ rn_status rn_batch_pairs_dev(const rn_batch *b, uint32_t i, const uint32_t **u, 
 rn_status rn_batch_stats_get(const rn_batch *b, rn_batch_stats *out);
 /* A batch runs one rn_batch_run at a time; no call on it may overlap rn_batch_free. */
 void rn_batch_free(rn_batch *b);
-/* The autotuner's plans (per size class: tile width, bucket width, sources per tile) to a
+/* The autotuner's plans (per size class: tile width -- 1 for the warp search --, bucket
+ * width, sources per tile) to a
  * text file, and back: a loaded file is merged into the process's plans, which later
  * batches use without tuning.  *classes receives how many plans the file held.  RN_EINVAL
  * for a file that cannot be written, opened or parsed. */

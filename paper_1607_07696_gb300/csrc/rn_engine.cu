@@ -5147,6 +5147,8 @@ void batch_tune(Batch *b) {
     batch_layout(b);
     b->laid_out_by_cost = false;  // costs of the chosen plan are measured by the next run
     b->stats.tuned = use_mixed ? 2 : 1;
+    b->stats.plan_tile_width = use_mixed ? 0 : cands[best].T;
+    b->stats.plan_delta_mult = use_mixed ? 0 : cands[best].delta_mult;
     b->stats.candidates = uint32_t(nc + 1);
 }
 

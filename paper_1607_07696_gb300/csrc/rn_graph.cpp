@@ -165,7 +165,10 @@ struct Bisector {
             parts.push_back((uint64_t(out_begin) << 32) | part.size());
         }
         if (part.size() <= leaf) {
-            std::sort(part.begin(), part.end());
+            // a leaf keeps the order its nodes joined their cluster in (growth from the seed,
+            // lightest horizon edge first): neighbours get near ids, so a search ball is a
+            // few runs of consecutive ids (spread evenly by the maps' multiplicative hash,
+            // and read from neighbouring CSR rows)
             std::copy(part.begin(), part.end(), order.begin() + out_begin);
             if (!part.empty()) {
                 std::lock_guard<std::mutex> lk(leaves_mu);

@@ -62,16 +62,20 @@ def test_components_stay_whole(rn):
 
 
 def test_leaves_are_compact(rn):
-    # on a uniform grid every leaf of <= 64 nodes should be a compact region:
-    # its bounding box is far smaller than the grid
+    # on a uniform grid, leaves of <= 64 nodes are compact regions and each keeps the order
+    # its nodes were grown in: consecutive ids are grid neighbours or nearly (a random
+    # order puts them ~42 steps apart), and any 64 consecutive ids -- at most two leaves --
+    # span less than half the grid
     wd = 64
     s, d, w = _grid(wd, wd, 1)
     o = rn.rn_bisection_order(s, d, w, wd * wd, cfg={"leaf_size": 64})
-    xs, ys = o % wd, o // wd
+    xs, ys = (o % wd).astype(int), (o // wd).astype(int)
+    step = np.abs(np.diff(xs)) + np.abs(np.diff(ys))
+    assert step.mean() < 6, step.mean()
     spans = []
     for i in range(0, wd * wd, 64):
         spans.append((xs[i:i + 64].max() - xs[i:i + 64].min()) + (ys[i:i + 64].max() - ys[i:i + 64].min()))
-    assert np.median(spans) < 24
+    assert np.median(spans) < wd // 2
 
 
 def test_alpha_out_of_range_rejected(rn):
