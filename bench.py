@@ -60,6 +60,8 @@ def parse():
     ap.add_argument("--serve-requests", type=int, default=2000)
     ap.add_argument("--no-legs", action="store_true",
                     help="only the headline workload: no secondary legs and no CPU baseline")
+    ap.add_argument("--leg", default="", choices=["", "kcp_1m", "batched", "join_264k", "hierarchical", "served"],
+                    help="run this one secondary leg alone (one GPU) and print its JSON object")
     return ap.parse_args()
 
 
@@ -397,10 +399,12 @@ def hier_leg(rn, steps: int) -> dict:
     return res
 
 
-def kcp_1m_leg(rn, steps: int, stream, flush) -> dict:
+def kcp_1m_leg(rn, steps: int, stream, flush, peak: float, peak_kind: str) -> dict:
     """k closest pairs on the 1.07M-node graph with 50,000 + 50,000 clustered sets, for
     k = 100, 10^4 and 10^6 (unbounded theta): device time per query (sets in device
-    memory, L2 flushed), the radius passes it took and the k-th distance."""
+    memory, L2 flushed), the radius passes it took, the k-th distance, and the roofline
+    of the search launch of the last pass (the candidates it emitted, before the
+    selection, count as its pairs)."""
     import numpy as np
     import torch
 
@@ -416,7 +420,7 @@ def kcp_1m_leg(rn, steps: int, stream, flush) -> dict:
     for k in (100, 10_000, 1_000_000):
         for _ in range(2):
             rn.rn_kcp_dev(g, dR, dS, k, rn.RN_INF, out, stream)
-        ms = []
+        ms, sms = [], []
         for i in range(steps):
             with torch.cuda.stream(stream):
                 flush.fill_(i & 0xFF)
@@ -427,9 +431,13 @@ def kcp_1m_leg(rn, steps: int, stream, flush) -> dict:
                 b.record(stream)
             b.synchronize()
             ms.append(a.elapsed_time(b))
+            sms.append(rn.rn_last_query_stats()["search_ms"])
         st = rn.rn_last_query_stats()
         res[f"k={k}"] = {"ms": statistics.median(ms), "pairs": int(n), "passes": st["passes"],
-                         "kth_distance": st["theta_final"], "launches": st["launches"]}
+                         "kth_distance": st["theta_final"], "launches": st["launches"],
+                         "tile_width": st["tile_width"], "candidates": int(st["search_pairs"]),
+                         "roofline": roofline(st, int(st["search_pairs"]), statistics.mean(sms),
+                                              f"road1070k_kcp_k{k}", peak, peak_kind)}
     return res
 
 
@@ -509,11 +517,13 @@ def serve_leg(rn, count: int) -> dict:
     srv.close()
     # the plain form: one query per call, one after the other
     t0 = time.perf_counter()
-    plain_pairs, plain_dev_ms = [], 0.0
+    plain_pairs, plain_dev_ms, kcp_dev_ms = [], 0.0, 0.0
     for r in reqs:
         out = rn.rn_distance_join(g, r.R, r.S, r.theta) if r.k == 0 else rn.rn_kcp(g, r.R, r.S, r.k, r.theta)
         plain_pairs.append(len(out[0]))
-        plain_dev_ms += rn.rn_last_query_stats()["device_ms"]
+        dms = rn.rn_last_query_stats()["device_ms"]
+        plain_dev_ms += dms
+        kcp_dev_ms += dms if r.k else 0.0
     plain_s = time.perf_counter() - t0
     assert plain_pairs == served_pairs, "served and plain pair counts differ"
     joins = [r for r in reqs if r.k == 0]
@@ -522,7 +532,7 @@ def serve_leg(rn, count: int) -> dict:
                     f"k 10-1e5, {count} requests",
         "unit": "queries/s", "requests": count, "joins": len(joins), "pairs": int(sum(served_pairs)),
         "served_qps": sat, "plain_qps": count / plain_s, "served_vs_plain": sat / (count / plain_s),
-        "plain_device_s": plain_dev_ms / 1e3, "plain_wall_s": plain_s,
+        "plain_device_s": plain_dev_ms / 1e3, "plain_kcp_device_s": kcp_dev_ms / 1e3, "plain_wall_s": plain_s,
         "phases": phases, "graph_load_s": load_s,
         "config": {"workers": 8, "max_blocks": "one per SM", "slab_mb": 4096},
     }
@@ -658,7 +668,7 @@ def run_engine(args):
     if legs and args.workload != "road264k_join":
         line["join_264k"] = join_264k_leg(rn, min(50, max(3, args.steps // 2)), stream, flush, peak, peak_kind)
     if legs:
-        line["kcp_1m"] = kcp_1m_leg(rn, min(10, max(3, args.steps // 2)), stream, flush)
+        line["kcp_1m"] = kcp_1m_leg(rn, min(10, max(3, args.steps // 2)), stream, flush, peak, peak_kind)
     if legs and not args.no_hier:
         line["hierarchical"] = hier_leg(rn, 5)
     if legs and not args.no_batch:
@@ -717,10 +727,40 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def run_leg(args):
+    """One secondary leg alone, for profiling it: prints {"leg": name, ...its figures}."""
+    import torch
+
+    from paper_1607_07696_gb300 import rn
+
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    if not os.path.exists(rn.LIB_PATH):
+        from paper_1607_07696_gb300 import build as B
+
+        B.build()
+    stream = torch.cuda.Stream()
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    peak, peak_kind = measured_peak_gbs()
+    steps = min(10, max(3, args.steps))
+    if args.leg == "kcp_1m":
+        res = kcp_1m_leg(rn, steps, stream, flush, peak, peak_kind)
+    elif args.leg == "batched":
+        res = batch_leg(rn, steps, args.warmup, stream, flush)
+    elif args.leg == "join_264k":
+        res = join_264k_leg(rn, steps, stream, flush, peak, peak_kind)
+    elif args.leg == "hierarchical":
+        res = hier_leg(rn, steps)
+    else:
+        res = serve_leg(rn, args.serve_requests)
+    print(json.dumps({"leg": args.leg, **res}), flush=True)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
+    elif args.leg:
+        run_leg(args)
     else:
         run_engine(args)
 

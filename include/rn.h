@@ -25,7 +25,9 @@
  *     failure rn_last_error() gives a message for the calling thread.
  *   - Host arrays passed in are read only and may be freed when the call returns.
  *     Results in rn_pairs are host memory owned by the library: free with
- *     rn_pairs_free.  Results in rn_dpairs are device memory owned by the library:
+ *     rn_pairs_free (page-locked where it could be had, so the copy from the device runs
+ *     at the link's speed; freed blocks are kept, up to 1 GiB, for later results; only
+ *     the u pointer identifies a result's block, and v and d must not be freed alone).  Results in rn_dpairs are device memory owned by the library:
  *     free with rn_dpairs_free (a struct may be reused across calls; its buffers grow
  *     as needed).
  *   - Queries may be issued from any host thread; those on one device run one at a
@@ -163,6 +165,9 @@ typedef struct {
                                1: the sum of the sources' balls) */
     uint64_t box_leaf_decided; /* queries in a rectangle: members of R and S kept or dropped
                                by their leaf's bounding rectangle alone */
+    uint64_t search_pairs;  /* pairs the search emitted: a join's pairs; k closest pairs: the
+                               candidates of the last radius pass, before the selection (the
+                               search fields above describe that pass) */
 } rn_query_stats;
 
 /*

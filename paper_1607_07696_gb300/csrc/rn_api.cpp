@@ -7,7 +7,9 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <map>
 #include <memory>
+#include <unordered_map>
 #include <mutex>
 #include <new>
 
@@ -18,16 +20,79 @@
 namespace rn {
 
 // Device pairs -> host arrays owned by the library (rn_pairs_free releases them).
+// Host pairs live in pinned (page-locked) blocks, u, v and d of one result in one block,
+// so the copy from the device runs at the link's speed rather than through a staging
+// buffer.  Freed blocks wait in a pool for the next result of their size (allocating
+// and freeing pinned memory is slow, and freeing it synchronises the device); the pool
+// keeps at most POOL_MAX bytes.
+namespace {
+constexpr size_t POOL_MAX = size_t(1) << 30;
+std::mutex g_pool_mu;
+std::multimap<size_t, void *> g_pool_free;        // capacity -> free block
+std::unordered_map<void *, size_t> g_pool_blocks;  // every block handed out or pooled
+size_t g_pool_free_bytes = 0;
+
+void *pinned_take(size_t bytes) {
+    {
+        std::lock_guard<std::mutex> lk(g_pool_mu);
+        auto it = g_pool_free.lower_bound(bytes);
+        if (it != g_pool_free.end() && it->first <= 2 * bytes) {
+            void *p = it->second;
+            g_pool_free_bytes -= it->first;
+            g_pool_free.erase(it);
+            return p;
+        }
+    }
+    size_t cap = 1 << 16;
+    while (cap < bytes) cap <<= 1;
+    void *p = nullptr;
+    if (cudaHostAlloc(&p, cap, cudaHostAllocPortable) != cudaSuccess || !p) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    std::lock_guard<std::mutex> lk(g_pool_mu);
+    g_pool_blocks[p] = cap;
+    return p;
+}
+
+// Whether p is a pool block; if so it goes back to the pool (or is released when the
+// pool is full).
+bool pinned_give(void *p) {
+    size_t cap = 0;
+    {
+        std::lock_guard<std::mutex> lk(g_pool_mu);
+        auto it = g_pool_blocks.find(p);
+        if (it == g_pool_blocks.end()) return false;
+        cap = it->second;
+        if (g_pool_free_bytes + cap <= POOL_MAX) {
+            g_pool_free.emplace(cap, p);
+            g_pool_free_bytes += cap;
+            return true;
+        }
+        g_pool_blocks.erase(it);
+    }
+    cudaFreeHost(p);
+    return true;
+}
+}  // namespace
+
 void to_host_pairs(const rn_dpairs &d, rn_pairs *out, void *stream) {
     cudaStream_t st = (cudaStream_t)stream;
     out->n = d.n;
-    size_t b = std::max<uint64_t>(d.n, 1) * 4;
-    out->u = (uint32_t *)std::malloc(b);
-    out->v = (uint32_t *)std::malloc(b);
-    out->d = (uint32_t *)std::malloc(b);
-    if (!out->u || !out->v || !out->d) {
-        rn_pairs_free(out);
-        fail(RN_ENOMEM, "host result allocation failed");
+    const size_t n = std::max<uint64_t>(d.n, 1);
+    uint32_t *blk = (uint32_t *)pinned_take(3 * n * 4);
+    if (blk) {
+        out->u = blk;
+        out->v = blk + n;
+        out->d = blk + 2 * n;
+    } else {  // no pinned memory to be had: pageable buffers
+        out->u = (uint32_t *)std::malloc(n * 4);
+        out->v = (uint32_t *)std::malloc(n * 4);
+        out->d = (uint32_t *)std::malloc(n * 4);
+        if (!out->u || !out->v || !out->d) {
+            rn_pairs_free(out);
+            fail(RN_ENOMEM, "host result allocation failed");
+        }
     }
     if (d.n) {
         cudaMemcpyAsync(out->u, d.u, d.n * 4, cudaMemcpyDeviceToHost, st);
@@ -870,9 +935,11 @@ void rn_serve_destroy(rn_server *h) {
 
 void rn_pairs_free(rn_pairs *p) {
     if (!p) return;
-    std::free(p->u);
-    std::free(p->v);
-    std::free(p->d);
+    if (!(p->u && rn::pinned_give(p->u))) {  // a pinned block holds all three arrays
+        std::free(p->u);
+        std::free(p->v);
+        std::free(p->d);
+    }
     p->u = p->v = p->d = nullptr;
     p->n = 0;
 }

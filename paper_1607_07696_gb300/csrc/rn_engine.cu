@@ -328,6 +328,7 @@ struct Workspace {
     // handed sources to the tile search (their pairs are then not in segments)
     uint2 *seg = nullptr;
     uint32_t seg_cap = 0;
+    uint32_t *slist = nullptr;  // the warp search's per-warp lists of S nodes (SRC_LIST_WORDS)
     bool src_tiles = false;
     uint32_t launches = 0;  // kernels launched by the current query
     int blocks_per_sm = 0;  // occupancy of the shared-map search kernel
@@ -394,6 +395,7 @@ void workspace_destroy(Workspace *ws) {
         device_free(p);
     device_free(ws->own_gmap);
     device_free(ws->seg);
+    device_free(ws->slist);
     if (ws->own_sh) {
         device_free(ws->own_sh->gretry);
         delete ws->own_sh;
@@ -573,6 +575,9 @@ struct SearchArgs {
     const uint32_t *inst_bound;
     // warp search: seg[si] = (first pair, pair count) of source si, or null
     uint2 *seg;
+    // warp search: per resident warp (block * warps per block + warp) a list of MS slots,
+    // the S nodes of the current source's ball in the order first scanned
+    uint32_t *slist;
     // the hierarchical variant's local searches: source si relaxes only arcs into its
     // part, internal ids [src_range[si].x, src_range[si].y), and records a route
     // (si << 32 | node, distance) to every border node of the part it settles (a node
@@ -766,7 +771,7 @@ __global__ void __launch_bounds__(THREADS, (THREADS == NARROW ? CTAS_PER_SM : 1)
     constexpr uint32_t QCAP = qcap_of(THREADS);
     constexpr uint32_t ICAP = icap_of(THREADS);
     constexpr uint32_t ICAP_POW2 = 1u << (31 - __builtin_clz(ICAP));  // the largest power of two <= ICAP
-    extern __shared__ uint32_t smem[];
+    extern __shared__ __align__(16) uint32_t smem[];
     uint32_t *hkeys, *qa;
     if constexpr (GMAP) {
         hkeys = a.gmap + size_t(blockIdx.x) * 3 * a.H;
@@ -1290,6 +1295,13 @@ __host__ __device__ constexpr uint32_t log2u(uint32_t x) { return x <= 1 ? 0 : 1
 __host__ __device__ constexpr uint32_t src_qcap(uint32_t ms) { return ms / 8; }
 __host__ __device__ constexpr uint32_t src_words(uint32_t ms) { return 2 * ms + 2 * src_qcap(ms); }
 __host__ __device__ constexpr uint32_t src_warps(uint32_t ms) { return SRC_BLOCK_SMEM / (4 * src_words(ms)); }
+// The warp search's S-node lists in global memory: MS entries per warp, for every warp of
+// every resident block (a block of src_warps(MS) warps holds src_warps(MS) * MS = 8192
+// entries whatever MS is).
+constexpr size_t SRC_LIST_WORDS_PER_BLOCK = 8192;
+static_assert(src_warps(1024) * 1024 <= SRC_LIST_WORDS_PER_BLOCK && src_warps(2048) * 2048 <= SRC_LIST_WORDS_PER_BLOCK &&
+                  src_warps(4096) * 4096 <= SRC_LIST_WORDS_PER_BLOCK && src_warps(8192) * 8192 <= SRC_LIST_WORDS_PER_BLOCK,
+              "S-node lists too small");
 
 // Slot of node y in a warp map of MS slots, probing from slot h on (linear probing) and
 // inserting y if absent; EMPTY when the map is full.
@@ -1365,7 +1377,7 @@ template <uint32_t MS, bool HIER>
 __global__ void __launch_bounds__(src_warps(MS) * 32, SRC_BLOCKS_PER_SM) k_source_search(SearchArgs a) {
     constexpr uint32_t QS = src_qcap(MS);
     constexpr int AP = 4;  // arcs per lane in flight
-    extern __shared__ uint32_t smem[];
+    extern __shared__ __align__(16) uint32_t smem[];  // (sixteen-byte stores clear the maps)
     const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const uint32_t lt = (1u << lane) - 1;
     uint32_t *key = smem + warp * src_words(MS);
@@ -1390,6 +1402,7 @@ __global__ void __launch_bounds__(src_warps(MS) * 32, SRC_BLOCKS_PER_SM) k_sourc
     if (lane < 2) s_max[warp][lane] = 0;
     __syncwarp();
     const bool kcp = a.kcp_hist != nullptr;
+    uint32_t *const slist = a.slist + size_t(blockIdx.x * src_warps(MS) + warp) * MS;
     uint32_t t_mark = uint32_t(clock());
 
     for (;;) {
@@ -1437,6 +1450,7 @@ __global__ void __launch_bounds__(src_warps(MS) * 32, SRC_BLOCKS_PER_SM) k_sourc
         }
         uint32_t n_scans = 0, n_arcs = 0, n_slot_arcs = 0, n_rounds = 0, n_bounds = 0;
         uint32_t cyc_round = 0, cyc_bound = 0;
+        uint32_t n_list = 0;  // S nodes of the ball listed so far (every lane the same)
         // the source, at distance 0, is the only item of the near queue
         if (lane == 0) {
             const uint32_t h = (y0 * 0x9E3779B1u) >> (32 - log2u(MS));
@@ -1481,13 +1495,14 @@ __global__ void __launch_bounds__(src_warps(MS) * 32, SRC_BLOCKS_PER_SM) k_sourc
                 uint32_t nnext = 0;
                 for (uint32_t c0 = 0; c0 < ncur && !fail; c0 += 64) {
                     // step A: items c0 + 2 lane and c0 + 2 lane + 1
-                    uint32_t beg[2], deg[2], dv[2];
+                    uint32_t beg[2], deg[2], dv[2], fresh_s[2];
 #pragma unroll
                     for (int t = 0; t < 2; t++) {
                         const uint32_t j = c0 + 2 * lane + t;
                         beg[t] = 0;
                         deg[t] = 0;
                         dv[t] = INF;
+                        fresh_s[t] = EMPTY;  // the slot, when this is an S node's first scan
                         if (j < ncur) {
                             const uint32_t x = qcur[j];
                             if (!RN_BAD(x < MS, 12, j, x)) {
@@ -1501,6 +1516,7 @@ __global__ void __launch_bounds__(src_warps(MS) * 32, SRC_BLOCKS_PER_SM) k_sourc
                                     if (!(k & SK_SEEN)) {  // first scan: S membership, arcs
                                         in_s = ((__ldg(&sbits[y >> 5]) >> (y & 31)) & 1u) ? SK_IN_S : 0u;
                                         n_slot_arcs += deg[t];
+                                        if (in_s) fresh_s[t] = x;
                                     }
                                     key[x] = y | SK_SEEN | in_s;
                                     if (RN_BAD(uint64_t(beg[t]) + deg[t] <= a.n_arcs, 14, y, beg[t])) deg[t] = 0;
@@ -1509,6 +1525,16 @@ __global__ void __launch_bounds__(src_warps(MS) * 32, SRC_BLOCKS_PER_SM) k_sourc
                                 }
                             }
                         }
+                    }
+                    // S nodes scanned for the first time join the ball's list (each once:
+                    // every node within the bound is scanned, so emission reads the list
+                    // instead of the whole map)
+#pragma unroll
+                    for (int t = 0; t < 2; t++) {
+                        const uint32_t fb = __ballot_sync(FULL, fresh_s[t] != EMPTY);
+                        const uint32_t at = n_list + __popc(fb & lt);
+                        if (fresh_s[t] != EMPTY && at < MS) __stcg(&slist[at], fresh_s[t]);
+                        n_list = min(n_list + __popc(fb), MS);  // (a ball never fills its map)
                     }
                     const uint32_t mine = deg[0] + deg[1];
                     uint32_t incl = mine;
@@ -1642,17 +1668,16 @@ __global__ void __launch_bounds__(src_warps(MS) * 32, SRC_BLOCKS_PER_SM) k_sourc
 
         // ---- emission: every slot of an S node (all lie within the bound), then the map
         // is left clean for the next source
-        uint32_t *hits = qa;  // the queues are free: one ballot word per 32 slots
         if (!fail) {
-            uint32_t cnt = 0;
-#pragma unroll 8
-            for (uint32_t c = 0; c < MS; c += 32) {
-                // an S slot within the bound (a join's slots all are; k closest pairs may
-                // have lowered the bound below slots reached before)
-                const bool hit = (key[c + lane] & SK_IN_S) != 0u && (!kcp || dist[c + lane] <= bound);
-                const uint32_t b = __ballot_sync(FULL, hit);  // never on SK_EMPTY
-                if (lane == 0) hits[c >> 5] = b;
-                cnt += __popc(b);
+            // the ball's S nodes are the list (a join's all lie within the bound; k closest
+            // pairs may have lowered the bound below nodes reached before)
+            uint32_t cnt = n_list;
+            if (kcp) {
+                cnt = 0;
+                for (uint32_t i = lane; i - lane < n_list; i += 32) {
+                    const bool in = i < n_list && dist[__ldcg(&slist[i])] <= bound;
+                    cnt += __popc(__ballot_sync(FULL, in));
+                }
             }
             if (HIER) {
                 // the routes to the part's border nodes (the inside routes that the search
@@ -1681,41 +1706,47 @@ __global__ void __launch_bounds__(src_warps(MS) * 32, SRC_BLOCKS_PER_SM) k_sourc
             if (lane == 0 && a.seg) a.seg[si] = make_uint2(uint32_t(base), cnt);
             if (lane == 0) s_max[warp][1] = max(s_max[warp][1], cnt);
             base = __shfl_sync(FULL, base, 0);
-            __syncwarp();
-            // four chunks of 32 slots at a time, every output-id load issued before the
-            // first write (so their latencies overlap)
+            // four chunks of 32 list entries at a time, every output-id load issued before
+            // the first write (so their latencies overlap)
             unsigned long long pos = base;
-            for (uint32_t c = 0; c < MS; c += 128) {
-                uint32_t b[4], dd[4], v[4];
+            for (uint32_t i0 = 0; i0 < n_list; i0 += 128) {
+                uint32_t dd[4], v[4];
+                bool ok[4];
 #pragma unroll
                 for (int q = 0; q < 4; q++) {
-                    const uint32_t h = c + 32 * q + lane;
-                    b[q] = hits[h >> 5];
+                    const uint32_t i = i0 + 32 * q + lane;
+                    ok[q] = false;
                     dd[q] = 0;
                     v[q] = 0;
-                    if ((b[q] >> lane) & 1u) {
+                    if (i < n_list) {
+                        const uint32_t h = __ldcg(&slist[i]);
                         const uint32_t y = key[h] & SK_NODE;
-                        if (!RN_BAD(y < a.n_nodes, 17, h, y)) {
+                        if (!RN_BAD(h < MS && y < a.n_nodes, 17, h, y)) {
                             dd[q] = dist[h];
-                            v[q] = __ldg(&a.iperm[y]);
+                            ok[q] = !kcp || dd[q] <= bound;
+                            if (ok[q]) v[q] = __ldg(&a.iperm[y]);
                         }
                     }
                 }
 #pragma unroll
                 for (int q = 0; q < 4; q++) {
-                    const uint32_t h = c + 32 * q + lane;
-                    if ((b[q] >> lane) & 1u) {
-                        const unsigned long long idx = pos + __popc(b[q] & lt);
+                    const uint32_t b = __ballot_sync(FULL, ok[q]);
+                    if (ok[q]) {
+                        const unsigned long long idx = pos + __popc(b & lt);
                         if (idx < a.out_cap) {
                             a.out_key[idx] = prefix | (u << a.vbits) | (unsigned long long)v[q];
                             a.out_d[idx] = dd[q];
                         }
                         if (kcp) atomicAdd(&a.kcp_hist[dd[q] >> a.hist_shift], 1u);
                     }
-                    pos += __popc(b[q]);
-                    key[h] = SK_EMPTY;
-                    dist[h] = INF;
+                    pos += __popc(b);
                 }
+            }
+            __syncwarp();
+            // the map back to empty for the next source, sixteen bytes a store
+            for (uint32_t h4 = lane; h4 < MS / 4; h4 += 32) {
+                reinterpret_cast<uint4 *>(key)[h4] = make_uint4(SK_EMPTY, SK_EMPTY, SK_EMPTY, SK_EMPTY);
+                reinterpret_cast<uint4 *>(dist)[h4] = make_uint4(INF, INF, INF, INF);
             }
             if (kcp && cnt) {
                 // the source's pairs are counted: once k pairs exist, lower the live bound
@@ -2441,6 +2472,15 @@ static int source_blocks_per_sm(uint32_t ms) {
     }
 }
 
+static uint32_t *ensure_slist(Workspace *ws) {
+    if (!ws->slist) {
+        const size_t words = size_t(ws->num_sms) * SRC_BLOCKS_PER_SM * SRC_LIST_WORDS_PER_BLOCK;
+        ws->slist = (uint32_t *)device_alloc(words * 4);
+        ws->bytes += words * 4;
+    }
+    return ws->slist;
+}
+
 // One warp-search launch over `items` sources with maps of ms slots: a block per
 // src_warps sources up to three blocks per SM of the device.  The warp search uses no slab,
 // so a server's request is not held to the slab regions it was given (those serve its
@@ -2451,6 +2491,7 @@ static void source_launch(uint32_t ms, SearchArgs a, uint32_t items, Workspace *
     a.hshift = 32 - log2u(ms);
     a.max_fill = ms * 7 / 8;
     a.gmap = nullptr;
+    a.slist = ensure_slist(ws);
     const uint32_t per_block = src_warps(ms);
     const uint32_t resident = std::max<uint32_t>(1, uint32_t(ws->num_sms) * SRC_BLOCKS_PER_SM);
     const uint32_t grid = std::max<uint32_t>(1, std::min<uint32_t>((items + per_block - 1) / per_block, resident));
@@ -2731,6 +2772,7 @@ void workspace_reserve(Workspace *ws, uint32_t max_r, uint64_t max_pairs) {
     ensure_ranges(&ws->failed2, &ws->failed2_cap, std::max<uint32_t>(max_r, 1));
     ensure_pairs(ws, max_pairs);
     grow(ws, &ws->hist, &ws->hist_cap, hist_words((max_pairs + RS_TILE - 1) / RS_TILE * 256), 4);
+    ensure_slist(ws);
     if (!ws->seg || ws->seg_cap < max_r) {  // the warp search's per-source segments
         device_free(ws->seg);
         ws->seg = nullptr;
@@ -2899,6 +2941,7 @@ void run_join(const DeviceGraph &g, Workspace *ws, const EngineConfig &cfg, uint
     stats->dirty_groups = c.dirty_groups;
     stats->retry_ms = ws->retry_ms;
     stats->slot_lanes = c.slot_lanes;
+    stats->search_pairs = np;
 }
 
 // ------------------------------------------------ several joins, one graph ----
@@ -3479,6 +3522,7 @@ void run_kcp(const DeviceGraph &g, Workspace *ws, const EngineConfig &cfg, uint3
         tau = std::min<uint64_t>(theta, uint64_t(double(tau) * f) + 1);
     }
     stats->tile_width = any_tiles ? T : 1;
+    const Control cs = c;  // the last search pass (the one the selection takes its pairs from)
     const uint64_t m = c.pairs;
     uint64_t kept = m;
     uint32_t theta_k = uint32_t(tau);
@@ -3531,6 +3575,15 @@ void run_kcp(const DeviceGraph &g, Workspace *ws, const EngineConfig &cfg, uint3
     stats->blocks_per_sm = uint32_t(ws->blocks_per_sm);
     stats->device_ms = ms;
     stats->search_ms = sms;
+    stats->search_pairs = m;
+    stats->slots = cs.slots;
+    stats->slot_arcs = cs.slot_arcs;
+    stats->slot_lanes = cs.slot_lanes;
+    stats->rounds = cs.rounds;
+    stats->round_items = cs.round_items;
+    stats->boundaries = cs.boundaries;
+    stats->round_arcs = cs.round_arcs;
+    stats->max_ball = cs.max_fill;
 }
 
 // ------------------------------------------------------------ points on edges ----
@@ -5053,6 +5106,7 @@ void batch_run(Batch *b, void *user_stream, bool use_graph) {
             b->laid_out_by_cost = true;
         } else if (use_graph && !b->exec) {
             b->exec_pairs = b->total;
+            ensure_slist(b->ws);  // allocates nothing inside the capture
             RN_CUDA(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
             try {
                 batch_record(b, st);

@@ -65,7 +65,7 @@ class rn_query_stats(C.Structure):
                 ("cycles_boundaries", C.c_uint64), ("cycles_emission", C.c_uint64),
                 ("cycles_step_a", C.c_uint64), ("round_arcs", C.c_uint64), ("max_ball", C.c_uint64),
                 ("retry_ms", C.c_double), ("dirty_groups", C.c_uint64), ("slot_lanes", C.c_uint64),
-                ("box_leaf_decided", C.c_uint64)]
+                ("box_leaf_decided", C.c_uint64), ("search_pairs", C.c_uint64)]
 
 
 class rn_query(C.Structure):
