@@ -1751,9 +1751,13 @@ __global__ void __launch_bounds__(src_warps(MS) * 32, SRC_BLOCKS_PER_SM) k_sourc
             if (kcp && cnt) {
                 // the source's pairs are counted: once k pairs exist, lower the live bound
                 // to the edge of the first histogram bin where the pairs emitted so far
-                // reach k (exact, distinct pairs: the k-th distance cannot lie above it)
-                const unsigned long long emitted = __shfl_sync(FULL, base, 0) + cnt;
-                if (emitted >= a.kcp_k) kcp_lower_bound(a, lane);
+                // reach k (exact, distinct pairs: the k-th distance cannot lie above it).
+                // The warp whose pairs reach k does it, then the warp whose pairs cross
+                // each further multiple of k/64 (not every source: each lowering reads the
+                // whole histogram)
+                const unsigned long long emitted = base + cnt;
+                const unsigned long long step = a.kcp_k / 64 + 1;
+                if (emitted >= a.kcp_k && (base < a.kcp_k || base / step != emitted / step)) kcp_lower_bound(a, lane);
             }
             if (lane == 0) {
                 s_tel[warp][W_SLOTS] += fill;
@@ -2543,11 +2547,18 @@ static bool use_source_search(const DeviceGraph &g, const Workspace *ws, const E
 
 // First warp map: the smallest whose 7/8 holds 1.3 times the predicted mean ball and
 // nearly the predicted largest (up to 15% over: the few sources that overflow are searched
-// again with a larger map, while a smaller map fits twice as many warps on an SM); 2048
-// slots with no history.
-static uint32_t source_first_map(const Workspace *ws, uint32_t theta) {
+// again with a larger map, while a smaller map fits twice as many warps on an SM).  With
+// no history: the smallest map that fits the ball estimated from the bound (`first`, the
+// largest ball a lattice would give: k closest pairs, whose searches teach the workspace
+// nothing), else 2048 slots (a join's first search, which its measured balls then size).
+static uint32_t source_first_map(const Workspace *ws, uint32_t theta, double first = 0) {
     const double b = predicted_ball(ws, theta);
-    if (b <= 0) return 2048;
+    if (b <= 0) {
+        if (first <= 0) return 2048;
+        for (uint32_t ms = SRC_MS_MIN; ms <= SRC_MS_MAX; ms *= 2)
+            if (first <= src_fit(ms)) return ms;
+        return SRC_MS_MAX;
+    }
     const double r = double(theta) / double(ws->ball_theta);
     const double mean = ws->ball_mean * r * r;
     for (uint32_t ms = SRC_MS_MIN; ms <= SRC_MS_MAX; ms *= 2) {
@@ -3500,7 +3511,9 @@ void run_kcp(const DeviceGraph &g, Workspace *ws, const EngineConfig &cfg, uint3
         if (by_source) {
             a.tile_src = 1;
             a.seg = nullptr;
-            c = source_search_all(g, ws, a, nR, source_first_map(ws, uint32_t(tau)), T, uint32_t(tau), {}, st,
+            c = source_search_all(g, ws, a, nR,
+                                  source_first_map(ws, uint32_t(tau), first_ball_estimate(g, uint32_t(tau), median_w)), T,
+                                  uint32_t(tau), {}, st,
                                   &retried, false);
         } else {
             a.tile_src = tile_src;
@@ -3584,6 +3597,9 @@ void run_kcp(const DeviceGraph &g, Workspace *ws, const EngineConfig &cfg, uint3
     stats->boundaries = cs.boundaries;
     stats->round_arcs = cs.round_arcs;
     stats->max_ball = cs.max_fill;
+    stats->cycles_rounds = cs.cyc_round;
+    stats->cycles_boundaries = cs.cyc_bound;
+    stats->cycles_emission = cs.cyc_emit;
 }
 
 // ------------------------------------------------------------ points on edges ----
