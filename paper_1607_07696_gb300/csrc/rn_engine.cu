@@ -1865,7 +1865,8 @@ template <int E>
 __device__ __forceinline__ void place_segment(uint32_t lane, uint32_t base, uint32_t cnt, uint32_t o, uint32_t u,
                                               const unsigned long long *__restrict__ key,
                                               const uint32_t *__restrict__ val, unsigned long long vmask,
-                                              uint32_t *out_u, uint32_t *out_v, uint32_t *out_d) {
+                                              uint32_t *out_u, uint32_t *out_v, uint32_t *out_d,
+                                              unsigned long long *out_key, uint32_t *out_val) {
     unsigned long long x[E];
 #pragma unroll
     for (int e = 0; e < E; e++) {
@@ -1873,6 +1874,18 @@ __device__ __forceinline__ void place_segment(uint32_t lane, uint32_t base, uint
         x[e] = i < cnt ? ((key[base + i] & vmask) << 32) | val[base + i] : ~0ull;  // v, then d
     }
     warp_bitonic<E>(x, lane);
+    if (out_key) {  // records (key, distance) for a sort that follows
+        const unsigned long long khi = key[base] & ~vmask;
+#pragma unroll
+        for (int e = 0; e < E; e++) {
+            const uint32_t i = lane * E + e;
+            if (i < cnt) {
+                out_key[o + i] = khi | (x[e] >> 32);
+                out_val[o + i] = uint32_t(x[e]);
+            }
+        }
+        return;
+    }
 #pragma unroll
     for (int e = 0; e < E; e++) {
         const uint32_t i = lane * E + e;
@@ -1884,10 +1897,12 @@ __device__ __forceinline__ void place_segment(uint32_t lane, uint32_t base, uint
     }
 }
 
-// One warp per source: its segment, sorted by v, at its offset off[si] of the result.
+// One warp per source: its segment, sorted by v, at its offset off[si] of the result
+// (u, v, d arrays; or, when out_key is given, (key, d) records).
 __global__ void k_place(const uint2 *__restrict__ seg, const uint32_t *__restrict__ off, uint32_t n,
                         const unsigned long long *__restrict__ key, const uint32_t *__restrict__ val, uint32_t vbits,
-                        uint32_t umask, uint32_t *out_u, uint32_t *out_v, uint32_t *out_d) {
+                        uint32_t umask, uint32_t *out_u, uint32_t *out_v, uint32_t *out_d,
+                        unsigned long long *out_key = nullptr, uint32_t *out_val = nullptr) {
     const uint32_t lane = threadIdx.x & 31;
     const uint32_t warps = gridDim.x * (blockDim.x / 32);
     const unsigned long long vmask = (1ull << vbits) - 1;
@@ -1897,10 +1912,10 @@ __global__ void k_place(const uint2 *__restrict__ seg, const uint32_t *__restric
         if (!cnt) continue;
         const uint32_t u = uint32_t(key[sg.x] >> vbits) & umask;
         const uint32_t o = off[si];
-        if (cnt <= 32) place_segment<1>(lane, sg.x, cnt, o, u, key, val, vmask, out_u, out_v, out_d);
-        else if (cnt <= 64) place_segment<2>(lane, sg.x, cnt, o, u, key, val, vmask, out_u, out_v, out_d);
-        else if (cnt <= 128) place_segment<4>(lane, sg.x, cnt, o, u, key, val, vmask, out_u, out_v, out_d);
-        else place_segment<8>(lane, sg.x, cnt, o, u, key, val, vmask, out_u, out_v, out_d);
+        if (cnt <= 32) place_segment<1>(lane, sg.x, cnt, o, u, key, val, vmask, out_u, out_v, out_d, out_key, out_val);
+        else if (cnt <= 64) place_segment<2>(lane, sg.x, cnt, o, u, key, val, vmask, out_u, out_v, out_d, out_key, out_val);
+        else if (cnt <= 128) place_segment<4>(lane, sg.x, cnt, o, u, key, val, vmask, out_u, out_v, out_d, out_key, out_val);
+        else place_segment<8>(lane, sg.x, cnt, o, u, key, val, vmask, out_u, out_v, out_d, out_key, out_val);
     }
 }
 
@@ -2705,7 +2720,8 @@ static bool can_place(const Workspace *ws, const Control &c) {
 }
 
 // The canonical order by placement: offsets from the segments' counts (source order is
-// the output order), then one warp per segment.
+// the output order), then one warp per segment; with no `out`, into the workspace's
+// (keyA, valA) records instead, in (u, v) order.
 static void place_pairs(Workspace *ws, uint32_t nsrc, uint32_t vbits, uint32_t umask, rn_dpairs *out,
                         cudaStream_t st) {
     if (!nsrc) return;
@@ -2713,10 +2729,15 @@ static void place_pairs(Workspace *ws, uint32_t nsrc, uint32_t vbits, uint32_t u
     const uint32_t nb = std::min<uint32_t>((nsrc + 255) / 256, 4096);
     k_seg_counts<<<nb, 256, 0, st>>>(ws->seg, nsrc, ws->hist);
     ws->launches += 1 + scan_hist(ws->hist, nsrc, st);
-    k_place<<<std::min<uint32_t>((nsrc + 7) / 8, 8192), 256, 0, st>>>(ws->seg, ws->hist, nsrc, ws->keyA, ws->valA,
-                                                                       vbits, umask, out->u, out->v, out->d);
+    k_place<<<std::min<uint32_t>((nsrc + 7) / 8, 8192), 256, 0, st>>>(
+        ws->seg, ws->hist, nsrc, ws->keyA, ws->valA, vbits, umask, out ? out->u : nullptr, out ? out->v : nullptr,
+        out ? out->d : nullptr, out ? nullptr : ws->keyB, out ? nullptr : ws->valB);
     ws->launches++;
     RN_CUDA(cudaGetLastError());
+    if (!out) {  // the placed records become the radix sort's input
+        std::swap(ws->keyA, ws->keyB);
+        std::swap(ws->valA, ws->valB);
+    }
 }
 
 // Bucket width unless configured: four median arc weights for the tile search, sixteen
@@ -3490,13 +3511,17 @@ void run_kcp(const DeviceGraph &g, Workspace *ws, const EngineConfig &cfg, uint3
     uint32_t passes = 0;
     Control c{};
     unsigned long long scans = 0;
-    bool any_tiles = false;
+    bool any_tiles = false, last_by_source = false;
     for (;;) {
         // every pass takes the warp search while the balls at tau fit a warp map
         const bool by_source = warp_ok && use_source_search(g, ws, cfg, uint32_t(tau), median_w);
         const uint32_t delta = choose_delta(cfg, median_w, by_source);
-        prep_sets(g, ws, dR, nR, dS, nS, st);
+        // the warp search takes R in output order and records each source's segment
+        const bool place = by_source && g.iperm_inverts_perm;
+        prep_sets(g, ws, dR, nR, dS, nS, st, place);
         a.src = ws->rsorted;  // prep_sets may have (re)allocated the R list
+        a.seg = place ? ensure_segments(ws, nR, st) : nullptr;
+        last_by_source = place;
         RN_CUDA(cudaMemsetAsync(hist, 0, KCP_BINS * 4, st));
         k_set_u32<<<1, 1, 0, st>>>(theta_live, uint32_t(tau));
         ws->launches++;
@@ -3510,7 +3535,6 @@ void run_kcp(const DeviceGraph &g, Workspace *ws, const EngineConfig &cfg, uint3
         a.out_cap = ws->pair_cap;
         if (by_source) {
             a.tile_src = 1;
-            a.seg = nullptr;
             c = source_search_all(g, ws, a, nR,
                                   source_first_map(ws, uint32_t(tau), first_ball_estimate(g, uint32_t(tau), median_w)), T,
                                   uint32_t(tau), {}, st,
@@ -3539,7 +3563,20 @@ void run_kcp(const DeviceGraph &g, Workspace *ws, const EngineConfig &cfg, uint3
     const uint64_t m = c.pairs;
     uint64_t kept = m;
     uint32_t theta_k = uint32_t(tau);
-    if (m > k) {
+    const bool placed = last_by_source && m && can_place(ws, cs);
+    if (placed) {
+        // the warp search's segments placed in (u, v) order, then a stable LSD sort of all
+        // candidates by distance alone: (d, u, v) order, of which the first k are the answer
+        // (no selection: three distance passes instead of the (u, v) digits' six)
+        place_pairs(ws, nR, vbits, 0xFFFFFFFFu, nullptr, st);
+        dpairs_reserve(out, m);
+        std::vector<int> shifts;
+        const uint32_t dbits = bits_for(uint32_t(std::min<uint64_t>(tau, RN_THETA_MAX)) + 1);
+        for (uint32_t sh = 0; sh < dbits; sh += 8) shifts.push_back(64 + int(sh));
+        radix_sort_to_pairs(ws, m, shifts, vbits, out, st);
+        out->n = std::min<uint64_t>(k, m);
+        if (m >= k) RN_CUDA(cudaMemcpyAsync(&theta_k, out->d + (k - 1), 4, cudaMemcpyDeviceToHost, st));
+    } else if (m > k) {
         // device radix select of the k-th distance (11 + 11 + 10 bits), then broadcast
         // through device memory to the compaction
         k_sel_init<<<1, 1, 0, st>>>(sel, k);
@@ -3564,14 +3601,16 @@ void run_kcp(const DeviceGraph &g, Workspace *ws, const EngineConfig &cfg, uint3
         std::swap(ws->keyA, ws->keyB);
         std::swap(ws->valA, ws->valB);
     }
-    // canonical (d, u, v) order: (u, v) digits first, then the distance digits
-    dpairs_reserve(out, kept);
-    std::vector<int> shifts;
-    for (uint32_t sh = 0; sh < 2 * vbits; sh += 8) shifts.push_back(int(sh));
-    const uint32_t dbits = bits_for(theta_k + 1);
-    for (uint32_t sh = 0; sh < dbits; sh += 8) shifts.push_back(64 + int(sh));
-    radix_sort_to_pairs(ws, kept, shifts, vbits, out, st);
-    out->n = std::min<uint64_t>(k, kept);
+    if (!placed) {
+        // canonical (d, u, v) order: (u, v) digits first, then the distance digits
+        dpairs_reserve(out, kept);
+        std::vector<int> shifts;
+        for (uint32_t sh = 0; sh < 2 * vbits; sh += 8) shifts.push_back(int(sh));
+        const uint32_t dbits = bits_for(theta_k + 1);
+        for (uint32_t sh = 0; sh < dbits; sh += 8) shifts.push_back(64 + int(sh));
+        radix_sort_to_pairs(ws, kept, shifts, vbits, out, st);
+        out->n = std::min<uint64_t>(k, kept);
+    }
     RN_CUDA(cudaEventRecord(ws->ev1, st));
     RN_CUDA(cudaEventSynchronize(ws->ev1));
     float ms = 0, sms = 0;
