@@ -174,11 +174,11 @@ def search_kernel(st: dict) -> str:
 
 
 def engine_hash() -> str:
-    """Hash of the search sections of the engine source (tile and source search, the
-    profiled kernels)."""
+    """Hash of the search sections of the engine source (the tile and the source search
+    kernels, the profiled ones)."""
     src = open(ENGINE_SRC).read()
     a = src.index("// ------------------------------------------------------------ tile search ----")
-    b = src.index("// ------------------------------------------------------------- radix sort ----")
+    b = src.index("// ------------------------------------------------- order without a sort ----")
     return hashlib.sha256(src[a:b].encode()).hexdigest()[:16]
 
 

@@ -112,7 +112,20 @@ typedef struct {
                              wide blocks, a larger power of two with a global-memory map of
                              that size (for queries whose balls are known to be large);
                              tiles that overflow are searched again with larger maps */
+    uint32_t search_from; /* which set the searches start from (Section 4 searches from
+                             each node of R): 0 (RN_FROM_AUTO) the smaller of R and S when
+                             the graph was loaded undirected -- distances are symmetric
+                             there, so the same pairs come out, (u in R, v in S) as always,
+                             from fewer searches -- S when it is at least a fifth smaller,
+                             else R; 1 (RN_FROM_R) always R; 2 (RN_FROM_S) always S
+                             (RN_EINVAL on a graph not loaded undirected).  Joins, k closest
+                             pairs, several joins in one call and batches follow it; points
+                             on edges and the hierarchical variant search from R */
 } rn_config;
+
+#define RN_FROM_AUTO 0u
+#define RN_FROM_R 1u
+#define RN_FROM_S 2u
 
 /* An edge list in host memory (library-owned arrays: free with rn_edges_free). */
 typedef struct {
@@ -168,6 +181,8 @@ typedef struct {
     uint64_t search_pairs;  /* pairs the search emitted: a join's pairs; k closest pairs: the
                                candidates of the last radius pass, before the selection (the
                                search fields above describe that pass) */
+    uint32_t from_s;        /* 1 when the searches started from the nodes of S
+                               (rn_config.search_from), 0 from R */
 } rn_query_stats;
 
 /*

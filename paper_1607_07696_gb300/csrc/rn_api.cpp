@@ -250,6 +250,10 @@ void apply_config(rn_graph *g, const rn_config *cfg) {
         if (ms && (ms < 8192 || (ms & (ms - 1)) || ms > (1u << 30)))
             rn::fail(RN_EINVAL, "map_slots must be 0 or a power of two in [8192, 2^30]");
         c.map_slots = ms;
+        if (cfg->search_from > RN_FROM_S) rn::fail(RN_EINVAL, "search_from must be 0, 1 or 2");
+        if (cfg->search_from == RN_FROM_S && !(g->info.flags & RN_UNDIRECTED))
+            rn::fail(RN_EINVAL, "searches from S need a graph loaded undirected");
+        c.search_from = cfg->search_from;
     }
     g->cfg = c;
 }
@@ -280,6 +284,7 @@ rn_status rn_graph_load(const uint32_t *src, const uint32_t *dst, const uint32_t
             for (uint64_t i = 0; i < 2ull * n; i++)
                 if (!std::isfinite(xy[i])) rn::fail(RN_EINVAL, "node coordinates must be finite");
         auto g = std::make_unique<rn_graph>();
+        g->info.flags = flags;
         apply_config(g.get(), cfg);
         rn::HostGraph h = rn::build_csr(n, m, src, dst, w, (flags & RN_UNDIRECTED) != 0);
         std::vector<uint32_t> order(n), perm(n), leaves;
@@ -321,6 +326,7 @@ rn_status rn_graph_load(const uint32_t *src, const uint32_t *dst, const uint32_t
         g->info.reorder_ms = std::chrono::duration<double, std::milli>(t1 - t0).count();
         cudaGetDevice(&g->device);
         rn::upload_graph(h, perm, order, &g->dev);
+        g->dev.symmetric = (flags & RN_UNDIRECTED) != 0;
         try {
             if (xy) rn::upload_geometry(xy, order, leaves, &g->dev);
             g->ws = rn::workspace_create(g->dev);
@@ -703,7 +709,7 @@ static rn::Batch *make_batch(const rn_query *q, uint32_t nq) {
     cudaGetDevice(&cur);
     std::vector<const rn::DeviceGraph *> graphs(nq);
     std::vector<const std::vector<uint32_t> *> perms(nq);
-    std::vector<uint32_t> med(nq), nR(nq), nS(nq), theta(nq);
+    std::vector<uint32_t> med(nq), nR(nq), nS(nq), theta(nq), from(nq);
     std::vector<const uint32_t *> R(nq), S(nq);
     for (uint32_t i = 0; i < nq; i++) {
         const rn_query &x = q[i];
@@ -723,8 +729,9 @@ static rn::Batch *make_batch(const rn_query *q, uint32_t nq) {
         nR[i] = x.nR;
         nS[i] = x.nS;
         theta[i] = x.theta;
+        from[i] = x.g->cfg.search_from;
     }
-    return rn::batch_create(graphs, perms, med, R, nR, S, nS, theta);
+    return rn::batch_create(graphs, perms, med, R, nR, S, nS, theta, from);
 }
 
 rn_status rn_batch_create(const rn_query *q, uint32_t nq, const rn_batch_config *cfg, rn_batch **out) {

@@ -319,6 +319,7 @@ struct Workspace {
     uint32_t *mq_first = nullptr, *mq_bound = nullptr, *mq_sbits = nullptr, *mq_sids = nullptr, *mq_soff = nullptr;
     const uint32_t **mq_sptr = nullptr;
     unsigned long long *mq_counts = nullptr;
+    uint8_t *mq_swap = nullptr;  // per query: searched from S
     uint64_t mq_cap_q = 0, mq_cap_bits = 0, mq_cap_sids = 0;
     // the largest source ball the last warp search met (or estimated, for sources
     // whose map overflowed) and its bound: predicts the next query's balls
@@ -391,7 +392,7 @@ void workspace_destroy(Workspace *ws) {
     if (ws->evs1) cudaEventDestroy(ws->evs1);
     if (ws->evr) cudaEventDestroy(ws->evr);
     for (void *p : {(void *)ws->mq_first, (void *)ws->mq_bound, (void *)ws->mq_sbits, (void *)ws->mq_sids,
-                    (void *)ws->mq_soff, (void *)ws->mq_sptr, (void *)ws->mq_counts})
+                    (void *)ws->mq_soff, (void *)ws->mq_sptr, (void *)ws->mq_counts, (void *)ws->mq_swap})
         device_free(p);
     device_free(ws->own_gmap);
     device_free(ws->seg);
@@ -573,6 +574,12 @@ struct SearchArgs {
     uint32_t inst_count, inst_shift;
     const uint32_t *const *inst_sbits;
     const uint32_t *inst_bound;
+    // searches from S (an undirected graph's distances are symmetric): a source is a node
+    // of S and its targets are R's, and every pair is written as (target, source) so the
+    // keys stay (u in R, v in S); per instance of a batch or query of several joins
+    // inst_swap[inst], else swap_uv for all
+    uint32_t swap_uv;
+    const uint8_t *inst_swap;
     // warp search: seg[si] = (first pair, pair count) of source si, or null
     uint2 *seg;
     // warp search: per resident warp (block * warps per block + warp) a list of MS slots,
@@ -600,6 +607,7 @@ struct TileCtx {
     unsigned long long key_prefix;
     uint32_t first, cnt;  // sources src[first .. first + cnt) of this tile (or part of one)
     uint32_t bound, delta, inst;
+    uint32_t swap;        // the tile's sources are S nodes: pairs written (target, source)
 };
 
 constexpr uint32_t KCP_BINS = 2048;
@@ -868,6 +876,7 @@ __global__ void __launch_bounds__(THREADS, (THREADS == NARROW ? CTAS_PER_SM : 1)
                 c.sbits = a.inst_sbits[lo];
                 c.key_prefix = (unsigned long long)lo << a.inst_shift;
             }
+            c.swap = a.inst_swap ? a.inst_swap[c.inst] : a.swap_uv;
             s_cx = c;
             s_tile0 = clock64();
         }
@@ -1169,7 +1178,7 @@ __global__ void __launch_bounds__(THREADS, (THREADS == NARROW ? CTAS_PER_SM : 1)
                             const unsigned long long idx = pos + __popc(bb & lt);
                             if (idx < a.out_cap) {
                                 const unsigned long long u = src_orig[lane * L + q];
-                                a.out_key[idx] = s_cx.key_prefix | (u << a.vbits) | v;
+                                a.out_key[idx] = s_cx.key_prefix | (s_cx.swap ? (v << a.vbits) | u : (u << a.vbits) | v);
                                 a.out_d[idx] = r.x[q];
                             }
                             if (a.kcp_hist) atomicAdd(&a.kcp_hist[r.x[q] >> a.hist_shift], 1u);
@@ -1435,6 +1444,7 @@ __global__ void __launch_bounds__(src_warps(MS) * 32, SRC_BLOCKS_PER_SM) k_sourc
             bound = a.tile_bound[si];
             delta = a.tile_delta[si];
         }
+        const bool swap = a.inst_swap ? a.inst_swap[inst] != 0 : a.swap_uv != 0;
         // k closest pairs: the live k-th distance bound (Algorithm 3's global threshold)
         // caps the source's bound, and is read again at every bucket boundary
         if (kcp) bound = min(bound, __ldcg(a.theta_live));
@@ -1734,7 +1744,8 @@ __global__ void __launch_bounds__(src_warps(MS) * 32, SRC_BLOCKS_PER_SM) k_sourc
                     if (ok[q]) {
                         const unsigned long long idx = pos + __popc(b & lt);
                         if (idx < a.out_cap) {
-                            a.out_key[idx] = prefix | (u << a.vbits) | (unsigned long long)v[q];
+                            a.out_key[idx] = prefix | (swap ? ((unsigned long long)v[q] << a.vbits) | u
+                                                            : (u << a.vbits) | (unsigned long long)v[q]);
                             a.out_d[idx] = dd[q];
                         }
                         if (kcp) atomicAdd(&a.kcp_hist[dd[q] >> a.hist_shift], 1u);
@@ -2849,6 +2860,20 @@ static void check_control(const Control &c) {
     if (c.err & 2u) fail(RN_EINVAL, "R or S repeats an id, or R and S overlap");
 }
 
+// Whether a query's searches start from S.  The paper searches from every node of R; on
+// an undirected graph d(u, v) = d(v, u), so searching from S instead finds the same pairs
+// (written back as (u in R, v in S)) with |S| searches instead of |R|.  By default that
+// is done when S is at least a fifth smaller than R (below that the saving does not pay
+// for losing the warp search's placement order).
+static bool search_from_s(const DeviceGraph &g, const EngineConfig &cfg, uint64_t nR, uint64_t nS) {
+    if (cfg.search_from == RN_FROM_R) return false;
+    if (cfg.search_from == RN_FROM_S) {
+        if (!g.symmetric) fail(RN_EINVAL, "searches from S need a graph loaded undirected");
+        return true;
+    }
+    return g.symmetric && nS * 5 < nR * 4;
+}
+
 void run_join(const DeviceGraph &g, Workspace *ws, const EngineConfig &cfg, uint32_t median_w,
               const uint32_t *dR, uint32_t nR, const uint32_t *dS, uint32_t nS, uint32_t theta,
               rn_dpairs *out, void *stream, rn_query_stats *stats) {
@@ -2860,9 +2885,16 @@ void run_join(const DeviceGraph &g, Workspace *ws, const EngineConfig &cfg, uint
     std::lock_guard<std::mutex> device_lock(ws->sh->mu);
     Range range("rn.join");
     *stats = rn_query_stats{};
+    const bool from_s = search_from_s(g, cfg, nR, nS);
+    if (from_s) {  // S's nodes are the sources, R's the targets (below, "R" is the sources)
+        std::swap(dR, dS);
+        std::swap(nR, nS);
+    }
+    stats->from_s = from_s;
     const bool by_source = use_source_search(g, ws, cfg, theta, median_w);
     // the warp search's segments give the output order when sources run in output order
-    const bool place = by_source && g.iperm_inverts_perm;
+    // (and are R's: a segment of an S source holds one v and many u)
+    const bool place = by_source && g.iperm_inverts_perm && !from_s;
     const uint32_t delta = choose_delta(cfg, median_w, by_source);
     stats->tile_width = by_source ? 1 : T;
     stats->delta = delta;
@@ -2905,6 +2937,7 @@ void run_join(const DeviceGraph &g, Workspace *ws, const EngineConfig &cfg, uint
     a.out_d = ws->valA;
     a.out_cap = ws->pair_cap;
     a.seg = place ? ensure_segments(ws, nR, st) : nullptr;
+    a.swap_uv = from_s;
     uint64_t retried = 0;
     const std::vector<uint32_t> one_query;
     auto search_pass = [&] {
@@ -3021,24 +3054,33 @@ void run_join_multi(const DeviceGraph &g, Workspace *ws, const EngineConfig &cfg
     stats->delta = delta;
     ws->launches = 0;
     RN_CUDA(cudaEventRecord(ws->ev0, st));
-    // the sources: every query's R in internal ids, ascending, one query after another
-    std::vector<uint32_t> src, first(nq + 1, 0), bound(nq), soff(nq + 1, 0), sids;
+    // the sources: every query's R (or, searched from S, its S) in internal ids, ascending,
+    // one query after another
+    std::vector<uint32_t> src, first(nq + 1, 0), bound(nq), soff(nq + 1, 0), sids, nsrc(nq);
+    std::vector<uint8_t> swp(nq, 0);
+    bool any_swap = false;
     for (uint32_t i = 0; i < nq; i++) {
+        const bool sw = search_from_s(g, cfg, nR[i], nS[i]);
+        swp[i] = sw;
+        any_swap |= sw;
+        const uint32_t *Ri = sw ? S[i] : R[i], *Si = sw ? R[i] : S[i];
+        nsrc[i] = sw ? nS[i] : nR[i];
+        const uint32_t nt = sw ? nR[i] : nS[i];
         first[i] = uint32_t(src.size());
         const size_t b = src.size();
         if (by_source && g.iperm_inverts_perm) {
             // each source alone: in increasing original id, the output order
-            std::vector<uint32_t> r(R[i], R[i] + nR[i]);
+            std::vector<uint32_t> r(Ri, Ri + nsrc[i]);
             std::sort(r.begin(), r.end());
             for (uint32_t x : r) src.push_back(perm[x]);
         } else {
-            for (uint32_t j = 0; j < nR[i]; j++) src.push_back(perm[R[i][j]]);
+            for (uint32_t j = 0; j < nsrc[i]; j++) src.push_back(perm[Ri[j]]);
             std::sort(src.begin() + b, src.end());  // graph neighbours share tiles
         }
         bound[i] = theta[i] == RN_INF ? RN_THETA_MAX : theta[i];
         if (bound[i] > RN_THETA_MAX) fail(RN_EINVAL, "theta must be <= 2^31 or RN_INF");
         soff[i] = uint32_t(sids.size());
-        sids.insert(sids.end(), S[i], S[i] + nS[i]);
+        sids.insert(sids.end(), Si, Si + nt);
         if (src.size() >= 0xFFFFFFFFull || sids.size() >= 0xFFFFFFFFull) fail(RN_EINVAL, "too many sources or targets");
     }
     first[nq] = uint32_t(src.size());
@@ -3057,17 +3099,18 @@ void run_join_multi(const DeviceGraph &g, Workspace *ws, const EngineConfig &cfg
     const uint32_t ms0 = by_source ? source_first_map(ws, max_bound) : 0;
     std::vector<uint4> ranges;
     for (uint32_t i = 0; i < nq; i++)
-        for (uint32_t j = 0; j < nR[i]; j += tile_src)
-            ranges.push_back(make_uint4(first[i] + j, std::min(tile_src, nR[i] - j), 0, 0));
+        for (uint32_t j = 0; j < nsrc[i]; j += tile_src)
+            ranges.push_back(make_uint4(first[i] + j, std::min(tile_src, nsrc[i] - j), 0, 0));
     // device copies
     ensure_u32(&ws->rsorted, &ws->rsorted_cap, std::max<uint32_t>(total, 1));
     if (ws->mq_cap_q < nq + 1) {
         for (void **p : {(void **)&ws->mq_first, (void **)&ws->mq_bound, (void **)&ws->mq_soff, (void **)&ws->mq_sptr,
-                         (void **)&ws->mq_counts}) {
+                         (void **)&ws->mq_counts, (void **)&ws->mq_swap}) {
             device_free(*p);
             *p = nullptr;
         }
         ws->mq_cap_q = std::max<uint64_t>(nq + 1, 64);
+        ws->mq_swap = (uint8_t *)device_alloc(ws->mq_cap_q);
         ws->mq_first = (uint32_t *)device_alloc(ws->mq_cap_q * 4);
         ws->mq_bound = (uint32_t *)device_alloc(ws->mq_cap_q * 4);
         ws->mq_soff = (uint32_t *)device_alloc(ws->mq_cap_q * 4);
@@ -3094,6 +3137,7 @@ void run_join_multi(const DeviceGraph &g, Workspace *ws, const EngineConfig &cfg
     RN_CUDA(cudaMemcpyAsync(ws->mq_bound, bound.data(), size_t(nq) * 4, cudaMemcpyHostToDevice, st));
     RN_CUDA(cudaMemcpyAsync(ws->mq_soff, soff.data(), size_t(nq + 1) * 4, cudaMemcpyHostToDevice, st));
     RN_CUDA(cudaMemcpyAsync(ws->mq_sptr, sptr.data(), size_t(nq) * 8, cudaMemcpyHostToDevice, st));
+    if (any_swap) RN_CUDA(cudaMemcpyAsync(ws->mq_swap, swp.data(), nq, cudaMemcpyHostToDevice, st));
     if (!sids.empty())
         RN_CUDA(cudaMemcpyAsync(ws->mq_sids, sids.data(), sids.size() * 4, cudaMemcpyHostToDevice, st));
     RN_CUDA(cudaMemsetAsync(ws->mq_sbits, 0, bits_words * 4, st));
@@ -3127,7 +3171,9 @@ void run_join_multi(const DeviceGraph &g, Workspace *ws, const EngineConfig &cfg
     a.inst_shift = 2 * vbits;
     a.inst_sbits = ws->mq_sptr;
     a.inst_bound = ws->mq_bound;
-    const bool place = by_source && g.iperm_inverts_perm;
+    a.inst_swap = any_swap ? ws->mq_swap : nullptr;
+    stats->from_s = any_swap;
+    const bool place = by_source && g.iperm_inverts_perm && !any_swap;
     a.seg = place ? ensure_segments(ws, total, st) : nullptr;
     uint64_t retried = 0;
     auto search_pass = [&] {
@@ -3461,6 +3507,12 @@ void run_kcp(const DeviceGraph &g, Workspace *ws, const EngineConfig &cfg, uint3
     std::lock_guard<std::mutex> device_lock(ws->sh->mu);
     Range range("rn.kcp");
     *stats = rn_query_stats{};
+    const bool from_s = search_from_s(g, cfg, nR, nS);
+    if (from_s) {  // S's nodes are the sources, R's the targets (below, "R" is the sources)
+        std::swap(dR, dS);
+        std::swap(nR, nS);
+    }
+    stats->from_s = from_s;
     ws->launches = 0;
     RN_CUDA(cudaEventRecord(ws->ev0, st));
 
@@ -3495,6 +3547,7 @@ void run_kcp(const DeviceGraph &g, Workspace *ws, const EngineConfig &cfg, uint3
     a.kcp_hist = hist;
     a.theta_live = theta_live;
     a.kcp_k = k;
+    a.swap_uv = from_s;
     // the first radius: one bucket of the warp search (16 median weights) when its ball
     // fits a warp map, else one bucket of the tile search (4 median weights)
     // a source's ball at the k-th distance holds about (k / |R|) (n / |S|) nodes (each
@@ -3517,7 +3570,7 @@ void run_kcp(const DeviceGraph &g, Workspace *ws, const EngineConfig &cfg, uint3
         const bool by_source = warp_ok && use_source_search(g, ws, cfg, uint32_t(tau), median_w);
         const uint32_t delta = choose_delta(cfg, median_w, by_source);
         // the warp search takes R in output order and records each source's segment
-        const bool place = by_source && g.iperm_inverts_perm;
+        const bool place = by_source && g.iperm_inverts_perm && !from_s;
         prep_sets(g, ws, dR, nR, dS, nS, st, place);
         a.src = ws->rsorted;  // prep_sets may have (re)allocated the R list
         a.seg = place ? ensure_segments(ws, nR, st) : nullptr;
@@ -3860,10 +3913,12 @@ void run_points(const DeviceGraph &g, const std::vector<uint32_t> &perm, PointsS
         Range r("rn.points.subdivide");
         points_graph(g, perm, R, nR, S, nS, ps, st);
     }
+    EngineConfig pc = cfg;
+    pc.search_from = RN_FROM_R;  // the points' searches start from R's points
     if (k == 0)
-        run_join(ps->aug, ps->ws, cfg, median_w, ps->ids, nR, ps->ids + nR, nS, theta, out, stream, stats);
+        run_join(ps->aug, ps->ws, pc, median_w, ps->ids, nR, ps->ids + nR, nS, theta, out, stream, stats);
     else
-        run_kcp(ps->aug, ps->ws, cfg, median_w, ps->ids, nR, ps->ids + nR, nS, k, theta, out, stream, stats);
+        run_kcp(ps->aug, ps->ws, pc, median_w, ps->ids, nR, ps->ids + nR, nS, k, theta, out, stream, stats);
 }
 
 // ----------------------------------------------------- queries in a rectangle ----
@@ -4791,8 +4846,8 @@ struct Batch {
     int device = 0;
     uint32_t nq = 0, n_u = 0, pad = 0, vbits = 1;
     uint64_t arcs_u = 0;
-    std::vector<uint32_t> n, nR, theta, median_w, cls, node_off;
-    std::vector<std::vector<uint32_t>> rint;  // per instance: R in union internal ids, ascending
+    std::vector<uint32_t> n, nR, theta, median_w, cls, node_off;  // nR: the instance's sources
+    std::vector<std::vector<uint32_t>> rint;  // per instance: its sources in union internal ids, ascending
     std::vector<BatchPlan> plan;
     std::vector<uint32_t> map;       // per instance: slots of the first map
     std::vector<uint32_t> ball;      // per instance: largest union ball seen under plan[i].T
@@ -4802,6 +4857,7 @@ struct Batch {
     bool laid_out_by_cost = false;   // the layout used measured costs
     DeviceGraph ug;  // the union graph (row_ptr, adj, iperm)
     uint32_t *sbits = nullptr, *node_off_d = nullptr, *inst_ball = nullptr;
+    uint8_t *inst_swap = nullptr;  // per instance: searched from S (null when none is)
     Workspace *ws = nullptr;  // control block, retry lists, global maps, events of the batch
     cudaStream_t stream = nullptr;
     unsigned long long *inst_pairs = nullptr, *inst_cycles = nullptr, *pair_off_d = nullptr;
@@ -4842,7 +4898,7 @@ void batch_destroy(Batch *b) {
     if (b->stream) cudaStreamSynchronize(b->stream);
     batch_drop_graph(b);
     batch_free_groups(b);
-    for (void *p : {(void *)b->sbits, (void *)b->node_off_d, (void *)b->inst_ball, (void *)b->inst_pairs,
+    for (void *p : {(void *)b->sbits, (void *)b->inst_swap, (void *)b->node_off_d, (void *)b->inst_ball, (void *)b->inst_pairs,
                     (void *)b->inst_cycles, (void *)b->pair_off_d, (void *)b->keyA, (void *)b->keyB,
                     (void *)b->valA, (void *)b->valB, (void *)b->hist, (void *)b->out_u, (void *)b->out_v,
                     (void *)b->out_d, (void *)b->ug.row_ptr, (void *)b->ug.adj, (void *)b->ug.iperm})
@@ -4972,6 +5028,7 @@ static SearchArgs batch_args(Batch *b, const Batch::Group &g) {
     a.inst_pairs = b->inst_pairs;
     a.inst_cycles = b->inst_cycles;
     a.inst_ball = b->inst_ball;
+    a.inst_swap = b->inst_swap;
     a.vbits = b->vbits;
     a.ctl = b->ws->ctl;
     a.out_key = b->keyA;
@@ -5264,12 +5321,24 @@ void batch_tune(Batch *b) {
 Batch *batch_create(const std::vector<const DeviceGraph *> &graphs, const std::vector<const std::vector<uint32_t> *> &perms,
                     const std::vector<uint32_t> &median_w, const std::vector<const uint32_t *> &R,
                     const std::vector<uint32_t> &nR, const std::vector<const uint32_t *> &S,
-                    const std::vector<uint32_t> &nS, const std::vector<uint32_t> &theta) {
+                    const std::vector<uint32_t> &nS, const std::vector<uint32_t> &theta,
+                    const std::vector<uint32_t> &search_from) {
     Batch *b = new Batch();
     try {
         b->nq = uint32_t(graphs.size());
         RN_CUDA(cudaGetDevice(&b->device));
-        b->nR = nR;
+        // each instance searches from its smaller set on an undirected graph (as a single
+        // join does): its sources and its target bitmap swap roles
+        std::vector<uint8_t> swp(b->nq, 0);
+        bool any_swap = false;
+        b->nR.resize(b->nq);
+        for (uint32_t i = 0; i < b->nq; i++) {
+            EngineConfig ec;
+            ec.search_from = search_from.empty() ? 0u : search_from[i];
+            swp[i] = search_from_s(*graphs[i], ec, nR[i], nS[i]);
+            any_swap |= swp[i] != 0;
+            b->nR[i] = swp[i] ? nS[i] : nR[i];
+        }
         b->median_w = median_w;
         b->n.resize(b->nq);
         b->theta.resize(b->nq);
@@ -5286,7 +5355,7 @@ Batch *batch_create(const std::vector<const DeviceGraph *> &graphs, const std::v
             b->n[i] = graphs[i]->n;
             b->theta[i] = theta[i] == RN_INF ? RN_THETA_MAX : theta[i];
             if (b->theta[i] > RN_THETA_MAX) fail(RN_EINVAL, "theta must be <= 2^31 or RN_INF");
-            b->cls[i] = size_class(b->n[i], nR[i], b->theta[i], median_w[i]);
+            b->cls[i] = size_class(b->n[i], b->nR[i], b->theta[i], median_w[i]);
             // the default plan: the warp search while the ball estimated from the bound
             // fits a 2048-slot warp map (a dozen warps per SM or more), else tiles, whose
             // sources share their searches' passes
@@ -5341,23 +5410,26 @@ Batch *batch_create(const std::vector<const DeviceGraph *> &graphs, const std::v
         b->rint.resize(b->nq);
         for (uint32_t i = 0; i < b->nq; i++) {
             const std::vector<uint32_t> &perm = *perms[i];
+            const uint32_t *src = swp[i] ? S[i] : R[i], *tgt = swp[i] ? R[i] : S[i];
+            const uint32_t ntgt = swp[i] ? nR[i] : nS[i];
             auto &r = b->rint[i];
-            r.resize(nR[i]);
-            for (uint32_t j = 0; j < nR[i]; j++) r[j] = perm[R[i][j]] + b->node_off[i];
+            r.resize(b->nR[i]);
+            for (uint32_t j = 0; j < b->nR[i]; j++) r[j] = perm[src[j]] + b->node_off[i];
             std::sort(r.begin(), r.end());
-            for (uint32_t j = 0; j < nS[i]; j++) {
-                const uint32_t x = perm[S[i][j]] + b->node_off[i];
+            for (uint32_t j = 0; j < ntgt; j++) {
+                const uint32_t x = perm[tgt[j]] + b->node_off[i];
                 sb[x >> 5] |= 1u << (x & 31);
             }
         }
         b->sbits = upload_vec(sb);
+        if (any_swap) b->inst_swap = upload_vec(swp);
         b->node_off_d = upload_vec(b->node_off);
         b->inst_pairs = (unsigned long long *)device_alloc(size_t(b->nq) * 8);
         b->inst_cycles = (unsigned long long *)device_alloc(size_t(b->nq) * 8);
         b->inst_ball = (uint32_t *)device_alloc(size_t(b->nq) * 4);
         b->pair_off_d = (unsigned long long *)device_alloc((size_t(b->nq) + 1) * 8);
         uint64_t totR = 0;
-        for (uint32_t x : nR) totR += x;
+        for (uint32_t x : b->nR) totR += x;
         batch_reserve_pairs(b, std::max<uint64_t>(totR * 64, 1 << 16));
         b->stats.instances = b->nq;
         if (b->n_u >= SK_NODE)  // the warp search keys nodes in 28 bits

@@ -67,6 +67,7 @@ struct DeviceGraph {
     uint32_t *perm = nullptr;     // original id -> internal id
     uint32_t *iperm = nullptr;    // internal id -> original id
     bool iperm_inverts_perm = true;  // false when output ids are not the input ids (points)
+    bool symmetric = false;          // every arc has its reverse with the same weight (undirected)
     // node coordinates (rn_graph_load's xy), or none: per node (x, y) by internal id, and
     // the leaves of the partition -- leaf i holds internal ids [leaf_start[i],
     // leaf_start[i + 1]) -- with their bounding rectangles (xmin, ymin, xmax, ymax)
@@ -92,6 +93,7 @@ struct EngineConfig {
     uint32_t tile_src = 0;  // sources per tile; 0: spread over whole waves of blocks
     uint32_t delta = 0;     // 0: derive from the weights
     uint32_t map_slots = 0; // first slot map: 0 / 8192 narrow, 16384 wide, larger: global
+    uint32_t search_from = 0;  // RN_FROM_AUTO, RN_FROM_R or RN_FROM_S
 };
 
 void run_join(const DeviceGraph &g, Workspace *ws, const EngineConfig &cfg, uint32_t median_w,
@@ -123,7 +125,8 @@ struct Batch;
 Batch *batch_create(const std::vector<const DeviceGraph *> &graphs, const std::vector<const std::vector<uint32_t> *> &perms,
                     const std::vector<uint32_t> &median_w, const std::vector<const uint32_t *> &R,
                     const std::vector<uint32_t> &nR, const std::vector<const uint32_t *> &S,
-                    const std::vector<uint32_t> &nS, const std::vector<uint32_t> &theta);
+                    const std::vector<uint32_t> &nS, const std::vector<uint32_t> &theta,
+                    const std::vector<uint32_t> &search_from);
 void batch_tune(Batch *b);
 void batch_run(Batch *b, void *stream, bool use_graph);
 void batch_pairs_dev(const Batch *b, uint32_t i, const uint32_t **u, const uint32_t **v, const uint32_t **d,

@@ -44,7 +44,8 @@ class rn_dpairs(C.Structure):
 
 class rn_config(C.Structure):
     _fields_ = [("tile_width", C.c_uint32), ("tile_sources", C.c_uint32), ("delta", C.c_uint32),
-                ("leaf_size", C.c_uint32), ("alpha", C.c_float), ("map_slots", C.c_uint32)]
+                ("leaf_size", C.c_uint32), ("alpha", C.c_float), ("map_slots", C.c_uint32),
+                ("search_from", C.c_uint32)]
 
 
 class rn_graph_stats(C.Structure):
@@ -65,7 +66,7 @@ class rn_query_stats(C.Structure):
                 ("cycles_boundaries", C.c_uint64), ("cycles_emission", C.c_uint64),
                 ("cycles_step_a", C.c_uint64), ("round_arcs", C.c_uint64), ("max_ball", C.c_uint64),
                 ("retry_ms", C.c_double), ("dirty_groups", C.c_uint64), ("slot_lanes", C.c_uint64),
-                ("box_leaf_decided", C.c_uint64), ("search_pairs", C.c_uint64)]
+                ("box_leaf_decided", C.c_uint64), ("search_pairs", C.c_uint64), ("from_s", C.c_uint32)]
 
 
 class rn_query(C.Structure):
@@ -250,6 +251,7 @@ def _config(cfg: dict | None):
     c.leaf_size = int(cfg.get("leaf_size", 0))
     c.alpha = float(cfg.get("alpha", -1.0))
     c.map_slots = int(cfg.get("map_slots", 0))
+    c.search_from = int(cfg.get("search_from", 0))
     return C.byref(c)
 
 
