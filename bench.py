@@ -315,8 +315,10 @@ def batch_leg(rn, steps: int, warmup: int, stream, flush) -> dict:
         "launches_per_run": int(s1["launches_per_run"]), "plain_launches": int(plain_launches),
         "autotune_s": tune_s, "default_plan_groups": int(s0["groups"]),
         "tuned": {1: f"one plan for all (tile width {int(s1['plan_tile_width'])}, buckets of "
-                     f"{int(s1['plan_delta_mult'])} median weights)",
-                  2: "plan per size class"}.get(int(s1["tuned"]), "no"),
+                     f"{int(s1['plan_delta_mult'])} median weights, {int(s1['plan_tile_sources'])} sources "
+                     f"per tile)",
+                  2: "plan per size class", 3: "the default plans (warp search for small balls, tiles of 8 "
+                                               "sources for large)"}.get(int(s1["tuned"]), "no"),
     }
     del b0, b1
     return res

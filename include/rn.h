@@ -413,11 +413,14 @@ typedef struct {
     uint64_t tiles, retried_tiles, pairs;
     uint32_t eager_runs, graph_runs, launches_per_run;
     uint32_t tuned;              /* 0: not tuned; 1: one candidate plan for every instance;
-                                    2: a plan per size class of instance */
+                                    2: a plan per size class of instance; 3: the plans the
+                                    batch had (the default, or a loaded cache's) were the
+                                    fastest */
     uint32_t candidates;         /* batch runs the tuning took */
     double device_ms;            /* last run, CUDA events on the batch's stream */
     uint32_t plan_tile_width;    /* tuned = 1: the plan's tile width (1: the warp search) */
     uint32_t plan_delta_mult;    /* tuned = 1: its bucket width in median arc weights */
+    uint32_t plan_tile_sources;  /* tuned = 1: its sources per tile (1 for the warp search) */
 } rn_batch_stats;
 
 /*

@@ -83,7 +83,7 @@ class rn_batch_stats(C.Structure):
                 ("retried_tiles", C.c_uint64), ("pairs", C.c_uint64), ("eager_runs", C.c_uint32),
                 ("graph_runs", C.c_uint32), ("launches_per_run", C.c_uint32), ("tuned", C.c_uint32),
                 ("candidates", C.c_uint32), ("device_ms", C.c_double), ("plan_tile_width", C.c_uint32),
-                ("plan_delta_mult", C.c_uint32)]
+                ("plan_delta_mult", C.c_uint32), ("plan_tile_sources", C.c_uint32)]
 
 
 class rn_edges(C.Structure):

@@ -72,7 +72,7 @@ def test_autotuned_batch_and_one_shot(rn, oracle):
             for (e, g, R, S, th) in inst]
     b = rn.rn_batch_create(qs, autotune=True)
     rn.rn_batch_run(b)
-    assert rn.rn_batch_stats_get(b)["tuned"] in (1, 2)
+    assert rn.rn_batch_stats_get(b)["tuned"] in (1, 2, 3)
     for i, ref in enumerate(refs):
         assert same(rn.rn_batch_pairs(b, i), ref), f"tuned instance {i}"
     outs = rn.rn_join_batch(qs)
