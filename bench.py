@@ -311,6 +311,8 @@ def batch_leg(rn, steps: int, warmup: int, stream, flush) -> dict:
         "batched_vs_plain": plain_ms / tuned_ms,
         "gteps_batched": WORKLOADS["batch512"]["alg_arcs"] / (tuned_ms / 1e3) / 1e9,
         "gteps_plain": WORKLOADS["batch512"]["alg_arcs"] / (plain_ms / 1e3) / 1e9,
+        "gteps_basis": "arcs of searches from every R node (the paper's method, counted by the oracle); "
+                       "searching from the smaller set the engine relaxes fewer",
         "tiles": int(s1["tiles"]), "groups": int(s1["groups"]), "graph_runs": int(s1["graph_runs"]),
         "launches_per_run": int(s1["launches_per_run"]), "plain_launches": int(plain_launches),
         "autotune_s": tune_s, "default_plan_groups": int(s0["groups"]),

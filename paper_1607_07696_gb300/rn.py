@@ -20,7 +20,9 @@ RN_OK, RN_EINVAL, RN_ENOMEM, RN_ECUDA, RN_ETIMEOUT = 0, 1, 2, 3, 4
 RN_ECANCELLED, RN_EBUSY, RN_EINTERNAL, RN_ENOTIMPL = 5, 6, 7, 8
 RN_UNDIRECTED, RN_REORDER = 1, 2
 RN_INF = 0xFFFFFFFF
+RN_FROM_AUTO, RN_FROM_R, RN_FROM_S = 0, 1, 2
 RN_THETA_MAX = 1 << 31
+RN_WEIGHT_LIMIT = 1 << 24  # weights must be below it
 
 _NAMES = {0: "RN_OK", 1: "RN_EINVAL", 2: "RN_ENOMEM", 3: "RN_ECUDA", 4: "RN_ETIMEOUT",
           5: "RN_ECANCELLED", 6: "RN_EBUSY", 7: "RN_EINTERNAL", 8: "RN_ENOTIMPL"}

@@ -48,3 +48,27 @@ def test_struct_layouts_match_the_header(tmp_path):
         assert got[(s.__name__, ".")] == C.sizeof(s), f"sizeof({s.__name__})"
         for f in s._fields_:
             assert got[(s.__name__, f[0])] == getattr(s, f[0]).offset, f"{s.__name__}.{f[0]}"
+
+
+def test_constants_match_the_header(tmp_path):
+    """Every RN_ constant the header defines (status codes, flags, bounds, search sides,
+    rectangle roles) has the same value in the binding."""
+    import re
+
+    from paper_1607_07696_gb300 import rn
+
+    header = open(os.path.join(ROOT, "include", "rn.h")).read()
+    names = sorted(set(re.findall(r"#define (RN_[A-Z_]+) ", header)) | set(re.findall(r"^\s+(RN_[A-Z]+) = ", header, re.M)))
+    names = [n for n in names if n != "RN_H"]
+    assert len(names) >= 15
+    lines = ["#include <stdio.h>", '#include "rn.h"', "int main(void) {"]
+    lines += [f'    printf("{n} %llu\\n", (unsigned long long)({n}));' for n in names]
+    lines += ["    return 0;", "}"]
+    src = tmp_path / "consts.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "consts"
+    subprocess.run(["gcc", "-std=c11", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    for line in subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.splitlines():
+        name, value = line.split()
+        assert hasattr(rn, name), f"{name} is missing from the binding"
+        assert getattr(rn, name) == int(value), name
