@@ -3548,18 +3548,25 @@ void run_kcp(const DeviceGraph &g, Workspace *ws, const EngineConfig &cfg, uint3
     a.theta_live = theta_live;
     a.kcp_k = k;
     a.swap_uv = from_s;
-    // the first radius: one bucket of the warp search (16 median weights) when its ball
-    // fits a warp map, else one bucket of the tile search (4 median weights)
     // a source's ball at the k-th distance holds about (k / |R|) (n / |S|) nodes (each
     // source's share of the k pairs, one S node per n / |S| nodes): a warp's map passes at
     // bucket boundaries and emission do not pay for balls of a few dozen nodes, which the
     // tile search shares between the sources of a tile
     const double kth_ball = nR && nS ? double(k) / nR * (double(g.n) / nS) : 0.0;
     const bool warp_ok = cfg.tile_width == 1 || kth_ball >= 64.0;
-    const uint32_t delta_src = choose_delta(cfg, median_w, true);
-    uint64_t tau = std::min<uint64_t>(theta, delta_src);
-    if (!warp_ok || !use_source_search(g, ws, cfg, uint32_t(tau), median_w))
-        tau = std::min<uint64_t>(theta, choose_delta(cfg, median_w, false));
+    // the first radius: where about 1.25 k pairs are expected, the balls growing as the
+    // workspace's last warp search measured them (mean ball at its bound, times the
+    // squared radius ratio) or, with none behind it, as a lattice's 2 (r / w_med)^2; a
+    // radius too small costs a second pass, one too large only candidates the live
+    // bound soon stops collecting
+    uint64_t tau = theta;
+    if (kth_ball > 0) {
+        const double need = 1.25 * kth_ball;  // nodes per ball
+        const double r = ws->ball_theta && ws->ball_mean > 0
+                             ? double(ws->ball_theta) * std::sqrt(need / ws->ball_mean)
+                             : double(std::max<uint32_t>(median_w, 1)) * std::sqrt(need / 2.0);
+        tau = std::min<uint64_t>(theta, std::max<uint64_t>(uint64_t(std::min(r, 4e9)), std::max<uint32_t>(median_w, 1)));
+    }
     uint64_t retried = 0;
     uint32_t passes = 0;
     Control c{};
