@@ -1828,6 +1828,436 @@ __global__ void __launch_bounds__(src_warps(MS) * 32, SRC_BLOCKS_PER_SM) k_sourc
     }
 }
 
+// ---------------------------------------------------- cooperative source search ----
+// A source whose ball needs a large warp map (4096 or 8192 slots) leaves a lone warp
+// with a map that fills a sixth or a third of an SM's shared memory: three to six warps
+// per SM, each walking its round's items alone.  Here W warps share one source's map.
+// A round is taken in waves of W x 64 items: every warp scans its 64 (flags cleared,
+// distance and CSR range read), a block barrier, every warp relaxes the arcs of its
+// items, a barrier -- so no warp clears a slot's flags while another relaxes into it,
+// and each wave sees the distances of the waves before it, as the warp search's chunks
+// do.  Queue pushes, the fill count and the S-node list go through shared atomics;
+// bucket boundaries split the map between the warps.  The protocol and the results
+// are the warp search's.
+template <uint32_t MS, uint32_t W>
+__global__ void __launch_bounds__(W * 32, (3 * 8192) / MS) k_source_coop(SearchArgs a) {
+    constexpr uint32_t QS = src_qcap(MS);
+    constexpr uint32_t NT = W * 32;
+    constexpr int AP = 4;
+    extern __shared__ __align__(16) uint32_t smem[];
+    // block-wide state of the current source, read by every thread after a barrier
+    __shared__ uint32_t s_item, s_ncur, s_nnext, s_fill, s_nlist, s_fail, s_bound, s_min, s_nq, s_cnt, s_stop;
+    __shared__ unsigned long long s_base;
+    __shared__ uint32_t s_wcnt[W];
+    const uint32_t tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const uint32_t lt = (1u << lane) - 1;
+    uint32_t *key = smem, *dist = smem + MS, *qa = dist + MS, *qb = qa + QS;
+    for (uint32_t h = tid; h < MS; h += NT) {
+        key[h] = SK_EMPTY;
+        dist[h] = INF;
+    }
+    if (tid == 0) s_stop = __ldcg(&a.ctl->err) != 0;
+    __syncthreads();
+    if (s_stop) return;
+    const uint32_t nR1 = a.nR_fixed ? a.nR_fixed : __ldcg(&a.ctl->r_count);
+    const uint32_t nitems = a.range_list ? a.ntiles : nR1;
+    const bool kcp = a.kcp_hist != nullptr;
+    uint32_t *const slist = a.slist + size_t(blockIdx.x) * MS;
+    // telemetry: per lane (scans, arcs, arcs of first scans), then per warp at the end;
+    // rounds, boundaries, slots and cycles counted by thread 0
+    unsigned long long t_scans = 0, t_arcs = 0, t_slot_arcs = 0;
+    unsigned long long t_rounds = 0, t_bounds = 0, t_slots = 0, t_cyc_round = 0, t_cyc_bound = 0, t_cyc_emit = 0;
+    uint32_t t_max_ball = 0, t_max_seg = 0;
+
+    for (;;) {
+        if (tid == 0) s_item = atomicAdd(&a.ctl->tile_next, 1u);
+        __syncthreads();
+        const uint32_t item = s_item;
+        __syncthreads();  // every thread has read s_item
+        if (item >= nitems) break;
+        const uint32_t si = a.range_list ? a.range_list[item].x : item;
+        if (si >= nR1) continue;  // never past R (the same for every thread)
+        uint32_t bound = a.bound;
+        const uint32_t *sbits = a.sbits;
+        unsigned long long prefix = 0;
+        uint32_t inst = 0;
+        if (a.inst_first) {
+            uint32_t lo = 0, hi = a.inst_count - 1;
+            while (lo < hi) {
+                const uint32_t mid = (lo + hi + 1) >> 1;
+                if (a.inst_first[mid] <= si) lo = mid;
+                else hi = mid - 1;
+            }
+            inst = lo;
+            bound = a.inst_bound[lo];
+            sbits = a.inst_sbits[lo];
+            prefix = (unsigned long long)lo << a.inst_shift;
+        }
+        uint64_t delta = a.delta;
+        if (a.tile_bound) {
+            inst = a.tile_inst[si];
+            bound = a.tile_bound[si];
+            delta = a.tile_delta[si];
+        }
+        const bool swap = a.inst_swap ? a.inst_swap[inst] != 0 : a.swap_uv != 0;
+        const uint32_t y0 = a.src[si];
+        if (y0 >= a.n_nodes) {  // (the same for every thread)
+            if (tid == 0) record_check(a.ctl, 11, si, y0);
+            continue;
+        }
+        const unsigned long long u = __ldg(&a.iperm[y0]);
+        const uint32_t t_source = uint32_t(clock());
+        uint32_t t_mark = t_source;
+        if (tid == 0) {
+            const uint32_t h = (y0 * 0x9E3779B1u) >> (32 - log2u(MS));
+            key[h] = y0 | SK_DIRTY | SK_QUEUED;
+            dist[h] = 0;
+            qa[0] = h;
+            s_ncur = 1;
+            s_nnext = 0;
+            s_fill = 1;
+            s_nlist = 0;
+            s_fail = 0;
+            s_bound = kcp ? min(bound, __ldcg(a.theta_live)) : bound;
+        }
+        __syncthreads();
+        bound = s_bound;  // the k-closest-pairs live bound, read once for the whole block
+        uint32_t *qcur = qa, *qnext = qb;
+        uint64_t tau = delta < uint64_t(bound) + 1 ? delta : uint64_t(bound) + 1;
+
+        // the dirty slots below lim go to the near queue (as many as fit), every other slot
+        // loses a stale queued flag; the least dirty distance goes to s_min.  The callers
+        // reset s_nq and s_min and hold a barrier before and after.
+        auto collect = [&](uint64_t lim) {
+            uint32_t m = INF;
+            for (uint32_t h = tid; h < MS; h += NT) {
+                const uint32_t k = key[h];
+                const bool dirty = (k & SK_DIRTY) != 0;
+                const uint32_t d = dirty ? dist[h] : INF;
+                m = min(m, d);
+                const bool take = dirty && d < lim;
+                const uint32_t b = __ballot_sync(FULL, take);
+                uint32_t qb0 = 0;
+                if (lane == 0 && b) qb0 = atomicAdd(&s_nq, uint32_t(__popc(b)));
+                const uint32_t qi = __shfl_sync(FULL, qb0, 0) + __popc(b & lt);
+                const bool queued = take && qi < QS;
+                if (queued) qcur[qi] = h;
+                const uint32_t nk = queued ? (k | SK_QUEUED) : (k & ~SK_QUEUED);
+                if (nk != k) key[h] = nk;
+            }
+            m = __reduce_min_sync(FULL, m);
+            if (lane == 0) atomicMin(&s_min, m);
+        };
+
+        for (;;) {
+            // ---- rounds of the current bucket
+            for (;;) {
+                const uint32_t ncur = s_ncur;
+                if (!ncur || s_fail) break;  // (read after a barrier: the same for every thread)
+                t_rounds++;
+                const uint32_t tau32 = uint32_t(tau);
+                for (uint32_t w0 = 0; w0 < ncur; w0 += W * 64) {
+                    // phase A: this warp's items w0 + 64 warp + 2 lane + t
+                    uint32_t beg[2], deg[2], dv[2], fresh_s[2];
+#pragma unroll
+                    for (int t = 0; t < 2; t++) {
+                        const uint32_t j = w0 + 64 * warp + 2 * lane + t;
+                        beg[t] = 0;
+                        deg[t] = 0;
+                        dv[t] = INF;
+                        fresh_s[t] = EMPTY;
+                        if (j < ncur) {
+                            const uint32_t x = qcur[j];
+                            if (!RN_BAD(x < MS, 12, j, x)) {
+                                const uint32_t k = key[x];
+                                const uint32_t y = k & SK_NODE;
+                                if (!RN_BAD(y < a.n_nodes, 13, x, y)) {
+                                    dv[t] = dist[x];
+                                    beg[t] = __ldg(&a.row_ptr[y]);
+                                    deg[t] = __ldg(&a.row_ptr[y + 1]) - beg[t];
+                                    uint32_t in_s = k & SK_IN_S;
+                                    if (!(k & SK_SEEN)) {
+                                        in_s = ((__ldg(&sbits[y >> 5]) >> (y & 31)) & 1u) ? SK_IN_S : 0u;
+                                        t_slot_arcs += deg[t];
+                                        if (in_s) fresh_s[t] = x;
+                                    }
+                                    key[x] = y | SK_SEEN | in_s;
+                                    if (RN_BAD(uint64_t(beg[t]) + deg[t] <= a.n_arcs, 14, y, beg[t])) deg[t] = 0;
+                                    t_scans++;
+                                    t_arcs += deg[t];
+                                }
+                            }
+                        }
+                    }
+#pragma unroll
+                    for (int t = 0; t < 2; t++) {
+                        const uint32_t fb = __ballot_sync(FULL, fresh_s[t] != EMPTY);
+                        if (fb) {
+                            uint32_t lb = 0;
+                            if (lane == 0) lb = atomicAdd(&s_nlist, uint32_t(__popc(fb)));
+                            const uint32_t at = __shfl_sync(FULL, lb, 0) + __popc(fb & lt);
+                            if (fresh_s[t] != EMPTY && at < MS) __stcg(&slist[at], fresh_s[t]);
+                        }
+                    }
+                    __syncthreads();  // every warp's items scanned before any relaxation
+                    // phase B: the arcs of this warp's items, 128 at a time
+                    const uint32_t mine = deg[0] + deg[1];
+                    uint32_t incl = mine;
+#pragma unroll
+                    for (int o = 1; o < 32; o <<= 1) {
+                        const uint32_t t = __shfl_up_sync(FULL, incl, o);
+                        if (lane >= uint32_t(o)) incl += t;
+                    }
+                    const uint32_t total = __shfl_sync(FULL, incl, 31);
+                    const uint32_t ex = incl - mine;
+                    bool wfail = false;
+                    for (uint32_t b0 = 0; b0 < total && !wfail; b0 += 32 * AP) {
+                        uint32_t y[AP], nd[AP];
+#pragma unroll
+                        for (int k = 0; k < AP; k++) {
+                            const uint32_t gi = b0 + 32 * k + lane;
+                            uint32_t l = 0;
+#pragma unroll
+                            for (uint32_t s = 16; s; s >>= 1)
+                                if (__shfl_sync(FULL, ex, l + s) <= gi) l += s;
+                            const uint32_t o = gi - __shfl_sync(FULL, ex, l);
+                            const uint32_t d0 = __shfl_sync(FULL, deg[0], l);
+                            const uint32_t bb0 = __shfl_sync(FULL, beg[0], l);
+                            const uint32_t bb1 = __shfl_sync(FULL, beg[1], l);
+                            const uint32_t v0 = __shfl_sync(FULL, dv[0], l);
+                            const uint32_t v1 = __shfl_sync(FULL, dv[1], l);
+                            const bool second = o >= d0;
+                            const uint32_t ai = second ? bb1 + (o - d0) : bb0 + o;
+                            nd[k] = INF;
+                            y[k] = 0;
+                            if (gi < total && !RN_BAD(ai < a.n_arcs, 15, gi, ai)) {
+                                const uint2 arc = __ldg(&a.adj[ai]);
+                                y[k] = arc.x;
+                                nd[k] = (second ? v1 : v0) + arc.y;
+                            }
+                        }
+                        uint32_t h[AP], kv[AP];
+#pragma unroll
+                        for (int k = 0; k < AP; k++) {
+                            if (nd[k] <= bound && RN_BAD(y[k] < a.n_nodes, 16, b0 + 32 * k + lane, y[k])) nd[k] = INF;
+                            h[k] = (y[k] * 0x9E3779B1u) >> (32 - log2u(MS));
+                            kv[k] = nd[k] <= bound ? ((volatile uint32_t *)key)[h[k]] : 0u;
+                        }
+                        uint32_t ins_count = 0;
+                        bool full = false;
+#pragma unroll
+                        for (int k = 0; k < AP; k++) {
+                            bool ins = false;
+                            if (nd[k] > bound) {
+                                h[k] = EMPTY;
+                            } else if ((kv[k] & SK_NODE) != y[k]) {
+                                const uint32_t h0 = kv[k] == SK_EMPTY ? h[k] : (h[k] + 1) & (MS - 1);
+                                h[k] = src_slot<MS>(key, y[k], h0, &ins);
+                            }
+                            ins_count += ins;
+                            full |= nd[k] <= bound && h[k] == EMPTY;
+                        }
+                        const uint32_t ins_tot = __reduce_add_sync(FULL, ins_count);
+                        uint32_t fnow = 0;
+                        if (lane == 0) fnow = ins_tot ? atomicAdd(&s_fill, ins_tot) + ins_tot : *(volatile uint32_t *)&s_fill;
+                        fnow = __shfl_sync(FULL, fnow, 0);
+                        uint32_t old[AP];
+#pragma unroll
+                        for (int k = 0; k < AP; k++) old[k] = h[k] != EMPTY ? atomicMin(&dist[h[k]], nd[k]) : 0u;
+                        uint32_t kf[AP];
+#pragma unroll
+                        for (int k = 0; k < AP; k++)
+                            kf[k] = h[k] != EMPTY && nd[k] < old[k]
+                                        ? atomicOr(&key[h[k]], nd[k] < tau32 ? (SK_DIRTY | SK_QUEUED) : SK_DIRTY)
+                                        : SK_QUEUED;
+#pragma unroll
+                        for (int k = 0; k < AP; k++) {
+                            const bool push = h[k] != EMPTY && nd[k] < old[k] && nd[k] < tau32 && !(kf[k] & SK_QUEUED);
+                            const uint32_t pb = __ballot_sync(FULL, push);
+                            if (pb) {
+                                uint32_t pbase = 0;
+                                if (lane == 0) pbase = atomicAdd(&s_nnext, uint32_t(__popc(pb)));
+                                const uint32_t qi = __shfl_sync(FULL, pbase, 0) + __popc(pb & lt);
+                                if (push && qi < QS) qnext[qi] = h[k];
+                            }
+                        }
+                        if (__any_sync(FULL, full) || fnow > a.max_fill) {
+                            wfail = true;
+                            if (lane == 0) s_fail = 1;
+                        }
+                    }
+                    __syncthreads();  // this wave's relaxations before the next wave's scans
+                }
+                if (tid == 0) {
+                    s_ncur = min(s_nnext, QS);
+                    s_nnext = 0;
+                }
+                uint32_t *t = qcur;
+                qcur = qnext;
+                qnext = t;
+                __syncthreads();
+            }
+            {
+                const uint32_t t = uint32_t(clock());
+                t_cyc_round += t - t_mark;
+                t_mark = t;
+            }
+            if (s_fail) break;
+            // ---- the near queue is empty: the next bucket
+            t_bounds++;
+            if (tid == 0) {
+                if (kcp) s_bound = min(s_bound, __ldcg(a.theta_live));
+                s_nq = 0;
+                s_min = INF;
+            }
+            __syncthreads();
+            bound = s_bound;
+            const uint64_t top = uint64_t(bound) + 1;
+            const uint64_t tau2 = tau + delta < top ? tau + delta : top;
+            collect(tau2);
+            __syncthreads();
+            const uint32_t m = s_min;
+            uint32_t nq = s_nq;
+            if (m == INF || m > bound) break;
+            if (m >= tau2) {
+                const uint64_t t = (uint64_t(m) / delta + 1) * delta;
+                tau = t < top ? t : top;
+                __syncthreads();  // every thread has read s_nq and s_min
+                if (tid == 0) {
+                    s_nq = 0;
+                    s_min = INF;
+                }
+                __syncthreads();
+                collect(tau);
+                __syncthreads();
+                nq = s_nq;
+            } else {
+                tau = tau2;
+            }
+            __syncthreads();  // every thread has read the boundary's results
+            if (tid == 0) s_ncur = min(nq, QS);
+            __syncthreads();
+            {
+                const uint32_t t = uint32_t(clock());
+                t_cyc_bound += t - t_mark;
+                t_mark = t;
+            }
+        }
+        __syncthreads();  // the last boundary's (or round's) reads of shared state are done
+
+        const uint32_t fill = s_fill;
+        if (!s_fail) {
+            const uint32_t n_list = min(s_nlist, MS);
+            // the pairs: the listed S nodes (k closest pairs: those within the lowered bound);
+            // warp w writes list entries [w per, (w + 1) per)
+            const uint32_t per = (n_list + W - 1) / W;
+            const uint32_t lo = min(n_list, warp * per), hi = min(n_list, lo + per);
+            uint32_t wc = hi - lo;
+            if (kcp) {
+                wc = 0;
+                for (uint32_t i = lo + lane; i - lane < hi; i += 32) {
+                    const bool in = i < hi && dist[__ldcg(&slist[i]) & (MS - 1)] <= bound;
+                    wc += __popc(__ballot_sync(FULL, in));
+                }
+            }
+            if (lane == 0) s_wcnt[warp] = wc;
+            __syncthreads();
+            uint32_t cnt = 0, before = 0;
+#pragma unroll
+            for (uint32_t w = 0; w < W; w++) {
+                if (w < warp) before += s_wcnt[w];
+                cnt += s_wcnt[w];
+            }
+            if (tid == 0) {
+                unsigned long long b = 0;
+                if (cnt) {
+                    b = atomicAdd(&a.ctl->pairs, (unsigned long long)cnt);
+                    if (a.inst_pairs) atomicAdd(&a.inst_pairs[inst], (unsigned long long)cnt);
+                }
+                s_base = b;
+                if (a.seg) a.seg[si] = make_uint2(uint32_t(b), cnt);
+                t_max_seg = max(t_max_seg, cnt);
+            }
+            __syncthreads();
+            unsigned long long pos = s_base + before;
+            for (uint32_t i0 = lo; i0 < hi; i0 += 32) {
+                const uint32_t i = i0 + lane;
+                bool ok = false;
+                uint32_t dd = 0, v = 0;
+                if (i < hi) {
+                    const uint32_t h = __ldcg(&slist[i]);
+                    const uint32_t y = key[h & (MS - 1)] & SK_NODE;
+                    if (!RN_BAD(h < MS && y < a.n_nodes, 17, h, y)) {
+                        dd = dist[h & (MS - 1)];
+                        ok = !kcp || dd <= bound;
+                        if (ok) v = __ldg(&a.iperm[y]);
+                    }
+                }
+                const uint32_t b = __ballot_sync(FULL, ok);
+                if (ok) {
+                    const unsigned long long idx = pos + __popc(b & lt);
+                    if (idx < a.out_cap) {
+                        a.out_key[idx] = prefix | (swap ? ((unsigned long long)v << a.vbits) | u
+                                                        : (u << a.vbits) | (unsigned long long)v);
+                        a.out_d[idx] = dd;
+                    }
+                    if (kcp) atomicAdd(&a.kcp_hist[dd >> a.hist_shift], 1u);
+                }
+                pos += __popc(b);
+            }
+            __syncthreads();  // the list and the map read before the map is cleared
+            for (uint32_t h4 = tid; h4 < MS / 4; h4 += NT) {
+                reinterpret_cast<uint4 *>(key)[h4] = make_uint4(SK_EMPTY, SK_EMPTY, SK_EMPTY, SK_EMPTY);
+                reinterpret_cast<uint4 *>(dist)[h4] = make_uint4(INF, INF, INF, INF);
+            }
+            if (kcp && cnt && warp == 0) {
+                const unsigned long long emitted = s_base + cnt;
+                const unsigned long long step = a.kcp_k / 64 + 1;
+                if (emitted >= a.kcp_k && (s_base < a.kcp_k || s_base / step != emitted / step)) kcp_lower_bound(a, lane);
+            }
+            if (tid == 0) {
+                t_slots += fill;
+                t_max_ball = max(t_max_ball, fill);
+                if (a.inst_ball) atomicMax(&a.inst_ball[inst], fill);
+            }
+        } else {
+            if (tid == 0)
+                a.failed[atomicAdd(&a.ctl->n_failed, 1u)] =
+                    make_uint4(si, bound, uint32_t(tau < 0xFFFFFFFFull ? tau : 0xFFFFFFFFull), fill);
+            for (uint32_t h = tid; h < MS; h += NT) {
+                key[h] = SK_EMPTY;
+                dist[h] = INF;
+            }
+        }
+        __syncthreads();  // the map is empty before the next source
+        const uint32_t t_end = uint32_t(clock());
+        t_cyc_emit += t_end - t_mark;
+        if (tid == 0 && a.inst_cycles)
+            atomicAdd(&a.inst_cycles[inst], (unsigned long long)(t_end - t_source) / ((3 * 8192) / MS));
+    }
+    // telemetry: lane sums per warp, the rest from thread 0
+    const unsigned long long ws_ = warp_sum64(t_scans), wa_ = warp_sum64(t_arcs), wsa_ = warp_sum64(t_slot_arcs);
+    if (lane == 0) {
+        atomicAdd(&a.ctl->scans, ws_);
+        atomicAdd(&a.ctl->dirty_groups, ws_);
+        atomicAdd(&a.ctl->round_items, ws_);
+        atomicAdd(&a.ctl->round_arcs, wa_);
+        atomicAdd(&a.ctl->slot_arcs, wsa_);
+    }
+    if (tid == 0) {
+        atomicAdd(&a.ctl->slots, t_slots);
+        atomicAdd(&a.ctl->slot_lanes, t_slots);
+        atomicAdd(&a.ctl->rounds, t_rounds);
+        atomicAdd(&a.ctl->boundaries, t_bounds);
+        atomicAdd(&a.ctl->cyc_round, t_cyc_round);
+        atomicAdd(&a.ctl->cyc_bound, t_cyc_bound);
+        atomicAdd(&a.ctl->cyc_emit, t_cyc_emit);
+        atomicMax(&a.ctl->max_fill, t_max_ball);
+        atomicMax(&a.ctl->src_max_ball, t_max_ball);
+        atomicMax(&a.ctl->max_seg, t_max_seg);
+    }
+}
+
 // ------------------------------------------------- order without a sort ----
 // The warp search writes every source's pairs contiguously (seg[si] = first pair, count);
 // with the sources in increasing original id, the (u, v) order is the sources' segments
@@ -2483,6 +2913,21 @@ static void launch_source(const SearchArgs &a, uint32_t grid, cudaStream_t st) {
     RN_CUDA(cudaGetLastError());
 }
 
+// The cooperative search for sources whose maps have 4096 or 8192 slots: four warps per
+// source, as many blocks per SM as the warp search's maps of that size (6 or 3).
+constexpr uint32_t COOP_MS_MIN = 4096, COOP_W = 4;
+template <uint32_t MS>
+static void launch_coop(const SearchArgs &a, uint32_t grid, cudaStream_t st) {
+    constexpr uint32_t smem = src_words(MS) * 4;
+    static std::once_flag once[MAX_DEVICES];
+    std::call_once(once[attr_device()], [&] {
+        RN_CUDA(cudaFuncSetAttribute(k_source_coop<MS, COOP_W>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)));
+        RN_CUDA(cudaFuncSetAttribute(k_source_coop<MS, COOP_W>, cudaFuncAttributePreferredSharedMemoryCarveout, 100));
+    });
+    k_source_coop<MS, COOP_W><<<grid, COOP_W * 32, smem, st>>>(a);
+    RN_CUDA(cudaGetLastError());
+}
+
 template <uint32_t MS>
 static int source_occupancy() {
     int b = 0;
@@ -2493,12 +2938,19 @@ static int source_occupancy() {
 
 // Resident warp-search blocks per SM with maps of ms slots (after the first launch set
 // the kernel's shared-memory limit).
+template <uint32_t MS>
+static int coop_occupancy() {
+    int b = 0;
+    RN_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_source_coop<MS, COOP_W>, COOP_W * 32, src_words(MS) * 4));
+    return b;
+}
+
 static int source_blocks_per_sm(uint32_t ms) {
     switch (ms) {
         case 1024: return source_occupancy<1024>();
         case 2048: return source_occupancy<2048>();
-        case 4096: return source_occupancy<4096>();
-        default: return source_occupancy<8192>();
+        case 4096: return coop_occupancy<4096>();
+        default: return coop_occupancy<8192>();
     }
 }
 
@@ -2522,6 +2974,17 @@ static void source_launch(uint32_t ms, SearchArgs a, uint32_t items, Workspace *
     a.max_fill = ms * 7 / 8;
     a.gmap = nullptr;
     a.slist = ensure_slist(ws);
+    if (ms >= COOP_MS_MIN && !hier) {
+        // a block per source (its list: MS entries at blockIdx.x MS, within the lists of
+        // the warp search's resident blocks)
+        const uint32_t per_sm = (3 * 8192) / ms;
+        const uint32_t grid = std::max<uint32_t>(1, std::min<uint32_t>(items, uint32_t(ws->num_sms) * per_sm));
+        if (ms == 4096) launch_coop<4096>(a, grid, st);
+        else if (ms == 8192) launch_coop<8192>(a, grid, st);
+        else fail(RN_EINTERNAL, "cooperative map size must be 4096 or 8192");
+        ws->launches++;
+        return;
+    }
     const uint32_t per_block = src_warps(ms);
     const uint32_t resident = std::max<uint32_t>(1, uint32_t(ws->num_sms) * SRC_BLOCKS_PER_SM);
     const uint32_t grid = std::max<uint32_t>(1, std::min<uint32_t>((items + per_block - 1) / per_block, resident));

@@ -269,6 +269,32 @@ def test_source_search_routes(rn, oracle):
     assert st["tile_width"] == 1 and st["slot_lanes"] == st["slots"]
 
 
+@pytest.mark.parametrize("ball", [2500, 3400, 6500])
+def test_large_warp_maps(rn, oracle, ball):
+    """Balls that need 4096- or 8192-slot warp maps, searched by four warps per source:
+    first with no history (a 2048-slot map, overflow, the cooperative search again), then
+    with the measured balls (the cooperative search from the start); directed and
+    undirected graphs, k closest pairs on the same maps."""
+    e = I.road_graph(40_000, 110_800, 63)
+    R, S = I.disjoint_sets(e.n, 700, 5000, 64)
+    theta = int(np.sort(oracle.graph(e.n, e.src, e.dst, e.w).sssp(int(R[0]))[0])[ball])
+    for directed in (False, True):
+        og = oracle.graph(e.n, e.src, e.dst, e.w, undirected=not directed)
+        flags = rn.RN_REORDER | (0 if directed else rn.RN_UNDIRECTED)
+        g = load(rn, e, flags=flags, cfg={"tile_width": 1, "search_from": 1})
+        ref = og.join(R, S, theta)
+        for i in range(2):
+            assert_same(dev_join(rn, g, R, S, theta), ref, f"ball ~{ball} directed {directed} run {i}")
+            st = rn.rn_last_query_stats()
+            assert st["tile_width"] == 1 and st["blocks_per_sm"] >= 1, st
+        if not directed:
+            assert st["max_ball"] > 1792
+        k = max(1, len(ref) // 2)
+        kref = og.kcp(R, S, k, theta)
+        u, v, d = rn.rn_kcp(g, R, S, k, theta)
+        assert_same((u, v, d), kref, f"kcp ball ~{ball} directed {directed}")
+
+
 def test_long_segments_sorted(rn, oracle):
     """Sources with more than 256 pairs each (S dense around them): the warp search's
     segments are too long to place, and the pairs are radix sorted instead."""
