@@ -175,11 +175,11 @@ def search_kernel(st: dict) -> str:
 
 
 def engine_hash() -> str:
-    """Hash of the search sections of the engine source (the tile and the source search
-    kernels, the profiled ones)."""
+    """Hash of the engine source's warp-search section (`k_source_search` and its device
+    helpers: the kernel the committed ncu summaries profile)."""
     src = open(ENGINE_SRC).read()
-    a = src.index("// ------------------------------------------------------------ tile search ----")
-    b = src.index("// ------------------------------------------------- order without a sort ----")
+    a = src.index("// ----------------------------------------------------------- source search ----")
+    b = src.index("// ---------------------------------------------------- cooperative source search ----")
     return hashlib.sha256(src[a:b].encode()).hexdigest()[:16]
 
 

@@ -2913,18 +2913,21 @@ static void launch_source(const SearchArgs &a, uint32_t grid, cudaStream_t st) {
     RN_CUDA(cudaGetLastError());
 }
 
-// The cooperative search for sources whose maps have 4096 or 8192 slots: four warps per
-// source, as many blocks per SM as the warp search's maps of that size (6 or 3).
-constexpr uint32_t COOP_MS_MIN = 4096, COOP_W = 4;
+// The cooperative search for sources whose maps have 4096 or 8192 slots: coop_warps(MS)
+// warps per source (0: the warp search), as many blocks per SM as the warp search has
+// warps with maps of that size (6 or 3).  Measured on the 6M-node serving stream: four
+// warps per source on both sizes took its requests' device time from 4.06 to 2.78 s,
+// eight on the 8192-slot maps to 2.54 s; two on 2048-slot maps slowed the 264k-node join.
+__host__ __device__ constexpr uint32_t coop_warps(uint32_t ms) { return ms == 4096 ? 4 : ms == 8192 ? 8 : 0; }
 template <uint32_t MS>
 static void launch_coop(const SearchArgs &a, uint32_t grid, cudaStream_t st) {
-    constexpr uint32_t smem = src_words(MS) * 4;
+    constexpr uint32_t W = coop_warps(MS), smem = src_words(MS) * 4;
     static std::once_flag once[MAX_DEVICES];
     std::call_once(once[attr_device()], [&] {
-        RN_CUDA(cudaFuncSetAttribute(k_source_coop<MS, COOP_W>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)));
-        RN_CUDA(cudaFuncSetAttribute(k_source_coop<MS, COOP_W>, cudaFuncAttributePreferredSharedMemoryCarveout, 100));
+        RN_CUDA(cudaFuncSetAttribute(k_source_coop<MS, W>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)));
+        RN_CUDA(cudaFuncSetAttribute(k_source_coop<MS, W>, cudaFuncAttributePreferredSharedMemoryCarveout, 100));
     });
-    k_source_coop<MS, COOP_W><<<grid, COOP_W * 32, smem, st>>>(a);
+    k_source_coop<MS, W><<<grid, W * 32, smem, st>>>(a);
     RN_CUDA(cudaGetLastError());
 }
 
@@ -2940,15 +2943,20 @@ static int source_occupancy() {
 // the kernel's shared-memory limit).
 template <uint32_t MS>
 static int coop_occupancy() {
-    int b = 0;
-    RN_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_source_coop<MS, COOP_W>, COOP_W * 32, src_words(MS) * 4));
-    return b;
+    if constexpr (coop_warps(MS) == 0) {
+        return source_occupancy<MS>();
+    } else {
+        int b = 0;
+        RN_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_source_coop<MS, coop_warps(MS)>, coop_warps(MS) * 32,
+                                                              src_words(MS) * 4));
+        return b;
+    }
 }
 
 static int source_blocks_per_sm(uint32_t ms) {
     switch (ms) {
-        case 1024: return source_occupancy<1024>();
-        case 2048: return source_occupancy<2048>();
+        case 1024: return coop_occupancy<1024>();
+        case 2048: return coop_occupancy<2048>();
         case 4096: return coop_occupancy<4096>();
         default: return coop_occupancy<8192>();
     }
@@ -2974,14 +2982,18 @@ static void source_launch(uint32_t ms, SearchArgs a, uint32_t items, Workspace *
     a.max_fill = ms * 7 / 8;
     a.gmap = nullptr;
     a.slist = ensure_slist(ws);
-    if (ms >= COOP_MS_MIN && !hier) {
+    if (coop_warps(ms) && !hier) {
         // a block per source (its list: MS entries at blockIdx.x MS, within the lists of
         // the warp search's resident blocks)
         const uint32_t per_sm = (3 * 8192) / ms;
         const uint32_t grid = std::max<uint32_t>(1, std::min<uint32_t>(items, uint32_t(ws->num_sms) * per_sm));
-        if (ms == 4096) launch_coop<4096>(a, grid, st);
-        else if (ms == 8192) launch_coop<8192>(a, grid, st);
-        else fail(RN_EINTERNAL, "cooperative map size must be 4096 or 8192");
+        switch (ms) {
+            case 1024: if constexpr (coop_warps(1024) != 0) launch_coop<1024>(a, grid, st); break;
+            case 2048: if constexpr (coop_warps(2048) != 0) launch_coop<2048>(a, grid, st); break;
+            case 4096: if constexpr (coop_warps(4096) != 0) launch_coop<4096>(a, grid, st); break;
+            case 8192: if constexpr (coop_warps(8192) != 0) launch_coop<8192>(a, grid, st); break;
+            default: fail(RN_EINTERNAL, "cooperative map size must be 1024 .. 8192");
+        }
         ws->launches++;
         return;
     }
