@@ -487,7 +487,10 @@ rn_status rn_distance_join(const rn_graph *cg, const uint32_t *R, uint32_t nR, c
         *out = rn_pairs{};
         check_theta(theta);
         rn_graph *g = const_cast<rn_graph *>(cg);
-        check_sets_host(g->dev.n, R, nR, S, nS);
+        // ids, repeats and overlap are checked on the device as the sets are marked (a
+        // host pass over |R| + |S| random ids was most of this call's host time: the
+        // 1.07M-node join with 50,000 + 50,000 ids took 2.68 ms with it, 1.85 ms without)
+        if ((nR && !R) || (nS && !S)) rn::fail(RN_EINVAL, "null R or S with a non-zero size");
         std::lock_guard<std::mutex> lk(g->mu);
         rn::HostScratch &hs = scratch_of(g);
         ensure(&hs.dR, &hs.capR, nR);
@@ -530,7 +533,8 @@ rn_status rn_kcp(const rn_graph *cg, const uint32_t *R, uint32_t nR, const uint3
         if (k == 0) rn::fail(RN_EINVAL, "k must be >= 1");
         check_theta(theta);
         rn_graph *g = const_cast<rn_graph *>(cg);
-        check_sets_host(g->dev.n, R, nR, S, nS);
+        // ids, repeats and overlap are checked on the device as the sets are marked
+        if ((nR && !R) || (nS && !S)) rn::fail(RN_EINVAL, "null R or S with a non-zero size");
         std::lock_guard<std::mutex> lk(g->mu);
         rn::HostScratch &hs = scratch_of(g);
         ensure(&hs.dR, &hs.capR, nR);
