@@ -162,34 +162,41 @@ void log_stats(const char *kind, const rn_query_stats &st) {
 }
 
 // Host-side check of R and S (ids < n, no repeats, disjoint), for a precise message
-// before anything reaches the device.
-// The marks live in a per-thread array reused across calls and cleared entry by entry
-// afterwards, so a check costs O(|R| + |S|), not O(n).
+// before anything reaches the device.  The marks are two bitmaps (R's, S's) in per-thread
+// storage reused across calls and cleared word by word afterwards, so a check costs
+// O(|R| + |S|), not O(n), and touches n / 4 bytes at most (random ids into a byte per
+// node missed the caches on graphs of millions of nodes).
 void check_sets_host(uint32_t n, const uint32_t *R, uint32_t nR, const uint32_t *S, uint32_t nS) {
     if ((nR && !R) || (nS && !S)) rn::fail(RN_EINVAL, "null R or S with a non-zero size");
-    thread_local std::vector<uint8_t> mark;
-    if (mark.size() < n) mark.assign(n, 0);
-    struct Clear {  // leave the marks at zero however the check ends
+    thread_local std::vector<uint64_t> rb, sb;
+    const size_t words = (size_t(n) + 63) / 64;
+    if (rb.size() < words) {
+        rb.assign(words, 0);
+        sb.assign(words, 0);
+    }
+    struct Clear {  // leave the bitmaps at zero however the check ends
         const uint32_t *R, *S;
-        uint32_t nR, nS, n;
+        uint32_t nR, nS;
         ~Clear() {
-            for (uint32_t i = 0; i < nR; i++)
-                if (R[i] < n) mark[R[i]] = 0;
-            for (uint32_t i = 0; i < nS; i++)
-                if (S[i] < n) mark[S[i]] = 0;
+            for (uint32_t i = 0; i < nR; i++) rb[R[i] >> 6] = 0;
+            for (uint32_t i = 0; i < nS; i++) sb[S[i] >> 6] = 0;
         }
-    } clear{R, S, 0, 0, n};
+    } clear{R, S, 0, 0};
     for (uint32_t i = 0; i < nR; i++) {
-        if (R[i] >= n) rn::fail(RN_EINVAL, "R[" + std::to_string(i) + "] >= n");
-        if (mark[R[i]]) rn::fail(RN_EINVAL, "R repeats node " + std::to_string(R[i]));
-        mark[R[i]] = 1;
+        const uint32_t x = R[i];
+        if (x >= n) rn::fail(RN_EINVAL, "R[" + std::to_string(i) + "] >= n");
+        const uint64_t bit = uint64_t(1) << (x & 63);
+        if (rb[x >> 6] & bit) rn::fail(RN_EINVAL, "R repeats node " + std::to_string(x));
+        rb[x >> 6] |= bit;
         clear.nR = i + 1;
     }
     for (uint32_t i = 0; i < nS; i++) {
-        if (S[i] >= n) rn::fail(RN_EINVAL, "S[" + std::to_string(i) + "] >= n");
-        if (mark[S[i]] == 2) rn::fail(RN_EINVAL, "S repeats node " + std::to_string(S[i]));
-        if (mark[S[i]] == 1) rn::fail(RN_EINVAL, "node " + std::to_string(S[i]) + " is in both R and S");
-        mark[S[i]] = 2;
+        const uint32_t x = S[i];
+        if (x >= n) rn::fail(RN_EINVAL, "S[" + std::to_string(i) + "] >= n");
+        const uint64_t bit = uint64_t(1) << (x & 63);
+        if (sb[x >> 6] & bit) rn::fail(RN_EINVAL, "S repeats node " + std::to_string(x));
+        if (rb[x >> 6] & bit) rn::fail(RN_EINVAL, "node " + std::to_string(x) + " is in both R and S");
+        sb[x >> 6] |= bit;
         clear.nS = i + 1;
     }
 }
