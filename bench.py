@@ -61,7 +61,8 @@ def parse():
     ap.add_argument("--serve-requests", type=int, default=2000)
     ap.add_argument("--no-legs", action="store_true",
                     help="only the headline workload: no secondary legs and no CPU baseline")
-    ap.add_argument("--leg", default="", choices=["", "kcp_1m", "batched", "join_264k", "hierarchical", "served"],
+    ap.add_argument("--leg", default="", choices=["", "kcp_1m", "batched", "join_264k", "hierarchical", "served",
+                                                  "large_balls"],
                     help="run this one secondary leg alone (one GPU) and print its JSON object")
     return ap.parse_args()
 
@@ -363,6 +364,51 @@ def join_264k_leg(rn, steps: int, stream, flush, peak: float, peak_kind: str) ->
             "ms_per_join": med, "gteps": spec["alg_arcs"] / (med / 1e3) / 1e9,
             "launches": int(st["launches"]), "retried_tiles": st["retried_tiles"],
             "roofline": roofline(st, n, statistics.mean(search), "road264k_join", peak, peak_kind)}
+
+
+def large_balls_leg(rn, steps: int, stream, flush, peak: float, peak_kind: str) -> dict:
+    """The θ-join on the 1.07M-node graph at a θ whose balls hold about 3,300 nodes (near
+    the serving stream's: 4096- and 8192-slot maps, searched by four or eight warps per
+    source), from
+    the first 5,000 of the clustered R nodes against all 50,000 S nodes: pairs/s and the
+    cooperative search's roofline."""
+    import numpy as np
+    import torch
+
+    from paper_1607_07696_gb300 import inputs as I
+
+    w = I.c3_road_clustered()
+    e = w.graph
+    g = rn.rn_graph_load(e.src, e.dst, e.w, e.n, cfg={"search_from": rn.RN_FROM_R})
+    R = w.R[:5000]
+    dR = torch.as_tensor(R.astype(np.int32), device="cuda")
+    dS = torch.as_tensor(w.S.astype(np.int32), device="cuda")
+    out = rn.DevicePairs()
+    theta = 340_000
+    for _ in range(3):
+        rn.rn_distance_join_dev(g, dR, dS, theta, out, stream)
+    ms, search = [], []
+    for i in range(steps):
+        with torch.cuda.stream(stream):
+            flush.fill_(i & 0xFF)
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            n = rn.rn_distance_join_dev(g, dR, dS, theta, out, stream)
+            b.record(stream)
+        b.synchronize()
+        ms.append(a.elapsed_time(b))
+        st = rn.rn_last_query_stats()
+        search.append(st["search_ms"] + st["retry_ms"])
+    med = statistics.median(ms)
+    return {"workload": "road1070k_large_balls: 1.07M nodes, |R| = 5,000 of the clustered R, |S| = 50,000, "
+                        "theta 340,000 (balls of about 3,300 nodes, a few far larger)",
+            "theta": theta, "pairs": int(n), "value": n / (med / 1e3), "unit": UNIT,
+            "ms_per_join": med, "max_ball": int(st["max_ball"]),
+            "blocks_per_sm": int(st["blocks_per_sm"]), "launches": int(st["launches"]),
+            "retried_tiles": int(st["retried_tiles"]),
+            "roofline": dict(roofline(st, n, statistics.mean(search), "road1070k_large_balls", peak, peak_kind),
+                             kernel="k_source_coop")}
 
 
 def hier_leg(rn, steps: int) -> dict:
@@ -755,6 +801,8 @@ def run_leg(args):
         res = join_264k_leg(rn, steps, stream, flush, peak, peak_kind)
     elif args.leg == "hierarchical":
         res = hier_leg(rn, steps)
+    elif args.leg == "large_balls":
+        res = large_balls_leg(rn, steps, stream, flush, peak, peak_kind)
     else:
         res = serve_leg(rn, args.serve_requests)
     print(json.dumps({"leg": args.leg, **res}), flush=True)

@@ -1957,16 +1957,20 @@ __global__ void __launch_bounds__(W * 32, (3 * 8192) / MS) k_source_coop(SearchA
                 t_rounds++;
                 const uint32_t tau32 = uint32_t(tau);
                 for (uint32_t w0 = 0; w0 < ncur; w0 += W * 64) {
-                    // phase A: this warp's items w0 + 64 warp + 2 lane + t
+                    // phase A: the wave's items split evenly between the warps (a round
+                    // of 72 items gives each of four warps 18, not the first warp 64):
+                    // this warp's are j0 + 2 lane + t below j1
+                    const uint32_t cw = min(ncur - w0, W * 64), per = (cw + W - 1) / W;
+                    const uint32_t j0 = w0 + min(cw, warp * per), j1 = w0 + min(cw, (warp + 1) * per);
                     uint32_t beg[2], deg[2], dv[2], fresh_s[2];
 #pragma unroll
                     for (int t = 0; t < 2; t++) {
-                        const uint32_t j = w0 + 64 * warp + 2 * lane + t;
+                        const uint32_t j = j0 + 2 * lane + t;
                         beg[t] = 0;
                         deg[t] = 0;
                         dv[t] = INF;
                         fresh_s[t] = EMPTY;
-                        if (j < ncur) {
+                        if (j < j1) {
                             const uint32_t x = qcur[j];
                             if (!RN_BAD(x < MS, 12, j, x)) {
                                 const uint32_t k = key[x];
