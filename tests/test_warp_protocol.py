@@ -7,7 +7,9 @@ a push only when the flag update finds the slot unqueued, a full queue leaving t
 dirty, the bucket boundary's pass that takes the least dirty distance, collects the next
 bucket (or skips a gap to the bucket holding that distance) and clears stale queued flags,
 the map's fill limit -- and runs it with queues of 1 to 64 entries against the oracle's
-bounded Dijkstra (Section 4's local search), so every overflow path is exercised.  Any
+bounded Dijkstra (Section 4's local search), so every overflow path is exercised.  With
+waves of 256 and 512 items (every item of a wave scanned before any is relaxed) it is
+also the protocol of the cooperative search, whose four or eight warps share a wave.  Any
 serial order of one warp's atomics is a valid execution of the kernel, so the model's
 order is one of them.
 
@@ -36,9 +38,12 @@ def csr(e):
     return np.cumsum(rp).tolist(), dst[o].tolist(), w[o].tolist()
 
 
-def warp_search(rp, adj, wt, y0, bound, delta, ms, qs, max_fill):
+def warp_search(rp, adj, wt, y0, bound, delta, ms, qs, max_fill, wave=64):
     """Distances of every node within bound of y0, or None when the ball outgrows the
-    map's fill limit (the kernel then reports the source for a larger map)."""
+    map's fill limit (the kernel then reports the source for a larger map).  A round's
+    items are taken `wave` at a time, all scanned before any is relaxed: 64 is the warp
+    search's chunk, W x 64 the cooperative search's wave of W warps (whose warps' scans
+    all precede the wave's relaxations, behind a block barrier)."""
     key = [EMPTY_KEY] * ms
     dist = [INF] * ms
     shift = 32 - (ms.bit_length() - 1)
@@ -76,9 +81,9 @@ def warp_search(rp, adj, wt, y0, bound, delta, ms, qs, max_fill):
     while True:
         while qcur:  # rounds of the bucket
             nxt, nnext = [], 0
-            for c0 in range(0, len(qcur), 64):
+            for c0 in range(0, len(qcur), wave):
                 items = []
-                for x in qcur[c0:c0 + 64]:  # step A: take the item, clear its flags
+                for x in qcur[c0:c0 + wave]:  # step A: take the item, clear its flags
                     k = key[x]
                     key[x] = (k & NODE) | SEEN
                     items.append((dist[x], k & NODE))
@@ -117,8 +122,8 @@ def warp_search(rp, adj, wt, y0, bound, delta, ms, qs, max_fill):
     return {key[h] & NODE: dist[h] for h in range(ms) if key[h] != EMPTY_KEY}
 
 
-@pytest.mark.parametrize("seed", range(4))
-def test_protocol_matches_dijkstra(oracle, seed):
+@pytest.mark.parametrize("seed,wave", [(0, 64), (1, 64), (2, 64), (3, 64), (4, 256), (5, 512)])
+def test_protocol_matches_dijkstra(oracle, seed, wave):
     rng = np.random.default_rng(900 + seed)
     n = int(rng.integers(200, 800))
     e = I.road_graph(n, int(2.77 * n), 910 + seed)
@@ -134,7 +139,7 @@ def test_protocol_matches_dijkstra(oracle, seed):
             ref = {int(v): int(D[v]) for v in np.flatnonzero(D != unreached)}
             for delta in (med // 2 + 1, 16 * med, 1 << 24):
                 for qs in (1, 4, 64):
-                    got = warp_search(rp, adj, wt, int(s), bound, delta, ms, qs, ms * 7 // 8)
+                    got = warp_search(rp, adj, wt, int(s), bound, delta, ms, qs, ms * 7 // 8, wave)
                     runs += 1
                     if got is None:  # the ball is larger than the map may hold
                         overflow += 1
