@@ -38,8 +38,7 @@ METRIC = "join pairs/s"
 UNIT = "pairs/s"
 WORKLOADS = json.load(open(os.path.join(ROOT, "tests", "golden", "workloads.json")))
 ENGINE_SRC = os.path.join(ROOT, "paper_1607_07696_gb300", "csrc", "rn_engine.cu")
-PROFILES = {"road264k_join": os.path.join(ROOT, "profiles", "search_road264k.json"),
-            "road1070k_join": os.path.join(ROOT, "profiles", "search_road1070k.json"),
+PROFILES = {"road1070k_join": os.path.join(ROOT, "profiles", "search_road1070k.json"),
             "road1070k_kcp_k1000000": os.path.join(ROOT, "profiles", "search_road1070k_kcp.json")}
 
 
